@@ -1,0 +1,146 @@
+"""FP64 modified uni-directional path tracer (Sec. 1, Fig. 1): the nearest-surface
+search of a classic path tracer is replaced by one DDF query per bounce.
+Test infrastructure only (see the package docstring).
+
+The paper gives no pseudo-code; the readings used here:
+
+* Camera: pinhole; forward f = normalise(look_at - eye), right r = normalise(f x up),
+  up' = r x f; for pixel (x, y) (row 0 at the top) and jitter (j0, j1),
+  dir = normalise(f + px r + py up') with px = (2 (x + j0) / W - 1) tan(vfov/2) W/H and
+  py = (1 - 2 (y + j1) / H) tan(vfov/2).
+* Path id pid = (y W + x) spp + s. Draws are Philox4x32-10 words of counter
+  (pid lo, pid hi, bounce, 0), key = seed; bounce 0 gives the pixel jitter (words 0, 1).
+* The DDF is defined for origins in the bounding domain B (Sec. 3.1), the unit ball:
+  a primary ray is advanced to its entry point into the unit ball (t0 = max(0, -b -
+  sqrt(b^2 - c))); a primary ray that misses the ball (b^2 - c <= 0, or the ball lies
+  behind it) returns the environment radiance without a query.
+* Bounce b = 1 .. B (B = max queries per path): query (d, logit, n). Miss (logit <= 0):
+  radiance = throughput * env, stop. Hit at b = B: radiance = 0, stop. Otherwise the hit
+  point q = o + max(d, 0) w (Sec. 3.1, q = x + phi theta), the normal n of Eq. 3, new
+  origin q + 1e-4 n, new direction by cosine-weighted hemisphere sampling about n
+  (u0, u1 = words 0, 1 of bounce b): local (sqrt(u0) cos 2 pi u1, sqrt(u0) sin 2 pi u1,
+  sqrt(1 - u0)) mapped through the orthonormal basis of Duff et al. 2017 ("Building an
+  orthonormal basis, revisited"), and throughput *= albedo (Lambertian BRDF albedo/pi,
+  cosine pdf cos/pi).
+* Pixel value = mean over its spp samples, summed in sample order.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .philox import path_uniforms
+
+
+def _normalize(v):
+    return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
+
+def camera_basis(cam):
+    eye = np.array(cam.eye, np.float64)
+    f = _normalize(np.array(cam.look_at, np.float64) - eye)
+    r = _normalize(np.cross(f, np.array(cam.up, np.float64)))
+    u = np.cross(r, f)
+    return eye, f, r, u
+
+
+def primary_rays(cam, pids, spp: int):
+    """Primary rays of the given path ids, advanced to the unit ball.
+    Returns (o, w, alive) with alive False for rays that miss the ball."""
+    pids = np.asarray(pids, np.int64)
+    W, H = cam.width, cam.height
+    pix = pids // spp
+    x = (pix % W).astype(np.float64)
+    y = (pix // W).astype(np.float64)
+    uni = path_uniforms(cam.seed, pids.astype(np.uint64), 0)
+    eye, f, r, u = camera_basis(cam)
+    th = math.tan(math.radians(cam.vfov_deg) * 0.5)
+    px = (2.0 * (x + uni[:, 0]) / W - 1.0) * th * (W / H)
+    py = (1.0 - 2.0 * (y + uni[:, 1]) / H) * th
+    d = _normalize(f[None] + px[:, None] * r[None] + py[:, None] * u[None])
+    b = d @ eye
+    c = float(eye @ eye) - 1.0
+    disc = b * b - c
+    sq = np.sqrt(np.maximum(disc, 0.0))
+    alive = (disc > 0) & (-b + sq > 0)
+    t0 = np.maximum(0.0, -b - sq)
+    o = eye[None] + t0[:, None] * d
+    return o, d, alive
+
+
+def onb_duff(n):
+    """Orthonormal basis (b1, b2) completing unit normals n (Duff et al. 2017)."""
+    sign = np.where(n[:, 2] >= 0, 1.0, -1.0)
+    a = -1.0 / (sign + n[:, 2])
+    b = n[:, 0] * n[:, 1] * a
+    b1 = np.stack([1.0 + sign * n[:, 0] * n[:, 0] * a, sign * b, -sign * n[:, 0]], -1)
+    b2 = np.stack([b, sign + n[:, 1] * n[:, 1] * a, -n[:, 1]], -1)
+    return b1, b2
+
+
+def cosine_direction(n, u0, u1):
+    r = np.sqrt(u0)
+    phi = 2.0 * np.pi * u1
+    lx, ly, lz = r * np.cos(phi), r * np.sin(phi), np.sqrt(1.0 - u0)
+    b1, b2 = onb_duff(n)
+    return lx[:, None] * b1 + ly[:, None] * b2 + lz[:, None] * n
+
+
+def trace_paths(query_fn, cam, spp: int, bounces: int, pids, eps: float = 1e-4):
+    """Trace the given paths. query_fn(o, w) -> dict(dist, logit, normal) in float64.
+
+    Returns dict: radiance (per pid), min_abs_logit (smallest |logit| of any hit/miss
+    decision taken on the path; +inf if none), first-bounce AOVs (dist, logit, normal,
+    queried flag)."""
+    pids = np.asarray(pids, np.int64)
+    n = pids.size
+    rad = np.zeros(n)
+    min_logit = np.full(n, np.inf)
+    aov_d = np.full(n, np.nan)
+    aov_l = np.full(n, np.nan)
+    aov_n = np.full((n, 3), np.nan)
+    o, w, alive = primary_rays(cam, pids, spp)
+    rad[~alive] = cam.env
+    idx = np.nonzero(alive)[0]
+    o, w = o[idx], w[idx]
+    thr = np.ones(idx.size)
+    for b in range(1, bounces + 1):
+        if idx.size == 0:
+            break
+        res = query_fn(o, w)
+        d, lg, nm = res["dist"], res["logit"], res["normal"]
+        min_logit[idx] = np.minimum(min_logit[idx], np.abs(lg))
+        if b == 1:
+            aov_d[idx], aov_l[idx], aov_n[idx] = d, lg, nm
+        hit = lg > 0
+        miss = ~hit
+        rad[idx[miss]] = thr[miss] * cam.env
+        if b == bounces:
+            rad[idx[hit]] = 0.0
+            break
+        keep = np.nonzero(hit)[0]
+        idx, o, w, d, nm, thr = idx[keep], o[keep], w[keep], d[keep], nm[keep], thr[keep]
+        q = o + np.maximum(d, 0.0)[:, None] * w
+        o = q + eps * nm
+        uni = path_uniforms(cam.seed, pids[idx].astype(np.uint64), b)
+        w = cosine_direction(nm, uni[:, 0], uni[:, 1])
+        thr = thr * cam.albedo
+    return {"radiance": rad, "min_abs_logit": min_logit, "dist": aov_d, "logit": aov_l,
+            "normal": aov_n}
+
+
+def render_pixels(query_fn, cam, spp: int, bounces: int, pixels):
+    """Per-pixel mean radiance of the listed pixel indices (y W + x), plus per-path info."""
+    pixels = np.asarray(pixels, np.int64)
+    pids = (pixels[:, None] * spp + np.arange(spp)[None, :]).ravel()
+    res = trace_paths(query_fn, cam, spp, bounces, pids)
+    rad = res["radiance"].reshape(-1, spp)
+    img = np.zeros(pixels.size)
+    for s in range(spp):
+        img += rad[:, s]
+    img /= spp
+    res["image"] = img
+    res["pids"] = pids
+    return res
