@@ -1,0 +1,212 @@
+/*
+ * ddf.h - C ABI of the GB300 (sm_103a) neural directed-distance-field library.
+ *
+ * The method (arXiv 2306.16142): a directed distance field phi(x, theta) gives, for a point x
+ * in the bounding domain B and a viewing direction theta, the distance to the first surface
+ * point along the ray, and a visibility bit saying whether the ray meets the surface at all
+ * (Sec. 3.1). The field is stored as an MLP (Sec. 4.1), its surface normal comes from the
+ * gradient of the field with respect to the query point (Eq. 3, Sec. 4.2), it is rendered by a
+ * path tracer that replaces the nearest-triangle search with one field query per bounce
+ * (Sec. 1, Fig. 1) and it is trained on rays labelled against a triangle mesh (Sec. 5).
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an int status: DDF_OK (0) or a negative DDF_ERR_* code. The text of
+ *    the last error of the calling thread is returned by ddf_last_error().
+ *  - Array arguments named d_* or documented as "device" are device pointers owned by the
+ *    caller; the library never frees them. Arguments documented as "host" are host pointers.
+ *  - Rays are two row-major (n, 3) float32 arrays: origins o and unit directions w
+ *    (normalisation is the caller's job). n is int64_t; n == 0 is a no-op returning DDF_OK.
+ *  - Calls are asynchronous and ordered on the given cudaStream_t (0 = legacy default
+ *    stream) unless documented as synchronous. All device memory the library allocates
+ *    belongs to a handle and is released by the handle's destroy function.
+ *  - Handles are not thread-safe: one handle must not be used by two calls at once.
+ *
+ * Network weights are exchanged as one flat float32 blob
+ *     [W_1, b_1, W_2, b_2, ..., W_L, b_L, W_out, b_out]
+ * with every W row-major [out][in] (W_1: width x E, W_l: width x width, W_out: 2 x width,
+ * E = 6 + 6 * in_freqs). Output 0 is the distance, output 1 the hit logit (hit <=> logit > 0).
+ */
+#ifndef DDF_H
+#define DDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#if defined(__GNUC__)
+#define DDF_API __attribute__((visibility("default")))
+#else
+#define DDF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define DDF_OK 0
+#define DDF_ERR_INVALID_ARG (-1) /* a pointer, size or shape argument is invalid          */
+#define DDF_ERR_CUDA (-2)        /* a CUDA runtime call or kernel launch failed             */
+#define DDF_ERR_OOM (-3)         /* a device allocation failed                              */
+#define DDF_ERR_UNSUPPORTED (-4) /* shape / precision combination not built into the library */
+#define DDF_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up                      */
+#define DDF_ERR_NUMERIC (-6)     /* a non-finite value where a finite one is required       */
+
+/* ---- precisions of the hidden-layer GEMMs ---------------------------------------------- */
+#define DDF_FP32 0 /* FP32 SIMT FMA, FP32 accumulate (the reference GPU path)               */
+#define DDF_BF16 1 /* BF16 tcgen05 tensor-core MMAs, FP32 accumulate in tensor memory       */
+#define DDF_FP8 2  /* FP8 E4M3 tcgen05 MMAs with per-output-channel weight scales and
+                      per-row activation scales, FP32 accumulate                             */
+
+typedef struct ddf_net_s* ddf_net;
+typedef struct ddf_mesh_s* ddf_mesh;
+
+/* Network architecture (Sec. 4.1 / 5.1): input encoding with in_freqs Fourier features per
+ * coordinate (0 = raw 6-D input; even, <= 20), hidden_layers (1..16) ReLU layers of width
+ * units (16..512, a multiple of 16), and a 2-unit linear output layer. */
+typedef struct {
+    int in_freqs;
+    int width;
+    int hidden_layers;
+    int precision; /* DDF_FP32 / DDF_BF16 / DDF_FP8 */
+} ddf_arch;
+
+/* Pinhole camera (Z-up scenes rendered from several azimuth / polar angles, Fig. 4).
+ * Pixel (x, y), row 0 at the top; jitter and every path's draws come from Philox4x32-10
+ * keyed by seed. albedo: grey Lambertian albedo of the object; env: constant environment
+ * radiance returned by rays that miss it. */
+typedef struct {
+    float eye[3], look_at[3], up[3];
+    float vfov_deg;
+    int width, height;
+    uint64_t seed;
+    float albedo, env;
+} ddf_camera;
+
+/* Adam hyper-parameters (the paper trains with Adam, Sec. 5.1). */
+typedef struct {
+    float lr, beta1, beta2, eps;
+} ddf_adam;
+
+/* Library version string (static storage). */
+DDF_API const char* ddf_version(void);
+
+/* Text of the last error raised on the calling thread ("" if none). Thread-local storage. */
+DDF_API const char* ddf_last_error(void);
+
+/* ---- network handle -------------------------------------------------------------------- */
+
+/* Create a network on the current device from a HOST float32 weight blob of nbytes bytes
+ * (layout above). Copies the weights into device FP32 masters and packs the precision's
+ * working copy. Synchronous. Errors: INVALID_ARG (bad arch / size), UNSUPPORTED, OOM, CUDA. */
+DDF_API int ddf_create(const ddf_arch* arch, const float* host_weights, size_t nbytes, ddf_net* out);
+
+/* Create a field handle that evaluates the closed-form DDF of a sphere of radius r centred
+ * at the origin (distance, logit = +1 on a hit / -1 on a miss, gradient q / sqrt(b^2 - c)),
+ * for checking the renderer against exact answers. Synchronous. */
+DDF_API int ddf_sphere_create(float radius, ddf_net* out);
+
+/* Release a handle and all device memory it owns. Synchronous. NULL is a no-op. */
+DDF_API int ddf_destroy(ddf_net net);
+
+/* Switch the hidden-layer GEMM precision; repacks the working copy from the FP32 masters.
+ * Synchronous. UNSUPPORTED if the precision is not built for this architecture. */
+DDF_API int ddf_set_precision(ddf_net net, int precision);
+
+/* Number of float32 values in the weight blob of this network. */
+DDF_API int ddf_num_params(ddf_net net, int64_t* out);
+
+/* Replace the FP32 masters with a DEVICE blob (n_params floats) and repack, ordered on
+ * stream. Adam moments are kept. */
+DDF_API int ddf_set_weights(ddf_net net, const float* d_weights, size_t nbytes, cudaStream_t stream);
+
+/* Copy the FP32 masters into a DEVICE buffer (n_params floats), ordered on stream. */
+DDF_API int ddf_get_weights(ddf_net net, float* d_out, size_t nbytes, cudaStream_t stream);
+
+/* ---- query ------------------------------------------------------------------------------ */
+
+/* The batched DDF query (Sec. 4.1, MLP_w(x, theta)): for each ray i,
+ *   dist[i]  = network distance output,
+ *   hit[i]   = 1 if the hit logit > 0 else 0,
+ *   logit[i] = the hit logit                                   (nullable),
+ *   normals[3i..3i+2] = Eq. 3 normal n = kappa g / |g|, g = d dist / d o (the gradient of the
+ *   distance output with respect to the query origin, Sec. 4.2), kappa chosen so that
+ *   n . w < 0; n = -w when g = 0. Written for rows with hit[i] = 1 only (nullable).
+ * All arrays are device arrays of n rows. */
+DDF_API int ddf_query(ddf_net net, const float* d_origins, const float* d_dirs, int64_t n, float* d_dist,
+              uint8_t* d_hit, float* d_logit, float* d_normals, cudaStream_t stream);
+
+/* ---- renderer --------------------------------------------------------------------------- */
+
+/* The modified uni-directional path tracer (Sec. 1, Fig. 1) as a wavefront loop on the
+ * device: camera rays are advanced to the unit ball (the field's domain B); each bounce
+ * queries the field for every live path (distance, hit, Eq. 3 normal), moves hit paths to
+ * q = o + max(d, 0) w + 1e-4 n, samples a cosine-weighted direction about n, multiplies the
+ * throughput by albedo and compacts the survivors; a miss returns throughput * env; a hit at
+ * the last of `bounces` queries returns 0. image: DEVICE float32 H x W, overwritten with the
+ * mean over spp samples of each pixel. Paths are processed in waves of at most 2^24 and the
+ * per-path result is independent of compaction order. The handle keeps its wavefront
+ * buffers between calls. */
+DDF_API int ddf_render(ddf_net net, const ddf_camera* cam, int spp, int bounces, float* d_image,
+               cudaStream_t stream);
+
+/* Number of field queries issued per bounce by the last ddf_render on this handle
+ * (counts[b-1] for b = 1..bounces; HOST array of max_bounces entries). Synchronises with
+ * the stream of that render. */
+DDF_API int ddf_render_stats(ddf_net net, int64_t* host_counts, int max_bounces);
+
+/* ---- labelling -------------------------------------------------------------------------- */
+
+/* Create a mesh from HOST float32 vertices (nv x 3) and int32 triangles (nt x 3), copied to
+ * the device together with per-triangle data for the labeller. Synchronous. */
+DDF_API int ddf_mesh_create(const float* host_verts, int64_t nv, const int32_t* host_tris, int64_t nt,
+                    ddf_mesh* out);
+DDF_API int ddf_mesh_destroy(ddf_mesh mesh);
+
+/* Ray labelling for training data (Sec. 5; the nearest-triangle search of Sec. 1): for each
+ * ray the nearest Moeller-Trumbore hit over all triangles with t > 0, barycentric bounds
+ * inclusive, ties to the lowest triangle index. Outputs (device, n rows): dist = t rounded
+ * to float32 (+inf on a miss), hit (0/1), tri (index or -1; nullable). A float32 pass
+ * with rigorous error bounds decides every clear case; every grazing or near-tie
+ * (ray, triangle) pair is re-tested in float64 with a fixed, FMA-free order of operations,
+ * and the winning triangle's t is evaluated in float64, so hit / tri / dist equal those of
+ * a float64 Moeller-Trumbore search bit for bit. */
+DDF_API int ddf_label_rays(ddf_mesh mesh, const float* d_origins, const float* d_dirs, int64_t n,
+                   float* d_dist, uint8_t* d_hit, int32_t* d_tri, cudaStream_t stream);
+
+/* Number of float64 (ray, triangle) evaluations of the last ddf_label_rays on this mesh:
+ * host_counts[0] = re-tests of ambiguous pairs, host_counts[1] = final-distance evaluations.
+ * Synchronises with the stream of that call. */
+DDF_API int ddf_label_stats(ddf_mesh mesh, int64_t* host_counts);
+
+/* ---- training ---------------------------------------------------------------------------- */
+
+/* Reverse pass of the network for output cotangents (g_dist, g_logit) (device, n each):
+ *   d_gweights (device, n_params floats) = sum over rays of d(g_dist*dist + g_logit*logit)/dW,
+ *   overwritten, in the blob layout;
+ *   d_ginput (device, n x 6, nullable)    = the same derivative with respect to (o, w).
+ * Activations are recomputed from (o, w) in row chunks that fit the handle's workspace limit,
+ * so no forward state is kept between the forward and this call. Deterministic: the same
+ * inputs give bit-identical outputs. */
+DDF_API int ddf_backward(ddf_net net, const float* d_origins, const float* d_dirs, int64_t n,
+                 const float* d_gdist, const float* d_glogit, float* d_gweights, float* d_ginput,
+                 cudaStream_t stream);
+
+/* One optimisation step on labelled rays: loss = mean over rays with hit_gt = 1 of
+ * |dist - dist_gt| + mean over all rays of BCE-with-logits(logit, hit_gt); its gradient by
+ * the reverse pass; one Adam step on the FP32 masters (step counter kept by the handle);
+ * the working copy repacked. d_loss (device float scalar, nullable) receives the loss before
+ * the update. */
+DDF_API int ddf_train_step(ddf_net net, const float* d_origins, const float* d_dirs,
+                   const float* d_dist_gt, const uint8_t* d_hit_gt, int64_t n,
+                   const ddf_adam* opt, float* d_loss, cudaStream_t stream);
+
+/* Cap, in bytes, of the activation workspace used by ddf_backward / ddf_train_step
+ * (default 1 GiB). Smaller caps process the batch in more row chunks (recomputation). */
+DDF_API int ddf_set_workspace_limit(ddf_net net, size_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDF_H */

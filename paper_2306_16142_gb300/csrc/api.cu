@@ -1,0 +1,342 @@
+// C ABI entry points: argument checking, handle management and dispatch.
+#include <stdarg.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "ddf_internal.cuh"
+
+namespace ddf {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int num_sms() {
+    static int sms[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!sms[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        sms[dev] = v > 0 ? v : 1;
+    }
+    return sms[dev];
+}
+
+NetLayout make_layout(int in_freqs, int width, int L) {
+    NetLayout lay;
+    memset(&lay, 0, sizeof(lay));
+    lay.in_freqs = in_freqs;
+    lay.E = 6 + 6 * in_freqs;
+    lay.width = width;
+    lay.L = L;
+    int64_t off = 0;
+    for (int l = 0; l <= L; ++l) {
+        const int64_t out = (l == L) ? 2 : width;
+        const int64_t in = (l == 0) ? lay.E : width;
+        lay.w_off[l] = off;
+        off += out * in;
+        lay.b_off[l] = off;
+        off += out;
+    }
+    lay.n_params = off;
+    return lay;
+}
+
+int field_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
+                const int* d_count, float* dist, float* logit, uint8_t* hit, float* normals,
+                cudaStream_t stream) {
+    if (net->is_sphere) return sphere_query(net, o, w, n, d_count, dist, logit, hit, normals, stream);
+    if (net->precision == DDF_FP32)
+        return mlp_fp32_query(net, o, w, n, d_count, dist, logit, hit, normals, stream);
+    return mlp_tc_query(net, o, w, n, d_count, dist, logit, hit, normals, stream);
+}
+
+}  // namespace ddf
+
+using namespace ddf;
+
+namespace {
+
+int check_arch(const ddf_arch* a) {
+    if (!a) return fail(DDF_ERR_INVALID_ARG, "arch is NULL");
+    if (a->in_freqs < 0 || a->in_freqs > kMaxFreqs || (a->in_freqs & 1))
+        return fail(DDF_ERR_INVALID_ARG, "in_freqs must be even and in [0, %d]", kMaxFreqs);
+    if (a->width < 16 || a->width > kMaxWidth || (a->width % 16))
+        return fail(DDF_ERR_INVALID_ARG, "width must be a multiple of 16 in [16, %d]", kMaxWidth);
+    if (a->hidden_layers < 1 || a->hidden_layers > kMaxLayers)
+        return fail(DDF_ERR_INVALID_ARG, "hidden_layers must be in [1, %d]", kMaxLayers);
+    if (a->precision != DDF_FP32 && a->precision != DDF_BF16 && a->precision != DDF_FP8)
+        return fail(DDF_ERR_INVALID_ARG, "unknown precision %d", a->precision);
+    return DDF_OK;
+}
+
+void free_net(ddf_net_s* n) {
+    if (!n) return;
+    tc_free(n);
+    cudaFree(n->master);
+    cudaFree(n->master_t);
+    cudaFree(n->adam_m);
+    cudaFree(n->adam_v);
+    cudaFree(n->train_ws);
+    cudaFree(n->render_ws);
+    cudaFree(n->render_counts);
+    delete n;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ddf_version(void) { return "ddf-gb300 0.1 (sm_103a)"; }
+
+const char* ddf_last_error(void) { return g_err; }
+
+int ddf_create(const ddf_arch* arch, const float* host_weights, size_t nbytes, ddf_net* out) {
+    if (!out) return fail(DDF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_arch(arch);
+    if (rc) return rc;
+    if (!host_weights) return fail(DDF_ERR_INVALID_ARG, "weights are NULL");
+    NetLayout lay = make_layout(arch->in_freqs, arch->width, arch->hidden_layers);
+    if (nbytes != sizeof(float) * (size_t)lay.n_params)
+        return fail(DDF_ERR_INVALID_ARG, "weight blob has %zu bytes, architecture needs %zu", nbytes,
+                    sizeof(float) * (size_t)lay.n_params);
+    if (arch->precision != DDF_FP32 && !tc_supported(lay, arch->precision))
+        return fail(DDF_ERR_UNSUPPORTED, "precision %d is not built for width %d / E %d",
+                    arch->precision, lay.width, lay.E);
+    ddf_net_s* n = new ddf_net_s();
+    n->lay = lay;
+    n->precision = arch->precision;
+    cudaGetDevice(&n->device);
+    cudaError_t e = cudaMalloc(&n->master, nbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&n->master_t, nbytes);
+    if (e != cudaSuccess) {
+        free_net(n);
+        return fail(e == cudaErrorMemoryAllocation ? DDF_ERR_OOM : DDF_ERR_CUDA, "cudaMalloc: %s",
+                    cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(n->master, host_weights, nbytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_net(n);
+        return fail(DDF_ERR_CUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+    }
+    rc = build_transposed(n, 0);
+    if (!rc && n->precision != DDF_FP32) rc = tc_pack(n, n->precision, 0);
+    if (!rc) {
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) rc = fail(DDF_ERR_CUDA, "create: %s", cudaGetErrorString(e));
+    }
+    if (rc) {
+        free_net(n);
+        return rc;
+    }
+    *out = n;
+    return DDF_OK;
+}
+
+int ddf_sphere_create(float radius, ddf_net* out) {
+    if (!out) return fail(DDF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!(radius > 0.f) || !(radius < 1e30f)) return fail(DDF_ERR_INVALID_ARG, "radius must be > 0");
+    ddf_net_s* n = new ddf_net_s();
+    n->is_sphere = true;
+    n->sphere_r = radius;
+    n->lay = make_layout(0, 16, 1);
+    cudaGetDevice(&n->device);
+    *out = n;
+    return DDF_OK;
+}
+
+int ddf_destroy(ddf_net net) {
+    if (!net) return DDF_OK;
+    cudaDeviceSynchronize();
+    free_net(net);
+    return DDF_OK;
+}
+
+int ddf_set_precision(ddf_net net, int precision) {
+    if (!net) return fail(DDF_ERR_INVALID_ARG, "net is NULL");
+    if (net->is_sphere) return fail(DDF_ERR_INVALID_ARG, "sphere field has no precision");
+    if (precision == DDF_FP32) {
+        net->precision = DDF_FP32;
+        return DDF_OK;
+    }
+    if (precision != DDF_BF16 && precision != DDF_FP8)
+        return fail(DDF_ERR_INVALID_ARG, "unknown precision %d", precision);
+    if (!tc_supported(net->lay, precision))
+        return fail(DDF_ERR_UNSUPPORTED, "precision %d is not built for width %d / E %d", precision,
+                    net->lay.width, net->lay.E);
+    int rc = tc_pack(net, precision, 0);
+    if (rc) return rc;
+    DDF_CUDA_TRY(cudaDeviceSynchronize());
+    net->precision = precision;
+    return DDF_OK;
+}
+
+int ddf_num_params(ddf_net net, int64_t* out) {
+    if (!net || !out) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    *out = net->is_sphere ? 0 : net->lay.n_params;
+    return DDF_OK;
+}
+
+int ddf_set_weights(ddf_net net, const float* d_weights, size_t nbytes, cudaStream_t stream) {
+    if (!net || !d_weights) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    if (net->is_sphere) return fail(DDF_ERR_INVALID_ARG, "sphere field has no weights");
+    if (nbytes != sizeof(float) * (size_t)net->lay.n_params)
+        return fail(DDF_ERR_INVALID_ARG, "weight blob size mismatch");
+    DDF_CUDA_TRY(cudaMemcpyAsync(net->master, d_weights, nbytes, cudaMemcpyDeviceToDevice, stream));
+    int rc = build_transposed(net, stream);
+    if (rc) return rc;
+    if (net->tc) return tc_pack(net, net->precision, stream);
+    return DDF_OK;
+}
+
+int ddf_get_weights(ddf_net net, float* d_out, size_t nbytes, cudaStream_t stream) {
+    if (!net || !d_out) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    if (net->is_sphere) return fail(DDF_ERR_INVALID_ARG, "sphere field has no weights");
+    if (nbytes != sizeof(float) * (size_t)net->lay.n_params)
+        return fail(DDF_ERR_INVALID_ARG, "weight blob size mismatch");
+    DDF_CUDA_TRY(cudaMemcpyAsync(d_out, net->master, nbytes, cudaMemcpyDeviceToDevice, stream));
+    return DDF_OK;
+}
+
+int ddf_query(ddf_net net, const float* d_origins, const float* d_dirs, int64_t n, float* d_dist,
+              uint8_t* d_hit, float* d_logit, float* d_normals, cudaStream_t stream) {
+    if (!net) return fail(DDF_ERR_INVALID_ARG, "net is NULL");
+    if (n < 0) return fail(DDF_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return DDF_OK;
+    if (!d_origins || !d_dirs || !d_dist || !d_hit)
+        return fail(DDF_ERR_INVALID_ARG, "origins, dirs, dist and hit must be non-NULL");
+    return field_query(net, d_origins, d_dirs, n, nullptr, d_dist, d_logit, d_hit, d_normals, stream);
+}
+
+int ddf_render(ddf_net net, const ddf_camera* cam, int spp, int bounces, float* d_image,
+               cudaStream_t stream) {
+    if (!net || !cam || !d_image) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    if (cam->width <= 0 || cam->height <= 0 || (int64_t)cam->width * cam->height > (int64_t(1) << 31))
+        return fail(DDF_ERR_INVALID_ARG, "bad image size %d x %d", cam->width, cam->height);
+    if (spp <= 0 || spp > (1 << 20)) return fail(DDF_ERR_INVALID_ARG, "spp must be in [1, 2^20]");
+    if (bounces < 1 || bounces > 63) return fail(DDF_ERR_INVALID_ARG, "bounces must be in [1, 63]");
+    if ((int64_t)cam->width * cam->height * spp >= (int64_t(1) << 40))
+        return fail(DDF_ERR_INVALID_ARG, "too many paths");
+    if (!(cam->vfov_deg > 0.f && cam->vfov_deg < 180.f))
+        return fail(DDF_ERR_INVALID_ARG, "vfov must be in (0, 180)");
+    return render(net, cam, spp, bounces, d_image, stream);
+}
+
+int ddf_render_stats(ddf_net net, int64_t* host_counts, int max_bounces) {
+    if (!net || !host_counts || max_bounces <= 0) return fail(DDF_ERR_INVALID_ARG, "bad argument");
+    for (int b = 0; b < max_bounces; ++b) host_counts[b] = 0;
+    if (!net->render_counts) return DDF_OK;
+    DDF_CUDA_TRY(cudaStreamSynchronize(net->last_stream));
+    const int nb = std::min(max_bounces, net->last_bounces);
+    DDF_CUDA_TRY(cudaMemcpy(host_counts, net->render_counts, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost));
+    return DDF_OK;
+}
+
+int ddf_mesh_create(const float* host_verts, int64_t nv, const int32_t* host_tris, int64_t nt,
+                    ddf_mesh* out) {
+    if (!out) return fail(DDF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!host_verts || !host_tris || nv <= 0 || nt <= 0 || nt > 0x7fffffff || nv > 0x7fffffff)
+        return fail(DDF_ERR_INVALID_ARG, "bad mesh arguments");
+    ddf_mesh_s* m = new ddf_mesh_s();
+    m->nv = nv;
+    m->nt = nt;
+    cudaError_t e = cudaMalloc(&m->verts, sizeof(float) * 3 * nv);
+    if (e == cudaSuccess) e = cudaMalloc(&m->tris, sizeof(int32_t) * 3 * nt);
+    if (e == cudaSuccess) e = cudaMemcpy(m->verts, host_verts, sizeof(float) * 3 * nv, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->tris, host_tris, sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice);
+    int rc = DDF_OK;
+    if (e != cudaSuccess) rc = fail(DDF_ERR_CUDA, "mesh upload: %s", cudaGetErrorString(e));
+    if (!rc) rc = mesh_prepare(m, host_verts, host_tris);
+    if (rc) {
+        ddf_mesh_destroy(m);
+        return rc;
+    }
+    *out = m;
+    return DDF_OK;
+}
+
+int ddf_mesh_destroy(ddf_mesh m) {
+    if (!m) return DDF_OK;
+    cudaDeviceSynchronize();
+    cudaFree(m->verts);
+    cudaFree(m->tris);
+    cudaFree(m->tri_hot);
+    cudaFree(m->tri_aux);
+    cudaFree(m->stats);
+    delete m;
+    return DDF_OK;
+}
+
+int ddf_label_rays(ddf_mesh mesh, const float* d_origins, const float* d_dirs, int64_t n,
+                   float* d_dist, uint8_t* d_hit, int32_t* d_tri, cudaStream_t stream) {
+    if (!mesh) return fail(DDF_ERR_INVALID_ARG, "mesh is NULL");
+    if (n < 0) return fail(DDF_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return DDF_OK;
+    if (!d_origins || !d_dirs || !d_dist || !d_hit)
+        return fail(DDF_ERR_INVALID_ARG, "origins, dirs, dist and hit must be non-NULL");
+    return label_rays(mesh, d_origins, d_dirs, n, d_dist, d_hit, d_tri, stream);
+}
+
+int ddf_label_stats(ddf_mesh mesh, int64_t* host_counts) {
+    if (!mesh || !host_counts) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    DDF_CUDA_TRY(cudaStreamSynchronize(mesh->last_stream));
+    unsigned long long h[2];
+    DDF_CUDA_TRY(cudaMemcpy(h, mesh->stats, sizeof(h), cudaMemcpyDeviceToHost));
+    host_counts[0] = (int64_t)h[0];
+    host_counts[1] = (int64_t)h[1];
+    return DDF_OK;
+}
+
+int ddf_backward(ddf_net net, const float* d_origins, const float* d_dirs, int64_t n,
+                 const float* d_gdist, const float* d_glogit, float* d_gweights, float* d_ginput,
+                 cudaStream_t stream) {
+    if (!net || net->is_sphere) return fail(DDF_ERR_INVALID_ARG, "net is NULL or not a network");
+    if (n < 0 || !d_gweights) return fail(DDF_ERR_INVALID_ARG, "bad arguments");
+    if (n == 0) {
+        DDF_CUDA_TRY(cudaMemsetAsync(d_gweights, 0, sizeof(float) * net->lay.n_params, stream));
+        return DDF_OK;
+    }
+    if (!d_origins || !d_dirs) return fail(DDF_ERR_INVALID_ARG, "origins / dirs are NULL");
+    if (n > 0x7fffffff) return fail(DDF_ERR_INVALID_ARG, "n too large");
+    return backward(net, d_origins, d_dirs, n, d_gdist, d_glogit, d_gweights, d_ginput, stream);
+}
+
+int ddf_train_step(ddf_net net, const float* d_origins, const float* d_dirs,
+                   const float* d_dist_gt, const uint8_t* d_hit_gt, int64_t n,
+                   const ddf_adam* opt, float* d_loss, cudaStream_t stream) {
+    if (!net || net->is_sphere) return fail(DDF_ERR_INVALID_ARG, "net is NULL or not a network");
+    if (!opt || n <= 0 || n > 0x7fffffff) return fail(DDF_ERR_INVALID_ARG, "bad arguments");
+    if (!d_origins || !d_dirs || !d_dist_gt || !d_hit_gt)
+        return fail(DDF_ERR_INVALID_ARG, "NULL input array");
+    if (!(opt->lr >= 0.f) || !(opt->beta1 >= 0.f && opt->beta1 < 1.f) ||
+        !(opt->beta2 >= 0.f && opt->beta2 < 1.f) || !(opt->eps > 0.f))
+        return fail(DDF_ERR_INVALID_ARG, "bad Adam hyper-parameters");
+    return train_step(net, d_origins, d_dirs, d_dist_gt, d_hit_gt, n, opt, d_loss, stream);
+}
+
+int ddf_set_workspace_limit(ddf_net net, size_t bytes) {
+    if (!net || bytes < (size_t(1) << 20)) return fail(DDF_ERR_INVALID_ARG, "limit must be >= 1 MiB");
+    net->ws_limit = bytes;
+    return DDF_OK;
+}
+
+}  // extern "C"

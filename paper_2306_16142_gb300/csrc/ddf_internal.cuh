@@ -1,0 +1,131 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "../../include/ddf.h"
+
+namespace ddf {
+
+constexpr int kMaxLayers = 16;      // hidden layers
+constexpr int kMaxWidth = 512;      // hidden width
+constexpr int kMaxFreqs = 20;       // Fourier features per coordinate
+constexpr int kMaxE = 6 + 6 * kMaxFreqs;
+constexpr int64_t kWaveMax = int64_t(1) << 24;   // paths per render wave
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+int fail(int code, const char* fmt, ...);
+
+#define DDF_CUDA_TRY(expr)                                                                 \
+    do {                                                                                   \
+        cudaError_t e_ = (expr);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return ::ddf::fail(e_ == cudaErrorMemoryAllocation ? DDF_ERR_OOM : DDF_ERR_CUDA, \
+                               "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                               __LINE__);                                                  \
+    } while (0)
+
+#define DDF_LAUNCH_CHECK() DDF_CUDA_TRY(cudaGetLastError())
+
+// ------------------------------------------------------------------ network description
+// Offsets (in floats) of each layer's W and b inside the flat blob. Layer l = 0..L-1 are the
+// hidden layers, l = L the output layer.
+struct NetLayout {
+    int in_freqs, E, width, L;
+    int64_t w_off[kMaxLayers + 1];
+    int64_t b_off[kMaxLayers + 1];
+    int64_t n_params;
+};
+
+NetLayout make_layout(int in_freqs, int width, int L);
+
+struct TcPack;   // tensor-core packed weights (mlp_tc.cu)
+
+}  // namespace ddf
+
+struct ddf_net_s {
+    ddf::NetLayout lay;
+    int precision = DDF_FP32;
+    int device = 0;
+    bool is_sphere = false;
+    float sphere_r = 0.f;
+    float* master = nullptr;     // FP32 masters, blob layout (device)
+    float* master_t = nullptr;   // per-layer transposed FP32 copies W^T [in][out] (device)
+    ddf::TcPack* tc = nullptr;   // BF16 / FP8 working copy
+    // Adam state
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    int64_t adam_step = 0;
+    // training workspace (grow-only)
+    void* train_ws = nullptr;
+    size_t train_ws_bytes = 0;
+    size_t ws_limit = size_t(1) << 30;
+    // render workspace (grow-only)
+    void* render_ws = nullptr;
+    size_t render_ws_bytes = 0;
+    int64_t* render_counts = nullptr;   // device, per-bounce query totals
+    int render_counts_len = 0;
+    int last_bounces = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+struct ddf_mesh_s {
+    int64_t nv = 0, nt = 0;
+    float* verts = nullptr;      // nv x 3 (device)
+    int32_t* tris = nullptr;     // nt x 3 (device)
+    float4* tri_hot = nullptr;   // nt x 3 float4: (v0, KE), (e1, KE*Sv), (e2, KE^2)
+    float4* tri_aux = nullptr;   // nt x 2 float4: (centroid, bounding radius), (E, 0, 0, 0)
+    unsigned long long* stats = nullptr;   // device [2]
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace ddf {
+
+// ------------------------------------------------------------------ FP32 SIMT MLP (mlp_simt.cu)
+// Forward of the whole network for rows [0, n) (n capped by *d_count when d_count != null),
+// writing dist / logit / hit and, for hit rows, the Eq. 3 normal.
+int mlp_fp32_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
+                   const int* d_count, float* dist, float* logit, uint8_t* hit, float* normals,
+                   cudaStream_t stream);
+int sphere_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
+                 const int* d_count, float* dist, float* logit, uint8_t* hit, float* normals,
+                 cudaStream_t stream);
+int build_transposed(ddf_net_s* net, cudaStream_t stream);
+
+// ------------------------------------------------------------------ tensor-core MLP (mlp_tc.cu)
+bool tc_supported(const NetLayout& lay, int precision);
+int tc_pack(ddf_net_s* net, int precision, cudaStream_t stream);
+void tc_free(ddf_net_s* net);
+int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
+                 const int* d_count, float* dist, float* logit, uint8_t* hit, float* normals,
+                 cudaStream_t stream);
+
+// Dispatch on the handle's kind and precision.
+int field_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
+                const int* d_count, float* dist, float* logit, uint8_t* hit, float* normals,
+                cudaStream_t stream);
+
+// ------------------------------------------------------------------ renderer (wavefront.cu)
+int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* image,
+           cudaStream_t stream);
+
+// ------------------------------------------------------------------ labelling (label.cu)
+int mesh_prepare(ddf_mesh_s* m, const float* host_verts, const int32_t* host_tris);
+int label_rays(ddf_mesh_s* m, const float* o, const float* w, int64_t n, float* dist,
+               uint8_t* hit, int32_t* tri, cudaStream_t stream);
+
+// ------------------------------------------------------------------ training (train.cu)
+int backward(ddf_net_s* net, const float* o, const float* w, int64_t n, const float* gdist,
+             const float* glogit, float* gweights, float* ginput, cudaStream_t stream);
+int train_step(ddf_net_s* net, const float* o, const float* w, const float* dist_gt,
+               const uint8_t* hit_gt, int64_t n, const ddf_adam* opt, float* loss,
+               cudaStream_t stream);
+
+int num_sms();
+
+}  // namespace ddf

@@ -1,0 +1,368 @@
+// FP32 SIMT fused DDF network query (the FP32 reference GPU path; no TF32).
+//
+// One persistent CTA per SM walks 64-row (or 32-row for width 512) tiles. A tile's inputs
+// are encoded in shared memory and every layer is evaluated on chip: activations live in two
+// shared buffers laid out [unit][row], weights stream from L2 in 32 x 128 chunks, each
+// thread keeps a TR x 8 register tile. ReLU masks are kept as bits so that, for hit rows,
+// the reverse pass d dist / d (o, w) (Sec. 4.2: the normal is the gradient of the field with
+// respect to the query point) runs through the same masks without re-reading activations.
+#include "ddf_internal.cuh"
+#include "device_common.cuh"
+
+namespace ddf {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int NC = 128;   // output columns per chunk
+constexpr int KC = 32;    // reduction rows per staged weight chunk
+constexpr int TC = 8;     // columns per thread
+
+enum { EPI_FWD = 0, EPI_BWD = 1, EPI_PLAIN = 2 };
+
+struct MlpArgs {
+    NetLayout lay;
+    const float* W;    // masters, blob layout
+    const float* Wt;   // transposed hidden/output weights, same offsets as W
+    const float* o;
+    const float* w;
+    int64_t n;
+    const int* d_count;
+    float* dist;
+    float* logit;
+    uint8_t* hit;
+    float* normals;
+    int kmax;          // max(width, E)
+};
+
+// out[N][MT] = epi(sum_k in[k][MT] * B[k][n]) with B row-major K x N at Bg (row stride ldb).
+template <int MT, int EPI>
+__device__ void gemm_layer(const float* __restrict__ Bg, int ldb, int K, int N,
+                           const float* __restrict__ in, float* __restrict__ out,
+                           float* __restrict__ Ws, const float* __restrict__ bias,
+                           uint32_t* __restrict__ mask) {
+    constexpr int TR = MT / 16;
+    constexpr int MW = MT / 32;   // mask words per unit
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const bool vec = (ldb % 4) == 0;
+    for (int n0 = 0; n0 < N; n0 += NC) {
+        float acc[TR][TC];
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+#pragma unroll
+            for (int j = 0; j < TC; ++j) acc[i][j] = 0.f;
+        float pre[16];
+        auto load_chunk = [&](int k0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int idx4 = tid + kThreads * q;
+                const int kk = idx4 >> 5, c = n0 + (idx4 & 31) * 4;
+                const int k = k0 + kk;
+                if (k < K && vec && c + 3 < N) {
+                    const float4 v = *reinterpret_cast<const float4*>(Bg + (int64_t)k * ldb + c);
+                    pre[4 * q + 0] = v.x;
+                    pre[4 * q + 1] = v.y;
+                    pre[4 * q + 2] = v.z;
+                    pre[4 * q + 3] = v.w;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        pre[4 * q + e] = (k < K && c + e < N) ? Bg[(int64_t)k * ldb + c + e] : 0.f;
+                }
+            }
+        };
+        load_chunk(0);
+        for (int k0 = 0; k0 < K; k0 += KC) {
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int idx4 = tid + kThreads * q;
+                *reinterpret_cast<float4*>(Ws + (idx4 >> 5) * NC + (idx4 & 31) * 4) =
+                    make_float4(pre[4 * q], pre[4 * q + 1], pre[4 * q + 2], pre[4 * q + 3]);
+            }
+            __syncthreads();
+            if (k0 + KC < K) load_chunk(k0 + KC);
+            const int kn = min(KC, K - k0);
+            for (int kk = 0; kk < kn; ++kk) {
+                float a[TR], b[TC];
+                const float* ap = in + (k0 + kk) * MT + ty * TR;
+                if constexpr (TR == 4) {
+                    const float4 v = *reinterpret_cast<const float4*>(ap);
+                    a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+                } else {
+                    const float2 v = *reinterpret_cast<const float2*>(ap);
+                    a[0] = v.x; a[1] = v.y;
+                }
+                const float4 b0 = *reinterpret_cast<const float4*>(Ws + kk * NC + tx * TC);
+                const float4 b1 = *reinterpret_cast<const float4*>(Ws + kk * NC + tx * TC + 4);
+                b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
+                b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+#pragma unroll
+                for (int i = 0; i < TR; ++i)
+#pragma unroll
+                    for (int j = 0; j < TC; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            }
+        }
+        // epilogue
+        const int r0 = ty * TR;
+#pragma unroll
+        for (int j = 0; j < TC; ++j) {
+            const int nn = n0 + tx * TC + j;
+            if (nn >= N) continue;
+            float v[TR];
+            if constexpr (EPI == EPI_FWD) {
+                const float bb = bias[nn];
+                uint32_t bits = 0;
+#pragma unroll
+                for (int i = 0; i < TR; ++i) {
+                    const float z = acc[i][j] + bb;
+                    v[i] = z > 0.f ? z : 0.f;
+                    bits |= (z > 0.f ? 1u : 0u) << i;
+                }
+                atomicOr(mask + nn * MW + (r0 >> 5), bits << (r0 & 31));
+            } else if constexpr (EPI == EPI_BWD) {
+                const uint32_t word = mask[nn * MW + (r0 >> 5)] >> (r0 & 31);
+#pragma unroll
+                for (int i = 0; i < TR; ++i) v[i] = ((word >> i) & 1u) ? acc[i][j] : 0.f;
+            } else {
+#pragma unroll
+                for (int i = 0; i < TR; ++i) v[i] = acc[i][j];
+            }
+            if constexpr (TR == 4)
+                *reinterpret_cast<float4*>(out + nn * MT + r0) = make_float4(v[0], v[1], v[2], v[3]);
+            else
+                *reinterpret_cast<float2*>(out + nn * MT + r0) = make_float2(v[0], v[1]);
+        }
+    }
+    __syncthreads();
+}
+
+template <int MT>
+__global__ void __launch_bounds__(kThreads, 1) mlp_fp32_kernel(const MlpArgs a) {
+    extern __shared__ __align__(16) float smem[];
+    constexpr int MW = MT / 32;
+    const NetLayout& lay = a.lay;
+    const int W = lay.width, E = lay.E, L = lay.L;
+    float* bufA = smem;
+    float* bufB = bufA + a.kmax * MT;
+    float* Ws = bufB + a.kmax * MT;
+    uint32_t* masks = reinterpret_cast<uint32_t*>(Ws + KC * NC);
+    float* rowv = reinterpret_cast<float*>(masks + L * W * MW);   // [6][MT]
+    float* red = rowv + 6 * MT;                                     // [kThreads / MT][2][MT]
+    int* flag = reinterpret_cast<int*>(red + 2 * kThreads);
+    const int tid = threadIdx.x;
+
+    int64_t n = a.n;
+    if (a.d_count) n = min(n, (int64_t)*a.d_count);
+    for (int64_t tile = blockIdx.x; tile * MT < n; tile += gridDim.x) {
+        const int64_t row0 = tile * MT;
+        const int rows = (int)min((int64_t)MT, n - row0);
+        for (int i = tid; i < 6 * MT; i += kThreads) {
+            const int r = i / 6, c = i % 6;
+            float v = 0.f;
+            if (r < rows) v = c < 3 ? a.o[(row0 + r) * 3 + c] : a.w[(row0 + r) * 3 + c - 3];
+            rowv[c * MT + r] = v;
+        }
+        for (int i = tid; i < L * W * MW; i += kThreads) masks[i] = 0u;
+        __syncthreads();
+        for (int i = tid; i < E * MT; i += kThreads) {
+            const int f = i / MT, r = i % MT;
+            float v[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) v[c] = rowv[c * MT + r];
+            bufA[f * MT + r] = encode_feature(f, v);
+        }
+        __syncthreads();
+        float* cur = bufA;
+        float* nxt = bufB;
+        int K = E;
+        for (int l = 0; l < L; ++l) {
+            gemm_layer<MT, EPI_FWD>(a.Wt + lay.w_off[l], W, K, W, cur, nxt, Ws, a.W + lay.b_off[l],
+                                    masks + l * W * MW);
+            float* t = cur; cur = nxt; nxt = t;
+            K = W;
+        }
+        // output layer (2 units), deterministic split over parts of the reduction
+        {
+            constexpr int P = kThreads / MT;
+            const int r = tid % MT, p = tid / MT;
+            const float* Wo = a.W + lay.w_off[L];
+            const int k0 = p * (W / P), k1 = (p + 1) * (W / P);
+            float s0 = 0.f, s1 = 0.f;
+            for (int k = k0; k < k1; ++k) {
+                const float x = cur[k * MT + r];
+                s0 = fmaf(Wo[k], x, s0);
+                s1 = fmaf(Wo[W + k], x, s1);
+            }
+            red[(p * 2 + 0) * MT + r] = s0;
+            red[(p * 2 + 1) * MT + r] = s1;
+        }
+        __syncthreads();
+        int my_hit = 0;
+        if (tid < MT) {
+            constexpr int P = kThreads / MT;
+            const float* bo = a.W + lay.b_off[L];
+            float y0 = 0.f, y1 = 0.f;
+            for (int p = 0; p < P; ++p) {
+                y0 += red[(p * 2 + 0) * MT + tid];
+                y1 += red[(p * 2 + 1) * MT + tid];
+            }
+            y0 += bo[0];
+            y1 += bo[1];
+            my_hit = (tid < rows) && (y1 > 0.f);
+            if (tid < rows) {
+                a.dist[row0 + tid] = y0;
+                if (a.logit) a.logit[row0 + tid] = y1;
+                if (a.hit) a.hit[row0 + tid] = (uint8_t)(y1 > 0.f);
+            }
+            flag[tid] = my_hit;   // reuse as per-row hit flags (MT <= kThreads)
+        }
+        const int any_hit = __syncthreads_or(my_hit);
+        if (!a.normals || !any_hit) continue;
+        // reverse pass for d dist / d input, hit rows only (other rows carry zeros)
+        {
+            const float* Wo = a.W + lay.w_off[L];
+            const uint32_t* mL = masks + (L - 1) * W * MW;
+            for (int i = tid; i < W * MT; i += kThreads) {
+                const int j = i / MT, r = i % MT;
+                const bool on = flag[r] && ((mL[j * MW + (r >> 5)] >> (r & 31)) & 1u);
+                nxt[j * MT + r] = on ? Wo[j] : 0.f;
+            }
+            float* t = cur; cur = nxt; nxt = t;
+        }
+        __syncthreads();
+        for (int l = L - 1; l >= 1; --l) {
+            gemm_layer<MT, EPI_BWD>(a.W + lay.w_off[l], W, W, W, cur, nxt, Ws, nullptr,
+                                    masks + (l - 1) * W * MW);
+            float* t = cur; cur = nxt; nxt = t;
+        }
+        gemm_layer<MT, EPI_PLAIN>(a.W + lay.w_off[0], E, W, E, cur, nxt, Ws, nullptr, nullptr);
+        if (tid < rows && flag[tid]) {
+            float v[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) v[c] = rowv[c * MT + tid];
+            float g[3] = {0.f, 0.f, 0.f};
+            for (int f = 0; f < E; ++f) {
+                const int c = f % 6;
+                if (c < 3) g[c] = fmaf(nxt[f * MT + tid], encode_dfeature(f, v), g[c]);
+            }
+            const float3 nrm = normal_from_grad(g[0], g[1], g[2], v[3], v[4], v[5]);
+            float* np = a.normals + (row0 + tid) * 3;
+            np[0] = nrm.x;
+            np[1] = nrm.y;
+            np[2] = nrm.z;
+        }
+        __syncthreads();
+    }
+}
+
+template <int MT>
+size_t smem_bytes(const NetLayout& lay, int kmax) {
+    return sizeof(float) * (2 * (size_t)kmax * MT + KC * NC) +
+           sizeof(uint32_t) * (size_t)lay.L * lay.width * (MT / 32) + sizeof(float) * 6 * MT +
+           sizeof(float) * 2 * kThreads + sizeof(int) * kThreads;
+}
+
+template <int MT>
+int launch(const MlpArgs& a, int64_t n, cudaStream_t stream) {
+    const size_t sm = smem_bytes<MT>(a.lay, a.kmax);
+    static bool attr_done = false;
+    if (!attr_done) {
+        DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_fp32_kernel<MT>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr_done = true;
+    }
+    if (sm > 227 * 1024) return fail(DDF_ERR_UNSUPPORTED, "FP32 MLP: shared memory %zu too large", sm);
+    int64_t tiles = (n + MT - 1) / MT;
+    int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms());
+    if (a.d_count) grid = num_sms();
+    if (grid <= 0) return DDF_OK;
+    mlp_fp32_kernel<MT><<<grid, kThreads, sm, stream>>>(a);
+    DDF_LAUNCH_CHECK();
+    return DDF_OK;
+}
+
+// Closed-form sphere field (test field for the renderer).
+__global__ void sphere_kernel(float r, const float* __restrict__ o, const float* __restrict__ w,
+                              int64_t n, const int* d_count, float* dist, float* logit,
+                              uint8_t* hit, float* normals) {
+    if (d_count) n = min(n, (int64_t)*d_count);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float ox = o[3 * i], oy = o[3 * i + 1], oz = o[3 * i + 2];
+        const float wx = w[3 * i], wy = w[3 * i + 1], wz = w[3 * i + 2];
+        const float b = ox * wx + oy * wy + oz * wz;
+        const float c = ox * ox + oy * oy + oz * oz - r * r;
+        const float disc = b * b - c;
+        const float sq = sqrtf(fmaxf(disc, 0.f));
+        const bool inside = c < 0.f;
+        const float t = inside ? -b + sq : -b - sq;
+        const bool h = disc >= 0.f && (inside || t > 0.f);
+        dist[i] = h ? t : INFINITY;
+        if (logit) logit[i] = h ? 1.f : -1.f;
+        if (hit) hit[i] = h;
+        if (normals && h) {
+            const float s = inside ? -1.f : 1.f;
+            const float3 nn = normal_from_grad(s * (ox + t * wx), s * (oy + t * wy),
+                                               s * (oz + t * wz), wx, wy, wz);
+            normals[3 * i] = nn.x;
+            normals[3 * i + 1] = nn.y;
+            normals[3 * i + 2] = nn.z;
+        }
+    }
+}
+
+// W^T copies of every layer (hidden and output), at the same offsets as the blob.
+__global__ void transpose_layers(const float* __restrict__ W, float* __restrict__ Wt, NetLayout lay) {
+    const int l = blockIdx.y;
+    const int out = (l == lay.L) ? 2 : lay.width;
+    const int in = (l == 0) ? lay.E : lay.width;
+    const float* src = W + lay.w_off[l];
+    float* dst = Wt + lay.w_off[l];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)out * in;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / in), c = (int)(i % in);
+        dst[(int64_t)c * out + r] = src[i];
+    }
+}
+
+}  // namespace
+
+int build_transposed(ddf_net_s* net, cudaStream_t stream) {
+    dim3 grid(64, net->lay.L + 1);
+    transpose_layers<<<grid, 256, 0, stream>>>(net->master, net->master_t, net->lay);
+    DDF_LAUNCH_CHECK();
+    return DDF_OK;
+}
+
+int mlp_fp32_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
+                   const int* d_count, float* dist, float* logit, uint8_t* hit, float* normals,
+                   cudaStream_t stream) {
+    MlpArgs a;
+    a.lay = net->lay;
+    a.W = net->master;
+    a.Wt = net->master_t;
+    a.o = o;
+    a.w = w;
+    a.n = n;
+    a.d_count = d_count;
+    a.dist = dist;
+    a.logit = logit;
+    a.hit = hit;
+    a.normals = normals;
+    a.kmax = std::max(net->lay.width, net->lay.E);
+    if (net->lay.width <= 256) return launch<64>(a, n, stream);
+    return launch<32>(a, n, stream);
+}
+
+int sphere_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
+                 const int* d_count, float* dist, float* logit, uint8_t* hit, float* normals,
+                 cudaStream_t stream) {
+    int grid = d_count ? num_sms() * 8 : (int)std::min<int64_t>((n + 255) / 256, num_sms() * 8);
+    if (grid <= 0) return DDF_OK;
+    sphere_kernel<<<grid, 256, 0, stream>>>(net->sphere_r, o, w, n, d_count, dist, logit, hit,
+                                            normals);
+    DDF_LAUNCH_CHECK();
+    return DDF_OK;
+}
+
+}  // namespace ddf

@@ -1,0 +1,269 @@
+// Wavefront form of the modified uni-directional path tracer (Sec. 1, Fig. 1): every bounce
+// is one batched field query over all live paths followed by one shading + compaction pass.
+//
+// Ray state is structure-of-arrays in HBM (o: n x 3, w: n x 3, path index: n, throughput: n),
+// ping-ponged between two buffers. Live counts stay in device memory, so the host never waits
+// inside a render: every kernel reads its count and strides over it with a fixed grid.
+// Compaction is a warp ballot plus one atomicAdd per warp. Every random number a path uses is
+// a Philox4x32-10 word of counter (pid, bounce), so a path's radiance does not depend on where
+// compaction put it.
+#include <math.h>
+
+#include "ddf_internal.cuh"
+#include "device_common.cuh"
+
+namespace ddf {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct CamDev {
+    float eye[3], f[3], r[3], u[3];
+    float th, aspect;
+    int W, H;
+    uint64_t seed;
+    float albedo, env;
+};
+
+__device__ __forceinline__ int warp_compact(bool alive, int* counter) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned m = __ballot_sync(0xffffffffu, alive);
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(counter, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    return base + __popc(m & ((1u << lane) - 1u));
+}
+
+// Camera rays of paths [pid0, pid0 + npaths), advanced to their entry into the unit ball.
+__global__ void __launch_bounds__(kThreads) raygen_kernel(CamDev cam, int spp, int64_t pid0,
+                                                          int64_t npaths, float* __restrict__ o,
+                                                          float* __restrict__ w,
+                                                          uint32_t* __restrict__ lid,
+                                                          float* __restrict__ thr,
+                                                          float* __restrict__ radiance, int* count) {
+    for (int64_t i0 = (int64_t)blockIdx.x * kThreads; i0 < npaths; i0 += (int64_t)gridDim.x * kThreads) {
+        const int64_t i = i0 + threadIdx.x;
+        const bool valid = i < npaths;
+        bool alive = false;
+        float ox = 0, oy = 0, oz = 0, dx = 0, dy = 0, dz = 0;
+        if (valid) {
+            const int64_t pid = pid0 + i;
+            const int64_t pix = pid / spp;
+            const float x = (float)(pix % cam.W), y = (float)(pix / cam.W);
+            const uint4 rnd = path_draw(cam.seed, (uint64_t)pid, 0u);
+            const float px = (2.f * (x + u24(rnd.x)) / cam.W - 1.f) * cam.th * cam.aspect;
+            const float py = (1.f - 2.f * (y + u24(rnd.y)) / cam.H) * cam.th;
+            dx = cam.f[0] + px * cam.r[0] + py * cam.u[0];
+            dy = cam.f[1] + px * cam.r[1] + py * cam.u[1];
+            dz = cam.f[2] + px * cam.r[2] + py * cam.u[2];
+            const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+            dx *= inv; dy *= inv; dz *= inv;
+            const float b = cam.eye[0] * dx + cam.eye[1] * dy + cam.eye[2] * dz;
+            const float c = cam.eye[0] * cam.eye[0] + cam.eye[1] * cam.eye[1] + cam.eye[2] * cam.eye[2] - 1.f;
+            const float disc = b * b - c;
+            const float sq = sqrtf(fmaxf(disc, 0.f));
+            alive = disc > 0.f && (-b + sq) > 0.f;
+            const float t0 = fmaxf(0.f, -b - sq);
+            ox = cam.eye[0] + t0 * dx;
+            oy = cam.eye[1] + t0 * dy;
+            oz = cam.eye[2] + t0 * dz;
+            if (!alive) radiance[i] = cam.env;
+        }
+        const int slot = warp_compact(alive, count);
+        if (alive) {
+            o[3 * slot] = ox; o[3 * slot + 1] = oy; o[3 * slot + 2] = oz;
+            w[3 * slot] = dx; w[3 * slot + 1] = dy; w[3 * slot + 2] = dz;
+            lid[slot] = (uint32_t)i;
+            thr[slot] = 1.f;
+        }
+    }
+}
+
+// One bounce of shading for the live paths of the previous query, compacting survivors.
+__global__ void __launch_bounds__(kThreads) shade_kernel(
+    CamDev cam, int64_t pid0, int bounce, int bounces, const int* __restrict__ count_in,
+    const float* __restrict__ o, const float* __restrict__ w, const uint32_t* __restrict__ lid,
+    const float* __restrict__ thr, const float* __restrict__ dist, const float* __restrict__ logit,
+    const float* __restrict__ nrm, float* __restrict__ o2, float* __restrict__ w2,
+    uint32_t* __restrict__ lid2, float* __restrict__ thr2, float* __restrict__ radiance,
+    int* count_out) {
+    const int n = *count_in;
+    for (int i0 = blockIdx.x * kThreads; i0 < n; i0 += gridDim.x * kThreads) {
+        const int i = i0 + threadIdx.x;
+        const bool valid = i < n;
+        bool alive = false;
+        float nox = 0, noy = 0, noz = 0, nwx = 0, nwy = 0, nwz = 0, nthr = 0;
+        uint32_t id = 0;
+        if (valid) {
+            id = lid[i];
+            const float t = thr[i];
+            const bool h = logit[i] > 0.f;
+            if (!h) {
+                radiance[id] = t * cam.env;
+            } else if (bounce == bounces) {
+                radiance[id] = 0.f;
+            } else {
+                alive = true;
+                const float d = fmaxf(dist[i], 0.f);
+                const float nx = nrm[3 * i], ny = nrm[3 * i + 1], nz = nrm[3 * i + 2];
+                nox = o[3 * i] + d * w[3 * i] + 1e-4f * nx;
+                noy = o[3 * i + 1] + d * w[3 * i + 1] + 1e-4f * ny;
+                noz = o[3 * i + 2] + d * w[3 * i + 2] + 1e-4f * nz;
+                const uint4 rnd = path_draw(cam.seed, (uint64_t)(pid0 + id), (uint32_t)bounce);
+                const float u0 = u24(rnd.x), u1 = u24(rnd.y);
+                const float rr = sqrtf(u0);
+                float sp, cp;
+                sincospif(2.f * u1, &sp, &cp);
+                const float lx = rr * cp, ly = rr * sp, lz = sqrtf(1.f - u0);
+                // orthonormal basis about n (Duff et al. 2017)
+                const float sign = nz >= 0.f ? 1.f : -1.f;
+                const float a = -1.f / (sign + nz);
+                const float b = nx * ny * a;
+                const float b1x = 1.f + sign * nx * nx * a, b1y = sign * b, b1z = -sign * nx;
+                const float b2x = b, b2y = sign + ny * ny * a, b2z = -ny;
+                nwx = lx * b1x + ly * b2x + lz * nx;
+                nwy = lx * b1y + ly * b2y + lz * ny;
+                nwz = lx * b1z + ly * b2z + lz * nz;
+                nthr = t * cam.albedo;
+            }
+        }
+        const int slot = warp_compact(alive, count_out);
+        if (alive) {
+            o2[3 * slot] = nox; o2[3 * slot + 1] = noy; o2[3 * slot + 2] = noz;
+            w2[3 * slot] = nwx; w2[3 * slot + 1] = nwy; w2[3 * slot + 2] = nwz;
+            lid2[slot] = id;
+            thr2[slot] = nthr;
+        }
+    }
+}
+
+// image[px0 + p] = mean of the spp radiance samples of pixel p, summed in sample order.
+__global__ void accumulate_kernel(const float* __restrict__ radiance, int spp, int64_t px0,
+                                  int64_t npx, float* __restrict__ image) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npx;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int k = 0; k < spp; ++k) s += radiance[p * spp + k];
+        image[px0 + p] = s / (float)spp;
+    }
+}
+
+__global__ void add_counts(const int* __restrict__ counts, int bounces, int64_t* __restrict__ totals) {
+    const int b = threadIdx.x;
+    if (b < bounces) totals[b] += counts[b];
+}
+
+struct WaveBufs {
+    float *o[2], *w[2], *thr[2];
+    uint32_t* lid[2];
+    float *dist, *logit, *nrm, *radiance;
+    int* counts;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* image,
+           cudaStream_t stream) {
+    const int64_t npix = (int64_t)cam->width * cam->height;
+    const int64_t px_per_wave = std::max<int64_t>(1, std::min<int64_t>(npix, kWaveMax / spp));
+    const int64_t wave_paths = px_per_wave * spp;
+    // workspace layout
+    const size_t fvec = align256(sizeof(float) * 3 * wave_paths);
+    const size_t fsc = align256(sizeof(float) * wave_paths);
+    const size_t need = 2 * (2 * fvec + 2 * fsc) + fsc * 3 + fvec + align256(sizeof(int) * 64);
+    if (net->render_ws_bytes < need) {
+        if (net->render_ws) cudaFree(net->render_ws);
+        net->render_ws = nullptr;
+        net->render_ws_bytes = 0;
+        DDF_CUDA_TRY(cudaMalloc(&net->render_ws, need));
+        net->render_ws_bytes = need;
+    }
+    if (net->render_counts_len < bounces) {
+        if (net->render_counts) cudaFree(net->render_counts);
+        net->render_counts = nullptr;
+        DDF_CUDA_TRY(cudaMalloc(&net->render_counts, sizeof(int64_t) * 64));
+        net->render_counts_len = 64;
+    }
+    char* p = (char*)net->render_ws;
+    WaveBufs B;
+    for (int k = 0; k < 2; ++k) {
+        B.o[k] = (float*)p; p += fvec;
+        B.w[k] = (float*)p; p += fvec;
+        B.thr[k] = (float*)p; p += fsc;
+        B.lid[k] = (uint32_t*)p; p += fsc;
+    }
+    B.dist = (float*)p; p += fsc;
+    B.logit = (float*)p; p += fsc;
+    B.radiance = (float*)p; p += fsc;
+    B.nrm = (float*)p; p += fvec;
+    B.counts = (int*)p;
+
+    // camera basis in double, rounded once
+    CamDev cd;
+    double eye[3], f[3], r[3], u[3];
+    for (int c = 0; c < 3; ++c) {
+        eye[c] = cam->eye[c];
+        f[c] = (double)cam->look_at[c] - eye[c];
+    }
+    double fn = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    for (int c = 0; c < 3; ++c) f[c] /= fn;
+    const double up[3] = {cam->up[0], cam->up[1], cam->up[2]};
+    r[0] = f[1] * up[2] - f[2] * up[1];
+    r[1] = f[2] * up[0] - f[0] * up[2];
+    r[2] = f[0] * up[1] - f[1] * up[0];
+    double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (!(rn > 0) || !(fn > 0)) return fail(DDF_ERR_INVALID_ARG, "degenerate camera basis");
+    for (int c = 0; c < 3; ++c) r[c] /= rn;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    for (int c = 0; c < 3; ++c) {
+        cd.eye[c] = (float)eye[c];
+        cd.f[c] = (float)f[c];
+        cd.r[c] = (float)r[c];
+        cd.u[c] = (float)u[c];
+    }
+    cd.th = (float)tan(cam->vfov_deg * M_PI / 360.0);
+    cd.aspect = (float)((double)cam->width / cam->height);
+    cd.W = cam->width;
+    cd.H = cam->height;
+    cd.seed = cam->seed;
+    cd.albedo = cam->albedo;
+    cd.env = cam->env;
+
+    DDF_CUDA_TRY(cudaMemsetAsync(net->render_counts, 0, sizeof(int64_t) * 64, stream));
+    net->last_bounces = bounces;
+    net->last_stream = stream;
+    const int grid = num_sms() * 4;
+    for (int64_t px0 = 0; px0 < npix; px0 += px_per_wave) {
+        const int64_t npx = std::min(px_per_wave, npix - px0);
+        const int64_t npaths = npx * spp;
+        DDF_CUDA_TRY(cudaMemsetAsync(B.counts, 0, sizeof(int) * (bounces + 1), stream));
+        const int64_t pid0 = px0 * spp;
+        const int rg = (int)std::min<int64_t>((npaths + kThreads - 1) / kThreads, grid);
+        raygen_kernel<<<rg, kThreads, 0, stream>>>(cd, spp, pid0, npaths, B.o[0], B.w[0], B.lid[0],
+                                                   B.thr[0], B.radiance, B.counts);
+        DDF_LAUNCH_CHECK();
+        for (int b = 1; b <= bounces; ++b) {
+            const int s = (b - 1) & 1;
+            int rc = field_query(net, B.o[s], B.w[s], npaths, B.counts + (b - 1), B.dist, B.logit,
+                                 nullptr, b < bounces ? B.nrm : nullptr, stream);
+            if (rc) return rc;
+            shade_kernel<<<grid, kThreads, 0, stream>>>(cd, pid0, b, bounces, B.counts + (b - 1),
+                                                        B.o[s], B.w[s], B.lid[s], B.thr[s], B.dist,
+                                                        B.logit, B.nrm, B.o[s ^ 1], B.w[s ^ 1],
+                                                        B.lid[s ^ 1], B.thr[s ^ 1], B.radiance,
+                                                        B.counts + b);
+            DDF_LAUNCH_CHECK();
+        }
+        accumulate_kernel<<<grid, kThreads, 0, stream>>>(B.radiance, spp, px0, npx, image);
+        DDF_LAUNCH_CHECK();
+        add_counts<<<1, 64, 0, stream>>>(B.counts, bounces, net->render_counts);
+        DDF_LAUNCH_CHECK();
+    }
+    return DDF_OK;
+}
+
+}  // namespace ddf

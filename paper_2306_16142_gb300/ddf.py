@@ -1,0 +1,185 @@
+"""Torch-tensor conveniences over the C ABI (argument marshalling only: every step runs in
+libddf.so's kernels). Tensors must be contiguous CUDA tensors of the stated dtypes; calls are
+ordered on torch's current CUDA stream."""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import check, ddf_adam, ddf_arch, ddf_camera
+
+PRECISIONS = {"fp32": _abi.DDF_FP32, "bf16": _abi.DDF_BF16, "fp8": _abi.DDF_FP8}
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _rays(o, w):
+    if o.dtype != torch.float32 or w.dtype != torch.float32 or o.shape != w.shape or o.dim() != 2 \
+            or o.shape[1] != 3:
+        raise ValueError("origins / directions must be float32 (n, 3) tensors of equal shape")
+    return o.shape[0]
+
+
+class DDFNet:
+    """A DDF network handle (or the closed-form sphere field, DDFNet.sphere(r))."""
+
+    def __init__(self, in_freqs: int, width: int, hidden_layers: int, weights,
+                 precision: str = "fp32"):
+        lib = _abi.load()
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32))
+        arch = ddf_arch(in_freqs, width, hidden_layers, PRECISIONS[precision])
+        h = C.c_void_p()
+        check("ddf_create", lib.ddf_create(C.byref(arch), w.ctypes.data_as(C.c_void_p), w.nbytes,
+                                          C.byref(h)))
+        self.h = h
+        self.arch = (in_freqs, width, hidden_layers)
+        self.precision = precision
+        self.n_params = w.size
+
+    @classmethod
+    def sphere(cls, radius: float):
+        obj = cls.__new__(cls)
+        h = C.c_void_p()
+        check("ddf_sphere_create", _abi.load().ddf_sphere_create(radius, C.byref(h)))
+        obj.h = h
+        obj.arch = None
+        obj.precision = "fp32"
+        obj.n_params = 0
+        return obj
+
+    def close(self):
+        if getattr(self, "h", None):
+            _abi.load().ddf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_precision(self, precision: str):
+        check("ddf_set_precision", _abi.load().ddf_set_precision(self.h, PRECISIONS[precision]))
+        self.precision = precision
+
+    def query(self, o: torch.Tensor, w: torch.Tensor, normals: bool = False, out=None):
+        n = _rays(o, w)
+        dev = o.device
+        if out is None:
+            out = {"dist": torch.empty(n, device=dev), "hit": torch.empty(n, dtype=torch.uint8, device=dev),
+                   "logit": torch.empty(n, device=dev),
+                   "normal": torch.zeros(n, 3, device=dev) if normals else None}
+        check("ddf_query", _abi.load().ddf_query(self.h, _ptr(o), _ptr(w), n, _ptr(out["dist"]),
+                                                 _ptr(out["hit"]), _ptr(out["logit"]),
+                                                 _ptr(out.get("normal")), _stream()))
+        return out
+
+    def render(self, cam, spp: int, bounces: int, image: torch.Tensor | None = None):
+        c = camera_struct(cam)
+        if image is None:
+            image = torch.empty(cam.height, cam.width, device="cuda")
+        check("ddf_render", _abi.load().ddf_render(self.h, C.byref(c), spp, bounces, _ptr(image),
+                                                   _stream()))
+        return image
+
+    def render_stats(self, bounces: int):
+        arr = (C.c_int64 * bounces)()
+        check("ddf_render_stats", _abi.load().ddf_render_stats(self.h, arr, bounces))
+        return list(arr)
+
+    def set_weights(self, wt: torch.Tensor):
+        check("ddf_set_weights", _abi.load().ddf_set_weights(self.h, _ptr(wt), wt.numel() * 4, _stream()))
+
+    def get_weights(self) -> torch.Tensor:
+        out = torch.empty(self.n_params, device="cuda")
+        check("ddf_get_weights", _abi.load().ddf_get_weights(self.h, _ptr(out), out.numel() * 4, _stream()))
+        return out
+
+    def backward(self, o, w, gdist, glogit, need_input: bool = False):
+        n = _rays(o, w)
+        gw = torch.empty(self.n_params, device=o.device)
+        gin = torch.empty(n, 6, device=o.device) if need_input else None
+        check("ddf_backward", _abi.load().ddf_backward(self.h, _ptr(o), _ptr(w), n, _ptr(gdist),
+                                                       _ptr(glogit), _ptr(gw), _ptr(gin), _stream()))
+        return gw, gin
+
+    def train_step(self, o, w, dist_gt, hit_gt, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, loss=None):
+        n = _rays(o, w)
+        if loss is None:
+            loss = torch.empty((), device=o.device)
+        opt = ddf_adam(lr, beta1, beta2, eps)
+        check("ddf_train_step", _abi.load().ddf_train_step(self.h, _ptr(o), _ptr(w), _ptr(dist_gt),
+                                                           _ptr(hit_gt), n, C.byref(opt), _ptr(loss),
+                                                           _stream()))
+        return loss
+
+    def set_workspace_limit(self, nbytes: int):
+        check("ddf_set_workspace_limit", _abi.load().ddf_set_workspace_limit(self.h, nbytes))
+
+
+class DDFMesh:
+    """A triangle mesh prepared for ray labelling."""
+
+    def __init__(self, verts, tris):
+        v = np.ascontiguousarray(np.asarray(verts, np.float32))
+        t = np.ascontiguousarray(np.asarray(tris, np.int32))
+        h = C.c_void_p()
+        check("ddf_mesh_create", _abi.load().ddf_mesh_create(v.ctypes.data_as(C.c_void_p), v.shape[0],
+                                                             t.ctypes.data_as(C.c_void_p), t.shape[0],
+                                                             C.byref(h)))
+        self.h = h
+        self.nt = t.shape[0]
+
+    def close(self):
+        if getattr(self, "h", None):
+            _abi.load().ddf_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def label(self, o, w, out=None):
+        n = _rays(o, w)
+        if out is None:
+            out = {"dist": torch.empty(n, device=o.device), "hit": torch.empty(n, dtype=torch.uint8, device=o.device),
+                   "tri": torch.empty(n, dtype=torch.int32, device=o.device)}
+        check("ddf_label_rays", _abi.load().ddf_label_rays(self.h, _ptr(o), _ptr(w), n, _ptr(out["dist"]),
+                                                           _ptr(out["hit"]), _ptr(out.get("tri")), _stream()))
+        return out
+
+    def stats(self):
+        arr = (C.c_int64 * 2)()
+        check("ddf_label_stats", _abi.load().ddf_label_stats(self.h, arr))
+        return {"retests": arr[0], "finals": arr[1]}
+
+
+def camera_struct(cam) -> ddf_camera:
+    c = ddf_camera()
+    for k in range(3):
+        c.eye[k] = cam.eye[k]
+        c.look_at[k] = cam.look_at[k]
+        c.up[k] = cam.up[k]
+    c.vfov_deg = cam.vfov_deg
+    c.width = cam.width
+    c.height = cam.height
+    c.seed = cam.seed
+    c.albedo = cam.albedo
+    c.env = cam.env
+    return c
