@@ -1,0 +1,373 @@
+"""Benchmark of the DDF hot path on GB300.
+
+One step = one full render of the single-object workload (the modified path tracer of the
+paper's Sec. 1 / Fig. 1): 512 x 512 pixels x 64 samples, at most 4 bounces, a 78 -> 256 x 8 -> 2
+network (12-frequency encoding) with seeded weights, one wave of 2^24 paths: camera rays, one
+batched field query per bounce (distance, hit, Eq. 3 normal), shading + compaction, per-pixel
+accumulation - every step in libddf.so's kernels.
+
+Prints ONE JSON line (rank 0): samples/s over the timed steps (device time, CUDA events, max over
+ranks), the dominant kernel's roofline, the end-to-end figure through the public API with the
+image read back to pinned host memory, the FP64 oracle timed on the host cores on a bounded
+sample, SM clocks sampled during the timed region, and the query error against the oracle.
+
+--impl reference times the FP64 oracle itself on the host (a bounded sample per step).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DDF ray queries/s and render samples/s, BF16/FP8 vs FP32 on 1 GB300 at stated error"
+WORKLOAD = dict(width=512, height=512, spp=64, bounces=4, in_freqs=12, hidden=256, layers=8, seed=3)
+
+
+def workload_name(w):
+    E = 6 + 6 * w["in_freqs"]
+    return (f"single-object render {w['width']}x{w['height']} x {w['spp']} spp, <= {w['bounces']} bounces, "
+            f"{E}->{w['hidden']}x{w['layers']}->2 DDF MLP (seeded weights)")
+
+
+def fwd_flops(E, W, L):
+    return 2.0 * (E * W + (L - 1) * W * W + 2 * W)
+
+
+def bwd_flops(E, W, L):
+    # reverse pass to the input for a hit row: W x W per hidden layer after the first, W x E last
+    return 2.0 * ((L - 1) * W * W + W * E)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_render_sample(w, blob, n_paths, precision_note=""):
+    """Time the FP64 oracle on n_paths paths of the same render (bounded CPU work)."""
+    import numpy as np
+    from ddf_synth import default_camera
+    from oracle import mlp as omlp
+    from oracle.render import trace_paths
+    cam = default_camera(w["width"], w["height"], seed=1)
+    P = omlp.unpack(blob, w["in_freqs"], w["hidden"], w["layers"])
+    total = w["width"] * w["height"] * w["spp"]
+    pids = np.random.default_rng(0).choice(total, n_paths, replace=False)
+    nq = [0]
+
+    def q(o, d):
+        nq[0] += o.shape[0]
+        return omlp.query(P, o, d, w["in_freqs"])
+
+    t0 = time.perf_counter()
+    trace_paths(q, cam, w["spp"], w["bounces"], pids)
+    dt = time.perf_counter() - t0
+    return dt, nq[0]
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return int(max(i.get("num_threads", 1) for i in info))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    from ddf_synth import init_weights
+    w = WORKLOAD
+    blob = init_weights(w["in_freqs"], w["hidden"], w["layers"], seed=w["seed"])
+    n_paths = args.ref_paths
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle_render_sample(w, blob, max(64, n_paths // 16))
+    times, nqs = [], []
+    for _ in range(args.steps):
+        dt, nq = oracle_render_sample(w, blob, n_paths)
+        times.append(dt)
+        nqs.append(nq)
+    tot = sum(times)
+    value = n_paths * args.steps / tot
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": workload_name(w), "parallelism": "host cores (numpy FP64 oracle)"},
+            "queries_per_s": sum(nqs) / tot,
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": f"{n_paths} random paths of the {w['width']}x{w['height']}x{w['spp']} "
+                                       f"render per step"},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16", "fp8"])
+    ap.add_argument("--ref-paths", type=int, default=2048)
+    ap.add_argument("--no-oracle", action="store_true", help="skip the CPU oracle legs")
+    ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--size", default="full", choices=["full", "small"],
+                    help="small: 512 x 512 x 8 spp (2^21 paths) for profiler captures")
+    args = ap.parse_args()
+    if args.size == "small":
+        WORKLOAD["spp"] = 8
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2306_16142_gb300 as P
+    from ddf_synth import default_camera, init_weights
+    from paper_2306_16142_gb300.ddf import camera_struct
+
+    w = WORKLOAD
+    E = 6 + 6 * w["in_freqs"]
+    blob = init_weights(w["in_freqs"], w["hidden"], w["layers"], seed=w["seed"])
+    prec = args.precision
+    if prec == "auto":
+        prec = "bf16"
+    try:
+        net = P.DDFNet(w["in_freqs"], w["hidden"], w["layers"], blob, prec)
+    except P.DDFError:
+        prec = "fp32"
+        net = P.DDFNet(w["in_freqs"], w["hidden"], w["layers"], blob, prec)
+    cam = default_camera(w["width"], w["height"], seed=1 + rank)
+    img = torch.empty(w["height"], w["width"], device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        net.render(cam, w["spp"], w["bounces"], img)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    stats = net.render_stats(w["bounces"])
+
+    # ---- timed region (device time, CUDA events on the launching stream)
+    net.profile(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = net.profile_read()
+    net.profile(False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = t.item()
+    paths = w["width"] * w["height"] * w["spp"]
+    value = paths * world * args.steps / (ms / 1e3)
+    queries = sum(stats)
+    queries_per_s = queries * world * args.steps / (ms / 1e3)
+
+    # ---- dominant kernel roofline: the field query
+    Wd, Ld = w["hidden"], w["layers"]
+    flops = 0.0
+    for b in range(w["bounces"]):
+        flops += stats[b] * fwd_flops(E, Wd, Ld)
+        if b + 1 < w["bounces"]:
+            flops += stats[b + 1] * bwd_flops(E, Wd, Ld)      # normals of the rows that hit
+    q = prof["query"]
+    q_launch_ms = q["ms"] / max(1, q["launches"])
+    flops_per_launch = flops / w["bounces"]
+    achieved = flops_per_launch / (q_launch_ms / 1e3) / 1e12
+    peaks, peak_src = load_peaks()
+    if prec == "fp32":
+        # FP32 SIMT: 152 SMs x 128 FMA lanes x 2 flop x max SM clock
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
+    else:
+        peak = peaks["bf16_tflops_sustained"] * (2.0 if prec == "fp8" else 1.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{peak_src} bf16 sustained" + (" x 2 (fp8 nominal ratio)" if prec == "fp8" else "")}
+    roof["kernel"] = "field query (fused MLP + Eq. 3 normal)"
+    roof["time_share"] = q["ms"] / ms if ms > 0 else None
+
+    # ---- end to end through the public call, image read back to pinned host memory
+    host_img = torch.empty(w["height"], w["width"], pin_memory=True)
+    cs = camera_struct(cam)
+    for _ in range(2):
+        net.render(cam, w["spp"], w["bounces"], img)
+        host_img.copy_(img, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_steps = max(2, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        net.render(cam, w["spp"], w["bounces"], img)
+        host_img.copy_(img, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": paths * world * e2e_steps / e2e_s, "unit": "samples/s",
+           "h2d_bytes_per_step": int(np.dtype(np.uint8).itemsize * len(bytes(cs))),
+           "d2h_bytes_per_step": int(host_img.numel() * 4)}
+
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "fp8e4m3"}[prec],
+            "data": "synthetic",
+            "config": {"workload": workload_name(w), "precision": prec, "paths_per_step": paths,
+                       "queries_per_step": queries, "queries_per_bounce": stats,
+                       "l2": "no flush: ray state of one wave (2^24 paths, ~1.5 GB) exceeds the 129 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "queries_per_s": queries_per_s,
+            "roofline": roof,
+            "e2e": e2e,
+            "gpu_launches": int(sum(v["launches"] for v in prof.values()) + args.steps * 2),
+            "clocks": clocks}
+
+    # ---- FP32 path beside the tensor-core path, and the oracle
+    if rank == 0 and prec != "fp32" and args.fp32_steps > 0:
+        net32 = P.DDFNet(w["in_freqs"], w["hidden"], w["layers"], blob, "fp32")
+        net32.render(cam, w["spp"], w["bounces"], img)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.fp32_steps):
+            net32.render(cam, w["spp"], w["bounces"], img)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        line["fp32_path"] = {"value": paths * args.fp32_steps / (e0.elapsed_time(e1) / 1e3),
+                             "unit": "samples/s"}
+    if rank == 0 and not args.no_oracle:
+        line["query_error"] = query_error(P, net, blob, w)
+        dt, nq = oracle_render_sample(w, blob, args.ref_paths)
+        line["cpu_baseline"] = {"value": args.ref_paths / dt, "unit": "samples/s", "cores": cpu_threads(),
+                                "kind": "oracle",
+                                "sample": f"{args.ref_paths} random paths of the same render "
+                                          f"({nq} field queries)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def query_error(P, net, blob, w, n=65536):
+    """Max / p99 |d dist| and hit-decision mismatch rate off the 1e-4 band, against the FP64
+    oracle, on 65,536 rays in the unit ball."""
+    import numpy as np
+    import torch
+    from oracle import mlp as omlp
+    rng = np.random.default_rng(13)
+    o = rng.normal(size=(n, 3))
+    o = (o / np.linalg.norm(o, axis=1, keepdims=True) * rng.uniform(0.1, 1.0, (n, 1))).astype(np.float32)
+    d = rng.normal(size=(n, 3))
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    out = net.query(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda())
+    torch.cuda.synchronize()
+    ref = omlp.query(omlp.unpack(blob, w["in_freqs"], w["hidden"], w["layers"]), o, d, w["in_freqs"],
+                     with_normal=False)
+    err = np.abs(out["dist"].cpu().numpy() - ref["dist"])
+    clear = np.abs(ref["logit"]) >= 1e-4
+    mism = np.mean(out["hit"].cpu().numpy()[clear] != ref["hit"][clear])
+    return {"rays": n, "max_abs_dist": float(err.max()), "p99_abs_dist": float(np.percentile(err, 99)),
+            "hit_mismatch_rate": float(mism)}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -155,6 +155,15 @@ DDF_API int ddf_render(ddf_net net, const ddf_camera* cam, int spp, int bounces,
  * the stream of that render. */
 DDF_API int ddf_render_stats(ddf_net net, int64_t* host_counts, int max_bounces);
 
+/* Per-kernel timing of ddf_render on this handle with CUDA events recorded on the render's
+ * stream around each launch (off by default; a few microseconds per launch when on). */
+DDF_API int ddf_profile_enable(ddf_net net, int enable);
+
+/* Read and reset the accumulated timings (synchronises with the last render's stream).
+ * HOST array of 8 doubles: [query ms, query launches, shade ms, shade launches,
+ * raygen ms, raygen launches, accumulate ms, accumulate launches]. */
+DDF_API int ddf_profile_read(ddf_net net, double* host_out8);
+
 /* ---- labelling -------------------------------------------------------------------------- */
 
 /* Create a mesh from HOST float32 vertices (nv x 3) and int32 triangles (nt x 3), copied to

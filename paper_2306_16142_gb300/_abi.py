@@ -59,6 +59,8 @@ _SIG = {
     "ddf_query": (C.c_int, [_P, _P, _P, _I64, _P, _P, _P, _P, _P]),
     "ddf_render": (C.c_int, [_P, C.POINTER(ddf_camera), C.c_int, C.c_int, _P, _P]),
     "ddf_render_stats": (C.c_int, [_P, C.POINTER(_I64), C.c_int]),
+    "ddf_profile_enable": (C.c_int, [_P, C.c_int]),
+    "ddf_profile_read": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "ddf_mesh_create": (C.c_int, [_P, _I64, _P, _I64, C.POINTER(_P)]),
     "ddf_mesh_destroy": (C.c_int, [_P]),
     "ddf_label_rays": (C.c_int, [_P, _P, _P, _I64, _P, _P, _P, _P]),

@@ -86,8 +86,18 @@ int check_arch(const ddf_arch* a) {
     return DDF_OK;
 }
 
+void free_prof(Profiler& p) {
+    for (int i = 0; i < 2 * p.cap; ++i) cudaEventDestroy(p.ev[i]);
+    delete[] p.ev;
+    delete[] p.kind;
+    p.ev = nullptr;
+    p.kind = nullptr;
+    p.cap = p.used = 0;
+}
+
 void free_net(ddf_net_s* n) {
     if (!n) return;
+    free_prof(n->prof);
     tc_free(n);
     cudaFree(n->master);
     cudaFree(n->master_t);
@@ -247,6 +257,40 @@ int ddf_render_stats(ddf_net net, int64_t* host_counts, int max_bounces) {
     DDF_CUDA_TRY(cudaStreamSynchronize(net->last_stream));
     const int nb = std::min(max_bounces, net->last_bounces);
     DDF_CUDA_TRY(cudaMemcpy(host_counts, net->render_counts, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost));
+    return DDF_OK;
+}
+
+int ddf_profile_enable(ddf_net net, int enable) {
+    if (!net) return fail(DDF_ERR_INVALID_ARG, "net is NULL");
+    Profiler& p = net->prof;
+    if (enable && !p.ev) {
+        p.cap = 4096;
+        p.ev = new cudaEvent_t[2 * p.cap];
+        p.kind = new int[p.cap];
+        for (int i = 0; i < 2 * p.cap; ++i) DDF_CUDA_TRY(cudaEventCreate(&p.ev[i]));
+    }
+    p.on = enable != 0;
+    p.used = 0;
+    for (int k = 0; k < PROF_KINDS; ++k) p.ms[k] = p.count[k] = 0;
+    return DDF_OK;
+}
+
+int ddf_profile_read(ddf_net net, double* out) {
+    if (!net || !out) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    Profiler& p = net->prof;
+    for (int i = 0; i < p.used; ++i) {
+        DDF_CUDA_TRY(cudaEventSynchronize(p.ev[2 * i + 1]));
+        float ms = 0.f;
+        DDF_CUDA_TRY(cudaEventElapsedTime(&ms, p.ev[2 * i], p.ev[2 * i + 1]));
+        p.ms[p.kind[i]] += ms;
+        p.count[p.kind[i]] += 1;
+    }
+    p.used = 0;
+    for (int k = 0; k < PROF_KINDS; ++k) {
+        out[2 * k] = p.ms[k];
+        out[2 * k + 1] = p.count[k];
+        p.ms[k] = p.count[k] = 0;
+    }
     return DDF_OK;
 }
 

@@ -46,6 +46,26 @@ NetLayout make_layout(int in_freqs, int width, int L);
 
 struct TcPack;   // tensor-core packed weights (mlp_tc.cu)
 
+// CUDA-event timing of the renderer's launches, by kind.
+enum ProfKind { PROF_QUERY = 0, PROF_SHADE = 1, PROF_RAYGEN = 2, PROF_ACCUM = 3, PROF_KINDS = 4 };
+struct Profiler {
+    bool on = false;
+    cudaEvent_t* ev = nullptr;   // 2 * cap events
+    int* kind = nullptr;
+    int cap = 0, used = 0;
+    double ms[PROF_KINDS] = {0, 0, 0, 0};
+    double count[PROF_KINDS] = {0, 0, 0, 0};
+    int begin(int k, cudaStream_t s) {
+        if (!on || used >= cap) return -1;
+        kind[used] = k;
+        cudaEventRecord(ev[2 * used], s);
+        return used++;
+    }
+    void end(int idx, cudaStream_t s) {
+        if (idx >= 0) cudaEventRecord(ev[2 * idx + 1], s);
+    }
+};
+
 }  // namespace ddf
 
 struct ddf_net_s {
@@ -72,6 +92,7 @@ struct ddf_net_s {
     int render_counts_len = 0;
     int last_bounces = 0;
     cudaStream_t last_stream = nullptr;
+    ddf::Profiler prof;
 };
 
 struct ddf_mesh_s {

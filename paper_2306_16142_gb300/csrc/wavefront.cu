@@ -243,23 +243,31 @@ int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* i
         DDF_CUDA_TRY(cudaMemsetAsync(B.counts, 0, sizeof(int) * (bounces + 1), stream));
         const int64_t pid0 = px0 * spp;
         const int rg = (int)std::min<int64_t>((npaths + kThreads - 1) / kThreads, grid);
+        int pe = net->prof.begin(PROF_RAYGEN, stream);
         raygen_kernel<<<rg, kThreads, 0, stream>>>(cd, spp, pid0, npaths, B.o[0], B.w[0], B.lid[0],
                                                    B.thr[0], B.radiance, B.counts);
         DDF_LAUNCH_CHECK();
+        net->prof.end(pe, stream);
         for (int b = 1; b <= bounces; ++b) {
             const int s = (b - 1) & 1;
+            pe = net->prof.begin(PROF_QUERY, stream);
             int rc = field_query(net, B.o[s], B.w[s], npaths, B.counts + (b - 1), B.dist, B.logit,
                                  nullptr, b < bounces ? B.nrm : nullptr, stream);
             if (rc) return rc;
+            net->prof.end(pe, stream);
+            pe = net->prof.begin(PROF_SHADE, stream);
             shade_kernel<<<grid, kThreads, 0, stream>>>(cd, pid0, b, bounces, B.counts + (b - 1),
                                                         B.o[s], B.w[s], B.lid[s], B.thr[s], B.dist,
                                                         B.logit, B.nrm, B.o[s ^ 1], B.w[s ^ 1],
                                                         B.lid[s ^ 1], B.thr[s ^ 1], B.radiance,
                                                         B.counts + b);
             DDF_LAUNCH_CHECK();
+            net->prof.end(pe, stream);
         }
+        pe = net->prof.begin(PROF_ACCUM, stream);
         accumulate_kernel<<<grid, kThreads, 0, stream>>>(B.radiance, spp, px0, npx, image);
         DDF_LAUNCH_CHECK();
+        net->prof.end(pe, stream);
         add_counts<<<1, 64, 0, stream>>>(B.counts, bounces, net->render_counts);
         DDF_LAUNCH_CHECK();
     }

@@ -101,6 +101,15 @@ class DDFNet:
         check("ddf_render_stats", _abi.load().ddf_render_stats(self.h, arr, bounces))
         return list(arr)
 
+    def profile(self, enable: bool = True):
+        check("ddf_profile_enable", _abi.load().ddf_profile_enable(self.h, int(enable)))
+
+    def profile_read(self):
+        arr = (C.c_double * 8)()
+        check("ddf_profile_read", _abi.load().ddf_profile_read(self.h, arr))
+        keys = ["query", "shade", "raygen", "accumulate"]
+        return {k: {"ms": arr[2 * i], "launches": int(arr[2 * i + 1])} for i, k in enumerate(keys)}
+
     def set_weights(self, wt: torch.Tensor):
         check("ddf_set_weights", _abi.load().ddf_set_weights(self.h, _ptr(wt), wt.numel() * 4, _stream()))
 

@@ -68,7 +68,7 @@ def test_label_icosphere_65536_bit_exact(P):
     g = _gpu_label(P, V, F, o, w)
     d, h, t, _ = label_rays(V, F, o, w)
     _assert_exact(g, d, h, t)
-    assert 0.1 < h.mean() < 0.5
+    assert 0.03 < h.mean() < 0.2          # uniform rays from the unit sphere: ~6.7% meet r = 0.5
 
 
 def test_label_stress_rays_bit_exact(P):
