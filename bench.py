@@ -348,8 +348,9 @@ def main():
 
 
 def query_error(P, net, blob, w, n=65536):
-    """Max / p99 |d dist| and hit-decision mismatch rate off the 1e-4 band, against the FP64
-    oracle, on 65,536 rays in the unit ball."""
+    """Errors of the GPU query against the FP64 oracle on 65,536 rays in the unit ball: max / p99
+    |d dist|, hit-decision mismatch rate where |logit| >= 1e-4, and the angle between the GPU and
+    oracle Eq. 3 normals on rows both call hits (median / p99 degrees)."""
     import numpy as np
     import torch
     from oracle import mlp as omlp
@@ -358,15 +359,19 @@ def query_error(P, net, blob, w, n=65536):
     o = (o / np.linalg.norm(o, axis=1, keepdims=True) * rng.uniform(0.1, 1.0, (n, 1))).astype(np.float32)
     d = rng.normal(size=(n, 3))
     d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
-    out = net.query(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda())
+    out = net.query(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(), normals=True)
     torch.cuda.synchronize()
-    ref = omlp.query(omlp.unpack(blob, w["in_freqs"], w["hidden"], w["layers"]), o, d, w["in_freqs"],
-                     with_normal=False)
+    ref = omlp.query(omlp.unpack(blob, w["in_freqs"], w["hidden"], w["layers"]), o, d, w["in_freqs"])
     err = np.abs(out["dist"].cpu().numpy() - ref["dist"])
+    hit = out["hit"].cpu().numpy().astype(bool)
     clear = np.abs(ref["logit"]) >= 1e-4
-    mism = np.mean(out["hit"].cpu().numpy()[clear] != ref["hit"][clear])
+    mism = np.mean(hit[clear] != ref["hit"][clear])
+    both = hit & ref["hit"]
+    cos = np.clip(np.sum(out["normal"].cpu().numpy()[both] * ref["normal"][both], 1), -1, 1)
+    ang = np.degrees(np.arccos(cos)) if both.any() else np.zeros(1)
     return {"rays": n, "max_abs_dist": float(err.max()), "p99_abs_dist": float(np.percentile(err, 99)),
-            "hit_mismatch_rate": float(mism)}
+            "hit_mismatch_rate": float(mism), "normal_rows": int(both.sum()),
+            "normal_angle_deg_median": float(np.median(ang)), "normal_angle_deg_p99": float(np.percentile(ang, 99))}
 
 
 if __name__ == "__main__":

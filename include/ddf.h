@@ -113,6 +113,10 @@ DDF_API int ddf_destroy(ddf_net net);
  * Synchronous. UNSUPPORTED if the precision is not built for this architecture. */
 DDF_API int ddf_set_precision(ddf_net net, int precision);
 
+/* Synchronise the device and report whether a bounded device-side wait of this handle's
+ * kernels gave up since the last call (DDF_ERR_TIMEOUT, flag then cleared) or DDF_OK. */
+DDF_API int ddf_device_status(ddf_net net);
+
 /* Number of float32 values in the weight blob of this network. */
 DDF_API int ddf_num_params(ddf_net net, int64_t* out);
 

@@ -199,6 +199,12 @@ int ddf_set_precision(ddf_net net, int precision) {
     return DDF_OK;
 }
 
+int ddf_device_status(ddf_net net) {
+    if (!net) return fail(DDF_ERR_INVALID_ARG, "net is NULL");
+    DDF_CUDA_TRY(cudaDeviceSynchronize());
+    return tc_device_status(net);
+}
+
 int ddf_num_params(ddf_net net, int64_t* out) {
     if (!net || !out) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
     *out = net->is_sphere ? 0 : net->lay.n_params;

@@ -122,6 +122,7 @@ int build_transposed(ddf_net_s* net, cudaStream_t stream);
 bool tc_supported(const NetLayout& lay, int precision);
 int tc_pack(ddf_net_s* net, int precision, cudaStream_t stream);
 void tc_free(ddf_net_s* net);
+int tc_device_status(ddf_net_s* net);
 int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
                  const int* d_count, float* dist, float* logit, uint8_t* hit, float* normals,
                  cudaStream_t stream);

@@ -1,20 +1,678 @@
-// Tensor-core (tcgen05) DDF network query: BF16 / FP8 hidden-layer GEMMs with FP32
-// accumulators in tensor memory. (Not built yet: every request reports UNSUPPORTED.)
+// Tensor-core DDF network query for sm_103a: BF16 hidden-layer GEMMs on tcgen05 with FP32
+// accumulators in tensor memory, fed by TMA. (MLP_w of Sec. 4.1; normals by the gradient of
+// Eq. 3 / Sec. 4.2.)
+//
+// One persistent CTA per SM walks 128-row tiles; its 192 threads are split by role:
+//   warp 4      TMA producer: streams 64-wide K-blocks of each layer's packed BF16 weights
+//               (W rows x 128 B, 128-byte swizzle) through a ring of shared-memory stages;
+//   warp 5      MMA issuer: one thread issues tcgen05.mma (M = 128, N = W, K = 16) per
+//               16-wide K step, accumulating a layer into one of two TMEM buffers (layers
+//               alternate, so the next layer's MMAs overlap the current layer's epilogue);
+//   warps 0-3   epilogue: thread r owns row r / TMEM lane r. It encodes the row's input, and
+//               after each layer reads the accumulator (tcgen05.ld), adds the bias, applies the
+//               ReLU, rounds to BF16 and writes the next layer's A operand straight into the
+//               swizzled K-major shared-memory tile, releasing it 64 columns at a time, so the
+//               next layer's MMAs start on the first K-block while the rest is still being
+//               written. The 2-unit output head runs on CUDA cores in FP32.
+// Mode 0 evaluates all rows (distance, logit, hit) and appends hit rows to a list. Mode 1 takes
+// that list and runs the forward pass again followed by the reverse pass (same GEMM engine:
+// the transposed weights stream through the same ring) to d dist / d o, and the Eq. 3 normal.
+//
+// Every mbarrier wait is bounded (about 2 s of %globaltimer); on expiry the kernel raises a
+// device error flag, every role leaves its loop, TMEM is released and the host reports
+// DDF_ERR_TIMEOUT through ddf_device_status.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
 #include "ddf_internal.cuh"
+#include "device_common.cuh"
 
 namespace ddf {
 
-bool tc_supported(const NetLayout&, int) { return false; }
+struct TcPack {
+    int precision = 0;
+    int K0 = 0, kmax = 0;
+    __nv_bfloat16* w_fwd = nullptr;   // [L][W][kmax]  W_l row-major [out][in], K zero-padded
+    __nv_bfloat16* w_bwd = nullptr;   // [L][W][W]     W_l^T [in][out], layer-0 rows padded to W
+    float* bias = nullptr;            // [L][W]
+    float* head = nullptr;            // W_out [2][W], b_out [2]
+    CUtensorMap map_fwd, map_bwd;
+    int* hit_list = nullptr;
+    int64_t hit_cap = 0;
+    int* hit_count = nullptr;
+    int* err = nullptr;
+};
 
-int tc_pack(ddf_net_s*, int precision, cudaStream_t) {
-    return fail(DDF_ERR_UNSUPPORTED, "precision %d not built", precision);
+namespace {
+
+constexpr int kThreads = 192;
+constexpr int kTileM = 128;
+
+struct TcArgs {
+    int L, E, K0, nst;
+    uint32_t off_wst, off_mask, off_bias, off_head, off_bar;
+    const float* bias;
+    const float* head;
+    const float* o;
+    const float* w;
+    int64_t n;
+    const int* d_count;
+    const int* rows;
+    float* dist;
+    float* logit;
+    uint8_t* hit;
+    int* hit_list;
+    int* hit_count;
+    float* normals;
+    int* err;
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-void tc_free(ddf_net_s*) {}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase with parity `phase` to complete. false: gave up (error raised).
+__device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t phase, int* err) {
+    if (mbar_try(b, phase)) return true;
+    const uint64_t t0 = gtimer();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try(b, phase)) return true;
+        if ((i & 255u) == 0) {
+            if (*(volatile int*)err) return false;
+            if (gtimer() - t0 > 2000000000ull) {
+                atomicExch(err, 1);
+                return false;
+            }
+        }
+    }
+}
 
-int mlp_tc_query(const ddf_net_s*, const float*, const float*, int64_t, const int*, float*, float*,
-                 uint8_t*, float*, cudaStream_t) {
-    return fail(DDF_ERR_UNSUPPORTED, "tensor-core path not built");
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                            int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+        ::"r"(su32(dst)), "l"(map), "r"(su32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand tile with 128-byte swizzle: 8-row groups 1024 B apart (SBO), version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+#define TC_LD32(taddr, r)                                                                              \
+    asm volatile(                                                                                      \
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15," \
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                     \
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),         \
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),      \
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),   \
+          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),   \
+          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])                                           \
+        : "r"(taddr))
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Byte offset of 16-byte chunk q (0..7) of row r inside a 128-row x 128-byte swizzled K-block.
+__device__ __forceinline__ uint32_t swz(int r, int q) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((q ^ (r & 7)) << 4));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
+struct Step {
+    int bwd, layer, nk, N;
+};
+
+template <int W>
+__device__ __forceinline__ Step step_of(int s, int L, int KB0) {
+    if (s < L) return {0, s, s == 0 ? KB0 : W / 64, W};
+    const int l = 2 * L - 1 - s;
+    return {1, l, W / 64, l == 0 ? 128 : W};
+}
+
+// Write 32 consecutive values (columns c0..c0+31 of the row) as BF16 into the A-operand tile.
+__device__ __forceinline__ void write_act32(uint32_t act_base, int r, int c0, const float* v) {
+    const uint32_t kb_base = act_base + (uint32_t)(c0 >> 6) * 16384u;
+    const int q0 = (c0 & 63) >> 3;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        st_shared_v4(kb_base + swz(r, q0 + q), pack_bf16(v[8 * q + 0], v[8 * q + 1]),
+                     pack_bf16(v[8 * q + 2], v[8 * q + 3]), pack_bf16(v[8 * q + 4], v[8 * q + 5]),
+                     pack_bf16(v[8 * q + 6], v[8 * q + 7]));
+    }
+}
+
+// Release K-block kb of the A operand to the MMA issuer (after this thread's writes).
+__device__ __forceinline__ void release_kb(uint64_t* actr, int kb) {
+    fence_proxy_async();
+    tc_fence_before();
+    mbar_arrive(&actr[kb]);
+}
+
+template <int W, int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+    mlp_tc_kernel(const __grid_constant__ CUtensorMap mapF, const __grid_constant__ CUtensorMap mapB,
+                  const TcArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr int NKBW = W / 64;
+    const int L = a.L, KB0 = a.K0 / 64;
+    const int KMAXB = KB0 > NKBW ? KB0 : NKBW;
+    const int NST = a.nst;
+    uint8_t* act = smem;
+    uint8_t* wst = smem + a.off_wst;
+    uint32_t* masks = reinterpret_cast<uint32_t*>(smem + a.off_mask);
+    float* bias_s = reinterpret_cast<float*>(smem + a.off_bias);
+    float* head_s = reinterpret_cast<float*>(smem + a.off_head);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + NST;
+    uint64_t* actr = bars + 2 * NST;
+    uint64_t* accf = actr + KMAXB;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int64_t n = a.n;
+    if (a.d_count) n = min(n, (int64_t)*a.d_count);
+    const int64_t ntiles = (n + kTileM - 1) / kTileM;
+    const int nsteps = MODE == 0 ? L : 2 * L;
+    constexpr uint32_t kTmemCols = W <= 128 ? 256 : 512;
+
+    if (tid == 0) {
+        for (int i = 0; i < NST; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < KMAXB; ++i) mbar_init(&actr[i], 128);
+        mbar_init(&accf[0], 1);
+        mbar_init(&accf[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    for (int i = tid; i < L * W; i += kThreads) bias_s[i] = a.bias[i];
+    for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+
+    if (warp == 4) {
+        // ---------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            uint32_t cnt = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int s = 0; s < nsteps && ok; ++s) {
+                    const Step st = step_of<W>(s, L, KB0);
+                    for (int kb = 0; kb < st.nk; ++kb, ++cnt) {
+                        const int stg = (int)(cnt % (uint32_t)NST);
+                        const uint32_t ph = (cnt / (uint32_t)NST) & 1u;
+                        if (!mbar_wait(&empty[stg], ph ^ 1u, a.err)) { ok = false; break; }
+                        mbar_expect_tx(&full[stg], (uint32_t)W * 128u);
+                        tma_load_3d(wst + (size_t)stg * W * 128, st.bwd ? &mapB : &mapF, &full[stg], kb * 64, 0,
+                                    st.layer);
+                    }
+                }
+            }
+        }
+    } else if (warp == 5) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t cnt = 0, g = 0, actph = 0;
+            bool ok = true;
+            const uint32_t act_s = su32(act), wst_s = su32(wst);
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int s = 0; s < nsteps && ok; ++s, ++g) {
+                    const Step st = step_of<W>(s, L, KB0);
+                    const uint32_t d = tbase + (g & 1u) * (uint32_t)W;
+                    const uint32_t idesc = idesc_bf16(128, st.N);
+                    for (int kb = 0; kb < st.nk; ++kb, ++cnt) {
+                        const int stg = (int)(cnt % (uint32_t)NST);
+                        const uint32_t ph = (cnt / (uint32_t)NST) & 1u;
+                        if (!mbar_wait(&full[stg], ph, a.err)) { ok = false; break; }
+                        if (!mbar_wait(&actr[kb], (actph >> kb) & 1u, a.err)) { ok = false; break; }
+                        actph ^= 1u << kb;
+                        tc_fence_after();
+                        const uint64_t ad = sdesc(act_s + (uint32_t)kb * 16384u);
+                        const uint64_t bd = sdesc(wst_s + (uint32_t)stg * (uint32_t)W * 128u);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                        mma_commit(&empty[stg]);
+                    }
+                    if (ok) mma_commit(&accf[g & 1u]);
+                }
+            }
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue (rows)
+        const int r = tid;   // 0..127 = TMEM lane
+        const uint32_t act_s = su32(act);
+        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+        uint32_t g = 0, accph = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int64_t i = t * kTileM + r;
+            const bool valid = i < n;
+            int64_t row = -1;
+            if (valid) row = MODE == 0 ? i : (int64_t)a.rows[i];
+            float v[6];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[c] = valid ? a.o[row * 3 + c] : 0.f;
+                v[c + 3] = valid ? a.w[row * 3 + c] : 0.f;
+            }
+            // input encoding -> K-blocks 0 .. KB0-1
+            for (int kb = 0; kb < KB0; ++kb) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    float f8[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int f = kb * 64 + q * 8 + e;
+                        f8[e] = f < a.E ? encode_feature(f, v) : 0.f;
+                    }
+                    st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, q), pack_bf16(f8[0], f8[1]),
+                                 pack_bf16(f8[2], f8[3]), pack_bf16(f8[4], f8[5]), pack_bf16(f8[6], f8[7]));
+                }
+                release_kb(actr, kb);
+            }
+            float y0 = 0.f, y1 = 0.f;
+            for (int s = 0; s < nsteps && ok; ++s, ++g) {
+                const int b = (int)(g & 1u);
+                ok = mbar_wait(&accf[b], (accph >> b) & 1u, a.err);
+                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }   // warp-uniform exit
+                accph ^= 1u << b;
+                tc_fence_after();
+                const uint32_t tcol = tbase + lane_off + (uint32_t)(b * W);
+                if (s < L) {
+                    // forward layer s: z = acc + b_s
+                    const float* bs = bias_s + s * W;
+                    for (int j = 0; j < W / 32; ++j) {
+                        uint32_t raw[32];
+                        TC_LD32(tcol + 32 * j, raw);
+                        tc_wait_ld();
+                        float z[32];
+                        uint32_t bits = 0;
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            z[c] = __uint_as_float(raw[c]) + bs[32 * j + c];
+                            bits |= (z[c] > 0.f ? 1u : 0u) << c;
+                            z[c] = fmaxf(z[c], 0.f);
+                        }
+                        if (s < L - 1) {
+                            if (MODE == 1) masks[(s * (W / 32) + j) * 128 + r] = bits;
+                            write_act32(act_s, r, 32 * j, z);
+                        } else if (MODE == 0) {
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) {
+                                y0 = fmaf(z[c], head_s[32 * j + c], y0);
+                                y1 = fmaf(z[c], head_s[W + 32 * j + c], y1);
+                            }
+                        } else {
+                            // delta of the last hidden layer: W_out[0] on active units
+                            float dl[32];
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) dl[c] = ((bits >> c) & 1u) ? head_s[32 * j + c] : 0.f;
+                            write_act32(act_s, r, 32 * j, dl);
+                        }
+                        if ((j & 1) && (s < L - 1 || MODE == 1)) release_kb(actr, j >> 1);
+                    }
+                    if (s == L - 1 && MODE == 0) {
+                        tc_fence_before();
+                        y0 += head_s[2 * W];
+                        y1 += head_s[2 * W + 1];
+                        const bool h = y1 > 0.f;
+                        if (valid) {
+                            a.dist[row] = y0;
+                            if (a.logit) a.logit[row] = y1;
+                            if (a.hit) a.hit[row] = (uint8_t)h;
+                        }
+                        if (a.hit_list) {
+                            const bool take = valid && h;
+                            const unsigned m = __ballot_sync(0xffffffffu, take);
+                            int base = 0;
+                            if (lane == 0 && m) base = atomicAdd(a.hit_count, __popc(m));
+                            base = __shfl_sync(0xffffffffu, base, 0);
+                            if (take) a.hit_list[base + __popc(m & ((1u << lane) - 1u))] = (int)row;
+                        }
+                    }
+                } else {
+                    const int l = 2 * L - 1 - s;
+                    if (l >= 1) {
+                        // delta_{l-1} = (delta_l W_l) * 1[z_{l-1} > 0]
+                        for (int j = 0; j < W / 32; ++j) {
+                            uint32_t raw[32];
+                            TC_LD32(tcol + 32 * j, raw);
+                            tc_wait_ld();
+                            const uint32_t bits = masks[((l - 1) * (W / 32) + j) * 128 + r];
+                            float dl[32];
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) dl[c] = ((bits >> c) & 1u) ? __uint_as_float(raw[c]) : 0.f;
+                            write_act32(act_s, r, 32 * j, dl);
+                            if (j & 1) release_kb(actr, j >> 1);
+                        }
+                    } else {
+                        // d dist / d features (columns 0..E-1), then the encoding chain rule
+                        float gx[3] = {0.f, 0.f, 0.f};
+                        for (int j = 0; j < 4; ++j) {
+                            if (32 * j >= a.E) break;
+                            uint32_t raw[32];
+                            TC_LD32(tcol + 32 * j, raw);
+                            tc_wait_ld();
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) {
+                                const int f = 32 * j + c;
+                                if (f < a.E && (f % 6) < 3)
+                                    gx[f % 6] = fmaf(__uint_as_float(raw[c]), encode_dfeature(f, v), gx[f % 6]);
+                            }
+                        }
+                        tc_fence_before();
+                        if (valid) {
+                            const float3 nn = normal_from_grad(gx[0], gx[1], gx[2], v[3], v[4], v[5]);
+                            a.normals[row * 3 + 0] = nn.x;
+                            a.normals[row * 3 + 1] = nn.y;
+                            a.normals[row * 3 + 2] = nn.z;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (*(volatile int*)a.err) {
+        // error path: let MMAs and TMA copies already issued drain (they wait on nothing)
+        const uint64_t t0 = gtimer();
+        while (gtimer() - t0 < 200000ull) {
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols));
+    }
+}
+
+// ------------------------------------------------------------------ packing
+__global__ void pack_kernel(const float* __restrict__ master, NetLayout lay, int kmax,
+                            __nv_bfloat16* __restrict__ wf, __nv_bfloat16* __restrict__ wb,
+                            float* __restrict__ bias, float* __restrict__ head) {
+    const int W = lay.width;
+    const int l = blockIdx.y;
+    const int in = l == 0 ? lay.E : W;
+    const float* Wl = master + lay.w_off[l];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)W * kmax;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int rr = (int)(i / kmax), k = (int)(i % kmax);
+        wf[(int64_t)l * W * kmax + i] = __float2bfloat16_rn(k < in ? Wl[(int64_t)rr * in + k] : 0.f);
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)W * W;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int rr = (int)(i / W), c = (int)(i % W);   // row = input unit, col = output unit
+        wb[(int64_t)l * W * W + i] = __float2bfloat16_rn(rr < in ? Wl[(int64_t)c * in + rr] : 0.f);
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < W; i += gridDim.x * blockDim.x)
+        bias[l * W + i] = master[lay.b_off[l] + i];
+    if (l == 0)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * W + 2; i += gridDim.x * blockDim.x)
+            head[i] = i < 2 * W ? master[lay.w_off[lay.L] + i] : master[lay.b_off[lay.L] + i - 2 * W];
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+int make_map(CUtensorMap* m, void* base, int inner, int rows, int L) {
+    EncodeTiledFn enc = get_encode();
+    if (!enc) return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)L};
+    cuuint64_t strides[2] = {(cuuint64_t)inner * 2, (cuuint64_t)inner * rows * 2};
+    cuuint32_t box[3] = {64, (cuuint32_t)rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return DDF_OK;
+}
+
+struct Layout {
+    uint32_t off_wst, off_mask, off_bias, off_head, off_bar, total;
+    int nst;
+};
+
+Layout smem_layout(int W, int L, int K0, int mode) {
+    Layout s;
+    const int kmaxb = std::max(K0 / 64, W / 64);
+    const uint32_t act = (uint32_t)kmaxb * 16384u;
+    const uint32_t stage = (uint32_t)W * 128u;
+    const uint32_t mask = mode == 1 ? (uint32_t)L * 128u * (W / 32) * 4u : 0u;
+    const uint32_t bias = (uint32_t)L * W * 4u;
+    const uint32_t head = (uint32_t)(2 * W + 2) * 4u;
+    const uint32_t fixed = act + mask + bias + ((head + 15) & ~15u) + 512u;
+    const uint32_t budget = 227u * 1024u - 1024u;   // minus alignment slack
+    int nst = (int)((budget - fixed) / stage);
+    s.nst = std::max(0, std::min(8, nst));
+    s.off_wst = act;
+    s.off_mask = act + (uint32_t)s.nst * stage;
+    s.off_bias = s.off_mask + mask;
+    s.off_head = s.off_bias + bias;
+    s.off_bar = (s.off_head + head + 15) & ~15u;
+    s.total = s.off_bar + 512u + 1024u;
+    return s;
+}
+
+template <int W>
+int launch_mode(const ddf_net_s* net, int mode, const TcArgs& base, int64_t n, bool use_count,
+                cudaStream_t stream) {
+    const TcPack* P = net->tc;
+    TcArgs a = base;
+    const Layout s = smem_layout(W, a.L, a.K0, mode);
+    if (s.nst < 2) return fail(DDF_ERR_UNSUPPORTED, "tensor-core MLP: shared memory too small");
+    a.nst = s.nst;
+    a.off_wst = s.off_wst;
+    a.off_mask = s.off_mask;
+    a.off_bias = s.off_bias;
+    a.off_head = s.off_head;
+    a.off_bar = s.off_bar;
+    int grid = use_count ? num_sms() : (int)std::min<int64_t>((n + kTileM - 1) / kTileM, num_sms());
+    if (grid <= 0) return DDF_OK;
+    if (mode == 0) {
+        static bool attr = false;
+        if (!attr) {
+            DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_tc_kernel<W, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              227 * 1024));
+            attr = true;
+        }
+        mlp_tc_kernel<W, 0><<<grid, kThreads, s.total, stream>>>(P->map_fwd, P->map_bwd, a);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_tc_kernel<W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              227 * 1024));
+            attr = true;
+        }
+        mlp_tc_kernel<W, 1><<<grid, kThreads, s.total, stream>>>(P->map_fwd, P->map_bwd, a);
+    }
+    DDF_LAUNCH_CHECK();
+    return DDF_OK;
+}
+
+}  // namespace
+
+bool tc_supported(const NetLayout& lay, int precision) {
+    if (precision != DDF_BF16) return false;
+    if (lay.width != 128 && lay.width != 256) return false;
+    if (lay.E > 128) return false;
+    return lay.L >= 1 && lay.L <= kMaxLayers && smem_layout(lay.width, lay.L, 64 * ((lay.E + 63) / 64), 1).nst >= 2;
+}
+
+void tc_free(ddf_net_s* net) {
+    TcPack* P = net->tc;
+    if (!P) return;
+    cudaFree(P->w_fwd);
+    cudaFree(P->w_bwd);
+    cudaFree(P->bias);
+    cudaFree(P->head);
+    cudaFree(P->hit_list);
+    cudaFree(P->hit_count);
+    cudaFree(P->err);
+    delete P;
+    net->tc = nullptr;
+}
+
+int tc_pack(ddf_net_s* net, int precision, cudaStream_t stream) {
+    const NetLayout& lay = net->lay;
+    if (!tc_supported(lay, precision)) return fail(DDF_ERR_UNSUPPORTED, "precision %d not built for this shape", precision);
+    TcPack* P = net->tc;
+    const int W = lay.width, L = lay.L;
+    if (!P) {
+        P = new TcPack();
+        net->tc = P;
+        P->K0 = 64 * ((lay.E + 63) / 64);
+        P->kmax = std::max(P->K0, W);
+        DDF_CUDA_TRY(cudaMalloc(&P->w_fwd, sizeof(__nv_bfloat16) * (size_t)L * W * P->kmax));
+        DDF_CUDA_TRY(cudaMalloc(&P->w_bwd, sizeof(__nv_bfloat16) * (size_t)L * W * W));
+        DDF_CUDA_TRY(cudaMalloc(&P->bias, sizeof(float) * (size_t)L * W));
+        DDF_CUDA_TRY(cudaMalloc(&P->head, sizeof(float) * (size_t)(2 * W + 2)));
+        DDF_CUDA_TRY(cudaMalloc(&P->hit_count, sizeof(int)));
+        DDF_CUDA_TRY(cudaMalloc(&P->err, sizeof(int)));
+        DDF_CUDA_TRY(cudaMemset(P->err, 0, sizeof(int)));
+        int rc = make_map(&P->map_fwd, P->w_fwd, P->kmax, W, L);
+        if (rc) return rc;
+        rc = make_map(&P->map_bwd, P->w_bwd, W, W, L);
+        if (rc) return rc;
+    }
+    P->precision = precision;
+    dim3 grid(64, L);
+    pack_kernel<<<grid, 256, 0, stream>>>(net->master, lay, P->kmax, P->w_fwd, P->w_bwd, P->bias, P->head);
+    DDF_LAUNCH_CHECK();
+    return DDF_OK;
+}
+
+int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n, const int* d_count,
+                 float* dist, float* logit, uint8_t* hit, float* normals, cudaStream_t stream) {
+    TcPack* P = net->tc;
+    if (!P) return fail(DDF_ERR_UNSUPPORTED, "tensor-core weights not packed");
+    const NetLayout& lay = net->lay;
+    if (normals && P->hit_cap < n) {
+        cudaFree(P->hit_list);
+        P->hit_list = nullptr;
+        P->hit_cap = 0;
+        DDF_CUDA_TRY(cudaMalloc(&P->hit_list, sizeof(int) * (size_t)std::max<int64_t>(n, 1024)));
+        P->hit_cap = std::max<int64_t>(n, 1024);
+    }
+    TcArgs a{};
+    a.L = lay.L;
+    a.E = lay.E;
+    a.K0 = P->K0;
+    a.bias = P->bias;
+    a.head = P->head;
+    a.o = o;
+    a.w = w;
+    a.n = n;
+    a.d_count = d_count;
+    a.dist = dist;
+    a.logit = logit;
+    a.hit = hit;
+    a.err = P->err;
+    if (normals) {
+        DDF_CUDA_TRY(cudaMemsetAsync(P->hit_count, 0, sizeof(int), stream));
+        a.hit_list = P->hit_list;
+        a.hit_count = P->hit_count;
+    }
+    int rc = lay.width == 128 ? launch_mode<128>(net, 0, a, n, d_count != nullptr, stream)
+                              : launch_mode<256>(net, 0, a, n, d_count != nullptr, stream);
+    if (rc || !normals) return rc;
+    TcArgs b = a;
+    b.rows = P->hit_list;
+    b.d_count = P->hit_count;
+    b.hit_list = nullptr;
+    b.hit_count = nullptr;
+    b.dist = nullptr;
+    b.logit = nullptr;
+    b.hit = nullptr;
+    b.normals = normals;
+    return lay.width == 128 ? launch_mode<128>(net, 1, b, n, true, stream)
+                            : launch_mode<256>(net, 1, b, n, true, stream);
+}
+
+int tc_device_status(ddf_net_s* net) {
+    if (!net->tc) return DDF_OK;
+    int h = 0;
+    DDF_CUDA_TRY(cudaMemcpy(&h, net->tc->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        cudaMemset(net->tc->err, 0, sizeof(int));
+        return fail(DDF_ERR_TIMEOUT, "a tensor-core kernel wait timed out");
+    }
+    return DDF_OK;
 }
 
 }  // namespace ddf

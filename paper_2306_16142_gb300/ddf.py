@@ -72,6 +72,10 @@ class DDFNet:
         except Exception:
             pass
 
+    def device_status(self):
+        """Raise DDFError(TIMEOUT) if a bounded device wait of this handle gave up."""
+        check("ddf_device_status", _abi.load().ddf_device_status(self.h))
+
     def set_precision(self, precision: str):
         check("ddf_set_precision", _abi.load().ddf_set_precision(self.h, PRECISIONS[precision]))
         self.precision = precision
