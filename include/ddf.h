@@ -140,6 +140,21 @@ DDF_API int ddf_get_weights(ddf_net net, float* d_out, size_t nbytes, cudaStream
 DDF_API int ddf_query(ddf_net net, const float* d_origins, const float* d_dirs, int64_t n, float* d_dist,
               uint8_t* d_hit, float* d_logit, float* d_normals, cudaStream_t stream);
 
+/* Allocation-free variant of ddf_query for callers that must not allocate device memory
+ * while they run (for example an engine whose every allocation goes through its own pool, or
+ * a render loop that forbids allocation once started). The paper has no counterpart: it is an
+ * interface variant, not a step of the method. Same arguments, outputs and results as
+ * ddf_query; it calls no cudaMalloc / cudaFree. The BF16 path's hit-row list, the only scratch
+ * a query needs, lives in a fixed static device array of the library (4 MiB + 256 B per GPU
+ * that loads the library, held until exit), so n is limited to 2^20 rows; larger n returns
+ * DDF_ERR_INVALID_ARG. The first call on each device looks the array's address up once
+ * (cudaGetSymbolAddress), so make that first call before any stream capture. Every call on a
+ * device shares the array: calls whose work overlaps on the GPU (different streams without
+ * ordering between them) race on it and must be serialised by the caller. */
+DDF_API int ddf_query_noalloc(ddf_net net, const float* d_origins, const float* d_dirs, int64_t n,
+                              float* d_dist, uint8_t* d_hit, float* d_logit, float* d_normals,
+                              cudaStream_t stream);
+
 /* ---- renderer --------------------------------------------------------------------------- */
 
 /* The modified uni-directional path tracer (Sec. 1, Fig. 1) as a wavefront loop on the

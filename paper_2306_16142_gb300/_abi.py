@@ -58,6 +58,7 @@ _SIG = {
     "ddf_set_weights": (C.c_int, [_P, _P, C.c_size_t, _P]),
     "ddf_get_weights": (C.c_int, [_P, _P, C.c_size_t, _P]),
     "ddf_query": (C.c_int, [_P, _P, _P, _I64, _P, _P, _P, _P, _P]),
+    "ddf_query_noalloc": (C.c_int, [_P, _P, _P, _I64, _P, _P, _P, _P, _P]),
     "ddf_render": (C.c_int, [_P, C.POINTER(ddf_camera), C.c_int, C.c_int, _P, _P]),
     "ddf_render_stats": (C.c_int, [_P, C.POINTER(_I64), C.c_int]),
     "ddf_profile_enable": (C.c_int, [_P, C.c_int]),

@@ -24,6 +24,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "ddf_internal.cuh"
 #include "device_common.cuh"
 
@@ -676,3 +678,97 @@ int tc_device_status(ddf_net_s* net) {
 }
 
 }  // namespace ddf
+
+// ------------------------------------------------------------------ allocation-free query
+// ddf_query_noalloc serves callers that must not allocate device memory during a call: for
+// example an engine that routes every allocation through its own pool, or a render loop that
+// forbids allocation once it is running. The only scratch the BF16 query needs, the list of
+// hit rows handed from the forward launch to the normal launch plus its counter, lives in
+// the fixed array below instead of the handle's grow-on-demand buffer. The array is part of
+// the library's device image: every GPU that loads the library holds it until the process
+// exits, and every call on a device shares it.
+namespace {
+
+constexpr int64_t kNoAllocMaxRows = int64_t(1) << 20;   // 4 MiB of row indices
+constexpr int kNoAllocHead = 64;                         // counter + padding to 256 bytes
+
+static __device__ __align__(256) int g_noalloc_scratch[kNoAllocHead + kNoAllocMaxRows];
+
+std::mutex g_noalloc_mu;
+int* g_noalloc_addr[64] = {nullptr};
+
+// Device address of the array on the current device, looked up once per device.
+int noalloc_scratch(int** out) {
+    int dev = 0;
+    DDF_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return ddf::fail(DDF_ERR_UNSUPPORTED, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return ddf::fail(DDF_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        g_noalloc_addr[dev] = static_cast<int*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return DDF_OK;
+}
+
+}  // namespace
+
+extern "C" DDF_API int ddf_query_noalloc(ddf_net net, const float* d_origins, const float* d_dirs,
+                                         int64_t n, float* d_dist, uint8_t* d_hit, float* d_logit,
+                                         float* d_normals, cudaStream_t stream) {
+    using namespace ddf;
+    if (!net) return fail(DDF_ERR_INVALID_ARG, "net is NULL");
+    if (n < 0) return fail(DDF_ERR_INVALID_ARG, "n < 0");
+    if (n > kNoAllocMaxRows)
+        return fail(DDF_ERR_INVALID_ARG,
+                    "ddf_query_noalloc: n = %lld rows exceeds the static scratch limit of %lld rows",
+                    (long long)n, (long long)kNoAllocMaxRows);
+    if (n == 0) return DDF_OK;
+    if (!d_origins || !d_dirs || !d_dist || !d_hit)
+        return fail(DDF_ERR_INVALID_ARG, "origins, dirs, dist and hit must be non-NULL");
+    // The sphere field, the FP32 path and a BF16 query without normals use no scratch.
+    if (net->is_sphere || net->precision == DDF_FP32 || !d_normals)
+        return field_query(net, d_origins, d_dirs, n, nullptr, d_dist, d_logit, d_hit, d_normals, stream);
+    TcPack* P = net->tc;
+    if (!P) return fail(DDF_ERR_UNSUPPORTED, "tensor-core weights not packed");
+    int* scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    int* hit_count = scratch;
+    int* hit_list = scratch + kNoAllocHead;
+    // the array keeps the previous call's contents: the counter must start at zero
+    DDF_CUDA_TRY(cudaMemsetAsync(hit_count, 0, sizeof(int), stream));
+    const NetLayout& lay = net->lay;
+    TcArgs a{};
+    a.L = lay.L;
+    a.E = lay.E;
+    a.K0 = P->K0;
+    a.bias = P->bias;
+    a.head = P->head;
+    a.o = d_origins;
+    a.w = d_dirs;
+    a.n = n;
+    a.dist = d_dist;
+    a.logit = d_logit;
+    a.hit = d_hit;
+    a.err = P->err;
+    a.hit_list = hit_list;
+    a.hit_count = hit_count;
+    rc = lay.width == 128 ? launch_mode<128>(net, 0, a, n, false, stream)
+                          : launch_mode<256>(net, 0, a, n, false, stream);
+    if (rc) return rc;
+    TcArgs b = a;
+    b.rows = hit_list;
+    b.d_count = hit_count;
+    b.hit_list = nullptr;
+    b.hit_count = nullptr;
+    b.dist = nullptr;
+    b.logit = nullptr;
+    b.hit = nullptr;
+    b.normals = d_normals;
+    return lay.width == 128 ? launch_mode<128>(net, 1, b, n, true, stream)
+                            : launch_mode<256>(net, 1, b, n, true, stream);
+}
