@@ -47,12 +47,13 @@ struct TcPack {
 
 namespace {
 
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = (kEpiWarps + 2) * 32;
 constexpr int kTileM = 128;
 
 struct TcArgs {
     int L, E, K0, nst;
-    uint32_t off_wst, off_mask, off_bias, off_head, off_bar;
+    uint32_t off_wst, off_mask, off_bias, off_head, off_part, off_bar;
     const float* bias;
     const float* head;
     const float* o;
@@ -172,6 +173,21 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
                  : "memory");
 }
 
+// d = a + b on two FP32 lanes at once (packed FP32 add).
+__device__ __forceinline__ void add2(float ax, float ay, float bx, float by, float& dx, float& dy) {
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " add.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}\n"
+        : "=f"(dx), "=f"(dy)
+        : "f"(ax), "f"(ay), "f"(bx), "f"(by));
+}
+// BF16x2 of (ReLU(lo), ReLU(hi)), lo in the low half.
+__device__ __forceinline__ uint32_t pack_relu(float lo, float hi) {
+    uint32_t p;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(p) : "f"(hi), "f"(lo));
+    return p;
+}
+__device__ __forceinline__ uint32_t pos(float z) { return (int)__float_as_uint(z) > 0 ? 1u : 0u; }
+
 struct Step {
     int bwd, layer, nk, N;
 };
@@ -202,6 +218,17 @@ __device__ __forceinline__ void release_kb(uint64_t* actr, int kb) {
     mbar_arrive(&actr[kb]);
 }
 
+// Input feature order inside the tensor-core path: the six raw coordinates, two zero columns,
+// then per octave k the sines and cosines of 2^k pi v_j (the order of the encoding with the raw
+// block padded to one 16-byte chunk). The packed first-layer weights use the same order.
+__device__ __forceinline__ float enc_internal(int p, int E, const float v[6]) {
+    if (p < 8) return p < 6 ? v[p] : 0.f;
+    const int f = p - 2;
+    return f < E ? encode_feature(f, v) : 0.f;
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
 template <int W, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     mlp_tc_kernel(const __grid_constant__ CUtensorMap mapF, const __grid_constant__ CUtensorMap mapB,
@@ -217,6 +244,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t* masks = reinterpret_cast<uint32_t*>(smem + a.off_mask);
     float* bias_s = reinterpret_cast<float*>(smem + a.off_bias);
     float* head_s = reinterpret_cast<float*>(smem + a.off_head);
+    float* part = reinterpret_cast<float*>(smem + a.off_part);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
     uint64_t* full = bars;
     uint64_t* empty = bars + NST;
@@ -236,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
-        for (int i = 0; i < KMAXB; ++i) mbar_init(&actr[i], 128);
+        for (int i = 0; i < KMAXB; ++i) mbar_init(&actr[i], 256);
         mbar_init(&accf[0], 1);
         mbar_init(&accf[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -252,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tbase = *tslot;
 
-    if (warp == 4) {
+    if (warp == kEpiWarps) {
         // ---------------------------------------------------------------- TMA producer
         if (lane == 0) {
             uint32_t cnt = 0;
@@ -271,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
-    } else if (warp == 5) {
+    } else if (warp == kEpiWarps + 1) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
             uint32_t cnt = 0, g = 0, actph = 0;
@@ -301,10 +329,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else {
-        // ---------------------------------------------------------------- epilogue (rows)
-        const int r = tid;   // 0..127 = TMEM lane
+        // ---------------------------------------------------------------- epilogue
+        // Two groups of four warps; warp w serves TMEM lanes 32 (w % 4) .. +31 (its rows) and
+        // group w / 4 owns columns [32 group, 32 group + 32) of every 64-column K-block, so each
+        // K-block of the next layer's A operand is written by both groups at once (256 arrivals)
+        // and K-block 0 is released after 32 columns of work per thread.
+        const int grp = warp >> 2;
+        const int r = (warp & 3) * 32 + lane;
         const uint32_t act_s = su32(act);
-        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         uint32_t g = 0, accph = 0;
         bool ok = true;
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -318,17 +351,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 v[c] = valid ? a.o[row * 3 + c] : 0.f;
                 v[c + 3] = valid ? a.w[row * 3 + c] : 0.f;
             }
-            // input encoding -> K-blocks 0 .. KB0-1
+            // input encoding: each group writes half of every first-layer K-block
             for (int kb = 0; kb < KB0; ++kb) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
+                for (int q = 0; q < 4; ++q) {
+                    const int qq = grp * 4 + q;
                     float f8[8];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int f = kb * 64 + q * 8 + e;
-                        f8[e] = f < a.E ? encode_feature(f, v) : 0.f;
-                    }
-                    st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, q), pack_bf16(f8[0], f8[1]),
+                    for (int e = 0; e < 8; ++e) f8[e] = enc_internal(kb * 64 + qq * 8 + e, a.E, v);
+                    st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, qq), pack_bf16(f8[0], f8[1]),
                                  pack_bf16(f8[2], f8[3]), pack_bf16(f8[4], f8[5]), pack_bf16(f8[6], f8[7]));
                 }
                 release_kb(actr, kb);
@@ -340,96 +371,139 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }   // warp-uniform exit
                 accph ^= 1u << b;
                 tc_fence_after();
-                const uint32_t tcol = tbase + lane_off + (uint32_t)(b * W);
-                if (s < L) {
-                    // forward layer s: z = acc + b_s
-                    const float* bs = bias_s + s * W;
-                    for (int j = 0; j < W / 32; ++j) {
-                        uint32_t raw[32];
-                        TC_LD32(tcol + 32 * j, raw);
-                        tc_wait_ld();
-                        float z[32];
-                        uint32_t bits = 0;
+                const uint32_t tcol = tbase + lane_off + (uint32_t)(b * W) + (uint32_t)(grp * 32);
+                const int l_bwd = 2 * L - 1 - s;
+                if (s < L || l_bwd >= 1) {
+                    // all of this thread's accumulator columns, one wait
+                    uint32_t raw[NKBW][32];
 #pragma unroll
-                        for (int c = 0; c < 32; ++c) {
-                            z[c] = __uint_as_float(raw[c]) + bs[32 * j + c];
-                            bits |= (z[c] > 0.f ? 1u : 0u) << c;
-                            z[c] = fmaxf(z[c], 0.f);
-                        }
-                        if (s < L - 1) {
-                            if (MODE == 1) masks[(s * (W / 32) + j) * 128 + r] = bits;
-                            write_act32(act_s, r, 32 * j, z);
-                        } else if (MODE == 0) {
+                    for (int kb = 0; kb < NKBW; ++kb) TC_LD32(tcol + kb * 64, raw[kb]);
+                    tc_wait_ld();
+                    if (s < L) {
+                        const float* bs = bias_s + s * W;
 #pragma unroll
-                            for (int c = 0; c < 32; ++c) {
-                                y0 = fmaf(z[c], head_s[32 * j + c], y0);
-                                y1 = fmaf(z[c], head_s[W + 32 * j + c], y1);
+                        for (int kb = 0; kb < NKBW; ++kb) {
+                            const int c0 = kb * 64 + grp * 32;
+                            const float4* b4 = reinterpret_cast<const float4*>(bs + c0);
+                            if (s < L - 1) {
+                                // a = ReLU(acc + b) rounded to BF16 -> next A operand
+                                uint32_t pk[16];
+                                uint32_t bits = 0;
+#pragma unroll
+                                for (int q = 0; q < 8; ++q) {
+                                    const float4 bb = b4[q];
+                                    float z0, z1, z2, z3;
+                                    add2(__uint_as_float(raw[kb][4 * q]), __uint_as_float(raw[kb][4 * q + 1]), bb.x,
+                                         bb.y, z0, z1);
+                                    add2(__uint_as_float(raw[kb][4 * q + 2]), __uint_as_float(raw[kb][4 * q + 3]),
+                                         bb.z, bb.w, z2, z3);
+                                    pk[2 * q] = pack_relu(z0, z1);
+                                    pk[2 * q + 1] = pack_relu(z2, z3);
+                                    if (MODE == 1)
+                                        bits |= (pos(z0) | pos(z1) << 1 | pos(z2) << 2 | pos(z3) << 3) << (4 * q);
+                                }
+                                if (MODE == 1) masks[(s * (W / 32) + (c0 >> 5)) * 128 + r] = bits;
+#pragma unroll
+                                for (int m = 0; m < 4; ++m)
+                                    st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
+                                                 pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
+                                release_kb(actr, kb);
+                            } else if (MODE == 0) {
+                                // output head on this thread's columns (FP32)
+#pragma unroll
+                                for (int c = 0; c < 32; ++c) {
+                                    const float z = fmaxf(__uint_as_float(raw[kb][c]) + bs[c0 + c], 0.f);
+                                    y0 = fmaf(z, head_s[c0 + c], y0);
+                                    y1 = fmaf(z, head_s[W + c0 + c], y1);
+                                }
+                            } else {
+                                // delta of the last hidden layer: W_out[0] on active units
+                                uint32_t pk[16];
+#pragma unroll
+                                for (int q = 0; q < 16; ++q) {
+                                    const float z0 = __uint_as_float(raw[kb][2 * q]) + bs[c0 + 2 * q];
+                                    const float z1 = __uint_as_float(raw[kb][2 * q + 1]) + bs[c0 + 2 * q + 1];
+                                    pk[q] = pack_bf16(z0 > 0.f ? head_s[c0 + 2 * q] : 0.f,
+                                                      z1 > 0.f ? head_s[c0 + 2 * q + 1] : 0.f);
+                                }
+#pragma unroll
+                                for (int m = 0; m < 4; ++m)
+                                    st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
+                                                 pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
+                                release_kb(actr, kb);
                             }
-                        } else {
-                            // delta of the last hidden layer: W_out[0] on active units
-                            float dl[32];
-#pragma unroll
-                            for (int c = 0; c < 32; ++c) dl[c] = ((bits >> c) & 1u) ? head_s[32 * j + c] : 0.f;
-                            write_act32(act_s, r, 32 * j, dl);
                         }
-                        if ((j & 1) && (s < L - 1 || MODE == 1)) release_kb(actr, j >> 1);
+                    } else {
+                        // delta_{l-1} = (delta_l W_l) * 1[z_{l-1} > 0]
+#pragma unroll
+                        for (int kb = 0; kb < NKBW; ++kb) {
+                            const int c0 = kb * 64 + grp * 32;
+                            const uint32_t bits = masks[((l_bwd - 1) * (W / 32) + (c0 >> 5)) * 128 + r];
+                            uint32_t pk[16];
+#pragma unroll
+                            for (int q = 0; q < 16; ++q)
+                                pk[q] = pack_bf16(((bits >> (2 * q)) & 1u) ? __uint_as_float(raw[kb][2 * q]) : 0.f,
+                                                  ((bits >> (2 * q + 1)) & 1u) ? __uint_as_float(raw[kb][2 * q + 1]) : 0.f);
+#pragma unroll
+                            for (int m = 0; m < 4; ++m)
+                                st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
+                                             pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
+                            release_kb(actr, kb);
+                        }
                     }
                     if (s == L - 1 && MODE == 0) {
                         tc_fence_before();
-                        y0 += head_s[2 * W];
-                        y1 += head_s[2 * W + 1];
-                        const bool h = y1 > 0.f;
-                        if (valid) {
-                            a.dist[row] = y0;
-                            if (a.logit) a.logit[row] = y1;
-                            if (a.hit) a.hit[row] = (uint8_t)h;
+                        if (grp == 1) {
+                            part[2 * r] = y0;
+                            part[2 * r + 1] = y1;
                         }
-                        if (a.hit_list) {
-                            const bool take = valid && h;
-                            const unsigned m = __ballot_sync(0xffffffffu, take);
-                            int base = 0;
-                            if (lane == 0 && m) base = atomicAdd(a.hit_count, __popc(m));
-                            base = __shfl_sync(0xffffffffu, base, 0);
-                            if (take) a.hit_list[base + __popc(m & ((1u << lane) - 1u))] = (int)row;
-                        }
-                    }
-                } else {
-                    const int l = 2 * L - 1 - s;
-                    if (l >= 1) {
-                        // delta_{l-1} = (delta_l W_l) * 1[z_{l-1} > 0]
-                        for (int j = 0; j < W / 32; ++j) {
-                            uint32_t raw[32];
-                            TC_LD32(tcol + 32 * j, raw);
-                            tc_wait_ld();
-                            const uint32_t bits = masks[((l - 1) * (W / 32) + j) * 128 + r];
-                            float dl[32];
-#pragma unroll
-                            for (int c = 0; c < 32; ++c) dl[c] = ((bits >> c) & 1u) ? __uint_as_float(raw[c]) : 0.f;
-                            write_act32(act_s, r, 32 * j, dl);
-                            if (j & 1) release_kb(actr, j >> 1);
-                        }
-                    } else {
-                        // d dist / d features (columns 0..E-1), then the encoding chain rule
-                        float gx[3] = {0.f, 0.f, 0.f};
-                        for (int j = 0; j < 4; ++j) {
-                            if (32 * j >= a.E) break;
-                            uint32_t raw[32];
-                            TC_LD32(tcol + 32 * j, raw);
-                            tc_wait_ld();
-#pragma unroll
-                            for (int c = 0; c < 32; ++c) {
-                                const int f = 32 * j + c;
-                                if (f < a.E && (f % 6) < 3)
-                                    gx[f % 6] = fmaf(__uint_as_float(raw[c]), encode_dfeature(f, v), gx[f % 6]);
+                        epi_bar();
+                        if (grp == 0) {
+                            y0 += part[2 * r] + head_s[2 * W];
+                            y1 += part[2 * r + 1] + head_s[2 * W + 1];
+                            const bool hh = y1 > 0.f;
+                            if (valid) {
+                                a.dist[row] = y0;
+                                if (a.logit) a.logit[row] = y1;
+                                if (a.hit) a.hit[row] = (uint8_t)hh;
+                            }
+                            if (a.hit_list) {
+                                const bool take = valid && hh;
+                                const unsigned m = __ballot_sync(0xffffffffu, take);
+                                int base = 0;
+                                if (lane == 0 && m) base = atomicAdd(a.hit_count, __popc(m));
+                                base = __shfl_sync(0xffffffffu, base, 0);
+                                if (take) a.hit_list[base + __popc(m & ((1u << lane) - 1u))] = (int)row;
                             }
                         }
-                        tc_fence_before();
-                        if (valid) {
-                            const float3 nn = normal_from_grad(gx[0], gx[1], gx[2], v[3], v[4], v[5]);
-                            a.normals[row * 3 + 0] = nn.x;
-                            a.normals[row * 3 + 1] = nn.y;
-                            a.normals[row * 3 + 2] = nn.z;
+                    }
+                } else if (grp == 0) {
+                    // d dist / d features (columns 0 .. K0-1), then the encoding chain rule
+                    const uint32_t tc0 = tbase + lane_off + (uint32_t)(b * W);
+                    float gx[3] = {0.f, 0.f, 0.f};
+                    for (int j = 0; j < 4; ++j) {
+                        if (32 * j >= a.K0) break;
+                        uint32_t raw[32];
+                        TC_LD32(tc0 + 32 * j, raw);
+                        tc_wait_ld();
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            const int p = 32 * j + c;
+                            const float gv = __uint_as_float(raw[c]);
+                            if (p < 3) {
+                                gx[p] += gv;
+                            } else if (p >= 8 && p - 2 < a.E) {
+                                const int jj = (p - 8) % 6;
+                                if (jj < 3) gx[jj] = fmaf(gv, encode_dfeature(p - 2, v), gx[jj]);
+                            }
                         }
+                    }
+                    tc_fence_before();
+                    if (valid) {
+                        const float3 nn = normal_from_grad(gx[0], gx[1], gx[2], v[3], v[4], v[5]);
+                        a.normals[row * 3 + 0] = nn.x;
+                        a.normals[row * 3 + 1] = nn.y;
+                        a.normals[row * 3 + 2] = nn.z;
                     }
                 }
             }
@@ -450,6 +524,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ------------------------------------------------------------------ packing
+// Encoding feature behind internal first-layer column p (-1: a zero pad column).
+__device__ __forceinline__ int in_feature(int p) { return p < 6 ? p : (p < 8 ? -1 : p - 2); }
+
 __global__ void pack_kernel(const float* __restrict__ master, NetLayout lay, int kmax,
                             __nv_bfloat16* __restrict__ wf, __nv_bfloat16* __restrict__ wb,
                             float* __restrict__ bias, float* __restrict__ head) {
@@ -460,12 +537,14 @@ __global__ void pack_kernel(const float* __restrict__ master, NetLayout lay, int
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)W * kmax;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int rr = (int)(i / kmax), k = (int)(i % kmax);
-        wf[(int64_t)l * W * kmax + i] = __float2bfloat16_rn(k < in ? Wl[(int64_t)rr * in + k] : 0.f);
+        const int src = l == 0 ? in_feature(k) : k;   // layer 0: internal feature order
+        wf[(int64_t)l * W * kmax + i] = __float2bfloat16_rn(src >= 0 && src < in ? Wl[(int64_t)rr * in + src] : 0.f);
     }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)W * W;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int rr = (int)(i / W), c = (int)(i % W);   // row = input unit, col = output unit
-        wb[(int64_t)l * W * W + i] = __float2bfloat16_rn(rr < in ? Wl[(int64_t)c * in + rr] : 0.f);
+        const int src = l == 0 ? in_feature(rr) : rr;
+        wb[(int64_t)l * W * W + i] = __float2bfloat16_rn(src >= 0 && src < in ? Wl[(int64_t)c * in + src] : 0.f);
     }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < W; i += gridDim.x * blockDim.x)
         bias[l * W + i] = master[lay.b_off[l] + i];
@@ -506,7 +585,7 @@ int make_map(CUtensorMap* m, void* base, int inner, int rows, int L) {
 }
 
 struct Layout {
-    uint32_t off_wst, off_mask, off_bias, off_head, off_bar, total;
+    uint32_t off_wst, off_mask, off_bias, off_head, off_part, off_bar, total;
     int nst;
 };
 
@@ -517,8 +596,9 @@ Layout smem_layout(int W, int L, int K0, int mode) {
     const uint32_t stage = (uint32_t)W * 128u;
     const uint32_t mask = mode == 1 ? (uint32_t)L * 128u * (W / 32) * 4u : 0u;
     const uint32_t bias = (uint32_t)L * W * 4u;
-    const uint32_t head = (uint32_t)(2 * W + 2) * 4u;
-    const uint32_t fixed = act + mask + bias + ((head + 15) & ~15u) + 512u;
+    const uint32_t head = ((uint32_t)(2 * W + 2) * 4u + 15u) & ~15u;
+    const uint32_t partb = 128u * 2u * 4u;
+    const uint32_t fixed = act + mask + bias + head + partb + 512u;
     const uint32_t budget = 227u * 1024u - 1024u;   // minus alignment slack
     int nst = (int)((budget - fixed) / stage);
     s.nst = std::max(0, std::min(8, nst));
@@ -526,7 +606,8 @@ Layout smem_layout(int W, int L, int K0, int mode) {
     s.off_mask = act + (uint32_t)s.nst * stage;
     s.off_bias = s.off_mask + mask;
     s.off_head = s.off_bias + bias;
-    s.off_bar = (s.off_head + head + 15) & ~15u;
+    s.off_part = s.off_head + head;
+    s.off_bar = s.off_part + partb;
     s.total = s.off_bar + 512u + 1024u;
     return s;
 }
@@ -543,6 +624,7 @@ int launch_mode(const ddf_net_s* net, int mode, const TcArgs& base, int64_t n, b
     a.off_mask = s.off_mask;
     a.off_bias = s.off_bias;
     a.off_head = s.off_head;
+    a.off_part = s.off_part;
     a.off_bar = s.off_bar;
     int grid = use_count ? num_sms() : (int)std::min<int64_t>((n + kTileM - 1) / kTileM, num_sms());
     if (grid <= 0) return DDF_OK;
@@ -572,8 +654,8 @@ int launch_mode(const ddf_net_s* net, int mode, const TcArgs& base, int64_t n, b
 bool tc_supported(const NetLayout& lay, int precision) {
     if (precision != DDF_BF16) return false;
     if (lay.width != 128 && lay.width != 256) return false;
-    if (lay.E > 128) return false;
-    return lay.L >= 1 && lay.L <= kMaxLayers && smem_layout(lay.width, lay.L, 64 * ((lay.E + 63) / 64), 1).nst >= 2;
+    if (lay.E + 2 > 128) return false;
+    return lay.L >= 1 && lay.L <= kMaxLayers && smem_layout(lay.width, lay.L, 64 * ((lay.E + 2 + 63) / 64), 1).nst >= 2;
 }
 
 void tc_free(ddf_net_s* net) {
@@ -598,7 +680,7 @@ int tc_pack(ddf_net_s* net, int precision, cudaStream_t stream) {
     if (!P) {
         P = new TcPack();
         net->tc = P;
-        P->K0 = 64 * ((lay.E + 63) / 64);
+        P->K0 = 64 * ((lay.E + 2 + 63) / 64);
         P->kmax = std::max(P->K0, W);
         DDF_CUDA_TRY(cudaMalloc(&P->w_fwd, sizeof(__nv_bfloat16) * (size_t)L * W * P->kmax));
         DDF_CUDA_TRY(cudaMalloc(&P->w_bwd, sizeof(__nv_bfloat16) * (size_t)L * W * W));
