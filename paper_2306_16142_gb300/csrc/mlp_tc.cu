@@ -98,8 +98,8 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t phase) {
     return ok != 0;
 }
 // Bounded wait for the phase with parity `phase` to complete. false: gave up (error raised).
-__device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t phase, int* err) {
-    if (mbar_try(b, phase)) return true;
+// The completed-phase test is inlined; only a wait that actually has to spin takes the call.
+__device__ __noinline__ bool mbar_wait_slow(uint64_t* b, uint32_t phase, int* err) {
     const uint64_t t0 = gtimer();
     for (uint32_t i = 1;; ++i) {
         if (mbar_try(b, phase)) return true;
@@ -111,6 +111,10 @@ __device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t phase, int* err) {
             }
         }
     }
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t phase, int* err) {
+    if (mbar_try(b, phase)) return true;
+    return mbar_wait_slow(b, phase, err);
 }
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
