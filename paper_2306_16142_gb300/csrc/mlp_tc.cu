@@ -52,7 +52,7 @@ constexpr int kThreads = (kEpiWarps + 2) * 32;
 constexpr int kTileM = 128;
 
 struct TcArgs {
-    int L, E, K0, nst;
+    int L, E, K0, F, nst;
     uint32_t off_wst, off_mask, off_bias, off_head, off_part, off_bar;
     const float* bias;
     const float* head;
@@ -191,6 +191,43 @@ __device__ __forceinline__ uint32_t pack_relu(float lo, float hi) {
     return p;
 }
 __device__ __forceinline__ uint32_t pos(float z) { return (int)__float_as_uint(z) > 0 ? 1u : 0u; }
+
+// The 64 internal features [64 kb, 64 kb + 64) of one row, as 32 BF16 pairs. sin / cos of
+// 2^k pi v for k >= 1 come from the double-angle recurrence s' = 2 s c, c' = (c - s)(c + s)
+// seeded by sincospi(v): about 2^k ulp of absolute error (< 1e-5 for k <= 9), far below the
+// BF16 rounding the features get next.
+template <int KB>
+__device__ __forceinline__ void encode_kblock(const float v[6], int F, uint32_t pk[32]) {
+    float fe[64];
+#pragma unroll
+    for (int q = 0; q < 64; ++q) fe[q] = 0.f;
+    if (KB == 0) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) fe[j] = v[j];
+    }
+    float sn[6], cs[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) sincospif(v[j], &sn[j], &cs[j]);
+#pragma unroll
+    for (int k = 0; k < kMaxFreqs / 2; ++k) {
+        if (k < F / 2) {
+#pragma unroll
+            for (int r = 0; r < 12; ++r) {
+                const int p = 8 + 12 * k + r - 64 * KB;
+                if (p >= 0 && p < 64) fe[p] = r < 6 ? sn[r] : cs[r - 6];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            const float s2 = 2.f * sn[j] * cs[j];
+            const float c2 = (cs[j] - sn[j]) * (cs[j] + sn[j]);
+            sn[j] = s2;
+            cs[j] = c2;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) pk[q] = pack_bf16(fe[2 * q], fe[2 * q + 1]);
+}
 
 struct Step {
     int bwd, layer, nk, N;
@@ -344,33 +381,47 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         uint32_t g = 0, accph = 0;
         bool ok = true;
-        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const int64_t i = t * kTileM + r;
-            const bool valid = i < n;
-            int64_t row = -1;
-            if (valid) row = MODE == 0 ? i : (int64_t)a.rows[i];
-            float v[6];
+        // this thread's row of a tile: index, validity and (o, w); the next tile's row is
+        // fetched during the current tile's last step so its latency hides behind the MMAs
+        auto fetch_row = [&](int64_t tt, int64_t& row_out, bool& valid_out, float* vv) {
+            const int64_t ii = tt * kTileM + r;
+            valid_out = tt < ntiles && ii < n;
+            row_out = -1;
+            if (valid_out) row_out = MODE == 0 ? ii : (int64_t)a.rows[ii];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                v[c] = valid ? a.o[row * 3 + c] : 0.f;
-                v[c + 3] = valid ? a.w[row * 3 + c] : 0.f;
+                vv[c] = valid_out ? a.o[row_out * 3 + c] : 0.f;
+                vv[c + 3] = valid_out ? a.w[row_out * 3 + c] : 0.f;
             }
-            // input encoding: each group writes half of every first-layer K-block
-            for (int kb = 0; kb < KB0; ++kb) {
+        };
+        int64_t row_next = -1;
+        bool valid_next = false;
+        float v_next[6];
+        fetch_row(blockIdx.x, row_next, valid_next, v_next);
+        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int64_t row = row_next;
+            const bool valid = valid_next;
+            float v[6];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int qq = grp * 4 + q;
-                    float f8[8];
+            for (int c = 0; c < 6; ++c) v[c] = v_next[c];
+            // input encoding: group g writes first-layer K-block g (K0 <= 128)
+            if (grp < KB0) {
+                uint32_t pk[32];
+                if (grp == 0) encode_kblock<0>(v, a.F, pk);
+                else encode_kblock<1>(v, a.F, pk);
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) f8[e] = enc_internal(kb * 64 + qq * 8 + e, a.E, v);
-                    st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, qq), pack_bf16(f8[0], f8[1]),
-                                 pack_bf16(f8[2], f8[3]), pack_bf16(f8[4], f8[5]), pack_bf16(f8[6], f8[7]));
-                }
-                release_kb(actr, kb);
+                for (int m = 0; m < 8; ++m)
+                    st_shared_v4(act_s + (uint32_t)grp * 16384u + swz(r, m), pk[4 * m], pk[4 * m + 1], pk[4 * m + 2],
+                                 pk[4 * m + 3]);
+                release_kb(actr, grp);
             }
+            // K-blocks are released by 256 arrivals: each group also arrives on the other's block
+            for (int kb = 0; kb < KB0; ++kb)
+                if (kb != grp) mbar_arrive(&actr[kb]);
             float y0 = 0.f, y1 = 0.f;
             for (int s = 0; s < nsteps && ok; ++s, ++g) {
                 const int b = (int)(g & 1u);
+                if (s == nsteps - 1) fetch_row(t + gridDim.x, row_next, valid_next, v_next);
                 ok = mbar_wait(&accf[b], (accph >> b) & 1u, a.err);
                 if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }   // warp-uniform exit
                 accph ^= 1u << b;
@@ -721,6 +772,7 @@ int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n
     a.L = lay.L;
     a.E = lay.E;
     a.K0 = P->K0;
+    a.F = lay.in_freqs;
     a.bias = P->bias;
     a.head = P->head;
     a.o = o;
@@ -832,6 +884,7 @@ extern "C" DDF_API int ddf_query_noalloc(ddf_net net, const float* d_origins, co
     a.L = lay.L;
     a.E = lay.E;
     a.K0 = P->K0;
+    a.F = lay.in_freqs;
     a.bias = P->bias;
     a.head = P->head;
     a.o = d_origins;
