@@ -155,6 +155,47 @@ DDF_API int ddf_query_noalloc(ddf_net net, const float* d_origins, const float* 
                               float* d_dist, uint8_t* d_hit, float* d_logit, float* d_normals,
                               cudaStream_t stream);
 
+/* ---- grouped multi-object query ---------------------------------------------------------- */
+
+typedef struct ddf_group_s* ddf_group;
+
+/* Group several BF16 networks (widths 128 and 256, up to 64 per width) for one grouped query
+ * per width class. The networks must outlive the group. Synchronous. */
+DDF_API int ddf_group_create(int n_obj, const ddf_net* nets, ddf_group* out);
+DDF_API int ddf_group_destroy(ddf_group group);
+
+/* Query object i's field for rows [d_offsets[i], d_offsets[i+1]) of the concatenated device
+ * arrays (d_offsets: DEVICE int64 array of n_obj + 1 non-decreasing entries, d_offsets[0] the
+ * first row). Outputs as in ddf_query (dist, hit, logit nullable; no normals). One persistent
+ * launch per width class walks a device work list of (object, 128-row tile); nothing depends
+ * on host-side counts, so the call can be captured in a CUDA graph. */
+DDF_API int ddf_query_grouped(ddf_group group, const int64_t* d_offsets, const float* d_origins,
+                              const float* d_dirs, float* d_dist, uint8_t* d_hit, float* d_logit,
+                              cudaStream_t stream);
+
+/* Capture one ddf_query_grouped with these pointers into a CUDA graph kept by the group
+ * (replacing an earlier one); ddf_group_replay launches it on a stream (e.g. once per bounce
+ * after the offsets were updated on the device). Capture is synchronous. */
+DDF_API int ddf_group_capture(ddf_group group, const int64_t* d_offsets, const float* d_origins,
+                              const float* d_dirs, float* d_dist, uint8_t* d_hit, float* d_logit,
+                              cudaStream_t stream);
+DDF_API int ddf_group_replay(ddf_group group, cudaStream_t stream);
+
+/* Synchronise and report DDF_ERR_TIMEOUT if a bounded device wait of the group's launches gave
+ * up (flag then cleared), else DDF_OK. */
+DDF_API int ddf_group_status(ddf_group group);
+
+/* Autotune the launch shape (weight-ring depth, persistent grid size) of each width class by
+ * timing every candidate reps times on this workload; cache_path (nullable) is a text cache of
+ * "signature depth grid" lines read first and appended to. Synchronous. Call before capture. */
+DDF_API int ddf_group_autotune(ddf_group group, const int64_t* d_offsets, const float* d_origins,
+                               const float* d_dirs, float* d_dist, uint8_t* d_hit, int reps,
+                               const char* cache_path, cudaStream_t stream);
+
+/* The chosen shapes: host_out6[3c..3c+2] = (width, ring depth, grid) for class c = 0 (width 128)
+ * and c = 1 (width 256); zeros mean absent / default. */
+DDF_API int ddf_group_config(ddf_group group, int* host_out6);
+
 /* ---- renderer --------------------------------------------------------------------------- */
 
 /* The modified uni-directional path tracer (Sec. 1, Fig. 1) as a wavefront loop on the

@@ -59,6 +59,14 @@ _SIG = {
     "ddf_get_weights": (C.c_int, [_P, _P, C.c_size_t, _P]),
     "ddf_query": (C.c_int, [_P, _P, _P, _I64, _P, _P, _P, _P, _P]),
     "ddf_query_noalloc": (C.c_int, [_P, _P, _P, _I64, _P, _P, _P, _P, _P]),
+    "ddf_group_create": (C.c_int, [C.c_int, _P, C.POINTER(_P)]),
+    "ddf_group_destroy": (C.c_int, [_P]),
+    "ddf_query_grouped": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "ddf_group_capture": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "ddf_group_replay": (C.c_int, [_P, _P]),
+    "ddf_group_status": (C.c_int, [_P]),
+    "ddf_group_autotune": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int, C.c_char_p, _P]),
+    "ddf_group_config": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "ddf_render": (C.c_int, [_P, C.POINTER(ddf_camera), C.c_int, C.c_int, _P, _P]),
     "ddf_render_stats": (C.c_int, [_P, C.POINTER(_I64), C.c_int]),
     "ddf_profile_enable": (C.c_int, [_P, C.c_int]),

@@ -25,6 +25,8 @@
 #include <cuda_bf16.h>
 
 #include <mutex>
+#include <string.h>
+#include <vector>
 
 #include "ddf_internal.cuh"
 #include "device_common.cuh"
@@ -45,9 +47,20 @@ struct TcPack {
     int* err = nullptr;
 };
 
+// One object of a grouped launch: its packed network and the rows it owns.
+struct GNet {
+    const CUtensorMap* map;   // forward weight map (device copy)
+    const float* bias;        // [L][W]
+    const float* head;        // W_out [2][W], b_out [2]
+    int L, K0, F, E;
+    int orig;                 // index of the object in the caller's offset array
+    int pad;
+};
+
 namespace {
 
 constexpr int kEpiWarps = 8;
+constexpr int kMaxGroup = 64;
 constexpr int kThreads = (kEpiWarps + 2) * 32;
 constexpr int kTileM = 128;
 
@@ -68,6 +81,14 @@ struct TcArgs {
     int* hit_count;
     float* normals;
     int* err;
+    // grouped launch (MODE 2): objects of one width class, their row ranges and tile prefix
+    const GNet* gnets;
+    const int64_t* grow0;
+    const int64_t* grows;
+    const int64_t* gtile0;   // [gnobj + 1]
+    int gnobj;
+    uint32_t off_grp;
+    int maxL;
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -296,9 +317,57 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int64_t n = a.n;
     if (a.d_count) n = min(n, (int64_t)*a.d_count);
-    const int64_t ntiles = (n + kTileM - 1) / kTileM;
-    const int nsteps = MODE == 0 ? L : 2 * L;
+    int64_t ntiles = (n + kTileM - 1) / kTileM;
     constexpr uint32_t kTmemCols = W <= 128 ? 256 : 512;
+    // grouped mode: the class table in shared memory
+    GNet* gn_s = reinterpret_cast<GNet*>(smem + a.off_grp);
+    int64_t* gt0_s = reinterpret_cast<int64_t*>(gn_s + kMaxGroup);
+    int64_t* gr0_s = gt0_s + kMaxGroup + 1;
+    int64_t* grn_s = gr0_s + kMaxGroup;
+    if (MODE == 2) {
+        for (int i = tid; i < a.gnobj; i += kThreads) {
+            gn_s[i] = a.gnets[i];
+            gr0_s[i] = a.grow0[i];
+            grn_s[i] = a.grows[i];
+        }
+        for (int i = tid; i <= a.gnobj; i += kThreads) gt0_s[i] = a.gtile0[i];
+    }
+    // Per-tile description: rows, network depth, first-layer K-blocks, weight map, object.
+    struct TileInfo {
+        int64_t row0;
+        int rows, L, KB0, F, E, obj;
+        const CUtensorMap* map;
+    };
+    auto tile_info = [&](int64_t t) -> TileInfo {
+        TileInfo ti;
+        if (MODE != 2) {
+            ti.row0 = t * kTileM;
+            ti.rows = (int)min((int64_t)kTileM, n - ti.row0);
+            ti.L = L;
+            ti.KB0 = KB0;
+            ti.F = a.F;
+            ti.E = a.E;
+            ti.obj = 0;
+            ti.map = &mapF;
+        } else {
+            int lo = 0, hi = a.gnobj - 1;   // last object with gt0_s[obj] <= t
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (gt0_s[mid] <= t) lo = mid; else hi = mid - 1;
+            }
+            const GNet& g = gn_s[lo];
+            const int64_t lt = t - gt0_s[lo];
+            ti.row0 = gr0_s[lo] + lt * kTileM;
+            ti.rows = (int)min((int64_t)kTileM, grn_s[lo] - lt * kTileM);
+            ti.L = g.L;
+            ti.KB0 = g.K0 / 64;
+            ti.F = g.F;
+            ti.E = g.E;
+            ti.obj = lo;
+            ti.map = g.map;
+        }
+        return ti;
+    };
 
     if (tid == 0) {
         for (int i = 0; i < NST; ++i) {
@@ -315,9 +384,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    for (int i = tid; i < L * W; i += kThreads) bias_s[i] = a.bias[i];
-    for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
+    if (MODE != 2) {
+        for (int i = tid; i < L * W; i += kThreads) bias_s[i] = a.bias[i];
+        for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
+    }
     __syncthreads();
+    if (MODE == 2) ntiles = gt0_s[a.gnobj];
     tc_fence_after();
     const uint32_t tbase = *tslot;
 
@@ -327,14 +399,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t cnt = 0;
             bool ok = true;
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const TileInfo ti = tile_info(t);
+                const int nsteps = MODE == 1 ? 2 * ti.L : ti.L;
                 for (int s = 0; s < nsteps && ok; ++s) {
-                    const Step st = step_of<W>(s, L, KB0);
+                    const Step st = step_of<W>(s, ti.L, ti.KB0);
                     for (int kb = 0; kb < st.nk; ++kb, ++cnt) {
                         const int stg = (int)(cnt % (uint32_t)NST);
                         const uint32_t ph = (cnt / (uint32_t)NST) & 1u;
                         if (!mbar_wait(&empty[stg], ph ^ 1u, a.err)) { ok = false; break; }
                         mbar_expect_tx(&full[stg], (uint32_t)W * 128u);
-                        tma_load_3d(wst + (size_t)stg * W * 128, st.bwd ? &mapB : &mapF, &full[stg], kb * 64, 0,
+                        tma_load_3d(wst + (size_t)stg * W * 128, st.bwd ? &mapB : ti.map, &full[stg], kb * 64, 0,
                                     st.layer);
                     }
                 }
@@ -347,8 +421,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             const uint32_t act_s = su32(act), wst_s = su32(wst);
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const TileInfo ti = tile_info(t);
+                const int nsteps = MODE == 1 ? 2 * ti.L : ti.L;
                 for (int s = 0; s < nsteps && ok; ++s, ++g) {
-                    const Step st = step_of<W>(s, L, KB0);
+                    const Step st = step_of<W>(s, ti.L, ti.KB0);
                     const uint32_t d = tbase + (g & 1u) * (uint32_t)W;
                     const uint32_t idesc = idesc_bf16(128, st.N);
                     for (int kb = 0; kb < st.nk; ++kb, ++cnt) {
@@ -384,10 +460,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         // this thread's row of a tile: index, validity and (o, w); the next tile's row is
         // fetched during the current tile's last step so its latency hides behind the MMAs
         auto fetch_row = [&](int64_t tt, int64_t& row_out, bool& valid_out, float* vv) {
-            const int64_t ii = tt * kTileM + r;
-            valid_out = tt < ntiles && ii < n;
+            valid_out = false;
             row_out = -1;
-            if (valid_out) row_out = MODE == 0 ? ii : (int64_t)a.rows[ii];
+            if (tt < ntiles) {
+                const TileInfo tn = tile_info(tt);
+                valid_out = r < tn.rows;
+                if (valid_out) row_out = MODE == 1 ? (int64_t)a.rows[tn.row0 + r] : tn.row0 + r;
+            }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 vv[c] = valid_out ? a.o[row_out * 3 + c] : 0.f;
@@ -398,17 +477,30 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool valid_next = false;
         float v_next[6];
         fetch_row(blockIdx.x, row_next, valid_next, v_next);
+        int cur_obj = -1;
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const TileInfo ti = tile_info(t);
+            const int Lt = ti.L, KB0t = ti.KB0;
+            const int nsteps = MODE == 1 ? 2 * Lt : Lt;
+            if (MODE == 2 && ti.obj != cur_obj) {
+                // a new object: its biases and output head replace the previous one's
+                epi_bar();
+                const GNet& gobj = gn_s[ti.obj];
+                for (int i = tid; i < Lt * W; i += 256) bias_s[i] = gobj.bias[i];
+                for (int i = tid; i < 2 * W + 2; i += 256) head_s[i] = gobj.head[i];
+                epi_bar();
+                cur_obj = ti.obj;
+            }
             const int64_t row = row_next;
             const bool valid = valid_next;
             float v[6];
 #pragma unroll
             for (int c = 0; c < 6; ++c) v[c] = v_next[c];
             // input encoding: group g writes first-layer K-block g (K0 <= 128)
-            if (grp < KB0) {
+            if (grp < KB0t) {
                 uint32_t pk[32];
-                if (grp == 0) encode_kblock<0>(v, a.F, pk);
-                else encode_kblock<1>(v, a.F, pk);
+                if (grp == 0) encode_kblock<0>(v, ti.F, pk);
+                else encode_kblock<1>(v, ti.F, pk);
 #pragma unroll
                 for (int m = 0; m < 8; ++m)
                     st_shared_v4(act_s + (uint32_t)grp * 16384u + swz(r, m), pk[4 * m], pk[4 * m + 1], pk[4 * m + 2],
@@ -416,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 release_kb(actr, grp);
             }
             // K-blocks are released by 256 arrivals: each group also arrives on the other's block
-            for (int kb = 0; kb < KB0; ++kb)
+            for (int kb = 0; kb < KB0t; ++kb)
                 if (kb != grp) mbar_arrive(&actr[kb]);
             float y0 = 0.f, y1 = 0.f;
             for (int s = 0; s < nsteps && ok; ++s, ++g) {
@@ -427,20 +519,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                 accph ^= 1u << b;
                 tc_fence_after();
                 const uint32_t tcol = tbase + lane_off + (uint32_t)(b * W) + (uint32_t)(grp * 32);
-                const int l_bwd = 2 * L - 1 - s;
-                if (s < L || l_bwd >= 1) {
+                const int l_bwd = 2 * Lt - 1 - s;
+                if (s < Lt || l_bwd >= 1) {
                     // all of this thread's accumulator columns, one wait
                     uint32_t raw[NKBW][32];
 #pragma unroll
                     for (int kb = 0; kb < NKBW; ++kb) TC_LD32(tcol + kb * 64, raw[kb]);
                     tc_wait_ld();
-                    if (s < L) {
+                    if (s < Lt) {
                         const float* bs = bias_s + s * W;
 #pragma unroll
                         for (int kb = 0; kb < NKBW; ++kb) {
                             const int c0 = kb * 64 + grp * 32;
                             const float4* b4 = reinterpret_cast<const float4*>(bs + c0);
-                            if (s < L - 1) {
+                            if (s < Lt - 1) {
                                 // a = ReLU(acc + b) rounded to BF16 -> next A operand
                                 uint32_t pk[16];
                                 uint32_t bits = 0;
@@ -463,7 +555,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                     st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
                                                  pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
                                 release_kb(actr, kb);
-                            } else if (MODE == 0) {
+                            } else if (MODE != 1) {
                                 // output head on this thread's columns (FP32)
 #pragma unroll
                                 for (int c = 0; c < 32; ++c) {
@@ -506,7 +598,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             release_kb(actr, kb);
                         }
                     }
-                    if (s == L - 1 && MODE == 0) {
+                    if (s == Lt - 1 && MODE != 1) {
                         tc_fence_before();
                         if (grp == 1) {
                             part[2 * r] = y0;
@@ -547,7 +639,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const float gv = __uint_as_float(raw[c]);
                             if (p < 3) {
                                 gx[p] += gv;
-                            } else if (p >= 8 && p - 2 < a.E) {
+                            } else if (p >= 8 && p - 2 < ti.E) {
                                 const int jj = (p - 8) % 6;
                                 if (jj < 3) gx[jj] = fmaf(gv, encode_dfeature(p - 2, v), gx[jj]);
                             }
@@ -640,7 +732,7 @@ int make_map(CUtensorMap* m, void* base, int inner, int rows, int L) {
 }
 
 struct Layout {
-    uint32_t off_wst, off_mask, off_bias, off_head, off_part, off_bar, total;
+    uint32_t off_wst, off_mask, off_bias, off_head, off_part, off_grp, off_bar, total;
     int nst;
 };
 
@@ -653,7 +745,8 @@ Layout smem_layout(int W, int L, int K0, int mode) {
     const uint32_t bias = (uint32_t)L * W * 4u;
     const uint32_t head = ((uint32_t)(2 * W + 2) * 4u + 15u) & ~15u;
     const uint32_t partb = 128u * 2u * 4u;
-    const uint32_t fixed = act + mask + bias + head + partb + 512u;
+    const uint32_t grpb = (uint32_t)(sizeof(GNet) * kMaxGroup + sizeof(int64_t) * (3 * kMaxGroup + 1) + 15) & ~15u;
+    const uint32_t fixed = act + mask + bias + head + partb + grpb + 512u;
     const uint32_t budget = 227u * 1024u - 1024u;   // minus alignment slack
     int nst = (int)((budget - fixed) / stage);
     s.nst = std::max(0, std::min(8, nst));
@@ -662,46 +755,74 @@ Layout smem_layout(int W, int L, int K0, int mode) {
     s.off_bias = s.off_mask + mask;
     s.off_head = s.off_bias + bias;
     s.off_part = s.off_head + head;
-    s.off_bar = s.off_part + partb;
+    s.off_grp = s.off_part + partb;
+    s.off_bar = s.off_grp + grpb;
     s.total = s.off_bar + 512u + 1024u;
     return s;
 }
 
+template <int W, int MODE>
+int ensure_attr() {
+    static bool done = false;
+    if (!done) {
+        DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_tc_kernel<W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          227 * 1024));
+        done = true;
+    }
+    return DDF_OK;
+}
+
 template <int W>
 int launch_mode(const ddf_net_s* net, int mode, const TcArgs& base, int64_t n, bool use_count,
-                cudaStream_t stream) {
-    const TcPack* P = net->tc;
+                cudaStream_t stream, int nst_override = 0, int grid_override = 0,
+                const CUtensorMap* mapF = nullptr, const CUtensorMap* mapB = nullptr) {
+    const TcPack* P = net ? net->tc : nullptr;
     TcArgs a = base;
-    const Layout s = smem_layout(W, a.L, a.K0, mode);
+    const Layout s = smem_layout(W, a.L, a.K0, mode == 1 ? 1 : 0);
     if (s.nst < 2) return fail(DDF_ERR_UNSUPPORTED, "tensor-core MLP: shared memory too small");
-    a.nst = s.nst;
+    a.nst = nst_override > 0 ? std::min(nst_override, s.nst) : s.nst;
     a.off_wst = s.off_wst;
     a.off_mask = s.off_mask;
     a.off_bias = s.off_bias;
     a.off_head = s.off_head;
     a.off_part = s.off_part;
+    a.off_grp = s.off_grp;
     a.off_bar = s.off_bar;
     int grid = use_count ? num_sms() : (int)std::min<int64_t>((n + kTileM - 1) / kTileM, num_sms());
+    if (grid_override > 0) grid = grid_override;
     if (grid <= 0) return DDF_OK;
+    const CUtensorMap& mf = mapF ? *mapF : P->map_fwd;
+    const CUtensorMap& mb = mapB ? *mapB : P->map_bwd;
+    int rc;
     if (mode == 0) {
-        static bool attr = false;
-        if (!attr) {
-            DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_tc_kernel<W, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              227 * 1024));
-            attr = true;
-        }
-        mlp_tc_kernel<W, 0><<<grid, kThreads, s.total, stream>>>(P->map_fwd, P->map_bwd, a);
+        if ((rc = ensure_attr<W, 0>())) return rc;
+        mlp_tc_kernel<W, 0><<<grid, kThreads, s.total, stream>>>(mf, mb, a);
+    } else if (mode == 1) {
+        if ((rc = ensure_attr<W, 1>())) return rc;
+        mlp_tc_kernel<W, 1><<<grid, kThreads, s.total, stream>>>(mf, mb, a);
     } else {
-        static bool attr = false;
-        if (!attr) {
-            DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_tc_kernel<W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              227 * 1024));
-            attr = true;
-        }
-        mlp_tc_kernel<W, 1><<<grid, kThreads, s.total, stream>>>(P->map_fwd, P->map_bwd, a);
+        if ((rc = ensure_attr<W, 2>())) return rc;
+        mlp_tc_kernel<W, 2><<<grid, kThreads, s.total, stream>>>(mf, mb, a);
     }
     DDF_LAUNCH_CHECK();
     return DDF_OK;
+}
+
+// Row ranges and tile prefix of one width class of a group, from the device offsets.
+__global__ void grouped_prep(const int64_t* __restrict__ offsets, const GNet* __restrict__ gn, int nobj,
+                             int64_t* __restrict__ row0, int64_t* __restrict__ rows, int64_t* __restrict__ tile0) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t acc = 0;
+    for (int i = 0; i < nobj; ++i) {
+        const int o = gn[i].orig;
+        const int64_t r0 = offsets[o];
+        const int64_t nr = offsets[o + 1] > r0 ? offsets[o + 1] - r0 : 0;
+        row0[i] = r0;
+        rows[i] = nr;
+        tile0[i] = acc;
+        acc += (nr + kTileM - 1) / kTileM;
+    }
+    tile0[nobj] = acc;
 }
 
 }  // namespace
@@ -910,4 +1031,326 @@ extern "C" DDF_API int ddf_query_noalloc(ddf_net net, const float* d_origins, co
     b.normals = d_normals;
     return lay.width == 128 ? launch_mode<128>(net, 1, b, n, true, stream)
                             : launch_mode<256>(net, 1, b, n, true, stream);
+}
+
+// ------------------------------------------------------------------ grouped multi-object query
+// Many objects, each with its own BF16 network, queried by one persistent launch per width
+// class over a device work list of (object, 128-row tile): rows of object i are
+// [offsets[i], offsets[i+1]) of the concatenated ray arrays, offsets in device memory, so the
+// launch can be captured once in a CUDA graph and replayed every bounce as counts change.
+struct ddf_group_s {
+    struct Class {
+        int W = 0, nobj = 0, maxL = 0, K0 = 0;
+        int nst = 0, grid = 0;            // launch shape (0 = default); set by the autotuner
+        ddf::GNet* d_gnets = nullptr;
+        CUtensorMap* d_maps = nullptr;
+        int64_t* d_tab = nullptr;         // row0[64], rows[64], tile0[65]
+        ddf_net first = nullptr;
+    } cls[2];                             // [0]: width 128, [1]: width 256
+    int n = 0;
+    int* err = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+};
+
+using namespace ddf;
+
+namespace {
+
+int group_class_launch(ddf_group_s* g, int c, const float* o, const float* w, float* dist, uint8_t* hit,
+                       float* logit, cudaStream_t stream) {
+    using namespace ddf;
+    ddf_group_s::Class& C = g->cls[c];
+    if (!C.nobj) return DDF_OK;
+    TcArgs a{};
+    a.L = C.maxL;
+    a.E = 6;
+    a.K0 = C.K0;
+    a.o = o;
+    a.w = w;
+    a.dist = dist;
+    a.logit = logit;
+    a.hit = hit;
+    a.err = g->err;
+    a.gnets = C.d_gnets;
+    a.grow0 = C.d_tab;
+    a.grows = C.d_tab + kMaxGroup;
+    a.gtile0 = C.d_tab + 2 * kMaxGroup;
+    a.gnobj = C.nobj;
+    const int grid = C.grid > 0 ? C.grid : num_sms();
+    if (C.W == 128) return launch_mode<128>(C.first, 2, a, 0, true, stream, C.nst, grid);
+    return launch_mode<256>(C.first, 2, a, 0, true, stream, C.nst, grid);
+}
+
+int group_prep(ddf_group_s* g, const int64_t* d_offsets, cudaStream_t stream) {
+    for (int c = 0; c < 2; ++c) {
+        ddf_group_s::Class& C = g->cls[c];
+        if (!C.nobj) continue;
+        grouped_prep<<<1, 32, 0, stream>>>(d_offsets, C.d_gnets, C.nobj, C.d_tab, C.d_tab + kMaxGroup,
+                                           C.d_tab + 2 * kMaxGroup);
+        DDF_LAUNCH_CHECK();
+    }
+    return DDF_OK;
+}
+
+void group_free(ddf_group_s* g) {
+    if (!g) return;
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    for (auto& C : g->cls) {
+        cudaFree(C.d_gnets);
+        cudaFree(C.d_maps);
+        cudaFree(C.d_tab);
+    }
+    cudaFree(g->err);
+    delete g;
+}
+
+}  // namespace
+
+extern "C" DDF_API int ddf_group_create(int n_obj, const ddf_net* nets, ddf_group* out) {
+    using namespace ddf;
+    if (!out) return fail(DDF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_obj <= 0 || !nets) return fail(DDF_ERR_INVALID_ARG, "need at least one network");
+    ddf_group_s* g = new ddf_group_s();
+    g->n = n_obj;
+    std::vector<GNet> host[2];
+    std::vector<CUtensorMap> maps[2];
+    for (int i = 0; i < n_obj; ++i) {
+        ddf_net_s* nt = nets[i];
+        if (!nt || nt->is_sphere || nt->precision != DDF_BF16 || !nt->tc) {
+            group_free(g);
+            return fail(DDF_ERR_UNSUPPORTED, "object %d: grouped queries need BF16 tensor-core networks", i);
+        }
+        const int c = nt->lay.width == 128 ? 0 : (nt->lay.width == 256 ? 1 : -1);
+        if (c < 0) {
+            group_free(g);
+            return fail(DDF_ERR_UNSUPPORTED, "object %d: width %d not built for grouped queries", i, nt->lay.width);
+        }
+        ddf_group_s::Class& C = g->cls[c];
+        if (C.nobj >= kMaxGroup) {
+            group_free(g);
+            return fail(DDF_ERR_INVALID_ARG, "more than %d objects of one width", kMaxGroup);
+        }
+        GNet gn{};
+        gn.bias = nt->tc->bias;
+        gn.head = nt->tc->head;
+        gn.L = nt->lay.L;
+        gn.K0 = nt->tc->K0;
+        gn.F = nt->lay.in_freqs;
+        gn.E = nt->lay.E;
+        gn.orig = i;
+        host[c].push_back(gn);
+        maps[c].push_back(nt->tc->map_fwd);
+        C.W = nt->lay.width;
+        C.maxL = std::max(C.maxL, nt->lay.L);
+        C.K0 = std::max(C.K0, nt->tc->K0);
+        if (!C.first) C.first = nt;
+        C.nobj++;
+    }
+    cudaError_t e = cudaMalloc(&g->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(int));
+    for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+        ddf_group_s::Class& C = g->cls[c];
+        if (!C.nobj) continue;
+        if (smem_layout(C.W, C.maxL, C.K0, 0).nst < 2) {
+            group_free(g);
+            return fail(DDF_ERR_UNSUPPORTED, "width %d x %d layers does not fit the grouped kernel", C.W, C.maxL);
+        }
+        e = cudaMalloc(&C.d_maps, sizeof(CUtensorMap) * C.nobj);
+        if (e == cudaSuccess) e = cudaMemcpy(C.d_maps, maps[c].data(), sizeof(CUtensorMap) * C.nobj, cudaMemcpyHostToDevice);
+        for (int i = 0; i < C.nobj; ++i) host[c][i].map = C.d_maps + i;
+        if (e == cudaSuccess) e = cudaMalloc(&C.d_gnets, sizeof(GNet) * C.nobj);
+        if (e == cudaSuccess) e = cudaMemcpy(C.d_gnets, host[c].data(), sizeof(GNet) * C.nobj, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&C.d_tab, sizeof(int64_t) * (3 * kMaxGroup + 1));
+    }
+    if (e != cudaSuccess) {
+        group_free(g);
+        return fail(DDF_ERR_CUDA, "group create: %s", cudaGetErrorString(e));
+    }
+    // kernel attributes are set here, outside any stream capture
+    int rc = ensure_attr<128, 2>();
+    if (!rc) rc = ensure_attr<256, 2>();
+    if (rc) {
+        group_free(g);
+        return rc;
+    }
+    *out = g;
+    return DDF_OK;
+}
+
+extern "C" DDF_API int ddf_group_destroy(ddf_group g) {
+    if (!g) return DDF_OK;
+    cudaDeviceSynchronize();
+    group_free(g);
+    return DDF_OK;
+}
+
+extern "C" DDF_API int ddf_query_grouped(ddf_group g, const int64_t* d_offsets, const float* d_origins,
+                                         const float* d_dirs, float* d_dist, uint8_t* d_hit, float* d_logit,
+                                         cudaStream_t stream) {
+    using namespace ddf;
+    if (!g || !d_offsets || !d_origins || !d_dirs || !d_dist || !d_hit)
+        return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    int rc = group_prep(g, d_offsets, stream);
+    if (rc) return rc;
+    for (int c = 0; c < 2; ++c) {
+        rc = group_class_launch(g, c, d_origins, d_dirs, d_dist, d_hit, d_logit, stream);
+        if (rc) return rc;
+    }
+    return DDF_OK;
+}
+
+extern "C" DDF_API int ddf_group_capture(ddf_group g, const int64_t* d_offsets, const float* d_origins,
+                                         const float* d_dirs, float* d_dist, uint8_t* d_hit, float* d_logit,
+                                         cudaStream_t stream) {
+    using namespace ddf;
+    if (!g) return fail(DDF_ERR_INVALID_ARG, "group is NULL");
+    if (g->gexec) {
+        cudaGraphExecDestroy(g->gexec);
+        g->gexec = nullptr;
+    }
+    if (g->graph) {
+        cudaGraphDestroy(g->graph);
+        g->graph = nullptr;
+    }
+    cudaStream_t cs = nullptr;
+    DDF_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    int rc = DDF_OK;
+    if (e == cudaSuccess) rc = ddf_query_grouped(g, d_offsets, d_origins, d_dirs, d_dist, d_hit, d_logit, cs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess || e2 != cudaSuccess || rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc ? rc : fail(DDF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    g->graph = graph;
+    DDF_CUDA_TRY(cudaGraphInstantiate(&g->gexec, graph, 0));
+    (void)stream;
+    return DDF_OK;
+}
+
+extern "C" DDF_API int ddf_group_replay(ddf_group g, cudaStream_t stream) {
+    using namespace ddf;
+    if (!g || !g->gexec) return fail(DDF_ERR_INVALID_ARG, "no captured graph");
+    DDF_CUDA_TRY(cudaGraphLaunch(g->gexec, stream));
+    return DDF_OK;
+}
+
+extern "C" DDF_API int ddf_group_status(ddf_group g) {
+    using namespace ddf;
+    if (!g) return fail(DDF_ERR_INVALID_ARG, "group is NULL");
+    DDF_CUDA_TRY(cudaDeviceSynchronize());
+    int h = 0;
+    DDF_CUDA_TRY(cudaMemcpy(&h, g->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        cudaMemset(g->err, 0, sizeof(int));
+        return fail(DDF_ERR_TIMEOUT, "a grouped-query wait timed out");
+    }
+    return DDF_OK;
+}
+
+// Launch-shape autotuner: per width class, time every (weight-ring depth, persistent grid)
+// candidate on the caller's workload and keep the fastest. With a cache file, a class whose
+// signature (width, depths, encodings, ray-count bucket) is already recorded reuses the stored
+// choice without timing; new choices are appended as "signature nst grid" lines.
+extern "C" DDF_API int ddf_group_autotune(ddf_group g, const int64_t* d_offsets, const float* d_origins,
+                                          const float* d_dirs, float* d_dist, uint8_t* d_hit, int reps,
+                                          const char* cache_path, cudaStream_t stream) {
+    using namespace ddf;
+    if (!g || !d_offsets || !d_origins || !d_dirs || !d_dist || !d_hit || reps <= 0)
+        return fail(DDF_ERR_INVALID_ARG, "bad arguments");
+    int rc = group_prep(g, d_offsets, stream);
+    if (rc) return rc;
+    DDF_CUDA_TRY(cudaStreamSynchronize(stream));
+    int64_t total = 0;
+    {
+        std::vector<int64_t> off(g->n + 1);
+        DDF_CUDA_TRY(cudaMemcpy(off.data(), d_offsets, sizeof(int64_t) * (g->n + 1), cudaMemcpyDeviceToHost));
+        total = off[g->n] - off[0];
+    }
+    int bucket = 0;
+    while ((int64_t(1) << bucket) < total && bucket < 62) ++bucket;
+    cudaEvent_t e0, e1;
+    DDF_CUDA_TRY(cudaEventCreate(&e0));
+    DDF_CUDA_TRY(cudaEventCreate(&e1));
+    for (int c = 0; c < 2; ++c) {
+        ddf_group_s::Class& C = g->cls[c];
+        if (!C.nobj) continue;
+        std::vector<GNet> hn(C.nobj);
+        DDF_CUDA_TRY(cudaMemcpy(hn.data(), C.d_gnets, sizeof(GNet) * C.nobj, cudaMemcpyDeviceToHost));
+        char sig[512];
+        int pos = snprintf(sig, sizeof(sig), "W%d;rows2^%d;", C.W, bucket);
+        for (int i = 0; i < C.nobj && pos < (int)sizeof(sig) - 16; ++i)
+            pos += snprintf(sig + pos, sizeof(sig) - pos, "%d/%d,", hn[i].L, hn[i].F);
+        bool cached = false;
+        if (cache_path) {
+            FILE* f = fopen(cache_path, "r");
+            if (f) {
+                char key[512];
+                int nst = 0, grid = 0;
+                while (fscanf(f, "%511s %d %d", key, &nst, &grid) == 3)
+                    if (!strcmp(key, sig)) {
+                        C.nst = nst;
+                        C.grid = grid;
+                        cached = true;
+                    }
+                fclose(f);
+            }
+        }
+        if (cached) continue;
+        const int nst_max = smem_layout(C.W, C.maxL, C.K0, 0).nst;
+        const int sms = num_sms();
+        const int grids[3] = {sms, (3 * sms) / 4, sms / 2};
+        float best = 1e30f;
+        int best_nst = nst_max, best_grid = sms;
+        for (int nst = 2; nst <= nst_max; ++nst)
+            for (int gi = 0; gi < 3; ++gi) {
+                C.nst = nst;
+                C.grid = grids[gi];
+                rc = group_class_launch(g, c, d_origins, d_dirs, d_dist, d_hit, nullptr, stream);   // warm
+                if (rc) break;
+                DDF_CUDA_TRY(cudaEventRecord(e0, stream));
+                for (int k = 0; k < reps && !rc; ++k)
+                    rc = group_class_launch(g, c, d_origins, d_dirs, d_dist, d_hit, nullptr, stream);
+                DDF_CUDA_TRY(cudaEventRecord(e1, stream));
+                DDF_CUDA_TRY(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                DDF_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                if (!rc && ms < best) {
+                    best = ms;
+                    best_nst = nst;
+                    best_grid = grids[gi];
+                }
+            }
+        if (rc) break;
+        C.nst = best_nst;
+        C.grid = best_grid;
+        if (cache_path) {
+            FILE* f = fopen(cache_path, "a");
+            if (f) {
+                fprintf(f, "%s %d %d\n", sig, C.nst, C.grid);
+                fclose(f);
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+// Chosen launch shape per width class: host_out[3 c .. 3 c + 2] = (width, ring depth, grid)
+// for c = 0 (width 128) and 1 (width 256); zeros for an absent class or a default shape.
+extern "C" DDF_API int ddf_group_config(ddf_group g, int* host_out6) {
+    using namespace ddf;
+    if (!g || !host_out6) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    for (int c = 0; c < 2; ++c) {
+        host_out6[3 * c] = g->cls[c].nobj ? g->cls[c].W : 0;
+        host_out6[3 * c + 1] = g->cls[c].nst;
+        host_out6[3 * c + 2] = g->cls[c].grid;
+    }
+    return DDF_OK;
 }

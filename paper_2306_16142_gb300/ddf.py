@@ -196,3 +196,58 @@ def camera_struct(cam) -> ddf_camera:
     c.albedo = cam.albedo
     c.env = cam.env
     return c
+
+
+class DDFGroup:
+    """Several BF16 networks queried together (ddf_query_grouped): rows of object i are
+    [offsets[i], offsets[i+1]) of the concatenated ray tensors; offsets is a CUDA int64 tensor."""
+
+    def __init__(self, nets):
+        self.nets = list(nets)
+        arr = (C.c_void_p * len(self.nets))(*[n.h.value for n in self.nets])
+        h = C.c_void_p()
+        check("ddf_group_create", _abi.load().ddf_group_create(len(self.nets), arr, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _abi.load().ddf_group_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _out(n, dev):
+        return {"dist": torch.empty(n, device=dev), "hit": torch.empty(n, dtype=torch.uint8, device=dev),
+                "logit": torch.empty(n, device=dev)}
+
+    def query(self, offsets, o, w, out=None):
+        n = _rays(o, w)
+        out = out or self._out(n, o.device)
+        check("ddf_query_grouped", _abi.load().ddf_query_grouped(
+            self.h, _ptr(offsets), _ptr(o), _ptr(w), _ptr(out["dist"]), _ptr(out["hit"]), _ptr(out["logit"]),
+            _stream()))
+        return out
+
+    def capture(self, offsets, o, w, out):
+        check("ddf_group_capture", _abi.load().ddf_group_capture(
+            self.h, _ptr(offsets), _ptr(o), _ptr(w), _ptr(out["dist"]), _ptr(out["hit"]), _ptr(out["logit"]),
+            _stream()))
+
+    def replay(self):
+        check("ddf_group_replay", _abi.load().ddf_group_replay(self.h, _stream()))
+
+    def status(self):
+        check("ddf_group_status", _abi.load().ddf_group_status(self.h))
+
+    def autotune(self, offsets, o, w, out, reps=3, cache_path=None):
+        check("ddf_group_autotune", _abi.load().ddf_group_autotune(
+            self.h, _ptr(offsets), _ptr(o), _ptr(w), _ptr(out["dist"]), _ptr(out["hit"]), reps,
+            cache_path.encode() if cache_path else None, _stream()))
+        cfg = (C.c_int * 6)()
+        check("ddf_group_config", _abi.load().ddf_group_config(self.h, cfg))
+        return [(cfg[0], cfg[1], cfg[2]), (cfg[3], cfg[4], cfg[5])]
