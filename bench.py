@@ -190,6 +190,7 @@ def main():
     ap.add_argument("--ref-paths", type=int, default=2048)
     ap.add_argument("--no-oracle", action="store_true", help="skip the CPU oracle legs")
     ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--no-rows", action="store_true", help="skip the labelling / training / grouped rows")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: 512 x 512 x 8 spp (2^21 paths) for profiler captures")
     args = ap.parse_args()
@@ -333,6 +334,8 @@ def main():
         torch.cuda.synchronize()
         line["fp32_path"] = {"value": paths * args.fp32_steps / (e0.elapsed_time(e1) / 1e3),
                              "unit": "samples/s"}
+    if rank == 0 and not args.no_rows:
+        line["rows"] = other_rows(P, torch, np, peaks)
     if rank == 0 and not args.no_oracle:
         line["query_error"] = query_error(P, net, blob, w)
         dt, nq = oracle_render_sample(w, blob, args.ref_paths)
@@ -345,6 +348,91 @@ def main():
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def _time(torch, fn, reps, stream=None):
+    """Device time per call of fn (CUDA events on the current stream), after 2 warm-up calls."""
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps / 1e3
+
+
+def other_rows(P, torch, np, peaks):
+    """The other hot-path rows on their own workloads: ray labelling (2^20 training rays x 8,192-
+    triangle knot), the training step (batch 65,536, 78 -> 256 x 8 -> 2, FP32 GEMMs) and the grouped
+    16-object BF16 query replayed from a CUDA graph (ray counts log-uniform on [1e3, 1e6])."""
+    from ddf_synth import init_weights, labelled_ray_set, torus_knot
+    rows = {}
+    # ---- a8 labelling
+    V, F = torus_knot(3, 2, 0.08, 256, 16)
+    o, w = labelled_ray_set(V, F, 1 << 20, seed=11)
+    mesh = P.DDFMesh(V, F)
+    to, tw = torch.from_numpy(o).cuda(), torch.from_numpy(w).cuda()
+    out = mesh.label(to, tw)
+    sec = _time(torch, lambda: mesh.label(to, tw, out), 5)
+    st = mesh.stats()
+    tests = o.shape[0] * F.shape[0]
+    alu_peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6      # FP32 lane-instructions / s
+    rows["label"] = {"workload": "2^20 rays (half uniform, half surface-aimed, sigma 0.05 rad) x 8,192-triangle (3,2) knot",
+                     "rays_per_s": o.shape[0] / sec, "tests_per_s": tests / sec, "ms": sec * 1e3,
+                     "fp64_retests_per_ray": st["retests"] / o.shape[0], "fp64_final_evals": st["finals"],
+                     "roofline": {"bound": "alu", "achieved": tests / sec * 34 / 1e12,
+                                  "peak": alu_peak / 1e12, "unit": "T FP32-instr/s",
+                                  "frac": tests / sec * 34 / alu_peak,
+                                  "note": "34 FP32 instructions per filter test (count of the hot loop)"},
+                     "hbm_gbs": (o.shape[0] * 33) / sec / 1e9}
+    # ---- a9 training step
+    Fq, Wd, Ld = 12, 256, 8
+    net = P.DDFNet(Fq, Wd, Ld, init_weights(Fq, Wd, Ld, seed=2), "fp32")
+    n = 65536
+    lab = mesh.label(to[:n].contiguous(), tw[:n].contiguous())
+    dgt, hgt = lab["dist"].clone(), lab["hit"].clone()
+    tsub, wsub = to[:n].contiguous(), tw[:n].contiguous()
+    loss = torch.empty((), device="cuda")
+    sec = _time(torch, lambda: net.train_step(tsub, wsub, dgt, hgt, lr=1e-4, loss=loss), 3)
+    E = 6 + 6 * Fq
+    macs = E * Wd + (Ld - 1) * Wd * Wd + 2 * Wd
+    flop = 2.0 * macs * n * 4     # forward, recomputed forward, dgrad, wgrad
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    rows["train_step"] = {"workload": "batch 65,536 labelled rays, 78 -> 256 x 8 -> 2, L1 + BCE, Adam; FP32 SIMT GEMMs",
+                          "ms": sec * 1e3, "samples_per_s": n / sec,
+                          "roofline": {"bound": "alu", "achieved": flop / sec / 1e12, "peak": fp32_peak / 1e12,
+                                       "unit": "TFLOP/s", "frac": flop / sec / fp32_peak}}
+    # ---- a10 grouped query (16 objects, widths 128 / 256, 4-8 layers)
+    rng = np.random.default_rng(14)
+    specs = [(12, 128 if i % 2 == 0 else 256, 4 + (i % 5), 100 + i) for i in range(16)]
+    nets = [P.DDFNet(Fq2, W2, L2, init_weights(Fq2, W2, L2, seed=s2), "bf16") for Fq2, W2, L2, s2 in specs]
+    counts = np.floor(10 ** (3 + 3 * rng.random(16))).astype(np.int64)
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    tot = int(off[-1])
+    g = torch.Generator(device="cuda").manual_seed(15)
+    go = torch.randn(tot, 3, device="cuda", generator=g)
+    go = go / go.norm(dim=1, keepdim=True) * torch.rand(tot, 1, device="cuda", generator=g)
+    gw = torch.randn(tot, 3, device="cuda", generator=g)
+    gw = gw / gw.norm(dim=1, keepdim=True)
+    toff = torch.from_numpy(off).cuda()
+    grp = P.DDFGroup(nets)
+    gout = grp._out(tot, "cuda")
+    cfg = grp.autotune(toff, go, gw, gout, reps=2)
+    grp.capture(toff, go, gw, gout)
+    sec = _time(torch, grp.replay, 10)
+    grp.status()
+    flop = sum(2.0 * ((6 + 6 * f) * W2 + (L2 - 1) * W2 * W2 + 2 * W2) * c for (f, W2, L2, _), c in zip(specs, counts))
+    peak = peaks["bf16_tflops_sustained"]
+    rows["grouped_query"] = {"workload": "16 BF16 networks (widths 128/256, 4-8 layers, 12-frequency encoding), "
+                                         "ray counts log-uniform on [1e3, 1e6], one CUDA-graph replay per bounce",
+                             "rays": tot, "queries_per_s": tot / sec, "ms": sec * 1e3,
+                             "launch_shapes": cfg,
+                             "roofline": {"bound": "tensor", "achieved": flop / sec / 1e12, "peak": peak,
+                                          "unit": "TFLOP/s", "frac": flop / sec / 1e12 / peak}}
+    return rows
 
 
 def query_error(P, net, blob, w, n=65536):
