@@ -22,25 +22,29 @@ enum { G_STORE = 0, G_BIAS_RELU = 1, G_BIAS = 2, G_MASK = 3, G_ACCUM = 4 };
 __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(
     int M, int N, int K, const float* __restrict__ A, int64_t sai, int64_t sak,
     const float* __restrict__ Bm, int64_t sbk, int64_t sbj, float* __restrict__ C, int64_t ldc,
-    int epi, const float* __restrict__ bias, const float* __restrict__ mask, int64_t ldm) {
+    int epi, const float* __restrict__ bias, const float* __restrict__ mask, int64_t ldm, int kslice,
+    int64_t zstride) {
     __shared__ float As[BK][BM + 4];
     __shared__ float Bs[BK][BN + 4];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+    // split-K: slice z covers k in [z kslice, (z + 1) kslice) and writes its own partial C
+    const int k_lo = blockIdx.z * kslice, k_hi = min(K, k_lo + kslice);
+    C += blockIdx.z * zstride;
     float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int k0 = k_lo; k0 < k_hi; k0 += BK) {
         // A tile: BM x BK
         for (int e = tid; e < BM * BK; e += kGemmThreads) {
             int ii, kk;
             if (sak == 1) { ii = e / BK; kk = e % BK; } else { kk = e / BM; ii = e % BM; }
             const int gi = i0 + ii, gk = k0 + kk;
-            As[kk][ii] = (gi < M && gk < K) ? A[gi * sai + gk * sak] : 0.f;
+            As[kk][ii] = (gi < M && gk < k_hi) ? A[gi * sai + gk * sak] : 0.f;
         }
         for (int e = tid; e < BK * BN; e += kGemmThreads) {
             int kk, jj;
             if (sbj == 1) { kk = e / BN; jj = e % BN; } else { jj = e / BK; kk = e % BK; }
             const int gk = k0 + kk, gj = j0 + jj;
-            Bs[kk][jj] = (gk < K && gj < N) ? Bm[gk * sbk + gj * sbj] : 0.f;
+            Bs[kk][jj] = (gk < k_hi && gj < N) ? Bm[gk * sbk + gj * sbj] : 0.f;
         }
         __syncthreads();
 #pragma unroll
@@ -86,7 +90,41 @@ int gemm(cudaStream_t s, int M, int N, int K, const float* A, int64_t sai, int64
     if (M <= 0 || N <= 0) return DDF_OK;
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
     gemm_kernel<<<grid, kGemmThreads, 0, s>>>(M, N, K, A, sai, sak, Bm, sbk, sbj, C, ldc, epi, bias,
-                                              mask, ldm);
+                                              mask, ldm, K > 0 ? K : 1, 0);
+    DDF_LAUNCH_CHECK();
+    return DDF_OK;
+}
+
+// C[M][N] (ldc) += partials summed in slice order (deterministic).
+__global__ void splitk_reduce(const float* __restrict__ part, int S, int M, int N, float* __restrict__ C,
+                              int64_t ldc) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)M * N;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / N), j = (int)(e % N);
+        float acc = 0.f;
+        for (int z = 0; z < S; ++z) acc += part[(int64_t)z * M * N + e];
+        C[i * ldc + j] += acc;
+    }
+}
+
+// C += A B with the reduction dimension (the batch) split across slices when the output is small,
+// so that the grid covers the GPU; partials are reduced in a fixed order.
+int gemm_accum_splitk(cudaStream_t s, int M, int N, int K, const float* A, int64_t sai, int64_t sak,
+                      const float* Bm, int64_t sbk, int64_t sbj, float* C, int64_t ldc, float* scratch,
+                      size_t scratch_floats) {
+    if (M <= 0 || N <= 0) return DDF_OK;
+    const int tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+    int S = std::max(1, std::min(64, (4 * num_sms() + tiles - 1) / tiles));
+    S = std::min(S, std::max(1, K / 512));
+    while (S > 1 && (size_t)S * M * N > scratch_floats) --S;
+    if (S == 1) return gemm(s, M, N, K, A, sai, sak, Bm, sbk, sbj, C, ldc, G_ACCUM);
+    const int ks = ((K + S - 1) / S + BK - 1) / BK * BK;
+    S = (K + ks - 1) / ks;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, S);
+    gemm_kernel<<<grid, kGemmThreads, 0, s>>>(M, N, K, A, sai, sak, Bm, sbk, sbj, scratch, N, G_STORE, nullptr,
+                                              nullptr, 0, ks, (int64_t)M * N);
+    DDF_LAUNCH_CHECK();
+    splitk_reduce<<<std::min(4096, (M * N + 255) / 256), 256, 0, s>>>(scratch, S, M, N, C, ldc);
     DDF_LAUNCH_CHECK();
     return DDF_OK;
 }
@@ -243,6 +281,8 @@ struct ChunkWs {
     float* D[2];   // [m][W]
     float* GX;     // [m][E]
     float* part;   // colsum partials [(m/256)+1][W]
+    float* splitk; // split-K partials
+    size_t splitk_floats;
     int64_t m;
 };
 
@@ -257,8 +297,9 @@ int ensure_ws(ddf_net_s* net, int64_t n, ChunkWs& ws) {
     int64_t m = (int64_t)(net->ws_limit / per_row);
     m = std::max<int64_t>(256, std::min<int64_t>(m, n));
     m = (m + 255) / 256 * 256;
+    const size_t splitk = (size_t)64 * L.width * std::max(L.width, L.E);
     const size_t need = per_row * (size_t)m + 4096 + sizeof(float) * 2 * (size_t)n +
-                        sizeof(float) * (size_t)L.n_params + 64;
+                        sizeof(float) * (size_t)L.n_params + 64 + sizeof(float) * splitk;
     if (net->train_ws_bytes < need) {
         if (net->train_ws) cudaFree(net->train_ws);
         net->train_ws = nullptr;
@@ -275,6 +316,8 @@ int ensure_ws(ddf_net_s* net, int64_t n, ChunkWs& ws) {
     ws.D[0] = p; p += (size_t)m * L.width;
     ws.D[1] = p; p += (size_t)m * L.width;
     ws.GX = p; p += (size_t)m * L.E;
+    ws.splitk = p; p += (size_t)64 * L.width * std::max(L.width, L.E);
+    ws.splitk_floats = (size_t)64 * L.width * std::max(L.width, L.E);
     ws.part = p;
     return DDF_OK;
 }
@@ -328,7 +371,8 @@ int chunk_backward(ddf_net_s* net, const float* o, const float* w, int64_t m, Ch
     };
     auto act_ld = [&](int l) -> int64_t { return l == 0 ? L.E : W; };
     // output layer: dWo[2][W] += G^T A_L, dbo += colsum(G), D = (G Wo) * mask_L
-    int rc = gemm(s, 2, W, (int)m, ws.G, 1, 2, act(L.L), W, 1, grad + L.w_off[L.L], W, G_ACCUM);
+    int rc = gemm_accum_splitk(s, 2, W, (int)m, ws.G, 1, 2, act(L.L), W, 1, grad + L.w_off[L.L], W, ws.splitk,
+                               ws.splitk_floats);
     if (rc) return rc;
     {
         const int64_t nb = (m + kColRows - 1) / kColRows;
@@ -343,7 +387,8 @@ int chunk_backward(ddf_net_s* net, const float* o, const float* w, int64_t m, Ch
     for (int l = L.L - 1; l >= 0; --l) {
         const int K = l == 0 ? L.E : W;
         // dW_l[W][K] += D^T A_{l}   (A entering layer l)
-        rc = gemm(s, W, K, (int)m, ws.D[cur], 1, W, act(l), act_ld(l), 1, grad + L.w_off[l], K, G_ACCUM);
+        rc = gemm_accum_splitk(s, W, K, (int)m, ws.D[cur], 1, W, act(l), act_ld(l), 1, grad + L.w_off[l], K,
+                               ws.splitk, ws.splitk_floats);
         if (rc) return rc;
         const int64_t nb = (m + kColRows - 1) / kColRows;
         colsum_partial_kernel<<<dim3((W + 127) / 128, (unsigned)nb), 128, 0, s>>>(ws.D[cur], m, W, ws.part);
