@@ -45,6 +45,7 @@ struct TcPack {
     int64_t hit_cap = 0;
     int* hit_count = nullptr;
     int* err = nullptr;
+    uint32_t* gmask = nullptr;        // width 512: per-CTA reverse-pass ReLU masks
 };
 
 // One object of a grouped launch: its packed network and the rows it owns.
@@ -89,6 +90,7 @@ struct TcArgs {
     int gnobj;
     uint32_t off_grp;
     int maxL;
+    uint32_t* gmask;   // width 512: per-CTA ReLU masks of the reverse pass
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -670,6 +672,347 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// Width 512. Shared memory holds the 128 x 512 BF16 activation tile (8 K-blocks, 128 KB) and a
+// ring of three 32 KB weight stages (one N-half of one K-block: 256 rows x 64 K); biases, the
+// output head and the reverse pass's ReLU masks are read from global memory. The 512-column
+// accumulator fills TMEM, so each layer's MMAs run N-half by N-half (N = 256) with a commit per
+// half: the epilogue turns half 0 into BF16 in registers while half 1 is multiplied, writes it as
+// soon as the layer's last MMA has read the previous activations, and the next layer's MMAs
+// start on K-blocks 0-3 while half 1 is being converted.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+    mlp_tc512_kernel(const __grid_constant__ CUtensorMap mapF, const __grid_constant__ CUtensorMap mapB,
+                     const TcArgs a) {
+    constexpr int W = 512;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int L = a.L, KB0 = a.K0 / 64;
+    const int NST = a.nst;
+    uint8_t* act = smem;                                     // 8 x 16 KB
+    uint8_t* wst = smem + 8 * 16384;                         // NST x 32 KB
+    float* part = reinterpret_cast<float*>(act);             // reuses the free activation tile
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wst + (size_t)NST * 32768);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + NST;
+    uint64_t* actr = bars + 2 * NST;     // [8]
+    uint64_t* accf = actr + 8;           // [2] per N-half
+    uint64_t* accfree = accf + 2;        // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(accfree + 2);
+    uint32_t* gmask = a.gmask + (size_t)blockIdx.x * L * 16 * 128;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int64_t n = a.n;
+    if (a.d_count) n = min(n, (int64_t)*a.d_count);
+    const int64_t ntiles = (n + kTileM - 1) / kTileM;
+    const int nsteps = MODE == 0 ? L : 2 * L;
+
+    if (tid == 0) {
+        for (int i = 0; i < NST; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 8; ++i) mbar_init(&actr[i], 256);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accf[i], 1);
+            mbar_init(&accfree[i], 256);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+
+    if (warp == kEpiWarps) {
+        // ---------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            uint32_t cnt = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int s = 0; s < nsteps && ok; ++s) {
+                    const Step st = step_of<W>(s, L, KB0);
+                    const int nh = st.N == W ? 2 : 1;
+                    for (int h = 0; h < nh && ok; ++h)
+                        for (int kb = 0; kb < st.nk; ++kb, ++cnt) {
+                            const int stg = (int)(cnt % (uint32_t)NST);
+                            const uint32_t ph = (cnt / (uint32_t)NST) & 1u;
+                            if (!mbar_wait(&empty[stg], ph ^ 1u, a.err)) { ok = false; break; }
+                            mbar_expect_tx(&full[stg], 32768u);
+                            tma_load_3d(wst + (size_t)stg * 32768, st.bwd ? &mapB : &mapF, &full[stg], kb * 64,
+                                        h * 256, st.layer);
+                        }
+                }
+            }
+        }
+    } else if (warp == kEpiWarps + 1) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t cnt = 0, actph = 0, freeph = 0;
+            uint32_t accph_unused = 0;
+            (void)accph_unused;
+            bool ok = true;
+            const uint32_t act_s = su32(act), wst_s = su32(wst);
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int s = 0; s < nsteps && ok; ++s) {
+                    const Step st = step_of<W>(s, L, KB0);
+                    const int nh = st.N == W ? 2 : 1;
+                    const uint32_t idesc = idesc_bf16(128, st.N == W ? 256 : st.N);
+                    for (int h = 0; h < nh && ok; ++h) {
+                        if (!mbar_wait(&accfree[h], ((freeph >> h) & 1u) ^ 1u, a.err)) { ok = false; break; }
+                        freeph ^= 1u << h;
+                        for (int kb = 0; kb < st.nk; ++kb, ++cnt) {
+                            const int stg = (int)(cnt % (uint32_t)NST);
+                            if (!mbar_wait(&full[stg], (cnt / (uint32_t)NST) & 1u, a.err)) { ok = false; break; }
+                            if (h == 0) {
+                                if (!mbar_wait(&actr[kb], (actph >> kb) & 1u, a.err)) { ok = false; break; }
+                                actph ^= 1u << kb;
+                            }
+                            tc_fence_after();
+                            const uint64_t ad = sdesc(act_s + (uint32_t)kb * 16384u);
+                            const uint64_t bd = sdesc(wst_s + (uint32_t)stg * 32768u);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                mma_bf16(tbase + (uint32_t)h * 256u, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                            mma_commit(&empty[stg]);
+                        }
+                        if (ok) mma_commit(&accf[h]);
+                    }
+                }
+            }
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int grp = warp >> 2;
+        const int r = (warp & 3) * 32 + lane;
+        const uint32_t act_s = su32(act);
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        uint32_t accph = 0;
+        bool ok = true;
+        auto fetch_row = [&](int64_t tt, int64_t& row_out, bool& valid_out, float* vv) {
+            valid_out = false;
+            row_out = -1;
+            if (tt < ntiles) {
+                const int64_t ii = tt * kTileM + r;
+                valid_out = ii < n;
+                if (valid_out) row_out = MODE == 1 ? (int64_t)a.rows[ii] : ii;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                vv[c] = valid_out ? a.o[row_out * 3 + c] : 0.f;
+                vv[c + 3] = valid_out ? a.w[row_out * 3 + c] : 0.f;
+            }
+        };
+        // K-block kb of the next A operand from 32 packed pairs of this thread (columns kb*64+grp*32)
+        auto store_kb = [&](int kb, const uint32_t* pk) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m], pk[4 * m + 1],
+                             pk[4 * m + 2], pk[4 * m + 3]);
+        };
+        int64_t row_next = -1;
+        bool valid_next = false;
+        float v_next[6];
+        fetch_row(blockIdx.x, row_next, valid_next, v_next);
+        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int64_t row = row_next;
+            const bool valid = valid_next;
+            float v[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) v[c] = v_next[c];
+            if (grp < KB0) {
+                uint32_t pk[32];
+                if (grp == 0) encode_kblock<0>(v, a.F, pk);
+                else encode_kblock<1>(v, a.F, pk);
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    st_shared_v4(act_s + (uint32_t)grp * 16384u + swz(r, m), pk[4 * m], pk[4 * m + 1], pk[4 * m + 2],
+                                 pk[4 * m + 3]);
+                release_kb(actr, grp);
+            }
+            for (int kb = 0; kb < KB0; ++kb)
+                if (kb != grp) mbar_arrive(&actr[kb]);
+            float y0 = 0.f, y1 = 0.f;
+            for (int s = 0; s < nsteps && ok; ++s) {
+                if (s == nsteps - 1) fetch_row(t + gridDim.x, row_next, valid_next, v_next);
+                const Step st = step_of<W>(s, L, KB0);
+                const int l_bwd = 2 * L - 1 - s;
+                const bool final_bwd = s >= L && l_bwd == 0;
+                const bool head = MODE == 0 && s == L - 1;
+                // what a K-block's 32 columns of this thread become
+                auto convert = [&](int kb, const uint32_t* raw, uint32_t* pk) {
+                    const int c0 = kb * 64 + grp * 32;
+                    if (s < L) {
+                        const float* bs = a.bias + (size_t)s * W + c0;
+                        uint32_t bits = 0;
+                        if (s < L - 1) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                const float4 bb = __ldg(reinterpret_cast<const float4*>(bs) + q);
+                                float z0, z1, z2, z3;
+                                add2(__uint_as_float(raw[4 * q]), __uint_as_float(raw[4 * q + 1]), bb.x, bb.y, z0, z1);
+                                add2(__uint_as_float(raw[4 * q + 2]), __uint_as_float(raw[4 * q + 3]), bb.z, bb.w, z2, z3);
+                                pk[2 * q] = pack_relu(z0, z1);
+                                pk[2 * q + 1] = pack_relu(z2, z3);
+                                if (MODE == 1) bits |= (pos(z0) | pos(z1) << 1 | pos(z2) << 2 | pos(z3) << 3) << (4 * q);
+                            }
+                            if (MODE == 1) gmask[(s * 16 + (c0 >> 5)) * 128 + r] = bits;
+                        } else if (MODE == 0) {
+#pragma unroll
+                            for (int q = 0; q < 32; ++q) {
+                                const float z = fmaxf(__uint_as_float(raw[q]) + __ldg(bs + q), 0.f);
+                                y0 = fmaf(z, __ldg(a.head + c0 + q), y0);
+                                y1 = fmaf(z, __ldg(a.head + W + c0 + q), y1);
+                            }
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) {
+                                const float z0 = __uint_as_float(raw[2 * q]) + __ldg(bs + 2 * q);
+                                const float z1 = __uint_as_float(raw[2 * q + 1]) + __ldg(bs + 2 * q + 1);
+                                pk[q] = pack_bf16(z0 > 0.f ? __ldg(a.head + c0 + 2 * q) : 0.f,
+                                                  z1 > 0.f ? __ldg(a.head + c0 + 2 * q + 1) : 0.f);
+                            }
+                        }
+                    } else {
+                        const uint32_t bits = gmask[((l_bwd - 1) * 16 + (c0 >> 5)) * 128 + r];
+#pragma unroll
+                        for (int q = 0; q < 16; ++q)
+                            pk[q] = pack_bf16(((bits >> (2 * q)) & 1u) ? __uint_as_float(raw[2 * q]) : 0.f,
+                                              ((bits >> (2 * q + 1)) & 1u) ? __uint_as_float(raw[2 * q + 1]) : 0.f);
+                    }
+                };
+                if (final_bwd) {
+                    ok = mbar_wait(&accf[0], accph & 1u, a.err);
+                    if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                    accph ^= 1u;
+                    tc_fence_after();
+                    if (grp == 0) {
+                        float gx[3] = {0.f, 0.f, 0.f};
+                        for (int j = 0; j < 4; ++j) {
+                            if (32 * j >= a.K0) break;
+                            uint32_t raw[32];
+                            TC_LD32(tbase + lane_off + 32 * j, raw);
+                            tc_wait_ld();
+                            float gv[32];
+#pragma unroll
+                            for (int q = 0; q < 32; ++q) gv[q] = __uint_as_float(raw[q]);
+#pragma unroll 1
+                            for (int q = 0; q < 32; ++q) {
+                                const int p = 32 * j + q;
+                                if (p < 3) {
+                                    gx[p] += gv[q];
+                                } else if (p >= 8 && p - 2 < a.E) {
+                                    const int jj = (p - 8) % 6;
+                                    if (jj < 3) gx[jj] = fmaf(gv[q], encode_dfeature(p - 2, v), gx[jj]);
+                                }
+                            }
+                        }
+                        if (valid) {
+                            const float3 nn = normal_from_grad(gx[0], gx[1], gx[2], v[3], v[4], v[5]);
+                            a.normals[row * 3 + 0] = nn.x;
+                            a.normals[row * 3 + 1] = nn.y;
+                            a.normals[row * 3 + 2] = nn.z;
+                        }
+                    }
+                    tc_fence_before();
+                    mbar_arrive(&accfree[0]);
+                    continue;
+                }
+                // ---- half 0: read and convert into registers
+                ok = mbar_wait(&accf[0], accph & 1u, a.err);
+                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                tc_fence_after();
+                uint32_t stash[4][16];
+#pragma unroll
+                for (int pass = 0; pass < 2; ++pass) {
+                    uint32_t raw[2][32];
+#pragma unroll
+                    for (int i = 0; i < 2; ++i)
+                        TC_LD32(tbase + lane_off + (uint32_t)((2 * pass + i) * 64 + grp * 32), raw[i]);
+                    tc_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) convert(2 * pass + i, raw[i], stash[2 * pass + i]);
+                }
+                tc_fence_before();
+                mbar_arrive(&accfree[0]);
+                // ---- the layer's last MMA is done: the previous activations are free
+                ok = mbar_wait(&accf[1], (accph >> 1) & 1u, a.err);
+                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                accph ^= 3u;
+                tc_fence_after();
+                if (!head) {
+#pragma unroll
+                    for (int kb = 0; kb < 4; ++kb) {
+                        store_kb(kb, stash[kb]);
+                        release_kb(actr, kb);
+                    }
+                }
+                // ---- half 1
+#pragma unroll
+                for (int pass = 0; pass < 2; ++pass) {
+                    uint32_t raw[2][32];
+#pragma unroll
+                    for (int i = 0; i < 2; ++i)
+                        TC_LD32(tbase + lane_off + (uint32_t)(256 + (2 * pass + i) * 64 + grp * 32), raw[i]);
+                    tc_wait_ld();
+                    if (pass == 1) {
+                        tc_fence_before();
+                        mbar_arrive(&accfree[1]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        uint32_t pk[16];
+                        convert(4 + 2 * pass + i, raw[i], pk);
+                        if (!head) {
+                            store_kb(4 + 2 * pass + i, pk);
+                            release_kb(actr, 4 + 2 * pass + i);
+                        }
+                    }
+                }
+                if (head) {
+                    if (grp == 1) {
+                        part[4 * r] = y0;
+                        part[4 * r + 1] = y1;
+                    }
+                    epi_bar();
+                    if (grp == 0) {
+                        y0 += part[4 * r] + __ldg(a.head + 2 * W);
+                        y1 += part[4 * r + 1] + __ldg(a.head + 2 * W + 1);
+                        const bool hh = y1 > 0.f;
+                        if (valid) {
+                            a.dist[row] = y0;
+                            if (a.logit) a.logit[row] = y1;
+                            if (a.hit) a.hit[row] = (uint8_t)hh;
+                        }
+                        if (a.hit_list) {
+                            const bool take = valid && hh;
+                            const unsigned m = __ballot_sync(0xffffffffu, take);
+                            int base = 0;
+                            if (lane == 0 && m) base = atomicAdd(a.hit_count, __popc(m));
+                            base = __shfl_sync(0xffffffffu, base, 0);
+                            if (take) a.hit_list[base + __popc(m & ((1u << lane) - 1u))] = (int)row;
+                        }
+                    }
+                    epi_bar();
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (*(volatile int*)a.err) {
+        const uint64_t t0 = gtimer();
+        while (gtimer() - t0 < 200000ull) {
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));
+    }
+}
+
 // ------------------------------------------------------------------ packing
 // Encoding feature behind internal first-layer column p (-1: a zero pad column).
 __device__ __forceinline__ int in_feature(int p) { return p < 6 ? p : (p < 8 ? -1 : p - 2); }
@@ -722,7 +1065,7 @@ int make_map(CUtensorMap* m, void* base, int inner, int rows, int L) {
     if (!enc) return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
     cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)L};
     cuuint64_t strides[2] = {(cuuint64_t)inner * 2, (cuuint64_t)inner * rows * 2};
-    cuuint32_t box[3] = {64, (cuuint32_t)rows, 1};
+    cuuint32_t box[3] = {64, (cuuint32_t)(rows < 256 ? rows : 256), 1};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -808,6 +1151,34 @@ int launch_mode(const ddf_net_s* net, int mode, const TcArgs& base, int64_t n, b
     return DDF_OK;
 }
 
+uint32_t smem512(int nst) { return 8u * 16384u + (uint32_t)nst * 32768u + 512u + 1024u; }
+
+int launch512(const ddf_net_s* net, int mode, const TcArgs& base, int64_t n, bool use_count, cudaStream_t stream) {
+    const TcPack* P = net->tc;
+    TcArgs a = base;
+    a.nst = 3;
+    a.gmask = P->gmask;
+    const uint32_t sm = smem512(a.nst);
+    int grid = use_count ? num_sms() : (int)std::min<int64_t>((n + kTileM - 1) / kTileM, num_sms());
+    if (grid <= 0) return DDF_OK;
+    static bool attr0 = false, attr1 = false;
+    if (mode == 0) {
+        if (!attr0) {
+            DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_tc512_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+            attr0 = true;
+        }
+        mlp_tc512_kernel<0><<<grid, kThreads, sm, stream>>>(P->map_fwd, P->map_bwd, a);
+    } else {
+        if (!attr1) {
+            DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_tc512_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+            attr1 = true;
+        }
+        mlp_tc512_kernel<1><<<grid, kThreads, sm, stream>>>(P->map_fwd, P->map_bwd, a);
+    }
+    DDF_LAUNCH_CHECK();
+    return DDF_OK;
+}
+
 // Row ranges and tile prefix of one width class of a group, from the device offsets.
 __global__ void grouped_prep(const int64_t* __restrict__ offsets, const GNet* __restrict__ gn, int nobj,
                              int64_t* __restrict__ row0, int64_t* __restrict__ rows, int64_t* __restrict__ tile0) {
@@ -829,8 +1200,9 @@ __global__ void grouped_prep(const int64_t* __restrict__ offsets, const GNet* __
 
 bool tc_supported(const NetLayout& lay, int precision) {
     if (precision != DDF_BF16) return false;
-    if (lay.width != 128 && lay.width != 256) return false;
+    if (lay.width != 128 && lay.width != 256 && lay.width != 512) return false;
     if (lay.E + 2 > 128) return false;
+    if (lay.width == 512) return lay.L >= 1 && lay.L <= kMaxLayers && smem512(3) <= 227u * 1024u;
     return lay.L >= 1 && lay.L <= kMaxLayers && smem_layout(lay.width, lay.L, 64 * ((lay.E + 2 + 63) / 64), 1).nst >= 2;
 }
 
@@ -844,6 +1216,7 @@ void tc_free(ddf_net_s* net) {
     cudaFree(P->hit_list);
     cudaFree(P->hit_count);
     cudaFree(P->err);
+    cudaFree(P->gmask);
     delete P;
     net->tc = nullptr;
 }
@@ -865,6 +1238,8 @@ int tc_pack(ddf_net_s* net, int precision, cudaStream_t stream) {
         DDF_CUDA_TRY(cudaMalloc(&P->hit_count, sizeof(int)));
         DDF_CUDA_TRY(cudaMalloc(&P->err, sizeof(int)));
         DDF_CUDA_TRY(cudaMemset(P->err, 0, sizeof(int)));
+        if (W == 512)
+            DDF_CUDA_TRY(cudaMalloc(&P->gmask, sizeof(uint32_t) * (size_t)num_sms() * L * 16 * 128));
         int rc = make_map(&P->map_fwd, P->w_fwd, P->kmax, W, L);
         if (rc) return rc;
         rc = make_map(&P->map_bwd, P->w_bwd, W, W, L);
@@ -909,8 +1284,9 @@ int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n
         a.hit_list = P->hit_list;
         a.hit_count = P->hit_count;
     }
-    int rc = lay.width == 128 ? launch_mode<128>(net, 0, a, n, d_count != nullptr, stream)
-                              : launch_mode<256>(net, 0, a, n, d_count != nullptr, stream);
+    int rc = lay.width == 128   ? launch_mode<128>(net, 0, a, n, d_count != nullptr, stream)
+             : lay.width == 256 ? launch_mode<256>(net, 0, a, n, d_count != nullptr, stream)
+                                : launch512(net, 0, a, n, d_count != nullptr, stream);
     if (rc || !normals) return rc;
     TcArgs b = a;
     b.rows = P->hit_list;
@@ -921,8 +1297,9 @@ int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n
     b.logit = nullptr;
     b.hit = nullptr;
     b.normals = normals;
-    return lay.width == 128 ? launch_mode<128>(net, 1, b, n, true, stream)
-                            : launch_mode<256>(net, 1, b, n, true, stream);
+    return lay.width == 128   ? launch_mode<128>(net, 1, b, n, true, stream)
+           : lay.width == 256 ? launch_mode<256>(net, 1, b, n, true, stream)
+                              : launch512(net, 1, b, n, true, stream);
 }
 
 int tc_device_status(ddf_net_s* net) {
@@ -993,6 +1370,8 @@ extern "C" DDF_API int ddf_query_noalloc(ddf_net net, const float* d_origins, co
         return field_query(net, d_origins, d_dirs, n, nullptr, d_dist, d_logit, d_hit, d_normals, stream);
     TcPack* P = net->tc;
     if (!P) return fail(DDF_ERR_UNSUPPORTED, "tensor-core weights not packed");
+    if (net->lay.width == 512)
+        return fail(DDF_ERR_UNSUPPORTED, "ddf_query_noalloc: width-512 normals need the handle's mask scratch");
     int* scratch = nullptr;
     int rc = noalloc_scratch(&scratch);
     if (rc) return rc;

@@ -14,7 +14,7 @@ from tests._helpers import BF16_ABS, ensure_built, rays_in_ball
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(12, 256, 8, 2), (12, 128, 4, 7), (0, 128, 6, 9), (16, 256, 5, 4)]
+SHAPES = [(12, 256, 8, 2), (12, 128, 4, 7), (0, 128, 6, 9), (16, 256, 5, 4), (16, 512, 8, 5), (12, 512, 3, 11)]
 
 
 @pytest.fixture(scope="module")
