@@ -46,6 +46,10 @@ struct TcPack {
     int* hit_count = nullptr;
     int* err = nullptr;
     uint32_t* gmask = nullptr;        // width 512: per-CTA reverse-pass ReLU masks
+    uint8_t* w8 = nullptr;            // FP8: [L][W][kmax8] E4M3, per-output-channel scaled
+    float* sw8 = nullptr;             // FP8: [L][W] scales
+    int kmax8 = 0;
+    CUtensorMap map_f8;
 };
 
 // One object of a grouped launch: its packed network and the rows it owns.
@@ -91,6 +95,7 @@ struct TcArgs {
     uint32_t off_grp;
     int maxL;
     uint32_t* gmask;   // width 512: per-CTA ReLU masks of the reverse pass
+    const float* wscale;   // FP8: per-output-channel weight scales [L][W]
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -1013,6 +1018,292 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// ------------------------------------------------------------------ FP8 E4M3 forward
+// kind::f8f6f4 MMAs (E4M3 x E4M3 -> FP32, K = 32 per instruction) on 128-feature K-blocks
+// (128-byte swizzled rows, the same byte layout as the BF16 path). Weights carry one scale per
+// output channel (max |W[n][:]| / 448); every activation row carries one scale (max |a[r][:]| /
+// 448), so z[r][n] = acc[r][n] * s_a[r] * s_w[n] + b[n]. The two epilogue warp groups hold halves
+// of each row: they exchange their partial maxima through shared memory before quantising the
+// next layer's input.
+__device__ __forceinline__ uint32_t idesc_f8(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);   // E4M3 x E4M3 -> F32
+}
+__device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+// Four floats -> four E4M3 bytes (first value in the lowest byte), saturating to +-448.
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+    unsigned short lo, hi;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(b), "f"(a));
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(d), "f"(c));
+    return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
+// The 64 internal input features [64 half, 64 half + 64) of one row (see encode_kblock).
+template <int HALF>
+__device__ __forceinline__ void encode_feats64(const float v[6], int F, float fe[64]) {
+#pragma unroll
+    for (int q = 0; q < 64; ++q) fe[q] = 0.f;
+    if (HALF == 0) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) fe[j] = v[j];
+    }
+    float sn[6], cs[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) sincospif(v[j], &sn[j], &cs[j]);
+#pragma unroll
+    for (int k = 0; k < kMaxFreqs / 2; ++k) {
+        if (k < F / 2) {
+#pragma unroll
+            for (int r = 0; r < 12; ++r) {
+                const int p = 8 + 12 * k + r - 64 * HALF;
+                if (p >= 0 && p < 64) fe[p] = r < 6 ? sn[r] : cs[r - 6];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            const float s2 = 2.f * sn[j] * cs[j];
+            const float c2 = (cs[j] - sn[j]) * (cs[j] + sn[j]);
+            sn[j] = s2;
+            cs[j] = c2;
+        }
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads, 1)
+    mlp_f8_kernel(const __grid_constant__ CUtensorMap map8, const TcArgs a) {
+    constexpr int NKB = W / 128;                     // hidden-layer K-blocks of 128 features
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int L = a.L;
+    const int NST = a.nst;
+    uint8_t* act = smem;                             // max(1, NKB) x 16 KB
+    uint8_t* wst = smem + a.off_wst;
+    float* bias_s = reinterpret_cast<float*>(smem + a.off_bias);
+    float* sw_s = reinterpret_cast<float*>(smem + a.off_mask);   // per-channel weight scales [L][W]
+    float* head_s = reinterpret_cast<float*>(smem + a.off_head);
+    float* part = reinterpret_cast<float*>(smem + a.off_part);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + NST;
+    uint64_t* actr = bars + 2 * NST;   // [2]
+    uint64_t* accf = actr + 2;         // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int64_t n = a.n;
+    if (a.d_count) n = min(n, (int64_t)*a.d_count);
+    const int64_t ntiles = (n + kTileM - 1) / kTileM;
+    constexpr uint32_t kTmemCols = W <= 128 ? 256 : 512;
+
+    if (tid == 0) {
+        for (int i = 0; i < NST; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(&actr[0], 256);
+        mbar_init(&actr[1], 256);
+        mbar_init(&accf[0], 1);
+        mbar_init(&accf[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    for (int i = tid; i < L * W; i += kThreads) {
+        bias_s[i] = a.bias[i];
+        sw_s[i] = a.wscale[i];
+    }
+    for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+
+    if (warp == kEpiWarps) {
+        if (lane == 0) {
+            uint32_t cnt = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
+                for (int s = 0; s < L && ok; ++s) {
+                    const int nk = s == 0 ? 1 : NKB;
+                    for (int kb = 0; kb < nk; ++kb, ++cnt) {
+                        const int stg = (int)(cnt % (uint32_t)NST);
+                        if (!mbar_wait(&empty[stg], ((cnt / (uint32_t)NST) & 1u) ^ 1u, a.err)) { ok = false; break; }
+                        mbar_expect_tx(&full[stg], (uint32_t)W * 128u);
+                        tma_load_3d(wst + (size_t)stg * W * 128, &map8, &full[stg], kb * 128, 0, s);
+                    }
+                }
+        }
+    } else if (warp == kEpiWarps + 1) {
+        if (lane == 0) {
+            uint32_t cnt = 0, g = 0, actph = 0;
+            bool ok = true;
+            const uint32_t act_s = su32(act), wst_s = su32(wst);
+            const uint32_t idesc = idesc_f8(128, W);
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
+                for (int s = 0; s < L && ok; ++s, ++g) {
+                    const int nk = s == 0 ? 1 : NKB;
+                    const uint32_t d = tbase + (g & 1u) * (uint32_t)W;
+                    for (int kb = 0; kb < nk; ++kb, ++cnt) {
+                        const int stg = (int)(cnt % (uint32_t)NST);
+                        if (!mbar_wait(&full[stg], (cnt / (uint32_t)NST) & 1u, a.err)) { ok = false; break; }
+                        if (!mbar_wait(&actr[kb], (actph >> kb) & 1u, a.err)) { ok = false; break; }
+                        actph ^= 1u << kb;
+                        tc_fence_after();
+                        const uint64_t ad = sdesc(act_s + (uint32_t)kb * 16384u);
+                        const uint64_t bd = sdesc(wst_s + (uint32_t)stg * (uint32_t)W * 128u);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) mma_f8(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                        mma_commit(&empty[stg]);
+                    }
+                    if (ok) mma_commit(&accf[g & 1u]);
+                }
+        }
+    } else {
+        // epilogue: warp w serves rows 32 (w % 4) .. +31; group w / 4 owns the 64 columns
+        // [128 kb + 64 group, +64) of every 128-column K-block
+        const int grp = warp >> 2;
+        const int r = (warp & 3) * 32 + lane;
+        const uint32_t act_s = su32(act);
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        uint32_t g = 0, accph = 0;
+        bool ok = true;
+        auto write64 = [&](int kb, const float* z, float inv) {
+            uint32_t q[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) q[i] = pack_e4m3x4(z[4 * i] * inv, z[4 * i + 1] * inv, z[4 * i + 2] * inv, z[4 * i + 3] * inv);
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), q[4 * m], q[4 * m + 1], q[4 * m + 2],
+                             q[4 * m + 3]);
+        };
+        // the row's maximum over both groups (both threads of the row get it)
+        auto row_max = [&](float mx) {
+            part[2 * r + grp] = mx;
+            epi_bar();
+            const float m2 = fmaxf(part[2 * r], part[2 * r + 1]);
+            epi_bar();
+            return m2;
+        };
+        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int64_t i = t * kTileM + r;
+            const bool valid = i < n;
+            const int64_t row = valid ? i : -1;
+            float v[6];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[c] = valid ? a.o[row * 3 + c] : 0.f;
+                v[c + 3] = valid ? a.w[row * 3 + c] : 0.f;
+            }
+            float sa;
+            {
+                float fe[64];
+                if (grp == 0) encode_feats64<0>(v, a.F, fe);
+                else encode_feats64<1>(v, a.F, fe);
+                float mx = 0.f;
+#pragma unroll
+                for (int q = 0; q < 64; ++q) mx = fmaxf(mx, fabsf(fe[q]));
+                mx = row_max(mx);
+                sa = mx > 0.f ? mx * (1.f / 448.f) : 1.f;
+                write64(0, fe, 1.f / sa);
+                release_kb(actr, 0);
+            }
+            float y0 = 0.f, y1 = 0.f;
+            for (int s = 0; s < L && ok; ++s, ++g) {
+                const int b = (int)(g & 1u);
+                ok = mbar_wait(&accf[b], (accph >> b) & 1u, a.err);
+                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                accph ^= 1u << b;
+                tc_fence_after();
+                const uint32_t tcol = tbase + lane_off + (uint32_t)(b * W);
+                float z[NKB][64];
+                {
+                    uint32_t raw[NKB][2][32];
+#pragma unroll
+                    for (int kb = 0; kb < NKB; ++kb)
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) TC_LD32(tcol + kb * 128 + grp * 64 + h * 32, raw[kb][h]);
+                    tc_wait_ld();
+                    const float* bs = bias_s + s * W;
+                    const float* ws = sw_s + s * W;
+#pragma unroll
+                    for (int kb = 0; kb < NKB; ++kb)
+#pragma unroll
+                        for (int c = 0; c < 64; ++c) {
+                            const int col = kb * 128 + grp * 64 + c;
+                            z[kb][c] = fmaxf(fmaf(__uint_as_float(raw[kb][c >> 5][c & 31]) * ws[col], sa, bs[col]), 0.f);
+                        }
+                }
+                if (s < L - 1) {
+                    float mx = 0.f;
+#pragma unroll
+                    for (int kb = 0; kb < NKB; ++kb)
+#pragma unroll
+                        for (int c = 0; c < 64; ++c) mx = fmaxf(mx, z[kb][c]);
+                    mx = row_max(mx);
+                    sa = mx > 0.f ? mx * (1.f / 448.f) : 1.f;
+                    const float inv = 1.f / sa;
+#pragma unroll
+                    for (int kb = 0; kb < NKB; ++kb) {
+                        write64(kb, z[kb], inv);
+                        release_kb(actr, kb);
+                    }
+                } else {
+#pragma unroll
+                    for (int kb = 0; kb < NKB; ++kb)
+#pragma unroll
+                        for (int c = 0; c < 64; ++c) {
+                            const int col = kb * 128 + grp * 64 + c;
+                            y0 = fmaf(z[kb][c], head_s[col], y0);
+                            y1 = fmaf(z[kb][c], head_s[W + col], y1);
+                        }
+                    tc_fence_before();
+                    if (grp == 1) {
+                        part[2 * r] = y0;
+                        part[2 * r + 1] = y1;
+                    }
+                    epi_bar();
+                    if (grp == 0) {
+                        y0 += part[2 * r] + head_s[2 * W];
+                        y1 += part[2 * r + 1] + head_s[2 * W + 1];
+                        const bool hh = y1 > 0.f;
+                        if (valid) {
+                            a.dist[row] = y0;
+                            if (a.logit) a.logit[row] = y1;
+                            if (a.hit) a.hit[row] = (uint8_t)hh;
+                        }
+                        if (a.hit_list) {
+                            const bool take = valid && hh;
+                            const unsigned m = __ballot_sync(0xffffffffu, take);
+                            int base = 0;
+                            if (lane == 0 && m) base = atomicAdd(a.hit_count, __popc(m));
+                            base = __shfl_sync(0xffffffffu, base, 0);
+                            if (take) a.hit_list[base + __popc(m & ((1u << lane) - 1u))] = (int)row;
+                        }
+                    }
+                    epi_bar();
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (*(volatile int*)a.err) {
+        const uint64_t t0 = gtimer();
+        while (gtimer() - t0 < 200000ull) {
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols));
+    }
+}
+
 // ------------------------------------------------------------------ packing
 // Encoding feature behind internal first-layer column p (-1: a zero pad column).
 __device__ __forceinline__ int in_feature(int p) { return p < 6 ? p : (p < 8 ? -1 : p - 2); }
@@ -1043,6 +1334,41 @@ __global__ void pack_kernel(const float* __restrict__ master, NetLayout lay, int
             head[i] = i < 2 * W ? master[lay.w_off[lay.L] + i] : master[lay.b_off[lay.L] + i - 2 * W];
 }
 
+// FP8 E4M3 copy of the hidden layers: one block per output channel n of layer l; scale
+// s = max_k |W[n][k]| / 448 (1 for an all-zero row), byte = E4M3(W[n][k] / s), layer 0 in the
+// internal feature order.
+__global__ void pack_f8_kernel(const float* __restrict__ master, NetLayout lay, int kmax8, uint8_t* __restrict__ w8,
+                               float* __restrict__ sw8) {
+    const int l = blockIdx.y, nrow = blockIdx.x, W = lay.width;
+    const int in = l == 0 ? lay.E : W;
+    const float* Wrow = master + lay.w_off[l] + (int64_t)nrow * in;
+    __shared__ float red[32];
+    float mx = 0.f;
+    for (int k = threadIdx.x; k < in; k += blockDim.x) mx = fmaxf(mx, fabsf(Wrow[k]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        mx = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        if (threadIdx.x == 0) red[0] = mx;
+    }
+    __syncthreads();
+    const float sc = red[0] > 0.f ? red[0] / 448.f : 1.f;
+    if (threadIdx.x == 0) sw8[(int64_t)l * W + nrow] = sc;
+    const float inv = 1.f / sc;
+    uint8_t* dst = w8 + ((int64_t)l * W + nrow) * kmax8;
+    for (int k = threadIdx.x; k < kmax8; k += blockDim.x) {
+        const int src = l == 0 ? in_feature(k) : k;
+        const float x = (src >= 0 && src < in) ? Wrow[src] * inv : 0.f;
+        unsigned short h;
+        asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(h) : "f"(0.f), "f"(x));
+        dst[k] = (uint8_t)(h & 0xffu);
+    }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -1071,6 +1397,19 @@ int make_map(CUtensorMap* m, void* base, int inner, int rows, int L) {
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return DDF_OK;
+}
+
+int make_map_u8(CUtensorMap* m, void* base, int inner, int rows, int L) {
+    EncodeTiledFn enc = get_encode();
+    if (!enc) return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)L};
+    cuuint64_t strides[2] = {(cuuint64_t)inner, (cuuint64_t)inner * rows};
+    cuuint32_t box[3] = {128, (cuuint32_t)rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled (u8) failed (%d)", (int)r);
     return DDF_OK;
 }
 
@@ -1151,6 +1490,53 @@ int launch_mode(const ddf_net_s* net, int mode, const TcArgs& base, int64_t n, b
     return DDF_OK;
 }
 
+Layout smem_layout_f8(int W, int L) {
+    Layout s{};
+    const uint32_t act = (uint32_t)std::max(1, W / 128) * 16384u;
+    const uint32_t stage = (uint32_t)W * 128u;
+    const uint32_t vec = (uint32_t)L * W * 4u;
+    const uint32_t head = ((uint32_t)(2 * W + 2) * 4u + 15u) & ~15u;
+    const uint32_t partb = 128u * 2u * 4u;
+    const uint32_t fixed = act + 2 * vec + head + partb + 512u;
+    const uint32_t budget = 227u * 1024u - 1024u;
+    s.nst = std::max(0, std::min(8, (int)((budget - fixed) / stage)));
+    s.off_wst = act;
+    s.off_mask = act + (uint32_t)s.nst * stage;   // weight scales
+    s.off_bias = s.off_mask + vec;
+    s.off_head = s.off_bias + vec;
+    s.off_part = s.off_head + head;
+    s.off_grp = s.off_part + partb;
+    s.off_bar = s.off_grp;
+    s.total = s.off_bar + 512u + 1024u;
+    return s;
+}
+
+template <int W>
+int launch_f8(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_count, cudaStream_t stream) {
+    const TcPack* P = net->tc;
+    TcArgs a = base;
+    const Layout s = smem_layout_f8(W, a.L);
+    if (s.nst < 2) return fail(DDF_ERR_UNSUPPORTED, "FP8 MLP: shared memory too small");
+    a.nst = s.nst;
+    a.off_wst = s.off_wst;
+    a.off_mask = s.off_mask;
+    a.off_bias = s.off_bias;
+    a.off_head = s.off_head;
+    a.off_part = s.off_part;
+    a.off_bar = s.off_bar;
+    a.wscale = P->sw8;
+    int grid = use_count ? num_sms() : (int)std::min<int64_t>((n + kTileM - 1) / kTileM, num_sms());
+    if (grid <= 0) return DDF_OK;
+    static bool attr = false;
+    if (!attr) {
+        DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_f8_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr = true;
+    }
+    mlp_f8_kernel<W><<<grid, kThreads, s.total, stream>>>(P->map_f8, a);
+    DDF_LAUNCH_CHECK();
+    return DDF_OK;
+}
+
 uint32_t smem512(int nst) { return 8u * 16384u + (uint32_t)nst * 32768u + 512u + 1024u; }
 
 int launch512(const ddf_net_s* net, int mode, const TcArgs& base, int64_t n, bool use_count, cudaStream_t stream) {
@@ -1199,6 +1585,11 @@ __global__ void grouped_prep(const int64_t* __restrict__ offsets, const GNet* __
 }  // namespace
 
 bool tc_supported(const NetLayout& lay, int precision) {
+    if (precision == DDF_FP8) {
+        if (lay.width != 128 && lay.width != 256) return false;
+        if (lay.E + 2 > 128 || lay.L < 1 || lay.L > kMaxLayers) return false;
+        return smem_layout_f8(lay.width, lay.L).nst >= 2 && tc_supported(lay, DDF_BF16);
+    }
     if (precision != DDF_BF16) return false;
     if (lay.width != 128 && lay.width != 256 && lay.width != 512) return false;
     if (lay.E + 2 > 128) return false;
@@ -1217,6 +1608,8 @@ void tc_free(ddf_net_s* net) {
     cudaFree(P->hit_count);
     cudaFree(P->err);
     cudaFree(P->gmask);
+    cudaFree(P->w8);
+    cudaFree(P->sw8);
     delete P;
     net->tc = nullptr;
 }
@@ -1249,6 +1642,17 @@ int tc_pack(ddf_net_s* net, int precision, cudaStream_t stream) {
     dim3 grid(64, L);
     pack_kernel<<<grid, 256, 0, stream>>>(net->master, lay, P->kmax, P->w_fwd, P->w_bwd, P->bias, P->head);
     DDF_LAUNCH_CHECK();
+    if (precision == DDF_FP8) {
+        if (!P->w8) {
+            P->kmax8 = std::max(128, W);
+            DDF_CUDA_TRY(cudaMalloc(&P->w8, (size_t)L * W * P->kmax8));
+            DDF_CUDA_TRY(cudaMalloc(&P->sw8, sizeof(float) * (size_t)L * W));
+            int rc = make_map_u8(&P->map_f8, P->w8, P->kmax8, W, L);
+            if (rc) return rc;
+        }
+        pack_f8_kernel<<<dim3(W, L), 128, 0, stream>>>(net->master, lay, P->kmax8, P->w8, P->sw8);
+        DDF_LAUNCH_CHECK();
+    }
     return DDF_OK;
 }
 
@@ -1284,7 +1688,12 @@ int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n
         a.hit_list = P->hit_list;
         a.hit_count = P->hit_count;
     }
-    int rc = lay.width == 128   ? launch_mode<128>(net, 0, a, n, d_count != nullptr, stream)
+    int rc;
+    if (net->precision == DDF_FP8)
+        rc = lay.width == 128 ? launch_f8<128>(net, a, n, d_count != nullptr, stream)
+                              : launch_f8<256>(net, a, n, d_count != nullptr, stream);
+    else
+        rc = lay.width == 128   ? launch_mode<128>(net, 0, a, n, d_count != nullptr, stream)
              : lay.width == 256 ? launch_mode<256>(net, 0, a, n, d_count != nullptr, stream)
                                 : launch512(net, 0, a, n, d_count != nullptr, stream);
     if (rc || !normals) return rc;
@@ -1396,8 +1805,11 @@ extern "C" DDF_API int ddf_query_noalloc(ddf_net net, const float* d_origins, co
     a.err = P->err;
     a.hit_list = hit_list;
     a.hit_count = hit_count;
-    rc = lay.width == 128 ? launch_mode<128>(net, 0, a, n, false, stream)
-                          : launch_mode<256>(net, 0, a, n, false, stream);
+    if (net->precision == DDF_FP8)
+        rc = lay.width == 128 ? launch_f8<128>(net, a, n, false, stream) : launch_f8<256>(net, a, n, false, stream);
+    else
+        rc = lay.width == 128 ? launch_mode<128>(net, 0, a, n, false, stream)
+                              : launch_mode<256>(net, 0, a, n, false, stream);
     if (rc) return rc;
     TcArgs b = a;
     b.rows = hit_list;
