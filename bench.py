@@ -289,6 +289,24 @@ def main():
     roof["kernel"] = "field query (fused MLP + Eq. 3 normal)"
     roof["time_share"] = q["ms"] / ms if ms > 0 else None
 
+    # ---- wavefront kernels against HBM: algorithmic bytes per launch / measured launch time
+    B = w["bounces"]
+    shade_bytes = 0.0
+    for b in range(B):
+        live = stats[b]
+        surv = stats[b + 1] if b + 1 < B else 0
+        shade_bytes += 52.0 * live + 32.0 * surv + 4.0 * (live - surv)
+    sh = prof["shade"]
+    hbm = peaks["hbm_gbs"]
+    shade_gbs = shade_bytes / B / (sh["ms"] / max(1, sh["launches"]) / 1e3) / 1e9
+    rg = prof["raygen"]
+    raygen_gbs = paths * (32.0 + 4.0 * 0) / (rg["ms"] / max(1, rg["launches"]) / 1e3) / 1e9
+    wavefront_roofline = {
+        "shade": {"bound": "hbm", "achieved": shade_gbs, "peak": hbm, "unit": "GB/s", "frac": shade_gbs / hbm,
+                  "bytes": "52 B read per live ray + 32 B written per survivor + 4 B per terminated path"},
+        "raygen": {"bound": "hbm", "achieved": raygen_gbs, "peak": hbm, "unit": "GB/s", "frac": raygen_gbs / hbm,
+                   "bytes": "32 B of ray state written per path"}}
+
     # ---- end to end through the public call, image read back to pinned host memory
     host_img = torch.empty(w["height"], w["width"], pin_memory=True)
     cs = camera_struct(cam)
@@ -317,10 +335,26 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "queries_per_s": queries_per_s,
             "roofline": roof,
+            "wavefront_roofline": wavefront_roofline,
             "e2e": e2e,
             "gpu_launches": int(sum(v["launches"] for v in prof.values()) + args.steps * 2),
             "clocks": clocks}
 
+    # ---- FP8 path on the same render, with its query error
+    if rank == 0 and prec == "bf16" and args.fp32_steps > 0:
+        net8 = P.DDFNet(w["in_freqs"], w["hidden"], w["layers"], blob, "fp8")
+        net8.render(cam, w["spp"], w["bounces"], img)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(max(2, args.fp32_steps)):
+            net8.render(cam, w["spp"], w["bounces"], img)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        line["fp8_path"] = {"value": paths * max(2, args.fp32_steps) / (e0.elapsed_time(e1) / 1e3),
+                            "unit": "samples/s"}
+        if not args.no_oracle:
+            line["fp8_path"]["query_error"] = query_error(P, net8, blob, w)
     # ---- FP32 path beside the tensor-core path, and the oracle
     if rank == 0 and prec != "fp32" and args.fp32_steps > 0:
         net32 = P.DDFNet(w["in_freqs"], w["hidden"], w["layers"], blob, "fp32")
@@ -432,6 +466,32 @@ def other_rows(P, torch, np, peaks):
                              "launch_shapes": cfg,
                              "roofline": {"bound": "tensor", "achieved": flop / sec / 1e12, "peak": peak,
                                           "unit": "TFLOP/s", "frac": flop / sec / 1e12 / peak}}
+    # ---- width-512 network (102 -> 512 x 8 -> 2) queries and one wave of the large render
+    F5, W5, L5 = 16, 512, 8
+    blob5 = init_weights(F5, W5, L5, seed=5)
+    n5 = P.DDFNet(F5, W5, L5, blob5, "bf16")
+    nq = 1 << 22
+    g5 = torch.Generator(device="cuda").manual_seed(16)
+    qo = torch.randn(nq, 3, device="cuda", generator=g5)
+    qo = qo / qo.norm(dim=1, keepdim=True) * torch.rand(nq, 1, device="cuda", generator=g5)
+    qw = torch.randn(nq, 3, device="cuda", generator=g5)
+    qw = qw / qw.norm(dim=1, keepdim=True)
+    qout = n5.query(qo, qw)
+    sec = _time(torch, lambda: n5.query(qo, qw, out=qout), 3)
+    f5 = 2.0 * ((6 + 6 * F5) * W5 + (L5 - 1) * W5 * W5 + 2 * W5)
+    peak = peaks["bf16_tflops_sustained"]
+    rows["query_w512"] = {"workload": "2^22 queries, 102 -> 512 x 8 -> 2, BF16, no normals",
+                          "queries_per_s": nq / sec,
+                          "roofline": {"bound": "tensor", "achieved": f5 * nq / sec / 1e12, "peak": peak,
+                                       "unit": "TFLOP/s", "frac": f5 * nq / sec / 1e12 / peak}}
+    from ddf_synth import default_camera
+    cam5 = default_camera(1920, 1080, seed=1)
+    img5 = torch.empty(1080, 1920, device="cuda")
+    sec = _time(torch, lambda: n5.render(cam5, 8, 8, img5), 1)
+    rows["large_render_wave"] = {"workload": "1920 x 1080 x 8 spp (one wave of 16.6M paths), <= 8 bounces, "
+                                             "102 -> 512 x 8 -> 2 BF16 (the full 256-spp render is 32 such waves)",
+                                 "samples_per_s": 1920 * 1080 * 8 / sec, "ms": sec * 1e3,
+                                 "queries_per_bounce": n5.render_stats(8)}
     return rows
 
 
