@@ -528,15 +528,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t tcol = tbase + lane_off + (uint32_t)(b * W) + (uint32_t)(grp * 32);
                 const int l_bwd = 2 * Lt - 1 - s;
                 if (s < Lt || l_bwd >= 1) {
-                    // all of this thread's accumulator columns, one wait
-                    uint32_t raw[NKBW][32];
+                    // this thread's accumulator columns in two passes of two K-blocks: K-block 0
+                    // is released after two TMEM loads, and half the registers stay live
 #pragma unroll
-                    for (int kb = 0; kb < NKBW; ++kb) TC_LD32(tcol + kb * 64, raw[kb]);
+                    for (int pass = 0; pass < (NKBW + 1) / 2; ++pass) {
+                    constexpr int PB = NKBW < 2 ? NKBW : 2;
+                    uint32_t raw[PB][32];
+#pragma unroll
+                    for (int i = 0; i < PB; ++i) TC_LD32(tcol + (2 * pass + i) * 64, raw[i]);
                     tc_wait_ld();
                     if (s < Lt) {
                         const float* bs = bias_s + s * W;
 #pragma unroll
-                        for (int kb = 0; kb < NKBW; ++kb) {
+                        for (int i = 0; i < PB; ++i) {
+                            const int kb = 2 * pass + i;
                             const int c0 = kb * 64 + grp * 32;
                             const float4* b4 = reinterpret_cast<const float4*>(bs + c0);
                             if (s < Lt - 1) {
@@ -547,9 +552,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 for (int q = 0; q < 8; ++q) {
                                     const float4 bb = b4[q];
                                     float z0, z1, z2, z3;
-                                    add2(__uint_as_float(raw[kb][4 * q]), __uint_as_float(raw[kb][4 * q + 1]), bb.x,
+                                    add2(__uint_as_float(raw[i][4 * q]), __uint_as_float(raw[i][4 * q + 1]), bb.x,
                                          bb.y, z0, z1);
-                                    add2(__uint_as_float(raw[kb][4 * q + 2]), __uint_as_float(raw[kb][4 * q + 3]),
+                                    add2(__uint_as_float(raw[i][4 * q + 2]), __uint_as_float(raw[i][4 * q + 3]),
                                          bb.z, bb.w, z2, z3);
                                     pk[2 * q] = pack_relu(z0, z1);
                                     pk[2 * q + 1] = pack_relu(z2, z3);
@@ -566,7 +571,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 // output head on this thread's columns (FP32)
 #pragma unroll
                                 for (int c = 0; c < 32; ++c) {
-                                    const float z = fmaxf(__uint_as_float(raw[kb][c]) + bs[c0 + c], 0.f);
+                                    const float z = fmaxf(__uint_as_float(raw[i][c]) + bs[c0 + c], 0.f);
                                     y0 = fmaf(z, head_s[c0 + c], y0);
                                     y1 = fmaf(z, head_s[W + c0 + c], y1);
                                 }
@@ -575,8 +580,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 uint32_t pk[16];
 #pragma unroll
                                 for (int q = 0; q < 16; ++q) {
-                                    const float z0 = __uint_as_float(raw[kb][2 * q]) + bs[c0 + 2 * q];
-                                    const float z1 = __uint_as_float(raw[kb][2 * q + 1]) + bs[c0 + 2 * q + 1];
+                                    const float z0 = __uint_as_float(raw[i][2 * q]) + bs[c0 + 2 * q];
+                                    const float z1 = __uint_as_float(raw[i][2 * q + 1]) + bs[c0 + 2 * q + 1];
                                     pk[q] = pack_bf16(z0 > 0.f ? head_s[c0 + 2 * q] : 0.f,
                                                       z1 > 0.f ? head_s[c0 + 2 * q + 1] : 0.f);
                                 }
@@ -590,20 +595,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                     } else {
                         // delta_{l-1} = (delta_l W_l) * 1[z_{l-1} > 0]
 #pragma unroll
-                        for (int kb = 0; kb < NKBW; ++kb) {
+                        for (int i = 0; i < PB; ++i) {
+                            const int kb = 2 * pass + i;
                             const int c0 = kb * 64 + grp * 32;
                             const uint32_t bits = masks[((l_bwd - 1) * (W / 32) + (c0 >> 5)) * 128 + r];
                             uint32_t pk[16];
 #pragma unroll
                             for (int q = 0; q < 16; ++q)
-                                pk[q] = pack_bf16(((bits >> (2 * q)) & 1u) ? __uint_as_float(raw[kb][2 * q]) : 0.f,
-                                                  ((bits >> (2 * q + 1)) & 1u) ? __uint_as_float(raw[kb][2 * q + 1]) : 0.f);
+                                pk[q] = pack_bf16(((bits >> (2 * q)) & 1u) ? __uint_as_float(raw[i][2 * q]) : 0.f,
+                                                  ((bits >> (2 * q + 1)) & 1u) ? __uint_as_float(raw[i][2 * q + 1]) : 0.f);
 #pragma unroll
                             for (int m = 0; m < 4; ++m)
                                 st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
                                              pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
                             release_kb(actr, kb);
                         }
+                    }
                     }
                     if (s == Lt - 1 && MODE != 1) {
                         tc_fence_before();
