@@ -117,6 +117,13 @@ DDF_API int ddf_set_precision(ddf_net net, int precision);
  * kernels gave up since the last call (DDF_ERR_TIMEOUT, flag then cleared) or DDF_OK. */
 DDF_API int ddf_device_status(ddf_net net);
 
+/* Self-test of the bounded device waits used by the tensor-core kernels: one thread waits on
+ * an mbarrier with a limit of limit_ms (1..10000); a second thread arrives on it after ~1 ms
+ * only if `arrive` is non-zero. Returns DDF_ERR_TIMEOUT when the wait gave up and raised the
+ * device flag (no arrival), DDF_OK when it completed. The GPU context stays usable either way.
+ * Synchronous; allocates one int. */
+DDF_API int ddf_selftest_wait(int limit_ms, int arrive);
+
 /* Number of float32 values in the weight blob of this network. */
 DDF_API int ddf_num_params(ddf_net net, int64_t* out);
 

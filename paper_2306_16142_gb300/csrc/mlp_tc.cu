@@ -127,13 +127,14 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t phase) {
 }
 // Bounded wait for the phase with parity `phase` to complete. false: gave up (error raised).
 // The completed-phase test is inlined; only a wait that actually has to spin takes the call.
-__device__ __noinline__ bool mbar_wait_slow(uint64_t* b, uint32_t phase, int* err) {
+__device__ __noinline__ bool mbar_wait_slow(uint64_t* b, uint32_t phase, int* err,
+                                            uint64_t limit_ns = 2000000000ull) {
     const uint64_t t0 = gtimer();
     for (uint32_t i = 1;; ++i) {
         if (mbar_try(b, phase)) return true;
         if ((i & 255u) == 0) {
             if (*(volatile int*)err) return false;
-            if (gtimer() - t0 > 2000000000ull) {
+            if (gtimer() - t0 > limit_ns) {
                 atomicExch(err, 1);
                 return false;
             }
@@ -2150,5 +2151,50 @@ extern "C" DDF_API int ddf_group_config(ddf_group g, int* host_out6) {
         host_out6[3 * c + 1] = g->cls[c].nst;
         host_out6[3 * c + 2] = g->cls[c].grid;
     }
+    return DDF_OK;
+}
+
+// ------------------------------------------------------------------ bounded-wait self-test
+namespace ddf {
+namespace {
+// Thread 0 waits on a fresh mbarrier with the kernels' bounded wait; thread 1 arrives on it
+// (after ~1 ms) only when `arrive` is set. Without the arrival the wait must give up after
+// limit_ns, raise *err and return: the path every tensor-core kernel takes on a lost signal.
+__global__ void wait_probe_kernel(int* err, uint64_t limit_ns, int arrive) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!mbar_try(&bar, 0)) mbar_wait_slow(&bar, 0, err, limit_ns);
+    } else if (threadIdx.x == 1 && arrive) {
+        const uint64_t t0 = gtimer();
+        while (gtimer() - t0 < 1000000ull) {
+        }
+        mbar_arrive(&bar);
+    }
+    __syncthreads();
+}
+}  // namespace
+}  // namespace ddf
+
+extern "C" DDF_API int ddf_selftest_wait(int limit_ms, int arrive) {
+    using namespace ddf;
+    if (limit_ms <= 0 || limit_ms > 10000) return fail(DDF_ERR_INVALID_ARG, "limit_ms must be in (0, 10000]");
+    int* d = nullptr;
+    DDF_CUDA_TRY(cudaMalloc(&d, sizeof(int)));
+    cudaError_t e = cudaMemset(d, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        wait_probe_kernel<<<1, 32>>>(d, (uint64_t)limit_ms * 1000000ull, arrive);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(DDF_ERR_CUDA, "wait self-test: %s", cudaGetErrorString(e));
+    if (h) return fail(DDF_ERR_TIMEOUT, "bounded wait gave up after %d ms (device flag raised)", limit_ms);
     return DDF_OK;
 }
