@@ -400,7 +400,7 @@ def _time(torch, fn, reps, stream=None):
 
 def other_rows(P, torch, np, peaks):
     """The other hot-path rows on their own workloads: ray labelling (2^20 training rays x 8,192-
-    triangle knot), the training step (batch 65,536, 78 -> 256 x 8 -> 2, FP32 GEMMs) and the grouped
+    triangle knot), the training step (batch 65,536, 78 -> 256 x 8 -> 2; BF16 tensor-core and FP32) and the grouped
     16-object BF16 query replayed from a CUDA graph (ray counts log-uniform on [1e3, 1e6])."""
     from ddf_synth import init_weights, labelled_ray_set, torus_knot
     rows = {}
@@ -422,23 +422,36 @@ def other_rows(P, torch, np, peaks):
                                   "frac": tests / sec * 34 / alu_peak,
                                   "note": "34 FP32 instructions per filter test (count of the hot loop)"},
                      "hbm_gbs": (o.shape[0] * 33) / sec / 1e9}
-    # ---- a9 training step
+    # ---- a9 training step: BF16 tensor-core GEMMs (FP32 accumulate, FP32 masters), and the FP32 path
     Fq, Wd, Ld = 12, 256, 8
-    net = P.DDFNet(Fq, Wd, Ld, init_weights(Fq, Wd, Ld, seed=2), "fp32")
     n = 65536
     lab = mesh.label(to[:n].contiguous(), tw[:n].contiguous())
     dgt, hgt = lab["dist"].clone(), lab["hit"].clone()
     tsub, wsub = to[:n].contiguous(), tw[:n].contiguous()
     loss = torch.empty((), device="cuda")
-    sec = _time(torch, lambda: net.train_step(tsub, wsub, dgt, hgt, lr=1e-4, loss=loss), 3)
     E = 6 + 6 * Fq
     macs = E * Wd + (Ld - 1) * Wd * Wd + 2 * Wd
-    flop = 2.0 * macs * n * 4     # forward, recomputed forward, dgrad, wgrad
-    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
-    rows["train_step"] = {"workload": "batch 65,536 labelled rays, 78 -> 256 x 8 -> 2, L1 + BCE, Adam; FP32 SIMT GEMMs",
-                          "ms": sec * 1e3, "samples_per_s": n / sec,
-                          "roofline": {"bound": "alu", "achieved": flop / sec / 1e12, "peak": fp32_peak / 1e12,
-                                       "unit": "TFLOP/s", "frac": flop / sec / fp32_peak}}
+    for prec in ("bf16", "fp32"):
+        net = P.DDFNet(Fq, Wd, Ld, init_weights(Fq, Wd, Ld, seed=2), prec)
+        sec = _time(torch, lambda: net.train_step(tsub, wsub, dgt, hgt, lr=1e-4, loss=loss), 10 if prec == "bf16" else 3)
+        net.device_status()
+        if prec == "bf16":
+            flop = 2.0 * macs * n * 3     # forward, dgrad, wgrad (activations kept, no recompute)
+            peak = peaks["bf16_tflops_sustained"]
+            rows["train_step"] = {"workload": "batch 65,536 labelled rays, 78 -> 256 x 8 -> 2, L1 + BCE, Adam; "
+                                              "BF16 tcgen05 GEMMs, FP32 accumulate and masters",
+                                  "ms": sec * 1e3, "samples_per_s": n / sec, "loss": float(loss.item()),
+                                  "roofline": {"bound": "tensor", "achieved": flop / sec / 1e12, "peak": peak,
+                                               "unit": "TFLOP/s", "frac": flop / sec / 1e12 / peak}}
+        else:
+            flop = 2.0 * macs * n * 4     # forward, recomputed forward, dgrad, wgrad
+            fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+            rows["train_step_fp32"] = {"workload": "the same step on the FP32 SIMT GEMMs",
+                                       "ms": sec * 1e3, "samples_per_s": n / sec,
+                                       "roofline": {"bound": "alu", "achieved": flop / sec / 1e12,
+                                                    "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                                                    "frac": flop / sec / fp32_peak}}
+        del net
     # ---- a10 grouped query (16 objects, widths 128 / 256, 4-8 layers)
     rng = np.random.default_rng(14)
     specs = [(12, 128 if i % 2 == 0 else 256, 4 + (i % 5), 100 + i) for i in range(16)]

@@ -147,6 +147,20 @@ int backward(ddf_net_s* net, const float* o, const float* w, int64_t n, const fl
 int train_step(ddf_net_s* net, const float* o, const float* w, const float* dist_gt,
                const uint8_t* hit_gt, int64_t n, const ddf_adam* opt, float* loss,
                cudaStream_t stream);
+int count_hits(const uint8_t* hit_gt, int64_t n, int* out, cudaStream_t stream);
+// Loss = sum(row_l1) / n_hit + sum(row_bce) / n; part: 256 doubles of device scratch.
+int loss_reduce(const float* row_l1, const float* row_bce, int64_t n, const int* n_hit, float* loss,
+                double* part, cudaStream_t stream);
+// One Adam step on the FP32 masters, then the working copies are rebuilt from them.
+int adam_and_repack(ddf_net_s* net, const float* grad, const ddf_adam* opt, cudaStream_t stream);
+
+// ------------------------------------------------------------------ BF16 tensor-core training (train_tc.cu)
+bool tct_supported(const ddf_net_s* net);
+int tct_train_step(ddf_net_s* net, const float* o, const float* w, const float* dist_gt,
+                   const uint8_t* hit_gt, int64_t n, const ddf_adam* opt, float* loss,
+                   cudaStream_t stream);
+int tct_backward(ddf_net_s* net, const float* o, const float* w, int64_t n, const float* gdist,
+                 const float* glogit, float* gweights, float* ginput, cudaStream_t stream);
 
 int num_sms();
 

@@ -175,16 +175,11 @@ __global__ void gather_cot_kernel(const float* __restrict__ gd, const float* __r
 
 // Number of labelled hit rays (single block, fixed order).
 __global__ void count_hits_kernel(const uint8_t* __restrict__ h, int64_t n, int* out) {
-    __shared__ int part[256];
     int c = 0;
-    for (int64_t i = threadIdx.x; i < n; i += 256) c += h[i] ? 1 : 0;
-    part[threadIdx.x] = c;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int s = 0;
-        for (int k = 0; k < 256; ++k) s += part[k];
-        *out = s;
-    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += h[i] ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);   // integer sum: order-independent
 }
 
 // Per-row loss terms and output cotangents of the L1 (hit rows) + BCE-with-logits loss.
@@ -214,23 +209,48 @@ __global__ void loss_kernel(const float* __restrict__ Y, const float* __restrict
     }
 }
 
-__global__ void loss_reduce_kernel(const float* __restrict__ l1, const float* __restrict__ bce,
-                                   int64_t n, const int* __restrict__ n_hit, float* out) {
+// Loss = sum(l1) / n_hit + sum(bce) / n, in two fixed-order stages: kLossBlocks contiguous row
+// ranges (double partial sums), then one block over the partials.
+constexpr int kLossBlocks = 128;
+__global__ void loss_partial_kernel(const float* __restrict__ l1, const float* __restrict__ bce, int64_t n,
+                                    double* __restrict__ part) {
+    const int64_t per = (n + kLossBlocks - 1) / kLossBlocks;
+    const int64_t r0 = blockIdx.x * per, r1 = min(n, r0 + per);
     __shared__ double p1[256], p2[256];
     double a = 0, b = 0;
-    for (int64_t i = threadIdx.x; i < n; i += 256) {
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += 256) {
         a += l1[i];
         b += bce[i];
     }
     p1[threadIdx.x] = a;
     p2[threadIdx.x] = b;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s1 = 0, s2 = 0;
-        for (int k = 0; k < 256; ++k) {
-            s1 += p1[k];
-            s2 += p2[k];
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            p1[threadIdx.x] += p1[threadIdx.x + h];
+            p2[threadIdx.x] += p2[threadIdx.x + h];
         }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = p1[0];
+        part[2 * blockIdx.x + 1] = p2[0];
+    }
+}
+
+__global__ void loss_final_kernel(const double* __restrict__ part, int64_t n, const int* __restrict__ n_hit,
+                                  float* out) {
+    // one warp: lane k sums partials k, k + 32, ... in order, then a fixed shuffle tree
+    double s1 = 0, s2 = 0;
+    for (int k = threadIdx.x; k < kLossBlocks; k += 32) {
+        s1 += part[2 * k];
+        s2 += part[2 * k + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (threadIdx.x == 0) {
         const int nh = *n_hit;
         *out = (float)((nh > 0 ? s1 / nh : 0.0) + s2 / (double)n);
     }
@@ -298,7 +318,7 @@ int ensure_ws(ddf_net_s* net, int64_t n, ChunkWs& ws) {
     m = std::max<int64_t>(256, std::min<int64_t>(m, n));
     m = (m + 255) / 256 * 256;
     const size_t splitk = (size_t)64 * L.width * std::max(L.width, L.E);
-    const size_t need = per_row * (size_t)m + 4096 + sizeof(float) * 2 * (size_t)n +
+    const size_t need = per_row * (size_t)m + 8192 + sizeof(float) * 2 * (size_t)n +
                         sizeof(float) * (size_t)L.n_params + 64 + sizeof(float) * splitk;
     if (net->train_ws_bytes < need) {
         if (net->train_ws) cudaFree(net->train_ws);
@@ -328,6 +348,7 @@ struct RunWs {
     float* row_bce;
     float* grad;
     int* n_hit;
+    double* loss_part;
 };
 RunWs run_ws(ddf_net_s* net, const ChunkWs& ws, int64_t n) {
     const NetLayout& L = net->lay;
@@ -337,6 +358,7 @@ RunWs run_ws(ddf_net_s* net, const ChunkWs& ws, int64_t n) {
     r.row_bce = p; p += n;
     r.grad = p; p += L.n_params;
     r.n_hit = (int*)p;
+    r.loss_part = (double*)(((uintptr_t)(p + 2) + 255) & ~(uintptr_t)255);   // 2 kLossBlocks doubles
     return r;
 }
 
@@ -414,6 +436,7 @@ int chunk_backward(ddf_net_s* net, const float* o, const float* w, int64_t m, Ch
 
 int backward(ddf_net_s* net, const float* o, const float* w, int64_t n, const float* gdist,
              const float* glogit, float* gweights, float* ginput, cudaStream_t s) {
+    if (tct_supported(net)) return tct_backward(net, o, w, n, gdist, glogit, gweights, ginput, s);
     ChunkWs ws;
     int rc = ensure_ws(net, n, ws);
     if (rc) return rc;
@@ -432,31 +455,23 @@ int backward(ddf_net_s* net, const float* o, const float* w, int64_t n, const fl
     return DDF_OK;
 }
 
-int train_step(ddf_net_s* net, const float* o, const float* w, const float* dist_gt,
-               const uint8_t* hit_gt, int64_t n, const ddf_adam* opt, float* loss,
-               cudaStream_t s) {
-    ChunkWs ws;
-    int rc = ensure_ws(net, n, ws);
-    if (rc) return rc;
-    RunWs R = run_ws(net, ws, n);
-    const int64_t P = net->lay.n_params;
-    DDF_CUDA_TRY(cudaMemsetAsync(R.grad, 0, sizeof(float) * P, s));
-    count_hits_kernel<<<1, 256, 0, s>>>(hit_gt, n, R.n_hit);
+int count_hits(const uint8_t* hit_gt, int64_t n, int* out, cudaStream_t s) {
+    DDF_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(int), s));
+    count_hits_kernel<<<(unsigned)std::min<int64_t>(1024, (n + 255) / 256), 256, 0, s>>>(hit_gt, n, out);
     DDF_LAUNCH_CHECK();
-    for (int64_t r0 = 0; r0 < n; r0 += ws.m) {
-        const int64_t m = std::min(ws.m, n - r0);
-        rc = chunk_forward(net, o + 3 * r0, w + 3 * r0, m, ws, s);
-        if (rc) return rc;
-        loss_kernel<<<grid1d(m), 256, 0, s>>>(ws.Y, dist_gt + r0, hit_gt + r0, m, n, R.n_hit, ws.G,
-                                              R.row_l1 + r0, R.row_bce + r0);
-        DDF_LAUNCH_CHECK();
-        rc = chunk_backward(net, o + 3 * r0, w + 3 * r0, m, ws, R.grad, nullptr, s);
-        if (rc) return rc;
-    }
-    if (loss) {
-        loss_reduce_kernel<<<1, 256, 0, s>>>(R.row_l1, R.row_bce, n, R.n_hit, loss);
-        DDF_LAUNCH_CHECK();
-    }
+    return DDF_OK;
+}
+
+int loss_reduce(const float* row_l1, const float* row_bce, int64_t n, const int* n_hit, float* loss,
+                double* part, cudaStream_t s) {
+    loss_partial_kernel<<<kLossBlocks, 256, 0, s>>>(row_l1, row_bce, n, part);
+    loss_final_kernel<<<1, 32, 0, s>>>(part, n, n_hit, loss);
+    DDF_LAUNCH_CHECK();
+    return DDF_OK;
+}
+
+int adam_and_repack(ddf_net_s* net, const float* grad, const ddf_adam* opt, cudaStream_t s) {
+    const int64_t P = net->lay.n_params;
     if (!net->adam_m) {
         DDF_CUDA_TRY(cudaMalloc(&net->adam_m, sizeof(float) * P));
         DDF_CUDA_TRY(cudaMalloc(&net->adam_v, sizeof(float) * P));
@@ -467,13 +482,38 @@ int train_step(ddf_net_s* net, const float* o, const float* w, const float* dist
     const double t = (double)net->adam_step;
     const float c1 = (float)(1.0 - pow((double)opt->beta1, t));
     const float c2 = (float)(1.0 - pow((double)opt->beta2, t));
-    adam_kernel<<<grid1d(P), 256, 0, s>>>(net->master, R.grad, net->adam_m, net->adam_v, P, opt->lr,
+    adam_kernel<<<grid1d(P), 256, 0, s>>>(net->master, grad, net->adam_m, net->adam_v, P, opt->lr,
                                           opt->beta1, opt->beta2, opt->eps, c1, c2);
     DDF_LAUNCH_CHECK();
-    rc = build_transposed(net, s);
+    int rc = build_transposed(net, s);
     if (rc) return rc;
     if (net->tc) return tc_pack(net, net->precision, s);
     return DDF_OK;
+}
+
+int train_step(ddf_net_s* net, const float* o, const float* w, const float* dist_gt,
+               const uint8_t* hit_gt, int64_t n, const ddf_adam* opt, float* loss,
+               cudaStream_t s) {
+    if (tct_supported(net)) return tct_train_step(net, o, w, dist_gt, hit_gt, n, opt, loss, s);
+    ChunkWs ws;
+    int rc = ensure_ws(net, n, ws);
+    if (rc) return rc;
+    RunWs R = run_ws(net, ws, n);
+    const int64_t P = net->lay.n_params;
+    DDF_CUDA_TRY(cudaMemsetAsync(R.grad, 0, sizeof(float) * P, s));
+    if ((rc = count_hits(hit_gt, n, R.n_hit, s))) return rc;
+    for (int64_t r0 = 0; r0 < n; r0 += ws.m) {
+        const int64_t m = std::min(ws.m, n - r0);
+        rc = chunk_forward(net, o + 3 * r0, w + 3 * r0, m, ws, s);
+        if (rc) return rc;
+        loss_kernel<<<grid1d(m), 256, 0, s>>>(ws.Y, dist_gt + r0, hit_gt + r0, m, n, R.n_hit, ws.G,
+                                              R.row_l1 + r0, R.row_bce + r0);
+        DDF_LAUNCH_CHECK();
+        rc = chunk_backward(net, o + 3 * r0, w + 3 * r0, m, ws, R.grad, nullptr, s);
+        if (rc) return rc;
+    }
+    if (loss && (rc = loss_reduce(R.row_l1, R.row_bce, n, R.n_hit, loss, R.loss_part, s))) return rc;
+    return adam_and_repack(net, R.grad, opt, s);
 }
 
 }  // namespace ddf

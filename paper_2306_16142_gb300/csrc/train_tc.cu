@@ -1,0 +1,955 @@
+// Tensor-core training path of the BF16 working copy (Sec. 5.1: the DDF network is optimised
+// with Adam on the loss of its two outputs). Every contraction of the forward and reverse
+// passes is a tcgen05 BF16 GEMM with FP32 accumulators in tensor memory, fed by TMA:
+//
+//   forward  a_{l+1} = ReLU(a_l W_l^T + b_l)          A = a_l      [m][K_l]   B = W_l   [W][K_l]
+//   head     y = a_L W_out^T + b_out, the loss, G = dLoss/dy and
+//            delta_{L-1} = (G W_out) * 1[a_L > 0]      (epilogue of the last forward GEMM)
+//   dgrad    delta_{l-1} = (delta_l W_l) * 1[a_l > 0] A = delta_l  [m][W]     B = W_l^T [K_l][W]
+//   wgrad    dW_l = delta_l^T a_l                     A = delta_l^T [W][m]    B = a_l^T [K_l][m]
+//            (K = the batch: split over CTAs, partials summed in a fixed order)
+//
+// One persistent kernel serves all four: per CTA a TMA producer warp, an MMA warp (one thread
+// issues M = 128, N = BN, K = 16 MMAs into one of two TMEM accumulators, so a tile's epilogue
+// overlaps the next tile's MMAs) and eight epilogue warps (two column halves x four TMEM lane
+// quadrants; thread = row). The epilogues write activations and deltas twice: row-major BF16
+// (the next GEMM's K-major A operand) and transposed (the wgrad operands, whose K is the batch),
+// the transpose going through a 32 x 32 block per warp in shared memory. ReLU masks are kept as
+// bits; bias gradients and the output layer's gradients are per-32-row partial sums taken from
+// the same transposed blocks and reduced in a fixed order afterwards, so a step is
+// bit-reproducible.
+#include <math.h>
+
+#include <algorithm>
+
+#include "ddf_internal.cuh"
+#include "device_common.cuh"
+#include "tc_common.cuh"
+
+namespace ddf {
+namespace {
+
+constexpr int kTEpi = 8;                       // epilogue warps
+constexpr int kTThreads = (kTEpi + 2) * 32;    // + TMA producer warp + MMA warp
+constexpr uint32_t kSmemMax = 232448;          // 227 KB of dynamic shared memory per CTA
+
+enum { T_FWD = 0, T_HEAD = 1, T_DGRAD = 2, T_WGRAD = 3, T_STORE = 4 };
+
+struct TArgs {
+    int mode;
+    int M, N, BN;             // A has M rows, B has N rows; BN: N per tile (64..256, multiple of 64)
+    int nkb, kb_per, ksplit;  // K-blocks (64 wide) in total and per split; number of splits
+    int b_layer;              // third coordinate of B's tensor map
+    int nst;                  // pipeline stages
+    int64_t ldt;              // row length (elements) of the transposed outputs
+    int64_t m_valid;          // T_HEAD: rows below this are real
+    uint32_t off_blk, off_bias, off_head, off_y, off_g, off_bar;
+    const float* bias;        // [N]
+    const float* head;        // W_out [2][N], b_out [2]
+    __nv_bfloat16* out;       // [rows][N]
+    __nv_bfloat16* outT;      // [N][ldt]
+    uint32_t* mask_out;       // [rows][N / 32]
+    const uint32_t* mask_in;  // [rows][N / 32]
+    float* colpart;           // [rows / 32][N]
+    float* headpart;          // [rows / 32][2N + 2]
+    float* fout;              // T_WGRAD: [ksplit][M][N]; T_STORE: [rows][N]
+    const float* dist_gt;     // T_HEAD, loss form
+    const uint8_t* hit_gt;
+    const int* n_hit;
+    int64_t n_total;
+    const float* gd_in;       // T_HEAD, cotangent form
+    const float* gl_in;
+    float* row_l1;
+    float* row_bce;
+    int* err;
+};
+
+__device__ __forceinline__ float bf_lo(uint32_t p) { return __uint_as_float(p << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t p) { return __uint_as_float(p & 0xffff0000u); }
+
+// A warp's 32 x 32 BF16 block lives in 2 KB of shared memory: 32 lines of 64 B, the four 16-byte
+// pieces of line l stored at piece ^ ((l >> 1) & 3), so that eight consecutive lines written at
+// one logical piece, and two consecutive lines read whole, both touch every bank once. Reads go
+// four lanes to a line (lane: line 8 i + lane / 4, piece lane % 4), so every global store
+// instruction writes eight 64-byte segments: whole sectors, each written once.
+__device__ __forceinline__ uint32_t blk_off(int line, int piece) {
+    return (uint32_t)(line * 64 + 16 * (piece ^ ((line >> 1) & 3)));
+}
+
+// line = this lane's row (row-major staging of the lane's 32 values)
+__device__ __forceinline__ void stage_rows(uint8_t* tb, int lane, const uint32_t pk[16]) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+        *reinterpret_cast<uint4*>(tb + blk_off(lane, p)) =
+            make_uint4(pk[4 * p], pk[4 * p + 1], pk[4 * p + 2], pk[4 * p + 3]);
+    __syncwarp();
+}
+
+// line = column j of the block, position = row (transposed staging)
+__device__ __forceinline__ void stage_cols(uint8_t* tb, int lane, const uint32_t pk[16]) {
+    unsigned short* t16 = reinterpret_cast<unsigned short*>(tb);
+    const int pc = lane >> 3, wi = lane & 7;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const uint32_t h = (j & 1) ? (pk[j >> 1] >> 16) : (pk[j >> 1] & 0xffffu);
+        t16[j * 32 + 8 * (pc ^ ((j >> 1) & 3)) + wi] = (unsigned short)h;
+    }
+    __syncwarp();
+}
+
+// Piece (lane % 4) of line (8 i + lane / 4).
+__device__ __forceinline__ uint4 blk_read(const uint8_t* tb, int lane, int i) {
+    return *reinterpret_cast<const uint4*>(tb + blk_off(8 * i + (lane >> 2), lane & 3));
+}
+
+__device__ __forceinline__ float sum8(const uint4 v) {
+    float s = bf_lo(v.x);
+    s += bf_hi(v.x);
+    s += bf_lo(v.y);
+    s += bf_hi(v.y);
+    s += bf_lo(v.z);
+    s += bf_hi(v.z);
+    s += bf_lo(v.w);
+    s += bf_hi(v.w);
+    return s;
+}
+
+// Sum over the four lanes of a line; every one of them gets the same value (fixed pairing).
+__device__ __forceinline__ float line_sum(float s) {
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    return s;
+}
+
+// Rows row0..row0+31 (lane = row) of columns col0..col0+31 to a row-major [.][ld] array.
+__device__ __forceinline__ void store_rows(uint8_t* tb, int lane, const uint32_t pk[16], __nv_bfloat16* out,
+                                           int64_t ld, int64_t row0, int col0) {
+    stage_rows(tb, lane, pk);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<uint4*>(out + (row0 + 8 * i + (lane >> 2)) * ld + col0 + 8 * (lane & 3)) =
+            blk_read(tb, lane, i);
+    __syncwarp();
+}
+
+// The same block transposed into [col][ldt]; colsum (nullable) gets each column's sum over the
+// 32 rows of the BF16 values, in a fixed order.
+__device__ __forceinline__ void store_cols(uint8_t* tb, int lane, const uint32_t pk[16], __nv_bfloat16* outT,
+                                           int64_t ldt, int64_t row0, int col0, float* colsum) {
+    stage_cols(tb, lane, pk);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint4 v = blk_read(tb, lane, i);
+        const int line = 8 * i + (lane >> 2);
+        *reinterpret_cast<uint4*>(outT + (int64_t)(col0 + line) * ldt + row0 + 8 * (lane & 3)) = v;
+        if (colsum) {
+            const float t = line_sum(sum8(v));
+            if ((lane & 3) == 0) colsum[col0 + line] = t;
+        }
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kTThreads, 1)
+    train_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                      const TArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int NST = a.nst, BN = a.BN, N = a.N;
+    const uint32_t stage_bytes = 16384u + (uint32_t)BN * 128u;
+    uint8_t* blk = smem + a.off_blk;
+    float* bias_s = reinterpret_cast<float*>(smem + a.off_bias);
+    float* head_s = reinterpret_cast<float*>(smem + a.off_head);
+    float* ypart = reinterpret_cast<float*>(smem + a.off_y);   // [2 parity][2 groups][128][2]
+    float* gst = reinterpret_cast<float*>(smem + a.off_g);     // [8 warps][32][2]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + NST;
+    uint64_t* accf = bars + 2 * NST;
+    uint64_t* acce = accf + 2;
+    uint64_t* ybar = acce + 2;   // T_HEAD: both column halves' partial outputs written
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(ybar + 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntm = (a.M + 127) / 128, ntn = N / BN;
+    const int64_t ntiles = (int64_t)ntm * ntn * a.ksplit;
+    const uint32_t tcols = BN <= 128 ? 256u : 512u;
+
+    if (tid == 0) {
+        for (int i = 0; i < NST; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(&accf[0], 1);
+        mbar_init(&accf[1], 1);
+        mbar_init(&acce[0], kTEpi * 32);
+        mbar_init(&acce[1], kTEpi * 32);
+        mbar_init(&ybar[0], kTEpi * 32);
+        mbar_init(&ybar[1], kTEpi * 32);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                     "r"(tcols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (a.mode == T_FWD || a.mode == T_HEAD)
+        for (int i = tid; i < N; i += kTThreads) bias_s[i] = a.bias[i];
+    if (a.mode == T_HEAD)
+        for (int i = tid; i < 2 * N + 2; i += kTThreads) head_s[i] = a.head[i];
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+
+    if (warp == kTEpi) {
+        // ---------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            uint32_t cnt = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int s = (int)(t / (ntm * ntn)), rem = (int)(t % (ntm * ntn));
+                const int tm = rem % ntm, tn = rem / ntm;
+                const int kb0 = s * a.kb_per, kb1 = min(a.nkb, kb0 + a.kb_per);
+                for (int kb = kb0; kb < kb1; ++kb, ++cnt) {
+                    const int stg = (int)(cnt % (uint32_t)NST);
+                    const uint32_t ph = (cnt / (uint32_t)NST) & 1u;
+                    if (!mbar_wait(&empty[stg], ph ^ 1u, a.err)) { ok = false; break; }
+                    uint8_t* sa = smem + (size_t)stg * stage_bytes;
+                    mbar_expect_tx(&full[stg], stage_bytes);
+                    tma_load_3d(sa, &mapA, &full[stg], kb * 64, tm * 128, 0);
+                    tma_load_3d(sa + 16384, &mapB, &full[stg], kb * 64, tn * BN, a.b_layer);
+                }
+            }
+        }
+    } else if (warp == kTEpi + 1) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t cnt = 0, tl = 0;
+            bool ok = true;
+            const uint32_t idesc = idesc_bf16(128, BN);
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+                const int s = (int)(t / (ntm * ntn));
+                const int kb0 = s * a.kb_per, kb1 = min(a.nkb, kb0 + a.kb_per);
+                const uint32_t buf = tl & 1u;
+                if (!mbar_wait(&acce[buf], ((tl >> 1) & 1u) ^ 1u, a.err)) break;
+                tc_fence_after();
+                const uint32_t d = tbase + buf * (uint32_t)BN;
+                for (int kb = kb0; kb < kb1; ++kb, ++cnt) {
+                    const int stg = (int)(cnt % (uint32_t)NST);
+                    const uint32_t ph = (cnt / (uint32_t)NST) & 1u;
+                    if (!mbar_wait(&full[stg], ph, a.err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t sa = su32(smem + (size_t)stg * stage_bytes);
+                    const uint64_t ad = sdesc(sa), bd = sdesc(sa + 16384u);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, (kb > kb0 || k > 0));
+                    mma_commit(&empty[stg]);
+                }
+                if (ok) mma_commit(&accf[buf]);
+            }
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int grp = warp >> 2, q = warp & 3;
+        const int r = q * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        uint8_t* tb = blk + warp * 2048;
+        float* gw = gst + warp * 64;
+        const int nhalf = BN / 64;             // 32-column chunks per column group (1..4)
+        const int ch0 = grp * nhalf;
+        const int NW = N / 32;
+        uint32_t tl = 0;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+            const int s = (int)(t / (ntm * ntn)), rem = (int)(t % (ntm * ntn));
+            const int tm = rem % ntm, tn = rem / ntm;
+            const uint32_t buf = tl & 1u;
+            const int64_t row = (int64_t)tm * 128 + r;
+            const int64_t wrow0 = (int64_t)tm * 128 + q * 32;   // first row of this warp
+            const int64_t rblk = (int64_t)tm * 4 + q;           // 32-row block index
+            uint32_t mwords[4] = {0u, 0u, 0u, 0u};
+            if (a.mode == T_DGRAD) {
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc)
+                    if (cc < nhalf) mwords[cc] = a.mask_in[row * NW + (tn * BN) / 32 + ch0 + cc];
+            }
+            if (!mbar_wait(&accf[buf], (tl >> 1) & 1u, a.err)) break;
+            tc_fence_after();
+            const uint32_t tacc = tbase + lane_off + buf * (uint32_t)BN;
+
+            if (a.mode == T_FWD || a.mode == T_DGRAD) {
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    if (cc >= nhalf) break;
+                    const int c = ch0 + cc;
+                    const int col0 = tn * BN + c * 32;
+                    uint32_t raw[32], pk[16];
+                    TC_LD32(tacc + c * 32, raw);
+                    tc_wait_ld();
+                    if (a.mode == T_FWD) {
+                        uint32_t bits = 0;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float x0 = __uint_as_float(raw[2 * j]) + bias_s[col0 + 2 * j];
+                            const float x1 = __uint_as_float(raw[2 * j + 1]) + bias_s[col0 + 2 * j + 1];
+                            bits |= (pos(x0) << (2 * j)) | (pos(x1) << (2 * j + 1));
+                            pk[j] = pack_relu(x0, x1);
+                        }
+                        mwords[cc] = bits;
+                    } else {
+                        const uint32_t bits = mwords[cc];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float x0 = (bits >> (2 * j)) & 1u ? __uint_as_float(raw[2 * j]) : 0.f;
+                            const float x1 = (bits >> (2 * j + 1)) & 1u ? __uint_as_float(raw[2 * j + 1]) : 0.f;
+                            pk[j] = pack_bf16(x0, x1);
+                        }
+                    }
+                    store_rows(tb, lane, pk, a.out, N, wrow0, col0);
+                    store_cols(tb, lane, pk, a.outT, a.ldt, wrow0, col0,
+                               a.mode == T_DGRAD ? a.colpart + rblk * N : nullptr);
+                }
+                if (a.mode == T_FWD) {
+                    uint32_t* mo = a.mask_out + row * NW + (tn * BN) / 32 + ch0;
+                    if (nhalf == 4)
+                        *reinterpret_cast<uint4*>(mo) = make_uint4(mwords[0], mwords[1], mwords[2], mwords[3]);
+                    else
+                        for (int cc = 0; cc < nhalf; ++cc) mo[cc] = mwords[cc];
+                }
+            } else if (a.mode == T_WGRAD) {
+                // fragment order: each store instruction writes 512 contiguous bytes
+                float* base = a.fout + ((((int64_t)s * ntm + tm) * 4 + q) * (BN / 32)) * 1024;
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    if (cc >= nhalf) break;
+                    const int c = ch0 + cc;
+                    uint32_t raw[32];
+                    TC_LD32(tacc + c * 32, raw);
+                    tc_wait_ld();
+                    float4* dst = reinterpret_cast<float4*>(base + (int64_t)c * 1024) + lane;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        dst[32 * i] = make_float4(__uint_as_float(raw[4 * i]), __uint_as_float(raw[4 * i + 1]),
+                                                  __uint_as_float(raw[4 * i + 2]), __uint_as_float(raw[4 * i + 3]));
+                }
+            } else if (a.mode == T_STORE) {
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    if (cc >= nhalf) break;
+                    const int c = ch0 + cc;
+                    uint32_t raw[32];
+                    TC_LD32(tacc + c * 32, raw);
+                    tc_wait_ld();
+                    float4* dst = reinterpret_cast<float4*>(a.fout + row * N + tn * BN + c * 32);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        dst[i] = make_float4(__uint_as_float(raw[4 * i]), __uint_as_float(raw[4 * i + 1]),
+                                             __uint_as_float(raw[4 * i + 2]), __uint_as_float(raw[4 * i + 3]));
+                }
+            } else {
+                // T_HEAD: pass 1, the two output units from this half of the row
+                uint32_t hbits[4] = {0u, 0u, 0u, 0u};
+                float y0 = 0.f, y1 = 0.f;
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    if (cc >= nhalf) break;
+                    const int c = ch0 + cc;
+                    uint32_t raw[32];
+                    TC_LD32(tacc + c * 32, raw);
+                    tc_wait_ld();
+                    uint32_t bits = 0;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = c * 32 + j;
+                        const float x = __uint_as_float(raw[j]) + bias_s[col];
+                        bits |= pos(x) << j;
+                        const float h = fmaxf(x, 0.f);
+                        y0 = fmaf(h, head_s[col], y0);
+                        y1 = fmaf(h, head_s[N + col], y1);
+                    }
+                    hbits[cc] = bits;
+                }
+                float* yp = ypart + (tl & 1u) * 512;
+                yp[(grp * 128 + r) * 2] = y0;
+                yp[(grp * 128 + r) * 2 + 1] = y1;
+                mbar_arrive(&ybar[tl & 1u]);
+                if (!mbar_wait(&ybar[tl & 1u], (tl >> 1) & 1u, a.err)) break;
+                const float d = (yp[r * 2] + yp[(128 + r) * 2]) + head_s[2 * N];
+                const float z = (yp[r * 2 + 1] + yp[(128 + r) * 2 + 1]) + head_s[2 * N + 1];
+                float gd = 0.f, gl = 0.f;
+                if (row < a.m_valid) {
+                    if (a.hit_gt) {
+                        const int nh = *a.n_hit;
+                        const float inv_h = nh > 0 ? 1.f / (float)nh : 0.f;
+                        const float inv_n = 1.f / (float)a.n_total;
+                        const bool hit = a.hit_gt[row] != 0;
+                        const float h = hit ? 1.f : 0.f;
+                        float l1 = 0.f;
+                        if (hit) {
+                            const float diff = d - a.dist_gt[row];
+                            l1 = fabsf(diff);
+                            gd = (diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f)) * inv_h;
+                        }
+                        const float sig = 1.f / (1.f + expf(-z));
+                        gl = (sig - h) * inv_n;
+                        if (grp == 0) {
+                            a.row_l1[row] = l1;
+                            a.row_bce[row] = fmaxf(z, 0.f) - z * h + log1pf(expf(-fabsf(z)));
+                        }
+                    } else {
+                        gd = a.gd_in ? a.gd_in[row] : 0.f;
+                        gl = a.gl_in ? a.gl_in[row] : 0.f;
+                    }
+                }
+                gw[2 * lane] = gd;
+                gw[2 * lane + 1] = gl;
+                __syncwarp();
+                float* hp = a.headpart + rblk * (2 * N + 2);
+                // pass 2: output-layer gradient partials and delta_{L-1}
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    if (cc >= nhalf) break;
+                    const int c = ch0 + cc;
+                    const int col0 = c * 32;
+                    uint32_t raw[32], pk[16];
+                    TC_LD32(tacc + c * 32, raw);
+                    tc_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        pk[j] = pack_relu(__uint_as_float(raw[2 * j]) + bias_s[col0 + 2 * j],
+                                          __uint_as_float(raw[2 * j + 1]) + bias_s[col0 + 2 * j + 1]);
+                    stage_cols(tb, lane, pk);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const uint4 v = blk_read(tb, lane, i);   // column line, rows 8 p .. 8 p + 7
+                        const float* g8 = gw + 16 * (lane & 3);
+                        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+                        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            s0 = fmaf(g8[4 * k], bf_lo(vv[k]), s0);
+                            s1 = fmaf(g8[4 * k + 1], bf_lo(vv[k]), s1);
+                            s0 = fmaf(g8[4 * k + 2], bf_hi(vv[k]), s0);
+                            s1 = fmaf(g8[4 * k + 3], bf_hi(vv[k]), s1);
+                        }
+                        s0 = line_sum(s0);
+                        s1 = line_sum(s1);
+                        const int line = 8 * i + (lane >> 2);
+                        if ((lane & 3) == 0) {
+                            hp[col0 + line] = s0;
+                            hp[N + col0 + line] = s1;
+                        }
+                    }
+                    __syncwarp();
+                    const uint32_t bits = hbits[cc];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int cj = col0 + 2 * j;
+                        const float d0 = (bits >> (2 * j)) & 1u ? fmaf(gd, head_s[cj], gl * head_s[N + cj]) : 0.f;
+                        const float d1 =
+                            (bits >> (2 * j + 1)) & 1u ? fmaf(gd, head_s[cj + 1], gl * head_s[N + cj + 1]) : 0.f;
+                        pk[j] = pack_bf16(d0, d1);
+                    }
+                    store_rows(tb, lane, pk, a.out, N, wrow0, col0);
+                    store_cols(tb, lane, pk, a.outT, a.ldt, wrow0, col0, a.colpart + rblk * N);
+                }
+                if (grp == 0 && lane < 2) {
+                    float sg = 0.f;
+                    for (int i = 0; i < 32; ++i) sg += gw[2 * i + lane];
+                    hp[2 * N + lane] = sg;
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acce[buf]);
+        }
+    }
+    __syncthreads();
+    if (*(volatile int*)a.err) {
+        // error path: let MMAs and TMA copies already issued drain (they wait on nothing)
+        const uint64_t t0 = gtimer();
+        while (gtimer() - t0 < 200000ull) {
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(tcols));
+    }
+}
+
+// Rows of the batch encoded in the tensor-core feature order (six raw coordinates, two zero
+// columns, then per octave the sines and cosines), BF16, row-major [mp][K0] and transposed
+// [K0][mp]; rows m..mp-1 are zero.
+__global__ void tenc_kernel(const float* __restrict__ o, const float* __restrict__ w, int64_t m, int64_t mp,
+                            int E, int K0, __nv_bfloat16* __restrict__ X, __nv_bfloat16* __restrict__ XT) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= mp) return;
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const bool real = r < m;
+    if (real)
+        for (int j = 0; j < 3; ++j) {
+            v[j] = o[3 * r + j];
+            v[3 + j] = w[3 * r + j];
+        }
+    for (int p0 = 0; p0 < K0; p0 += 8) {
+        uint32_t pk[4];
+        for (int i = 0; i < 4; ++i) {
+            float f[2];
+            for (int h = 0; h < 2; ++h) {
+                const int src = in_feature(p0 + 2 * i + h);
+                f[h] = (real && src >= 0 && src < E) ? encode_feature(src, v) : 0.f;
+            }
+            pk[i] = pack_bf16(f[0], f[1]);
+            XT[(int64_t)(p0 + 2 * i) * mp + r] = __ushort_as_bfloat16((unsigned short)(pk[i] & 0xffffu));
+            XT[(int64_t)(p0 + 2 * i + 1) * mp + r] = __ushort_as_bfloat16((unsigned short)(pk[i] >> 16));
+        }
+        *reinterpret_cast<uint4*>(X + r * K0 + p0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+}
+
+// dW_l (blob layout, [W][in]) += the split-K partials summed in split order. Partials are in the
+// wgrad epilogue's fragment order (per split: M-tile, lane quadrant, 32-column chunk, float4
+// index, lane); layer 0's internal columns are scattered back to the encoding order and its pad
+// columns dropped.
+__global__ void wsum_kernel(const float4* __restrict__ part, int ksplit, int M, int N, int in_dim, int layer0,
+                            float* __restrict__ gW) {
+    // block (32, 8): x = one float4 of the slab, y = a lane over the splits (y, y + 8, ...)
+    const int64_t t = blockIdx.x * 32 + threadIdx.x;
+    const int64_t slab4 = (int64_t)M * N / 4;
+    __shared__ float4 red[8][32];
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t < slab4)
+        for (int k = threadIdx.y; k < ksplit; k += 8) {
+            const float4 v = part[(int64_t)k * slab4 + t];
+            acc.x += v.x;
+            acc.y += v.y;
+            acc.z += v.z;
+            acc.w += v.w;
+        }
+    red[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y != 0 || t >= slab4) return;
+    for (int k = 1; k < 8; ++k) {
+        const float4 v = red[k][threadIdx.x];
+        acc.x += v.x;
+        acc.y += v.y;
+        acc.z += v.z;
+        acc.w += v.w;
+    }
+    const int nch = N / 32;
+    const int lane = (int)(t & 31), i = (int)((t >> 5) & 7);
+    const int64_t u = t >> 8;
+    const int c = (int)(u % nch), q = (int)((u / nch) & 3), tm = (int)(u / (nch * 4));
+    const int o = tm * 128 + q * 32 + lane;
+    const float vals[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int p = c * 32 + 4 * i + e;
+        const int src = layer0 ? in_feature(p) : p;
+        if (src >= 0 && src < in_dim) gW[(int64_t)o * in_dim + src] += vals[e];
+    }
+}
+
+// Bias gradients db_l (blockIdx.y = l < L, from the per-32-row delta column sums) and the output
+// layer's dW_out / db_out (blockIdx.y = L, from the head partials), in two fixed-order stages:
+// kBGroups row groups of the partials (block (32, 8): 32 consecutive outputs x 8 row lanes), then
+// the groups in order.
+constexpr int kBGroups = 16;
+__global__ void bgrad_partial_kernel(const float* __restrict__ colpart, int64_t nrb, int64_t lstride, NetLayout lay,
+                                     const float* __restrict__ headpart, float* __restrict__ bpart) {
+    const int l = blockIdx.y, g = blockIdx.z, W = lay.width;
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    const int ncol = l < lay.L ? W : 2 * W + 2;
+    const int64_t ld = l < lay.L ? W : 2 * W + 2;
+    const float* P = l < lay.L ? colpart + (int64_t)l * lstride : headpart;
+    const int64_t per = (nrb + kBGroups - 1) / kBGroups;
+    const int64_t b0 = g * per, b1 = min(nrb, b0 + per);
+    __shared__ float red[8][33];
+    float s = 0.f;
+    if (c < ncol)
+        for (int64_t b = b0 + threadIdx.y; b < b1; b += 8) s += P[b * ld + c];
+    red[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < ncol) {
+        float t = red[0][threadIdx.x];
+        for (int k = 1; k < 8; ++k) t += red[k][threadIdx.x];
+        bpart[((int64_t)l * kBGroups + g) * (2 * W + 2) + c] = t;
+    }
+}
+
+__global__ void bgrad_final_kernel(const float* __restrict__ bpart, NetLayout lay, float* __restrict__ grad) {
+    const int l = blockIdx.y, W = lay.width;
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    const int ncol = l < lay.L ? W : 2 * W + 2;
+    if (c >= ncol) return;
+    float t = 0.f;
+    for (int g = 0; g < kBGroups; ++g) t += bpart[((int64_t)l * kBGroups + g) * (2 * W + 2) + c];
+    float* out = l < lay.L ? grad + lay.b_off[l] + c
+                           : (c < 2 * W ? grad + lay.w_off[lay.L] + c : grad + lay.b_off[lay.L] + (c - 2 * W));
+    *out += t;
+}
+
+// d/d(o, w) from the gradient of the internal first-layer inputs gx [mp][K0].
+__global__ void tenc_backward_kernel(const float* __restrict__ o, const float* __restrict__ w, int64_t m, int E,
+                                     int K0, const float* __restrict__ gx, float* __restrict__ gin) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= m) return;
+    float v[6];
+    for (int j = 0; j < 3; ++j) {
+        v[j] = o[3 * r + j];
+        v[3 + j] = w[3 * r + j];
+    }
+    float g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int p = 0; p < K0; ++p) {
+        const int f = in_feature(p);
+        if (f < 0 || f >= E) continue;
+        const int j = f < 6 ? f : (f - 6) % 6;
+        g[j] += gx[r * K0 + p] * encode_dfeature(f, v);
+    }
+    for (int j = 0; j < 6; ++j) gin[6 * r + j] = g[j];
+}
+
+// ------------------------------------------------------------------ host side
+struct TLayout {
+    uint32_t off_blk, off_bias, off_head, off_y, off_g, off_bar, total;
+    int nst;
+};
+
+TLayout tlayout(int BN) {
+    TLayout s;
+    const uint32_t stage = 16384u + (uint32_t)BN * 128u;
+    const uint32_t fixed = kTEpi * 2048 + 1024 + 2304 + 4096 + 2048 + 256;
+    s.nst = (int)std::min<uint32_t>(8u, (kSmemMax - 1024u - fixed) / stage);
+    uint32_t off = (uint32_t)s.nst * stage;
+    s.off_blk = off;  off += kTEpi * 2048;
+    s.off_bias = off; off += 1024;
+    s.off_head = off; off += 2304;
+    s.off_y = off;    off += 4096;
+    s.off_g = off;    off += 2048;
+    s.off_bar = off;  off += 256;
+    s.total = off + 1024;
+    return s;
+}
+
+// BF16 3-D tensor map: `inner` elements per row (row stride `ld` elements), `rows` rows per
+// slice, `depth` slices (slice stride rows * ld); box 64 x box_rows x 1, 128-byte swizzle.
+int tmap(CUtensorMap* m, const void* base, uint64_t inner, uint64_t ld, uint64_t rows, uint64_t depth,
+         uint32_t box_rows) {
+    EncodeTiledFn enc = get_encode();
+    if (!enc) return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[3] = {inner, rows, depth};
+    cuuint64_t strides[2] = {ld * 2, ld * rows * 2};
+    cuuint32_t box[3] = {64, box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return DDF_OK;
+}
+
+int launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, TArgs a, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        DDF_CUDA_TRY(cudaFuncSetAttribute(train_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+        attr = true;
+    }
+    if (a.BN % 64 || a.BN > 256 || a.N % a.BN) return fail(DDF_ERR_UNSUPPORTED, "training GEMM tile N=%d", a.BN);
+    const TLayout L = tlayout(a.BN);
+    if (L.nst < 2 || L.total > kSmemMax) return fail(DDF_ERR_UNSUPPORTED, "training GEMM shared memory");
+    a.nst = L.nst;
+    a.off_blk = L.off_blk;
+    a.off_bias = L.off_bias;
+    a.off_head = L.off_head;
+    a.off_y = L.off_y;
+    a.off_g = L.off_g;
+    a.off_bar = L.off_bar;
+    const int64_t ntiles = (int64_t)((a.M + 127) / 128) * (a.N / a.BN) * a.ksplit;
+    const int grid = (int)std::min<int64_t>(ntiles, num_sms());
+    train_gemm_kernel<<<grid, kTThreads, L.total, s>>>(mA, mB, a);
+    DDF_LAUNCH_CHECK();
+    return DDF_OK;
+}
+
+struct TcWs {
+    int64_t m = 0, mp = 0;   // rows per chunk, padded to 128
+    int ksplit_max = 0;
+    __nv_bfloat16* act[2];   // row-major activations [mp][max(K0, W)]
+    __nv_bfloat16* actT;     // a_l^T, l = 0..L-1: [K0][mp], then [W][mp] each
+    uint32_t* masks;         // ReLU masks of a_1..a_{L-1}: [mp][W / 32] each
+    __nv_bfloat16* dl[2];    // deltas, row-major [mp][W]
+    __nv_bfloat16* dT;       // delta^T [W][mp]
+    float* colpart;          // L x [mp / 32][W]
+    float* headpart;         // [mp / 32][2W + 2]
+    float* wpart;            // [ksplit][W][max(K0, W)]
+    float* gx;               // [mp][K0]
+    float* grad;             // [n_params]
+    float* row_l1;           // [n]
+    float* row_bce;          // [n]
+    int* n_hit;
+    double* loss_part;       // [256]
+    float* bpart;            // (L + 1) x kBGroups x (2W + 2)
+};
+
+int ensure_tc_ws(ddf_net_s* net, int64_t n, TcWs& ws) {
+    const NetLayout& lay = net->lay;
+    const int W = lay.width, L = lay.L, K0 = net->tc->K0, KM = std::max(K0, W);
+    const int ntm = W / 128;
+    ws.ksplit_max = std::max(1, num_sms() / ntm);
+    // buffer sizes in bytes for chunks of mp rows, in carving order
+    auto sizes = [&](size_t mp, size_t out[17]) {
+        out[0] = out[1] = mp * KM * 2;                                   // act[2]
+        out[2] = ((size_t)K0 + (size_t)(L - 1) * W) * mp * 2;            // actT
+        out[3] = (size_t)(L - 1) * mp * W / 8 + 4;                       // masks
+        out[4] = out[5] = out[6] = mp * W * 2;                           // dl[2], dT
+        out[7] = (size_t)L * (mp / 32) * W * 4;                          // colpart
+        out[8] = (mp / 32) * (2 * W + 2) * 4;                            // headpart
+        out[9] = (size_t)ws.ksplit_max * W * KM * 4;                     // wpart
+        out[10] = mp * K0 * 4;                                           // gx
+        out[11] = (size_t)lay.n_params * 4;                              // grad
+        out[12] = out[13] = (size_t)n * 4;                               // row_l1, row_bce
+        out[14] = 4;                                                     // n_hit
+        out[15] = 256 * sizeof(double);                                  // loss partials
+        out[16] = (size_t)(L + 1) * kBGroups * (2 * W + 2) * 4;          // bias-gradient partials
+    };
+    auto total = [&](size_t mp) {
+        size_t b[17], t = 0;
+        sizes(mp, b);
+        for (size_t x : b) t += (x + 255) / 256 * 256;
+        return t;
+    };
+    const size_t fixed = total(0);
+    const size_t per_128 = total(128) - fixed + 17 * 256;   // bytes per 128 rows (with rounding slack)
+    int64_t m = net->ws_limit > fixed ? (int64_t)((net->ws_limit - fixed) / per_128) * 128 : 0;
+    m = std::max<int64_t>(128, std::min<int64_t>(m, (n + 127) / 128 * 128));
+    ws.m = m;
+    ws.mp = m;
+    const size_t need = total((size_t)m);
+    if (net->train_ws_bytes < need) {
+        if (net->train_ws) cudaFree(net->train_ws);
+        net->train_ws = nullptr;
+        net->train_ws_bytes = 0;
+        DDF_CUDA_TRY(cudaMalloc(&net->train_ws, need));
+        net->train_ws_bytes = need;
+    }
+    size_t b[17];
+    sizes((size_t)m, b);
+    uint8_t* p = (uint8_t*)net->train_ws;
+    void* q[17];
+    for (int i = 0; i < 17; ++i) {
+        q[i] = p;
+        p += (b[i] + 255) / 256 * 256;
+    }
+    ws.act[0] = (__nv_bfloat16*)q[0];
+    ws.act[1] = (__nv_bfloat16*)q[1];
+    ws.actT = (__nv_bfloat16*)q[2];
+    ws.masks = (uint32_t*)q[3];
+    ws.dl[0] = (__nv_bfloat16*)q[4];
+    ws.dl[1] = (__nv_bfloat16*)q[5];
+    ws.dT = (__nv_bfloat16*)q[6];
+    ws.colpart = (float*)q[7];
+    ws.headpart = (float*)q[8];
+    ws.wpart = (float*)q[9];
+    ws.gx = (float*)q[10];
+    ws.grad = (float*)q[11];
+    ws.row_l1 = (float*)q[12];
+    ws.row_bce = (float*)q[13];
+    ws.n_hit = (int*)q[14];
+    ws.loss_part = (double*)q[15];
+    ws.bpart = (float*)q[16];
+    return DDF_OK;
+}
+
+// The loss inputs of one chunk (labels) or its output cotangents.
+struct ChunkTargets {
+    const float* dist_gt = nullptr;
+    const uint8_t* hit_gt = nullptr;
+    const int* n_hit = nullptr;
+    int64_t n_total = 0;
+    float* row_l1 = nullptr;
+    float* row_bce = nullptr;
+    const float* gd = nullptr;
+    const float* gl = nullptr;
+};
+
+// Forward and reverse pass of rows [0, m) of one chunk; gradients accumulate into grad.
+int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m, const ChunkTargets& tg,
+             float* grad, float* gin, cudaStream_t s) {
+    const NetLayout& lay = net->lay;
+    TcPack* P = net->tc;
+    const int W = lay.width, L = lay.L, K0 = P->K0;
+    const int64_t mp = (m + 127) / 128 * 128, ld = ws.mp;
+    auto actT = [&](int l) { return ws.actT + (l == 0 ? 0 : ((int64_t)K0 + (int64_t)(l - 1) * W) * ld); };
+    auto masks = [&](int l) { return ws.masks + (int64_t)(l - 1) * ld * (W / 32); };
+    auto colpart = [&](int l) { return ws.colpart + (int64_t)l * (ld / 32) * W; };
+    int rc;
+
+    tenc_kernel<<<(unsigned)((mp + 127) / 128), 128, 0, s>>>(o, w, m, ld, lay.E, K0, ws.act[0], ws.actT);
+    DDF_LAUNCH_CHECK();
+
+    // ---------------------------------------------------------------- forward (+ head)
+    for (int l = 0; l < L; ++l) {
+        const int K = l == 0 ? K0 : W;
+        CUtensorMap mA;
+        if ((rc = tmap(&mA, ws.act[l & 1], K, K, m, 1, 128))) return rc;
+        TArgs a{};
+        a.mode = l == L - 1 ? T_HEAD : T_FWD;
+        a.M = (int)m;
+        a.N = W;
+        a.BN = W;
+        a.nkb = K / 64;
+        a.kb_per = a.nkb;
+        a.ksplit = 1;
+        a.b_layer = l;
+        a.ldt = ld;
+        a.m_valid = m;
+        a.bias = P->bias + (int64_t)l * W;
+        a.err = P->err;
+        if (a.mode == T_FWD) {
+            a.out = ws.act[(l + 1) & 1];
+            a.outT = actT(l + 1);
+            a.mask_out = masks(l + 1);
+        } else {
+            a.head = P->head;
+            a.out = ws.dl[0];
+            a.outT = ws.dT;
+            a.colpart = colpart(L - 1);
+            a.headpart = ws.headpart;
+            a.dist_gt = tg.dist_gt;
+            a.hit_gt = tg.hit_gt;
+            a.n_hit = tg.n_hit;
+            a.n_total = tg.n_total;
+            a.row_l1 = tg.row_l1;
+            a.row_bce = tg.row_bce;
+            a.gd_in = tg.gd;
+            a.gl_in = tg.gl;
+        }
+        if ((rc = launch_gemm(mA, P->map_fwd, a, s))) return rc;
+    }
+
+    // ---------------------------------------------------------------- reverse
+    int cur = 0;
+    for (int l = L - 1; l >= 0; --l) {
+        const int K = l == 0 ? K0 : W;
+        {   // dW_l = delta_l^T a_l, split over the rows
+            CUtensorMap mA, mB;
+            if ((rc = tmap(&mA, ws.dT, m, ld, W, 1, 128))) return rc;
+            if ((rc = tmap(&mB, actT(l), m, ld, K, 1, K))) return rc;
+            const int nkb = (int)((m + 63) / 64);
+            const int want = std::max(1, std::min(ws.ksplit_max, nkb));
+            const int kb_per = (nkb + want - 1) / want;
+            TArgs a{};
+            a.mode = T_WGRAD;
+            a.M = W;
+            a.N = K;
+            a.BN = K;
+            a.nkb = nkb;
+            a.kb_per = kb_per;
+            a.ksplit = (nkb + kb_per - 1) / kb_per;
+            a.b_layer = 0;
+            a.fout = ws.wpart;
+            a.err = P->err;
+            if ((rc = launch_gemm(mA, mB, a, s))) return rc;
+            const int64_t tot4 = (int64_t)W * K / 4;
+            wsum_kernel<<<(unsigned)((tot4 + 31) / 32), dim3(32, 8), 0, s>>>((const float4*)ws.wpart, a.ksplit, W, K,
+                                                                     l == 0 ? lay.E : W, l == 0,
+                                                                     grad + lay.w_off[l]);
+            DDF_LAUNCH_CHECK();
+        }
+        if (l > 0) {   // delta_{l-1} = (delta_l W_l) * 1[a_l > 0]
+            CUtensorMap mA;
+            if ((rc = tmap(&mA, ws.dl[cur], W, W, m, 1, 128))) return rc;
+            TArgs a{};
+            a.mode = T_DGRAD;
+            a.M = (int)m;
+            a.N = W;
+            a.BN = W;
+            a.nkb = W / 64;
+            a.kb_per = a.nkb;
+            a.ksplit = 1;
+            a.b_layer = l;
+            a.ldt = ld;
+            a.mask_in = masks(l);
+            a.out = ws.dl[cur ^ 1];
+            a.outT = ws.dT;
+            a.colpart = colpart(l - 1);
+            a.err = P->err;
+            if ((rc = launch_gemm(mA, P->map_bwd, a, s))) return rc;
+            cur ^= 1;
+        } else if (gin) {   // d/d(internal inputs) = delta_0 W_0, then the encoding's Jacobian
+            CUtensorMap mA, mB;
+            if ((rc = tmap(&mA, ws.dl[cur], W, W, m, 1, 128))) return rc;
+            if ((rc = tmap(&mB, P->w_bwd, W, W, W, L, K0))) return rc;
+            TArgs a{};
+            a.mode = T_STORE;
+            a.M = (int)m;
+            a.N = K0;
+            a.BN = K0;
+            a.nkb = W / 64;
+            a.kb_per = a.nkb;
+            a.ksplit = 1;
+            a.b_layer = 0;
+            a.fout = ws.gx;
+            a.err = P->err;
+            if ((rc = launch_gemm(mA, mB, a, s))) return rc;
+            tenc_backward_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(o, w, m, lay.E, K0, ws.gx, gin);
+            DDF_LAUNCH_CHECK();
+        }
+    }
+    const unsigned gx = (unsigned)((2 * W + 2 + 31) / 32);
+    bgrad_partial_kernel<<<dim3(gx, (unsigned)(L + 1), kBGroups), dim3(32, 8), 0, s>>>(
+        ws.colpart, mp / 32, (ld / 32) * W, lay, ws.headpart, ws.bpart);
+    bgrad_final_kernel<<<dim3(gx, (unsigned)(L + 1)), 32, 0, s>>>(ws.bpart, lay, grad);
+    DDF_LAUNCH_CHECK();
+    return DDF_OK;
+}
+
+}  // namespace
+
+bool tct_supported(const ddf_net_s* net) {
+    if (net->is_sphere || !net->tc) return false;
+    if (net->precision != DDF_BF16 && net->precision != DDF_FP8) return false;
+    const int W = net->lay.width;
+    return (W == 128 || W == 256) && net->tc->K0 <= 256;
+}
+
+int tct_train_step(ddf_net_s* net, const float* o, const float* w, const float* dist_gt, const uint8_t* hit_gt,
+                   int64_t n, const ddf_adam* opt, float* loss, cudaStream_t s) {
+    TcWs ws;
+    int rc = ensure_tc_ws(net, n, ws);
+    if (rc) return rc;
+    DDF_CUDA_TRY(cudaMemsetAsync(ws.grad, 0, sizeof(float) * net->lay.n_params, s));
+    if ((rc = count_hits(hit_gt, n, ws.n_hit, s))) return rc;
+    for (int64_t r0 = 0; r0 < n; r0 += ws.m) {
+        const int64_t m = std::min(ws.m, n - r0);
+        ChunkTargets tg;
+        tg.dist_gt = dist_gt + r0;
+        tg.hit_gt = hit_gt + r0;
+        tg.n_hit = ws.n_hit;
+        tg.n_total = n;
+        tg.row_l1 = ws.row_l1 + r0;
+        tg.row_bce = ws.row_bce + r0;
+        if ((rc = tc_chunk(net, ws, o + 3 * r0, w + 3 * r0, m, tg, ws.grad, nullptr, s))) return rc;
+    }
+    if (loss && (rc = loss_reduce(ws.row_l1, ws.row_bce, n, ws.n_hit, loss, ws.loss_part, s))) return rc;
+    return adam_and_repack(net, ws.grad, opt, s);
+}
+
+int tct_backward(ddf_net_s* net, const float* o, const float* w, int64_t n, const float* gdist,
+                 const float* glogit, float* gweights, float* ginput, cudaStream_t s) {
+    TcWs ws;
+    int rc = ensure_tc_ws(net, n, ws);
+    if (rc) return rc;
+    DDF_CUDA_TRY(cudaMemsetAsync(gweights, 0, sizeof(float) * net->lay.n_params, s));
+    for (int64_t r0 = 0; r0 < n; r0 += ws.m) {
+        const int64_t m = std::min(ws.m, n - r0);
+        ChunkTargets tg;
+        tg.gd = gdist ? gdist + r0 : nullptr;
+        tg.gl = glogit ? glogit + r0 : nullptr;
+        if ((rc = tc_chunk(net, ws, o + 3 * r0, w + 3 * r0, m, tg, gweights, ginput ? ginput + 6 * r0 : nullptr,
+                           s)))
+            return rc;
+    }
+    return DDF_OK;
+}
+
+}  // namespace ddf

@@ -42,3 +42,45 @@ def query_bf16(params, o, w, in_freqs):
         g[:, f % 6] += gf[:, f]
     return {"dist": y[:, 0], "logit": y[:, 1], "hit": y[:, 1] > 0, "grad": g,
             "normal": omlp.normal_from_gradient(g[:, :3], w)}
+
+
+def train_grad_bf16(params, o, w, in_freqs, gy=None, dist_gt=None, hit_gt=None, snap=False):
+    """The reverse pass of the tensor-core training path with its BF16 rounding points: the
+    encoded input, the weights and every hidden activation that feeds a GEMM, every delta;
+    the head (y and G) and the output-layer delta product in full precision, dW_out from the
+    BF16-rounded last activation. Returns (loss or None, [(dW, db)], d/d(o, w) (n, 6)).
+
+    snap: round the encoded features to multiples of 2^-20, for inputs whose features are
+    exactly 0 or +-1 (sin(k pi) evaluates to ~1e-16 in floating point, sinpi to exactly 0)."""
+    X, dX = omlp.encode(o, w, in_freqs)
+    if snap:
+        X = np.round(X * 2.0 ** 20) / 2.0 ** 20
+    L = len(params) - 1
+    a = bf16(X)
+    acts, masks = [a], []
+    for l in range(L):
+        Wl, b = params[l]
+        z = a @ bf16(Wl).T + b
+        masks.append(z > 0)
+        a = np.maximum(z, 0.0)
+        if l < L - 1:
+            a = bf16(a)
+            acts.append(a)
+    Wo, bo = params[L]
+    y = a @ Wo.T + bo
+    loss = None
+    if gy is None:
+        loss, gy = omlp.loss_and_output_grad(y, dist_gt, hit_gt)
+    grads = [None] * (L + 1)
+    grads[L] = (gy.T @ bf16(a), gy.sum(0))
+    d = bf16((gy @ Wo) * masks[L - 1])
+    for l in range(L - 1, -1, -1):
+        grads[l] = (d.T @ acts[l], d.sum(0))
+        if l > 0:
+            d = bf16((d @ bf16(params[l][0])) * masks[l - 1])
+    gX = d @ bf16(params[0][0])
+    gf = gX * dX
+    g = np.zeros((X.shape[0], 6))
+    for f in range(X.shape[1]):
+        g[:, f % 6] += gf[:, f]
+    return loss, grads, g

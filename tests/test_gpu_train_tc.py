@@ -1,0 +1,200 @@
+"""GPU parity of the BF16 tensor-core training path (BF16 / FP8 handles of width 128 or 256).
+
+Kernel correctness is pinned against tests/_bf16_model.train_grad_bf16, the same reverse pass
+with the path's BF16 rounding points. On a network and rays whose arithmetic is exact (dyadic
+weights with few terms per unit, features in {0, +-1, +-1/2}) every activation, ReLU mask and
+delta agrees exactly, so the gradients must match to FP32 summation order (1e-5 relative). On
+ordinary weights a ReLU unit whose pre-activation sits within rounding of zero flips between
+FP32 and FP64 accumulation and carries one row's delta down every layer below it, so there the
+bound is 3e-2 per tensor; the distance of the BF16 gradient from the FP64 oracle gradient is the
+BF16 network's own and is printed and only loosely bounded. Also: determinism, ragged batches
+and row chunks, the cotangent form with the input gradient, the loss and the first Adam step, and
+a short training run that lowers the loss."""
+
+import numpy as np
+import pytest
+import torch
+
+from ddf_synth import init_weights
+from oracle import mlp as omlp
+from oracle.sphere import sphere_ddf
+from tests._bf16_model import train_grad_bf16
+from tests._helpers import ensure_built, rays_in_ball
+
+pytestmark = pytest.mark.gpu
+
+EXACT_REL = 1e-5
+MODEL_REL = 3e-2
+SHAPES = [(12, 256, 8, 2), (12, 128, 4, 7), (0, 128, 6, 9), (16, 256, 3, 4)]
+
+
+@pytest.fixture(scope="module")
+def P():
+    ensure_built()
+    import paper_2306_16142_gb300 as P
+    return P
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def _split(blob, F, W, L):
+    return omlp.unpack(np.asarray(blob, np.float64), F, W, L)
+
+
+def dyadic_net(F, W, L, seed, nnz=8):
+    """Weights k/8 (|k| <= 4, eight per unit), biases k/32, head k/16: every sum the path forms
+    is exact in FP32."""
+    rng = np.random.default_rng(seed)
+    E = 6 + 6 * F
+    params = []
+    for l in range(L):
+        K = E if l == 0 else W
+        Wl = np.zeros((W, K))
+        for r in range(W):
+            idx = rng.choice(K, size=min(nnz, K), replace=False)
+            Wl[r, idx] = rng.integers(1, 5, size=len(idx)) * rng.choice([-1, 1], size=len(idx)) / 8.0
+        params.append((Wl, rng.integers(-4, 5, size=W) / 32.0))
+    params.append((rng.integers(-8, 9, size=(2, W)) / 16.0, rng.integers(-4, 5, size=2) / 16.0))
+    return params
+
+
+def dyadic_rays(n, F, seed):
+    """Origins and directions whose encoded features are exact: coordinates in {0, +-1/2} and
+    axis directions when the encoding is on, any multiple of 1/16 without it."""
+    rng = np.random.default_rng(seed)
+    if F == 0:
+        return ((rng.integers(-15, 16, size=(n, 3)) / 16.0).astype(np.float32),
+                (rng.integers(-15, 16, size=(n, 3)) / 16.0).astype(np.float32))
+    o = rng.integers(-1, 2, size=(n, 3)) * 0.5
+    w = np.zeros((n, 3))
+    w[np.arange(n), rng.integers(0, 3, size=n)] = rng.choice([-1.0, 1.0], size=n)
+    return o.astype(np.float32), w.astype(np.float32)
+
+
+@pytest.mark.parametrize("F,W,L", [(12, 256, 8), (0, 128, 6), (16, 256, 3), (12, 128, 4)])
+@pytest.mark.parametrize("n", [1, 200, 4096, 20000])
+def test_tc_backward_exact_arithmetic(P, F, W, L, n):
+    params = dyadic_net(F, W, L, seed=W + L)
+    blob = omlp.pack(params).astype(np.float32)
+    assert np.array_equal(blob.astype(np.float64), omlp.pack(params))
+    net = P.DDFNet(F, W, L, blob, "bf16")
+    o, w = dyadic_rays(n, F, seed=n)
+    gy = np.random.default_rng(n + 1).integers(-8, 9, size=(n, 2)) / 16.0
+    t = [torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda() for x in (o, w, gy[:, 0], gy[:, 1])]
+    gw, gin = net.backward(*t, need_input=True)
+    net.device_status()
+    _, mg, mgin = train_grad_bf16(params, o, w, F, gy=gy, snap=True)
+    _check_grads(gw.cpu().numpy().astype(np.float64), mg, F, W, L, tol=EXACT_REL)
+    assert _rel(gin.cpu().numpy(), mgin) < EXACT_REL
+
+
+def _check_grads(got_blob, model_grads, F, W, L, tol=MODEL_REL):
+    for l, ((gW, gb), (mW, mb)) in enumerate(zip(_split(got_blob, F, W, L), model_grads)):
+        assert _rel(gW, mW) < tol, (l, _rel(gW, mW))
+        assert _rel(gb, mb) < tol, (l, _rel(gb, mb))
+
+
+@pytest.mark.parametrize("F,W,L,seed", SHAPES)
+@pytest.mark.parametrize("n", [1, 129, 1000, 4096])
+def test_tc_backward_matches_bf16_model(P, F, W, L, seed, n):
+    blob = init_weights(F, W, L, seed=seed)
+    net = P.DDFNet(F, W, L, blob, "bf16")
+    o, w = rays_in_ball(n, seed=30 + n)
+    rng = np.random.default_rng(n)
+    gd = rng.normal(size=n).astype(np.float32)
+    gl = rng.normal(size=n).astype(np.float32)
+    to, tw = torch.from_numpy(o).cuda(), torch.from_numpy(w).cuda()
+    tgd, tgl = torch.from_numpy(gd).cuda(), torch.from_numpy(gl).cuda()
+    gw, gin = net.backward(to, tw, tgd, tgl, need_input=True)
+    gw2, _ = net.backward(to, tw, tgd, tgl)
+    net.device_status()
+    assert torch.equal(gw, gw2)
+    Pm = _split(blob, F, W, L)
+    gy = np.stack([gd, gl], 1).astype(np.float64)
+    _, mg, mgin = train_grad_bf16(Pm, o, w, F, gy=gy)
+    got = gw.cpu().numpy().astype(np.float64)
+    _check_grads(got, mg, F, W, L)
+    assert _rel(gin.cpu().numpy(), mgin) < MODEL_REL
+    # the BF16 network's own distance from the FP64 gradient (stated, loosely bounded)
+    X, _ = omlp.encode(o, w, F)
+    y, pres, acts = omlp.forward(Pm, X)
+    ref, _ = omlp.backward(Pm, pres, acts, gy)
+    errs = [_rel(a[0], b[0]) for a, b in zip(_split(got, F, W, L), ref)]
+    print(f"BF16 vs FP64 dW rel L2 per layer ({F},{W},{L}) n={n}: " + " ".join(f"{e:.3g}" for e in errs))
+    if n >= 1000:
+        assert max(errs) < 0.3
+
+
+def test_tc_backward_row_chunks(P):
+    """128-row chunks with a ragged last chunk give the one-chunk gradient up to FP32 order."""
+    F, W, L, seed = SHAPES[0]
+    n = 3000
+    net = P.DDFNet(F, W, L, init_weights(F, W, L, seed=seed), "bf16")
+    o, w = rays_in_ball(n, seed=5)
+    to, tw = torch.from_numpy(o).cuda(), torch.from_numpy(w).cuda()
+    gd = torch.ones(n, device="cuda")
+    gl = torch.full((n,), -0.5, device="cuda")
+    full, gin_full = net.backward(to, tw, gd, gl, need_input=True)
+    net.set_workspace_limit(1 << 20)
+    chunked, gin_chunked = net.backward(to, tw, gd, gl, need_input=True)
+    net.device_status()
+    assert _rel(chunked.cpu().numpy(), full.cpu().numpy()) < 1e-5
+    assert torch.equal(gin_full, gin_chunked)      # row-local: chunking changes nothing
+
+
+def _labels(o, w, r=0.5):
+    dist, hit, _ = sphere_ddf(o, w, r)
+    dgt = np.where(hit, dist, np.inf).astype(np.float32)
+    return dgt, hit.astype(np.uint8)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_tc_train_step_loss_and_update(P, precision):
+    F, W, L, seed = SHAPES[0]
+    n = 5000
+    blob = init_weights(F, W, L, seed=seed)
+    net = P.DDFNet(F, W, L, blob, precision)
+    o, w = rays_in_ball(n, seed=12)
+    dgt, hgt = _labels(o, w)
+    assert 0.1 < hgt.mean() < 0.9
+    loss = net.train_step(torch.from_numpy(o).cuda(), torch.from_numpy(w).cuda(),
+                          torch.from_numpy(dgt).cuda(), torch.from_numpy(hgt).cuda(), lr=1e-3)
+    net.device_status()
+    new = net.get_weights().cpu().numpy().astype(np.float64)
+    Pm = _split(blob, F, W, L)
+    lm, mg, _ = train_grad_bf16(Pm, o, w, F, dist_gt=dgt, hit_gt=hgt)
+    assert abs(loss.item() - lm) <= 1e-4 * max(1.0, abs(lm))
+    L64, _, _ = omlp.param_gradient(Pm, o, w, F, dgt, hgt)
+    print(f"loss: GPU {loss.item():.6f}  BF16 model {lm:.6f}  FP64 {L64:.6f}")
+    g = omlp.pack(mg)
+    w1, _, _ = omlp.adam_update(blob.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1,
+                                1e-3, 0.9, 0.999, 1e-8)
+    # step 1 moves each weight by ~lr * sign(g): compare where g is clear of the BF16 noise
+    big = np.abs(g) > 1e-3 * np.abs(g).max()
+    assert big.mean() > 0.05
+    agree = np.abs(new[big] - w1[big]) <= 2e-6
+    print(f"Adam step agrees with the BF16 model on {agree.mean():.5f} of {big.sum()} weights")
+    assert agree.mean() > 0.98
+    assert np.all(np.abs(new - blob) <= 1e-3 * 1.0001 + 1e-7)
+
+
+def test_tc_training_lowers_the_loss(P):
+    """Forty Adam steps on one batch of sphere-labelled rays: the BF16 path's loss falls like the
+    FP32 path's, and the trained BF16 network answers queries."""
+    F, W, L, seed = 12, 128, 4, 7
+    n = 8192
+    blob = init_weights(F, W, L, seed=seed)
+    o, w = rays_in_ball(n, seed=77)
+    dgt, hgt = _labels(o, w)
+    args = [torch.from_numpy(x).cuda() for x in (o, w, dgt, hgt)]
+    curves = {}
+    for prec in ("fp32", "bf16"):
+        net = P.DDFNet(F, W, L, blob, prec)
+        curves[prec] = [net.train_step(*args, lr=2e-3).item() for _ in range(40)]
+        net.device_status()
+    a, b = np.array(curves["fp32"]), np.array(curves["bf16"])
+    print("loss fp32:", a[[0, 9, 19, 39]], " bf16:", b[[0, 9, 19, 39]])
+    assert b[-1] < 0.7 * b[0]
+    assert abs(b[-1] - a[-1]) < 0.1 * a[0]
