@@ -12,12 +12,13 @@
 // One persistent kernel serves all four: per CTA a TMA producer warp, an MMA warp (one thread
 // issues M = 128, N = BN, K = 16 MMAs into one of two TMEM accumulators, so a tile's epilogue
 // overlaps the next tile's MMAs) and eight epilogue warps (two column halves x four TMEM lane
-// quadrants; thread = row). The epilogues write activations and deltas twice: row-major BF16
-// (the next GEMM's K-major A operand) and transposed (the wgrad operands, whose K is the batch),
-// the transpose going through a 32 x 32 block per warp in shared memory. ReLU masks are kept as
-// bits; bias gradients and the output layer's gradients are per-32-row partial sums taken from
-// the same transposed blocks and reduced in a fixed order afterwards, so a step is
-// bit-reproducible.
+// quadrants; thread = row). Activations and deltas are written once, row-major BF16: the next
+// forward / dgrad GEMM reads them K-major, and the wgrad reads the same arrays as MN-major
+// operands (its K is the batch), so no transposed copy is ever made. Epilogue stores go through
+// a swizzled 32 x 32 block per warp in shared memory so that each store instruction writes whole
+// sectors. ReLU masks are kept as bits; bias gradients and the output layer's gradients are
+// per-32-row partial sums taken in the same epilogues and reduced in a fixed order afterwards,
+// so a step is bit-reproducible.
 #include <math.h>
 
 #include <algorithm>
@@ -41,13 +42,12 @@ struct TArgs {
     int nkb, kb_per, ksplit;  // K-blocks (64 wide) in total and per split; number of splits
     int b_layer;              // third coordinate of B's tensor map
     int nst;                  // pipeline stages
-    int64_t ldt;              // row length (elements) of the transposed outputs
+    int mn_major;             // operands are MN-major (wgrad: A and B read from row-major [K][MN])
     int64_t m_valid;          // T_HEAD: rows below this are real
     uint32_t off_blk, off_bias, off_head, off_y, off_g, off_bar;
     const float* bias;        // [N]
     const float* head;        // W_out [2][N], b_out [2]
     __nv_bfloat16* out;       // [rows][N]
-    __nv_bfloat16* outT;      // [N][ldt]
     uint32_t* mask_out;       // [rows][N / 32]
     const uint32_t* mask_in;  // [rows][N / 32]
     float* colpart;           // [rows / 32][N]
@@ -102,18 +102,6 @@ __device__ __forceinline__ uint4 blk_read(const uint8_t* tb, int lane, int i) {
     return *reinterpret_cast<const uint4*>(tb + blk_off(8 * i + (lane >> 2), lane & 3));
 }
 
-__device__ __forceinline__ float sum8(const uint4 v) {
-    float s = bf_lo(v.x);
-    s += bf_hi(v.x);
-    s += bf_lo(v.y);
-    s += bf_hi(v.y);
-    s += bf_lo(v.z);
-    s += bf_hi(v.z);
-    s += bf_lo(v.w);
-    s += bf_hi(v.w);
-    return s;
-}
-
 // Sum over the four lanes of a line; every one of them gets the same value (fixed pairing).
 __device__ __forceinline__ float line_sum(float s) {
     s += __shfl_xor_sync(0xffffffffu, s, 1);
@@ -122,32 +110,49 @@ __device__ __forceinline__ float line_sum(float s) {
 }
 
 // Rows row0..row0+31 (lane = row) of columns col0..col0+31 to a row-major [.][ld] array.
+// colsum (nullable) gets each column's sum over the 32 rows of the BF16 values: every lane sums
+// its piece's 8 columns over its 4 rows, then the 8 lanes holding one piece combine in a fixed
+// butterfly.
 __device__ __forceinline__ void store_rows(uint8_t* tb, int lane, const uint32_t pk[16], __nv_bfloat16* out,
-                                           int64_t ld, int64_t row0, int col0) {
+                                           int64_t ld, int64_t row0, int col0, float* colsum) {
     stage_rows(tb, lane, pk);
+    float cs[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-        *reinterpret_cast<uint4*>(out + (row0 + 8 * i + (lane >> 2)) * ld + col0 + 8 * (lane & 3)) =
-            blk_read(tb, lane, i);
-    __syncwarp();
-}
-
-// The same block transposed into [col][ldt]; colsum (nullable) gets each column's sum over the
-// 32 rows of the BF16 values, in a fixed order.
-__device__ __forceinline__ void store_cols(uint8_t* tb, int lane, const uint32_t pk[16], __nv_bfloat16* outT,
-                                           int64_t ldt, int64_t row0, int col0, float* colsum) {
-    stage_cols(tb, lane, pk);
+    for (int e = 0; e < 8; ++e) cs[e] = 0.f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const uint4 v = blk_read(tb, lane, i);
-        const int line = 8 * i + (lane >> 2);
-        *reinterpret_cast<uint4*>(outT + (int64_t)(col0 + line) * ldt + row0 + 8 * (lane & 3)) = v;
+        *reinterpret_cast<uint4*>(out + (row0 + 8 * i + (lane >> 2)) * ld + col0 + 8 * (lane & 3)) = v;
         if (colsum) {
-            const float t = line_sum(sum8(v));
-            if ((lane & 3) == 0) colsum[col0 + line] = t;
+            cs[0] += bf_lo(v.x); cs[1] += bf_hi(v.x);
+            cs[2] += bf_lo(v.y); cs[3] += bf_hi(v.y);
+            cs[4] += bf_lo(v.z); cs[5] += bf_hi(v.z);
+            cs[6] += bf_lo(v.w); cs[7] += bf_hi(v.w);
+        }
+    }
+    if (colsum) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            float t = cs[e];
+            t += __shfl_xor_sync(0xffffffffu, t, 4);
+            t += __shfl_xor_sync(0xffffffffu, t, 8);
+            t += __shfl_xor_sync(0xffffffffu, t, 16);
+            cs[e] = t;
+        }
+        if (lane < 4) {
+            float4* dst = reinterpret_cast<float4*>(colsum + col0 + 8 * lane);
+            dst[0] = make_float4(cs[0], cs[1], cs[2], cs[3]);
+            dst[1] = make_float4(cs[4], cs[5], cs[6], cs[7]);
         }
     }
     __syncwarp();
+}
+
+// MN-major operand with 128-byte swizzle: rows of 64 MN elements (128 B), one row per K index;
+// 8-row K groups 1024 B apart (SBO), 64-wide MN atoms 8 KB apart (LBO: one 64 x 64 TMA box).
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(8192 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
 __global__ void __launch_bounds__(kTThreads, 1)
@@ -216,8 +221,16 @@ __global__ void __launch_bounds__(kTThreads, 1)
                     if (!mbar_wait(&empty[stg], ph ^ 1u, a.err)) { ok = false; break; }
                     uint8_t* sa = smem + (size_t)stg * stage_bytes;
                     mbar_expect_tx(&full[stg], stage_bytes);
-                    tma_load_3d(sa, &mapA, &full[stg], kb * 64, tm * 128, 0);
-                    tma_load_3d(sa + 16384, &mapB, &full[stg], kb * 64, tn * BN, a.b_layer);
+                    if (a.mn_major) {
+                        // 64 x 64 boxes of the row-major [K][MN] arrays, 8 KB apart
+                        for (int j = 0; j < 2; ++j)
+                            tma_load_3d(sa + j * 8192, &mapA, &full[stg], tm * 128 + 64 * j, kb * 64, 0);
+                        for (int j = 0; j < BN / 64; ++j)
+                            tma_load_3d(sa + 16384 + j * 8192, &mapB, &full[stg], tn * BN + 64 * j, kb * 64, 0);
+                    } else {
+                        tma_load_3d(sa, &mapA, &full[stg], kb * 64, tm * 128, 0);
+                        tma_load_3d(sa + 16384, &mapB, &full[stg], kb * 64, tn * BN, a.b_layer);
+                    }
                 }
             }
         }
@@ -226,7 +239,8 @@ __global__ void __launch_bounds__(kTThreads, 1)
         if (lane == 0) {
             uint32_t cnt = 0, tl = 0;
             bool ok = true;
-            const uint32_t idesc = idesc_bf16(128, BN);
+            // MN-major operands: bits 15 / 16 of the instruction descriptor
+            const uint32_t idesc = idesc_bf16(128, BN) | (a.mn_major ? (3u << 15) : 0u);
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
                 const int s = (int)(t / (ntm * ntn));
                 const int kb0 = s * a.kb_per, kb1 = min(a.nkb, kb0 + a.kb_per);
@@ -240,9 +254,17 @@ __global__ void __launch_bounds__(kTThreads, 1)
                     if (!mbar_wait(&full[stg], ph, a.err)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = su32(smem + (size_t)stg * stage_bytes);
-                    const uint64_t ad = sdesc(sa), bd = sdesc(sa + 16384u);
+                    if (a.mn_major) {
+                        // K step of 16 rows = two 1024-byte swizzle atoms
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, (kb > kb0 || k > 0));
+                        for (int k = 0; k < 4; ++k)
+                            mma_bf16(d, sdesc_mn(sa + 2048u * k), sdesc_mn(sa + 16384u + 2048u * k), idesc,
+                                     (kb > kb0 || k > 0));
+                    } else {
+                        const uint64_t ad = sdesc(sa), bd = sdesc(sa + 16384u);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, (kb > kb0 || k > 0));
+                    }
                     mma_commit(&empty[stg]);
                 }
                 if (ok) mma_commit(&accf[buf]);
@@ -304,8 +326,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
                             pk[j] = pack_bf16(x0, x1);
                         }
                     }
-                    store_rows(tb, lane, pk, a.out, N, wrow0, col0);
-                    store_cols(tb, lane, pk, a.outT, a.ldt, wrow0, col0,
+                    store_rows(tb, lane, pk, a.out, N, wrow0, col0,
                                a.mode == T_DGRAD ? a.colpart + rblk * N : nullptr);
                 }
                 if (a.mode == T_FWD) {
@@ -449,8 +470,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
                             (bits >> (2 * j + 1)) & 1u ? fmaf(gd, head_s[cj + 1], gl * head_s[N + cj + 1]) : 0.f;
                         pk[j] = pack_bf16(d0, d1);
                     }
-                    store_rows(tb, lane, pk, a.out, N, wrow0, col0);
-                    store_cols(tb, lane, pk, a.outT, a.ldt, wrow0, col0, a.colpart + rblk * N);
+                    store_rows(tb, lane, pk, a.out, N, wrow0, col0, a.colpart + rblk * N);
                 }
                 if (grp == 0 && lane < 2) {
                     float sg = 0.f;
@@ -477,10 +497,10 @@ __global__ void __launch_bounds__(kTThreads, 1)
 }
 
 // Rows of the batch encoded in the tensor-core feature order (six raw coordinates, two zero
-// columns, then per octave the sines and cosines), BF16, row-major [mp][K0] and transposed
-// [K0][mp]; rows m..mp-1 are zero.
+// columns, then per octave the sines and cosines), BF16, row-major [mp][K0]; rows m..mp-1 are
+// zero.
 __global__ void tenc_kernel(const float* __restrict__ o, const float* __restrict__ w, int64_t m, int64_t mp,
-                            int E, int K0, __nv_bfloat16* __restrict__ X, __nv_bfloat16* __restrict__ XT) {
+                            int E, int K0, __nv_bfloat16* __restrict__ X) {
     const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= mp) return;
     float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -499,8 +519,6 @@ __global__ void tenc_kernel(const float* __restrict__ o, const float* __restrict
                 f[h] = (real && src >= 0 && src < E) ? encode_feature(src, v) : 0.f;
             }
             pk[i] = pack_bf16(f[0], f[1]);
-            XT[(int64_t)(p0 + 2 * i) * mp + r] = __ushort_as_bfloat16((unsigned short)(pk[i] & 0xffffu));
-            XT[(int64_t)(p0 + 2 * i + 1) * mp + r] = __ushort_as_bfloat16((unsigned short)(pk[i] >> 16));
         }
         *reinterpret_cast<uint4*>(X + r * K0 + p0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     }
@@ -673,11 +691,9 @@ int launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, TArgs a, cudaStrea
 struct TcWs {
     int64_t m = 0, mp = 0;   // rows per chunk, padded to 128
     int ksplit_max = 0;
-    __nv_bfloat16* act[2];   // row-major activations [mp][max(K0, W)]
-    __nv_bfloat16* actT;     // a_l^T, l = 0..L-1: [K0][mp], then [W][mp] each
+    __nv_bfloat16* act;      // a_l, l = 0..L-1, row-major: [mp][K0], then [mp][W] each
     uint32_t* masks;         // ReLU masks of a_1..a_{L-1}: [mp][W / 32] each
     __nv_bfloat16* dl[2];    // deltas, row-major [mp][W]
-    __nv_bfloat16* dT;       // delta^T [W][mp]
     float* colpart;          // L x [mp / 32][W]
     float* headpart;         // [mp / 32][2W + 2]
     float* wpart;            // [ksplit][W][max(K0, W)]
@@ -693,14 +709,15 @@ struct TcWs {
 int ensure_tc_ws(ddf_net_s* net, int64_t n, TcWs& ws) {
     const NetLayout& lay = net->lay;
     const int W = lay.width, L = lay.L, K0 = net->tc->K0, KM = std::max(K0, W);
-    const int ntm = W / 128;
+    const int ntm = W / 128;   // wgrad M tiles
     ws.ksplit_max = std::max(1, num_sms() / ntm);
     // buffer sizes in bytes for chunks of mp rows, in carving order
     auto sizes = [&](size_t mp, size_t out[17]) {
-        out[0] = out[1] = mp * KM * 2;                                   // act[2]
-        out[2] = ((size_t)K0 + (size_t)(L - 1) * W) * mp * 2;            // actT
+        out[0] = ((size_t)K0 + (size_t)(L - 1) * W) * mp * 2;            // act
+        out[1] = out[2] = 0;
         out[3] = (size_t)(L - 1) * mp * W / 8 + 4;                       // masks
-        out[4] = out[5] = out[6] = mp * W * 2;                           // dl[2], dT
+        out[4] = out[5] = mp * W * 2;                                    // dl[2]
+        out[6] = 0;
         out[7] = (size_t)L * (mp / 32) * W * 4;                          // colpart
         out[8] = (mp / 32) * (2 * W + 2) * 4;                            // headpart
         out[9] = (size_t)ws.ksplit_max * W * KM * 4;                     // wpart
@@ -739,13 +756,10 @@ int ensure_tc_ws(ddf_net_s* net, int64_t n, TcWs& ws) {
         q[i] = p;
         p += (b[i] + 255) / 256 * 256;
     }
-    ws.act[0] = (__nv_bfloat16*)q[0];
-    ws.act[1] = (__nv_bfloat16*)q[1];
-    ws.actT = (__nv_bfloat16*)q[2];
+    ws.act = (__nv_bfloat16*)q[0];
     ws.masks = (uint32_t*)q[3];
     ws.dl[0] = (__nv_bfloat16*)q[4];
     ws.dl[1] = (__nv_bfloat16*)q[5];
-    ws.dT = (__nv_bfloat16*)q[6];
     ws.colpart = (float*)q[7];
     ws.headpart = (float*)q[8];
     ws.wpart = (float*)q[9];
@@ -778,19 +792,19 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
     TcPack* P = net->tc;
     const int W = lay.width, L = lay.L, K0 = P->K0;
     const int64_t mp = (m + 127) / 128 * 128, ld = ws.mp;
-    auto actT = [&](int l) { return ws.actT + (l == 0 ? 0 : ((int64_t)K0 + (int64_t)(l - 1) * W) * ld); };
+    auto act = [&](int l) { return ws.act + (l == 0 ? 0 : ((int64_t)K0 + (int64_t)(l - 1) * W) * ld); };
     auto masks = [&](int l) { return ws.masks + (int64_t)(l - 1) * ld * (W / 32); };
     auto colpart = [&](int l) { return ws.colpart + (int64_t)l * (ld / 32) * W; };
     int rc;
 
-    tenc_kernel<<<(unsigned)((mp + 127) / 128), 128, 0, s>>>(o, w, m, ld, lay.E, K0, ws.act[0], ws.actT);
+    tenc_kernel<<<(unsigned)((mp + 127) / 128), 128, 0, s>>>(o, w, m, mp, lay.E, K0, act(0));
     DDF_LAUNCH_CHECK();
 
     // ---------------------------------------------------------------- forward (+ head)
     for (int l = 0; l < L; ++l) {
         const int K = l == 0 ? K0 : W;
         CUtensorMap mA;
-        if ((rc = tmap(&mA, ws.act[l & 1], K, K, m, 1, 128))) return rc;
+        if ((rc = tmap(&mA, act(l), K, K, m, 1, 128))) return rc;
         TArgs a{};
         a.mode = l == L - 1 ? T_HEAD : T_FWD;
         a.M = (int)m;
@@ -800,18 +814,15 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
         a.kb_per = a.nkb;
         a.ksplit = 1;
         a.b_layer = l;
-        a.ldt = ld;
         a.m_valid = m;
         a.bias = P->bias + (int64_t)l * W;
         a.err = P->err;
         if (a.mode == T_FWD) {
-            a.out = ws.act[(l + 1) & 1];
-            a.outT = actT(l + 1);
+            a.out = act(l + 1);
             a.mask_out = masks(l + 1);
         } else {
             a.head = P->head;
             a.out = ws.dl[0];
-            a.outT = ws.dT;
             a.colpart = colpart(L - 1);
             a.headpart = ws.headpart;
             a.dist_gt = tg.dist_gt;
@@ -830,15 +841,16 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
     int cur = 0;
     for (int l = L - 1; l >= 0; --l) {
         const int K = l == 0 ? K0 : W;
-        {   // dW_l = delta_l^T a_l, split over the rows
+        {   // dW_l = delta_l^T a_l, split over the rows; both operands MN-major from row-major arrays
             CUtensorMap mA, mB;
-            if ((rc = tmap(&mA, ws.dT, m, ld, W, 1, 128))) return rc;
-            if ((rc = tmap(&mB, actT(l), m, ld, K, 1, K))) return rc;
+            if ((rc = tmap(&mA, ws.dl[cur], W, W, m, 1, 64))) return rc;
+            if ((rc = tmap(&mB, act(l), K, K, m, 1, 64))) return rc;
             const int nkb = (int)((m + 63) / 64);
             const int want = std::max(1, std::min(ws.ksplit_max, nkb));
             const int kb_per = (nkb + want - 1) / want;
             TArgs a{};
             a.mode = T_WGRAD;
+            a.mn_major = 1;
             a.M = W;
             a.N = K;
             a.BN = K;
@@ -851,8 +863,8 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
             if ((rc = launch_gemm(mA, mB, a, s))) return rc;
             const int64_t tot4 = (int64_t)W * K / 4;
             wsum_kernel<<<(unsigned)((tot4 + 31) / 32), dim3(32, 8), 0, s>>>((const float4*)ws.wpart, a.ksplit, W, K,
-                                                                     l == 0 ? lay.E : W, l == 0,
-                                                                     grad + lay.w_off[l]);
+                                                                            l == 0 ? lay.E : W, l == 0,
+                                                                            grad + lay.w_off[l]);
             DDF_LAUNCH_CHECK();
         }
         if (l > 0) {   // delta_{l-1} = (delta_l W_l) * 1[a_l > 0]
@@ -867,10 +879,8 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
             a.kb_per = a.nkb;
             a.ksplit = 1;
             a.b_layer = l;
-            a.ldt = ld;
             a.mask_in = masks(l);
             a.out = ws.dl[cur ^ 1];
-            a.outT = ws.dT;
             a.colpart = colpart(l - 1);
             a.err = P->err;
             if ((rc = launch_gemm(mA, P->map_bwd, a, s))) return rc;
