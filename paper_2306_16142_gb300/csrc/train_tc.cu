@@ -34,7 +34,7 @@ constexpr int kTEpi = 8;                       // epilogue warps
 constexpr int kTThreads = (kTEpi + 2) * 32;    // + TMA producer warp + MMA warp
 constexpr uint32_t kSmemMax = 232448;          // 227 KB of dynamic shared memory per CTA
 
-enum { T_FWD = 0, T_HEAD = 1, T_DGRAD = 2, T_WGRAD = 3, T_STORE = 4 };
+enum { T_FWD = 0, T_DGRAD = 2, T_WGRAD = 3, T_STORE = 4 };
 
 struct TArgs {
     int mode;
@@ -43,24 +43,14 @@ struct TArgs {
     int b_layer;              // third coordinate of B's tensor map
     int nst;                  // pipeline stages
     int mn_major;             // operands are MN-major (wgrad: A and B read from row-major [K][MN])
-    int64_t m_valid;          // T_HEAD: rows below this are real
-    uint32_t off_blk, off_bias, off_head, off_y, off_g, off_bar;
+    int bres;                 // B (the weights, N == BN) loaded once per CTA and kept in shared memory
+    uint32_t off_stage, off_blk, off_bias, off_bar;
     const float* bias;        // [N]
-    const float* head;        // W_out [2][N], b_out [2]
     __nv_bfloat16* out;       // [rows][N]
-    uint32_t* mask_out;       // [rows][N / 32]
+    uint32_t* mask_out;       // [rows][N / 32] (nullable)
     const uint32_t* mask_in;  // [rows][N / 32]
     float* colpart;           // [rows / 32][N]
-    float* headpart;          // [rows / 32][2N + 2]
     float* fout;              // T_WGRAD: [ksplit][M][N]; T_STORE: [rows][N]
-    const float* dist_gt;     // T_HEAD, loss form
-    const uint8_t* hit_gt;
-    const int* n_hit;
-    int64_t n_total;
-    const float* gd_in;       // T_HEAD, cotangent form
-    const float* gl_in;
-    float* row_l1;
-    float* row_bce;
     int* err;
 };
 
@@ -161,19 +151,18 @@ __global__ void __launch_bounds__(kTThreads, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int NST = a.nst, BN = a.BN, N = a.N;
-    const uint32_t stage_bytes = 16384u + (uint32_t)BN * 128u;
+    const uint32_t stage_bytes = 16384u + (a.bres ? 0u : (uint32_t)BN * 128u);
+    uint8_t* bres = smem;                    // resident B: K-block kb at kb * BN * 128
+    uint8_t* stages = smem + a.off_stage;
     uint8_t* blk = smem + a.off_blk;
     float* bias_s = reinterpret_cast<float*>(smem + a.off_bias);
-    float* head_s = reinterpret_cast<float*>(smem + a.off_head);
-    float* ypart = reinterpret_cast<float*>(smem + a.off_y);   // [2 parity][2 groups][128][2]
-    float* gst = reinterpret_cast<float*>(smem + a.off_g);     // [8 warps][32][2]
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
     uint64_t* full = bars;
     uint64_t* empty = bars + NST;
     uint64_t* accf = bars + 2 * NST;
     uint64_t* acce = accf + 2;
-    uint64_t* ybar = acce + 2;   // T_HEAD: both column halves' partial outputs written
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(ybar + 2);
+    uint64_t* bfull = acce + 2;  // resident B loaded
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bfull + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntm = (a.M + 127) / 128, ntn = N / BN;
@@ -189,8 +178,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
         mbar_init(&accf[1], 1);
         mbar_init(&acce[0], kTEpi * 32);
         mbar_init(&acce[1], kTEpi * 32);
-        mbar_init(&ybar[0], kTEpi * 32);
-        mbar_init(&ybar[1], kTEpi * 32);
+        mbar_init(bfull, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -198,13 +186,21 @@ __global__ void __launch_bounds__(kTThreads, 1)
                      "r"(tcols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (a.mode == T_FWD || a.mode == T_HEAD)
+    if (a.mode == T_FWD)
         for (int i = tid; i < N; i += kTThreads) bias_s[i] = a.bias[i];
-    if (a.mode == T_HEAD)
-        for (int i = tid; i < 2 * N + 2; i += kTThreads) head_s[i] = a.head[i];
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
+    // Launched as a programmatic dependent of the previous kernel in the stream: the set-up above
+    // (and the resident weights, which no kernel of the step writes) overlaps its tail; nothing
+    // it produced is read, and nothing it reads is written, before this wait.
+    if (a.bres && tid == kTEpi * 32) {
+        mbar_expect_tx(bfull, (uint32_t)a.nkb * (uint32_t)BN * 128u);
+        for (int kb = 0; kb < a.nkb; ++kb)
+            tma_load_3d(bres + (size_t)kb * BN * 128, &mapB, bfull, kb * 64, 0, a.b_layer);
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     if (warp == kTEpi) {
         // ---------------------------------------------------------------- TMA producer
@@ -219,9 +215,11 @@ __global__ void __launch_bounds__(kTThreads, 1)
                     const int stg = (int)(cnt % (uint32_t)NST);
                     const uint32_t ph = (cnt / (uint32_t)NST) & 1u;
                     if (!mbar_wait(&empty[stg], ph ^ 1u, a.err)) { ok = false; break; }
-                    uint8_t* sa = smem + (size_t)stg * stage_bytes;
+                    uint8_t* sa = stages + (size_t)stg * stage_bytes;
                     mbar_expect_tx(&full[stg], stage_bytes);
-                    if (a.mn_major) {
+                    if (a.bres) {
+                        tma_load_3d(sa, &mapA, &full[stg], kb * 64, tm * 128, 0);
+                    } else if (a.mn_major) {
                         // 64 x 64 boxes of the row-major [K][MN] arrays, 8 KB apart
                         for (int j = 0; j < 2; ++j)
                             tma_load_3d(sa + j * 8192, &mapA, &full[stg], tm * 128 + 64 * j, kb * 64, 0);
@@ -241,6 +239,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
             bool ok = true;
             // MN-major operands: bits 15 / 16 of the instruction descriptor
             const uint32_t idesc = idesc_bf16(128, BN) | (a.mn_major ? (3u << 15) : 0u);
+            if (a.bres && !mbar_wait(bfull, 0u, a.err)) ok = false;
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
                 const int s = (int)(t / (ntm * ntn));
                 const int kb0 = s * a.kb_per, kb1 = min(a.nkb, kb0 + a.kb_per);
@@ -253,8 +252,12 @@ __global__ void __launch_bounds__(kTThreads, 1)
                     const uint32_t ph = (cnt / (uint32_t)NST) & 1u;
                     if (!mbar_wait(&full[stg], ph, a.err)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t sa = su32(smem + (size_t)stg * stage_bytes);
-                    if (a.mn_major) {
+                    const uint32_t sa = su32(stages + (size_t)stg * stage_bytes);
+                    if (a.bres) {
+                        const uint64_t ad = sdesc(sa), bd = sdesc(su32(bres) + (uint32_t)kb * (uint32_t)BN * 128u);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, (kb > kb0 || k > 0));
+                    } else if (a.mn_major) {
                         // K step of 16 rows = two 1024-byte swizzle atoms
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
@@ -276,7 +279,6 @@ __global__ void __launch_bounds__(kTThreads, 1)
         const int r = q * 32 + lane;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         uint8_t* tb = blk + warp * 2048;
-        float* gw = gst + warp * 64;
         const int nhalf = BN / 64;             // 32-column chunks per column group (1..4)
         const int ch0 = grp * nhalf;
         const int NW = N / 32;
@@ -299,22 +301,23 @@ __global__ void __launch_bounds__(kTThreads, 1)
             const uint32_t tacc = tbase + lane_off + buf * (uint32_t)BN;
 
             if (a.mode == T_FWD || a.mode == T_DGRAD) {
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    if (cc >= nhalf) break;
-                    const int c = ch0 + cc;
-                    const int col0 = tn * BN + c * 32;
-                    uint32_t raw[32], pk[16];
-                    TC_LD32(tacc + c * 32, raw);
-                    tc_wait_ld();
+                // chunks in pairs: two TMEM loads behind one wait
+                auto chunk = [&](int cc, const uint32_t* raw) {
+                    const int col0 = tn * BN + (ch0 + cc) * 32;
+                    uint32_t pk[16];
                     if (a.mode == T_FWD) {
                         uint32_t bits = 0;
+                        const float4* b4 = reinterpret_cast<const float4*>(bias_s + col0);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const float x0 = __uint_as_float(raw[2 * j]) + bias_s[col0 + 2 * j];
-                            const float x1 = __uint_as_float(raw[2 * j + 1]) + bias_s[col0 + 2 * j + 1];
-                            bits |= (pos(x0) << (2 * j)) | (pos(x1) << (2 * j + 1));
-                            pk[j] = pack_relu(x0, x1);
+                        for (int j4 = 0; j4 < 8; ++j4) {
+                            const float4 b = b4[j4];
+                            float x0, x1, x2, x3;
+                            add2(__uint_as_float(raw[4 * j4]), __uint_as_float(raw[4 * j4 + 1]), b.x, b.y, x0, x1);
+                            add2(__uint_as_float(raw[4 * j4 + 2]), __uint_as_float(raw[4 * j4 + 3]), b.z, b.w, x2, x3);
+                            bits |= (pos(x0) << (4 * j4)) | (pos(x1) << (4 * j4 + 1)) | (pos(x2) << (4 * j4 + 2)) |
+                                    (pos(x3) << (4 * j4 + 3));
+                            pk[2 * j4] = pack_relu(x0, x1);
+                            pk[2 * j4 + 1] = pack_relu(x2, x3);
                         }
                         mwords[cc] = bits;
                     } else {
@@ -328,8 +331,18 @@ __global__ void __launch_bounds__(kTThreads, 1)
                     }
                     store_rows(tb, lane, pk, a.out, N, wrow0, col0,
                                a.mode == T_DGRAD ? a.colpart + rblk * N : nullptr);
+                };
+#pragma unroll
+                for (int cc = 0; cc < 4; cc += 2) {
+                    if (cc >= nhalf) break;
+                    uint32_t r0[32], r1[32];
+                    TC_LD32(tacc + (ch0 + cc) * 32, r0);
+                    if (cc + 1 < nhalf) TC_LD32(tacc + (ch0 + cc + 1) * 32, r1);
+                    tc_wait_ld();
+                    chunk(cc, r0);
+                    if (cc + 1 < nhalf) chunk(cc + 1, r1);
                 }
-                if (a.mode == T_FWD) {
+                if (a.mode == T_FWD && a.mask_out) {
                     uint32_t* mo = a.mask_out + row * NW + (tn * BN) / 32 + ch0;
                     if (nhalf == 4)
                         *reinterpret_cast<uint4*>(mo) = make_uint4(mwords[0], mwords[1], mwords[2], mwords[3]);
@@ -366,117 +379,6 @@ __global__ void __launch_bounds__(kTThreads, 1)
                         dst[i] = make_float4(__uint_as_float(raw[4 * i]), __uint_as_float(raw[4 * i + 1]),
                                              __uint_as_float(raw[4 * i + 2]), __uint_as_float(raw[4 * i + 3]));
                 }
-            } else {
-                // T_HEAD: pass 1, the two output units from this half of the row
-                uint32_t hbits[4] = {0u, 0u, 0u, 0u};
-                float y0 = 0.f, y1 = 0.f;
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    if (cc >= nhalf) break;
-                    const int c = ch0 + cc;
-                    uint32_t raw[32];
-                    TC_LD32(tacc + c * 32, raw);
-                    tc_wait_ld();
-                    uint32_t bits = 0;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = c * 32 + j;
-                        const float x = __uint_as_float(raw[j]) + bias_s[col];
-                        bits |= pos(x) << j;
-                        const float h = fmaxf(x, 0.f);
-                        y0 = fmaf(h, head_s[col], y0);
-                        y1 = fmaf(h, head_s[N + col], y1);
-                    }
-                    hbits[cc] = bits;
-                }
-                float* yp = ypart + (tl & 1u) * 512;
-                yp[(grp * 128 + r) * 2] = y0;
-                yp[(grp * 128 + r) * 2 + 1] = y1;
-                mbar_arrive(&ybar[tl & 1u]);
-                if (!mbar_wait(&ybar[tl & 1u], (tl >> 1) & 1u, a.err)) break;
-                const float d = (yp[r * 2] + yp[(128 + r) * 2]) + head_s[2 * N];
-                const float z = (yp[r * 2 + 1] + yp[(128 + r) * 2 + 1]) + head_s[2 * N + 1];
-                float gd = 0.f, gl = 0.f;
-                if (row < a.m_valid) {
-                    if (a.hit_gt) {
-                        const int nh = *a.n_hit;
-                        const float inv_h = nh > 0 ? 1.f / (float)nh : 0.f;
-                        const float inv_n = 1.f / (float)a.n_total;
-                        const bool hit = a.hit_gt[row] != 0;
-                        const float h = hit ? 1.f : 0.f;
-                        float l1 = 0.f;
-                        if (hit) {
-                            const float diff = d - a.dist_gt[row];
-                            l1 = fabsf(diff);
-                            gd = (diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f)) * inv_h;
-                        }
-                        const float sig = 1.f / (1.f + expf(-z));
-                        gl = (sig - h) * inv_n;
-                        if (grp == 0) {
-                            a.row_l1[row] = l1;
-                            a.row_bce[row] = fmaxf(z, 0.f) - z * h + log1pf(expf(-fabsf(z)));
-                        }
-                    } else {
-                        gd = a.gd_in ? a.gd_in[row] : 0.f;
-                        gl = a.gl_in ? a.gl_in[row] : 0.f;
-                    }
-                }
-                gw[2 * lane] = gd;
-                gw[2 * lane + 1] = gl;
-                __syncwarp();
-                float* hp = a.headpart + rblk * (2 * N + 2);
-                // pass 2: output-layer gradient partials and delta_{L-1}
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    if (cc >= nhalf) break;
-                    const int c = ch0 + cc;
-                    const int col0 = c * 32;
-                    uint32_t raw[32], pk[16];
-                    TC_LD32(tacc + c * 32, raw);
-                    tc_wait_ld();
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        pk[j] = pack_relu(__uint_as_float(raw[2 * j]) + bias_s[col0 + 2 * j],
-                                          __uint_as_float(raw[2 * j + 1]) + bias_s[col0 + 2 * j + 1]);
-                    stage_cols(tb, lane, pk);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const uint4 v = blk_read(tb, lane, i);   // column line, rows 8 p .. 8 p + 7
-                        const float* g8 = gw + 16 * (lane & 3);
-                        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
-                        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            s0 = fmaf(g8[4 * k], bf_lo(vv[k]), s0);
-                            s1 = fmaf(g8[4 * k + 1], bf_lo(vv[k]), s1);
-                            s0 = fmaf(g8[4 * k + 2], bf_hi(vv[k]), s0);
-                            s1 = fmaf(g8[4 * k + 3], bf_hi(vv[k]), s1);
-                        }
-                        s0 = line_sum(s0);
-                        s1 = line_sum(s1);
-                        const int line = 8 * i + (lane >> 2);
-                        if ((lane & 3) == 0) {
-                            hp[col0 + line] = s0;
-                            hp[N + col0 + line] = s1;
-                        }
-                    }
-                    __syncwarp();
-                    const uint32_t bits = hbits[cc];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int cj = col0 + 2 * j;
-                        const float d0 = (bits >> (2 * j)) & 1u ? fmaf(gd, head_s[cj], gl * head_s[N + cj]) : 0.f;
-                        const float d1 =
-                            (bits >> (2 * j + 1)) & 1u ? fmaf(gd, head_s[cj + 1], gl * head_s[N + cj + 1]) : 0.f;
-                        pk[j] = pack_bf16(d0, d1);
-                    }
-                    store_rows(tb, lane, pk, a.out, N, wrow0, col0, a.colpart + rblk * N);
-                }
-                if (grp == 0 && lane < 2) {
-                    float sg = 0.f;
-                    for (int i = 0; i < 32; ++i) sg += gw[2 * i + lane];
-                    hp[2 * N + lane] = sg;
-                }
             }
             tc_fence_before();
             mbar_arrive(&acce[buf]);
@@ -501,27 +403,44 @@ __global__ void __launch_bounds__(kTThreads, 1)
 // zero.
 __global__ void tenc_kernel(const float* __restrict__ o, const float* __restrict__ w, int64_t m, int64_t mp,
                             int E, int K0, __nv_bfloat16* __restrict__ X) {
+    // one thread per row. sin / cos of 2^k pi v for k >= 1 by the double-angle recurrence seeded
+    // by sincospi(v) (about 2^k ulp, far below the BF16 rounding that follows); exact for the
+    // v whose sin / cos are 0 or +-1
     const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= mp) return;
     float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const bool real = r < m;
-    if (real)
+    if (r < m)
         for (int j = 0; j < 3; ++j) {
             v[j] = o[3 * r + j];
             v[3 + j] = w[3 * r + j];
         }
-    for (int p0 = 0; p0 < K0; p0 += 8) {
-        uint32_t pk[4];
-        for (int i = 0; i < 4; ++i) {
-            float f[2];
-            for (int h = 0; h < 2; ++h) {
-                const int src = in_feature(p0 + 2 * i + h);
-                f[h] = (real && src >= 0 && src < E) ? encode_feature(src, v) : 0.f;
+    const int noct = (E - 6) / 12;
+    uint4* dst = reinterpret_cast<uint4*>(X + r * K0);
+    float sn[6], cs[6];
+    for (int j = 0; j < 6; ++j) sincospif(v[j], &sn[j], &cs[j]);
+    dst[0] = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), 0u);
+    int q = 1;   // next 16-byte chunk; octave k fills chunks 1 + 1.5 k .. (12 features)
+    uint32_t pend[6];
+    int np = 0;
+    for (int k = 0; k < noct; ++k) {
+        const float f[12] = {sn[0], sn[1], sn[2], sn[3], sn[4], sn[5], cs[0], cs[1], cs[2], cs[3], cs[4], cs[5]};
+        for (int i = 0; i < 6; ++i) {
+            pend[np++] = r < m ? pack_bf16(f[2 * i], f[2 * i + 1]) : 0u;
+            if (np == 4) {
+                dst[q++] = make_uint4(pend[0], pend[1], pend[2], pend[3]);
+                np = 0;
             }
-            pk[i] = pack_bf16(f[0], f[1]);
         }
-        *reinterpret_cast<uint4*>(X + r * K0 + p0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        for (int j = 0; j < 6; ++j) {
+            const float s2 = 2.f * sn[j] * cs[j];
+            const float c2 = (cs[j] - sn[j]) * (cs[j] + sn[j]);
+            sn[j] = s2;
+            cs[j] = c2;
+        }
     }
+    while (np != 0 && np < 4) pend[np++] = 0u;
+    if (np == 4) dst[q++] = make_uint4(pend[0], pend[1], pend[2], pend[3]);
+    for (; q < K0 / 8; ++q) dst[q] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // dW_l (blob layout, [W][in]) += the split-K partials summed in split order. Partials are in the
@@ -626,23 +545,181 @@ __global__ void tenc_backward_kernel(const float* __restrict__ o, const float* _
     for (int j = 0; j < 6; ++j) gin[6 * r + j] = g[j];
 }
 
+// The output layer on the stored last activation a_L (row-major BF16 [mp][W], Sec. 4.1's
+// two-output head): y = a_L W_out^T + b_out; the per-row loss terms and G = dLoss/dy (L1 on hit
+// rows + BCE with logits; or the caller's cotangents); delta_{L-1} = (G W_out) * 1[a_L > 0],
+// row-major BF16; and per-32-row partial sums of delta (db_{L-1}), of G a_L (dW_out) and of G
+// (db_out). One warp per 32 rows; lane l owns columns [CPL l, CPL l + CPL).
+struct HeadArgs {
+    const __nv_bfloat16* aL;
+    const float* head;        // W_out [2][W], b_out [2]
+    __nv_bfloat16* delta;     // [mp][W]
+    float* colpart;           // [mp / 32][W]
+    float* headpart;          // [mp / 32][2W + 2]
+    int64_t m, mp;
+    const float* dist_gt;     // loss form
+    const uint8_t* hit_gt;
+    const int* n_hit;
+    int64_t n_total;
+    float* row_l1;
+    float* row_bce;
+    const float* gd_in;       // cotangent form
+    const float* gl_in;
+};
+
+template <int W>
+__global__ void __launch_bounds__(128) head_kernel(const HeadArgs h) {
+    // half-warp per row, two rows per step: lane (hw = lane / 16, j = lane % 16) owns columns
+    // [CPL j, CPL j + CPL) of the rows 2 i + hw
+    constexpr int CPL = W / 16;
+    const int lane = threadIdx.x & 31, hw = lane >> 4, j = lane & 15;
+    const int64_t rblk = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (rblk * 32 >= h.mp) return;
+    float wo0[CPL], wo1[CPL], cd[CPL], cw0[CPL], cw1[CPL];
+#pragma unroll
+    for (int e = 0; e < CPL; ++e) {
+        wo0[e] = h.head[CPL * j + e];
+        wo1[e] = h.head[W + CPL * j + e];
+        cd[e] = cw0[e] = cw1[e] = 0.f;
+    }
+    const float bo0 = h.head[2 * W], bo1 = h.head[2 * W + 1];
+    float sg0 = 0.f, sg1 = 0.f;
+    float inv_h = 0.f, inv_n = 0.f;
+    // this block's 32 labels / cotangents, one per lane, fetched once (no load on the row loop's path)
+    const int64_t rl = rblk * 32 + lane;
+    float lab_a = 0.f, lab_b = 0.f;   // (dist_gt, hit) or (g_dist, g_logit)
+    if (h.hit_gt) {
+        const int nh = *h.n_hit;
+        inv_h = nh > 0 ? 1.f / (float)nh : 0.f;
+        inv_n = 1.f / (float)h.n_total;
+        if (rl < h.m) {
+            lab_b = h.hit_gt[rl] ? 1.f : 0.f;
+            lab_a = lab_b > 0.f ? h.dist_gt[rl] : 0.f;
+        }
+    } else if (rl < h.m) {
+        lab_a = h.gd_in ? h.gd_in[rl] : 0.f;
+        lab_b = h.gl_in ? h.gl_in[rl] : 0.f;
+    }
+    constexpr int AHEAD = 4;   // rows of this half-warp whose loads are in flight together
+    for (int i0 = 0; i0 < 16; i0 += AHEAD) {
+      uint4 raw[AHEAD][CPL / 8];
+#pragma unroll
+      for (int t = 0; t < AHEAD; ++t) {
+          const uint4* src = reinterpret_cast<const uint4*>(h.aL + (rblk * 32 + 2 * (i0 + t) + hw) * W + CPL * j);
+#pragma unroll
+          for (int q = 0; q < CPL / 8; ++q) raw[t][q] = src[q];
+      }
+#pragma unroll
+      for (int t = 0; t < AHEAD; ++t) {
+        const int i = i0 + t;
+        const int64_t row = rblk * 32 + 2 * i + hw;
+        float av[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL / 8; ++q) {
+            const uint4 u = raw[t][q];
+            const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                av[8 * q + 2 * k] = bf_lo(uu[k]);
+                av[8 * q + 2 * k + 1] = bf_hi(uu[k]);
+            }
+        }
+        float p0 = 0.f, p1 = 0.f;
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) {
+            p0 = fmaf(av[e], wo0[e], p0);
+            p1 = fmaf(av[e], wo1[e], p1);
+        }
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {   // fixed butterfly within the half-warp
+            p0 += __shfl_xor_sync(0xffffffffu, p0, o);
+            p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+        }
+        const float d = p0 + bo0, z = p1 + bo1;
+        const float la = __shfl_sync(0xffffffffu, lab_a, 2 * i + hw);
+        const float lb = __shfl_sync(0xffffffffu, lab_b, 2 * i + hw);
+        float gd = 0.f, gl = 0.f;
+        if (row < h.m) {
+            if (h.hit_gt) {
+                const bool hit = lb > 0.f;
+                float l1 = 0.f;
+                if (hit) {
+                    const float diff = d - la;
+                    l1 = fabsf(diff);
+                    gd = (diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f)) * inv_h;
+                }
+                gl = (1.f / (1.f + expf(-z)) - lb) * inv_n;
+                if (j == 0) {
+                    h.row_l1[row] = l1;
+                    h.row_bce[row] = fmaxf(z, 0.f) - z * lb + log1pf(expf(-fabsf(z)));
+                }
+            } else {
+                gd = la;
+                gl = lb;
+            }
+        }
+        uint32_t pk[CPL / 2];
+#pragma unroll
+        for (int k = 0; k < CPL / 2; ++k) {
+            const float d0 = av[2 * k] > 0.f ? fmaf(gd, wo0[2 * k], gl * wo1[2 * k]) : 0.f;
+            const float d1 = av[2 * k + 1] > 0.f ? fmaf(gd, wo0[2 * k + 1], gl * wo1[2 * k + 1]) : 0.f;
+            pk[k] = pack_bf16(d0, d1);
+            cd[2 * k] += bf_lo(pk[k]);
+            cd[2 * k + 1] += bf_hi(pk[k]);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(h.delta + row * W + CPL * j);
+#pragma unroll
+        for (int q = 0; q < CPL / 8; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) {
+            cw0[e] = fmaf(gd, av[e], cw0[e]);
+            cw1[e] = fmaf(gl, av[e], cw1[e]);
+        }
+        sg0 += gd;
+        sg1 += gl;
+      }
+    }
+    // the two half-warps' sums (even rows + odd rows), same value in both
+#pragma unroll
+    for (int e = 0; e < CPL; ++e) {
+        cd[e] += __shfl_xor_sync(0xffffffffu, cd[e], 16);
+        cw0[e] += __shfl_xor_sync(0xffffffffu, cw0[e], 16);
+        cw1[e] += __shfl_xor_sync(0xffffffffu, cw1[e], 16);
+    }
+    sg0 += __shfl_xor_sync(0xffffffffu, sg0, 16);
+    sg1 += __shfl_xor_sync(0xffffffffu, sg1, 16);
+    if (hw == 0) {
+        float* hp = h.headpart + rblk * (2 * W + 2);
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) {
+            h.colpart[rblk * W + CPL * j + e] = cd[e];
+            hp[CPL * j + e] = cw0[e];
+            hp[W + CPL * j + e] = cw1[e];
+        }
+        if (j == 0) {
+            hp[2 * W] = sg0;
+            hp[2 * W + 1] = sg1;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ host side
 struct TLayout {
-    uint32_t off_blk, off_bias, off_head, off_y, off_g, off_bar, total;
+    uint32_t off_stage, off_blk, off_bias, off_bar, total;
     int nst;
 };
 
-TLayout tlayout(int BN) {
+// Shared memory: [resident B][stage ring][epilogue blocks][bias][barriers].
+TLayout tlayout(int BN, uint32_t bres_bytes) {
     TLayout s;
-    const uint32_t stage = 16384u + (uint32_t)BN * 128u;
-    const uint32_t fixed = kTEpi * 2048 + 1024 + 2304 + 4096 + 2048 + 256;
-    s.nst = (int)std::min<uint32_t>(8u, (kSmemMax - 1024u - fixed) / stage);
-    uint32_t off = (uint32_t)s.nst * stage;
+    const uint32_t stage = 16384u + (bres_bytes ? 0u : (uint32_t)BN * 128u);
+    const uint32_t fixed = kTEpi * 2048 + 1024 + 256;
+    const uint32_t avail = kSmemMax - 1024u - fixed - bres_bytes;
+    s.nst = (int)std::min<uint32_t>(8u, avail / stage);
+    uint32_t off = bres_bytes;
+    s.off_stage = off; off += (uint32_t)s.nst * stage;
     s.off_blk = off;  off += kTEpi * 2048;
     s.off_bias = off; off += 1024;
-    s.off_head = off; off += 2304;
-    s.off_y = off;    off += 4096;
-    s.off_g = off;    off += 2048;
     s.off_bar = off;  off += 256;
     s.total = off + 1024;
     return s;
@@ -672,26 +749,36 @@ int launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, TArgs a, cudaStrea
         attr = true;
     }
     if (a.BN % 64 || a.BN > 256 || a.N % a.BN) return fail(DDF_ERR_UNSUPPORTED, "training GEMM tile N=%d", a.BN);
-    const TLayout L = tlayout(a.BN);
+    // weights as B (a single N tile): keep all of B in shared memory when it fits beside 2 A stages
+    const uint32_t bres_bytes = (uint32_t)a.nkb * (uint32_t)a.BN * 128u;
+    a.bres = (!a.mn_major && a.N == a.BN && a.ksplit == 1 && tlayout(a.BN, bres_bytes).nst >= 2) ? 1 : 0;
+    const TLayout L = tlayout(a.BN, a.bres ? bres_bytes : 0u);
     if (L.nst < 2 || L.total > kSmemMax) return fail(DDF_ERR_UNSUPPORTED, "training GEMM shared memory");
     a.nst = L.nst;
+    a.off_stage = L.off_stage;
     a.off_blk = L.off_blk;
     a.off_bias = L.off_bias;
-    a.off_head = L.off_head;
-    a.off_y = L.off_y;
-    a.off_g = L.off_g;
     a.off_bar = L.off_bar;
     const int64_t ntiles = (int64_t)((a.M + 127) / 128) * (a.N / a.BN) * a.ksplit;
     const int grid = (int)std::min<int64_t>(ntiles, num_sms());
-    train_gemm_kernel<<<grid, kTThreads, L.total, s>>>(mA, mB, a);
-    DDF_LAUNCH_CHECK();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kTThreads);
+    cfg.dynamicSmemBytes = L.total;
+    cfg.stream = s;
+    cudaLaunchAttribute attrs[1];
+    attrs[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attrs[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attrs;
+    cfg.numAttrs = 1;
+    DDF_CUDA_TRY(cudaLaunchKernelEx(&cfg, train_gemm_kernel, mA, mB, a));
     return DDF_OK;
 }
 
 struct TcWs {
     int64_t m = 0, mp = 0;   // rows per chunk, padded to 128
     int ksplit_max = 0;
-    __nv_bfloat16* act;      // a_l, l = 0..L-1, row-major: [mp][K0], then [mp][W] each
+    __nv_bfloat16* act;      // a_l, l = 0..L, row-major: [mp][K0], then [mp][W] each
     uint32_t* masks;         // ReLU masks of a_1..a_{L-1}: [mp][W / 32] each
     __nv_bfloat16* dl[2];    // deltas, row-major [mp][W]
     float* colpart;          // L x [mp / 32][W]
@@ -713,7 +800,7 @@ int ensure_tc_ws(ddf_net_s* net, int64_t n, TcWs& ws) {
     ws.ksplit_max = std::max(1, num_sms() / ntm);
     // buffer sizes in bytes for chunks of mp rows, in carving order
     auto sizes = [&](size_t mp, size_t out[17]) {
-        out[0] = ((size_t)K0 + (size_t)(L - 1) * W) * mp * 2;            // act
+        out[0] = ((size_t)K0 + (size_t)L * W) * mp * 2;                  // act (a_0 .. a_L)
         out[1] = out[2] = 0;
         out[3] = (size_t)(L - 1) * mp * W / 8 + 4;                       // masks
         out[4] = out[5] = mp * W * 2;                                    // dl[2]
@@ -800,13 +887,13 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
     tenc_kernel<<<(unsigned)((mp + 127) / 128), 128, 0, s>>>(o, w, m, mp, lay.E, K0, act(0));
     DDF_LAUNCH_CHECK();
 
-    // ---------------------------------------------------------------- forward (+ head)
+    // ---------------------------------------------------------------- forward
     for (int l = 0; l < L; ++l) {
         const int K = l == 0 ? K0 : W;
         CUtensorMap mA;
         if ((rc = tmap(&mA, act(l), K, K, m, 1, 128))) return rc;
         TArgs a{};
-        a.mode = l == L - 1 ? T_HEAD : T_FWD;
+        a.mode = T_FWD;
         a.M = (int)m;
         a.N = W;
         a.BN = W;
@@ -814,27 +901,35 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
         a.kb_per = a.nkb;
         a.ksplit = 1;
         a.b_layer = l;
-        a.m_valid = m;
         a.bias = P->bias + (int64_t)l * W;
         a.err = P->err;
-        if (a.mode == T_FWD) {
-            a.out = act(l + 1);
-            a.mask_out = masks(l + 1);
-        } else {
-            a.head = P->head;
-            a.out = ws.dl[0];
-            a.colpart = colpart(L - 1);
-            a.headpart = ws.headpart;
-            a.dist_gt = tg.dist_gt;
-            a.hit_gt = tg.hit_gt;
-            a.n_hit = tg.n_hit;
-            a.n_total = tg.n_total;
-            a.row_l1 = tg.row_l1;
-            a.row_bce = tg.row_bce;
-            a.gd_in = tg.gd;
-            a.gl_in = tg.gl;
-        }
+        a.out = act(l + 1);
+        a.mask_out = l + 1 < L ? masks(l + 1) : nullptr;
         if ((rc = launch_gemm(mA, P->map_fwd, a, s))) return rc;
+    }
+    {   // output layer, loss and delta_{L-1}
+        HeadArgs h{};
+        h.aL = act(L);
+        h.head = P->head;
+        h.delta = ws.dl[0];
+        h.colpart = colpart(L - 1);
+        h.headpart = ws.headpart;
+        h.m = m;
+        h.mp = mp;
+        h.dist_gt = tg.dist_gt;
+        h.hit_gt = tg.hit_gt;
+        h.n_hit = tg.n_hit;
+        h.n_total = tg.n_total;
+        h.row_l1 = tg.row_l1;
+        h.row_bce = tg.row_bce;
+        h.gd_in = tg.gd;
+        h.gl_in = tg.gl;
+        const unsigned grid = (unsigned)((mp / 32 + 3) / 4);
+        if (W == 256)
+            head_kernel<256><<<grid, 128, 0, s>>>(h);
+        else
+            head_kernel<128><<<grid, 128, 0, s>>>(h);
+        DDF_LAUNCH_CHECK();
     }
 
     // ---------------------------------------------------------------- reverse

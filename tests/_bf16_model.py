@@ -46,9 +46,10 @@ def query_bf16(params, o, w, in_freqs):
 
 def train_grad_bf16(params, o, w, in_freqs, gy=None, dist_gt=None, hit_gt=None, snap=False):
     """The reverse pass of the tensor-core training path with its BF16 rounding points: the
-    encoded input, the weights and every hidden activation that feeds a GEMM, every delta;
-    the head (y and G) and the output-layer delta product in full precision, dW_out from the
-    BF16-rounded last activation. Returns (loss or None, [(dW, db)], d/d(o, w) (n, 6)).
+    encoded input, the hidden-layer weights, every hidden activation (the last one included:
+    the output head reads it from memory), every delta; the output weights, y, G and the
+    output-layer delta product in full precision. Returns (loss or None, [(dW, db)],
+    d/d(o, w) (n, 6)).
 
     snap: round the encoded features to multiples of 2^-20, for inputs whose features are
     exactly 0 or +-1 (sin(k pi) evaluates to ~1e-16 in floating point, sinpi to exactly 0)."""
@@ -67,12 +68,13 @@ def train_grad_bf16(params, o, w, in_freqs, gy=None, dist_gt=None, hit_gt=None, 
             a = bf16(a)
             acts.append(a)
     Wo, bo = params[L]
-    y = a @ Wo.T + bo
+    aL = bf16(a)
+    y = aL @ Wo.T + bo
     loss = None
     if gy is None:
         loss, gy = omlp.loss_and_output_grad(y, dist_gt, hit_gt)
     grads = [None] * (L + 1)
-    grads[L] = (gy.T @ bf16(a), gy.sum(0))
+    grads[L] = (gy.T @ aL, gy.sum(0))
     d = bf16((gy @ Wo) * masks[L - 1])
     for l in range(L - 1, -1, -1):
         grads[l] = (d.T @ acts[l], d.sum(0))
