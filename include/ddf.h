@@ -51,6 +51,7 @@ extern "C" {
 #define DDF_ERR_UNSUPPORTED (-4) /* shape / precision combination not built into the library */
 #define DDF_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up                      */
 #define DDF_ERR_NUMERIC (-6)     /* a non-finite value where a finite one is required       */
+#define DDF_ERR_IO (-7)          /* a checkpoint file could not be opened, read or written   */
 
 /* ---- precisions of the hidden-layer GEMMs ---------------------------------------------- */
 #define DDF_FP32 0 /* FP32 SIMT FMA, FP32 accumulate (the reference GPU path)               */
@@ -276,6 +277,23 @@ DDF_API int ddf_backward(ddf_net net, const float* d_origins, const float* d_dir
 DDF_API int ddf_train_step(ddf_net net, const float* d_origins, const float* d_dirs,
                    const float* d_dist_gt, const uint8_t* d_hit_gt, int64_t n,
                    const ddf_adam* opt, float* d_loss, cudaStream_t stream);
+
+/* The forward pass of a training step (Sec. 5.1): d_dist and d_logit (device, n floats each) of
+ * the rays, in the handle's precision: the same arithmetic as ddf_query. No context is kept:
+ * ddf_backward recomputes the activations it needs from (o, w), chunk by chunk, so this call,
+ * ddf_backward and ddf_train_step can be issued in any order on the same handle. */
+DDF_API int ddf_forward_train(ddf_net net, const float* d_origins, const float* d_dirs, int64_t n,
+                      float* d_dist, float* d_logit, cudaStream_t stream);
+
+/* Checkpoint / resume (no counterpart in the paper; the training state of Sec. 5.1 made
+ * persistent). ddf_save writes the architecture, the precision, the FP32 master weights and the
+ * Adam state (moments and step count) to `path` (host file, little-endian, overwritten);
+ * synchronises the device. ddf_load creates a new handle from such a file on the current
+ * device, with the same precision, weights and Adam state, so ddf_train_step continues
+ * bit-identically. DDF_ERR_IO on a file error or a file that is not a checkpoint;
+ * DDF_ERR_UNSUPPORTED for the analytic sphere handle. */
+DDF_API int ddf_save(ddf_net net, const char* path);
+DDF_API int ddf_load(const char* path, ddf_net* out);
 
 /* Cap, in bytes, of the activation workspace used by ddf_backward / ddf_train_step
  * (default 1 GiB). Smaller caps process the batch in more row chunks (recomputation). */

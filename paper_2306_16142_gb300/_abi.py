@@ -17,10 +17,11 @@ DDF_ERR_OOM = -3
 DDF_ERR_UNSUPPORTED = -4
 DDF_ERR_TIMEOUT = -5
 DDF_ERR_NUMERIC = -6
+DDF_ERR_IO = -7
 DDF_FP32, DDF_BF16, DDF_FP8 = 0, 1, 2
 
 ERR_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "UNSUPPORTED", -5: "TIMEOUT",
-             -6: "NUMERIC"}
+             -6: "NUMERIC", -7: "IO"}
 
 
 class DDFError(RuntimeError):
@@ -79,6 +80,9 @@ _SIG = {
     "ddf_backward": (C.c_int, [_P, _P, _P, _I64, _P, _P, _P, _P, _P]),
     "ddf_train_step": (C.c_int, [_P, _P, _P, _P, _P, _I64, C.POINTER(ddf_adam), _P, _P]),
     "ddf_set_workspace_limit": (C.c_int, [_P, C.c_size_t]),
+    "ddf_forward_train": (C.c_int, [_P, _P, _P, _I64, _P, _P, _P]),
+    "ddf_save": (C.c_int, [_P, C.c_char_p]),
+    "ddf_load": (C.c_int, [C.c_char_p, C.POINTER(_P)]),
 }
 
 _lib = None

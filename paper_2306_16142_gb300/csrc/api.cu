@@ -2,6 +2,8 @@
 #include <stdarg.h>
 #include <string.h>
 
+#include <vector>
+
 #include <mutex>
 
 #include "ddf_internal.cuh"
@@ -381,6 +383,104 @@ int ddf_train_step(ddf_net net, const float* d_origins, const float* d_dirs,
         !(opt->beta2 >= 0.f && opt->beta2 < 1.f) || !(opt->eps > 0.f))
         return fail(DDF_ERR_INVALID_ARG, "bad Adam hyper-parameters");
     return train_step(net, d_origins, d_dirs, d_dist_gt, d_hit_gt, n, opt, d_loss, stream);
+}
+
+int ddf_forward_train(ddf_net net, const float* d_origins, const float* d_dirs, int64_t n,
+                      float* d_dist, float* d_logit, cudaStream_t stream) {
+    if (!net || net->is_sphere) return fail(DDF_ERR_INVALID_ARG, "net is NULL or not a network");
+    if (n < 0) return fail(DDF_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return DDF_OK;
+    if (!d_origins || !d_dirs || !d_dist || !d_logit)
+        return fail(DDF_ERR_INVALID_ARG, "origins, dirs, dist and logit must be non-NULL");
+    return field_query(net, d_origins, d_dirs, n, nullptr, d_dist, d_logit, nullptr, nullptr, stream);
+}
+
+// Checkpoint layout: 64-byte header, then the FP32 masters and (when has_adam) the two Adam
+// moments, n_params floats each.
+namespace {
+struct CkptHeader {
+    char magic[8];           // "DDFCKPT1"
+    int32_t in_freqs, width, hidden_layers, precision;
+    int64_t n_params;
+    int64_t adam_step;
+    int32_t has_adam;
+    int32_t reserved[5];
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
+const char kMagic[8] = {'D', 'D', 'F', 'C', 'K', 'P', 'T', '1'};
+}  // namespace
+
+int ddf_save(ddf_net net, const char* path) {
+    if (!net || !path) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    if (net->is_sphere) return fail(DDF_ERR_UNSUPPORTED, "the analytic sphere has no weights to save");
+    const int64_t P = net->lay.n_params;
+    CkptHeader h{};
+    memcpy(h.magic, kMagic, 8);
+    h.in_freqs = net->lay.in_freqs;
+    h.width = net->lay.width;
+    h.hidden_layers = net->lay.L;
+    h.precision = net->precision;
+    h.n_params = P;
+    h.adam_step = net->adam_step;
+    h.has_adam = net->adam_m ? 1 : 0;
+    std::vector<float> buf((size_t)P * (h.has_adam ? 3 : 1));
+    DDF_CUDA_TRY(cudaDeviceSynchronize());
+    DDF_CUDA_TRY(cudaMemcpy(buf.data(), net->master, sizeof(float) * P, cudaMemcpyDeviceToHost));
+    if (h.has_adam) {
+        DDF_CUDA_TRY(cudaMemcpy(buf.data() + P, net->adam_m, sizeof(float) * P, cudaMemcpyDeviceToHost));
+        DDF_CUDA_TRY(cudaMemcpy(buf.data() + 2 * P, net->adam_v, sizeof(float) * P, cudaMemcpyDeviceToHost));
+    }
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(DDF_ERR_IO, "cannot open %s for writing", path);
+    const bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    const bool closed = fclose(f) == 0;
+    if (!ok || !closed) return fail(DDF_ERR_IO, "short write to %s", path);
+    return DDF_OK;
+}
+
+int ddf_load(const char* path, ddf_net* out) {
+    if (!path || !out) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(DDF_ERR_IO, "cannot open %s", path);
+    CkptHeader h{};
+    if (fread(&h, sizeof h, 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0) {
+        fclose(f);
+        return fail(DDF_ERR_IO, "%s is not a DDF checkpoint", path);
+    }
+    ddf_arch arch{h.in_freqs, h.width, h.hidden_layers, h.precision};
+    int rc = check_arch(&arch);
+    if (rc) {
+        fclose(f);
+        return fail(DDF_ERR_IO, "%s: bad architecture in header", path);
+    }
+    const NetLayout lay = make_layout(h.in_freqs, h.width, h.hidden_layers);
+    if (h.n_params != lay.n_params || h.has_adam < 0 || h.has_adam > 1 || h.adam_step < 0) {
+        fclose(f);
+        return fail(DDF_ERR_IO, "%s: header does not match its architecture", path);
+    }
+    const int64_t P = lay.n_params;
+    std::vector<float> buf((size_t)P * (h.has_adam ? 3 : 1));
+    const bool ok = fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    fclose(f);
+    if (!ok) return fail(DDF_ERR_IO, "%s is truncated", path);
+    ddf_net n = nullptr;
+    rc = ddf_create(&arch, buf.data(), sizeof(float) * (size_t)P, &n);
+    if (rc) return rc;
+    if (h.has_adam) {
+        cudaError_t e = cudaMalloc(&n->adam_m, sizeof(float) * P);
+        if (e == cudaSuccess) e = cudaMalloc(&n->adam_v, sizeof(float) * P);
+        if (e == cudaSuccess) e = cudaMemcpy(n->adam_m, buf.data() + P, sizeof(float) * P, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(n->adam_v, buf.data() + 2 * P, sizeof(float) * P, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            ddf_destroy(n);
+            return fail(e == cudaErrorMemoryAllocation ? DDF_ERR_OOM : DDF_ERR_CUDA, "restoring Adam state: %s",
+                        cudaGetErrorString(e));
+        }
+    }
+    n->adam_step = h.adam_step;
+    *out = n;
+    return DDF_OK;
 }
 
 int ddf_set_workspace_limit(ddf_net net, size_t bytes) {

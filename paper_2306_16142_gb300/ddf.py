@@ -61,6 +61,23 @@ class DDFNet:
         obj.n_params = 0
         return obj
 
+    @classmethod
+    def load(cls, path: str):
+        """A new handle from a checkpoint written by save() (weights, precision, Adam state)."""
+        obj = cls.__new__(cls)
+        h = C.c_void_p()
+        check("ddf_load", _abi.load().ddf_load(str(path).encode(), C.byref(h)))
+        obj.h = h
+        n = C.c_int64()
+        check("ddf_num_params", _abi.load().ddf_num_params(h, C.byref(n)))
+        obj.n_params = n.value
+        obj.arch = None
+        obj.precision = None
+        return obj
+
+    def save(self, path: str):
+        check("ddf_save", _abi.load().ddf_save(self.h, str(path).encode()))
+
     def close(self):
         if getattr(self, "h", None):
             _abi.load().ddf_destroy(self.h)
@@ -122,6 +139,15 @@ class DDFNet:
         check("ddf_get_weights", _abi.load().ddf_get_weights(self.h, _ptr(out), out.numel() * 4, _stream()))
         return out
 
+    def forward_train(self, o, w):
+        """(dist, logit) of the training forward pass."""
+        n = _rays(o, w)
+        dist = torch.empty(n, device=o.device)
+        logit = torch.empty(n, device=o.device)
+        check("ddf_forward_train", _abi.load().ddf_forward_train(self.h, _ptr(o), _ptr(w), n, _ptr(dist),
+                                                                 _ptr(logit), _stream()))
+        return dist, logit
+
     def backward(self, o, w, gdist, glogit, need_input: bool = False):
         n = _rays(o, w)
         gw = torch.empty(self.n_params, device=o.device)
@@ -156,6 +182,23 @@ class DDFMesh:
                                                              C.byref(h)))
         self.h = h
         self.nt = t.shape[0]
+
+    @classmethod
+    def load(cls, path: str):
+        """A new handle from a checkpoint written by save() (weights, precision, Adam state)."""
+        obj = cls.__new__(cls)
+        h = C.c_void_p()
+        check("ddf_load", _abi.load().ddf_load(str(path).encode(), C.byref(h)))
+        obj.h = h
+        n = C.c_int64()
+        check("ddf_num_params", _abi.load().ddf_num_params(h, C.byref(n)))
+        obj.n_params = n.value
+        obj.arch = None
+        obj.precision = None
+        return obj
+
+    def save(self, path: str):
+        check("ddf_save", _abi.load().ddf_save(self.h, str(path).encode()))
 
     def close(self):
         if getattr(self, "h", None):
@@ -208,6 +251,23 @@ class DDFGroup:
         h = C.c_void_p()
         check("ddf_group_create", _abi.load().ddf_group_create(len(self.nets), arr, C.byref(h)))
         self.h = h
+
+    @classmethod
+    def load(cls, path: str):
+        """A new handle from a checkpoint written by save() (weights, precision, Adam state)."""
+        obj = cls.__new__(cls)
+        h = C.c_void_p()
+        check("ddf_load", _abi.load().ddf_load(str(path).encode(), C.byref(h)))
+        obj.h = h
+        n = C.c_int64()
+        check("ddf_num_params", _abi.load().ddf_num_params(h, C.byref(n)))
+        obj.n_params = n.value
+        obj.arch = None
+        obj.precision = None
+        return obj
+
+    def save(self, path: str):
+        check("ddf_save", _abi.load().ddf_save(self.h, str(path).encode()))
 
     def close(self):
         if getattr(self, "h", None):
