@@ -48,6 +48,11 @@ def bwd_flops(E, W, L):
     return 2.0 * ((L - 1) * W * W + W * E)
 
 
+# ncu-measured DRAM traffic of the BF16 query kernels (mlp_tc_kernel<256,0/1>, the 7 launches of
+# one 512 x 512 x 64 spp render); to be re-measured whenever the kernel changes.
+QUERY_DRAM_BYTES_PER_RENDER = 756.1e6
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -193,6 +198,8 @@ def main():
     ap.add_argument("--no-rows", action="store_true", help="skip the labelling / training / grouped rows")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: 512 x 512 x 8 spp (2^21 paths) for profiler captures")
+    ap.add_argument("--row", default=None, choices=["label", "train", "grouped", "w512"],
+                    help="run only this row's workload (for profiler captures) and print it")
     args = ap.parse_args()
     if args.size == "small":
         WORKLOAD["spp"] = 8
@@ -210,6 +217,9 @@ def main():
     import paper_2306_16142_gb300 as P
     from ddf_synth import default_camera, init_weights
     from paper_2306_16142_gb300.ddf import camera_struct
+    if args.row:
+        print(json.dumps({"rows": other_rows(P, torch, np, load_peaks()[0], only=args.row)}), flush=True)
+        return 0
 
     w = WORKLOAD
     E = 6 + 6 * w["in_freqs"]
@@ -286,6 +296,12 @@ def main():
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": f"{peak_src} bf16 sustained" + (" x 2 (fp8 nominal ratio)" if prec == "fp8" else "")}
+        if prec == "bf16" and args.size == "full":
+            # DRAM bytes (read + write) of the query kernels of one bench render, measured by ncu
+            # (dram__bytes_read.sum + dram__bytes_write.sum, one pass, full size; summary in
+            # profiles/bf16_query_render512x512.md), per bounce query like `achieved`
+            roof["traffic"] = QUERY_DRAM_BYTES_PER_RENDER / w["bounces"]
+            roof["traffic_unit"] = "bytes per bounce query (forward + normals launches)"
     roof["kernel"] = "field query (fused MLP + Eq. 3 normal)"
     roof["time_share"] = q["ms"] / ms if ms > 0 else None
 
@@ -398,113 +414,125 @@ def _time(torch, fn, reps, stream=None):
     return e0.elapsed_time(e1) / reps / 1e3
 
 
-def other_rows(P, torch, np, peaks):
+def other_rows(P, torch, np, peaks, only=None):
     """The other hot-path rows on their own workloads: ray labelling (2^20 training rays x 8,192-
-    triangle knot), the training step (batch 65,536, 78 -> 256 x 8 -> 2; BF16 tensor-core and FP32) and the grouped
-    16-object BF16 query replayed from a CUDA graph (ray counts log-uniform on [1e3, 1e6])."""
-    from ddf_synth import init_weights, labelled_ray_set, torus_knot
+    triangle knot), the training step (batch 65,536, 78 -> 256 x 8 -> 2; BF16 tensor-core and FP32),
+    the grouped 16-object BF16 query replayed from a CUDA graph (ray counts log-uniform on
+    [1e3, 1e6]), the width-512 query and one wave of the large render. only: one of
+    label / train / grouped / w512 (the others are skipped)."""
+    from ddf_synth import default_camera, init_weights, labelled_ray_set, torus_knot
     rows = {}
-    # ---- a8 labelling
+    want = lambda name: only is None or only == name
     V, F = torus_knot(3, 2, 0.08, 256, 16)
-    o, w = labelled_ray_set(V, F, 1 << 20, seed=11)
     mesh = P.DDFMesh(V, F)
-    to, tw = torch.from_numpy(o).cuda(), torch.from_numpy(w).cuda()
-    out = mesh.label(to, tw)
-    sec = _time(torch, lambda: mesh.label(to, tw, out), 5)
-    st = mesh.stats()
-    tests = o.shape[0] * F.shape[0]
-    alu_peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6      # FP32 lane-instructions / s
-    rows["label"] = {"workload": "2^20 rays (half uniform, half surface-aimed, sigma 0.05 rad) x 8,192-triangle (3,2) knot",
-                     "rays_per_s": o.shape[0] / sec, "tests_per_s": tests / sec, "ms": sec * 1e3,
-                     "fp64_retests_per_ray": st["retests"] / o.shape[0], "fp64_final_evals": st["finals"],
-                     "roofline": {"bound": "alu", "achieved": tests / sec * 34 / 1e12,
-                                  "peak": alu_peak / 1e12, "unit": "T FP32-instr/s",
-                                  "frac": tests / sec * 34 / alu_peak,
-                                  "note": "34 FP32 instructions per filter test (count of the hot loop)"},
-                     "hbm_gbs": (o.shape[0] * 33) / sec / 1e9}
+    if want("label") or want("train"):
+        o, w = labelled_ray_set(V, F, 1 << 20, seed=11)
+        to, tw = torch.from_numpy(o).cuda(), torch.from_numpy(w).cuda()
+    # ---- a8 labelling
+    if want("label"):
+        out = mesh.label(to, tw)
+        sec = _time(torch, lambda: mesh.label(to, tw, out), 5)
+        st = mesh.stats()
+        tests = o.shape[0] * F.shape[0]
+        alu_peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6      # FP32 lane-instructions / s
+        rows["label"] = {"workload": "2^20 rays (half uniform, half surface-aimed, sigma 0.05 rad) x 8,192-triangle "
+                                     "(3,2) knot",
+                         "rays_per_s": o.shape[0] / sec, "tests_per_s": tests / sec, "ms": sec * 1e3,
+                         "fp64_retests_per_ray": st["retests"] / o.shape[0], "fp64_final_evals": st["finals"],
+                         "roofline": {"bound": "alu", "achieved": tests / sec * 34 / 1e12,
+                                      "peak": alu_peak / 1e12, "unit": "T FP32-instr/s",
+                                      "frac": tests / sec * 34 / alu_peak,
+                                      "note": "34 FP32 instructions per filter test (count of the hot loop)"},
+                         "hbm_gbs": (o.shape[0] * 33) / sec / 1e9}
     # ---- a9 training step: BF16 tensor-core GEMMs (FP32 accumulate, FP32 masters), and the FP32 path
-    Fq, Wd, Ld = 12, 256, 8
-    n = 65536
-    lab = mesh.label(to[:n].contiguous(), tw[:n].contiguous())
-    dgt, hgt = lab["dist"].clone(), lab["hit"].clone()
-    tsub, wsub = to[:n].contiguous(), tw[:n].contiguous()
-    loss = torch.empty((), device="cuda")
-    E = 6 + 6 * Fq
-    macs = E * Wd + (Ld - 1) * Wd * Wd + 2 * Wd
-    for prec in ("bf16", "fp32"):
-        net = P.DDFNet(Fq, Wd, Ld, init_weights(Fq, Wd, Ld, seed=2), prec)
-        sec = _time(torch, lambda: net.train_step(tsub, wsub, dgt, hgt, lr=1e-4, loss=loss), 10 if prec == "bf16" else 3)
-        net.device_status()
-        if prec == "bf16":
-            flop = 2.0 * macs * n * 3     # forward, dgrad, wgrad (activations kept, no recompute)
-            peak = peaks["bf16_tflops_sustained"]
-            rows["train_step"] = {"workload": "batch 65,536 labelled rays, 78 -> 256 x 8 -> 2, L1 + BCE, Adam; "
-                                              "BF16 tcgen05 GEMMs, FP32 accumulate and masters",
-                                  "ms": sec * 1e3, "samples_per_s": n / sec, "loss": float(loss.item()),
-                                  "roofline": {"bound": "tensor", "achieved": flop / sec / 1e12, "peak": peak,
-                                               "unit": "TFLOP/s", "frac": flop / sec / 1e12 / peak}}
-        else:
-            flop = 2.0 * macs * n * 4     # forward, recomputed forward, dgrad, wgrad
-            fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
-            rows["train_step_fp32"] = {"workload": "the same step on the FP32 SIMT GEMMs",
-                                       "ms": sec * 1e3, "samples_per_s": n / sec,
-                                       "roofline": {"bound": "alu", "achieved": flop / sec / 1e12,
-                                                    "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
-                                                    "frac": flop / sec / fp32_peak}}
-        del net
+    if want("train"):
+        Fq, Wd, Ld = 12, 256, 8
+        n = 65536
+        lab = mesh.label(to[:n].contiguous(), tw[:n].contiguous())
+        dgt, hgt = lab["dist"].clone(), lab["hit"].clone()
+        tsub, wsub = to[:n].contiguous(), tw[:n].contiguous()
+        loss = torch.empty((), device="cuda")
+        E = 6 + 6 * Fq
+        macs = E * Wd + (Ld - 1) * Wd * Wd + 2 * Wd
+        for prec in ("bf16", "fp32") if only is None else ("bf16",):
+            net = P.DDFNet(Fq, Wd, Ld, init_weights(Fq, Wd, Ld, seed=2), prec)
+            sec = _time(torch, lambda: net.train_step(tsub, wsub, dgt, hgt, lr=1e-4, loss=loss),
+                        10 if prec == "bf16" else 3)
+            net.device_status()
+            if prec == "bf16":
+                flop = 2.0 * macs * n * 3     # forward, dgrad, wgrad (activations kept, no recompute)
+                peak = peaks["bf16_tflops_sustained"]
+                rows["train_step"] = {"workload": "batch 65,536 labelled rays, 78 -> 256 x 8 -> 2, L1 + BCE, Adam; "
+                                                  "BF16 tcgen05 GEMMs, FP32 accumulate and masters",
+                                      "ms": sec * 1e3, "samples_per_s": n / sec, "loss": float(loss.item()),
+                                      "roofline": {"bound": "tensor", "achieved": flop / sec / 1e12, "peak": peak,
+                                                   "unit": "TFLOP/s", "frac": flop / sec / 1e12 / peak}}
+            else:
+                flop = 2.0 * macs * n * 4     # forward, recomputed forward, dgrad, wgrad
+                fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+                rows["train_step_fp32"] = {"workload": "the same step on the FP32 SIMT GEMMs",
+                                           "ms": sec * 1e3, "samples_per_s": n / sec,
+                                           "roofline": {"bound": "alu", "achieved": flop / sec / 1e12,
+                                                        "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                                                        "frac": flop / sec / fp32_peak}}
+            del net
     # ---- a10 grouped query (16 objects, widths 128 / 256, 4-8 layers)
-    rng = np.random.default_rng(14)
-    specs = [(12, 128 if i % 2 == 0 else 256, 4 + (i % 5), 100 + i) for i in range(16)]
-    nets = [P.DDFNet(Fq2, W2, L2, init_weights(Fq2, W2, L2, seed=s2), "bf16") for Fq2, W2, L2, s2 in specs]
-    counts = np.floor(10 ** (3 + 3 * rng.random(16))).astype(np.int64)
-    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
-    tot = int(off[-1])
-    g = torch.Generator(device="cuda").manual_seed(15)
-    go = torch.randn(tot, 3, device="cuda", generator=g)
-    go = go / go.norm(dim=1, keepdim=True) * torch.rand(tot, 1, device="cuda", generator=g)
-    gw = torch.randn(tot, 3, device="cuda", generator=g)
-    gw = gw / gw.norm(dim=1, keepdim=True)
-    toff = torch.from_numpy(off).cuda()
-    grp = P.DDFGroup(nets)
-    gout = grp._out(tot, "cuda")
-    cfg = grp.autotune(toff, go, gw, gout, reps=2)
-    grp.capture(toff, go, gw, gout)
-    sec = _time(torch, grp.replay, 10)
-    grp.status()
-    flop = sum(2.0 * ((6 + 6 * f) * W2 + (L2 - 1) * W2 * W2 + 2 * W2) * c for (f, W2, L2, _), c in zip(specs, counts))
-    peak = peaks["bf16_tflops_sustained"]
-    rows["grouped_query"] = {"workload": "16 BF16 networks (widths 128/256, 4-8 layers, 12-frequency encoding), "
-                                         "ray counts log-uniform on [1e3, 1e6], one CUDA-graph replay per bounce",
-                             "rays": tot, "queries_per_s": tot / sec, "ms": sec * 1e3,
-                             "launch_shapes": cfg,
-                             "roofline": {"bound": "tensor", "achieved": flop / sec / 1e12, "peak": peak,
-                                          "unit": "TFLOP/s", "frac": flop / sec / 1e12 / peak}}
+    if want("grouped"):
+        rng = np.random.default_rng(14)
+        specs = [(12, 128 if i % 2 == 0 else 256, 4 + (i % 5), 100 + i) for i in range(16)]
+        nets = [P.DDFNet(Fq2, W2, L2, init_weights(Fq2, W2, L2, seed=s2), "bf16") for Fq2, W2, L2, s2 in specs]
+        counts = np.floor(10 ** (3 + 3 * rng.random(16))).astype(np.int64)
+        off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+        tot = int(off[-1])
+        g = torch.Generator(device="cuda").manual_seed(15)
+        go = torch.randn(tot, 3, device="cuda", generator=g)
+        go = go / go.norm(dim=1, keepdim=True) * torch.rand(tot, 1, device="cuda", generator=g)
+        gw = torch.randn(tot, 3, device="cuda", generator=g)
+        gw = gw / gw.norm(dim=1, keepdim=True)
+        toff = torch.from_numpy(off).cuda()
+        grp = P.DDFGroup(nets)
+        gout = grp._out(tot, "cuda")
+        cfg = grp.autotune(toff, go, gw, gout, reps=2)
+        grp.capture(toff, go, gw, gout)
+        sec = _time(torch, grp.replay, 10)
+        grp.status()
+        flop = sum(2.0 * ((6 + 6 * f) * W2 + (L2 - 1) * W2 * W2 + 2 * W2) * c
+                   for (f, W2, L2, _), c in zip(specs, counts))
+        peak = peaks["bf16_tflops_sustained"]
+        rows["grouped_query"] = {"workload": "16 BF16 networks (widths 128/256, 4-8 layers, 12-frequency encoding), "
+                                             "ray counts log-uniform on [1e3, 1e6], one CUDA-graph replay per bounce",
+                                 "rays": tot, "queries_per_s": tot / sec, "ms": sec * 1e3,
+                                 "launch_shapes": cfg,
+                                 "roofline": {"bound": "tensor", "achieved": flop / sec / 1e12, "peak": peak,
+                                              "unit": "TFLOP/s", "frac": flop / sec / 1e12 / peak}}
     # ---- width-512 network (102 -> 512 x 8 -> 2) queries and one wave of the large render
-    F5, W5, L5 = 16, 512, 8
-    blob5 = init_weights(F5, W5, L5, seed=5)
-    n5 = P.DDFNet(F5, W5, L5, blob5, "bf16")
-    nq = 1 << 22
-    g5 = torch.Generator(device="cuda").manual_seed(16)
-    qo = torch.randn(nq, 3, device="cuda", generator=g5)
-    qo = qo / qo.norm(dim=1, keepdim=True) * torch.rand(nq, 1, device="cuda", generator=g5)
-    qw = torch.randn(nq, 3, device="cuda", generator=g5)
-    qw = qw / qw.norm(dim=1, keepdim=True)
-    qout = n5.query(qo, qw)
-    sec = _time(torch, lambda: n5.query(qo, qw, out=qout), 3)
-    f5 = 2.0 * ((6 + 6 * F5) * W5 + (L5 - 1) * W5 * W5 + 2 * W5)
-    peak = peaks["bf16_tflops_sustained"]
-    rows["query_w512"] = {"workload": "2^22 queries, 102 -> 512 x 8 -> 2, BF16, no normals",
-                          "queries_per_s": nq / sec,
-                          "roofline": {"bound": "tensor", "achieved": f5 * nq / sec / 1e12, "peak": peak,
-                                       "unit": "TFLOP/s", "frac": f5 * nq / sec / 1e12 / peak}}
-    from ddf_synth import default_camera
-    cam5 = default_camera(1920, 1080, seed=1)
-    img5 = torch.empty(1080, 1920, device="cuda")
-    sec = _time(torch, lambda: n5.render(cam5, 8, 8, img5), 1)
-    rows["large_render_wave"] = {"workload": "1920 x 1080 x 8 spp (one wave of 16.6M paths), <= 8 bounces, "
-                                             "102 -> 512 x 8 -> 2 BF16 (the full 256-spp render is 32 such waves)",
-                                 "samples_per_s": 1920 * 1080 * 8 / sec, "ms": sec * 1e3,
-                                 "queries_per_bounce": n5.render_stats(8)}
+    if want("w512"):
+        F5, W5, L5 = 16, 512, 8
+        blob5 = init_weights(F5, W5, L5, seed=5)
+        n5 = P.DDFNet(F5, W5, L5, blob5, "bf16")
+        nq = 1 << 22
+        g5 = torch.Generator(device="cuda").manual_seed(16)
+        qo = torch.randn(nq, 3, device="cuda", generator=g5)
+        qo = qo / qo.norm(dim=1, keepdim=True) * torch.rand(nq, 1, device="cuda", generator=g5)
+        qw = torch.randn(nq, 3, device="cuda", generator=g5)
+        qw = qw / qw.norm(dim=1, keepdim=True)
+        qout = n5.query(qo, qw)
+        sec = _time(torch, lambda: n5.query(qo, qw, out=qout), 3)
+        f5 = 2.0 * ((6 + 6 * F5) * W5 + (L5 - 1) * W5 * W5 + 2 * W5)
+        peak = peaks["bf16_tflops_sustained"]
+        rows["query_w512"] = {"workload": "2^22 queries, 102 -> 512 x 8 -> 2, BF16, no normals",
+                              "queries_per_s": nq / sec,
+                              "roofline": {"bound": "tensor", "achieved": f5 * nq / sec / 1e12, "peak": peak,
+                                           "unit": "TFLOP/s", "frac": f5 * nq / sec / 1e12 / peak}}
+        if only is None:
+            cam5 = default_camera(1920, 1080, seed=1)
+            img5 = torch.empty(1080, 1920, device="cuda")
+            sec = _time(torch, lambda: n5.render(cam5, 8, 8, img5), 1)
+            rows["large_render_wave"] = {"workload": "1920 x 1080 x 8 spp (one wave of 16.6M paths), <= 8 bounces, "
+                                                     "102 -> 512 x 8 -> 2 BF16 (the full 256-spp render is 32 such "
+                                                     "waves)",
+                                         "samples_per_s": 1920 * 1080 * 8 / sec, "ms": sec * 1e3,
+                                         "queries_per_bounce": n5.render_stats(8)}
     return rows
 
 
