@@ -442,7 +442,8 @@ def other_rows(P, torch, np, peaks, only=None):
                          "roofline": {"bound": "alu", "achieved": tests / sec * 34 / 1e12,
                                       "peak": alu_peak / 1e12, "unit": "T FP32-instr/s",
                                       "frac": tests / sec * 34 / alu_peak,
-                                      "note": "34 FP32 instructions per filter test (count of the hot loop)"},
+                                      "note": "34 FP32 operations per filter test (count of the hot loop; the "
+                                              "thread's two rays run as the lanes of packed FP32 pairs)"},
                          "hbm_gbs": (o.shape[0] * 33) / sec / 1e9}
     # ---- a9 training step: BF16 tensor-core GEMMs (FP32 accumulate, FP32 masters), and the FP32 path
     if want("train"):

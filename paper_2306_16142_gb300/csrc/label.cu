@@ -158,6 +158,38 @@ __device__ __noinline__ void candidate(RayState& st, int k, float4 ta, float4 tb
     if (h) offer_exact(st, k, t64, V, F, o, w);
 }
 
+// Packed FP32 pair arithmetic (one instruction, two lanes; sm_100+): d = a * b + c, a * b, a - b,
+// with `f` variants broadcasting a scalar operand to both lanes.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+        " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}\n"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " mul.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}\n"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}\n"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 fma2f(float2 a, float b, float2 c) { return fma2(a, make_float2(b, b), c); }
+__device__ __forceinline__ float2 mul2f(float2 a, float b) { return mul2(a, make_float2(b, b)); }
+__device__ __forceinline__ float2 sub2f(float2 a, float b) { return sub2(a, make_float2(b, b)); }
+__device__ __forceinline__ float2 fma2v(float a, float2 b, float2 c) { return fma2(make_float2(a, a), b, c); }
+__device__ __forceinline__ float2 mul2v(float a, float2 b) { return mul2(make_float2(a, a), b); }
+
 __global__ void __launch_bounds__(kThreads) label_kernel(
     const float4* __restrict__ hot, const float4* __restrict__ aux, const float* __restrict__ V,
     const int32_t* __restrict__ F, int64_t nt, const float* __restrict__ O,
@@ -179,6 +211,13 @@ __global__ void __launch_bounds__(kThreads) label_kernel(
         So[r] = (fabsf(o[r][0]) + fabsf(o[r][1]) + fabsf(o[r][2])) * 1.000001f;
         st[r].bi = -1; st[r].blo = INFINITY; st[r].bhi = INFINITY; st[r].bexact = false;
         st[r].bt64 = 0.0; st[r].retests = 0; st[r].finals = 0;
+    }
+    static_assert(RPT == 2, "the filter packs the thread's two rays into FP32 pairs");
+    float2 O2[3], W2[3];   // (ray 0, ray 1) per coordinate
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        O2[c] = make_float2(o[0][c], o[1][c]);
+        W2[c] = make_float2(w[0][c], w[1][c]);
     }
     const int64_t ntiles = (nt + TT - 1) / TT;
     auto stage = [&](int64_t t, int buf) {
@@ -206,23 +245,25 @@ __global__ void __launch_bounds__(kThreads) label_kernel(
         const int cnt = (int)min((int64_t)TT, nt - t * TT);
         for (int j = 0; j < cnt; ++j) {
             const float4 a = tb[3 * j], b = tb[3 * j + 1], c = tb[3 * j + 2];
-            // a = (v0, K E), b = (e1, K E |v0|_1), c = (e2, K E^2)
+            // a = (v0, K E), b = (e1, K E |v0|_1), c = (e2, K E^2). The two rays of the thread run
+            // as the two lanes of packed FP32 operations (one instruction for both rays).
+            const float2 sx = sub2f(O2[0], a.x), sy = sub2f(O2[1], a.y), sz = sub2f(O2[2], a.z);
+            const float2 px = fma2f(W2[1], c.z, mul2f(W2[2], -c.y));
+            const float2 py = fma2f(W2[2], c.x, mul2f(W2[0], -c.z));
+            const float2 pz = fma2f(W2[0], c.y, mul2f(W2[1], -c.x));
+            const float2 det = fma2v(b.x, px, fma2v(b.y, py, mul2v(b.z, pz)));
+            const float2 Nu = fma2(sx, px, fma2(sy, py, mul2(sz, pz)));
+            const float2 qx = fma2f(sy, b.z, mul2f(sz, -b.y));
+            const float2 qy = fma2f(sz, b.x, mul2f(sx, -b.z));
+            const float2 qz = fma2f(sx, b.y, mul2f(sy, -b.x));
+            const float2 Nv = fma2(W2[0], qx, fma2(W2[1], qy, mul2(W2[2], qz)));
+            const float dd[2] = {det.x, det.y}, uu[2] = {Nu.x, Nu.y}, vv[2] = {Nv.x, Nv.y};
 #pragma unroll
             for (int r = 0; r < RPT; ++r) {
-                const float sx = o[r][0] - a.x, sy = o[r][1] - a.y, sz = o[r][2] - a.z;
-                const float px = w[r][1] * c.z - w[r][2] * c.y;
-                const float py = w[r][2] * c.x - w[r][0] * c.z;
-                const float pz = w[r][0] * c.y - w[r][1] * c.x;
-                const float det = b.x * px + b.y * py + b.z * pz;
-                const float Nu = sx * px + sy * py + sz * pz;
-                const float qx = sy * b.z - sz * b.y;
-                const float qy = sz * b.x - sx * b.z;
-                const float qz = sx * b.y - sy * b.x;
-                const float Nv = w[r][0] * qx + w[r][1] * qy + w[r][2] * qz;
-                const float ad = fabsf(det);
+                const float ad = fabsf(dd[r]);
                 const float B = fmaf(a.w, So[r], b.w);
-                const float xu = copysignf(1.f, det) * Nu;
-                const float xv = copysignf(1.f, det) * Nv;
+                const float xu = copysignf(1.f, dd[r]) * uu[r];
+                const float xv = copysignf(1.f, dd[r]) * vv[r];
                 const bool reject = (ad > c.w) && ((xu < -B) || (xv < -B) || (xu + xv > ad + 2.f * B + c.w));
                 if (!reject && valid[r])
                     candidate(st[r], (int)(t * TT + j), a, b, c, aux, V, F, o[r], w[r]);
