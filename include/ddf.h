@@ -57,7 +57,7 @@ extern "C" {
 #define DDF_FP32 0 /* FP32 SIMT FMA, FP32 accumulate (the reference GPU path)               */
 #define DDF_BF16 1 /* BF16 tcgen05 tensor-core MMAs, FP32 accumulate in tensor memory       */
 #define DDF_FP8 2  /* FP8 E4M3 tcgen05 MMAs with per-output-channel weight scales and
-                      per-row activation scales, FP32 accumulate                             */
+                      static per-input-channel activation scales, FP32 accumulate            */
 
 typedef struct ddf_net_s* ddf_net;
 typedef struct ddf_mesh_s* ddf_mesh;
@@ -113,6 +113,20 @@ DDF_API int ddf_destroy(ddf_net net);
 /* Switch the hidden-layer GEMM precision; repacks the working copy from the FP32 masters.
  * Synchronous. UNSUPPORTED if the precision is not built for this architecture. */
 DDF_API int ddf_set_precision(ddf_net net, int precision);
+
+/* The FP8 path's static activation scales, copied into a HOST buffer of L * width floats
+ * (nbytes = 4 L width): entry [l][k] is the scale s_a of input channel k of hidden layer l,
+ * the E4M3 code of an activation a being E4M3(a / s_a). Layer 0 (the encoded features, which lie
+ * in [-1, 1]) has s_a = 1/448 for every channel; layers 1 .. L-1 have twice the channel's maximum
+ * |activation| on a fixed calibration set of 8,192 rays under the BF16 forward pass, floored at
+ * 1e-3 of the layer's maximum, divided by 448. Calibration ray i draws Philox4x32-10 words with
+ * key 0x43414C4942 (low word first): counter (i, 0, 0, 0) gives u0..u2 and the origin
+ * r (sqrt(1 - z^2) cos phi, sqrt(1 - z^2) sin phi, z) with z = 1 - 2 u0, phi = 2 pi u1,
+ * r = cbrt(u2); counter (i, 0, 1, 0) gives the direction the same way with r = 1
+ * (u = (word >> 8) 2^-24). They are recomputed whenever the FP8 copy is repacked (set_weights,
+ * set_precision, train_step). Synchronous. INVALID_ARG if the handle is not in DDF_FP8 precision
+ * or nbytes is wrong. */
+DDF_API int ddf_fp8_scales(ddf_net net, float* host_out, size_t nbytes);
 
 /* Synchronise the device and report whether a bounded device-side wait of this handle's
  * kernels gave up since the last call (DDF_ERR_TIMEOUT, flag then cleared) or DDF_OK. */

@@ -55,6 +55,7 @@ _SIG = {
     "ddf_destroy": (C.c_int, [_P]),
     "ddf_set_precision": (C.c_int, [_P, C.c_int]),
     "ddf_device_status": (C.c_int, [_P]),
+    "ddf_fp8_scales": (C.c_int, [_P, _P, C.c_size_t]),
     "ddf_selftest_wait": (C.c_int, [C.c_int, C.c_int]),
     "ddf_num_params": (C.c_int, [_P, C.POINTER(_I64)]),
     "ddf_set_weights": (C.c_int, [_P, _P, C.c_size_t, _P]),

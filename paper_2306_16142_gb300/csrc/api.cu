@@ -201,6 +201,14 @@ int ddf_set_precision(ddf_net net, int precision) {
     return DDF_OK;
 }
 
+int ddf_fp8_scales(ddf_net net, float* host_out, size_t nbytes) {
+    if (!net || !host_out) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    if (net->is_sphere || net->precision != DDF_FP8) return fail(DDF_ERR_INVALID_ARG, "handle is not in FP8 precision");
+    if (nbytes != sizeof(float) * (size_t)net->lay.L * net->lay.width)
+        return fail(DDF_ERR_INVALID_ARG, "scale buffer size mismatch");
+    return tc_fp8_scales(net, host_out);
+}
+
 int ddf_device_status(ddf_net net) {
     if (!net) return fail(DDF_ERR_INVALID_ARG, "net is NULL");
     DDF_CUDA_TRY(cudaDeviceSynchronize());

@@ -123,6 +123,7 @@ bool tc_supported(const NetLayout& lay, int precision);
 int tc_pack(ddf_net_s* net, int precision, cudaStream_t stream);
 void tc_free(ddf_net_s* net);
 int tc_device_status(ddf_net_s* net);
+int tc_fp8_scales(ddf_net_s* net, float* host_out);   // [L][W] static activation scales
 int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
                  const int* d_count, float* dist, float* logit, uint8_t* hit, float* normals,
                  cudaStream_t stream);
@@ -161,6 +162,9 @@ int tct_train_step(ddf_net_s* net, const float* o, const float* w, const float* 
                    cudaStream_t stream);
 int tct_backward(ddf_net_s* net, const float* o, const float* w, int64_t n, const float* gdist,
                  const float* glogit, float* gweights, float* ginput, cudaStream_t stream);
+// Per-channel maxima of the hidden-layer inputs a_1 .. a_{L-1} (d_amax [L][W], row 0 zero) over
+// a fixed calibration set of rays, from the BF16 tensor-core forward (FP8 static scales).
+int tct_calibrate_fp8(ddf_net_s* net, float* d_amax, cudaStream_t stream);
 
 int num_sms();
 

@@ -77,7 +77,8 @@ struct TcArgs {
     uint32_t off_grp;
     int maxL;
     uint32_t* gmask;   // width 512: per-CTA ReLU masks of the reverse pass
-    const float* wscale;   // FP8: per-output-channel weight scales [L][W]
+    const float* f8_mul;   // FP8 epilogue [L][W]: accumulator multiplier (weight scale / next input scale)
+    const float* f8_add;   // FP8 epilogue [L][W]: addend (bias / next input scale)
 };
 
 
@@ -888,11 +889,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // ------------------------------------------------------------------ FP8 E4M3 forward
 // kind::f8f6f4 MMAs (E4M3 x E4M3 -> FP32, K = 32 per instruction) on 128-feature K-blocks
-// (128-byte swizzled rows, the same byte layout as the BF16 path). Weights carry one scale per
-// output channel (max |W[n][:]| / 448); every activation row carries one scale (max |a[r][:]| /
-// 448), so z[r][n] = acc[r][n] * s_a[r] * s_w[n] + b[n]. The two epilogue warp groups hold halves
-// of each row: they exchange their partial maxima through shared memory before quantising the
-// next layer's input.
+// (128-byte swizzled rows, the same byte layout as the BF16 path). Activation scales are static
+// and per input channel (calibrated at packing, folded into the weights); weights carry one scale
+// per output channel, so z[r][n] = acc[r][n] * s_w[n] + b[n] and the next layer's input is
+// E4M3(a[r][k] / s_a[k]). With no per-row reduction, each K-block of the next A operand is
+// quantised and released as soon as its accumulator columns are read.
 __device__ __forceinline__ uint32_t idesc_f8(int M, int N) {
     return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);   // E4M3 x E4M3 -> F32
 }
@@ -950,8 +951,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int NST = a.nst;
     uint8_t* act = smem;                             // max(1, NKB) x 16 KB
     uint8_t* wst = smem + a.off_wst;
-    float* bias_s = reinterpret_cast<float*>(smem + a.off_bias);
-    float* sw_s = reinterpret_cast<float*>(smem + a.off_mask);   // per-channel weight scales [L][W]
+    float* mul_s = reinterpret_cast<float*>(smem + a.off_mask);   // epilogue multipliers [L][W]
+    float* add_s = reinterpret_cast<float*>(smem + a.off_bias);   // epilogue addends [L][W]
     float* head_s = reinterpret_cast<float*>(smem + a.off_head);
     float* part = reinterpret_cast<float*>(smem + a.off_part);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
@@ -984,8 +985,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     for (int i = tid; i < L * W; i += kThreads) {
-        bias_s[i] = a.bias[i];
-        sw_s[i] = a.wscale[i];
+        mul_s[i] = a.f8_mul[i];
+        add_s[i] = a.f8_add[i];
     }
     for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
     __syncthreads();
@@ -1041,22 +1042,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         uint32_t g = 0, accph = 0;
         bool ok = true;
-        auto write64 = [&](int kb, const float* z, float inv) {
-            uint32_t q[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) q[i] = pack_e4m3x4(z[4 * i] * inv, z[4 * i + 1] * inv, z[4 * i + 2] * inv, z[4 * i + 3] * inv);
+        // 16 words of E4M3 bytes (this thread's row, columns [128 kb + 64 group, +64)) into K-block kb
+        auto store64 = [&](int kb, const uint32_t* q) {
 #pragma unroll
             for (int m = 0; m < 4; ++m)
                 st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), q[4 * m], q[4 * m + 1], q[4 * m + 2],
                              q[4 * m + 3]);
-        };
-        // the row's maximum over both groups (both threads of the row get it)
-        auto row_max = [&](float mx) {
-            part[2 * r + grp] = mx;
-            epi_bar();
-            const float m2 = fmaxf(part[2 * r], part[2 * r + 1]);
-            epi_bar();
-            return m2;
         };
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const int64_t i = t * kTileM + r;
@@ -1068,17 +1059,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 v[c] = valid ? a.o[row * 3 + c] : 0.f;
                 v[c + 3] = valid ? a.w[row * 3 + c] : 0.f;
             }
-            float sa;
-            {
+            {   // layer 0: features in [-1, 1], fixed input scale 1 / 448
                 float fe[64];
                 if (grp == 0) encode_feats64<0>(v, a.F, fe);
                 else encode_feats64<1>(v, a.F, fe);
-                float mx = 0.f;
+                uint32_t q[16];
 #pragma unroll
-                for (int q = 0; q < 64; ++q) mx = fmaxf(mx, fabsf(fe[q]));
-                mx = row_max(mx);
-                sa = mx > 0.f ? mx * (1.f / 448.f) : 1.f;
-                write64(0, fe, 1.f / sa);
+                for (int i = 0; i < 16; ++i)
+                    q[i] = pack_e4m3x4(fe[4 * i] * 448.f, fe[4 * i + 1] * 448.f, fe[4 * i + 2] * 448.f,
+                                       fe[4 * i + 3] * 448.f);
+                store64(0, q);
                 release_kb(actr, 0);
             }
             float y0 = 0.f, y1 = 0.f;
@@ -1089,47 +1079,48 @@ __global__ void __launch_bounds__(kThreads, 1)
                 accph ^= 1u << b;
                 tc_fence_after();
                 const uint32_t tcol = tbase + lane_off + (uint32_t)(b * W);
-                float z[NKB][64];
-                {
-                    uint32_t raw[NKB][2][32];
 #pragma unroll
-                    for (int kb = 0; kb < NKB; ++kb)
+                for (int kb = 0; kb < NKB; ++kb) {
+                    // this thread's 64 columns of K-block kb: u = acc m + c (m, c fold the weight
+                    // scale, the bias and the next layer's input scale), then ReLU
+                    uint32_t raw[2][32];
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) TC_LD32(tcol + kb * 128 + grp * 64 + h * 32, raw[kb][h]);
+                    for (int h = 0; h < 2; ++h) TC_LD32(tcol + kb * 128 + grp * 64 + h * 32, raw[h]);
                     tc_wait_ld();
-                    const float* bs = bias_s + s * W;
-                    const float* ws = sw_s + s * W;
+                    const int c0 = kb * 128 + grp * 64;
+                    const float4* m4 = reinterpret_cast<const float4*>(mul_s + s * W + c0);
+                    const float4* a4 = reinterpret_cast<const float4*>(add_s + s * W + c0);
+                    if (s < L - 1) {
+                        uint32_t q[16];
 #pragma unroll
-                    for (int kb = 0; kb < NKB; ++kb)
-#pragma unroll
-                        for (int c = 0; c < 64; ++c) {
-                            const int col = kb * 128 + grp * 64 + c;
-                            z[kb][c] = fmaxf(fmaf(__uint_as_float(raw[kb][c >> 5][c & 31]) * ws[col], sa, bs[col]), 0.f);
+                        for (int i = 0; i < 16; ++i) {
+                            const float4 mm = m4[i], aa = a4[i];
+                            const uint32_t* x = &raw[i >> 3][(4 * i) & 31];
+                            float u0, u1, u2, u3;
+                            fma2p(__uint_as_float(x[0]), __uint_as_float(x[1]), mm.x, mm.y, aa.x, aa.y, u0, u1);
+                            fma2p(__uint_as_float(x[2]), __uint_as_float(x[3]), mm.z, mm.w, aa.z, aa.w, u2, u3);
+                            q[i] = pack_relu_e4m3x4(u0, u1, u2, u3);
                         }
-                }
-                if (s < L - 1) {
-                    float mx = 0.f;
-#pragma unroll
-                    for (int kb = 0; kb < NKB; ++kb)
-#pragma unroll
-                        for (int c = 0; c < 64; ++c) mx = fmaxf(mx, z[kb][c]);
-                    mx = row_max(mx);
-                    sa = mx > 0.f ? mx * (1.f / 448.f) : 1.f;
-                    const float inv = 1.f / sa;
-#pragma unroll
-                    for (int kb = 0; kb < NKB; ++kb) {
-                        write64(kb, z[kb], inv);
+                        store64(kb, q);
                         release_kb(actr, kb);
-                    }
-                } else {
+                    } else {
 #pragma unroll
-                    for (int kb = 0; kb < NKB; ++kb)
+                        for (int i = 0; i < 16; ++i) {
+                            const float4 mm = m4[i], aa = a4[i];
+                            const uint32_t* x = &raw[i >> 3][(4 * i) & 31];
+                            float u[4];
+                            fma2p(__uint_as_float(x[0]), __uint_as_float(x[1]), mm.x, mm.y, aa.x, aa.y, u[0], u[1]);
+                            fma2p(__uint_as_float(x[2]), __uint_as_float(x[3]), mm.z, mm.w, aa.z, aa.w, u[2], u[3]);
 #pragma unroll
-                        for (int c = 0; c < 64; ++c) {
-                            const int col = kb * 128 + grp * 64 + c;
-                            y0 = fmaf(z[kb][c], head_s[col], y0);
-                            y1 = fmaf(z[kb][c], head_s[W + col], y1);
+                            for (int j = 0; j < 4; ++j) {
+                                const float z = fmaxf(u[j], 0.f);
+                                y0 = fmaf(z, head_s[c0 + 4 * i + j], y0);
+                                y1 = fmaf(z, head_s[W + c0 + 4 * i + j], y1);
+                            }
                         }
+                    }
+                }
+                if (s == L - 1) {
                     tc_fence_before();
                     if (grp == 1) {
                         part[2 * r] = y0;
@@ -1200,17 +1191,57 @@ __global__ void pack_kernel(const float* __restrict__ master, NetLayout lay, int
             head[i] = i < 2 * W ? master[lay.w_off[lay.L] + i] : master[lay.b_off[lay.L] + i - 2 * W];
 }
 
-// FP8 E4M3 copy of the hidden layers: one block per output channel n of layer l; scale
-// s = max_k |W[n][k]| / 448 (1 for an all-zero row), byte = E4M3(W[n][k] / s), layer 0 in the
-// internal feature order.
+// FP8 E4M3 copy of the hidden layers with static activation scales. Input channel k of layer l
+// carries the scale s_a[l][k] (layer 0, whose features lie in [-1, 1]: 1 / 448; hidden layers:
+// twice the channel's calibration maximum / 448, floored at 1e-3 of the layer's maximum), folded
+// into the weights: W'[n][k] = W[n][k] s_a[l][k]. One block per output channel n of layer l;
+// s_w[l][n] = max_k |W'[n][k]| / 448 (1 for an all-zero row), byte = E4M3(W'[n][k] / s_w[l][n]),
+// layer 0 in the internal feature order. The query kernel then forms the next layer's input
+// code as E4M3(ReLU(acc m + c)) with m = s_w[l][n] / s_a[l + 1][n], c = b[l][n] / s_a[l + 1][n]
+// (the last hidden layer: m = s_w, c = b, ReLU, then the FP32 head).
+__device__ float f8_layer_max(const float* __restrict__ amax, int l, int W, float* red) {
+    float lmax = 0.f;
+    for (int k = threadIdx.x; k < W; k += blockDim.x) lmax = fmaxf(lmax, amax[(int64_t)l * W + k]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, off));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lmax;
+    __syncthreads();
+    lmax = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) lmax = fmaxf(lmax, red[i]);
+    return lmax;
+}
+
+__device__ __forceinline__ float f8_act_scale(float amax_k, float lmax) {
+    const float floor_ = lmax > 0.f ? 1e-3f * lmax : 1.f;
+    return 2.f * fmaxf(amax_k, floor_) / 448.f;
+}
+
 __global__ void pack_f8_kernel(const float* __restrict__ master, NetLayout lay, int kmax8, uint8_t* __restrict__ w8,
-                               float* __restrict__ sw8) {
-    const int l = blockIdx.y, nrow = blockIdx.x, W = lay.width;
+                               float* __restrict__ sw8, const float* __restrict__ amax, float* __restrict__ sa8,
+                               float* __restrict__ ep8) {
+    const int l = blockIdx.y, nrow = blockIdx.x, W = lay.width, L = lay.L;
     const int in = l == 0 ? lay.E : W;
     const float* Wrow = master + lay.w_off[l] + (int64_t)nrow * in;
     __shared__ float red[32];
+    __shared__ float sa_s[kMaxWidth];
+    // this layer's input scales (every block of the layer computes the same values)
+    const float lmax = l > 0 ? f8_layer_max(amax, l, W, red) : 0.f;
+    for (int k = threadIdx.x; k < W; k += blockDim.x) {
+        const float sa = l == 0 ? 1.f / 448.f : f8_act_scale(amax[(int64_t)l * W + k], lmax);
+        sa_s[k] = sa;
+        if (nrow == 0) sa8[(int64_t)l * W + k] = sa;
+    }
+    // the next layer's input scale of channel nrow (the same arithmetic as that layer's blocks)
+    const float lmax_next = l + 1 < L ? f8_layer_max(amax, l + 1, W, red) : 0.f;
+    __syncthreads();
+    auto wk = [&](int k) -> float {   // W'[nrow][internal column k]
+        const int src = l == 0 ? in_feature(k) : k;
+        if (src < 0 || src >= in) return 0.f;
+        return Wrow[src] * (l == 0 ? 1.f / 448.f : sa_s[k]);
+    };
     float mx = 0.f;
-    for (int k = threadIdx.x; k < in; k += blockDim.x) mx = fmaxf(mx, fabsf(Wrow[k]));
+    for (int k = threadIdx.x; k < kmax8; k += blockDim.x) mx = fmaxf(mx, fabsf(wk(k)));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
@@ -1223,18 +1254,27 @@ __global__ void pack_f8_kernel(const float* __restrict__ master, NetLayout lay, 
     }
     __syncthreads();
     const float sc = red[0] > 0.f ? red[0] / 448.f : 1.f;
-    if (threadIdx.x == 0) sw8[(int64_t)l * W + nrow] = sc;
+    if (threadIdx.x == 0) {
+        const float bn = master[lay.b_off[l] + nrow];
+        sw8[(int64_t)l * W + nrow] = sc;
+        float m = sc, c = bn;
+        if (l + 1 < L) {
+            const float inv_next = 1.f / f8_act_scale(amax[(int64_t)(l + 1) * W + nrow], lmax_next);
+            m = sc * inv_next;
+            c = bn * inv_next;
+        }
+        ep8[(int64_t)l * W + nrow] = m;
+        ep8[(int64_t)(L + l) * W + nrow] = c;
+    }
     const float inv = 1.f / sc;
     uint8_t* dst = w8 + ((int64_t)l * W + nrow) * kmax8;
     for (int k = threadIdx.x; k < kmax8; k += blockDim.x) {
-        const int src = l == 0 ? in_feature(k) : k;
-        const float x = (src >= 0 && src < in) ? Wrow[src] * inv : 0.f;
+        const float x = wk(k) * inv;
         unsigned short h;
         asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(h) : "f"(0.f), "f"(x));
         dst[k] = (uint8_t)(h & 0xffu);
     }
 }
-
 
 int make_map(CUtensorMap* m, void* base, int inner, int rows, int L) {
     EncodeTiledFn enc = get_encode();
@@ -1351,12 +1391,12 @@ Layout smem_layout_f8(int W, int L) {
     const uint32_t budget = 227u * 1024u - 1024u;
     s.nst = std::max(0, std::min(8, (int)((budget - fixed) / stage)));
     s.off_wst = act;
-    s.off_mask = act + (uint32_t)s.nst * stage;   // weight scales
-    s.off_bias = s.off_mask + vec;
+    s.off_mask = act + (uint32_t)s.nst * stage;   // epilogue multipliers
+    s.off_bias = s.off_mask + vec;                 // epilogue addends
+    s.off_grp = 0;
     s.off_head = s.off_bias + vec;
     s.off_part = s.off_head + head;
-    s.off_grp = s.off_part + partb;
-    s.off_bar = s.off_grp;
+    s.off_bar = s.off_part + partb;
     s.total = s.off_bar + 512u + 1024u;
     return s;
 }
@@ -1374,7 +1414,8 @@ int launch_f8(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_coun
     a.off_head = s.off_head;
     a.off_part = s.off_part;
     a.off_bar = s.off_bar;
-    a.wscale = P->sw8;
+    a.f8_mul = P->ep8;
+    a.f8_add = P->ep8 + (size_t)a.L * W;
     int grid = use_count ? num_sms() : (int)std::min<int64_t>((n + kTileM - 1) / kTileM, num_sms());
     if (grid <= 0) return DDF_OK;
     static bool attr = false;
@@ -1460,6 +1501,9 @@ void tc_free(ddf_net_s* net) {
     cudaFree(P->gmask);
     cudaFree(P->w8);
     cudaFree(P->sw8);
+    cudaFree(P->sa8);
+    cudaFree(P->ep8);
+    cudaFree(P->amax8);
     delete P;
     net->tc = nullptr;
 }
@@ -1497,10 +1541,18 @@ int tc_pack(ddf_net_s* net, int precision, cudaStream_t stream) {
             P->kmax8 = std::max(128, W);
             DDF_CUDA_TRY(cudaMalloc(&P->w8, (size_t)L * W * P->kmax8));
             DDF_CUDA_TRY(cudaMalloc(&P->sw8, sizeof(float) * (size_t)L * W));
+            DDF_CUDA_TRY(cudaMalloc(&P->sa8, sizeof(float) * (size_t)L * W));
+            DDF_CUDA_TRY(cudaMalloc(&P->ep8, sizeof(float) * 2 * (size_t)L * W));
+            DDF_CUDA_TRY(cudaMalloc(&P->amax8, sizeof(float) * (size_t)L * W));
             int rc = make_map_u8(&P->map_f8, P->w8, P->kmax8, W, L);
             if (rc) return rc;
         }
-        pack_f8_kernel<<<dim3(W, L), 128, 0, stream>>>(net->master, lay, P->kmax8, P->w8, P->sw8);
+        // static activation scales: calibration maxima of the hidden-layer inputs from the BF16
+        // tensor-core forward on a fixed set of rays (needs the BF16 copy packed above)
+        int rc = tct_calibrate_fp8(net, P->amax8, stream);
+        if (rc) return rc;
+        pack_f8_kernel<<<dim3(W, L), 128, 0, stream>>>(net->master, lay, P->kmax8, P->w8, P->sw8, P->amax8, P->sa8,
+                                                       P->ep8);
         DDF_LAUNCH_CHECK();
     }
     return DDF_OK;
@@ -1559,6 +1611,14 @@ int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n
     return lay.width == 128   ? launch_mode<128>(net, 1, b, n, true, stream)
            : lay.width == 256 ? launch_mode<256>(net, 1, b, n, true, stream)
                               : launch512(net, 1, b, n, true, stream);
+}
+
+int tc_fp8_scales(ddf_net_s* net, float* host_out) {
+    if (!net->tc || !net->tc->sa8) return fail(DDF_ERR_INVALID_ARG, "FP8 copy not packed");
+    DDF_CUDA_TRY(cudaDeviceSynchronize());
+    DDF_CUDA_TRY(cudaMemcpy(host_out, net->tc->sa8, sizeof(float) * (size_t)net->lay.L * net->lay.width,
+                            cudaMemcpyDeviceToHost));
+    return DDF_OK;
 }
 
 int tc_device_status(ddf_net_s* net) {

@@ -24,7 +24,12 @@ struct TcPack {
     int* err = nullptr;
     uint32_t* gmask = nullptr;        // width 512: per-CTA reverse-pass ReLU masks
     uint8_t* w8 = nullptr;            // FP8: [L][W][kmax8] E4M3, per-output-channel scaled
-    float* sw8 = nullptr;             // FP8: [L][W] scales
+    float* sw8 = nullptr;             // FP8: [L][W] per-output-channel weight scales
+    float* sa8 = nullptr;             // FP8: [L][W] per-input-channel activation scales (layer 0: 1/448)
+    float* ep8 = nullptr;             // FP8: [2][L][W] epilogue multiplier and addend of layer l's
+                                      // output channel n: (s_w / s_a', b / s_a'), s_a' the next
+                                      // layer's input scale (the last layer: s_w, b)
+    float* amax8 = nullptr;           // FP8: [L][W] calibration maxima of the hidden-layer inputs
     int kmax8 = 0;
     CUtensorMap map_f8;
 };
@@ -145,6 +150,21 @@ __device__ __forceinline__ void add2(float ax, float ay, float bx, float by, flo
         " add.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}\n"
         : "=f"(dx), "=f"(dy)
         : "f"(ax), "f"(ay), "f"(bx), "f"(by));
+}
+// (dx, dy) = (ax bx + cx, ay by + cy) as one packed FP32x2 FMA.
+__device__ __forceinline__ void fma2p(float ax, float ay, float bx, float by, float cx, float cy, float& dx,
+                                      float& dy) {
+    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}\n"
+        : "=f"(dx), "=f"(dy)
+        : "f"(ax), "f"(ay), "f"(bx), "f"(by), "f"(cx), "f"(cy));
+}
+// Four E4M3 bytes of (ReLU(v0), .., ReLU(v3)), saturating at +-448, v0 in the low byte.
+__device__ __forceinline__ uint32_t pack_relu_e4m3x4(float v0, float v1, float v2, float v3) {
+    unsigned short lo, hi;
+    asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(v1), "f"(v0));
+    asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(v3), "f"(v2));
+    return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 // BF16x2 of (ReLU(lo), ReLU(hi)), lo in the low half.
 __device__ __forceinline__ uint32_t pack_relu(float lo, float hi) {

@@ -872,18 +872,16 @@ struct ChunkTargets {
     const float* gl = nullptr;
 };
 
-// Forward and reverse pass of rows [0, m) of one chunk; gradients accumulate into grad.
-int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m, const ChunkTargets& tg,
-             float* grad, float* gin, cudaStream_t s) {
+// Encoding and forward GEMMs of rows [0, m): a_1 .. a_L row-major BF16 in ws.act (and the ReLU
+// masks of a_1 .. a_{L-1} when masks is set).
+int tc_forward(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m, bool with_masks, cudaStream_t s) {
     const NetLayout& lay = net->lay;
     TcPack* P = net->tc;
     const int W = lay.width, L = lay.L, K0 = P->K0;
     const int64_t mp = (m + 127) / 128 * 128, ld = ws.mp;
     auto act = [&](int l) { return ws.act + (l == 0 ? 0 : ((int64_t)K0 + (int64_t)(l - 1) * W) * ld); };
     auto masks = [&](int l) { return ws.masks + (int64_t)(l - 1) * ld * (W / 32); };
-    auto colpart = [&](int l) { return ws.colpart + (int64_t)l * (ld / 32) * W; };
     int rc;
-
     tenc_kernel<<<(unsigned)((mp + 127) / 128), 128, 0, s>>>(o, w, m, mp, lay.E, K0, act(0));
     DDF_LAUNCH_CHECK();
 
@@ -904,9 +902,26 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
         a.bias = P->bias + (int64_t)l * W;
         a.err = P->err;
         a.out = act(l + 1);
-        a.mask_out = l + 1 < L ? masks(l + 1) : nullptr;
+        a.mask_out = with_masks && l + 1 < L ? masks(l + 1) : nullptr;
         if ((rc = launch_gemm(mA, P->map_fwd, a, s))) return rc;
     }
+    return DDF_OK;
+}
+
+// Forward and reverse pass of rows [0, m) of one chunk; gradients accumulate into grad.
+int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m, const ChunkTargets& tg,
+             float* grad, float* gin, cudaStream_t s) {
+    const NetLayout& lay = net->lay;
+    TcPack* P = net->tc;
+    const int W = lay.width, L = lay.L, K0 = P->K0;
+    const int64_t mp = (m + 127) / 128 * 128, ld = ws.mp;
+    auto act = [&](int l) { return ws.act + (l == 0 ? 0 : ((int64_t)K0 + (int64_t)(l - 1) * W) * ld); };
+    auto masks = [&](int l) { return ws.masks + (int64_t)(l - 1) * ld * (W / 32); };
+    auto colpart = [&](int l) { return ws.colpart + (int64_t)l * (ld / 32) * W; };
+    int rc;
+
+    if ((rc = tc_forward(net, ws, o, w, m, true, s))) return rc;
+
     {   // output layer, loss and delta_{L-1}
         HeadArgs h{};
         h.aL = act(L);
@@ -1008,6 +1023,44 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
     return DDF_OK;
 }
 
+// Calibration rays for the FP8 activation scales: origins uniform in the unit ball, directions
+// uniform on the sphere, from Philox4x32-10 (key = seed, counter = (ray, 0, slot, 0)).
+__global__ void cal_rays_kernel(float* __restrict__ o, float* __restrict__ w, int n, uint64_t seed) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint4 a = philox4x32_10(make_uint4((uint32_t)i, 0u, 0u, 0u), key);
+    const uint4 b = philox4x32_10(make_uint4((uint32_t)i, 0u, 1u, 0u), key);
+    const float z0 = 1.f - 2.f * u24(a.x), p0 = 6.2831853f * u24(a.y), r0 = cbrtf(u24(a.z));
+    const float s0 = sqrtf(fmaxf(0.f, 1.f - z0 * z0));
+    o[3 * i + 0] = r0 * s0 * cosf(p0);
+    o[3 * i + 1] = r0 * s0 * sinf(p0);
+    o[3 * i + 2] = r0 * z0;
+    const float z1 = 1.f - 2.f * u24(b.x), p1 = 6.2831853f * u24(b.y);
+    const float s1 = sqrtf(fmaxf(0.f, 1.f - z1 * z1));
+    w[3 * i + 0] = s1 * cosf(p1);
+    w[3 * i + 1] = s1 * sinf(p1);
+    w[3 * i + 2] = z1;
+}
+
+// amax[c] = max over rows of |a[r][c]| (BF16 [m][W]); block (32, 8): 32 columns x 8 row lanes.
+__global__ void colmax_kernel(const __nv_bfloat16* __restrict__ a, int64_t m, int W, float* __restrict__ amax) {
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    __shared__ float red[8][33];
+    float mx = 0.f;
+    if (c < W)
+        for (int64_t r = threadIdx.y; r < m; r += 8) mx = fmaxf(mx, fabsf(__bfloat162float(a[r * W + c])));
+    red[threadIdx.y][threadIdx.x] = mx;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < W) {
+        for (int k = 1; k < 8; ++k) mx = fmaxf(mx, red[k][threadIdx.x]);
+        amax[c] = mx;
+    }
+}
+
+constexpr int kCalRows = 8192;
+constexpr uint64_t kCalSeed = 0x43414C4942ull;
+
 }  // namespace
 
 bool tct_supported(const ddf_net_s* net) {
@@ -1057,4 +1110,26 @@ int tct_backward(ddf_net_s* net, const float* o, const float* w, int64_t n, cons
     return DDF_OK;
 }
 
+int tct_calibrate_fp8(ddf_net_s* net, float* d_amax, cudaStream_t s) {
+    const NetLayout& lay = net->lay;
+    const int W = lay.width, L = lay.L;
+    TcWs ws;
+    int rc = ensure_tc_ws(net, kCalRows, ws);
+    if (rc) return rc;
+    float* o = ws.gx;                      // scratch for the calibration rays
+    float* w = ws.gx + 3 * kCalRows;
+    cal_rays_kernel<<<(kCalRows + 255) / 256, 256, 0, s>>>(o, w, kCalRows, kCalSeed);
+    DDF_LAUNCH_CHECK();
+    if ((rc = tc_forward(net, ws, o, w, kCalRows, false, s))) return rc;
+    DDF_CUDA_TRY(cudaMemsetAsync(d_amax, 0, sizeof(float) * W, s));   // layer 0: fixed scale
+    const int64_t ld = ws.mp;
+    for (int l = 1; l < L; ++l) {
+        const __nv_bfloat16* a = ws.act + ((int64_t)net->tc->K0 + (int64_t)(l - 1) * W) * ld;
+        colmax_kernel<<<(W + 31) / 32, dim3(32, 8), 0, s>>>(a, kCalRows, W, d_amax + (int64_t)l * W);
+        DDF_LAUNCH_CHECK();
+    }
+    return DDF_OK;
+}
+
 }  // namespace ddf
+

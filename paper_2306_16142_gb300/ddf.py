@@ -93,6 +93,15 @@ class DDFNet:
         """Raise DDFError(TIMEOUT) if a bounded device wait of this handle gave up."""
         check("ddf_device_status", _abi.load().ddf_device_status(self.h))
 
+    def fp8_scales(self):
+        """The FP8 path's static activation scales, float32 numpy [L, width] (layer 0: 1/448)."""
+        if self.arch is None:
+            raise ValueError("architecture unknown for this handle")
+        _, width, layers = self.arch
+        out = np.empty((layers, width), np.float32)
+        check("ddf_fp8_scales", _abi.load().ddf_fp8_scales(self.h, out.ctypes.data, out.nbytes))
+        return out
+
     def set_precision(self, precision: str):
         check("ddf_set_precision", _abi.load().ddf_set_precision(self.h, PRECISIONS[precision]))
         self.precision = precision

@@ -1,9 +1,11 @@
 """A numpy/torch model of the FP8 E4M3 tensor-core arithmetic (test infrastructure).
 
-It restates the network of Sec. 4.1 with the FP8 path's quantisation: every hidden layer's
-weights scaled per output channel by max |W[n, :]| / 448 and rounded to E4M3, every layer input
-row scaled by max |a[r, :]| / 448 and rounded to E4M3, exact accumulation, then
-z = acc * s_a * s_w + b; the last hidden layer and the output head stay in floating point.
+It restates the network of Sec. 4.1 with the FP8 path's quantisation, given the path's static
+activation scales s_a [L][W] (read back from the library: they come from a calibration pass):
+hidden layer l's weights are folded with its input scales, W'[n, k] = W[n, k] s_a[l][k], then
+scaled per output channel by s_w[n] = max_k |W'[n, k]| / 448 and rounded to E4M3; its input is
+rounded to E4M3 as a[k] / s_a[l][k] (layer 0: a[k] 448); the products accumulate exactly and z = acc s_w + b. The
+last hidden layer's output and the output head stay in floating point.
 """
 
 import numpy as np
@@ -13,24 +15,46 @@ from oracle import mlp as omlp
 
 
 def e4m3(x):
-    t = torch.from_numpy(np.asarray(x, np.float64).astype(np.float32))
+    """Round to E4M3 with saturation at +-448 (the conversion the kernels use)."""
+    t = torch.from_numpy(np.clip(np.asarray(x, np.float64).astype(np.float32), -448.0, 448.0))
     return t.to(torch.float8_e4m3fn).to(torch.float64).numpy()
 
 
-def query_fp8(params, o, w, in_freqs):
+def f32(x):
+    return np.asarray(x, np.float64).astype(np.float32).astype(np.float64)
+
+
+def query_fp8(params, o, w, in_freqs, sa):
+    """sa: float32 [L, width] static activation scales; layer 0 uses sa[0][:E]."""
     X, _ = omlp.encode(o, w, in_freqs)
     L = len(params) - 1
     a = X
     for l in range(L):
         Wl, b = params[l]
-        sw = np.abs(Wl).max(axis=1) / 448.0
+        s = np.asarray(sa[l][: Wl.shape[1]], np.float64)
+        Wp = f32(f32(Wl) * s[None, :])
+        sw = f32(np.abs(Wp).max(axis=1) / 448.0)
         sw[sw == 0] = 1.0
-        Wq = e4m3(Wl / sw[:, None])
-        sa = np.abs(a).max(axis=1) / 448.0
-        sa[sa == 0] = 1.0
-        aq = e4m3(a / sa[:, None])
-        z = (aq @ Wq.T) * sa[:, None] * sw[None, :] + b
+        Wq = e4m3(Wp * f32(1.0 / sw)[:, None])
+        inv = np.full_like(s, 448.0) if l == 0 else f32(1.0 / s)
+        aq = e4m3(f32(a) * inv[None, :])
+        z = (aq @ Wq.T) * sw[None, :] + b
         a = np.maximum(z, 0.0)
     Wo, bo = params[L]
     y = a @ Wo.T + bo
     return {"dist": y[:, 0], "logit": y[:, 1], "hit": y[:, 1] > 0}
+
+
+def calibration_bound(params, o, w, in_freqs):
+    """Column maxima of |a_l| (FP64 forward) for l = 1 .. L-1 on the given rays: [L, width],
+    row 0 zero. The static scales must cover them: 448 s_a / 2 is about this maximum."""
+    X, _ = omlp.encode(o, w, in_freqs)
+    L = len(params) - 1
+    W = params[0][0].shape[0]
+    out = np.zeros((L, W))
+    a = X
+    for l in range(L - 1):
+        Wl, b = params[l]
+        a = np.maximum(a @ Wl.T + b, 0.0)
+        out[l + 1] = np.abs(a).max(axis=0)
+    return out

@@ -1,6 +1,7 @@
-"""GPU FP8 E4M3 query path (per-output-channel weight scales, per-row activation scales):
-against a model of its quantisation (tests/_fp8_model.py) and, with the error stated, against
-the FP64 oracle; FP8 renders run with Eq. 3 normals from the BF16 reverse pass."""
+"""GPU FP8 E4M3 query path (per-output-channel weight scales, static per-input-channel
+activation scales from a calibration pass): against a model of its quantisation given the
+library's scales (tests/_fp8_model.py) and, with the error stated, against the FP64 oracle; the
+scales against their definition; FP8 renders run with Eq. 3 normals from the BF16 reverse pass."""
 
 import numpy as np
 import pytest
@@ -8,7 +9,7 @@ import torch
 
 from ddf_synth import default_camera, init_weights
 from oracle import mlp as omlp
-from tests._fp8_model import query_fp8
+from tests._fp8_model import calibration_bound, query_fp8
 from tests._helpers import ensure_built, rays_in_ball
 
 pytestmark = pytest.mark.gpu
@@ -31,7 +32,7 @@ def test_fp8_query_against_model_and_oracle(P, F, W, L, seed, n):
     net.device_status()
     g = {k: v.cpu().numpy() for k, v in out.items()}
     Pm = omlp.unpack(blob, F, W, L)
-    m = query_fp8(Pm, o, w, F)
+    m = query_fp8(Pm, o, w, F, net.fp8_scales())
     d = np.abs(g["dist"] - m["dist"])
     assert np.quantile(d, 0.99) <= 5e-3 and d.max() <= 3e-2, (np.quantile(d, 0.99), d.max())
     clear = np.abs(m["logit"]) >= 0.05
@@ -57,3 +58,57 @@ def test_fp8_render_runs_and_tracks_bf16(P):
     assert np.isfinite(a).all()
     print(f"FP8 vs BF16 render mean |d pixel| = {np.abs(a - b).mean():.4f}")
     assert np.abs(a - b).mean() < 0.1
+
+
+def _calibration_rays(n=8192, seed=0x43414C4942):
+    """The library's calibration rays, rebuilt from their stated definition: Philox4x32-10 with
+    key = seed, counter (i, 0, 0, 0) gives the origin (z = 1 - 2 u0, phi = 2 pi u1, r = cbrt(u2),
+    uniform in the unit ball) and counter (i, 0, 1, 0) the direction (z = 1 - 2 u0, phi = 2 pi u1)."""
+    from oracle.philox import path_uniforms
+    ids = np.arange(n)
+    a = path_uniforms(seed, ids, 0)
+    b = path_uniforms(seed, ids, 1)
+    z0, p0, r0 = 1 - 2 * a[:, 0], 2 * np.pi * a[:, 1], np.cbrt(a[:, 2])
+    s0 = np.sqrt(np.maximum(0, 1 - z0 * z0))
+    o = np.stack([r0 * s0 * np.cos(p0), r0 * s0 * np.sin(p0), r0 * z0], 1)
+    z1, p1 = 1 - 2 * b[:, 0], 2 * np.pi * b[:, 1]
+    s1 = np.sqrt(np.maximum(0, 1 - z1 * z1))
+    w = np.stack([s1 * np.cos(p1), s1 * np.sin(p1), z1], 1)
+    return o.astype(np.float32), w.astype(np.float32)
+
+
+@pytest.mark.parametrize("F,W,L,seed", [(12, 256, 8, 2), (0, 128, 6, 9)])
+def test_fp8_static_scales_cover_the_activations(P, F, W, L, seed):
+    """Layer 0's scale is 1/448; a hidden layer's is twice the channel's calibration maximum
+    (floored at 1e-3 of the layer's maximum) / 448: compared with the FP64 column maxima on the
+    same 8,192 calibration rays (the library's maxima come from its BF16 forward)."""
+    blob = init_weights(F, W, L, seed=seed)
+    net = P.DDFNet(F, W, L, blob, "fp8")
+    sa = net.fp8_scales().astype(np.float64)
+    assert (sa[0] == np.float32(1 / 448)).all()
+    o, w = _calibration_rays()
+    c = calibration_bound(omlp.unpack(blob, F, W, L), o, w, F)
+    for l in range(1, L):
+        g = sa[l] * 448 / 2
+        assert (g >= 1e-3 * g.max() * (1 - 1e-6)).all()
+        live = c[l] > 0.05 * c[l].max()
+        ratio = g[live] / c[l][live]
+        assert 0.95 <= ratio.min() and ratio.max() <= 1.05, (l, ratio.min(), ratio.max())
+
+
+def test_fp8_scales_follow_set_weights(P):
+    """Repacking after new weights recalibrates: doubling every weight of layer 0 doubles the
+    activations of layer 1 and so its scales (to BF16 rounding)."""
+    F, W, L, seed = 12, 128, 4, 5
+    blob = init_weights(F, W, L, seed=seed)
+    net = P.DDFNet(F, W, L, blob, "fp8")
+    s1 = net.fp8_scales()
+    Pm = omlp.unpack(blob, F, W, L)
+    blob2 = blob.copy()
+    n0 = Pm[0][0].size + Pm[0][1].size
+    blob2[:n0] *= 2
+    net.set_weights(torch.from_numpy(blob2).cuda())
+    s2 = net.fp8_scales()
+    assert (s2[0] == s1[0]).all()
+    r = s2[1] / s1[1]
+    assert np.allclose(r, 2.0, rtol=2e-2), (r.min(), r.max())
