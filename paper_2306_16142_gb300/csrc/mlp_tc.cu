@@ -77,6 +77,7 @@ struct TcArgs {
     uint32_t off_grp;
     int maxL;
     uint32_t* gmask;   // width 512: per-CTA ReLU masks of the reverse pass
+    const uint8_t* bias_mn;   // BF16 pair kernel: [L][32 W bytes] bias operand tiles
     const float* f8_mul;   // FP8 epilogue [L][W]: accumulator multiplier (weight scale / next input scale)
     const float* f8_add;   // FP8 epilogue [L][W]: addend (bias / next input scale)
 };
@@ -147,6 +148,14 @@ __device__ __forceinline__ void release_kb(uint64_t* actr, int kb) {
     fence_proxy_async();
     tc_fence_before();
     mbar_arrive(&actr[kb]);
+}
+// The same with one arrival per warp (barrier count = warps): every lane fences its own stores
+// for the async proxy, the warp synchronises, lane 0 arrives. Call from warp-uniform code.
+__device__ __forceinline__ void release_kb_warp(uint64_t* actr, int kb) {
+    fence_proxy_async();
+    tc_fence_before();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&actr[kb]);
 }
 
 // Input feature order inside the tensor-core path: the six raw coordinates, two zero columns,
@@ -894,6 +903,288 @@ __global__ void __launch_bounds__(kThreads, 1)
 // per output channel, so z[r][n] = acc[r][n] * s_w[n] + b[n] and the next layer's input is
 // E4M3(a[r][k] / s_a[k]). With no per-row reduction, each K-block of the next A operand is
 // quantised and released as soon as its accumulator columns are read.
+// ------------------------------------------------------------------ BF16 forward, tile pairs
+// The forward query (mode 0) on two 128-row tiles per CTA. Both tiles of a pair consume every
+// weight stage (tile 0's MMAs on a K-block, then tile 1's), so a stage is released after both and
+// the weight bytes per row are half those of a one-tile CTA; tile 0's accumulator is committed
+// before tile 1's last K-block, so its epilogue overlaps tile 1's MMAs. Each layer's accumulator starts as the bias: one K = 16 MMA of a ones column
+// (A: M x 16, K rows 0 and 1 equal to 1) by the layer's bias tile (B: K row 0 = bf16(b), row 1 =
+// bf16(b - bf16(b)), both MN-major), streamed with the layer's first weight stage. The epilogue
+// then needs no per-column constants: ReLU and BF16 rounding straight from the accumulator.
+// Shared memory per CTA (W = 256): 2 x 64 KB activation tiles, 2 stages of 32 KB weights + 8 KB
+// bias, the 4 KB ones tile, the output head.
+
+// MN-major 128-byte-swizzled operand of 16 K rows: 64-wide MN atoms 2 KB apart (LBO), the two
+// 8-row K groups 1 KB apart (SBO).
+__device__ __forceinline__ uint64_t sdesc_mn16(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(2048 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads, 1)
+    mlp_pair_kernel(const __grid_constant__ CUtensorMap mapF, const TcArgs a) {
+    constexpr int NKBW = W / 64;
+    constexpr uint32_t kWBytes = (uint32_t)W * 128u;   // one 64-wide K-block of the weights
+    constexpr uint32_t kBBytes = (uint32_t)W * 32u;    // one layer's bias tile
+    constexpr uint32_t kStage = kWBytes + kBBytes;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int L = a.L, KB0 = a.K0 / 64;
+    const int KMAXB = KB0 > NKBW ? KB0 : NKBW;
+    const uint32_t kTile = (uint32_t)KMAXB * 16384u;   // one tile's A operand
+    const int NST = a.nst;
+    uint8_t* act = smem;                                // [tile 0, tile 1] x kTile
+    uint8_t* wst = smem + a.off_wst;                    // NST x kStage
+    uint8_t* ones = smem + a.off_mask;                  // 4 KB
+    float* head_s = reinterpret_cast<float*>(smem + a.off_head);
+    float* part = reinterpret_cast<float*>(smem + a.off_part);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + NST;
+    uint64_t* actr = bars + 2 * NST;   // [tile][K-block], 2 x 4
+    uint64_t* accf = actr + 8;         // [tile]
+    uint64_t* tfree = accf + 2;        // [tile]: the epilogue has read the tile's accumulator
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tfree + 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int64_t n = a.n;
+    if (a.d_count) n = min(n, (int64_t)*a.d_count);
+    const int64_t npairs = (n + 2 * kTileM - 1) / (2 * kTileM);
+    constexpr uint32_t kTmemCols = 2 * W;
+
+    if (tid == 0) {
+        for (int i = 0; i < NST; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 8; ++i) mbar_init(&actr[i], kEpiWarps);
+        mbar_init(&accf[0], 1);
+        mbar_init(&accf[1], 1);
+        mbar_init(&tfree[0], kEpiWarps);
+        mbar_init(&tfree[1], kEpiWarps);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // the ones tile: K rows 0 and 1 of both 64-row MN atoms are 1.0 (BF16 0x3F80), the rest 0
+    for (int i = tid; i < 1024; i += kThreads) {
+        const int line = (i >> 5) & 15;   // K row within the atom (32 words of 4 bytes per line)
+        reinterpret_cast<uint32_t*>(ones)[i] = line < 2 ? 0x3F803F80u : 0u;
+    }
+    fence_proxy_async();
+    for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+
+    if (warp == kEpiWarps) {
+        // ---------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            uint32_t cnt = 0;
+            bool ok = true;
+            for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x)
+                for (int s = 0; s < L && ok; ++s) {
+                    const int nk = s == 0 ? KB0 : NKBW;
+                    for (int kb = 0; kb < nk; ++kb, ++cnt) {
+                        const int stg = (int)(cnt % (uint32_t)NST);
+                        if (!mbar_wait(&empty[stg], ((cnt / (uint32_t)NST) & 1u) ^ 1u, a.err)) { ok = false; break; }
+                        uint8_t* dst = wst + (size_t)stg * kStage;
+                        mbar_expect_tx(&full[stg], kWBytes + (kb == 0 ? kBBytes : 0u));
+                        tma_load_3d(dst, &mapF, &full[stg], kb * 64, 0, s);
+                        if (kb == 0) bulk_load(dst + kWBytes, a.bias_mn + (size_t)s * kBBytes, kBBytes, &full[stg]);
+                    }
+                }
+        }
+    } else if (warp == kEpiWarps + 1) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t cnt = 0, actph = 0, tfph = 0;
+            bool ok = true, first = true;
+            const uint32_t act_s = su32(act), wst_s = su32(wst);
+            const uint32_t idesc = idesc_bf16(128, W);
+            const uint32_t idesc_b = idesc_bf16(128, W) | (3u << 15);   // both operands MN-major
+            const uint64_t ones_d = sdesc_mn16(su32(ones));
+            for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x)
+                for (int s = 0; s < L && ok; ++s) {
+                    // K-block by K-block, tile 0 then tile 1 on each weight stage; a tile's
+                    // accumulator is committed right after its last K-block
+                    const int nk = s == 0 ? KB0 : NKBW;
+                    for (int kb = 0; kb < nk && ok; ++kb, ++cnt) {
+                        const int stg = (int)(cnt % (uint32_t)NST);
+                        if (!mbar_wait(&full[stg], (cnt / (uint32_t)NST) & 1u, a.err)) { ok = false; break; }
+                        const uint32_t sb = wst_s + (uint32_t)stg * kStage;
+                        for (int t = 0; t < 2; ++t) {
+                            const int ab = 4 * t + kb;
+                            if (!mbar_wait(&actr[ab], (actph >> ab) & 1u, a.err)) { ok = false; break; }
+                            actph ^= 1u << ab;
+                            // the bias MMA overwrites the whole accumulator: wait until the
+                            // epilogue has read the tile's previous layer
+                            if (kb == 0 && !first) {
+                                if (!mbar_wait(&tfree[t], (tfph >> t) & 1u, a.err)) { ok = false; break; }
+                                tfph ^= 1u << t;
+                            }
+                            tc_fence_after();
+                            const uint32_t d = tbase + (uint32_t)(t * W);
+                            if (kb == 0) mma_bf16(d, ones_d, sdesc_mn16(sb + kWBytes), idesc_b, 0u);   // D = b
+                            const uint64_t ad = sdesc(act_s + (uint32_t)t * kTile + (uint32_t)kb * 16384u);
+                            const uint64_t bd = sdesc(sb);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, 1u);
+                            if (kb == nk - 1) mma_commit(&accf[t]);
+                        }
+                        if (ok) mma_commit(&empty[stg]);   // both tiles have read the stage
+                    }
+                    first = false;
+                }
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        // warp w serves rows 32 (w % 4) .. +31 of the tile in hand; group w / 4 owns columns
+        // [32 group, +32) of every 64-column K-block
+        const int grp = warp >> 2;
+        const int r = (warp & 3) * 32 + lane;
+        const uint32_t act_s = su32(act);
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        uint32_t accph = 0;
+        bool ok = true;
+        auto load_row = [&](int64_t p, int t, float* vv) {
+            const int64_t i = (2 * p + t) * kTileM + r;
+            const bool valid = p < npairs && i < n;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                vv[c] = valid ? a.o[i * 3 + c] : 0.f;
+                vv[c + 3] = valid ? a.w[i * 3 + c] : 0.f;
+            }
+        };
+        // layer 0 of tile t: group g writes first-layer K-block g; every warp arrives on each
+        auto encode = [&](int t, const float* vv) {
+            if (grp < KB0) {
+                uint32_t pk[32];
+                if (grp == 0) encode_kblock<0>(vv, a.F, pk);
+                else encode_kblock<1>(vv, a.F, pk);
+                const uint32_t base = act_s + (uint32_t)t * kTile + (uint32_t)grp * 16384u;
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    st_shared_v4(base + swz(r, m), pk[4 * m], pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
+            }
+            fence_proxy_async();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0)
+                for (int kb = 0; kb < KB0; ++kb) mbar_arrive(&actr[4 * t + kb]);
+        };
+        float vnext[2][6];
+        if ((int64_t)blockIdx.x < npairs) {
+            load_row(blockIdx.x, 0, vnext[0]);
+            load_row(blockIdx.x, 1, vnext[1]);
+            encode(0, vnext[0]);
+            encode(1, vnext[1]);
+        }
+        for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x) {
+            const int64_t pn = p + gridDim.x;   // the next pair of this CTA
+            for (int s = 0; s < L && ok; ++s) {
+                if (s == L - 1) {
+                    load_row(pn, 0, vnext[0]);
+                    load_row(pn, 1, vnext[1]);
+                }
+                for (int t = 0; t < 2; ++t) {
+                    ok = mbar_wait(&accf[t], (accph >> t) & 1u, a.err);
+                    if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                    accph ^= 1u << t;
+                    tc_fence_after();
+                    const uint32_t tcol = tbase + lane_off + (uint32_t)(t * W) + (uint32_t)(grp * 32);
+                    const uint32_t tact = act_s + (uint32_t)t * kTile;
+                    float y0 = 0.f, y1 = 0.f;
+                    // pairs of K-blocks per TMEM wait
+#pragma unroll
+                    for (int pass = 0; pass < NKBW / 2; ++pass) {
+                        uint32_t raw[2][32];
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) TC_LD32(tcol + (2 * pass + i) * 64, raw[i]);
+                        tc_wait_ld();
+                        if (pass == NKBW / 2 - 1) {   // accumulator read: the next layer may overwrite it
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&tfree[t]);
+                        }
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            const int kb = 2 * pass + i;
+                            const int c0 = kb * 64 + grp * 32;
+                            if (s < L - 1) {
+                                // a = ReLU(acc) rounded to BF16 -> next A operand
+                                uint32_t pk[16];
+#pragma unroll
+                                for (int q = 0; q < 16; ++q)
+                                    pk[q] = pack_relu(__uint_as_float(raw[i][2 * q]), __uint_as_float(raw[i][2 * q + 1]));
+#pragma unroll
+                                for (int m = 0; m < 4; ++m)
+                                    st_shared_v4(tact + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
+                                                 pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
+                                release_kb_warp(actr, 4 * t + kb);
+                            } else {
+                                // output head on this thread's columns (FP32)
+#pragma unroll
+                                for (int c = 0; c < 32; ++c) {
+                                    const float z = fmaxf(__uint_as_float(raw[i][c]), 0.f);
+                                    y0 = fmaf(z, head_s[c0 + c], y0);
+                                    y1 = fmaf(z, head_s[W + c0 + c], y1);
+                                }
+                            }
+                        }
+                    }
+                    if (s == L - 1) {
+                        // outputs, then tile t of the next pair takes over the accumulator
+                        tc_fence_before();
+                        if (grp == 1) {
+                            part[2 * r] = y0;
+                            part[2 * r + 1] = y1;
+                        }
+                        epi_bar();
+                        if (grp == 0) {
+                            const int64_t i = (2 * p + t) * kTileM + r;
+                            const bool valid = i < n;
+                            y0 += part[2 * r] + head_s[2 * W];
+                            y1 += part[2 * r + 1] + head_s[2 * W + 1];
+                            const bool hh = y1 > 0.f;
+                            if (valid) {
+                                a.dist[i] = y0;
+                                if (a.logit) a.logit[i] = y1;
+                                if (a.hit) a.hit[i] = (uint8_t)hh;
+                            }
+                            if (a.hit_list) {
+                                const bool take = valid && hh;
+                                const unsigned m = __ballot_sync(0xffffffffu, take);
+                                int base = 0;
+                                if (lane == 0 && m) base = atomicAdd(a.hit_count, __popc(m));
+                                base = __shfl_sync(0xffffffffu, base, 0);
+                                if (take) a.hit_list[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
+                            }
+                        }
+                        epi_bar();
+                        if (pn < npairs) encode(t, vnext[t]);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (*(volatile int*)a.err) {
+        const uint64_t t0 = gtimer();
+        while (gtimer() - t0 < 200000ull) {
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols));
+    }
+}
+
 __device__ __forceinline__ uint32_t idesc_f8(int M, int N) {
     return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);   // E4M3 x E4M3 -> F32
 }
@@ -941,15 +1232,22 @@ __device__ __forceinline__ void encode_feats64(const float v[6], int F, float fe
     }
 }
 
+// FP8 query, two 128-row tiles per CTA ("pair"). Both tiles of a pair consume every weight stage
+// (half the weight bytes per row of a one-tile CTA) and the tensor pipe alternates between them
+// layer by layer: tile 0's MMAs of layer l, then tile 1's, then tile 0's of layer l + 1, so each
+// tile's epilogue (TMEM load -> scale, bias, ReLU, E4M3 -> next A operand) runs while the other
+// tile is multiplied. TMEM holds one W-column accumulator per tile; a tile's next-layer MMA
+// starts only after its epilogue has read the whole accumulator and written the first K-block.
 template <int W>
 __global__ void __launch_bounds__(kThreads, 1)
     mlp_f8_kernel(const __grid_constant__ CUtensorMap map8, const TcArgs a) {
     constexpr int NKB = W / 128;                     // hidden-layer K-blocks of 128 features
+    constexpr uint32_t kTileAct = (uint32_t)(NKB > 1 ? NKB : 1) * 16384u;   // one tile's A operand
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int L = a.L;
     const int NST = a.nst;
-    uint8_t* act = smem;                             // max(1, NKB) x 16 KB
+    uint8_t* act = smem;                             // [tile 0, tile 1] x kTileAct
     uint8_t* wst = smem + a.off_wst;
     float* mul_s = reinterpret_cast<float*>(smem + a.off_mask);   // epilogue multipliers [L][W]
     float* add_s = reinterpret_cast<float*>(smem + a.off_bias);   // epilogue addends [L][W]
@@ -958,25 +1256,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
     uint64_t* full = bars;
     uint64_t* empty = bars + NST;
-    uint64_t* actr = bars + 2 * NST;   // [2]
-    uint64_t* accf = actr + 2;         // [2]
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 2);
+    uint64_t* actr = bars + 2 * NST;   // [tile][K-block], 2 x 2
+    uint64_t* accf = actr + 4;         // [tile]
+    uint64_t* tfree = accf + 2;        // [tile]: the epilogue has read the tile's accumulator
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tfree + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int64_t n = a.n;
     if (a.d_count) n = min(n, (int64_t)*a.d_count);
-    const int64_t ntiles = (n + kTileM - 1) / kTileM;
-    constexpr uint32_t kTmemCols = W <= 128 ? 256 : 512;
+    const int64_t npairs = (n + 2 * kTileM - 1) / (2 * kTileM);
+    constexpr uint32_t kTmemCols = 2 * W;
 
     if (tid == 0) {
         for (int i = 0; i < NST; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
-        mbar_init(&actr[0], 256);
-        mbar_init(&actr[1], 256);
+        for (int i = 0; i < 4; ++i) mbar_init(&actr[i], kEpiWarps);
         mbar_init(&accf[0], 1);
         mbar_init(&accf[1], 1);
+        mbar_init(&tfree[0], kEpiWarps);
+        mbar_init(&tfree[1], kEpiWarps);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -994,10 +1294,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tbase = *tslot;
 
     if (warp == kEpiWarps) {
+        // ---------------------------------------------------------------- TMA producer
         if (lane == 0) {
             uint32_t cnt = 0;
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
+            for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x)
                 for (int s = 0; s < L && ok; ++s) {
                     const int nk = s == 0 ? 1 : NKB;
                     for (int kb = 0; kb < nk; ++kb, ++cnt) {
@@ -1009,143 +1310,180 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
         }
     } else if (warp == kEpiWarps + 1) {
+        // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            uint32_t cnt = 0, g = 0, actph = 0;
-            bool ok = true;
+            uint32_t cnt = 0, actph = 0, tfph = 0;
+            bool ok = true, first = true;
             const uint32_t act_s = su32(act), wst_s = su32(wst);
             const uint32_t idesc = idesc_f8(128, W);
-            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
-                for (int s = 0; s < L && ok; ++s, ++g) {
+            for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x)
+                for (int s = 0; s < L && ok; ++s) {
                     const int nk = s == 0 ? 1 : NKB;
-                    const uint32_t d = tbase + (g & 1u) * (uint32_t)W;
-                    for (int kb = 0; kb < nk; ++kb, ++cnt) {
-                        const int stg = (int)(cnt % (uint32_t)NST);
-                        if (!mbar_wait(&full[stg], (cnt / (uint32_t)NST) & 1u, a.err)) { ok = false; break; }
-                        if (!mbar_wait(&actr[kb], (actph >> kb) & 1u, a.err)) { ok = false; break; }
-                        actph ^= 1u << kb;
-                        tc_fence_after();
-                        const uint64_t ad = sdesc(act_s + (uint32_t)kb * 16384u);
-                        const uint64_t bd = sdesc(wst_s + (uint32_t)stg * (uint32_t)W * 128u);
+                    for (int t = 0; t < 2 && ok; ++t) {
+                        const uint32_t d = tbase + (uint32_t)(t * W);
+                        for (int kb = 0; kb < nk; ++kb) {
+                            const uint32_t c = cnt + (uint32_t)kb;
+                            const int stg = (int)(c % (uint32_t)NST);
+                            if (t == 0 && !mbar_wait(&full[stg], (c / (uint32_t)NST) & 1u, a.err)) { ok = false; break; }
+                            const int ab = 2 * t + kb;
+                            if (!mbar_wait(&actr[ab], (actph >> ab) & 1u, a.err)) { ok = false; break; }
+                            actph ^= 1u << ab;
+                            // the first MMA overwrites the whole accumulator: wait until the
+                            // epilogue has read the tile's previous layer
+                            if (kb == 0 && !first) {
+                                if (!mbar_wait(&tfree[t], (tfph >> t) & 1u, a.err)) { ok = false; break; }
+                                tfph ^= 1u << t;
+                            }
+                            tc_fence_after();
+                            const uint64_t ad = sdesc(act_s + (uint32_t)t * kTileAct + (uint32_t)kb * 16384u);
+                            const uint64_t bd = sdesc(wst_s + (uint32_t)stg * (uint32_t)W * 128u);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) mma_f8(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
-                        mma_commit(&empty[stg]);
+                            for (int k = 0; k < 4; ++k) mma_f8(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                            if (t == 1) mma_commit(&empty[stg]);   // both tiles have read the stage
+                        }
+                        if (ok) mma_commit(&accf[t]);
                     }
-                    if (ok) mma_commit(&accf[g & 1u]);
+                    cnt += (uint32_t)nk;
+                    first = false;
                 }
         }
     } else {
-        // epilogue: warp w serves rows 32 (w % 4) .. +31; group w / 4 owns the 64 columns
-        // [128 kb + 64 group, +64) of every 128-column K-block
+        // ---------------------------------------------------------------- epilogue
+        // warp w serves rows 32 (w % 4) .. +31 of the tile in hand; group w / 4 owns the 64
+        // columns [128 kb + 64 group, +64) of every 128-column K-block
         const int grp = warp >> 2;
         const int r = (warp & 3) * 32 + lane;
         const uint32_t act_s = su32(act);
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
-        uint32_t g = 0, accph = 0;
+        uint32_t accph = 0;
         bool ok = true;
-        // 16 words of E4M3 bytes (this thread's row, columns [128 kb + 64 group, +64)) into K-block kb
-        auto store64 = [&](int kb, const uint32_t* q) {
+        // 16 words of E4M3 bytes (this thread's row, columns [128 kb + 64 group, +64)) into
+        // K-block kb of tile t's A operand
+        auto store64 = [&](int t, int kb, const uint32_t* q) {
+            const uint32_t base = act_s + (uint32_t)t * kTileAct + (uint32_t)kb * 16384u;
 #pragma unroll
             for (int m = 0; m < 4; ++m)
-                st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), q[4 * m], q[4 * m + 1], q[4 * m + 2],
-                             q[4 * m + 3]);
+                st_shared_v4(base + swz(r, grp * 4 + m), q[4 * m], q[4 * m + 1], q[4 * m + 2], q[4 * m + 3]);
         };
-        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const int64_t i = t * kTileM + r;
-            const bool valid = i < n;
-            const int64_t row = valid ? i : -1;
-            float v[6];
+        auto load_row = [&](int64_t p, int t, float* vv) {
+            const int64_t i = (2 * p + t) * kTileM + r;
+            const bool valid = p < npairs && i < n;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                v[c] = valid ? a.o[row * 3 + c] : 0.f;
-                v[c + 3] = valid ? a.w[row * 3 + c] : 0.f;
+                vv[c] = valid ? a.o[i * 3 + c] : 0.f;
+                vv[c + 3] = valid ? a.w[i * 3 + c] : 0.f;
             }
-            {   // layer 0: features in [-1, 1], fixed input scale 1 / 448
-                float fe[64];
-                if (grp == 0) encode_feats64<0>(v, a.F, fe);
-                else encode_feats64<1>(v, a.F, fe);
-                uint32_t q[16];
+        };
+        // layer 0 of tile t: features in [-1, 1], fixed input scale 1 / 448
+        auto encode = [&](int t, const float* vv) {
+            float fe[64];
+            if (grp == 0) encode_feats64<0>(vv, a.F, fe);
+            else encode_feats64<1>(vv, a.F, fe);
+            uint32_t q[16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    q[i] = pack_e4m3x4(fe[4 * i] * 448.f, fe[4 * i + 1] * 448.f, fe[4 * i + 2] * 448.f,
-                                       fe[4 * i + 3] * 448.f);
-                store64(0, q);
-                release_kb(actr, 0);
-            }
-            float y0 = 0.f, y1 = 0.f;
-            for (int s = 0; s < L && ok; ++s, ++g) {
-                const int b = (int)(g & 1u);
-                ok = mbar_wait(&accf[b], (accph >> b) & 1u, a.err);
-                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
-                accph ^= 1u << b;
-                tc_fence_after();
-                const uint32_t tcol = tbase + lane_off + (uint32_t)(b * W);
+            for (int i = 0; i < 16; ++i)
+                q[i] = pack_e4m3x4(fe[4 * i] * 448.f, fe[4 * i + 1] * 448.f, fe[4 * i + 2] * 448.f, fe[4 * i + 3] * 448.f);
+            store64(t, 0, q);
+            release_kb_warp(actr, 2 * t);
+        };
+        float vnext[2][6];
+        if ((int64_t)blockIdx.x < npairs) {
+            load_row(blockIdx.x, 0, vnext[0]);
+            load_row(blockIdx.x, 1, vnext[1]);
+            encode(0, vnext[0]);
+            encode(1, vnext[1]);
+        }
+        for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x) {
+            const int64_t pn = p + gridDim.x;   // the next pair of this CTA
+            for (int s = 0; s < L && ok; ++s) {
+                if (s == L - 1) {
+                    load_row(pn, 0, vnext[0]);
+                    load_row(pn, 1, vnext[1]);
+                }
+                for (int t = 0; t < 2; ++t) {
+                    ok = mbar_wait(&accf[t], (accph >> t) & 1u, a.err);
+                    if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                    accph ^= 1u << t;
+                    tc_fence_after();
+                    const uint32_t tcol = tbase + lane_off + (uint32_t)(t * W);
+                    float y0 = 0.f, y1 = 0.f;
 #pragma unroll
-                for (int kb = 0; kb < NKB; ++kb) {
-                    // this thread's 64 columns of K-block kb: u = acc m + c (m, c fold the weight
-                    // scale, the bias and the next layer's input scale), then ReLU
-                    uint32_t raw[2][32];
+                    for (int kb = 0; kb < NKB; ++kb) {
+                        // this thread's 64 columns of K-block kb: u = acc m + c (m, c fold the
+                        // weight scale, the bias and the next layer's input scale), then ReLU
+                        uint32_t raw[2][32];
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) TC_LD32(tcol + kb * 128 + grp * 64 + h * 32, raw[h]);
-                    tc_wait_ld();
-                    const int c0 = kb * 128 + grp * 64;
-                    const float4* m4 = reinterpret_cast<const float4*>(mul_s + s * W + c0);
-                    const float4* a4 = reinterpret_cast<const float4*>(add_s + s * W + c0);
-                    if (s < L - 1) {
-                        uint32_t q[16];
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const float4 mm = m4[i], aa = a4[i];
-                            const uint32_t* x = &raw[i >> 3][(4 * i) & 31];
-                            float u0, u1, u2, u3;
-                            fma2p(__uint_as_float(x[0]), __uint_as_float(x[1]), mm.x, mm.y, aa.x, aa.y, u0, u1);
-                            fma2p(__uint_as_float(x[2]), __uint_as_float(x[3]), mm.z, mm.w, aa.z, aa.w, u2, u3);
-                            q[i] = pack_relu_e4m3x4(u0, u1, u2, u3);
+                        for (int h = 0; h < 2; ++h) TC_LD32(tcol + kb * 128 + grp * 64 + h * 32, raw[h]);
+                        tc_wait_ld();
+                        if (kb == NKB - 1) {   // accumulator read: the next layer may overwrite it
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&tfree[t]);
                         }
-                        store64(kb, q);
-                        release_kb(actr, kb);
-                    } else {
+                        const int c0 = kb * 128 + grp * 64;
+                        const float4* m4 = reinterpret_cast<const float4*>(mul_s + s * W + c0);
+                        const float4* a4 = reinterpret_cast<const float4*>(add_s + s * W + c0);
+                        if (s < L - 1) {
+                            uint32_t q[16];
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const float4 mm = m4[i], aa = a4[i];
-                            const uint32_t* x = &raw[i >> 3][(4 * i) & 31];
-                            float u[4];
-                            fma2p(__uint_as_float(x[0]), __uint_as_float(x[1]), mm.x, mm.y, aa.x, aa.y, u[0], u[1]);
-                            fma2p(__uint_as_float(x[2]), __uint_as_float(x[3]), mm.z, mm.w, aa.z, aa.w, u[2], u[3]);
+                            for (int i = 0; i < 16; ++i) {
+                                const float4 mm = m4[i], aa = a4[i];
+                                const uint32_t* x = &raw[i >> 3][(4 * i) & 31];
+                                float u0, u1, u2, u3;
+                                fma2p(__uint_as_float(x[0]), __uint_as_float(x[1]), mm.x, mm.y, aa.x, aa.y, u0, u1);
+                                fma2p(__uint_as_float(x[2]), __uint_as_float(x[3]), mm.z, mm.w, aa.z, aa.w, u2, u3);
+                                q[i] = pack_relu_e4m3x4(u0, u1, u2, u3);
+                            }
+                            store64(t, kb, q);
+                            release_kb_warp(actr, 2 * t + kb);
+                        } else {
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                const float z = fmaxf(u[j], 0.f);
-                                y0 = fmaf(z, head_s[c0 + 4 * i + j], y0);
-                                y1 = fmaf(z, head_s[W + c0 + 4 * i + j], y1);
+                            for (int i = 0; i < 16; ++i) {
+                                const float4 mm = m4[i], aa = a4[i];
+                                const uint32_t* x = &raw[i >> 3][(4 * i) & 31];
+                                float u[4];
+                                fma2p(__uint_as_float(x[0]), __uint_as_float(x[1]), mm.x, mm.y, aa.x, aa.y, u[0], u[1]);
+                                fma2p(__uint_as_float(x[2]), __uint_as_float(x[3]), mm.z, mm.w, aa.z, aa.w, u[2], u[3]);
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) {
+                                    const float z = fmaxf(u[j], 0.f);
+                                    y0 = fmaf(z, head_s[c0 + 4 * i + j], y0);
+                                    y1 = fmaf(z, head_s[W + c0 + 4 * i + j], y1);
+                                }
                             }
                         }
                     }
-                }
-                if (s == L - 1) {
-                    tc_fence_before();
-                    if (grp == 1) {
-                        part[2 * r] = y0;
-                        part[2 * r + 1] = y1;
-                    }
-                    epi_bar();
-                    if (grp == 0) {
-                        y0 += part[2 * r] + head_s[2 * W];
-                        y1 += part[2 * r + 1] + head_s[2 * W + 1];
-                        const bool hh = y1 > 0.f;
-                        if (valid) {
-                            a.dist[row] = y0;
-                            if (a.logit) a.logit[row] = y1;
-                            if (a.hit) a.hit[row] = (uint8_t)hh;
+                    if (s == L - 1) {
+                        // output head, then tile t of the next pair takes over the accumulator
+                        tc_fence_before();
+                        if (grp == 1) {
+                            part[2 * r] = y0;
+                            part[2 * r + 1] = y1;
                         }
-                        if (a.hit_list) {
-                            const bool take = valid && hh;
-                            const unsigned m = __ballot_sync(0xffffffffu, take);
-                            int base = 0;
-                            if (lane == 0 && m) base = atomicAdd(a.hit_count, __popc(m));
-                            base = __shfl_sync(0xffffffffu, base, 0);
-                            if (take) a.hit_list[base + __popc(m & ((1u << lane) - 1u))] = (int)row;
+                        epi_bar();
+                        if (grp == 0) {
+                            const int64_t i = (2 * p + t) * kTileM + r;
+                            const bool valid = i < n;
+                            y0 += part[2 * r] + head_s[2 * W];
+                            y1 += part[2 * r + 1] + head_s[2 * W + 1];
+                            const bool hh = y1 > 0.f;
+                            if (valid) {
+                                a.dist[i] = y0;
+                                if (a.logit) a.logit[i] = y1;
+                                if (a.hit) a.hit[i] = (uint8_t)hh;
+                            }
+                            if (a.hit_list) {
+                                const bool take = valid && hh;
+                                const unsigned m = __ballot_sync(0xffffffffu, take);
+                                int base = 0;
+                                if (lane == 0 && m) base = atomicAdd(a.hit_count, __popc(m));
+                                base = __shfl_sync(0xffffffffu, base, 0);
+                                if (take) a.hit_list[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
+                            }
                         }
+                        epi_bar();
+                        if (pn < npairs) encode(t, vnext[t]);
                     }
-                    epi_bar();
                 }
             }
         }
@@ -1276,6 +1614,28 @@ __global__ void pack_f8_kernel(const float* __restrict__ master, NetLayout lay, 
     }
 }
 
+// Bias of layer l as the B operand of the pair kernel's bias MMA: a 16 x W BF16 MN-major tile
+// with 128-byte swizzle (64-wide MN atoms of 16 K rows, 2 KB apart; element (k, m) of an atom at
+// k * 128 + (((m / 8) ^ (k % 8)) * 16) + (m % 8) * 2). K row 0 = bf16(b[n]), K row 1 =
+// bf16(b[n] - bf16(b[n])), rows 2..15 zero. One block per layer.
+__global__ void pack_bias_mn_kernel(const float* __restrict__ master, NetLayout lay, uint8_t* __restrict__ out) {
+    const int l = blockIdx.x, W = lay.width;
+    uint8_t* dst = out + (size_t)l * W * 32;
+    for (int i = threadIdx.x; i < W * 8; i += blockDim.x) reinterpret_cast<uint32_t*>(dst)[i] = 0u;
+    __syncthreads();
+    for (int nn = threadIdx.x; nn < W; nn += blockDim.x) {
+        const float b = master[lay.b_off[l] + nn];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(b - __bfloat162float(hi));
+        const int m = nn & 63;
+        for (int k = 0; k < 2; ++k) {
+            const uint32_t off = (uint32_t)(nn >> 6) * 2048u + (uint32_t)k * 128u + ((uint32_t)((m >> 3) ^ k) << 4) +
+                                 (uint32_t)(m & 7) * 2u;
+            *reinterpret_cast<__nv_bfloat16*>(dst + off) = k == 0 ? hi : lo;
+        }
+    }
+}
+
 int make_map(CUtensorMap* m, void* base, int inner, int rows, int L) {
     EncodeTiledFn enc = get_encode();
     if (!enc) return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
@@ -1380,9 +1740,57 @@ int launch_mode(const ddf_net_s* net, int mode, const TcArgs& base, int64_t n, b
     return DDF_OK;
 }
 
+Layout smem_layout_pair(int W, int K0) {
+    Layout s{};
+    const int kmaxb = std::max(K0 / 64, W / 64);
+    const uint32_t act = 2u * (uint32_t)kmaxb * 16384u;   // two tiles
+    const uint32_t stage = (uint32_t)W * 160u;            // weights K-block + bias tile
+    const uint32_t ones = 4096u;
+    const uint32_t head = ((uint32_t)(2 * W + 2) * 4u + 15u) & ~15u;
+    const uint32_t partb = 128u * 2u * 4u;
+    const uint32_t fixed = act + ones + head + partb + 512u;
+    const uint32_t budget = 227u * 1024u - 1024u;
+    s.nst = std::max(0, std::min(8, (int)((budget - fixed) / stage)));
+    s.off_wst = act;
+    s.off_mask = act + (uint32_t)s.nst * stage;   // ones tile (1 KB aligned: stages are multiples of 1 KB)
+    s.off_bias = 0;
+    s.off_grp = 0;
+    s.off_head = s.off_mask + ones;
+    s.off_part = s.off_head + head;
+    s.off_bar = s.off_part + partb;
+    s.total = s.off_bar + 512u + 1024u;
+    return s;
+}
+
+template <int W>
+int launch_pair(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_count, cudaStream_t stream) {
+    const TcPack* P = net->tc;
+    TcArgs a = base;
+    const Layout s = smem_layout_pair(W, a.K0);
+    if (s.nst < 2) return fail(DDF_ERR_UNSUPPORTED, "BF16 pair MLP: shared memory too small");
+    a.nst = s.nst;
+    a.off_wst = s.off_wst;
+    a.off_mask = s.off_mask;
+    a.off_head = s.off_head;
+    a.off_part = s.off_part;
+    a.off_bar = s.off_bar;
+    a.bias_mn = P->bias_mn;
+    // one CTA per SM, each walking pairs of 128-row tiles
+    int grid = use_count ? num_sms() : (int)std::min<int64_t>((n + 2 * kTileM - 1) / (2 * kTileM), num_sms());
+    if (grid <= 0) return DDF_OK;
+    static bool attr = false;
+    if (!attr) {
+        DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_pair_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr = true;
+    }
+    mlp_pair_kernel<W><<<grid, kThreads, s.total, stream>>>(P->map_fwd, a);
+    DDF_LAUNCH_CHECK();
+    return DDF_OK;
+}
+
 Layout smem_layout_f8(int W, int L) {
     Layout s{};
-    const uint32_t act = (uint32_t)std::max(1, W / 128) * 16384u;
+    const uint32_t act = 2u * (uint32_t)std::max(1, W / 128) * 16384u;   // two tiles
     const uint32_t stage = (uint32_t)W * 128u;
     const uint32_t vec = (uint32_t)L * W * 4u;
     const uint32_t head = ((uint32_t)(2 * W + 2) * 4u + 15u) & ~15u;
@@ -1416,7 +1824,8 @@ int launch_f8(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_coun
     a.off_bar = s.off_bar;
     a.f8_mul = P->ep8;
     a.f8_add = P->ep8 + (size_t)a.L * W;
-    int grid = use_count ? num_sms() : (int)std::min<int64_t>((n + kTileM - 1) / kTileM, num_sms());
+    // one CTA per SM, each walking pairs of 128-row tiles
+    int grid = use_count ? num_sms() : (int)std::min<int64_t>((n + 2 * kTileM - 1) / (2 * kTileM), num_sms());
     if (grid <= 0) return DDF_OK;
     static bool attr = false;
     if (!attr) {
@@ -1495,6 +1904,7 @@ void tc_free(ddf_net_s* net) {
     cudaFree(P->w_bwd);
     cudaFree(P->bias);
     cudaFree(P->head);
+    cudaFree(P->bias_mn);
     cudaFree(P->hit_list);
     cudaFree(P->hit_count);
     cudaFree(P->err);
@@ -1522,6 +1932,7 @@ int tc_pack(ddf_net_s* net, int precision, cudaStream_t stream) {
         DDF_CUDA_TRY(cudaMalloc(&P->w_bwd, sizeof(__nv_bfloat16) * (size_t)L * W * W));
         DDF_CUDA_TRY(cudaMalloc(&P->bias, sizeof(float) * (size_t)L * W));
         DDF_CUDA_TRY(cudaMalloc(&P->head, sizeof(float) * (size_t)(2 * W + 2)));
+        if (W <= 256) DDF_CUDA_TRY(cudaMalloc(&P->bias_mn, (size_t)L * W * 32));
         DDF_CUDA_TRY(cudaMalloc(&P->hit_count, sizeof(int)));
         DDF_CUDA_TRY(cudaMalloc(&P->err, sizeof(int)));
         DDF_CUDA_TRY(cudaMemset(P->err, 0, sizeof(int)));
@@ -1536,6 +1947,10 @@ int tc_pack(ddf_net_s* net, int precision, cudaStream_t stream) {
     dim3 grid(64, L);
     pack_kernel<<<grid, 256, 0, stream>>>(net->master, lay, P->kmax, P->w_fwd, P->w_bwd, P->bias, P->head);
     DDF_LAUNCH_CHECK();
+    if (P->bias_mn) {
+        pack_bias_mn_kernel<<<L, 256, 0, stream>>>(net->master, lay, P->bias_mn);
+        DDF_LAUNCH_CHECK();
+    }
     if (precision == DDF_FP8) {
         if (!P->w8) {
             P->kmax8 = std::max(128, W);
@@ -1595,8 +2010,8 @@ int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n
         rc = lay.width == 128 ? launch_f8<128>(net, a, n, d_count != nullptr, stream)
                               : launch_f8<256>(net, a, n, d_count != nullptr, stream);
     else
-        rc = lay.width == 128   ? launch_mode<128>(net, 0, a, n, d_count != nullptr, stream)
-             : lay.width == 256 ? launch_mode<256>(net, 0, a, n, d_count != nullptr, stream)
+        rc = lay.width == 128   ? launch_pair<128>(net, a, n, d_count != nullptr, stream)
+             : lay.width == 256 ? launch_pair<256>(net, a, n, d_count != nullptr, stream)
                                 : launch512(net, 0, a, n, d_count != nullptr, stream);
     if (rc || !normals) return rc;
     TcArgs b = a;
@@ -1718,8 +2133,8 @@ extern "C" DDF_API int ddf_query_noalloc(ddf_net net, const float* d_origins, co
     if (net->precision == DDF_FP8)
         rc = lay.width == 128 ? launch_f8<128>(net, a, n, false, stream) : launch_f8<256>(net, a, n, false, stream);
     else
-        rc = lay.width == 128 ? launch_mode<128>(net, 0, a, n, false, stream)
-                              : launch_mode<256>(net, 0, a, n, false, stream);
+        rc = lay.width == 128 ? launch_pair<128>(net, a, n, false, stream)
+                              : launch_pair<256>(net, a, n, false, stream);
     if (rc) return rc;
     TcArgs b = a;
     b.rows = hit_list;

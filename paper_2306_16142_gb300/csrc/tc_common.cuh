@@ -17,6 +17,7 @@ struct TcPack {
     __nv_bfloat16* w_bwd = nullptr;   // [L][W][W]     W_l^T [in][out], layer-0 rows padded to W
     float* bias = nullptr;            // [L][W]
     float* head = nullptr;            // W_out [2][W], b_out [2]
+    uint8_t* bias_mn = nullptr;       // [L][32 W bytes] biases as 16 x W BF16 MN-major MMA operands
     CUtensorMap map_fwd, map_bwd;
     int* hit_list = nullptr;
     int64_t hit_cap = 0;
@@ -90,6 +91,14 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
         ::"r"(su32(dst)), "l"(map), "r"(su32(bar)), "r"(c0), "r"(c1), "r"(c2)
         : "memory");
+}
+
+// One-dimensional bulk copy global -> shared (16-byte aligned, size a multiple of 16), completing
+// on an mbarrier's transaction count.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(su32(dst)), "l"(src), "r"(bytes), "r"(su32(bar))
+                 : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
