@@ -78,8 +78,7 @@ struct TcArgs {
     int maxL;
     uint32_t* gmask;   // width 512: per-CTA ReLU masks of the reverse pass
     const uint8_t* bias_mn;   // BF16 pair kernel: [L][32 W bytes] bias operand tiles
-    const float* f8_mul;   // FP8 epilogue [L][W]: accumulator multiplier (weight scale / next input scale)
-    const float* f8_add;   // FP8 epilogue [L][W]: addend (bias / next input scale)
+    const float* f8_emul;   // FP8 epilogue [L]: accumulator multiplier mu_l
 };
 
 
@@ -1249,8 +1248,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int NST = a.nst;
     uint8_t* act = smem;                             // [tile 0, tile 1] x kTileAct
     uint8_t* wst = smem + a.off_wst;
-    float* mul_s = reinterpret_cast<float*>(smem + a.off_mask);   // epilogue multipliers [L][W]
-    float* add_s = reinterpret_cast<float*>(smem + a.off_bias);   // epilogue addends [L][W]
+    uint8_t* ones = smem + a.off_mask;                            // 4 KB
+    uint8_t* bslot = smem + a.off_bias;                           // the current layer's bias tile
+    float* emul_s = reinterpret_cast<float*>(smem + a.off_grp);   // mu_l
     float* head_s = reinterpret_cast<float*>(smem + a.off_head);
     float* part = reinterpret_cast<float*>(smem + a.off_part);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
@@ -1259,7 +1259,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* actr = bars + 2 * NST;   // [tile][K-block], 2 x 2
     uint64_t* accf = actr + 4;         // [tile]
     uint64_t* tfree = accf + 2;        // [tile]: the epilogue has read the tile's accumulator
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(tfree + 2);
+    uint64_t* bfull = tfree + 2;       // bias slot loaded / consumed
+    uint64_t* bempty = bfull + 1;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bempty + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int64_t n = a.n;
@@ -1277,6 +1279,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_init(&accf[1], 1);
         mbar_init(&tfree[0], kEpiWarps);
         mbar_init(&tfree[1], kEpiWarps);
+        mbar_init(bfull, 1);
+        mbar_init(bempty, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -1284,10 +1288,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    for (int i = tid; i < L * W; i += kThreads) {
-        mul_s[i] = a.f8_mul[i];
-        add_s[i] = a.f8_add[i];
-    }
+    // the ones tile: K rows 0 and 1 of both 64-row MN atoms are 1.0 (BF16 0x3F80), the rest 0
+    for (int i = tid; i < 1024; i += kThreads)
+        reinterpret_cast<uint32_t*>(ones)[i] = ((i >> 5) & 15) < 2 ? 0x3F803F80u : 0u;
+    fence_proxy_async();
+    for (int i = tid; i < L; i += kThreads) emul_s[i] = a.f8_emul[i];
     for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
     __syncthreads();
     tc_fence_after();
@@ -1296,10 +1301,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == kEpiWarps) {
         // ---------------------------------------------------------------- TMA producer
         if (lane == 0) {
-            uint32_t cnt = 0;
+            uint32_t cnt = 0, nb = 0;
             bool ok = true;
             for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x)
-                for (int s = 0; s < L && ok; ++s) {
+                for (int s = 0; s < L && ok; ++s, ++nb) {
+                    if (!mbar_wait(bempty, (nb & 1u) ^ 1u, a.err)) { ok = false; break; }
+                    mbar_expect_tx(bfull, (uint32_t)W * 32u);
+                    bulk_load(bslot, a.bias_mn + (size_t)s * W * 32, (uint32_t)W * 32u, bfull);
                     const int nk = s == 0 ? 1 : NKB;
                     for (int kb = 0; kb < nk; ++kb, ++cnt) {
                         const int stg = (int)(cnt % (uint32_t)NST);
@@ -1312,13 +1320,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == kEpiWarps + 1) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            uint32_t cnt = 0, actph = 0, tfph = 0;
+            uint32_t cnt = 0, actph = 0, tfph = 0, nb = 0;
             bool ok = true, first = true;
             const uint32_t act_s = su32(act), wst_s = su32(wst);
             const uint32_t idesc = idesc_f8(128, W);
+            const uint32_t idesc_b = idesc_bf16(128, W) | (3u << 15);   // bias MMA: both operands MN-major
+            const uint64_t ones_d = sdesc_mn16(su32(ones)), bias_d = sdesc_mn16(su32(bslot));
             for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x)
-                for (int s = 0; s < L && ok; ++s) {
+                for (int s = 0; s < L && ok; ++s, ++nb) {
                     const int nk = s == 0 ? 1 : NKB;
+                    if (!mbar_wait(bfull, nb & 1u, a.err)) { ok = false; break; }
                     for (int t = 0; t < 2 && ok; ++t) {
                         const uint32_t d = tbase + (uint32_t)(t * W);
                         for (int kb = 0; kb < nk; ++kb) {
@@ -1335,10 +1346,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 tfph ^= 1u << t;
                             }
                             tc_fence_after();
+                            if (kb == 0) {   // D = b / s_w (BF16 MMA into the same FP32 accumulator)
+                                mma_bf16(d, ones_d, bias_d, idesc_b, 0u);
+                                if (t == 1) mma_commit(bempty);
+                            }
                             const uint64_t ad = sdesc(act_s + (uint32_t)t * kTileAct + (uint32_t)kb * 16384u);
                             const uint64_t bd = sdesc(wst_s + (uint32_t)stg * (uint32_t)W * 128u);
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) mma_f8(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                            for (int k = 0; k < 4; ++k) mma_f8(d, ad + 2 * k, bd + 2 * k, idesc, 1u);
                             if (t == 1) mma_commit(&empty[stg]);   // both tiles have read the stage
                         }
                         if (ok) mma_commit(&accf[t]);
@@ -1408,9 +1423,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t tcol = tbase + lane_off + (uint32_t)(t * W);
                     float y0 = 0.f, y1 = 0.f;
 #pragma unroll
+                    const float mu = emul_s[s];
                     for (int kb = 0; kb < NKB; ++kb) {
-                        // this thread's 64 columns of K-block kb: u = acc m + c (m, c fold the
-                        // weight scale, the bias and the next layer's input scale), then ReLU
+                        // this thread's 64 columns of K-block kb: the accumulator holds z / s_w;
+                        // the next input code is E4M3(ReLU(acc mu)) (mu = s_w / s_a')
                         uint32_t raw[2][32];
 #pragma unroll
                         for (int h = 0; h < 2; ++h) TC_LD32(tcol + kb * 128 + grp * 64 + h * 32, raw[h]);
@@ -1421,35 +1437,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if (lane == 0) mbar_arrive(&tfree[t]);
                         }
                         const int c0 = kb * 128 + grp * 64;
-                        const float4* m4 = reinterpret_cast<const float4*>(mul_s + s * W + c0);
-                        const float4* a4 = reinterpret_cast<const float4*>(add_s + s * W + c0);
                         if (s < L - 1) {
                             uint32_t q[16];
 #pragma unroll
                             for (int i = 0; i < 16; ++i) {
-                                const float4 mm = m4[i], aa = a4[i];
                                 const uint32_t* x = &raw[i >> 3][(4 * i) & 31];
                                 float u0, u1, u2, u3;
-                                fma2p(__uint_as_float(x[0]), __uint_as_float(x[1]), mm.x, mm.y, aa.x, aa.y, u0, u1);
-                                fma2p(__uint_as_float(x[2]), __uint_as_float(x[3]), mm.z, mm.w, aa.z, aa.w, u2, u3);
+                                mul2p(__uint_as_float(x[0]), __uint_as_float(x[1]), mu, u0, u1);
+                                mul2p(__uint_as_float(x[2]), __uint_as_float(x[3]), mu, u2, u3);
                                 q[i] = pack_relu_e4m3x4(u0, u1, u2, u3);
                             }
                             store64(t, kb, q);
                             release_kb_warp(actr, 2 * t + kb);
                         } else {
+                            // output head (s_w folded into its weights), FP32
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                const float4 mm = m4[i], aa = a4[i];
-                                const uint32_t* x = &raw[i >> 3][(4 * i) & 31];
-                                float u[4];
-                                fma2p(__uint_as_float(x[0]), __uint_as_float(x[1]), mm.x, mm.y, aa.x, aa.y, u[0], u[1]);
-                                fma2p(__uint_as_float(x[2]), __uint_as_float(x[3]), mm.z, mm.w, aa.z, aa.w, u[2], u[3]);
-#pragma unroll
-                                for (int j = 0; j < 4; ++j) {
-                                    const float z = fmaxf(u[j], 0.f);
-                                    y0 = fmaf(z, head_s[c0 + 4 * i + j], y0);
-                                    y1 = fmaf(z, head_s[W + c0 + 4 * i + j], y1);
-                                }
+                            for (int c = 0; c < 64; ++c) {
+                                const float z = fmaxf(__uint_as_float(raw[c >> 5][c & 31]), 0.f);
+                                y0 = fmaf(z, head_s[c0 + c], y0);
+                                y1 = fmaf(z, head_s[W + c0 + c], y1);
                             }
                         }
                     }
@@ -1532,11 +1538,13 @@ __global__ void pack_kernel(const float* __restrict__ master, NetLayout lay, int
 // FP8 E4M3 copy of the hidden layers with static activation scales. Input channel k of layer l
 // carries the scale s_a[l][k] (layer 0, whose features lie in [-1, 1]: 1 / 448; hidden layers:
 // twice the channel's calibration maximum / 448, floored at 1e-3 of the layer's maximum), folded
-// into the weights: W'[n][k] = W[n][k] s_a[l][k]. One block per output channel n of layer l;
-// s_w[l][n] = max_k |W'[n][k]| / 448 (1 for an all-zero row), byte = E4M3(W'[n][k] / s_w[l][n]),
-// layer 0 in the internal feature order. The query kernel then forms the next layer's input
-// code as E4M3(ReLU(acc m + c)) with m = s_w[l][n] / s_a[l + 1][n], c = b[l][n] / s_a[l + 1][n]
-// (the last hidden layer: m = s_w, c = b, ReLU, then the FP32 head).
+// into the weights: W'[n][k] = W[n][k] s_a[l][k]. Output channel n of layer l < L - 1 gets the
+// weight scale s_w[l][n] = mu_l s_a[l + 1][n], tied to the next layer's input scale of the same
+// unit, with mu_l = max_n max_k |W'[n][k]| / (448 s_a[l + 1][n]) so that the largest code is 448;
+// the last hidden layer gets s_w[n] = max_k |W'[n][k]| / 448. byte = E4M3(W'[n][k] / s_w[l][n]),
+// layer 0 in the internal feature order. The accumulator, started at b / s_w by the bias MMA,
+// approximates z / s_w, so the next layer's input code is E4M3(ReLU(acc mu_l)) with one scalar per
+// layer, and the last layer's s_w folds into the FP32 output head.
 __device__ float f8_layer_max(const float* __restrict__ amax, int l, int W, float* red) {
     float lmax = 0.f;
     for (int k = threadIdx.x; k < W; k += blockDim.x) lmax = fmaxf(lmax, amax[(int64_t)l * W + k]);
@@ -1555,62 +1563,96 @@ __device__ __forceinline__ float f8_act_scale(float amax_k, float lmax) {
     return 2.f * fmaxf(amax_k, floor_) / 448.f;
 }
 
-__global__ void pack_f8_kernel(const float* __restrict__ master, NetLayout lay, int kmax8, uint8_t* __restrict__ w8,
-                               float* __restrict__ sw8, const float* __restrict__ amax, float* __restrict__ sa8,
-                               float* __restrict__ ep8) {
+// Block maximum of v over the block's threads (every thread gets the result).
+__device__ float f8_block_max(float v, float* red) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    v = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) v = fmaxf(v, red[i]);
+    return v;
+}
+
+// s_a of every layer: one block per layer.
+__global__ void f8_act_scales_kernel(const float* __restrict__ amax, int W, float* __restrict__ sa8) {
+    __shared__ float red[32];
+    const int l = blockIdx.x;
+    const float lmax = l > 0 ? f8_layer_max(amax, l, W, red) : 0.f;
+    for (int k = threadIdx.x; k < W; k += blockDim.x)
+        sa8[(int64_t)l * W + k] = l == 0 ? 1.f / 448.f : f8_act_scale(amax[(int64_t)l * W + k], lmax);
+}
+
+// rmax[l][n] = max_k |W[n][k] s_a[l][k]|: one block per (n, l).
+__global__ void f8_rowmax_kernel(const float* __restrict__ master, NetLayout lay, const float* __restrict__ sa8,
+                                 float* __restrict__ rmax) {
+    __shared__ float red[32];
+    const int l = blockIdx.y, nrow = blockIdx.x, W = lay.width;
+    const int in = l == 0 ? lay.E : W;
+    const float* Wrow = master + lay.w_off[l] + (int64_t)nrow * in;
+    float mx = 0.f;
+    for (int k = threadIdx.x; k < in; k += blockDim.x)
+        mx = fmaxf(mx, fabsf(Wrow[k] * (l == 0 ? 1.f / 448.f : sa8[(int64_t)l * W + k])));
+    mx = f8_block_max(mx, red);
+    if (threadIdx.x == 0) rmax[(int64_t)l * W + nrow] = mx;
+}
+
+// Quantised weights, weight scales, the bias operand tiles (b / s_w, BF16 hi + lo, MN-major as in
+// pack_bias_mn_kernel), mu_l and the folded head: one block per (n, l).
+__global__ void f8_quant_kernel(const float* __restrict__ master, NetLayout lay, int kmax8,
+                                const float* __restrict__ sa8, const float* __restrict__ rmax,
+                                uint8_t* __restrict__ w8, float* __restrict__ sw8, float* __restrict__ emul8,
+                                uint8_t* __restrict__ bias_mn, float* __restrict__ head8) {
+    __shared__ float red[32];
     const int l = blockIdx.y, nrow = blockIdx.x, W = lay.width, L = lay.L;
     const int in = l == 0 ? lay.E : W;
     const float* Wrow = master + lay.w_off[l] + (int64_t)nrow * in;
-    __shared__ float red[32];
-    __shared__ float sa_s[kMaxWidth];
-    // this layer's input scales (every block of the layer computes the same values)
-    const float lmax = l > 0 ? f8_layer_max(amax, l, W, red) : 0.f;
-    for (int k = threadIdx.x; k < W; k += blockDim.x) {
-        const float sa = l == 0 ? 1.f / 448.f : f8_act_scale(amax[(int64_t)l * W + k], lmax);
-        sa_s[k] = sa;
-        if (nrow == 0) sa8[(int64_t)l * W + k] = sa;
+    float sw;
+    if (l + 1 < L) {
+        float mu = 0.f;
+        for (int c = threadIdx.x; c < W; c += blockDim.x)
+            mu = fmaxf(mu, rmax[(int64_t)l * W + c] / (448.f * sa8[(int64_t)(l + 1) * W + c]));
+        mu = f8_block_max(mu, red);
+        if (!(mu > 0.f)) mu = 1.f;
+        sw = mu * sa8[(int64_t)(l + 1) * W + nrow];
+        if (nrow == 0 && threadIdx.x == 0) emul8[l] = mu;
+    } else {
+        const float r = rmax[(int64_t)l * W + nrow];
+        sw = r > 0.f ? r / 448.f : 1.f;
+        if (nrow == 0 && threadIdx.x == 0) emul8[l] = 1.f;
     }
-    // the next layer's input scale of channel nrow (the same arithmetic as that layer's blocks)
-    const float lmax_next = l + 1 < L ? f8_layer_max(amax, l + 1, W, red) : 0.f;
-    __syncthreads();
-    auto wk = [&](int k) -> float {   // W'[nrow][internal column k]
-        const int src = l == 0 ? in_feature(k) : k;
-        if (src < 0 || src >= in) return 0.f;
-        return Wrow[src] * (l == 0 ? 1.f / 448.f : sa_s[k]);
-    };
-    float mx = 0.f;
-    for (int k = threadIdx.x; k < kmax8; k += blockDim.x) mx = fmaxf(mx, fabsf(wk(k)));
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        mx = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-        if (threadIdx.x == 0) red[0] = mx;
-    }
-    __syncthreads();
-    const float sc = red[0] > 0.f ? red[0] / 448.f : 1.f;
-    if (threadIdx.x == 0) {
-        const float bn = master[lay.b_off[l] + nrow];
-        sw8[(int64_t)l * W + nrow] = sc;
-        float m = sc, c = bn;
-        if (l + 1 < L) {
-            const float inv_next = 1.f / f8_act_scale(amax[(int64_t)(l + 1) * W + nrow], lmax_next);
-            m = sc * inv_next;
-            c = bn * inv_next;
-        }
-        ep8[(int64_t)l * W + nrow] = m;
-        ep8[(int64_t)(L + l) * W + nrow] = c;
-    }
-    const float inv = 1.f / sc;
+    const float inv = 1.f / sw;
     uint8_t* dst = w8 + ((int64_t)l * W + nrow) * kmax8;
     for (int k = threadIdx.x; k < kmax8; k += blockDim.x) {
-        const float x = wk(k) * inv;
+        const int src = l == 0 ? in_feature(k) : k;
+        const float x = src >= 0 && src < in ? Wrow[src] * (l == 0 ? 1.f / 448.f : sa8[(int64_t)l * W + k]) * inv : 0.f;
         unsigned short h;
         asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(h) : "f"(0.f), "f"(x));
         dst[k] = (uint8_t)(h & 0xffu);
+    }
+    if (threadIdx.x == 0) {
+        sw8[(int64_t)l * W + nrow] = sw;
+        // bias operand: rows 0 / 1 of the 16 x W tile (the rest was zeroed by the caller)
+        const float b = master[lay.b_off[l] + nrow] * inv;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(b - __bfloat162float(hi));
+        const int m = nrow & 63;
+        uint8_t* bt = bias_mn + (size_t)l * W * 32;
+        for (int k = 0; k < 2; ++k) {
+            const uint32_t off = (uint32_t)(nrow >> 6) * 2048u + (uint32_t)k * 128u + ((uint32_t)((m >> 3) ^ k) << 4) +
+                                 (uint32_t)(m & 7) * 2u;
+            *reinterpret_cast<__nv_bfloat16*>(bt + off) = k == 0 ? hi : lo;
+        }
+        if (l == L - 1) {
+            const float* hw = master + lay.w_off[L];
+            head8[nrow] = hw[nrow] * sw;
+            head8[W + nrow] = hw[W + nrow] * sw;
+            if (nrow == 0) {
+                head8[2 * W] = master[lay.b_off[L]];
+                head8[2 * W + 1] = master[lay.b_off[L] + 1];
+            }
+        }
     }
 }
 
@@ -1792,17 +1834,19 @@ Layout smem_layout_f8(int W, int L) {
     Layout s{};
     const uint32_t act = 2u * (uint32_t)std::max(1, W / 128) * 16384u;   // two tiles
     const uint32_t stage = (uint32_t)W * 128u;
-    const uint32_t vec = (uint32_t)L * W * 4u;
+    const uint32_t ones = 4096u;
+    const uint32_t bias = (uint32_t)W * 32u;
+    const uint32_t emul = ((uint32_t)L * 4u + 15u) & ~15u;
     const uint32_t head = ((uint32_t)(2 * W + 2) * 4u + 15u) & ~15u;
     const uint32_t partb = 128u * 2u * 4u;
-    const uint32_t fixed = act + 2 * vec + head + partb + 512u;
+    const uint32_t fixed = act + ones + bias + emul + head + partb + 512u;
     const uint32_t budget = 227u * 1024u - 1024u;
     s.nst = std::max(0, std::min(8, (int)((budget - fixed) / stage)));
     s.off_wst = act;
-    s.off_mask = act + (uint32_t)s.nst * stage;   // epilogue multipliers
-    s.off_bias = s.off_mask + vec;                 // epilogue addends
-    s.off_grp = 0;
-    s.off_head = s.off_bias + vec;
+    s.off_mask = act + (uint32_t)s.nst * stage;   // ones tile (1 KB aligned: stages are multiples of 1 KB)
+    s.off_bias = s.off_mask + ones;               // bias slot (1 KB aligned)
+    s.off_grp = s.off_bias + bias;                // mu_l
+    s.off_head = s.off_grp + emul;
     s.off_part = s.off_head + head;
     s.off_bar = s.off_part + partb;
     s.total = s.off_bar + 512u + 1024u;
@@ -1819,11 +1863,13 @@ int launch_f8(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_coun
     a.off_wst = s.off_wst;
     a.off_mask = s.off_mask;
     a.off_bias = s.off_bias;
+    a.off_grp = s.off_grp;
     a.off_head = s.off_head;
     a.off_part = s.off_part;
     a.off_bar = s.off_bar;
-    a.f8_mul = P->ep8;
-    a.f8_add = P->ep8 + (size_t)a.L * W;
+    a.f8_emul = P->emul8;
+    a.bias_mn = P->bias8_mn;
+    a.head = P->head8;
     // one CTA per SM, each walking pairs of 128-row tiles
     int grid = use_count ? num_sms() : (int)std::min<int64_t>((n + 2 * kTileM - 1) / (2 * kTileM), num_sms());
     if (grid <= 0) return DDF_OK;
@@ -1912,7 +1958,10 @@ void tc_free(ddf_net_s* net) {
     cudaFree(P->w8);
     cudaFree(P->sw8);
     cudaFree(P->sa8);
-    cudaFree(P->ep8);
+    cudaFree(P->rmax8);
+    cudaFree(P->emul8);
+    cudaFree(P->head8);
+    cudaFree(P->bias8_mn);
     cudaFree(P->amax8);
     delete P;
     net->tc = nullptr;
@@ -1957,7 +2006,10 @@ int tc_pack(ddf_net_s* net, int precision, cudaStream_t stream) {
             DDF_CUDA_TRY(cudaMalloc(&P->w8, (size_t)L * W * P->kmax8));
             DDF_CUDA_TRY(cudaMalloc(&P->sw8, sizeof(float) * (size_t)L * W));
             DDF_CUDA_TRY(cudaMalloc(&P->sa8, sizeof(float) * (size_t)L * W));
-            DDF_CUDA_TRY(cudaMalloc(&P->ep8, sizeof(float) * 2 * (size_t)L * W));
+            DDF_CUDA_TRY(cudaMalloc(&P->rmax8, sizeof(float) * (size_t)L * W));
+            DDF_CUDA_TRY(cudaMalloc(&P->emul8, sizeof(float) * (size_t)L));
+            DDF_CUDA_TRY(cudaMalloc(&P->head8, sizeof(float) * (size_t)(2 * W + 2)));
+            DDF_CUDA_TRY(cudaMalloc(&P->bias8_mn, (size_t)L * W * 32));
             DDF_CUDA_TRY(cudaMalloc(&P->amax8, sizeof(float) * (size_t)L * W));
             int rc = make_map_u8(&P->map_f8, P->w8, P->kmax8, W, L);
             if (rc) return rc;
@@ -1966,8 +2018,13 @@ int tc_pack(ddf_net_s* net, int precision, cudaStream_t stream) {
         // tensor-core forward on a fixed set of rays (needs the BF16 copy packed above)
         int rc = tct_calibrate_fp8(net, P->amax8, stream);
         if (rc) return rc;
-        pack_f8_kernel<<<dim3(W, L), 128, 0, stream>>>(net->master, lay, P->kmax8, P->w8, P->sw8, P->amax8, P->sa8,
-                                                       P->ep8);
+        f8_act_scales_kernel<<<L, 256, 0, stream>>>(P->amax8, W, P->sa8);
+        DDF_LAUNCH_CHECK();
+        f8_rowmax_kernel<<<dim3(W, L), 128, 0, stream>>>(net->master, lay, P->sa8, P->rmax8);
+        DDF_LAUNCH_CHECK();
+        DDF_CUDA_TRY(cudaMemsetAsync(P->bias8_mn, 0, (size_t)L * W * 32, stream));
+        f8_quant_kernel<<<dim3(W, L), 128, 0, stream>>>(net->master, lay, P->kmax8, P->sa8, P->rmax8, P->w8, P->sw8,
+                                                        P->emul8, P->bias8_mn, P->head8);
         DDF_LAUNCH_CHECK();
     }
     return DDF_OK;

@@ -27,9 +27,10 @@ struct TcPack {
     uint8_t* w8 = nullptr;            // FP8: [L][W][kmax8] E4M3, per-output-channel scaled
     float* sw8 = nullptr;             // FP8: [L][W] per-output-channel weight scales
     float* sa8 = nullptr;             // FP8: [L][W] per-input-channel activation scales (layer 0: 1/448)
-    float* ep8 = nullptr;             // FP8: [2][L][W] epilogue multiplier and addend of layer l's
-                                      // output channel n: (s_w / s_a', b / s_a'), s_a' the next
-                                      // layer's input scale (the last layer: s_w, b)
+    float* rmax8 = nullptr;           // FP8: [L][W] max_k |W[n][k] s_a[l][k]| of each weight row
+    float* emul8 = nullptr;           // FP8: [L] epilogue multiplier mu_l = s_w[l][n] / s_a[l + 1][n]
+    float* head8 = nullptr;           // FP8: output head with the last layer's s_w folded in
+    uint8_t* bias8_mn = nullptr;      // FP8: [L][32 W bytes] b / s_w as 16 x W BF16 MMA operands
     float* amax8 = nullptr;           // FP8: [L][W] calibration maxima of the hidden-layer inputs
     int kmax8 = 0;
     CUtensorMap map_f8;
@@ -167,6 +168,13 @@ __device__ __forceinline__ void fma2p(float ax, float ay, float bx, float by, fl
         " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}\n"
         : "=f"(dx), "=f"(dy)
         : "f"(ax), "f"(ay), "f"(bx), "f"(by), "f"(cx), "f"(cy));
+}
+// (dx, dy) = (ax m, ay m) as one packed FP32x2 multiply.
+__device__ __forceinline__ void mul2p(float ax, float ay, float m, float& dx, float& dy) {
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %4};\n"
+        " mul.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}\n"
+        : "=f"(dx), "=f"(dy)
+        : "f"(ax), "f"(ay), "f"(m));
 }
 // Four E4M3 bytes of (ReLU(v0), .., ReLU(v3)), saturating at +-448, v0 in the low byte.
 __device__ __forceinline__ uint32_t pack_relu_e4m3x4(float v0, float v1, float v2, float v3) {

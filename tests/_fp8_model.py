@@ -2,10 +2,13 @@
 
 It restates the network of Sec. 4.1 with the FP8 path's quantisation, given the path's static
 activation scales s_a [L][W] (read back from the library: they come from a calibration pass):
-hidden layer l's weights are folded with its input scales, W'[n, k] = W[n, k] s_a[l][k], then
-scaled per output channel by s_w[n] = max_k |W'[n, k]| / 448 and rounded to E4M3; its input is
-rounded to E4M3 as a[k] / s_a[l][k] (layer 0: a[k] 448); the products accumulate exactly and z = acc s_w + b. The
-last hidden layer's output and the output head stay in floating point.
+hidden layer l's weights are folded with its input scales, W'[n, k] = W[n, k] s_a[l][k], scaled
+per output channel by s_w[n] and rounded to E4M3. For l < L - 1 the weight scale is tied to the
+next layer's input scale of the same unit, s_w[n] = mu_l s_a[l + 1][n], with one mu_l per layer
+chosen so that the largest weight code is 448; the last hidden layer uses max_k |W'[n, k]| / 448.
+The layer input is rounded to E4M3 as a[k] / s_a[l][k] (layer 0: a[k] 448); the products
+accumulate exactly and z = acc s_w + b. The last hidden layer's output and the output head stay
+in floating point.
 """
 
 import numpy as np
@@ -33,8 +36,16 @@ def query_fp8(params, o, w, in_freqs, sa):
         Wl, b = params[l]
         s = np.asarray(sa[l][: Wl.shape[1]], np.float64)
         Wp = f32(f32(Wl) * s[None, :])
-        sw = f32(np.abs(Wp).max(axis=1) / 448.0)
-        sw[sw == 0] = 1.0
+        r = np.abs(Wp).max(axis=1)
+        if l < L - 1:
+            # weight scale tied to the next layer's input scale: s_w = mu s_a', one mu per layer
+            nxt = np.asarray(sa[l + 1][: Wl.shape[0]], np.float64)
+            mu = f32((r / f32(448.0 * nxt)).max())
+            mu = mu if mu > 0 else 1.0
+            sw = f32(mu * nxt)
+        else:
+            sw = f32(r / 448.0)
+            sw[sw == 0] = 1.0
         Wq = e4m3(Wp * f32(1.0 / sw)[:, None])
         inv = np.full_like(s, 448.0) if l == 0 else f32(1.0 / s)
         aq = e4m3(f32(a) * inv[None, :])
