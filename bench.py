@@ -48,9 +48,10 @@ def bwd_flops(E, W, L):
     return 2.0 * ((L - 1) * W * W + W * E)
 
 
-# ncu-measured DRAM traffic of the BF16 query kernels (mlp_tc_kernel<256,0/1>, the 7 launches of
-# one 512 x 512 x 64 spp render); to be re-measured whenever the kernel changes.
-QUERY_DRAM_BYTES_PER_RENDER = 756.1e6
+# ncu-measured DRAM traffic of the BF16 query kernels (mlp_pair_kernel<256> forward and
+# mlp_tc_kernel<256,1> normals, the 7 launches of one 512 x 512 x 64 spp render); to be
+# re-measured whenever the kernels change.
+QUERY_DRAM_BYTES_PER_RENDER = 757.8e6
 
 
 def load_peaks():
