@@ -39,6 +39,7 @@ struct GNet {
     const CUtensorMap* map;   // forward weight map (device copy)
     const float* bias;        // [L][W]
     const float* head;        // W_out [2][W], b_out [2]
+    const uint8_t* bias_mn;   // [L][32 W bytes] bias operand tiles of the pair kernel
     int L, K0, F, E;
     int orig;                 // index of the object in the caller's offset array
     int pad;
@@ -130,18 +131,6 @@ __device__ __forceinline__ Step step_of(int s, int L, int KB0) {
     return {1, l, W / 64, l == 0 ? 128 : W};
 }
 
-// Write 32 consecutive values (columns c0..c0+31 of the row) as BF16 into the A-operand tile.
-__device__ __forceinline__ void write_act32(uint32_t act_base, int r, int c0, const float* v) {
-    const uint32_t kb_base = act_base + (uint32_t)(c0 >> 6) * 16384u;
-    const int q0 = (c0 & 63) >> 3;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        st_shared_v4(kb_base + swz(r, q0 + q), pack_bf16(v[8 * q + 0], v[8 * q + 1]),
-                     pack_bf16(v[8 * q + 2], v[8 * q + 3]), pack_bf16(v[8 * q + 4], v[8 * q + 5]),
-                     pack_bf16(v[8 * q + 6], v[8 * q + 7]));
-    }
-}
-
 // Release K-block kb of the A operand to the MMA issuer (after this thread's writes).
 __device__ __forceinline__ void release_kb(uint64_t* actr, int kb) {
     fence_proxy_async();
@@ -155,15 +144,6 @@ __device__ __forceinline__ void release_kb_warp(uint64_t* actr, int kb) {
     tc_fence_before();
     __syncwarp();
     if ((threadIdx.x & 31) == 0) mbar_arrive(&actr[kb]);
-}
-
-// Input feature order inside the tensor-core path: the six raw coordinates, two zero columns,
-// then per octave k the sines and cosines of 2^k pi v_j (the order of the encoding with the raw
-// block padded to one 16-byte chunk). The packed first-layer weights use the same order.
-__device__ __forceinline__ float enc_internal(int p, int E, const float v[6]) {
-    if (p < 8) return p < 6 ? v[p] : 0.f;
-    const int f = p - 2;
-    return f < E ? encode_feature(f, v) : 0.f;
 }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
@@ -920,7 +900,18 @@ __device__ __forceinline__ uint64_t sdesc_mn16(uint32_t saddr) {
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-template <int W>
+// One pair of tiles: its rows and its network (GRP: an object of a grouped launch, whose pairs
+// are numbered by a device prefix table; otherwise rows [256 p, 256 p + 256) of the one network).
+struct PairInfo {
+    int64_t row0;
+    int rows;   // rows of the pair (<= 256)
+    int L, KB0, F, obj;
+    const CUtensorMap* map;
+    const uint8_t* bias_mn;
+    const float* head;
+};
+
+template <int W, bool GRP>
 __global__ void __launch_bounds__(kThreads, 1)
     mlp_pair_kernel(const __grid_constant__ CUtensorMap mapF, const TcArgs a) {
     constexpr int NKBW = W / 64;
@@ -929,8 +920,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr uint32_t kStage = kWBytes + kBBytes;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int L = a.L, KB0 = a.K0 / 64;
-    const int KMAXB = KB0 > NKBW ? KB0 : NKBW;
+    const int KB0max = a.K0 / 64;   // the largest first-layer K of the launch sizes the A tiles
+    const int KMAXB = KB0max > NKBW ? KB0max : NKBW;
     const uint32_t kTile = (uint32_t)KMAXB * 16384u;   // one tile's A operand
     const int NST = a.nst;
     uint8_t* act = smem;                                // [tile 0, tile 1] x kTile
@@ -949,7 +940,39 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int64_t n = a.n;
     if (a.d_count) n = min(n, (int64_t)*a.d_count);
-    const int64_t npairs = (n + 2 * kTileM - 1) / (2 * kTileM);
+    const int64_t npairs = GRP ? a.gtile0[a.gnobj] : (n + 2 * kTileM - 1) / (2 * kTileM);
+    auto pair_info = [&](int64_t p) -> PairInfo {
+        PairInfo pi;
+        if (!GRP) {
+            pi.row0 = p * 2 * kTileM;
+            pi.rows = (int)min((int64_t)2 * kTileM, n - pi.row0);
+            pi.L = a.L;
+            pi.KB0 = KB0max;
+            pi.F = a.F;
+            pi.obj = 0;
+            pi.map = &mapF;
+            pi.bias_mn = a.bias_mn;
+            pi.head = a.head;
+        } else {
+            int lo = 0, hi = a.gnobj - 1;   // last object with pair0[obj] <= p
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.gtile0[mid] <= p) lo = mid; else hi = mid - 1;
+            }
+            const GNet& g = a.gnets[lo];
+            const int64_t lp = p - a.gtile0[lo];
+            pi.row0 = a.grow0[lo] + lp * 2 * kTileM;
+            pi.rows = (int)min((int64_t)2 * kTileM, a.grows[lo] - lp * 2 * kTileM);
+            pi.L = g.L;
+            pi.KB0 = g.K0 / 64;
+            pi.F = g.F;
+            pi.obj = lo;
+            pi.map = g.map;
+            pi.bias_mn = g.bias_mn;
+            pi.head = g.head;
+        }
+        return pi;
+    };
     constexpr uint32_t kTmemCols = 2 * W;
 
     if (tid == 0) {
@@ -975,7 +998,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         reinterpret_cast<uint32_t*>(ones)[i] = line < 2 ? 0x3F803F80u : 0u;
     }
     fence_proxy_async();
-    for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
+    if (!GRP)
+        for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
@@ -985,18 +1009,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             uint32_t cnt = 0;
             bool ok = true;
-            for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x)
-                for (int s = 0; s < L && ok; ++s) {
-                    const int nk = s == 0 ? KB0 : NKBW;
+            for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x) {
+                const PairInfo pi = pair_info(p);
+                for (int s = 0; s < pi.L && ok; ++s) {
+                    const int nk = s == 0 ? pi.KB0 : NKBW;
                     for (int kb = 0; kb < nk; ++kb, ++cnt) {
                         const int stg = (int)(cnt % (uint32_t)NST);
                         if (!mbar_wait(&empty[stg], ((cnt / (uint32_t)NST) & 1u) ^ 1u, a.err)) { ok = false; break; }
                         uint8_t* dst = wst + (size_t)stg * kStage;
                         mbar_expect_tx(&full[stg], kWBytes + (kb == 0 ? kBBytes : 0u));
-                        tma_load_3d(dst, &mapF, &full[stg], kb * 64, 0, s);
-                        if (kb == 0) bulk_load(dst + kWBytes, a.bias_mn + (size_t)s * kBBytes, kBBytes, &full[stg]);
+                        tma_load_3d(dst, pi.map, &full[stg], kb * 64, 0, s);
+                        if (kb == 0) bulk_load(dst + kWBytes, pi.bias_mn + (size_t)s * kBBytes, kBBytes, &full[stg]);
                     }
                 }
+            }
         }
     } else if (warp == kEpiWarps + 1) {
         // ---------------------------------------------------------------- MMA issuer
@@ -1007,11 +1033,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t idesc = idesc_bf16(128, W);
             const uint32_t idesc_b = idesc_bf16(128, W) | (3u << 15);   // both operands MN-major
             const uint64_t ones_d = sdesc_mn16(su32(ones));
-            for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x)
-                for (int s = 0; s < L && ok; ++s) {
+            for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x) {
+                const PairInfo pi = pair_info(p);
+                for (int s = 0; s < pi.L && ok; ++s) {
                     // K-block by K-block, tile 0 then tile 1 on each weight stage; a tile's
                     // accumulator is committed right after its last K-block
-                    const int nk = s == 0 ? KB0 : NKBW;
+                    const int nk = s == 0 ? pi.KB0 : NKBW;
                     for (int kb = 0; kb < nk && ok; ++kb, ++cnt) {
                         const int stg = (int)(cnt % (uint32_t)NST);
                         if (!mbar_wait(&full[stg], (cnt / (uint32_t)NST) & 1u, a.err)) { ok = false; break; }
@@ -1039,6 +1066,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     first = false;
                 }
+            }
         }
     } else {
         // ---------------------------------------------------------------- epilogue
@@ -1050,9 +1078,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
         uint32_t accph = 0;
         bool ok = true;
-        auto load_row = [&](int64_t p, int t, float* vv) {
-            const int64_t i = (2 * p + t) * kTileM + r;
-            const bool valid = p < npairs && i < n;
+        auto load_row = [&](const PairInfo& pi, bool exists, int t, float* vv) {
+            const int64_t i = pi.row0 + t * kTileM + r;
+            const bool valid = exists && t * kTileM + r < pi.rows;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 vv[c] = valid ? a.o[i * 3 + c] : 0.f;
@@ -1060,11 +1088,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         };
         // layer 0 of tile t: group g writes first-layer K-block g; every warp arrives on each
-        auto encode = [&](int t, const float* vv) {
-            if (grp < KB0) {
+        auto encode = [&](int t, const float* vv, const PairInfo& pi) {
+            if (grp < pi.KB0) {
                 uint32_t pk[32];
-                if (grp == 0) encode_kblock<0>(vv, a.F, pk);
-                else encode_kblock<1>(vv, a.F, pk);
+                if (grp == 0) encode_kblock<0>(vv, pi.F, pk);
+                else encode_kblock<1>(vv, pi.F, pk);
                 const uint32_t base = act_s + (uint32_t)t * kTile + (uint32_t)grp * 16384u;
 #pragma unroll
                 for (int m = 0; m < 8; ++m)
@@ -1074,21 +1102,39 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0)
-                for (int kb = 0; kb < KB0; ++kb) mbar_arrive(&actr[4 * t + kb]);
+                for (int kb = 0; kb < pi.KB0; ++kb) mbar_arrive(&actr[4 * t + kb]);
+        };
+        // GRP: the output head of the pair's object (after every epilogue warp is done with the
+        // previous one)
+        int cur_obj = -1;
+        auto load_head = [&](const PairInfo& pi) {
+            if (GRP && pi.obj != cur_obj) {
+                epi_bar();
+                for (int i2 = tid; i2 < 2 * W + 2; i2 += 256) head_s[i2] = pi.head[i2];
+                epi_bar();
+                cur_obj = pi.obj;
+            }
         };
         float vnext[2][6];
+        PairInfo pcur{};
         if ((int64_t)blockIdx.x < npairs) {
-            load_row(blockIdx.x, 0, vnext[0]);
-            load_row(blockIdx.x, 1, vnext[1]);
-            encode(0, vnext[0]);
-            encode(1, vnext[1]);
+            pcur = pair_info(blockIdx.x);
+            load_row(pcur, true, 0, vnext[0]);
+            load_row(pcur, true, 1, vnext[1]);
+            encode(0, vnext[0], pcur);
+            encode(1, vnext[1], pcur);
         }
         for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x) {
+            const PairInfo pi = pcur;
             const int64_t pn = p + gridDim.x;   // the next pair of this CTA
+            const bool has_next = pn < npairs;
+            const PairInfo pnext = has_next ? pair_info(pn) : pi;
+            load_head(pi);
+            const int L = pi.L;
             for (int s = 0; s < L && ok; ++s) {
                 if (s == L - 1) {
-                    load_row(pn, 0, vnext[0]);
-                    load_row(pn, 1, vnext[1]);
+                    load_row(pnext, has_next, 0, vnext[0]);
+                    load_row(pnext, has_next, 1, vnext[1]);
                 }
                 for (int t = 0; t < 2; ++t) {
                     ok = mbar_wait(&accf[t], (accph >> t) & 1u, a.err);
@@ -1145,8 +1191,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                         epi_bar();
                         if (grp == 0) {
-                            const int64_t i = (2 * p + t) * kTileM + r;
-                            const bool valid = i < n;
+                            const int64_t i = pi.row0 + t * kTileM + r;
+                            const bool valid = t * kTileM + r < pi.rows;
                             y0 += part[2 * r] + head_s[2 * W];
                             y1 += part[2 * r + 1] + head_s[2 * W + 1];
                             const bool hh = y1 > 0.f;
@@ -1165,10 +1211,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                         }
                         epi_bar();
-                        if (pn < npairs) encode(t, vnext[t]);
+                        if (has_next) encode(t, vnext[t], pnext);
                     }
                 }
             }
+            pcur = pnext;
         }
     }
     __syncthreads();
@@ -1422,8 +1469,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                     const uint32_t tcol = tbase + lane_off + (uint32_t)(t * W);
                     float y0 = 0.f, y1 = 0.f;
-#pragma unroll
                     const float mu = emul_s[s];
+#pragma unroll
                     for (int kb = 0; kb < NKB; ++kb) {
                         // this thread's 64 columns of K-block kb: the accumulator holds z / s_w;
                         // the next input code is E4M3(ReLU(acc mu)) (mu = s_w / s_a')
@@ -1767,17 +1814,11 @@ int launch_mode(const ddf_net_s* net, int mode, const TcArgs& base, int64_t n, b
     if (grid <= 0) return DDF_OK;
     const CUtensorMap& mf = mapF ? *mapF : P->map_fwd;
     const CUtensorMap& mb = mapB ? *mapB : P->map_bwd;
+    // the forward (mode 0) and grouped (mode 2) queries run on mlp_pair_kernel
+    if (mode != 1) return fail(DDF_ERR_UNSUPPORTED, "one-tile MLP kernel: mode %d", mode);
     int rc;
-    if (mode == 0) {
-        if ((rc = ensure_attr<W, 0>())) return rc;
-        mlp_tc_kernel<W, 0><<<grid, kThreads, s.total, stream>>>(mf, mb, a);
-    } else if (mode == 1) {
-        if ((rc = ensure_attr<W, 1>())) return rc;
-        mlp_tc_kernel<W, 1><<<grid, kThreads, s.total, stream>>>(mf, mb, a);
-    } else {
-        if ((rc = ensure_attr<W, 2>())) return rc;
-        mlp_tc_kernel<W, 2><<<grid, kThreads, s.total, stream>>>(mf, mb, a);
-    }
+    if ((rc = ensure_attr<W, 1>())) return rc;
+    mlp_tc_kernel<W, 1><<<grid, kThreads, s.total, stream>>>(mf, mb, a);
     DDF_LAUNCH_CHECK();
     return DDF_OK;
 }
@@ -1804,8 +1845,20 @@ Layout smem_layout_pair(int W, int K0) {
     return s;
 }
 
-template <int W>
-int launch_pair(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_count, cudaStream_t stream) {
+template <int W, bool GRP>
+int ensure_pair_attr() {
+    static bool done = false;
+    if (!done) {
+        DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_pair_kernel<W, GRP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          227 * 1024));
+        done = true;
+    }
+    return DDF_OK;
+}
+
+template <int W, bool GRP>
+int launch_pair(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_count, cudaStream_t stream,
+                int grid_override = 0) {
     const TcPack* P = net->tc;
     TcArgs a = base;
     const Layout s = smem_layout_pair(W, a.K0);
@@ -1816,16 +1869,14 @@ int launch_pair(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_co
     a.off_head = s.off_head;
     a.off_part = s.off_part;
     a.off_bar = s.off_bar;
-    a.bias_mn = P->bias_mn;
+    if (!GRP) a.bias_mn = P->bias_mn;
     // one CTA per SM, each walking pairs of 128-row tiles
     int grid = use_count ? num_sms() : (int)std::min<int64_t>((n + 2 * kTileM - 1) / (2 * kTileM), num_sms());
+    if (grid_override > 0) grid = grid_override;
     if (grid <= 0) return DDF_OK;
-    static bool attr = false;
-    if (!attr) {
-        DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_pair_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        attr = true;
-    }
-    mlp_pair_kernel<W><<<grid, kThreads, s.total, stream>>>(P->map_fwd, a);
+    int rc = ensure_pair_attr<W, GRP>();
+    if (rc) return rc;
+    mlp_pair_kernel<W, GRP><<<grid, kThreads, s.total, stream>>>(P->map_fwd, a);
     DDF_LAUNCH_CHECK();
     return DDF_OK;
 }
@@ -1922,8 +1973,8 @@ __global__ void grouped_prep(const int64_t* __restrict__ offsets, const GNet* __
         const int64_t nr = offsets[o + 1] > r0 ? offsets[o + 1] - r0 : 0;
         row0[i] = r0;
         rows[i] = nr;
-        tile0[i] = acc;
-        acc += (nr + kTileM - 1) / kTileM;
+        tile0[i] = acc;   // first pair of object i
+        acc += (nr + 2 * kTileM - 1) / (2 * kTileM);
     }
     tile0[nobj] = acc;
 }
@@ -2067,8 +2118,8 @@ int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n
         rc = lay.width == 128 ? launch_f8<128>(net, a, n, d_count != nullptr, stream)
                               : launch_f8<256>(net, a, n, d_count != nullptr, stream);
     else
-        rc = lay.width == 128   ? launch_pair<128>(net, a, n, d_count != nullptr, stream)
-             : lay.width == 256 ? launch_pair<256>(net, a, n, d_count != nullptr, stream)
+        rc = lay.width == 128   ? launch_pair<128, false>(net, a, n, d_count != nullptr, stream)
+             : lay.width == 256 ? launch_pair<256, false>(net, a, n, d_count != nullptr, stream)
                                 : launch512(net, 0, a, n, d_count != nullptr, stream);
     if (rc || !normals) return rc;
     TcArgs b = a;
@@ -2190,8 +2241,8 @@ extern "C" DDF_API int ddf_query_noalloc(ddf_net net, const float* d_origins, co
     if (net->precision == DDF_FP8)
         rc = lay.width == 128 ? launch_f8<128>(net, a, n, false, stream) : launch_f8<256>(net, a, n, false, stream);
     else
-        rc = lay.width == 128 ? launch_pair<128>(net, a, n, false, stream)
-                              : launch_pair<256>(net, a, n, false, stream);
+        rc = lay.width == 128 ? launch_pair<128, false>(net, a, n, false, stream)
+                              : launch_pair<256, false>(net, a, n, false, stream);
     if (rc) return rc;
     TcArgs b = a;
     b.rows = hit_list;
@@ -2217,7 +2268,7 @@ struct ddf_group_s {
         int nst = 0, grid = 0;            // launch shape (0 = default); set by the autotuner
         ddf::GNet* d_gnets = nullptr;
         CUtensorMap* d_maps = nullptr;
-        int64_t* d_tab = nullptr;         // row0[64], rows[64], tile0[65]
+        int64_t* d_tab = nullptr;         // row0[64], rows[64], pair0[65]
         ddf_net first = nullptr;
     } cls[2];                             // [0]: width 128, [1]: width 256
     int n = 0;
@@ -2251,8 +2302,8 @@ int group_class_launch(ddf_group_s* g, int c, const float* o, const float* w, fl
     a.gtile0 = C.d_tab + 2 * kMaxGroup;
     a.gnobj = C.nobj;
     const int grid = C.grid > 0 ? C.grid : num_sms();
-    if (C.W == 128) return launch_mode<128>(C.first, 2, a, 0, true, stream, C.nst, grid);
-    return launch_mode<256>(C.first, 2, a, 0, true, stream, C.nst, grid);
+    if (C.W == 128) return launch_pair<128, true>(C.first, a, 0, true, stream, grid);
+    return launch_pair<256, true>(C.first, a, 0, true, stream, grid);
 }
 
 int group_prep(ddf_group_s* g, const int64_t* d_offsets, cudaStream_t stream) {
@@ -2309,6 +2360,7 @@ extern "C" DDF_API int ddf_group_create(int n_obj, const ddf_net* nets, ddf_grou
         GNet gn{};
         gn.bias = nt->tc->bias;
         gn.head = nt->tc->head;
+        gn.bias_mn = nt->tc->bias_mn;
         gn.L = nt->lay.L;
         gn.K0 = nt->tc->K0;
         gn.F = nt->lay.in_freqs;
@@ -2327,7 +2379,7 @@ extern "C" DDF_API int ddf_group_create(int n_obj, const ddf_net* nets, ddf_grou
     for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
         ddf_group_s::Class& C = g->cls[c];
         if (!C.nobj) continue;
-        if (smem_layout(C.W, C.maxL, C.K0, 0).nst < 2) {
+        if (smem_layout_pair(C.W, C.K0).nst < 2) {
             group_free(g);
             return fail(DDF_ERR_UNSUPPORTED, "width %d x %d layers does not fit the grouped kernel", C.W, C.maxL);
         }
@@ -2343,8 +2395,8 @@ extern "C" DDF_API int ddf_group_create(int n_obj, const ddf_net* nets, ddf_grou
         return fail(DDF_ERR_CUDA, "group create: %s", cudaGetErrorString(e));
     }
     // kernel attributes are set here, outside any stream capture
-    int rc = ensure_attr<128, 2>();
-    if (!rc) rc = ensure_attr<256, 2>();
+    int rc = ensure_pair_attr<128, true>();
+    if (!rc) rc = ensure_pair_attr<256, true>();
     if (rc) {
         group_free(g);
         return rc;
@@ -2475,12 +2527,12 @@ extern "C" DDF_API int ddf_group_autotune(ddf_group g, const int64_t* d_offsets,
             }
         }
         if (cached) continue;
-        const int nst_max = smem_layout(C.W, C.maxL, C.K0, 0).nst;
+        const int nst_max = smem_layout_pair(C.W, C.K0).nst;   // the pair kernel's ring depth is fixed
         const int sms = num_sms();
         const int grids[3] = {sms, (3 * sms) / 4, sms / 2};
         float best = 1e30f;
         int best_nst = nst_max, best_grid = sms;
-        for (int nst = 2; nst <= nst_max; ++nst)
+        for (int nst = nst_max; nst <= nst_max; ++nst)
             for (int gi = 0; gi < 3; ++gi) {
                 C.nst = nst;
                 C.grid = grids[gi];
