@@ -1,22 +1,23 @@
-// Tensor-core DDF network query for sm_103a: BF16 hidden-layer GEMMs on tcgen05 with FP32
-// accumulators in tensor memory, fed by TMA. (MLP_w of Sec. 4.1; normals by the gradient of
+// Tensor-core DDF network query for sm_103a: BF16 (and FP8) hidden-layer GEMMs on tcgen05 with
+// FP32 accumulators in tensor memory, fed by TMA. (MLP_w of Sec. 4.1; normals by the gradient of
 // Eq. 3 / Sec. 4.2.)
 //
-// One persistent CTA per SM walks 128-row tiles; its 192 threads are split by role:
-//   warp 4      TMA producer: streams 64-wide K-blocks of each layer's packed BF16 weights
-//               (W rows x 128 B, 128-byte swizzle) through a ring of shared-memory stages;
-//   warp 5      MMA issuer: one thread issues tcgen05.mma (M = 128, N = W, K = 16) per
-//               16-wide K step, accumulating a layer into one of two TMEM buffers (layers
-//               alternate, so the next layer's MMAs overlap the current layer's epilogue);
-//   warps 0-3   epilogue: thread r owns row r / TMEM lane r. It encodes the row's input, and
-//               after each layer reads the accumulator (tcgen05.ld), adds the bias, applies the
-//               ReLU, rounds to BF16 and writes the next layer's A operand straight into the
-//               swizzled K-major shared-memory tile, releasing it 64 columns at a time, so the
-//               next layer's MMAs start on the first K-block while the rest is still being
-//               written. The 2-unit output head runs on CUDA cores in FP32.
-// Mode 0 evaluates all rows (distance, logit, hit) and appends hit rows to a list. Mode 1 takes
-// that list and runs the forward pass again followed by the reverse pass (same GEMM engine:
-// the transposed weights stream through the same ring) to d dist / d o, and the Eq. 3 normal.
+// Every kernel here is persistent (one CTA per SM) with 320 threads split by role: one warp
+// streams weight K-blocks into a ring of shared-memory stages with TMA, one thread of another
+// warp issues tcgen05.mma, and eight epilogue warps (thread = row = TMEM lane, two column
+// groups) read the accumulators with tcgen05.ld and write the next layer's A operand straight
+// into the swizzled K-major shared-memory tile, releasing it one K-block at a time so the next
+// layer's MMAs start while the rest is still being written. The 2-unit output head runs on CUDA
+// cores in FP32.
+//   mlp_pair_kernel<W, GRP>   the forward query (W = 128, 256): two 128-row tiles per CTA share
+//                             every weight stage, each layer's bias enters through one MMA;
+//                             GRP = true serves grouped launches of many networks;
+//   mlp_tc_kernel<W, 1>       the normals of the hit rows: one tile per CTA, the forward pass
+//                             again (ReLU masks kept as bits in shared memory) and then the
+//                             reverse pass with the transposed weights through the same ring,
+//                             the encoding chain rule and Eq. 3;
+//   mlp_tc512_kernel<MODE>    both launches at width 512 (N-half schedule);
+//   mlp_f8_kernel<W>          the forward query with E4M3 weights and activations.
 //
 // Every mbarrier wait is bounded (about 2 s of %globaltimer); on expiry the kernel raises a
 // device error flag, every role leaves its loop, TMEM is released and the host reports
@@ -152,6 +153,7 @@ template <int W, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     mlp_tc_kernel(const __grid_constant__ CUtensorMap mapF, const __grid_constant__ CUtensorMap mapB,
                   const TcArgs a) {
+    static_assert(MODE == 1, "the forward and grouped queries run on mlp_pair_kernel");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr int NKBW = W / 64;
@@ -163,7 +165,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t* masks = reinterpret_cast<uint32_t*>(smem + a.off_mask);
     float* bias_s = reinterpret_cast<float*>(smem + a.off_bias);
     float* head_s = reinterpret_cast<float*>(smem + a.off_head);
-    float* part = reinterpret_cast<float*>(smem + a.off_part);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
     uint64_t* full = bars;
     uint64_t* empty = bars + NST;
@@ -174,55 +175,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int64_t n = a.n;
     if (a.d_count) n = min(n, (int64_t)*a.d_count);
-    int64_t ntiles = (n + kTileM - 1) / kTileM;
+    const int64_t ntiles = (n + kTileM - 1) / kTileM;
     constexpr uint32_t kTmemCols = W <= 128 ? 256 : 512;
-    // grouped mode: the class table in shared memory
-    GNet* gn_s = reinterpret_cast<GNet*>(smem + a.off_grp);
-    int64_t* gt0_s = reinterpret_cast<int64_t*>(gn_s + kMaxGroup);
-    int64_t* gr0_s = gt0_s + kMaxGroup + 1;
-    int64_t* grn_s = gr0_s + kMaxGroup;
-    if (MODE == 2) {
-        for (int i = tid; i < a.gnobj; i += kThreads) {
-            gn_s[i] = a.gnets[i];
-            gr0_s[i] = a.grow0[i];
-            grn_s[i] = a.grows[i];
-        }
-        for (int i = tid; i <= a.gnobj; i += kThreads) gt0_s[i] = a.gtile0[i];
-    }
-    // Per-tile description: rows, network depth, first-layer K-blocks, weight map, object.
+    // Per-tile description: rows of the hit list, network depth, first-layer K-blocks, weight map.
     struct TileInfo {
         int64_t row0;
-        int rows, L, KB0, F, E, obj;
+        int rows, L, KB0, F, E;
         const CUtensorMap* map;
     };
     auto tile_info = [&](int64_t t) -> TileInfo {
         TileInfo ti;
-        if (MODE != 2) {
-            ti.row0 = t * kTileM;
-            ti.rows = (int)min((int64_t)kTileM, n - ti.row0);
-            ti.L = L;
-            ti.KB0 = KB0;
-            ti.F = a.F;
-            ti.E = a.E;
-            ti.obj = 0;
-            ti.map = &mapF;
-        } else {
-            int lo = 0, hi = a.gnobj - 1;   // last object with gt0_s[obj] <= t
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (gt0_s[mid] <= t) lo = mid; else hi = mid - 1;
-            }
-            const GNet& g = gn_s[lo];
-            const int64_t lt = t - gt0_s[lo];
-            ti.row0 = gr0_s[lo] + lt * kTileM;
-            ti.rows = (int)min((int64_t)kTileM, grn_s[lo] - lt * kTileM);
-            ti.L = g.L;
-            ti.KB0 = g.K0 / 64;
-            ti.F = g.F;
-            ti.E = g.E;
-            ti.obj = lo;
-            ti.map = g.map;
-        }
+        ti.row0 = t * kTileM;
+        ti.rows = (int)min((int64_t)kTileM, n - ti.row0);
+        ti.L = L;
+        ti.KB0 = KB0;
+        ti.F = a.F;
+        ti.E = a.E;
+        ti.map = &mapF;
         return ti;
     };
 
@@ -241,12 +210,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (MODE != 2) {
-        for (int i = tid; i < L * W; i += kThreads) bias_s[i] = a.bias[i];
-        for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
-    }
+    for (int i = tid; i < L * W; i += kThreads) bias_s[i] = a.bias[i];
+    for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
     __syncthreads();
-    if (MODE == 2) ntiles = gt0_s[a.gnobj];
     tc_fence_after();
     const uint32_t tbase = *tslot;
 
@@ -322,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (tt < ntiles) {
                 const TileInfo tn = tile_info(tt);
                 valid_out = r < tn.rows;
-                if (valid_out) row_out = MODE == 1 ? (int64_t)a.rows[tn.row0 + r] : tn.row0 + r;
+                if (valid_out) row_out = (int64_t)a.rows[tn.row0 + r];
             }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -334,20 +300,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool valid_next = false;
         float v_next[6];
         fetch_row(blockIdx.x, row_next, valid_next, v_next);
-        int cur_obj = -1;
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const TileInfo ti = tile_info(t);
             const int Lt = ti.L, KB0t = ti.KB0;
             const int nsteps = MODE == 1 ? 2 * Lt : Lt;
-            if (MODE == 2 && ti.obj != cur_obj) {
-                // a new object: its biases and output head replace the previous one's
-                epi_bar();
-                const GNet& gobj = gn_s[ti.obj];
-                for (int i = tid; i < Lt * W; i += 256) bias_s[i] = gobj.bias[i];
-                for (int i = tid; i < 2 * W + 2; i += 256) head_s[i] = gobj.head[i];
-                epi_bar();
-                cur_obj = ti.obj;
-            }
             const int64_t row = row_next;
             const bool valid = valid_next;
             float v[6];
@@ -367,7 +323,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             // K-blocks are released by 256 arrivals: each group also arrives on the other's block
             for (int kb = 0; kb < KB0t; ++kb)
                 if (kb != grp) mbar_arrive(&actr[kb]);
-            float y0 = 0.f, y1 = 0.f;
             for (int s = 0; s < nsteps && ok; ++s, ++g) {
                 const int b = (int)(g & 1u);
                 if (s == nsteps - 1) fetch_row(t + gridDim.x, row_next, valid_next, v_next);
@@ -408,23 +363,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                                          bb.z, bb.w, z2, z3);
                                     pk[2 * q] = pack_relu(z0, z1);
                                     pk[2 * q + 1] = pack_relu(z2, z3);
-                                    if (MODE == 1)
-                                        bits |= (pos(z0) | pos(z1) << 1 | pos(z2) << 2 | pos(z3) << 3) << (4 * q);
+                                    bits |= (pos(z0) | pos(z1) << 1 | pos(z2) << 2 | pos(z3) << 3) << (4 * q);
                                 }
-                                if (MODE == 1) masks[(s * (W / 32) + (c0 >> 5)) * 128 + r] = bits;
+                                masks[(s * (W / 32) + (c0 >> 5)) * 128 + r] = bits;
 #pragma unroll
                                 for (int m = 0; m < 4; ++m)
                                     st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
                                                  pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
                                 release_kb(actr, kb);
-                            } else if (MODE != 1) {
-                                // output head on this thread's columns (FP32)
-#pragma unroll
-                                for (int c = 0; c < 32; ++c) {
-                                    const float z = fmaxf(__uint_as_float(raw[i][c]) + bs[c0 + c], 0.f);
-                                    y0 = fmaf(z, head_s[c0 + c], y0);
-                                    y1 = fmaf(z, head_s[W + c0 + c], y1);
-                                }
                             } else {
                                 // delta of the last hidden layer: W_out[0] on active units
                                 uint32_t pk[16];
@@ -461,32 +407,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                             release_kb(actr, kb);
                         }
                     }
-                    }
-                    if (s == Lt - 1 && MODE != 1) {
-                        tc_fence_before();
-                        if (grp == 1) {
-                            part[2 * r] = y0;
-                            part[2 * r + 1] = y1;
-                        }
-                        epi_bar();
-                        if (grp == 0) {
-                            y0 += part[2 * r] + head_s[2 * W];
-                            y1 += part[2 * r + 1] + head_s[2 * W + 1];
-                            const bool hh = y1 > 0.f;
-                            if (valid) {
-                                a.dist[row] = y0;
-                                if (a.logit) a.logit[row] = y1;
-                                if (a.hit) a.hit[row] = (uint8_t)hh;
-                            }
-                            if (a.hit_list) {
-                                const bool take = valid && hh;
-                                const unsigned m = __ballot_sync(0xffffffffu, take);
-                                int base = 0;
-                                if (lane == 0 && m) base = atomicAdd(a.hit_count, __popc(m));
-                                base = __shfl_sync(0xffffffffu, base, 0);
-                                if (take) a.hit_list[base + __popc(m & ((1u << lane) - 1u))] = (int)row;
-                            }
-                        }
                     }
                 } else if (grp == 0) {
                     // d dist / d features (columns 0 .. K0-1), then the encoding chain rule
@@ -1757,17 +1677,17 @@ struct Layout {
     int nst;
 };
 
-Layout smem_layout(int W, int L, int K0, int mode) {
-    Layout s;
+// Shared memory of the normals kernel: the A tile, the weight ring, the ReLU masks of every
+// hidden layer (a bit per row and unit), the biases and the output head.
+Layout smem_layout(int W, int L, int K0) {
+    Layout s{};
     const int kmaxb = std::max(K0 / 64, W / 64);
     const uint32_t act = (uint32_t)kmaxb * 16384u;
     const uint32_t stage = (uint32_t)W * 128u;
-    const uint32_t mask = mode == 1 ? (uint32_t)L * 128u * (W / 32) * 4u : 0u;
+    const uint32_t mask = (uint32_t)L * 128u * (W / 32) * 4u;
     const uint32_t bias = (uint32_t)L * W * 4u;
     const uint32_t head = ((uint32_t)(2 * W + 2) * 4u + 15u) & ~15u;
-    const uint32_t partb = 128u * 2u * 4u;
-    const uint32_t grpb = (uint32_t)(sizeof(GNet) * kMaxGroup + sizeof(int64_t) * (3 * kMaxGroup + 1) + 15) & ~15u;
-    const uint32_t fixed = act + mask + bias + head + partb + grpb + 512u;
+    const uint32_t fixed = act + mask + bias + head + 512u;
     const uint32_t budget = 227u * 1024u - 1024u;   // minus alignment slack
     int nst = (int)((budget - fixed) / stage);
     s.nst = std::max(0, std::min(8, nst));
@@ -1775,9 +1695,7 @@ Layout smem_layout(int W, int L, int K0, int mode) {
     s.off_mask = act + (uint32_t)s.nst * stage;
     s.off_bias = s.off_mask + mask;
     s.off_head = s.off_bias + bias;
-    s.off_part = s.off_head + head;
-    s.off_grp = s.off_part + partb;
-    s.off_bar = s.off_grp + grpb;
+    s.off_bar = s.off_head + head;
     s.total = s.off_bar + 512u + 1024u;
     return s;
 }
@@ -1799,15 +1717,13 @@ int launch_mode(const ddf_net_s* net, int mode, const TcArgs& base, int64_t n, b
                 const CUtensorMap* mapF = nullptr, const CUtensorMap* mapB = nullptr) {
     const TcPack* P = net ? net->tc : nullptr;
     TcArgs a = base;
-    const Layout s = smem_layout(W, a.L, a.K0, mode == 1 ? 1 : 0);
+    const Layout s = smem_layout(W, a.L, a.K0);
     if (s.nst < 2) return fail(DDF_ERR_UNSUPPORTED, "tensor-core MLP: shared memory too small");
     a.nst = nst_override > 0 ? std::min(nst_override, s.nst) : s.nst;
     a.off_wst = s.off_wst;
     a.off_mask = s.off_mask;
     a.off_bias = s.off_bias;
     a.off_head = s.off_head;
-    a.off_part = s.off_part;
-    a.off_grp = s.off_grp;
     a.off_bar = s.off_bar;
     int grid = use_count ? num_sms() : (int)std::min<int64_t>((n + kTileM - 1) / kTileM, num_sms());
     if (grid_override > 0) grid = grid_override;
@@ -1991,7 +1907,7 @@ bool tc_supported(const NetLayout& lay, int precision) {
     if (lay.width != 128 && lay.width != 256 && lay.width != 512) return false;
     if (lay.E + 2 > 128) return false;
     if (lay.width == 512) return lay.L >= 1 && lay.L <= kMaxLayers && smem512(3) <= 227u * 1024u;
-    return lay.L >= 1 && lay.L <= kMaxLayers && smem_layout(lay.width, lay.L, 64 * ((lay.E + 2 + 63) / 64), 1).nst >= 2;
+    return lay.L >= 1 && lay.L <= kMaxLayers && smem_layout(lay.width, lay.L, 64 * ((lay.E + 2 + 63) / 64)).nst >= 2;
 }
 
 void tc_free(ddf_net_s* net) {
