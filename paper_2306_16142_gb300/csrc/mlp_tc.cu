@@ -80,6 +80,9 @@ struct TcArgs {
     int maxL;
     uint32_t* gmask;   // width 512: per-CTA ReLU masks of the reverse pass
     const uint8_t* bias_mn;   // BF16 pair kernel: [L][32 W bytes] bias operand tiles
+    uint32_t* train_masks;    // training forward: ReLU masks of a_1 .. a_{L-1}, [ld][W / 32] each
+    __nv_bfloat16* train_aL;  // training forward: a_L, row-major [ld][W]
+    int64_t train_ld;         // training forward: rows of one workspace array
     const float* f8_emul;   // FP8 epilogue [L]: accumulator multiplier mu_l
 };
 
@@ -137,6 +140,13 @@ __device__ __forceinline__ void release_kb(uint64_t* actr, int kb) {
     fence_proxy_async();
     tc_fence_before();
     mbar_arrive(&actr[kb]);
+}
+// Bit c = 1 where accumulator value c of 32 is positive (the ReLU mask of 32 columns).
+__device__ __forceinline__ uint32_t pos_bits32(const uint32_t* raw) {
+    uint32_t b = 0;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) b |= ((int)raw[c] > 0 ? 1u : 0u) << c;
+    return b;
 }
 // The same with one arrival per warp (barrier count = warps): every lane fences its own stores
 // for the async proxy, the warp synchronises, lane 0 arrives. Call from warp-uniform code.
@@ -831,9 +841,15 @@ struct PairInfo {
     const float* head;
 };
 
-template <int W, bool GRP>
+// TRAIN: the forward pass of a training step. The head is skipped; the encoded input a_0 and the
+// hidden activations a_1 .. a_{L-1} are written to the workspace by TMA stores of the on-chip A
+// tiles (issued by the MMA thread once every epilogue warp has released the K-block), a_L and the
+// ReLU masks of a_1 .. a_{L-1} by the epilogue.
+template <int W, bool GRP, bool TRAIN>
 __global__ void __launch_bounds__(kThreads, 1)
-    mlp_pair_kernel(const __grid_constant__ CUtensorMap mapF, const TcArgs a) {
+    mlp_pair_kernel(const __grid_constant__ CUtensorMap mapF, const __grid_constant__ CUtensorMap mapA0,
+                    const __grid_constant__ CUtensorMap mapAct, const TcArgs a) {
+    static_assert(!(GRP && TRAIN), "grouped launches are queries");
     constexpr int NKBW = W / 64;
     constexpr uint32_t kWBytes = (uint32_t)W * 128u;   // one 64-wide K-block of the weights
     constexpr uint32_t kBBytes = (uint32_t)W * 32u;    // one layer's bias tile
@@ -967,6 +983,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const int ab = 4 * t + kb;
                             if (!mbar_wait(&actr[ab], (actph >> ab) & 1u, a.err)) { ok = false; break; }
                             actph ^= 1u << ab;
+                            if (TRAIN && t * kTileM < pi.rows) {   // a_s of this tile to the workspace
+                                tma_store_3d(s == 0 ? &mapA0 : &mapAct,
+                                             act_s + (uint32_t)t * kTile + (uint32_t)kb * 16384u, kb * 64,
+                                             (int)(pi.row0 + t * kTileM), s == 0 ? 0 : s - 1);
+                                bulk_commit();
+                            }
                             // the bias MMA overwrites the whole accumulator: wait until the
                             // epilogue has read the tile's previous layer
                             if (kb == 0 && !first) {
@@ -980,7 +1002,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const uint64_t bd = sdesc(sb);
 #pragma unroll
                             for (int k = 0; k < 4; ++k) mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, 1u);
-                            if (kb == nk - 1) mma_commit(&accf[t]);
+                            if (kb == nk - 1) {
+                                // the epilogue overwrites the A tile after this commit: the stores
+                                // must have read it
+                                if (TRAIN) bulk_wait_read();
+                                mma_commit(&accf[t]);
+                            }
                         }
                         if (ok) mma_commit(&empty[stg]);   // both tiles have read the stage
                     }
@@ -1091,6 +1118,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                                     st_shared_v4(tact + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
                                                  pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
                                 release_kb_warp(actr, 4 * t + kb);
+                                if (TRAIN && t * kTileM + r < pi.rows)   // ReLU mask of a_{s+1}
+                                    a.train_masks[((int64_t)s * a.train_ld + pi.row0 + t * kTileM + r) * (W / 32) +
+                                                  2 * kb + grp] = pos_bits32(raw[i]);
+                            } else if (TRAIN) {
+                                // a_L = ReLU(acc) rounded to BF16, for the output layer's kernel
+                                if (t * kTileM + r < pi.rows) {
+                                    uint32_t pk[16];
+#pragma unroll
+                                    for (int q = 0; q < 16; ++q)
+                                        pk[q] = pack_relu(__uint_as_float(raw[i][2 * q]),
+                                                          __uint_as_float(raw[i][2 * q + 1]));
+                                    uint4* dst = reinterpret_cast<uint4*>(a.train_aL + (pi.row0 + t * kTileM + r) * W + c0);
+#pragma unroll
+                                    for (int m = 0; m < 4; ++m)
+                                        dst[m] = make_uint4(pk[4 * m], pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
+                                }
                             } else {
                                 // output head on this thread's columns (FP32)
 #pragma unroll
@@ -1102,7 +1145,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                         }
                     }
-                    if (s == L - 1) {
+                    if (TRAIN && s == L - 1) {
+                        if (has_next) encode(t, vnext[t], pnext);
+                    } else if (s == L - 1) {
                         // outputs, then tile t of the next pair takes over the accumulator
                         tc_fence_before();
                         if (grp == 1) {
@@ -1761,20 +1806,20 @@ Layout smem_layout_pair(int W, int K0) {
     return s;
 }
 
-template <int W, bool GRP>
+template <int W, bool GRP, bool TRAIN>
 int ensure_pair_attr() {
     static bool done = false;
     if (!done) {
-        DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_pair_kernel<W, GRP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_pair_kernel<W, GRP, TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           227 * 1024));
         done = true;
     }
     return DDF_OK;
 }
 
-template <int W, bool GRP>
+template <int W, bool GRP, bool TRAIN = false>
 int launch_pair(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_count, cudaStream_t stream,
-                int grid_override = 0) {
+                int grid_override = 0, const CUtensorMap* mapA0 = nullptr, const CUtensorMap* mapAct = nullptr) {
     const TcPack* P = net->tc;
     TcArgs a = base;
     const Layout s = smem_layout_pair(W, a.K0);
@@ -1790,9 +1835,10 @@ int launch_pair(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_co
     int grid = use_count ? num_sms() : (int)std::min<int64_t>((n + 2 * kTileM - 1) / (2 * kTileM), num_sms());
     if (grid_override > 0) grid = grid_override;
     if (grid <= 0) return DDF_OK;
-    int rc = ensure_pair_attr<W, GRP>();
+    int rc = ensure_pair_attr<W, GRP, TRAIN>();
     if (rc) return rc;
-    mlp_pair_kernel<W, GRP><<<grid, kThreads, s.total, stream>>>(P->map_fwd, a);
+    mlp_pair_kernel<W, GRP, TRAIN><<<grid, kThreads, s.total, stream>>>(
+        P->map_fwd, mapA0 ? *mapA0 : P->map_fwd, mapAct ? *mapAct : P->map_fwd, a);
     DDF_LAUNCH_CHECK();
     return DDF_OK;
 }
@@ -2050,6 +2096,29 @@ int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n
     return lay.width == 128   ? launch_mode<128>(net, 1, b, n, true, stream)
            : lay.width == 256 ? launch_mode<256>(net, 1, b, n, true, stream)
                               : launch512(net, 1, b, n, true, stream);
+}
+
+int tc_train_forward(const ddf_net_s* net, const float* o, const float* w, int64_t m, const CUtensorMap* map_a0,
+                     const CUtensorMap* map_act, uint32_t* masks, __nv_bfloat16* aL, int64_t ld, cudaStream_t stream) {
+    const NetLayout& lay = net->lay;
+    const TcPack* P = net->tc;
+    if (!P || lay.width > 256 || P->K0 > 128 || !P->bias_mn)
+        return fail(DDF_ERR_UNSUPPORTED, "fused training forward: width %d / K0 %d", lay.width, P ? P->K0 : 0);
+    TcArgs a{};
+    a.L = lay.L;
+    a.E = lay.E;
+    a.K0 = P->K0;
+    a.F = lay.in_freqs;
+    a.head = P->head;
+    a.o = o;
+    a.w = w;
+    a.n = m;
+    a.err = P->err;
+    a.train_masks = masks;
+    a.train_aL = aL;
+    a.train_ld = ld;
+    return lay.width == 128 ? launch_pair<128, false, true>(net, a, m, false, stream, 0, map_a0, map_act)
+                            : launch_pair<256, false, true>(net, a, m, false, stream, 0, map_a0, map_act);
 }
 
 int tc_fp8_scales(ddf_net_s* net, float* host_out) {
@@ -2311,8 +2380,8 @@ extern "C" DDF_API int ddf_group_create(int n_obj, const ddf_net* nets, ddf_grou
         return fail(DDF_ERR_CUDA, "group create: %s", cudaGetErrorString(e));
     }
     // kernel attributes are set here, outside any stream capture
-    int rc = ensure_pair_attr<128, true>();
-    if (!rc) rc = ensure_pair_attr<256, true>();
+    int rc = ensure_pair_attr<128, true, false>();
+    if (!rc) rc = ensure_pair_attr<256, true, false>();
     if (rc) {
         group_free(g);
         return rc;

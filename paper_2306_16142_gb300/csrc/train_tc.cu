@@ -75,28 +75,9 @@ __device__ __forceinline__ void stage_rows(uint8_t* tb, int lane, const uint32_t
     __syncwarp();
 }
 
-// line = column j of the block, position = row (transposed staging)
-__device__ __forceinline__ void stage_cols(uint8_t* tb, int lane, const uint32_t pk[16]) {
-    unsigned short* t16 = reinterpret_cast<unsigned short*>(tb);
-    const int pc = lane >> 3, wi = lane & 7;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const uint32_t h = (j & 1) ? (pk[j >> 1] >> 16) : (pk[j >> 1] & 0xffffu);
-        t16[j * 32 + 8 * (pc ^ ((j >> 1) & 3)) + wi] = (unsigned short)h;
-    }
-    __syncwarp();
-}
-
 // Piece (lane % 4) of line (8 i + lane / 4).
 __device__ __forceinline__ uint4 blk_read(const uint8_t* tb, int lane, int i) {
     return *reinterpret_cast<const uint4*>(tb + blk_off(8 * i + (lane >> 2), lane & 3));
-}
-
-// Sum over the four lanes of a line; every one of them gets the same value (fixed pairing).
-__device__ __forceinline__ float line_sum(float s) {
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    return s;
 }
 
 // Rows row0..row0+31 (lane = row) of columns col0..col0+31 to a row-major [.][ld] array.
@@ -882,6 +863,14 @@ int tc_forward(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t
     auto act = [&](int l) { return ws.act + (l == 0 ? 0 : ((int64_t)K0 + (int64_t)(l - 1) * W) * ld); };
     auto masks = [&](int l) { return ws.masks + (int64_t)(l - 1) * ld * (W / 32); };
     int rc;
+    if (K0 <= 128) {
+        // one persistent launch (the query's pair kernel in its training form): a_0 .. a_{L-1}
+        // leave the chip by TMA stores of the A tiles, a_L and the masks from the epilogue
+        CUtensorMap m0, ma;
+        if ((rc = tmap(&m0, act(0), K0, K0, ld, 1, 128))) return rc;
+        if ((rc = tmap(&ma, act(1), W, W, ld, L, 128))) return rc;   // L consecutive [ld][W] arrays
+        return tc_train_forward(net, o, w, m, &m0, &ma, ws.masks, act(L), ld, s);
+    }
     tenc_kernel<<<(unsigned)((mp + 127) / 128), 128, 0, s>>>(o, w, m, mp, lay.E, K0, act(0));
     DDF_LAUNCH_CHECK();
 
