@@ -3,6 +3,7 @@
 It restates the network of Sec. 4.1 with BF16 rounding at the points where the tensor-core path
 rounds: the encoded input, every hidden activation fed to the next GEMM, every weight matrix,
 and every reverse-pass delta; products are accumulated exactly (the path accumulates in FP32).
+At widths 128 and 256 the bias enters the accumulator as a BF16 hi / lo pair (split_bias).
 The last hidden layer and the output head stay unrounded, as in the path. Comparing the GPU with
 this model isolates kernel bugs from the inherent difference between a BF16-evaluated network
 and the FP64 one (ReLU units whose sign flips under BF16 rounding change the gradient).
@@ -18,14 +19,25 @@ def bf16(x):
     return torch.from_numpy(np.asarray(x, np.float64).astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
 
 
-def query_bf16(params, o, w, in_freqs):
+def split_bias(b):
+    """The bias as the width-128/256 kernels add it: one MMA of a ones column by the BF16 pair
+    (bf16(b), bf16(b - bf16(b))), exact in the FP32 accumulator."""
+    b32 = np.asarray(b, np.float64).astype(np.float32)
+    hi = bf16(b32)
+    lo = bf16((b32 - hi.astype(np.float32)).astype(np.float32))
+    return hi + lo
+
+
+def query_bf16(params, o, w, in_freqs, bias_in_mma=True):
+    """bias_in_mma: the bias as split_bias gives it (widths 128 and 256); False: the FP32 bias
+    added after the accumulation (width 512)."""
     X, dX = omlp.encode(o, w, in_freqs)
     L = len(params) - 1
     a = bf16(X)
     masks = []
     for l in range(L):
         Wl, b = params[l]
-        z = a @ bf16(Wl).T + b
+        z = a @ bf16(Wl).T + (split_bias(b) if bias_in_mma else b)
         masks.append(z > 0)
         a = np.maximum(z, 0.0)
         if l < L - 1:
@@ -44,7 +56,7 @@ def query_bf16(params, o, w, in_freqs):
             "normal": omlp.normal_from_gradient(g[:, :3], w)}
 
 
-def train_grad_bf16(params, o, w, in_freqs, gy=None, dist_gt=None, hit_gt=None, snap=False):
+def train_grad_bf16(params, o, w, in_freqs, gy=None, dist_gt=None, hit_gt=None, snap=False, bias_in_mma=True):
     """The reverse pass of the tensor-core training path with its BF16 rounding points: the
     encoded input, the hidden-layer weights, every hidden activation (the last one included:
     the output head reads it from memory), every delta; the output weights, y, G and the
@@ -61,7 +73,7 @@ def train_grad_bf16(params, o, w, in_freqs, gy=None, dist_gt=None, hit_gt=None, 
     acts, masks = [a], []
     for l in range(L):
         Wl, b = params[l]
-        z = a @ bf16(Wl).T + b
+        z = a @ bf16(Wl).T + (split_bias(b) if bias_in_mma else b)
         masks.append(z > 0)
         a = np.maximum(z, 0.0)
         if l < L - 1:
