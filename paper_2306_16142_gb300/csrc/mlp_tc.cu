@@ -173,14 +173,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* act = smem;
     uint8_t* wst = smem + a.off_wst;
     uint32_t* masks = reinterpret_cast<uint32_t*>(smem + a.off_mask);
-    float* bias_s = reinterpret_cast<float*>(smem + a.off_bias);
+    uint8_t* ones = smem + a.off_grp;       // 4 KB: the A operand of the bias MMA
+    uint8_t* bslot = smem + a.off_bias;     // the current forward layer's bias tile
     float* head_s = reinterpret_cast<float*>(smem + a.off_head);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
     uint64_t* full = bars;
     uint64_t* empty = bars + NST;
     uint64_t* actr = bars + 2 * NST;
     uint64_t* accf = actr + KMAXB;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 2);
+    uint64_t* bfull = accf + 2;             // bias slot loaded / consumed
+    uint64_t* bempty = bfull + 1;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bempty + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int64_t n = a.n;
@@ -213,6 +216,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int i = 0; i < KMAXB; ++i) mbar_init(&actr[i], 256);
         mbar_init(&accf[0], 1);
         mbar_init(&accf[1], 1);
+        mbar_init(bfull, 1);
+        mbar_init(bempty, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -220,7 +225,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    for (int i = tid; i < L * W; i += kThreads) bias_s[i] = a.bias[i];
+    // the ones tile: K rows 0 and 1 of both 64-row MN atoms are 1.0 (BF16 0x3F80), the rest 0
+    for (int i = tid; i < 1024; i += kThreads)
+        reinterpret_cast<uint32_t*>(ones)[i] = ((i >> 5) & 15) < 2 ? 0x3F803F80u : 0u;
+    fence_proxy_async();
     for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
     __syncthreads();
     tc_fence_after();
@@ -229,13 +237,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == kEpiWarps) {
         // ---------------------------------------------------------------- TMA producer
         if (lane == 0) {
-            uint32_t cnt = 0;
+            uint32_t cnt = 0, nb = 0;
             bool ok = true;
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 const TileInfo ti = tile_info(t);
                 const int nsteps = MODE == 1 ? 2 * ti.L : ti.L;
                 for (int s = 0; s < nsteps && ok; ++s) {
                     const Step st = step_of<W>(s, ti.L, ti.KB0);
+                    if (!st.bwd) {   // the forward layer's bias tile into its slot
+                        if (!mbar_wait(bempty, (nb & 1u) ^ 1u, a.err)) { ok = false; break; }
+                        mbar_expect_tx(bfull, (uint32_t)W * 32u);
+                        bulk_load(bslot, a.bias_mn + (size_t)st.layer * W * 32, (uint32_t)W * 32u, bfull);
+                        ++nb;
+                    }
                     for (int kb = 0; kb < st.nk; ++kb, ++cnt) {
                         const int stg = (int)(cnt % (uint32_t)NST);
                         const uint32_t ph = (cnt / (uint32_t)NST) & 1u;
@@ -250,9 +264,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == kEpiWarps + 1) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            uint32_t cnt = 0, g = 0, actph = 0;
+            uint32_t cnt = 0, g = 0, actph = 0, nb = 0;
             bool ok = true;
             const uint32_t act_s = su32(act), wst_s = su32(wst);
+            const uint32_t idesc_b = idesc_bf16(128, W) | (3u << 15);   // bias MMA: both operands MN-major
+            const uint64_t ones_d = sdesc_mn16(su32(ones)), bias_d = sdesc_mn16(su32(bslot));
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 const TileInfo ti = tile_info(t);
                 const int nsteps = MODE == 1 ? 2 * ti.L : ti.L;
@@ -266,12 +282,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (!mbar_wait(&full[stg], ph, a.err)) { ok = false; break; }
                         if (!mbar_wait(&actr[kb], (actph >> kb) & 1u, a.err)) { ok = false; break; }
                         actph ^= 1u << kb;
+                        if (!st.bwd && kb == 0) {   // forward: the accumulator starts as the bias
+                            if (!mbar_wait(bfull, nb & 1u, a.err)) { ok = false; break; }
+                            ++nb;
+                            tc_fence_after();
+                            mma_bf16(d, ones_d, bias_d, idesc_b, 0u);
+                            mma_commit(bempty);
+                        }
                         tc_fence_after();
                         const uint64_t ad = sdesc(act_s + (uint32_t)kb * 16384u);
                         const uint64_t bd = sdesc(wst_s + (uint32_t)stg * (uint32_t)W * 128u);
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
-                            mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                            mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, st.bwd ? (uint32_t)((kb | k) != 0) : 1u);
                         mma_commit(&empty[stg]);
                     }
                     if (ok) mma_commit(&accf[g & 1u]);
@@ -353,29 +376,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int i = 0; i < PB; ++i) TC_LD32(tcol + (2 * pass + i) * 64, raw[i]);
                     tc_wait_ld();
                     if (s < Lt) {
-                        const float* bs = bias_s + s * W;
 #pragma unroll
                         for (int i = 0; i < PB; ++i) {
                             const int kb = 2 * pass + i;
                             const int c0 = kb * 64 + grp * 32;
-                            const float4* b4 = reinterpret_cast<const float4*>(bs + c0);
                             if (s < Lt - 1) {
-                                // a = ReLU(acc + b) rounded to BF16 -> next A operand
+                                // a = ReLU(acc) rounded to BF16 -> next A operand (the bias is in acc)
                                 uint32_t pk[16];
-                                uint32_t bits = 0;
 #pragma unroll
-                                for (int q = 0; q < 8; ++q) {
-                                    const float4 bb = b4[q];
-                                    float z0, z1, z2, z3;
-                                    add2(__uint_as_float(raw[i][4 * q]), __uint_as_float(raw[i][4 * q + 1]), bb.x,
-                                         bb.y, z0, z1);
-                                    add2(__uint_as_float(raw[i][4 * q + 2]), __uint_as_float(raw[i][4 * q + 3]),
-                                         bb.z, bb.w, z2, z3);
-                                    pk[2 * q] = pack_relu(z0, z1);
-                                    pk[2 * q + 1] = pack_relu(z2, z3);
-                                    bits |= (pos(z0) | pos(z1) << 1 | pos(z2) << 2 | pos(z3) << 3) << (4 * q);
-                                }
-                                masks[(s * (W / 32) + (c0 >> 5)) * 128 + r] = bits;
+                                for (int q = 0; q < 16; ++q)
+                                    pk[q] = pack_relu(__uint_as_float(raw[i][2 * q]), __uint_as_float(raw[i][2 * q + 1]));
+                                masks[(s * (W / 32) + (c0 >> 5)) * 128 + r] = pos_bits32(raw[i]);
 #pragma unroll
                                 for (int m = 0; m < 4; ++m)
                                     st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
@@ -385,12 +396,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 // delta of the last hidden layer: W_out[0] on active units
                                 uint32_t pk[16];
 #pragma unroll
-                                for (int q = 0; q < 16; ++q) {
-                                    const float z0 = __uint_as_float(raw[i][2 * q]) + bs[c0 + 2 * q];
-                                    const float z1 = __uint_as_float(raw[i][2 * q + 1]) + bs[c0 + 2 * q + 1];
-                                    pk[q] = pack_bf16(z0 > 0.f ? head_s[c0 + 2 * q] : 0.f,
-                                                      z1 > 0.f ? head_s[c0 + 2 * q + 1] : 0.f);
-                                }
+                                for (int q = 0; q < 16; ++q)
+                                    pk[q] = pack_bf16((int)raw[i][2 * q] > 0 ? head_s[c0 + 2 * q] : 0.f,
+                                                      (int)raw[i][2 * q + 1] > 0 ? head_s[c0 + 2 * q + 1] : 0.f);
 #pragma unroll
                                 for (int m = 0; m < 4; ++m)
                                     st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
@@ -823,12 +831,6 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Shared memory per CTA (W = 256): 2 x 64 KB activation tiles, 2 stages of 32 KB weights + 8 KB
 // bias, the 4 KB ones tile, the output head.
 
-// MN-major 128-byte-swizzled operand of 16 K rows: 64-wide MN atoms 2 KB apart (LBO), the two
-// 8-row K groups 1 KB apart (SBO).
-__device__ __forceinline__ uint64_t sdesc_mn16(uint32_t saddr) {
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(2048 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
 
 // One pair of tiles: its rows and its network (GRP: an object of a grouped launch, whose pairs
 // are numbered by a device prefix table; otherwise rows [256 p, 256 p + 256) of the one network).
@@ -1723,22 +1725,25 @@ struct Layout {
 };
 
 // Shared memory of the normals kernel: the A tile, the weight ring, the ReLU masks of every
-// hidden layer (a bit per row and unit), the biases and the output head.
+// hidden layer (a bit per row and unit), the ones tile and the bias slot of the bias MMA (both
+// 1 KB aligned) and the output head.
 Layout smem_layout(int W, int L, int K0) {
     Layout s{};
     const int kmaxb = std::max(K0 / 64, W / 64);
     const uint32_t act = (uint32_t)kmaxb * 16384u;
     const uint32_t stage = (uint32_t)W * 128u;
-    const uint32_t mask = (uint32_t)L * 128u * (W / 32) * 4u;
-    const uint32_t bias = (uint32_t)L * W * 4u;
+    const uint32_t mask = ((uint32_t)L * 128u * (W / 32) * 4u + 1023u) & ~1023u;
+    const uint32_t ones = 4096u;
+    const uint32_t bias = (uint32_t)W * 32u;
     const uint32_t head = ((uint32_t)(2 * W + 2) * 4u + 15u) & ~15u;
-    const uint32_t fixed = act + mask + bias + head + 512u;
+    const uint32_t fixed = act + mask + ones + bias + head + 512u;
     const uint32_t budget = 227u * 1024u - 1024u;   // minus alignment slack
     int nst = (int)((budget - fixed) / stage);
     s.nst = std::max(0, std::min(8, nst));
     s.off_wst = act;
     s.off_mask = act + (uint32_t)s.nst * stage;
-    s.off_bias = s.off_mask + mask;
+    s.off_grp = s.off_mask + mask;   // ones tile
+    s.off_bias = s.off_grp + ones;   // bias slot
     s.off_head = s.off_bias + bias;
     s.off_bar = s.off_head + head;
     s.total = s.off_bar + 512u + 1024u;
@@ -1767,9 +1772,11 @@ int launch_mode(const ddf_net_s* net, int mode, const TcArgs& base, int64_t n, b
     a.nst = nst_override > 0 ? std::min(nst_override, s.nst) : s.nst;
     a.off_wst = s.off_wst;
     a.off_mask = s.off_mask;
+    a.off_grp = s.off_grp;
     a.off_bias = s.off_bias;
     a.off_head = s.off_head;
     a.off_bar = s.off_bar;
+    a.bias_mn = P->bias_mn;
     int grid = use_count ? num_sms() : (int)std::min<int64_t>((n + kTileM - 1) / kTileM, num_sms());
     if (grid_override > 0) grid = grid_override;
     if (grid <= 0) return DDF_OK;

@@ -44,8 +44,8 @@ def test_bf16_query_parity(P, F, W, L, seed, n):
     assert (g["hit"][clear] == r["hit"][clear]).all()
     # normals: the reverse pass must reproduce the BF16 arithmetic model (tests/_bf16_model.py);
     # its distance from the FP64 normal is the BF16 network's own and is reported, not bounded.
-    # The normals launch recomputes the forward with the FP32 bias added after the accumulation.
-    m = query_bf16(Pm, o, w, F, bias_in_mma=False)
+    # Widths 128 / 256 add the bias inside the MMA; width 512 adds it in FP32 after the MMAs.
+    m = query_bf16(Pm, o, w, F, bias_in_mma=W <= 256)
     h = (g["hit"] == 1) & (m["hit"]) & clear
     gn = np.linalg.norm(m["grad"][:, :3], axis=1)
     kappa_clear = np.abs(np.sum(m["grad"][:, :3] * w, 1)) >= 0.02 * gn
