@@ -192,23 +192,6 @@ class DDFMesh:
         self.h = h
         self.nt = t.shape[0]
 
-    @classmethod
-    def load(cls, path: str):
-        """A new handle from a checkpoint written by save() (weights, precision, Adam state)."""
-        obj = cls.__new__(cls)
-        h = C.c_void_p()
-        check("ddf_load", _abi.load().ddf_load(str(path).encode(), C.byref(h)))
-        obj.h = h
-        n = C.c_int64()
-        check("ddf_num_params", _abi.load().ddf_num_params(h, C.byref(n)))
-        obj.n_params = n.value
-        obj.arch = None
-        obj.precision = None
-        return obj
-
-    def save(self, path: str):
-        check("ddf_save", _abi.load().ddf_save(self.h, str(path).encode()))
-
     def close(self):
         if getattr(self, "h", None):
             _abi.load().ddf_mesh_destroy(self.h)
@@ -260,23 +243,6 @@ class DDFGroup:
         h = C.c_void_p()
         check("ddf_group_create", _abi.load().ddf_group_create(len(self.nets), arr, C.byref(h)))
         self.h = h
-
-    @classmethod
-    def load(cls, path: str):
-        """A new handle from a checkpoint written by save() (weights, precision, Adam state)."""
-        obj = cls.__new__(cls)
-        h = C.c_void_p()
-        check("ddf_load", _abi.load().ddf_load(str(path).encode(), C.byref(h)))
-        obj.h = h
-        n = C.c_int64()
-        check("ddf_num_params", _abi.load().ddf_num_params(h, C.byref(n)))
-        obj.n_params = n.value
-        obj.arch = None
-        obj.precision = None
-        return obj
-
-    def save(self, path: str):
-        check("ddf_save", _abi.load().ddf_save(self.h, str(path).encode()))
 
     def close(self):
         if getattr(self, "h", None):
