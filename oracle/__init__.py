@@ -19,6 +19,8 @@ Modules and the passages they follow:
 * ``sphere``  - the analytic DDF of a sphere (closed form for the definitions of Sec. 3.1).
 * ``render``  - the modified uni-directional path tracer (Sec. 1, Fig. 1): camera rays,
   one DDF query per bounce, Lambertian shading with cosine-hemisphere sampling.
+* ``sampler`` - the surface-marching training-set sampler of Sec. 5.2 (Eqs. 8-12) with the
+  odd-even inside test, built on ``label``.
 
 Every floating-point step runs in float64 from the float32 inputs (promoted exactly).
 Where the paper is silent, the readings used are listed in each module's docstring.
