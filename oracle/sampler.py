@@ -37,7 +37,8 @@ Readings (the paper is silent or garbled):
   multiple of 2^-24 or 2^-25) come from ``sincospi``: an exact reduction of u to r in
   [-1/4, 1/4] and Taylor series of sin(pi r) and cos(pi r) in float64 in a fixed order, rounded
   to float32 at the end (the GPU evaluates the same series). t_end for a miss is
-  -b + sqrt(b^2 - c), b = p.theta, c = |p|^2 - 1, in float64 rounded to float32.
+  -b + sqrt(b^2 - c), b = p.theta, c = |p|^2 - 1 (dot products summed x, y, then z), in float64
+  rounded to float32.
 * Every sample carries a key ((c s_p + k - 1) 4 + kind), kind 0 for Eq. 10, 1 for Eq. 11, 2 and 3
   for Eq. 12 (+ then -); samples come out in key order.
 """
@@ -154,8 +155,8 @@ def sample_surface(verts, tris, s_fc: int, s_dr: int, s_p: int, eps: float, seed
     par = crossing_parity(V, F, ro, th)
     # t_end: the hit distance from p, or the exit through the unit sphere for a miss
     p64, th64 = p.astype(np.float64), th.astype(np.float64)
-    bq = np.sum(p64 * th64, axis=1)
-    cq = np.sum(p64 * p64, axis=1) - 1.0
+    bq = (p64[:, 0] * th64[:, 0] + p64[:, 1] * th64[:, 1]) + p64[:, 2] * th64[:, 2]
+    cq = ((p64[:, 0] * p64[:, 0] + p64[:, 1] * p64[:, 1]) + p64[:, 2] * p64[:, 2]) - 1.0
     with np.errstate(invalid="ignore"):
         t_exit = (-bq + np.sqrt(bq * bq - cq)).astype(np.float32)
     t_end = np.where(hit1 == 1, e32 + dist1, t_exit).astype(np.float32)
