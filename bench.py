@@ -199,7 +199,7 @@ def main():
     ap.add_argument("--no-rows", action="store_true", help="skip the labelling / training / grouped rows")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: 512 x 512 x 8 spp (2^21 paths) for profiler captures")
-    ap.add_argument("--row", default=None, choices=["label", "train", "grouped", "w512"],
+    ap.add_argument("--row", default=None, choices=["label", "sampler", "train", "grouped", "w512"],
                     help="run only this row's workload (for profiler captures) and print it")
     args = ap.parse_args()
     if args.size == "small":
@@ -446,6 +446,28 @@ def other_rows(P, torch, np, peaks, only=None):
                                       "note": "34 FP32 operations per filter test (count of the hot loop; the "
                                               "thread's two rays run as the lanes of packed FP32 pairs)"},
                          "hbm_gbs": (o.shape[0] * 33) / sec / 1e9}
+    # ---- the surface-marching training-set sampler (Sec. 5.2), Table 2's smallest setting
+    if want("sampler"):
+        s = 10
+        C = F.shape[0] * s * s
+        first = mesh.sample_surface(s, s, s, 1e-4, 21)
+        buf = P.DDFMesh.sample_buffers(first["count"])
+        sec = _time(torch, lambda: mesh.sample_surface(s, s, s, 1e-4, 21, out=buf), 2)
+        n = first["count"]
+        kinds = np.bincount((first["key"] % 4).cpu().numpy(), minlength=4)
+        rays = C + 2 * int(kinds[1])      # candidates + two Eq. 12 rays per march point of a missing one
+        tests = rays * F.shape[0]
+        alu_peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+        rows["sampler"] = {"workload": "s_fc = s_dr = s_p = 10 on the 8,192-triangle (3,2) knot: 819,200 candidate "
+                                       "rays, odd-even parity, marching, Eq. 12 rays of the missing candidates",
+                           "samples": n, "samples_per_s": n / sec, "ms": sec * 1e3,
+                           "kinds": [int(x) for x in kinds], "labelled_rays": rays,
+                           "roofline": {"bound": "alu", "achieved": tests / sec * 34 / 1e12,
+                                        "peak": alu_peak / 1e12, "unit": "T FP32-instr/s",
+                                        "frac": tests / sec * 34 / alu_peak,
+                                        "note": "the labeller's filter tests over the whole call (allocation, "
+                                                "two host scans and the other kernels included)"}}
+        del first, buf
     # ---- a9 training step: BF16 tensor-core GEMMs (FP32 accumulate, FP32 masters), and the FP32 path
     if want("train"):
         Fq, Wd, Ld = 12, 256, 8

@@ -270,6 +270,41 @@ DDF_API int ddf_label_rays(ddf_mesh mesh, const float* d_origins, const float* d
  * Synchronises with the stream of that call. */
 DDF_API int ddf_label_stats(ddf_mesh mesh, int64_t* host_counts);
 
+/* ---- training-set sampling --------------------------------------------------------------- */
+
+/* Parameters of the surface-marching sampler (Sec. 5.2, Eqs. 8-12). */
+typedef struct {
+    int32_t s_fc;   /* points per face (Eq. 8) */
+    int32_t s_dr;   /* directions per point (Eq. 9) */
+    int32_t s_p;    /* march points per ray (Eqs. 10-12) */
+    float eps;      /* offset of the cast ray's origin along theta (scene units, >= 0) */
+    uint64_t seed;  /* Philox4x32-10 key */
+} ddf_sampler;
+
+/* The surface-marching training set of a mesh (Sec. 5.2). For every face, s_fc points (Eq. 8; a
+ * pair with a + b > 1 is reflected to (1 - a, 1 - b)); for every point, s_dr directions (Eq. 9:
+ * polar angle a pi, azimuth 2 b pi). Each (point p, direction theta) ray is cast from
+ * p + eps theta. If it crosses the mesh an odd number of times it starts inside (the odd-even
+ * rule) and is dropped. Otherwise s_p points q_k = p + t_k theta, t_k = t_end k / (s_p + 1),
+ * split the way to its first hit (t_end = eps + hit distance), or, for a ray that hits nothing,
+ * the way to the unit sphere. They give the samples
+ *   Eq. 10: (q_k, -theta; t_k, hit 1);
+ *   Eq. 11: (q_k, theta; +inf, hit 0), for rays that hit nothing;
+ *   Eq. 12: (q_k, theta_perp; +inf, hit 0), for rays that hit nothing: the two directions at
+ *           polar angle +- pi/2 (same azimuth) whose own ray from q_k hits nothing.
+ * Outputs (DEVICE, caller-owned, cap rows each): origins cap x 3, dirs cap x 3, dist (+inf for
+ * the infinite samples), hit, key (int64 ((c s_p + k - 1) 4 + kind), c = (f s_fc + i) s_dr + j
+ * the candidate, kind 0 / 1 / 2 / 3 for Eq. 10 / 11 / 12 (+) / 12 (-)), in key order.
+ * *host_count gets the number of samples; rows beyond cap are not written. Random numbers:
+ * counter (f s_fc + i, 0, 2, 0) for the point, (c, 0, 3, 0) for the direction, u = (word >> 8)
+ * 2^-24. Every decision is the float64 labelling test of ddf_label_rays; coordinates are float32
+ * in a fixed order and the sines and cosines come from a float64 series, so the result is a
+ * deterministic function of the inputs. Synchronous; allocates a workspace of about 180 bytes
+ * per march point (faces x s_fc x s_dr x s_p). Errors: INVALID_ARG, OOM, CUDA. */
+DDF_API int ddf_sample_surface(ddf_mesh mesh, const ddf_sampler* params, float* d_origins, float* d_dirs,
+                               float* d_dist, uint8_t* d_hit, int64_t* d_key, int64_t cap, int64_t* host_count,
+                               cudaStream_t stream);
+
 /* ---- training ---------------------------------------------------------------------------- */
 
 /* Reverse pass of the network for output cotangents (g_dist, g_logit) (device, n each):

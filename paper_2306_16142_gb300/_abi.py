@@ -30,6 +30,11 @@ class DDFError(RuntimeError):
         self.code = code
 
 
+class ddf_sampler(C.Structure):
+    _fields_ = [("s_fc", C.c_int32), ("s_dr", C.c_int32), ("s_p", C.c_int32), ("eps", C.c_float),
+                ("seed", C.c_uint64)]
+
+
 class ddf_arch(C.Structure):
     _fields_ = [("in_freqs", C.c_int), ("width", C.c_int), ("hidden_layers", C.c_int),
                 ("precision", C.c_int)]
@@ -77,6 +82,7 @@ _SIG = {
     "ddf_mesh_create": (C.c_int, [_P, _I64, _P, _I64, C.POINTER(_P)]),
     "ddf_mesh_destroy": (C.c_int, [_P]),
     "ddf_label_rays": (C.c_int, [_P, _P, _P, _I64, _P, _P, _P, _P]),
+    "ddf_sample_surface": (C.c_int, [_P, C.POINTER(ddf_sampler), _P, _P, _P, _P, _P, _I64, C.POINTER(_I64), _P]),
     "ddf_label_stats": (C.c_int, [_P, C.POINTER(_I64)]),
     "ddf_backward": (C.c_int, [_P, _P, _P, _I64, _P, _P, _P, _P, _P]),
     "ddf_train_step": (C.c_int, [_P, _P, _P, _P, _P, _I64, C.POINTER(ddf_adam), _P, _P]),

@@ -356,6 +356,21 @@ int ddf_label_rays(ddf_mesh mesh, const float* d_origins, const float* d_dirs, i
     return label_rays(mesh, d_origins, d_dirs, n, d_dist, d_hit, d_tri, stream);
 }
 
+int ddf_sample_surface(ddf_mesh mesh, const ddf_sampler* params, float* d_origins, float* d_dirs, float* d_dist,
+                       uint8_t* d_hit, int64_t* d_key, int64_t cap, int64_t* host_count, cudaStream_t stream) {
+    if (!mesh || !params || !host_count) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    if (params->s_fc < 0 || params->s_dr < 0 || params->s_p < 0)
+        return fail(DDF_ERR_INVALID_ARG, "negative sample counts");
+    if (!(params->eps >= 0.f) || !isfinite(params->eps)) return fail(DDF_ERR_INVALID_ARG, "eps must be finite, >= 0");
+    if (cap < 0) return fail(DDF_ERR_INVALID_ARG, "cap < 0");
+    if (cap > 0 && (!d_origins || !d_dirs || !d_dist || !d_hit || !d_key))
+        return fail(DDF_ERR_INVALID_ARG, "outputs must be non-NULL when cap > 0");
+    const double slots = (double)mesh->nt * params->s_fc * params->s_dr * params->s_p * 4.0;
+    if (slots > 4.0e9) return fail(DDF_ERR_INVALID_ARG, "too many samples (%g slots)", slots);
+    return sample_surface(mesh, params->s_fc, params->s_dr, params->s_p, params->eps, params->seed, d_origins, d_dirs,
+                          d_dist, d_hit, d_key, cap, host_count, stream);
+}
+
 int ddf_label_stats(ddf_mesh mesh, int64_t* host_counts) {
     if (!mesh || !host_counts) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
     DDF_CUDA_TRY(cudaStreamSynchronize(mesh->last_stream));

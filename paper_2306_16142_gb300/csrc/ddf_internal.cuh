@@ -147,8 +147,13 @@ int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* i
 
 // ------------------------------------------------------------------ labelling (label.cu)
 int mesh_prepare(ddf_mesh_s* m, const float* host_verts, const int32_t* host_tris);
+// parity (optional): the parity of the number of faces each ray crosses at t > 0.
 int label_rays(ddf_mesh_s* m, const float* o, const float* w, int64_t n, float* dist,
-               uint8_t* hit, int32_t* tri, cudaStream_t stream);
+               uint8_t* hit, int32_t* tri, cudaStream_t stream, uint8_t* parity = nullptr);
+// The surface-marching sampler of Sec. 5.2 (ddf_sample_surface).
+int sample_surface(ddf_mesh_s* m, int s_fc, int s_dr, int s_p, float eps, uint64_t seed, float* d_o, float* d_w,
+                   float* d_dist, uint8_t* d_hit, int64_t* d_key, int64_t cap, int64_t* host_count,
+                   cudaStream_t stream);
 
 // ------------------------------------------------------------------ training (train.cu)
 int backward(ddf_net_s* net, const float* o, const float* w, int64_t n, const float* gdist,

@@ -10,7 +10,7 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import check, ddf_adam, ddf_arch, ddf_camera
+from ._abi import check, ddf_adam, ddf_arch, ddf_camera, ddf_sampler
 
 PRECISIONS = {"fp32": _abi.DDF_FP32, "bf16": _abi.DDF_BF16, "fp8": _abi.DDF_FP8}
 
@@ -216,6 +216,37 @@ class DDFMesh:
         arr = (C.c_int64 * 2)()
         check("ddf_label_stats", _abi.load().ddf_label_stats(self.h, arr))
         return {"retests": arr[0], "finals": arr[1]}
+
+    @staticmethod
+    def sample_buffers(cap: int):
+        """Output tensors for sample_surface holding up to cap samples."""
+        dev = torch.device("cuda")
+        n = max(cap, 1)
+        return {"o": torch.empty(n, 3, device=dev), "w": torch.empty(n, 3, device=dev),
+                "dist": torch.empty(n, device=dev), "hit": torch.empty(n, dtype=torch.uint8, device=dev),
+                "key": torch.empty(n, dtype=torch.int64, device=dev)}
+
+    def sample_surface(self, s_fc: int, s_dr: int, s_p: int, eps: float = 1e-4, seed: int = 0,
+                       cap: int | None = None, out: dict | None = None):
+        """The surface-marching training set of Sec. 5.2 (ddf_sample_surface): dict of CUDA
+        tensors o (n, 3), w (n, 3), dist (n,), hit (n,) and key (n,), in key order, and the
+        total count (which may exceed cap). out: buffers from sample_buffers to reuse; cap
+        defaults to their size, else to the 4 s_p samples of every candidate."""
+        if out is None:
+            cap = self.nt * s_fc * s_dr * s_p * 4 if cap is None else cap
+            out = self.sample_buffers(cap)
+        else:
+            room = out["key"].shape[0]
+            cap = room if cap is None else min(cap, room)
+        prm = ddf_sampler(s_fc, s_dr, s_p, eps, seed)
+        n = C.c_int64()
+        check("ddf_sample_surface", _abi.load().ddf_sample_surface(
+            self.h, C.byref(prm), _ptr(out["o"]), _ptr(out["w"]), _ptr(out["dist"]), _ptr(out["hit"]),
+            _ptr(out["key"]), cap, C.byref(n), _stream()))
+        k = min(n.value, cap)
+        res = {name: t[:k] for name, t in out.items()}
+        res["count"] = n.value
+        return res
 
 
 def camera_struct(cam) -> ddf_camera:
