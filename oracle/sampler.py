@@ -1,6 +1,7 @@
-"""The surface-marching training-set sampler of Sec. 5.2 (Eqs. 8-12) with the odd-even inside
-test, in float64 where it decides and in a stated float32 order where it produces coordinates.
-Test infrastructure only (see the package docstring).
+"""The training-set samplers: surface marching of Sec. 5.2 (Eqs. 8-12) with the odd-even inside
+test, and the point-of-view baseline of Sec. 6 (at the end of this module), in float64 where
+they decide and in a stated float32 order where they produce coordinates. Test infrastructure
+only (see the package docstring).
 
 For every face, s_fc points (Eq. 8); for every point, s_dr directions (Eq. 9); every (point,
 direction) ray is marched and the field values along it are collected (Eqs. 10-12):
@@ -203,3 +204,83 @@ def sample_surface(verts, tris, s_fc: int, s_dr: int, s_p: int, eps: float, seed
     res["cand_dir"] = th
     res["cand_point"] = p
     return res
+
+
+# --------------------------------------------------------------------------- POV sampling
+# The point-of-view baseline of Sec. 6 (Fig. 7's "pov" curve): cameras spaced uniformly in
+# azimuth and polar angle around the mesh centre, aimed at it; every pixel's ray is labelled.
+#
+# Readings (the paper gives only the camera counts, 10 x 5):
+# * camera (i, j), i < n_az, j < n_pol, has azimuth phi_i = 2 pi i / n_az and polar angle
+#   theta_j = pi (j + 1) / (n_pol + 1) (uniform, the poles excluded, where the azimuth is
+#   degenerate); it sits at distance `dist` from the origin (the mesh lies in the unit ball) and
+#   looks at the origin with +z up: eye = dist (s_t c_p, s_t s_p, c_t), forward -eye / dist, right
+#   (-s_p, c_p, 0), up (-c_t c_p, -c_t s_p, s_t) (right x up = -forward: a right-handed camera);
+# * the film is res x res pixels with tan(fov / 2) = tan_half_fov; pixel (x, y), y counted from
+#   the top row, has its ray through the pixel centre: px = ((2x + 1) / res - 1) tan_half_fov,
+#   py = (1 - (2y + 1) / res) tan_half_fov;
+# * a ray starts where it enters the unit ball (the field's domain, Sec. 3.1), or at the eye if
+#   it misses the ball (it then misses the mesh too); its label is the nearest-hit distance from
+#   there (the labelling of ``oracle.label``);
+# * rays are stored camera by camera (c = j n_az + i), each camera's rows top to bottom.
+#
+# Arithmetic: sin / cos from ``sincospi`` (its reduction r = u - n / 2 is exact for every u by
+# Sterbenz's lemma); eye and frame in float64, rounded to float32 once; px, py in float64,
+# rounded once; the unnormalised direction (f + px r) + py u in float32 without fused
+# multiply-adds; its length and the division in float64 (sums x, y, z in order); the entry
+# distance t0 = max(0, -b - sqrt(b^2 - c)), b = eye.w, c = |eye|^2 - 1, in float64, and the
+# origin eye + t0 w in float64, rounded once.
+
+
+def pov_cameras(n_az: int, n_pol: int, dist: float):
+    """(eye, forward, right, up) float32 arrays of shape (n_az n_pol, 3), camera c = j n_az + i."""
+    i = np.tile(np.arange(n_az, dtype=np.float64), n_pol)
+    j = np.repeat(np.arange(n_pol, dtype=np.float64), n_az)
+    sp, cp = sincospi(2.0 * i / float(n_az))
+    st, ct = sincospi((j + 1.0) / float(n_pol + 1))
+    d = float(np.float32(dist))
+    dirv = np.stack([st * cp, st * sp, ct], axis=1)                    # unit vector to the eye
+    eye = (d * dirv).astype(np.float32)
+    fwd = (-dirv).astype(np.float32)
+    right = np.stack([-sp, cp, np.zeros_like(sp)], axis=1).astype(np.float32)
+    up = np.stack([-(ct * cp), -(ct * sp), st], axis=1).astype(np.float32)
+    return eye, fwd, right, up
+
+
+def pov_rays(n_az: int, n_pol: int, res: int, dist: float, tan_half_fov: float):
+    """Every pixel ray of every camera: float32 origins and unit directions (N, 3), N =
+    n_az n_pol res^2, in the stored order."""
+    eye, fwd, right, up = pov_cameras(n_az, n_pol, dist)
+    th = float(np.float32(tan_half_fov))
+    pix = np.arange(res, dtype=np.float64)
+    px = (((2.0 * pix + 1.0) / res - 1.0) * th).astype(np.float32)    # by column x
+    py = ((1.0 - (2.0 * pix + 1.0) / res) * th).astype(np.float32)    # by row y
+    ncam = eye.shape[0]
+    PX = np.broadcast_to(px[None, None, :, None], (ncam, res, res, 1))
+    PY = np.broadcast_to(py[None, :, None, None], (ncam, res, res, 1))
+    F_ = fwd[:, None, None, :]
+    R_ = right[:, None, None, :]
+    U_ = up[:, None, None, :]
+    d = ((F_ + PX * R_) + PY * U_).reshape(-1, 3)                     # float32, no FMA
+    d64 = d.astype(np.float64)
+    n2 = (d64[:, 0] * d64[:, 0] + d64[:, 1] * d64[:, 1]) + d64[:, 2] * d64[:, 2]
+    w = (d64 / np.sqrt(n2)[:, None]).astype(np.float32)
+    e = np.repeat(eye, res * res, axis=0).astype(np.float64)
+    w64 = w.astype(np.float64)
+    b = (e[:, 0] * w64[:, 0] + e[:, 1] * w64[:, 1]) + e[:, 2] * w64[:, 2]
+    c = ((e[:, 0] * e[:, 0] + e[:, 1] * e[:, 1]) + e[:, 2] * e[:, 2]) - 1.0
+    disc = b * b - c
+    with np.errstate(invalid="ignore"):
+        sq = np.sqrt(disc)
+    enter = (disc > 0.0) & (-b + sq > 0.0)
+    t0 = np.where(enter, np.maximum(0.0, -b - sq), 0.0)
+    o = (e + t0[:, None] * w64).astype(np.float32)
+    return o, w
+
+
+def sample_pov(verts, tris, n_az: int = 10, n_pol: int = 5, res: int = 64, dist: float = 2.5,
+               tan_half_fov: float = 0.2679491924311227):
+    """POV samples: dict o, w (N, 3) float32, dist (N,) float32 (inf on a miss), hit (N,) uint8."""
+    o, w = pov_rays(n_az, n_pol, res, dist, tan_half_fov)
+    d, h, _, _ = label_rays(verts, tris, o, w)
+    return {"o": o, "w": w, "dist": d, "hit": h}
