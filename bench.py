@@ -199,7 +199,7 @@ def main():
     ap.add_argument("--no-rows", action="store_true", help="skip the labelling / training / grouped rows")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: 512 x 512 x 8 spp (2^21 paths) for profiler captures")
-    ap.add_argument("--row", default=None, choices=["label", "sampler", "train", "grouped", "w512"],
+    ap.add_argument("--row", default=None, choices=["label", "sampler", "pov", "train", "grouped", "w512"],
                     help="run only this row's workload (for profiler captures) and print it")
     args = ap.parse_args()
     if args.size == "small":
@@ -468,6 +468,21 @@ def other_rows(P, torch, np, peaks, only=None):
                                         "note": "the labeller's filter tests over the whole call (allocation, "
                                                 "two host scans and the other kernels included)"}}
         del first, buf
+    # ---- the point-of-view sampling of Sec. 6: 10 x 5 cameras, 256 x 256 films
+    if want("pov"):
+        n = 50 * 256 * 256
+        pbuf = mesh.sample_pov(10, 5, 256)
+        sec = _time(torch, lambda: mesh.sample_pov(10, 5, 256, out=pbuf), 3)
+        tests = n * F.shape[0]
+        alu_peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+        rows["pov"] = {"workload": "10 x 5 cameras at distance 2.5, 30 deg field of view, 256 x 256 pixels each "
+                                   "(3,276,800 rays) labelled against the 8,192-triangle (3,2) knot",
+                       "rays_per_s": n / sec, "ms": sec * 1e3, "hits": int(pbuf["hit"].sum().item()),
+                       "roofline": {"bound": "alu", "achieved": tests / sec * 34 / 1e12,
+                                    "peak": alu_peak / 1e12, "unit": "T FP32-instr/s",
+                                    "frac": tests / sec * 34 / alu_peak,
+                                    "note": "the labeller's filter tests; ray generation included"}}
+        del pbuf
     # ---- a9 training step: BF16 tensor-core GEMMs (FP32 accumulate, FP32 masters), and the FP32 path
     if want("train"):
         Fq, Wd, Ld = 12, 256, 8

@@ -305,6 +305,29 @@ DDF_API int ddf_sample_surface(ddf_mesh mesh, const ddf_sampler* params, float* 
                                float* d_dist, uint8_t* d_hit, int64_t* d_key, int64_t cap, int64_t* host_count,
                                cudaStream_t stream);
 
+/* Parameters of ddf_sample_pov. */
+typedef struct ddf_pov {
+    int32_t n_az;        /* cameras around the azimuth (10 in Sec. 6) */
+    int32_t n_pol;       /* cameras around the polar angle (5 in Sec. 6) */
+    int32_t res;         /* film side in pixels (res x res) */
+    float dist;          /* camera distance from the origin (> 0; > 1 puts the eye outside the unit ball) */
+    float tan_half_fov;  /* tangent of half the field of view (> 0) */
+} ddf_pov;
+
+/* The point-of-view training set of a mesh (the "pov" sampling of Sec. 6): n_az x n_pol cameras
+ * aimed at the origin, camera (i, j) at azimuth 2 pi i / n_az and polar angle pi (j + 1) /
+ * (n_pol + 1) (uniform, poles excluded), distance dist, +z up (right = (-sin az, cos az, 0));
+ * every pixel's ray passes through the pixel centre, starts where it enters the unit ball (the
+ * field's domain, Sec. 3.1; at the eye if it misses the ball) and is labelled as by
+ * ddf_label_rays. Outputs (DEVICE, caller-owned, N = n_az n_pol res^2 rows each, row
+ * ((j n_az + i) res + y) res + x with y counted from the top): origins N x 3, dirs N x 3 (unit),
+ * dist N (+inf on a miss), hit N. Ray coordinates are float32 in a fixed order (sines and
+ * cosines from a float64 series, normalisation and ball entry in float64), so the result is a
+ * deterministic function of the inputs. Asynchronous on stream; allocates nothing.
+ * Errors: INVALID_ARG (NULL, negative counts, dist or tan_half_fov not finite and > 0), CUDA. */
+DDF_API int ddf_sample_pov(ddf_mesh mesh, const ddf_pov* params, float* d_origins, float* d_dirs, float* d_dist,
+                           uint8_t* d_hit, cudaStream_t stream);
+
 /* ---- training ---------------------------------------------------------------------------- */
 
 /* Reverse pass of the network for output cotangents (g_dist, g_logit) (device, n each):

@@ -35,6 +35,11 @@ class ddf_sampler(C.Structure):
                 ("seed", C.c_uint64)]
 
 
+class ddf_pov(C.Structure):
+    _fields_ = [("n_az", C.c_int32), ("n_pol", C.c_int32), ("res", C.c_int32), ("dist", C.c_float),
+                ("tan_half_fov", C.c_float)]
+
+
 class ddf_arch(C.Structure):
     _fields_ = [("in_freqs", C.c_int), ("width", C.c_int), ("hidden_layers", C.c_int),
                 ("precision", C.c_int)]
@@ -83,6 +88,7 @@ _SIG = {
     "ddf_mesh_destroy": (C.c_int, [_P]),
     "ddf_label_rays": (C.c_int, [_P, _P, _P, _I64, _P, _P, _P, _P]),
     "ddf_sample_surface": (C.c_int, [_P, C.POINTER(ddf_sampler), _P, _P, _P, _P, _P, _I64, C.POINTER(_I64), _P]),
+    "ddf_sample_pov": (C.c_int, [_P, C.POINTER(ddf_pov), _P, _P, _P, _P, _P]),
     "ddf_label_stats": (C.c_int, [_P, C.POINTER(_I64)]),
     "ddf_backward": (C.c_int, [_P, _P, _P, _I64, _P, _P, _P, _P, _P]),
     "ddf_train_step": (C.c_int, [_P, _P, _P, _P, _P, _I64, C.POINTER(ddf_adam), _P, _P]),

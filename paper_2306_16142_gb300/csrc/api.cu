@@ -371,6 +371,23 @@ int ddf_sample_surface(ddf_mesh mesh, const ddf_sampler* params, float* d_origin
                           d_dist, d_hit, d_key, cap, host_count, stream);
 }
 
+int ddf_sample_pov(ddf_mesh mesh, const ddf_pov* params, float* d_origins, float* d_dirs, float* d_dist,
+                   uint8_t* d_hit, cudaStream_t stream) {
+    if (!mesh || !params) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    if (params->n_az < 0 || params->n_pol < 0 || params->res < 0)
+        return fail(DDF_ERR_INVALID_ARG, "negative camera or pixel counts");
+    if (!(params->dist > 0.f) || !isfinite(params->dist))
+        return fail(DDF_ERR_INVALID_ARG, "dist must be finite, > 0");
+    if (!(params->tan_half_fov > 0.f) || !isfinite(params->tan_half_fov))
+        return fail(DDF_ERR_INVALID_ARG, "tan_half_fov must be finite, > 0");
+    const double n = (double)params->n_az * params->n_pol * params->res * params->res;
+    if (n > 2.0e9) return fail(DDF_ERR_INVALID_ARG, "too many rays (%g)", n);
+    if (n > 0 && (!d_origins || !d_dirs || !d_dist || !d_hit))
+        return fail(DDF_ERR_INVALID_ARG, "NULL output");
+    return sample_pov(mesh, params->n_az, params->n_pol, params->res, params->dist, params->tan_half_fov, d_origins,
+                      d_dirs, d_dist, d_hit, stream);
+}
+
 int ddf_label_stats(ddf_mesh mesh, int64_t* host_counts) {
     if (!mesh || !host_counts) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
     DDF_CUDA_TRY(cudaStreamSynchronize(mesh->last_stream));

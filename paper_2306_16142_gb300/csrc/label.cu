@@ -573,6 +573,92 @@ __global__ void sampler_scatter_kernel(const uint8_t* __restrict__ sv, int64_t n
     }
 }
 
+// Taylor coefficients (-1)^k / j! of sin (j odd) and cos (j even), the factorial accumulated in float64.
+void fill_series(SinCosCoef& k) {
+    double f = 1.0;
+    for (int j = 0; j <= 23; ++j) {
+        if (j >= 2) f *= (double)j;
+        const double coef = ((j / 2) & 1 ? -1.0 : 1.0) / f;
+        if (j & 1) {
+            if (j / 2 < 11) k.s[j / 2] = coef;
+        } else if (j / 2 < 12) {
+            k.c[j / 2] = coef;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ point-of-view sampling
+// The "pov" training set of Sec. 6: cameras around the mesh aimed at its centre, one ray per
+// pixel centre, labelled like any ray. Camera (i, j) sits at azimuth 2 pi i / n_az, polar angle
+// pi (j + 1) / (n_pol + 1); its frame has a closed form in those angles (forward = -eye / dist,
+// right = (-sin az, cos az, 0), up = (-cos pol cos az, -cos pol sin az, sin pol)), so no
+// normalisation enters the frame; the series' reduction of u to r = u - n / 2 is exact for every u
+// (Sterbenz), these angles included.
+
+struct PovArgs {
+    int64_t n;           // rays
+    int n_az, res;
+    int n_pol;
+    float dist, th;      // camera distance, tan(fov / 2)
+    SinCosCoef coef;
+};
+
+// One pixel ray per thread: float32 direction (f + px r) + py u without contraction, normalised in
+// float64; origin where the ray from the eye enters the unit ball, in float64, rounded once.
+__global__ void pov_rays_kernel(PovArgs pa, float* __restrict__ o, float* __restrict__ w) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= pa.n) return;
+    const int64_t rr = (int64_t)pa.res * pa.res;
+    const int cam = (int)(g / rr);
+    const int pix = (int)(g - (int64_t)cam * rr);
+    const int y = pix / pa.res, x = pix - y * pa.res;
+    const int i = cam % pa.n_az, j = cam / pa.n_az;
+    double sp, cp, st, ct;
+    sincospi_series(__ddiv_rn(2.0 * i, (double)pa.n_az), pa.coef, &sp, &cp);
+    sincospi_series(__ddiv_rn((double)(j + 1), (double)(pa.n_pol + 1)), pa.coef, &st, &ct);
+    const double dir[3] = {__dmul_rn(st, cp), __dmul_rn(st, sp), ct};
+    const double d = (double)pa.dist;
+    float eye[3], f[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        eye[k] = __double2float_rn(__dmul_rn(d, dir[k]));
+        f[k] = __double2float_rn(-dir[k]);
+    }
+    const float r[3] = {__double2float_rn(-sp), __double2float_rn(cp), 0.f};
+    const float u[3] = {__double2float_rn(-__dmul_rn(ct, cp)), __double2float_rn(-__dmul_rn(ct, sp)),
+                        __double2float_rn(st)};
+    const double th = (double)pa.th;
+    const float px = __double2float_rn(
+        __dmul_rn(__dsub_rn(__ddiv_rn(__dadd_rn(2.0 * x, 1.0), (double)pa.res), 1.0), th));
+    const float py = __double2float_rn(
+        __dmul_rn(__dsub_rn(1.0, __ddiv_rn(__dadd_rn(2.0 * y, 1.0), (double)pa.res)), th));
+    float dv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dv[k] = __fadd_rn(__fadd_rn(f[k], __fmul_rn(px, r[k])), __fmul_rn(py, u[k]));
+    const double n2 = __dadd_rn(__dadd_rn(__dmul_rn((double)dv[0], (double)dv[0]), __dmul_rn((double)dv[1], (double)dv[1])),
+                                __dmul_rn((double)dv[2], (double)dv[2]));
+    const double len = __dsqrt_rn(n2);
+    float wv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) wv[k] = __double2float_rn(__ddiv_rn((double)dv[k], len));
+    const double e0 = eye[0], e1 = eye[1], e2 = eye[2];
+    const double b = __dadd_rn(__dadd_rn(__dmul_rn(e0, (double)wv[0]), __dmul_rn(e1, (double)wv[1])),
+                               __dmul_rn(e2, (double)wv[2]));
+    const double c = __dsub_rn(__dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2)), 1.0);
+    const double disc = __dsub_rn(__dmul_rn(b, b), c);
+    double t0 = 0.0;
+    if (disc > 0.0) {
+        const double sq = __dsqrt_rn(disc);
+        if (__dadd_rn(-b, sq) > 0.0) t0 = fmax(0.0, __dsub_rn(-b, sq));
+    }
+    const double ev[3] = {e0, e1, e2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        o[3 * g + k] = __double2float_rn(__dadd_rn(ev[k], __dmul_rn(t0, (double)wv[k])));
+        w[3 * g + k] = wv[k];
+    }
+}
+
 // Exclusive chunk offsets of the set flags of fl[0 .. n) into dev_offs (nblk entries, through the
 // host); returns the total in *total. Synchronises the stream.
 cudaError_t scan_flags(const uint8_t* fl, int64_t n, int64_t* dev_offs, std::vector<int64_t>& h, int64_t* total,
@@ -671,18 +757,7 @@ int sample_surface(ddf_mesh_s* m, int s_fc, int s_dr, int s_p, float eps, uint64
     sa.s_p = s_p;
     sa.eps = eps;
     sa.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-    {   // Taylor coefficients (-1)^k / j!, the factorial accumulated in float64
-        double f = 1.0;
-        for (int j = 0; j <= 23; ++j) {
-            if (j >= 2) f *= (double)j;
-            const double coef = ((j / 2) & 1 ? -1.0 : 1.0) / f;
-            if (j & 1) {
-                if (j / 2 < 11) sa.coef.s[j / 2] = coef;
-            } else if (j / 2 < 12) {
-                sa.coef.c[j / 2] = coef;
-            }
-        }
-    }
+    fill_series(sa.coef);
     // Workspace: the per-candidate and per-slot arrays now, the Eq. 12 rays once their count is known.
     const int64_t nblk = (std::max(NS, C) + kCompactChunk - 1) / kCompactChunk;
     const size_t sizes[] = {(size_t)C * 12, (size_t)C * 12, (size_t)C * 12, (size_t)C * 12,  // cp cth cro cperp
@@ -781,6 +856,22 @@ int sample_surface(ddf_mesh_s* m, int s_fc, int s_dr, int s_p, float eps, uint64
     if (rc) return rc;
     if (e != cudaSuccess) return fail(DDF_ERR_CUDA, "surface sampler: %s", cudaGetErrorString(e));
     return DDF_OK;
+}
+
+int sample_pov(ddf_mesh_s* m, int n_az, int n_pol, int res, float dist, float tan_half_fov, float* d_o, float* d_w,
+               float* d_dist, uint8_t* d_hit, cudaStream_t stream) {
+    PovArgs pa{};
+    pa.n = (int64_t)n_az * n_pol * res * res;
+    if (pa.n == 0) return DDF_OK;
+    pa.n_az = n_az;
+    pa.n_pol = n_pol;
+    pa.res = res;
+    pa.dist = dist;
+    pa.th = tan_half_fov;
+    fill_series(pa.coef);
+    pov_rays_kernel<<<(unsigned)((pa.n + 255) / 256), 256, 0, stream>>>(pa, d_o, d_w);
+    DDF_LAUNCH_CHECK();
+    return label_rays(m, d_o, d_w, pa.n, d_dist, d_hit, nullptr, stream);
 }
 
 }  // namespace ddf

@@ -10,7 +10,7 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import check, ddf_adam, ddf_arch, ddf_camera, ddf_sampler
+from ._abi import check, ddf_adam, ddf_arch, ddf_camera, ddf_pov, ddf_sampler
 
 PRECISIONS = {"fp32": _abi.DDF_FP32, "bf16": _abi.DDF_BF16, "fp8": _abi.DDF_FP8}
 
@@ -247,6 +247,24 @@ class DDFMesh:
         res = {name: t[:k] for name, t in out.items()}
         res["count"] = n.value
         return res
+
+    def sample_pov(self, n_az: int = 10, n_pol: int = 5, res: int = 64, dist: float = 2.5,
+                   tan_half_fov: float = 0.2679491924311227, out: dict | None = None):
+        """The point-of-view training set of Sec. 6 (ddf_sample_pov): dict of CUDA tensors o
+        (N, 3), w (N, 3), dist (N,), hit (N,), N = n_az n_pol res^2, camera by camera, rows from
+        the top. The default field of view is 30 degrees."""
+        n = n_az * n_pol * res * res
+        if out is None:
+            dev = torch.device("cuda")
+            out = {"o": torch.empty(max(n, 1), 3, device=dev), "w": torch.empty(max(n, 1), 3, device=dev),
+                   "dist": torch.empty(max(n, 1), device=dev),
+                   "hit": torch.empty(max(n, 1), dtype=torch.uint8, device=dev)}
+        elif out["hit"].shape[0] < n:
+            raise ValueError("output buffers hold fewer than n_az n_pol res^2 rows")
+        prm = ddf_pov(n_az, n_pol, res, dist, tan_half_fov)
+        check("ddf_sample_pov", _abi.load().ddf_sample_pov(
+            self.h, C.byref(prm), _ptr(out["o"]), _ptr(out["w"]), _ptr(out["dist"]), _ptr(out["hit"]), _stream()))
+        return {name: t[:n] for name, t in out.items()}
 
 
 def camera_struct(cam) -> ddf_camera:

@@ -72,3 +72,51 @@ def test_sampler_cap_empty_and_determinism(P):
         assert torch.equal(again[k], full[k])
     assert mesh.sample_surface(1, 2, 0, 1e-4, 5)["count"] == 0
     assert mesh.sample_surface(0, 2, 3, 1e-4, 5)["count"] == 0
+
+
+def _box(a):
+    a = np.float32(a)
+    V = np.array([[x, y, z] for x in (-a, a) for y in (-a, a) for z in (-a, a)], np.float32)
+    quads = [(0, 1, 3, 2), (4, 6, 7, 5), (0, 4, 5, 1), (2, 3, 7, 6), (0, 2, 6, 4), (1, 5, 7, 3)]
+    F = []
+    for q in quads:
+        F += [[q[0], q[1], q[2]], [q[0], q[2], q[3]]]
+    return V, np.array(F, np.int32)
+
+
+POV_CASES = {
+    # the paper's 10 x 5 cameras; an odd film (a centre pixel); a wide field of view whose corner
+    # rays miss the unit ball (origin left at the eye); a camera inside the ball
+    "icosphere": (lambda: icosphere(2, 0.5), dict(n_az=10, n_pol=5, res=12)),
+    "knot": (lambda: torus_knot(3, 2, 0.08, 64, 8), dict(n_az=10, n_pol=5, res=9)),
+    "box_wide": (lambda: _box(0.4), dict(n_az=7, n_pol=3, res=16, dist=2.5, tan_half_fov=1.2)),
+    "inside": (lambda: _box(0.3), dict(n_az=3, n_pol=2, res=8, dist=0.8, tan_half_fov=0.5)),
+}
+
+
+@pytest.mark.parametrize("name", list(POV_CASES))
+def test_pov_matches_oracle_bit_for_bit(P, name):
+    make, kw = POV_CASES[name]
+    V, T = make()
+    g = P.DDFMesh(V, T).sample_pov(**kw)
+    torch.cuda.synchronize()
+    r = S.sample_pov(V, T, **kw)
+    n = kw["n_az"] * kw["n_pol"] * kw["res"] ** 2
+    assert g["o"].shape[0] == n == r["o"].shape[0]
+    assert np.array_equal(g["w"].cpu().numpy(), r["w"])
+    assert np.array_equal(g["o"].cpu().numpy(), r["o"])
+    assert np.array_equal(g["hit"].cpu().numpy(), r["hit"])
+    assert np.array_equal(g["dist"].cpu().numpy(), r["dist"])
+    print(f"{name}: {n} rays, {int(r['hit'].sum())} hits")
+    if name == "box_wide":
+        assert (np.linalg.norm(r["o"].astype(np.float64), axis=1) > 2.0).any()   # rays that miss the ball
+
+
+def test_pov_rejects_bad_arguments(P):
+    V, T = _box(0.4)
+    mesh = P.DDFMesh(V, T)
+    for kw in (dict(dist=0.0), dict(dist=float("inf")), dict(tan_half_fov=0.0), dict(tan_half_fov=float("nan")),
+               dict(res=-1)):
+        with pytest.raises(P.DDFError):
+            mesh.sample_pov(**kw)
+    assert mesh.sample_pov(n_az=0)["o"].shape[0] == 0
