@@ -20,7 +20,9 @@ Modules and the passages they follow:
 * ``render``  - the modified uni-directional path tracer (Sec. 1, Fig. 1): camera rays,
   one DDF query per bounce, Lambertian shading with cosine-hemisphere sampling.
 * ``sampler`` - the surface-marching training-set sampler of Sec. 5.2 (Eqs. 8-12) with the
-  odd-even inside test, built on ``label``.
+  odd-even inside test, and the point-of-view sampling of Sec. 6, built on ``label``.
+* ``head``    - the paper's single-output head with the clamp loss of Eq. 7 or the squish
+  loss of Eq. 5, and the weight-normalised hidden layers of Sec. 5.1.
 
 Every floating-point step runs in float64 from the float32 inputs (promoted exactly).
 Where the paper is silent, the readings used are listed in each module's docstring.

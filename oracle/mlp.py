@@ -7,7 +7,7 @@ a_l = ReLU(z_l), and an output layer y = W_out a_L + b_out with two outputs:
 y_0 = distance, y_1 = hit logit (hit <=> y_1 > 0). The two-output head, the 6-D input
 (origin + unit direction instead of two angles, the angle form of Eq. 1 being only a
 parameterisation of the same direction) and the Fourier encoding are readings of this
-implementation; the paper's single clamped output is a different head.
+implementation; the paper's single clamped output is the head of ``oracle.head``.
 
 Encoding (reading): v = (o_x, o_y, o_z, w_x, w_y, w_z); with F = in_freqs (even),
 gamma(v) = [v_0..v_5, then for k = 0 .. F/2 - 1: sin(2^k pi v_j) for j = 0..5,
