@@ -59,6 +59,11 @@ extern "C" {
 #define DDF_FP8 2  /* FP8 E4M3 tcgen05 MMAs with per-output-channel weight scales and
                       static per-input-channel activation scales, FP32 accumulate            */
 
+/* ---- output heads and training losses (ddf_set_head) -------------------------------------- */
+#define DDF_HEAD_TWO 0    /* distance + hit logit; L1 on hit rays + BCE with logits (default)      */
+#define DDF_HEAD_CLAMP 1  /* the paper's single field value y~, clamp loss of Eq. 7                */
+#define DDF_HEAD_SQUISH 2 /* single field value y~, squish loss of Eq. 5 with sigma = tanh         */
+
 typedef struct ddf_net_s* ddf_net;
 typedef struct ddf_mesh_s* ddf_mesh;
 
@@ -142,12 +147,47 @@ DDF_API int ddf_selftest_wait(int limit_ms, int arrive);
 /* Number of float32 values in the weight blob of this network. */
 DDF_API int ddf_num_params(ddf_net net, int64_t* out);
 
+/* The architecture and current precision of a handle (a loaded one included). INVALID_ARG for
+ * the analytic sphere. */
+DDF_API int ddf_get_arch(ddf_net net, ddf_arch* out);
+
 /* Replace the FP32 masters with a DEVICE blob (n_params floats) and repack, ordered on
  * stream. Adam moments are kept. */
 DDF_API int ddf_set_weights(ddf_net net, const float* d_weights, size_t nbytes, cudaStream_t stream);
 
 /* Copy the FP32 masters into a DEVICE buffer (n_params floats), ordered on stream. */
 DDF_API int ddf_get_weights(ddf_net net, float* d_out, size_t nbytes, cudaStream_t stream);
+
+/* Output head and training variant (Sec. 4.1, Sec. 5.1). */
+typedef struct ddf_head {
+    int32_t kind;        /* DDF_HEAD_TWO / _CLAMP / _SQUISH */
+    float delta;         /* single-output kinds: the clamp half-width of Eq. 7 and the hit threshold
+                            (a ray hits <=> y~ < delta); finite, > 0. Ignored for DDF_HEAD_TWO. */
+    int32_t weight_norm; /* 1: train every hidden layer as W[r, :] = g[r] v[r, :] / |v[r, :]| */
+} ddf_head;
+
+/* Select the head and training variant of a handle.
+ * Single-output kinds: y~ is output 0 (the distance). Row 1 of the output layer is derived,
+ * W_out[1] = -W_out[0] and b_out[1] = delta - b_out[0]. The logit every call returns is
+ * therefore delta - y~, and hit <=> y~ < delta in queries and renders. ddf_train_step then
+ * minimises the mean over rays of |clamp(y, delta) - clamp(y~, delta)| (CLAMP, Eq. 7) or
+ * |tanh(y) - tanh(y~)| (SQUISH, Eq. 5 read with an absolute value). The target y is dist_gt for
+ * rays with hit_gt = 1 and +inf otherwise. Row 1 is derived again after every update and by
+ * ddf_set_weights.
+ * weight_norm = 1 (Sec. 5.1) trains v and g per output row of every hidden layer. Switching it
+ * on sets v = W and g = the row norms; the FP32 masters (ddf_get_weights) then hold the folded
+ * g v / |v|, recomputed after every update. ddf_set_weights sets v and g again from the new
+ * weights (clearing g's Adam moments). Changing weight_norm resets the Adam state.
+ * Ordered on stream. Errors: INVALID_ARG (unknown kind, bad delta, the analytic sphere), OOM,
+ * CUDA. */
+DDF_API int ddf_set_head(ddf_net net, const ddf_head* head, cudaStream_t stream);
+
+/* The weight-normalisation state: d_v (DEVICE, n_params floats, the blob layout with v in the
+ * hidden-weight slots and the biases and output layer as in the masters) and d_g (DEVICE,
+ * hidden_layers x width floats, layer-major). Ordered on stream. INVALID_ARG if weight_norm is
+ * off or a size differs. */
+DDF_API int ddf_get_weight_norm(ddf_net net, float* d_v, size_t v_bytes, float* d_g, size_t g_bytes,
+                                cudaStream_t stream);
 
 /* ---- query ------------------------------------------------------------------------------ */
 

@@ -19,6 +19,7 @@ DDF_ERR_TIMEOUT = -5
 DDF_ERR_NUMERIC = -6
 DDF_ERR_IO = -7
 DDF_FP32, DDF_BF16, DDF_FP8 = 0, 1, 2
+DDF_HEAD_TWO, DDF_HEAD_CLAMP, DDF_HEAD_SQUISH = 0, 1, 2
 
 ERR_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "UNSUPPORTED", -5: "TIMEOUT",
              -6: "NUMERIC", -7: "IO"}
@@ -49,6 +50,10 @@ class ddf_camera(C.Structure):
     _fields_ = [("eye", C.c_float * 3), ("look_at", C.c_float * 3), ("up", C.c_float * 3),
                 ("vfov_deg", C.c_float), ("width", C.c_int), ("height", C.c_int),
                 ("seed", C.c_uint64), ("albedo", C.c_float), ("env", C.c_float)]
+
+
+class ddf_head(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("delta", C.c_float), ("weight_norm", C.c_int32)]
 
 
 class ddf_adam(C.Structure):
@@ -89,6 +94,9 @@ _SIG = {
     "ddf_label_rays": (C.c_int, [_P, _P, _P, _I64, _P, _P, _P, _P]),
     "ddf_sample_surface": (C.c_int, [_P, C.POINTER(ddf_sampler), _P, _P, _P, _P, _P, _I64, C.POINTER(_I64), _P]),
     "ddf_sample_pov": (C.c_int, [_P, C.POINTER(ddf_pov), _P, _P, _P, _P, _P]),
+    "ddf_set_head": (C.c_int, [_P, C.POINTER(ddf_head), _P]),
+    "ddf_get_arch": (C.c_int, [_P, C.POINTER(ddf_arch)]),
+    "ddf_get_weight_norm": (C.c_int, [_P, _P, C.c_size_t, _P, C.c_size_t, _P]),
     "ddf_label_stats": (C.c_int, [_P, C.POINTER(_I64)]),
     "ddf_backward": (C.c_int, [_P, _P, _P, _I64, _P, _P, _P, _P, _P]),
     "ddf_train_step": (C.c_int, [_P, _P, _P, _P, _P, _I64, C.POINTER(ddf_adam), _P, _P]),

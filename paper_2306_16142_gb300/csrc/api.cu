@@ -105,6 +105,7 @@ void free_net(ddf_net_s* n) {
     cudaFree(n->master_t);
     cudaFree(n->adam_m);
     cudaFree(n->adam_v);
+    wn_free(n);
     cudaFree(n->train_ws);
     cudaFree(n->render_ws);
     cudaFree(n->render_counts);
@@ -221,13 +222,26 @@ int ddf_num_params(ddf_net net, int64_t* out) {
     return DDF_OK;
 }
 
+int ddf_get_arch(ddf_net net, ddf_arch* out) {
+    if (!net || !out) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    if (net->is_sphere) return fail(DDF_ERR_INVALID_ARG, "the analytic sphere has no architecture");
+    out->in_freqs = net->lay.in_freqs;
+    out->width = net->lay.width;
+    out->hidden_layers = net->lay.L;
+    out->precision = net->precision;
+    return DDF_OK;
+}
+
 int ddf_set_weights(ddf_net net, const float* d_weights, size_t nbytes, cudaStream_t stream) {
     if (!net || !d_weights) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
     if (net->is_sphere) return fail(DDF_ERR_INVALID_ARG, "sphere field has no weights");
     if (nbytes != sizeof(float) * (size_t)net->lay.n_params)
         return fail(DDF_ERR_INVALID_ARG, "weight blob size mismatch");
     DDF_CUDA_TRY(cudaMemcpyAsync(net->master, d_weights, nbytes, cudaMemcpyDeviceToDevice, stream));
-    int rc = build_transposed(net, stream);
+    int rc = head_derive(net, net->master, stream);
+    if (rc) return rc;
+    if (net->wn_p && (rc = wn_init(net, stream))) return rc;
+    rc = build_transposed(net, stream);
     if (rc) return rc;
     if (net->tc) return tc_pack(net, net->precision, stream);
     return DDF_OK;
@@ -239,6 +253,54 @@ int ddf_get_weights(ddf_net net, float* d_out, size_t nbytes, cudaStream_t strea
     if (nbytes != sizeof(float) * (size_t)net->lay.n_params)
         return fail(DDF_ERR_INVALID_ARG, "weight blob size mismatch");
     DDF_CUDA_TRY(cudaMemcpyAsync(d_out, net->master, nbytes, cudaMemcpyDeviceToDevice, stream));
+    return DDF_OK;
+}
+
+int ddf_set_head(ddf_net net, const ddf_head* head, cudaStream_t stream) {
+    if (!net || !head) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    if (net->is_sphere) return fail(DDF_ERR_INVALID_ARG, "the analytic sphere has no head");
+    if (head->kind != DDF_HEAD_TWO && head->kind != DDF_HEAD_CLAMP && head->kind != DDF_HEAD_SQUISH)
+        return fail(DDF_ERR_INVALID_ARG, "unknown head kind %d", head->kind);
+    if (head->kind != DDF_HEAD_TWO && !(head->delta > 0.f && isfinite(head->delta)))
+        return fail(DDF_ERR_INVALID_ARG, "delta must be finite, > 0");
+    if (head->weight_norm != 0 && head->weight_norm != 1) return fail(DDF_ERR_INVALID_ARG, "weight_norm is 0 or 1");
+    int rc;
+    const bool want_wn = head->weight_norm == 1;
+    bool fresh_wn = false;
+    if (want_wn != (net->wn_p != nullptr)) {
+        DDF_CUDA_TRY(cudaStreamSynchronize(stream));
+        cudaFree(net->adam_m);
+        cudaFree(net->adam_v);
+        net->adam_m = net->adam_v = nullptr;
+        net->adam_step = 0;
+        if (want_wn) {
+            if ((rc = wn_alloc(net))) return rc;
+            fresh_wn = true;
+        } else {
+            wn_free(net);
+        }
+    }
+    net->head_kind = head->kind;
+    net->head_delta = head->kind == DDF_HEAD_TWO ? 0.f : head->delta;
+    if ((rc = head_derive(net, net->master, stream))) return rc;
+    if (fresh_wn) {
+        if ((rc = wn_init(net, stream))) return rc;
+    } else if (net->wn_p && (rc = head_derive(net, net->wn_p, stream))) {
+        return rc;
+    }
+    if ((rc = build_transposed(net, stream))) return rc;
+    if (net->tc) return tc_pack(net, net->precision, stream);
+    return DDF_OK;
+}
+
+int ddf_get_weight_norm(ddf_net net, float* d_v, size_t v_bytes, float* d_g, size_t g_bytes, cudaStream_t stream) {
+    if (!net || !d_v || !d_g) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    if (!net->wn_p) return fail(DDF_ERR_INVALID_ARG, "weight normalisation is off");
+    if (v_bytes != sizeof(float) * (size_t)net->lay.n_params ||
+        g_bytes != sizeof(float) * (size_t)net->lay.L * net->lay.width)
+        return fail(DDF_ERR_INVALID_ARG, "buffer size mismatch");
+    DDF_CUDA_TRY(cudaMemcpyAsync(d_v, net->wn_p, v_bytes, cudaMemcpyDeviceToDevice, stream));
+    DDF_CUDA_TRY(cudaMemcpyAsync(d_g, net->wn_g, g_bytes, cudaMemcpyDeviceToDevice, stream));
     return DDF_OK;
 }
 
@@ -444,7 +506,10 @@ struct CkptHeader {
     int64_t n_params;
     int64_t adam_step;
     int32_t has_adam;
-    int32_t reserved[5];
+    int32_t head_kind;       // DDF_HEAD_* (0 in files written before heads existed)
+    float head_delta;
+    int32_t weight_norm;     // 1: v [n_params], g [L W] (and g's Adam moments) follow the masters / moments
+    int32_t reserved[2];
 };
 static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
 const char kMagic[8] = {'D', 'D', 'F', 'C', 'K', 'P', 'T', '1'};
@@ -463,12 +528,26 @@ int ddf_save(ddf_net net, const char* path) {
     h.n_params = P;
     h.adam_step = net->adam_step;
     h.has_adam = net->adam_m ? 1 : 0;
-    std::vector<float> buf((size_t)P * (h.has_adam ? 3 : 1));
+    h.head_kind = net->head_kind;
+    h.head_delta = net->head_delta;
+    h.weight_norm = net->wn_p ? 1 : 0;
+    const int64_t G = (int64_t)net->lay.L * net->lay.width;
+    const int64_t wn_len = h.weight_norm ? P + G * (h.has_adam ? 3 : 1) : 0;
+    std::vector<float> buf((size_t)P * (h.has_adam ? 3 : 1) + (size_t)wn_len);
     DDF_CUDA_TRY(cudaDeviceSynchronize());
     DDF_CUDA_TRY(cudaMemcpy(buf.data(), net->master, sizeof(float) * P, cudaMemcpyDeviceToHost));
     if (h.has_adam) {
         DDF_CUDA_TRY(cudaMemcpy(buf.data() + P, net->adam_m, sizeof(float) * P, cudaMemcpyDeviceToHost));
         DDF_CUDA_TRY(cudaMemcpy(buf.data() + 2 * P, net->adam_v, sizeof(float) * P, cudaMemcpyDeviceToHost));
+    }
+    if (h.weight_norm) {
+        float* wb = buf.data() + (size_t)P * (h.has_adam ? 3 : 1);
+        DDF_CUDA_TRY(cudaMemcpy(wb, net->wn_p, sizeof(float) * P, cudaMemcpyDeviceToHost));
+        DDF_CUDA_TRY(cudaMemcpy(wb + P, net->wn_g, sizeof(float) * G, cudaMemcpyDeviceToHost));
+        if (h.has_adam) {
+            DDF_CUDA_TRY(cudaMemcpy(wb + P + G, net->wn_gm, sizeof(float) * G, cudaMemcpyDeviceToHost));
+            DDF_CUDA_TRY(cudaMemcpy(wb + P + 2 * G, net->wn_gv, sizeof(float) * G, cudaMemcpyDeviceToHost));
+        }
     }
     FILE* f = fopen(path, "wb");
     if (!f) return fail(DDF_ERR_IO, "cannot open %s for writing", path);
@@ -495,12 +574,16 @@ int ddf_load(const char* path, ddf_net* out) {
         return fail(DDF_ERR_IO, "%s: bad architecture in header", path);
     }
     const NetLayout lay = make_layout(h.in_freqs, h.width, h.hidden_layers);
-    if (h.n_params != lay.n_params || h.has_adam < 0 || h.has_adam > 1 || h.adam_step < 0) {
+    if (h.n_params != lay.n_params || h.has_adam < 0 || h.has_adam > 1 || h.adam_step < 0 ||
+        h.head_kind < DDF_HEAD_TWO || h.head_kind > DDF_HEAD_SQUISH || h.weight_norm < 0 || h.weight_norm > 1 ||
+        (h.head_kind != DDF_HEAD_TWO && !(h.head_delta > 0.f && isfinite(h.head_delta)))) {
         fclose(f);
         return fail(DDF_ERR_IO, "%s: header does not match its architecture", path);
     }
     const int64_t P = lay.n_params;
-    std::vector<float> buf((size_t)P * (h.has_adam ? 3 : 1));
+    const int64_t G = (int64_t)lay.L * lay.width;
+    const int64_t wn_len = h.weight_norm ? P + G * (h.has_adam ? 3 : 1) : 0;
+    std::vector<float> buf((size_t)P * (h.has_adam ? 3 : 1) + (size_t)wn_len);
     const bool ok = fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
     fclose(f);
     if (!ok) return fail(DDF_ERR_IO, "%s is truncated", path);
@@ -519,6 +602,28 @@ int ddf_load(const char* path, ddf_net* out) {
         }
     }
     n->adam_step = h.adam_step;
+    n->head_kind = h.head_kind;
+    n->head_delta = h.head_delta;
+    if (h.weight_norm) {
+        const float* wb = buf.data() + (size_t)P * (h.has_adam ? 3 : 1);
+        int rc2 = wn_alloc(n);
+        cudaError_t e = cudaSuccess;
+        if (!rc2) {
+            e = cudaMemcpy(n->wn_p, wb, sizeof(float) * P, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(n->wn_g, wb + P, sizeof(float) * G, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess && h.has_adam) {
+                e = cudaMemcpy(n->wn_gm, wb + P + G, sizeof(float) * G, cudaMemcpyHostToDevice);
+                if (e == cudaSuccess) e = cudaMemcpy(n->wn_gv, wb + P + 2 * G, sizeof(float) * G, cudaMemcpyHostToDevice);
+            } else if (e == cudaSuccess) {
+                e = cudaMemset(n->wn_gm, 0, sizeof(float) * G);
+                if (e == cudaSuccess) e = cudaMemset(n->wn_gv, 0, sizeof(float) * G);
+            }
+        }
+        if (rc2 || e != cudaSuccess) {
+            ddf_destroy(n);
+            return rc2 ? rc2 : fail(DDF_ERR_CUDA, "restoring weight-norm state: %s", cudaGetErrorString(e));
+        }
+    }
     *out = n;
     return DDF_OK;
 }

@@ -83,6 +83,14 @@ struct ddf_net_s {
     float* adam_m = nullptr;
     float* adam_v = nullptr;
     int64_t adam_step = 0;
+    // output head (DDF_HEAD_*) and the weight-normalisation state (head.cu; null when off)
+    int head_kind = DDF_HEAD_TWO;
+    float head_delta = 0.f;
+    float* wn_p = nullptr;       // blob layout, v in the hidden-weight slots (Adam runs on it)
+    float* wn_g = nullptr;       // [L][W] row gains
+    float* wn_dg = nullptr;      // [L][W] their gradient (scratch)
+    float* wn_gm = nullptr;      // [L][W] Adam moments of g
+    float* wn_gv = nullptr;
     // training workspace (grow-only)
     void* train_ws = nullptr;
     size_t train_ws_bytes = 0;
@@ -158,6 +166,19 @@ int sample_surface(ddf_mesh_s* m, int s_fc, int s_dr, int s_p, float eps, uint64
 int sample_pov(ddf_mesh_s* m, int n_az, int n_pol, int res, float dist, float tan_half_fov, float* d_o, float* d_w,
                float* d_dist, uint8_t* d_hit, cudaStream_t stream);
 
+// ------------------------------------------------------------------ heads (head.cu)
+bool head_single(const ddf_net_s* net);
+// Derive output row 1 from row 0 of `blob` (a blob-layout array) for a single-output head.
+int head_derive(ddf_net_s* net, float* blob, cudaStream_t s);
+int wn_alloc(ddf_net_s* net);
+void wn_free(ddf_net_s* net);
+// v = masters, g = their row norms, Adam moments of g zeroed.
+int wn_init(ddf_net_s* net, cudaStream_t s);
+// Hidden-weight slots of grad: dW -> dv in place; wn_dg = dg.
+int wn_grad(ddf_net_s* net, float* grad, cudaStream_t s);
+// masters = wn_p with the hidden weights folded, g v / |v|.
+int wn_refold(ddf_net_s* net, cudaStream_t s);
+
 // ------------------------------------------------------------------ training (train.cu)
 int backward(ddf_net_s* net, const float* o, const float* w, int64_t n, const float* gdist,
              const float* glogit, float* gweights, float* ginput, cudaStream_t stream);
@@ -169,7 +190,8 @@ int count_hits(const uint8_t* hit_gt, int64_t n, int* out, cudaStream_t stream);
 int loss_reduce(const float* row_l1, const float* row_bce, int64_t n, const int* n_hit, float* loss,
                 double* part, cudaStream_t stream);
 // One Adam step on the FP32 masters, then the working copies are rebuilt from them.
-int adam_and_repack(ddf_net_s* net, const float* grad, const ddf_adam* opt, cudaStream_t stream);
+// grad (the batch's weight gradient) is scratch: the weight-normalised path rewrites it in place.
+int adam_and_repack(ddf_net_s* net, float* grad, const ddf_adam* opt, cudaStream_t stream);
 
 // ------------------------------------------------------------------ BF16 tensor-core training (train_tc.cu)
 bool tct_supported(const ddf_net_s* net);

@@ -64,4 +64,25 @@ __device__ __forceinline__ float3 normal_from_grad(float gx, float gy, float gz,
     return n;
 }
 
+// Per-row loss of the single-output heads and its derivative d loss / d y~ including the 1 / n of
+// the mean over rays. Target: dist_gt for a ray that hits, +inf otherwise (clamp(+inf) = delta,
+// tanh(+inf) = 1). Clamp (Eq. 7): |clamp(y) - clamp(y~)|, the clamp's slope 1 on [-delta, delta];
+// squish (Eq. 5 with an absolute value): |tanh(y) - tanh(y~)|, slope 1 - tanh(y~)^2.
+__device__ __forceinline__ void single_head_loss(int kind, float delta, float d, bool hit, float dgt, float inv_n,
+                                                 float* loss, float* gd) {
+    float diff, slope;
+    if (kind == 1) {   // DDF_HEAD_CLAMP
+        const float cy = hit ? fminf(delta, fmaxf(-delta, dgt)) : delta;
+        diff = fminf(delta, fmaxf(-delta, d)) - cy;
+        slope = (d >= -delta && d <= delta) ? 1.f : 0.f;
+    } else {           // DDF_HEAD_SQUISH
+        const float ty = hit ? tanhf(dgt) : 1.f;
+        const float td = tanhf(d);
+        diff = td - ty;
+        slope = 1.f - td * td;
+    }
+    *loss = fabsf(diff);
+    *gd = (diff > 0.f ? slope : (diff < 0.f ? -slope : 0.f)) * inv_n;
+}
+
 }  // namespace ddf

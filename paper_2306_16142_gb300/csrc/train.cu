@@ -182,17 +182,28 @@ __global__ void count_hits_kernel(const uint8_t* __restrict__ h, int64_t n, int*
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);   // integer sum: order-independent
 }
 
-// Per-row loss terms and output cotangents of the L1 (hit rows) + BCE-with-logits loss.
+// Per-row loss terms and output cotangents: L1 (hit rows) + BCE with logits for the two-output
+// head; for the single-output heads the clamp (Eq. 7) or squish (Eq. 5) term, in row_bce (so
+// the reduction's mean over all rays is the loss), and no logit cotangent.
 __global__ void loss_kernel(const float* __restrict__ Y, const float* __restrict__ dgt,
                             const uint8_t* __restrict__ hgt, int64_t m, int64_t n_total,
                             const int* __restrict__ n_hit, float* __restrict__ G,
-                            float* __restrict__ row_l1, float* __restrict__ row_bce) {
+                            float* __restrict__ row_l1, float* __restrict__ row_bce, int head_kind, float delta) {
     const int nh = *n_hit;
     const float inv_h = nh > 0 ? 1.f / (float)nh : 0.f;
     const float inv_n = 1.f / (float)n_total;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
          r += (int64_t)gridDim.x * blockDim.x) {
         const float d = Y[2 * r], z = Y[2 * r + 1];
+        if (head_kind != DDF_HEAD_TWO) {
+            float gd, l;
+            single_head_loss(head_kind, delta, d, hgt[r] != 0, hgt[r] ? dgt[r] : 0.f, inv_n, &l, &gd);
+            G[2 * r] = gd;
+            G[2 * r + 1] = 0.f;
+            row_l1[r] = 0.f;
+            row_bce[r] = l;
+            continue;
+        }
         const float h = hgt[r] ? 1.f : 0.f;
         float gd = 0.f, l1 = 0.f;
         if (hgt[r]) {
@@ -470,7 +481,7 @@ int loss_reduce(const float* row_l1, const float* row_bce, int64_t n, const int*
     return DDF_OK;
 }
 
-int adam_and_repack(ddf_net_s* net, const float* grad, const ddf_adam* opt, cudaStream_t s) {
+int adam_and_repack(ddf_net_s* net, float* grad, const ddf_adam* opt, cudaStream_t s) {
     const int64_t P = net->lay.n_params;
     if (!net->adam_m) {
         DDF_CUDA_TRY(cudaMalloc(&net->adam_m, sizeof(float) * P));
@@ -482,10 +493,25 @@ int adam_and_repack(ddf_net_s* net, const float* grad, const ddf_adam* opt, cuda
     const double t = (double)net->adam_step;
     const float c1 = (float)(1.0 - pow((double)opt->beta1, t));
     const float c2 = (float)(1.0 - pow((double)opt->beta2, t));
-    adam_kernel<<<grid1d(P), 256, 0, s>>>(net->master, grad, net->adam_m, net->adam_v, P, opt->lr,
-                                          opt->beta1, opt->beta2, opt->eps, c1, c2);
-    DDF_LAUNCH_CHECK();
-    int rc = build_transposed(net, s);
+    int rc;
+    if (net->wn_p) {
+        // Sec. 5.1's weight-normalised layers: Adam on (v, biases, head) and on g, then fold
+        const int64_t G = (int64_t)net->lay.L * net->lay.width;
+        if ((rc = wn_grad(net, grad, s))) return rc;
+        adam_kernel<<<grid1d(P), 256, 0, s>>>(net->wn_p, grad, net->adam_m, net->adam_v, P, opt->lr, opt->beta1,
+                                              opt->beta2, opt->eps, c1, c2);
+        adam_kernel<<<grid1d(G), 256, 0, s>>>(net->wn_g, net->wn_dg, net->wn_gm, net->wn_gv, G, opt->lr, opt->beta1,
+                                              opt->beta2, opt->eps, c1, c2);
+        DDF_LAUNCH_CHECK();
+        if ((rc = head_derive(net, net->wn_p, s))) return rc;
+        if ((rc = wn_refold(net, s))) return rc;
+    } else {
+        adam_kernel<<<grid1d(P), 256, 0, s>>>(net->master, grad, net->adam_m, net->adam_v, P, opt->lr,
+                                              opt->beta1, opt->beta2, opt->eps, c1, c2);
+        DDF_LAUNCH_CHECK();
+        if ((rc = head_derive(net, net->master, s))) return rc;
+    }
+    rc = build_transposed(net, s);
     if (rc) return rc;
     if (net->tc) return tc_pack(net, net->precision, s);
     return DDF_OK;
@@ -507,7 +533,7 @@ int train_step(ddf_net_s* net, const float* o, const float* w, const float* dist
         rc = chunk_forward(net, o + 3 * r0, w + 3 * r0, m, ws, s);
         if (rc) return rc;
         loss_kernel<<<grid1d(m), 256, 0, s>>>(ws.Y, dist_gt + r0, hit_gt + r0, m, n, R.n_hit, ws.G,
-                                              R.row_l1 + r0, R.row_bce + r0);
+                                              R.row_l1 + r0, R.row_bce + r0, net->head_kind, net->head_delta);
         DDF_LAUNCH_CHECK();
         rc = chunk_backward(net, o + 3 * r0, w + 3 * r0, m, ws, R.grad, nullptr, s);
         if (rc) return rc;

@@ -546,6 +546,8 @@ struct HeadArgs {
     float* row_bce;
     const float* gd_in;       // cotangent form
     const float* gl_in;
+    int head_kind;            // DDF_HEAD_* (loss form)
+    float head_delta;
 };
 
 template <int W>
@@ -621,7 +623,14 @@ __global__ void __launch_bounds__(128) head_kernel(const HeadArgs h) {
         const float lb = __shfl_sync(0xffffffffu, lab_b, 2 * i + hw);
         float gd = 0.f, gl = 0.f;
         if (row < h.m) {
-            if (h.hit_gt) {
+            if (h.hit_gt && h.head_kind != DDF_HEAD_TWO) {   // single output: y~ only (Eqs. 5, 7)
+                float l;
+                single_head_loss(h.head_kind, h.head_delta, d, lb > 0.f, la, inv_n, &l, &gd);
+                if (j == 0) {
+                    h.row_l1[row] = 0.f;
+                    h.row_bce[row] = l;
+                }
+            } else if (h.hit_gt) {
                 const bool hit = lb > 0.f;
                 float l1 = 0.f;
                 if (hit) {
@@ -928,6 +937,8 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
         h.row_bce = tg.row_bce;
         h.gd_in = tg.gd;
         h.gl_in = tg.gl;
+        h.head_kind = net->head_kind;
+        h.head_delta = net->head_delta;
         const unsigned grid = (unsigned)((mp / 32 + 3) / 4);
         if (W == 256)
             head_kernel<256><<<grid, 128, 0, s>>>(h);

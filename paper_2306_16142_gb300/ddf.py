@@ -10,9 +10,10 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import check, ddf_adam, ddf_arch, ddf_camera, ddf_pov, ddf_sampler
+from ._abi import check, ddf_adam, ddf_arch, ddf_camera, ddf_head, ddf_pov, ddf_sampler
 
 PRECISIONS = {"fp32": _abi.DDF_FP32, "bf16": _abi.DDF_BF16, "fp8": _abi.DDF_FP8}
+HEADS = {"two": _abi.DDF_HEAD_TWO, "clamp": _abi.DDF_HEAD_CLAMP, "squish": _abi.DDF_HEAD_SQUISH}
 
 
 def _stream():
@@ -71,8 +72,10 @@ class DDFNet:
         n = C.c_int64()
         check("ddf_num_params", _abi.load().ddf_num_params(h, C.byref(n)))
         obj.n_params = n.value
-        obj.arch = None
-        obj.precision = None
+        a = ddf_arch()
+        check("ddf_get_arch", _abi.load().ddf_get_arch(h, C.byref(a)))
+        obj.arch = (a.in_freqs, a.width, a.hidden_layers)
+        obj.precision = {v: k for k, v in PRECISIONS.items()}[a.precision]
         return obj
 
     def save(self, path: str):
@@ -105,6 +108,24 @@ class DDFNet:
     def set_precision(self, precision: str):
         check("ddf_set_precision", _abi.load().ddf_set_precision(self.h, PRECISIONS[precision]))
         self.precision = precision
+
+    def set_head(self, kind: str = "two", delta: float = 0.0, weight_norm: bool = False):
+        """Head and training variant (ddf_set_head): "two" (distance + hit logit), or the
+        paper's single field value with the clamp loss of Eq. 7 ("clamp") or the squish loss of
+        Eq. 5 ("squish"), hit <=> value < delta; weight_norm trains the hidden layers as g v / |v|."""
+        h = ddf_head(HEADS[kind], delta, int(bool(weight_norm)))
+        check("ddf_set_head", _abi.load().ddf_set_head(self.h, C.byref(h), _stream()))
+
+    def weight_norm_state(self):
+        """(v, g): v in the blob layout (v in the hidden-weight slots), g [L * width]."""
+        if self.arch is None:
+            raise ValueError("architecture unknown for this handle")
+        _, width, layers = self.arch
+        v = torch.empty(self.n_params, device="cuda")
+        g = torch.empty(layers * width, device="cuda")
+        check("ddf_get_weight_norm", _abi.load().ddf_get_weight_norm(self.h, _ptr(v), v.numel() * 4, _ptr(g),
+                                                                     g.numel() * 4, _stream()))
+        return v, g
 
     def query(self, o: torch.Tensor, w: torch.Tensor, normals: bool = False, out=None):
         n = _rays(o, w)

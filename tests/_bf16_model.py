@@ -56,7 +56,8 @@ def query_bf16(params, o, w, in_freqs, bias_in_mma=True):
             "normal": omlp.normal_from_gradient(g[:, :3], w)}
 
 
-def train_grad_bf16(params, o, w, in_freqs, gy=None, dist_gt=None, hit_gt=None, snap=False, bias_in_mma=True):
+def train_grad_bf16(params, o, w, in_freqs, gy=None, dist_gt=None, hit_gt=None, snap=False, bias_in_mma=True,
+                    loss_fn=None):
     """The reverse pass of the tensor-core training path with its BF16 rounding points: the
     encoded input, the hidden-layer weights, every hidden activation (the last one included:
     the output head reads it from memory), every delta; the output weights, y, G and the
@@ -64,7 +65,8 @@ def train_grad_bf16(params, o, w, in_freqs, gy=None, dist_gt=None, hit_gt=None, 
     d/d(o, w) (n, 6)).
 
     snap: round the encoded features to multiples of 2^-20, for inputs whose features are
-    exactly 0 or +-1 (sin(k pi) evaluates to ~1e-16 in floating point, sinpi to exactly 0)."""
+    exactly 0 or +-1 (sin(k pi) evaluates to ~1e-16 in floating point, sinpi to exactly 0).
+    loss_fn: y -> (loss, d loss / d y) in place of the two-output loss (the single-output heads)."""
     X, dX = omlp.encode(o, w, in_freqs)
     if snap:
         X = np.round(X * 2.0 ** 20) / 2.0 ** 20
@@ -83,7 +85,9 @@ def train_grad_bf16(params, o, w, in_freqs, gy=None, dist_gt=None, hit_gt=None, 
     aL = bf16(a)
     y = aL @ Wo.T + bo
     loss = None
-    if gy is None:
+    if gy is None and loss_fn is not None:
+        loss, gy = loss_fn(y)
+    elif gy is None:
         loss, gy = omlp.loss_and_output_grad(y, dist_gt, hit_gt)
     grads = [None] * (L + 1)
     grads[L] = (gy.T @ aL, gy.sum(0))
