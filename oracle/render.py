@@ -144,3 +144,54 @@ def render_pixels(query_fn, cam, spp: int, bounces: int, pixels):
     res["image"] = img
     res["pids"] = pids
     return res
+
+
+# --------------------------------------------------------------------------- AOV renders
+# The t-value and normal images of Fig. 3 / Fig. 4. Readings: one primary ray per pixel, the
+# renderer's camera and bounce-0 jitter with spp = 1 (path id = pixel index); the t-value is the
+# distance from the eye to the hit point, |entry - eye| + max(dist, 0) for the field (whose rays
+# start where they enter the unit ball), +inf where nothing is hit; the normal is the Eq. 3 normal
+# for the field and the unit face normal turned towards the eye for a mesh, 0 on a miss.
+
+
+def field_aov(query_fn, cam):
+    """Depth (H W,), normal (H W, 3) and the |logit| of the hit decision (+inf where the ray
+    misses the ball) of the field's AOV render, pixel-major."""
+    n = cam.width * cam.height
+    pids = np.arange(n, dtype=np.int64)
+    o, w, alive = primary_rays(cam, pids, 1)
+    eye = np.array(cam.eye, np.float64)
+    depth = np.full(n, np.inf)
+    normal = np.zeros((n, 3))
+    margin = np.full(n, np.inf)
+    idx = np.nonzero(alive)[0]
+    res = query_fn(o[idx], w[idx])
+    hit = res["logit"] > 0
+    t0 = np.linalg.norm(o[idx] - eye[None], axis=1)
+    h = idx[hit]
+    depth[h] = t0[hit] + np.maximum(res["dist"][hit], 0.0)
+    normal[h] = res["normal"][hit]
+    margin[idx] = np.abs(res["logit"])
+    return depth, normal, margin
+
+
+def mesh_aov(verts, tris, cam):
+    """Depth, normal and hit face of the pixel rays cast from the eye against a mesh; the float32
+    rays are returned too (o, w)."""
+    from .label import label_rays
+    n = cam.width * cam.height
+    _, w, _ = primary_rays(cam, np.arange(n, dtype=np.int64), 1)
+    o = np.broadcast_to(np.array(cam.eye, np.float64), (n, 3)).astype(np.float32)
+    w = w.astype(np.float32)
+    d, _, tri, _ = label_rays(verts, tris, o, w)
+    V = np.asarray(verts, np.float64)
+    F = np.asarray(tris, np.int64)
+    normal = np.zeros((n, 3))
+    h = tri >= 0
+    k = F[tri[h]]
+    fn = np.cross(V[k[:, 1]] - V[k[:, 0]], V[k[:, 2]] - V[k[:, 0]])
+    fn /= np.linalg.norm(fn, axis=1, keepdims=True)
+    facing = np.sum(fn * w[h].astype(np.float64), axis=1) > 0
+    fn[facing] = -fn[facing]
+    normal[h] = fn
+    return d.astype(np.float64), normal, tri, o, w
