@@ -199,7 +199,7 @@ def main():
     ap.add_argument("--no-rows", action="store_true", help="skip the labelling / training / grouped rows")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: 512 x 512 x 8 spp (2^21 paths) for profiler captures")
-    ap.add_argument("--row", default=None, choices=["label", "sampler", "pov", "train", "grouped", "w512"],
+    ap.add_argument("--row", default=None, choices=["label", "sampler", "pov", "aov", "train", "grouped", "w512"],
                     help="run only this row's workload (for profiler captures) and print it")
     args = ap.parse_args()
     if args.size == "small":
@@ -483,6 +483,24 @@ def other_rows(P, torch, np, peaks, only=None):
                                     "frac": tests / sec * 34 / alu_peak,
                                     "note": "the labeller's filter tests; ray generation included"}}
         del pbuf
+    # ---- depth + normal images (Fig. 3 / 4) from the field and from the mesh (Fig. 5's comparison)
+    if want("aov"):
+        w_ = WORKLOAD
+        camA = default_camera(1920, 1080, seed=1)
+        netA = P.DDFNet(w_["in_freqs"], w_["hidden"], w_["layers"],
+                        init_weights(w_["in_freqs"], w_["hidden"], w_["layers"], seed=w_["seed"]), "bf16")
+        secA = _time(torch, lambda: netA.render_aov(camA), 5)
+        npx = 1920 * 1080
+        mesh_ms = {}
+        for label_, (Vm, Fm) in (("8,192-triangle knot", (V, F)),
+                                 ("131,072-triangle knot", torus_knot(3, 2, 0.08, 1024, 64))):
+            mA = P.DDFMesh(Vm, Fm)
+            mesh_ms[label_] = _time(torch, lambda: mA.render_aov(camA), 2) * 1e3
+            del mA
+        rows["aov"] = {"workload": "1920 x 1080 depth + normal images, one ray per pixel: the BF16 field "
+                                   "(78 -> 256 x 8 -> 2) against brute-force casting of the same rays on meshes",
+                       "field_ms": secA * 1e3, "field_rays_per_s": npx / secA, "mesh_ms": mesh_ms}
+        del netA
     # ---- a9 training step: BF16 tensor-core GEMMs (FP32 accumulate, FP32 masters), and the FP32 path
     if want("train"):
         Fq, Wd, Ld = 12, 256, 8

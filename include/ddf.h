@@ -272,6 +272,21 @@ DDF_API int ddf_group_config(ddf_group group, int* host_out6);
 DDF_API int ddf_render(ddf_net net, const ddf_camera* cam, int spp, int bounces, float* d_image,
                cudaStream_t stream);
 
+/* Depth and normal maps (the t-value and normal images of Fig. 3 and Fig. 4): one primary ray
+ * per pixel (the renderer's camera, its bounce-0 jitter with spp = 1), advanced to the unit ball
+ * and queried once with the Eq. 3 normal. d_depth (DEVICE float32 H x W): distance from the eye
+ * to the hit point along the ray, |entry - eye| + max(dist, 0), +inf where the ray misses
+ * (logit <= 0 or the ball). d_normal (DEVICE float32 H x W x 3): the normal, 0 on a miss.
+ * Ordered on stream; uses the handle's render buffers. Errors as ddf_render. */
+DDF_API int ddf_render_aov(ddf_net net, const ddf_camera* cam, float* d_depth, float* d_normal, cudaStream_t stream);
+
+/* The same pixel rays cast against a mesh from the eye by the labeller (the paper's non-DDF ray
+ * tracer, here brute force): d_depth (H x W) = nearest-hit distance (+inf on a miss), d_normal
+ * (H x W x 3) = unit normal of the hit face turned towards the eye (0 on a miss), d_tri (H x W,
+ * nullable) = the hit face (-1 on a miss). Synchronous (frees its ray buffers). */
+DDF_API int ddf_mesh_render_aov(ddf_mesh mesh, const ddf_camera* cam, float* d_depth, float* d_normal, int32_t* d_tri,
+                                cudaStream_t stream);
+
 /* Number of field queries issued per bounce by the last ddf_render on this handle
  * (counts[b-1] for b = 1..bounces; HOST array of max_bounces entries). Synchronises with
  * the stream of that render. */

@@ -95,6 +95,8 @@ _SIG = {
     "ddf_sample_surface": (C.c_int, [_P, C.POINTER(ddf_sampler), _P, _P, _P, _P, _P, _I64, C.POINTER(_I64), _P]),
     "ddf_sample_pov": (C.c_int, [_P, C.POINTER(ddf_pov), _P, _P, _P, _P, _P]),
     "ddf_set_head": (C.c_int, [_P, C.POINTER(ddf_head), _P]),
+    "ddf_render_aov": (C.c_int, [_P, C.POINTER(ddf_camera), _P, _P, _P]),
+    "ddf_mesh_render_aov": (C.c_int, [_P, C.POINTER(ddf_camera), _P, _P, _P, _P]),
     "ddf_get_arch": (C.c_int, [_P, C.POINTER(ddf_arch)]),
     "ddf_get_weight_norm": (C.c_int, [_P, _P, C.c_size_t, _P, C.c_size_t, _P]),
     "ddf_label_stats": (C.c_int, [_P, C.POINTER(_I64)]),

@@ -328,6 +328,30 @@ int ddf_render(ddf_net net, const ddf_camera* cam, int spp, int bounces, float* 
     return render(net, cam, spp, bounces, d_image, stream);
 }
 
+namespace {
+int check_aov_camera(const ddf_camera* cam) {
+    if (cam->width <= 0 || cam->height <= 0 || (int64_t)cam->width * cam->height > (int64_t(1) << 28))
+        return fail(DDF_ERR_INVALID_ARG, "bad image size %d x %d (at most 2^28 pixels)", cam->width, cam->height);
+    if (!(cam->vfov_deg > 0.f && cam->vfov_deg < 180.f)) return fail(DDF_ERR_INVALID_ARG, "vfov must be in (0, 180)");
+    return DDF_OK;
+}
+}  // namespace
+
+int ddf_render_aov(ddf_net net, const ddf_camera* cam, float* d_depth, float* d_normal, cudaStream_t stream) {
+    if (!net || !cam || !d_depth || !d_normal) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    int rc = check_aov_camera(cam);
+    if (rc) return rc;
+    return render_aov(net, cam, d_depth, d_normal, stream);
+}
+
+int ddf_mesh_render_aov(ddf_mesh mesh, const ddf_camera* cam, float* d_depth, float* d_normal, int32_t* d_tri,
+                        cudaStream_t stream) {
+    if (!mesh || !cam || !d_depth || !d_normal) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    int rc = check_aov_camera(cam);
+    if (rc) return rc;
+    return mesh_render_aov(mesh, cam, d_depth, d_normal, d_tri, stream);
+}
+
 int ddf_render_stats(ddf_net net, int64_t* host_counts, int max_bounces) {
     if (!net || !host_counts || max_bounces <= 0) return fail(DDF_ERR_INVALID_ARG, "bad argument");
     for (int b = 0; b < max_bounces; ++b) host_counts[b] = 0;

@@ -152,6 +152,11 @@ int field_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
 // ------------------------------------------------------------------ renderer (wavefront.cu)
 int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* image,
            cudaStream_t stream);
+// Depth (t from the eye) and normal maps of the field (ddf_render_aov) and of a mesh
+// (ddf_mesh_render_aov) from the same pixel rays.
+int render_aov(ddf_net_s* net, const ddf_camera* cam, float* depth, float* normal, cudaStream_t stream);
+int mesh_render_aov(ddf_mesh_s* m, const ddf_camera* cam, float* depth, float* normal, int32_t* tri,
+                    cudaStream_t stream);
 
 // ------------------------------------------------------------------ labelling (label.cu)
 int mesh_prepare(ddf_mesh_s* m, const float* host_verts, const int32_t* host_tris);

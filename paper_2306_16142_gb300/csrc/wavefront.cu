@@ -25,6 +25,23 @@ struct CamDev {
     float albedo, env;
 };
 
+// Unit direction of path pid's primary ray: pixel pid / spp, jitter from the bounce-0 draw.
+__device__ __forceinline__ void primary_dir(const CamDev& cam, int64_t pid, int spp, float* dx, float* dy,
+                                            float* dz) {
+    const int64_t pix = pid / spp;
+    const float x = (float)(pix % cam.W), y = (float)(pix / cam.W);
+    const uint4 rnd = path_draw(cam.seed, (uint64_t)pid, 0u);
+    const float px = (2.f * (x + u24(rnd.x)) / cam.W - 1.f) * cam.th * cam.aspect;
+    const float py = (1.f - 2.f * (y + u24(rnd.y)) / cam.H) * cam.th;
+    float vx = cam.f[0] + px * cam.r[0] + py * cam.u[0];
+    float vy = cam.f[1] + px * cam.r[1] + py * cam.u[1];
+    float vz = cam.f[2] + px * cam.r[2] + py * cam.u[2];
+    const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
+    *dx = vx * inv;
+    *dy = vy * inv;
+    *dz = vz * inv;
+}
+
 __device__ __forceinline__ int warp_compact(bool alive, int* counter) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned m = __ballot_sync(0xffffffffu, alive);
@@ -47,17 +64,7 @@ __global__ void __launch_bounds__(kThreads) raygen_kernel(CamDev cam, int spp, i
         bool alive = false;
         float ox = 0, oy = 0, oz = 0, dx = 0, dy = 0, dz = 0;
         if (valid) {
-            const int64_t pid = pid0 + i;
-            const int64_t pix = pid / spp;
-            const float x = (float)(pix % cam.W), y = (float)(pix / cam.W);
-            const uint4 rnd = path_draw(cam.seed, (uint64_t)pid, 0u);
-            const float px = (2.f * (x + u24(rnd.x)) / cam.W - 1.f) * cam.th * cam.aspect;
-            const float py = (1.f - 2.f * (y + u24(rnd.y)) / cam.H) * cam.th;
-            dx = cam.f[0] + px * cam.r[0] + py * cam.u[0];
-            dy = cam.f[1] + px * cam.r[1] + py * cam.u[1];
-            dz = cam.f[2] + px * cam.r[2] + py * cam.u[2];
-            const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-            dx *= inv; dy *= inv; dz *= inv;
+            primary_dir(cam, pid0 + i, spp, &dx, &dy, &dz);
             const float b = cam.eye[0] * dx + cam.eye[1] * dy + cam.eye[2] * dz;
             const float c = cam.eye[0] * cam.eye[0] + cam.eye[1] * cam.eye[1] + cam.eye[2] * cam.eye[2] - 1.f;
             const float disc = b * b - c;
@@ -153,6 +160,72 @@ __global__ void add_counts(const int* __restrict__ counts, int bounces, int64_t*
     if (b < bounces) totals[b] += counts[b];
 }
 
+// ---- AOV renders (Fig. 3 / Fig. 4: t-value and normal maps)
+__global__ void aov_fill_kernel(int64_t px0, int64_t npx, float* __restrict__ depth, float* __restrict__ normal) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npx; p += (int64_t)gridDim.x * blockDim.x) {
+        depth[px0 + p] = __int_as_float(0x7f800000);
+        normal[3 * (px0 + p)] = normal[3 * (px0 + p) + 1] = normal[3 * (px0 + p) + 2] = 0.f;
+    }
+}
+
+// Per queried primary ray: a hit (logit > 0) gives depth = |o - eye| + max(dist, 0) (the origin
+// was advanced from the eye to the unit ball) and the Eq. 3 normal.
+__global__ void aov_kernel(CamDev cam, int64_t px0, const int* __restrict__ count, const float* __restrict__ o,
+                           const uint32_t* __restrict__ lid, const float* __restrict__ dist,
+                           const float* __restrict__ logit, const float* __restrict__ nrm, float* __restrict__ depth,
+                           float* __restrict__ normal) {
+    const int n = *count;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (!(logit[i] > 0.f)) continue;
+        const int64_t p = px0 + lid[i];
+        const float ex = o[3 * i] - cam.eye[0], ey = o[3 * i + 1] - cam.eye[1], ez = o[3 * i + 2] - cam.eye[2];
+        depth[p] = sqrtf(ex * ex + ey * ey + ez * ez) + fmaxf(dist[i], 0.f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) normal[3 * p + c] = nrm[3 * i + c];
+    }
+}
+
+// The same pixel rays from the eye (spp = 1), for casting against a mesh.
+__global__ void camera_rays_kernel(CamDev cam, int64_t npx, float* __restrict__ o, float* __restrict__ w) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npx; p += (int64_t)gridDim.x * blockDim.x) {
+        float dx, dy, dz;
+        primary_dir(cam, p, 1, &dx, &dy, &dz);
+        o[3 * p] = cam.eye[0];
+        o[3 * p + 1] = cam.eye[1];
+        o[3 * p + 2] = cam.eye[2];
+        w[3 * p] = dx;
+        w[3 * p + 1] = dy;
+        w[3 * p + 2] = dz;
+    }
+}
+
+// Unit normal of the hit face, turned towards the viewer (n . w < 0); 0 on a miss.
+__global__ void face_normal_kernel(const float* __restrict__ V, const int32_t* __restrict__ F,
+                                   const float* __restrict__ w, const int32_t* __restrict__ tri, int64_t n,
+                                   float* __restrict__ normal) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int k = tri[p];
+        float nx = 0.f, ny = 0.f, nz = 0.f;
+        if (k >= 0) {
+            const int i0 = F[3 * k], i1 = F[3 * k + 1], i2 = F[3 * k + 2];
+            const float ax = V[3 * i1] - V[3 * i0], ay = V[3 * i1 + 1] - V[3 * i0 + 1], az = V[3 * i1 + 2] - V[3 * i0 + 2];
+            const float bx = V[3 * i2] - V[3 * i0], by = V[3 * i2 + 1] - V[3 * i0 + 1], bz = V[3 * i2 + 2] - V[3 * i0 + 2];
+            nx = ay * bz - az * by;
+            ny = az * bx - ax * bz;
+            nz = ax * by - ay * bx;
+            const float len = sqrtf(nx * nx + ny * ny + nz * nz);
+            const float sgn = (nx * w[3 * p] + ny * w[3 * p + 1] + nz * w[3 * p + 2]) > 0.f ? -1.f : 1.f;
+            const float s = len > 0.f ? sgn / len : 0.f;
+            nx *= s;
+            ny *= s;
+            nz *= s;
+        }
+        normal[3 * p] = nx;
+        normal[3 * p + 1] = ny;
+        normal[3 * p + 2] = nz;
+    }
+}
+
 struct WaveBufs {
     float *o[2], *w[2], *thr[2];
     uint32_t* lid[2];
@@ -162,45 +235,8 @@ struct WaveBufs {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-}  // namespace
-
-int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* image,
-           cudaStream_t stream) {
-    const int64_t npix = (int64_t)cam->width * cam->height;
-    const int64_t px_per_wave = std::max<int64_t>(1, std::min<int64_t>(npix, kWaveMax / spp));
-    const int64_t wave_paths = px_per_wave * spp;
-    // workspace layout
-    const size_t fvec = align256(sizeof(float) * 3 * wave_paths);
-    const size_t fsc = align256(sizeof(float) * wave_paths);
-    const size_t need = 2 * (2 * fvec + 2 * fsc) + fsc * 3 + fvec + align256(sizeof(int) * 64);
-    if (net->render_ws_bytes < need) {
-        if (net->render_ws) cudaFree(net->render_ws);
-        net->render_ws = nullptr;
-        net->render_ws_bytes = 0;
-        DDF_CUDA_TRY(cudaMalloc(&net->render_ws, need));
-        net->render_ws_bytes = need;
-    }
-    if (net->render_counts_len < bounces) {
-        if (net->render_counts) cudaFree(net->render_counts);
-        net->render_counts = nullptr;
-        DDF_CUDA_TRY(cudaMalloc(&net->render_counts, sizeof(int64_t) * 64));
-        net->render_counts_len = 64;
-    }
-    char* p = (char*)net->render_ws;
-    WaveBufs B;
-    for (int k = 0; k < 2; ++k) {
-        B.o[k] = (float*)p; p += fvec;
-        B.w[k] = (float*)p; p += fvec;
-        B.thr[k] = (float*)p; p += fsc;
-        B.lid[k] = (uint32_t*)p; p += fsc;
-    }
-    B.dist = (float*)p; p += fsc;
-    B.logit = (float*)p; p += fsc;
-    B.radiance = (float*)p; p += fsc;
-    B.nrm = (float*)p; p += fvec;
-    B.counts = (int*)p;
-
-    // camera basis in double, rounded once
+// Camera basis in double, rounded once: forward f = look_at - eye, right = f x up, up' = right x f.
+int make_cam(const ddf_camera* cam, CamDev* out) {
     CamDev cd;
     double eye[3], f[3], r[3], u[3];
     for (int c = 0; c < 3; ++c) {
@@ -232,6 +268,56 @@ int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* i
     cd.seed = cam->seed;
     cd.albedo = cam->albedo;
     cd.env = cam->env;
+    *out = cd;
+    return DDF_OK;
+}
+
+// The handle's grow-only render workspace for waves of wave_paths paths.
+int render_bufs(ddf_net_s* net, int64_t wave_paths, WaveBufs* out) {
+    const size_t fvec = align256(sizeof(float) * 3 * wave_paths);
+    const size_t fsc = align256(sizeof(float) * wave_paths);
+    const size_t need = 2 * (2 * fvec + 2 * fsc) + fsc * 3 + fvec + align256(sizeof(int) * 64);
+    if (net->render_ws_bytes < need) {
+        if (net->render_ws) cudaFree(net->render_ws);
+        net->render_ws = nullptr;
+        net->render_ws_bytes = 0;
+        DDF_CUDA_TRY(cudaMalloc(&net->render_ws, need));
+        net->render_ws_bytes = need;
+    }
+    char* p = (char*)net->render_ws;
+    WaveBufs& B = *out;
+    for (int k = 0; k < 2; ++k) {
+        B.o[k] = (float*)p; p += fvec;
+        B.w[k] = (float*)p; p += fvec;
+        B.thr[k] = (float*)p; p += fsc;
+        B.lid[k] = (uint32_t*)p; p += fsc;
+    }
+    B.dist = (float*)p; p += fsc;
+    B.logit = (float*)p; p += fsc;
+    B.radiance = (float*)p; p += fsc;
+    B.nrm = (float*)p; p += fvec;
+    B.counts = (int*)p;
+    return DDF_OK;
+}
+
+}  // namespace
+
+int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* image,
+           cudaStream_t stream) {
+    const int64_t npix = (int64_t)cam->width * cam->height;
+    const int64_t px_per_wave = std::max<int64_t>(1, std::min<int64_t>(npix, kWaveMax / spp));
+    const int64_t wave_paths = px_per_wave * spp;
+    WaveBufs B;
+    int rc0 = render_bufs(net, wave_paths, &B);
+    if (rc0) return rc0;
+    if (net->render_counts_len < bounces) {
+        if (net->render_counts) cudaFree(net->render_counts);
+        net->render_counts = nullptr;
+        DDF_CUDA_TRY(cudaMalloc(&net->render_counts, sizeof(int64_t) * 64));
+        net->render_counts_len = 64;
+    }
+    CamDev cd;
+    if ((rc0 = make_cam(cam, &cd))) return rc0;
 
     DDF_CUDA_TRY(cudaMemsetAsync(net->render_counts, 0, sizeof(int64_t) * 64, stream));
     net->last_bounces = bounces;
@@ -271,6 +357,61 @@ int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* i
         add_counts<<<1, 64, 0, stream>>>(B.counts, bounces, net->render_counts);
         DDF_LAUNCH_CHECK();
     }
+    return DDF_OK;
+}
+
+int render_aov(ddf_net_s* net, const ddf_camera* cam, float* depth, float* normal, cudaStream_t stream) {
+    const int64_t npix = (int64_t)cam->width * cam->height;
+    const int64_t px_per_wave = std::min<int64_t>(npix, kWaveMax);
+    WaveBufs B;
+    int rc = render_bufs(net, px_per_wave, &B);
+    if (rc) return rc;
+    CamDev cd;
+    if ((rc = make_cam(cam, &cd))) return rc;
+    const int grid = num_sms() * 4;
+    for (int64_t px0 = 0; px0 < npix; px0 += px_per_wave) {
+        const int64_t npx = std::min(px_per_wave, npix - px0);
+        DDF_CUDA_TRY(cudaMemsetAsync(B.counts, 0, sizeof(int), stream));
+        aov_fill_kernel<<<grid, kThreads, 0, stream>>>(px0, npx, depth, normal);
+        const int rg = (int)std::min<int64_t>((npx + kThreads - 1) / kThreads, grid);
+        raygen_kernel<<<rg, kThreads, 0, stream>>>(cd, 1, px0, npx, B.o[0], B.w[0], B.lid[0], B.thr[0], B.radiance,
+                                                   B.counts);
+        DDF_LAUNCH_CHECK();
+        if ((rc = field_query(net, B.o[0], B.w[0], npx, B.counts, B.dist, B.logit, nullptr, B.nrm, stream))) return rc;
+        aov_kernel<<<grid, kThreads, 0, stream>>>(cd, px0, B.counts, B.o[0], B.lid[0], B.dist, B.logit, B.nrm, depth,
+                                                  normal);
+        DDF_LAUNCH_CHECK();
+    }
+    return DDF_OK;
+}
+
+int mesh_render_aov(ddf_mesh_s* m, const ddf_camera* cam, float* depth, float* normal, int32_t* tri,
+                    cudaStream_t stream) {
+    const int64_t npix = (int64_t)cam->width * cam->height;
+    CamDev cd;
+    int rc = make_cam(cam, &cd);
+    if (rc) return rc;
+    const size_t fvec = align256(sizeof(float) * 3 * npix);
+    const size_t need = 2 * fvec + align256(npix) + (tri ? 0 : align256(sizeof(int32_t) * npix));
+    char* ws = nullptr;
+    DDF_CUDA_TRY(cudaMalloc(&ws, need));
+    float* o = (float*)ws;
+    float* w = (float*)(ws + fvec);
+    uint8_t* hit = (uint8_t*)(ws + 2 * fvec);
+    int32_t* t = tri ? tri : (int32_t*)(ws + 2 * fvec + align256(npix));
+    const int grid = num_sms() * 4;
+    camera_rays_kernel<<<grid, kThreads, 0, stream>>>(cd, npix, o, w);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) rc = label_rays(m, o, w, npix, depth, hit, t, stream);
+    if (e == cudaSuccess && !rc) {
+        face_normal_kernel<<<grid, kThreads, 0, stream>>>(m->verts, m->tris, w, t, npix, normal);
+        e = cudaGetLastError();
+    }
+    // the workspace is freed once the kernels that read it are done
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    cudaFree(ws);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(DDF_ERR_CUDA, "mesh AOV render: %s", cudaGetErrorString(e));
     return DDF_OK;
 }
 

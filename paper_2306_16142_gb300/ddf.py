@@ -147,6 +147,15 @@ class DDFNet:
                                                    _stream()))
         return image
 
+    def render_aov(self, cam):
+        """Depth (H, W; distance from the eye, inf on a miss) and normal (H, W, 3) maps of one
+        primary ray per pixel (ddf_render_aov)."""
+        c = camera_struct(cam)
+        depth = torch.empty(cam.height, cam.width, device="cuda")
+        normal = torch.empty(cam.height, cam.width, 3, device="cuda")
+        check("ddf_render_aov", _abi.load().ddf_render_aov(self.h, C.byref(c), _ptr(depth), _ptr(normal), _stream()))
+        return depth, normal
+
     def render_stats(self, bounces: int):
         arr = (C.c_int64 * bounces)()
         check("ddf_render_stats", _abi.load().ddf_render_stats(self.h, arr, bounces))
@@ -237,6 +246,17 @@ class DDFMesh:
         arr = (C.c_int64 * 2)()
         check("ddf_label_stats", _abi.load().ddf_label_stats(self.h, arr))
         return {"retests": arr[0], "finals": arr[1]}
+
+    def render_aov(self, cam):
+        """Depth, normal and hit-face maps of the camera's pixel rays cast against the mesh
+        (ddf_mesh_render_aov)."""
+        c = camera_struct(cam)
+        depth = torch.empty(cam.height, cam.width, device="cuda")
+        normal = torch.empty(cam.height, cam.width, 3, device="cuda")
+        tri = torch.empty(cam.height, cam.width, dtype=torch.int32, device="cuda")
+        check("ddf_mesh_render_aov", _abi.load().ddf_mesh_render_aov(self.h, C.byref(c), _ptr(depth), _ptr(normal),
+                                                                     _ptr(tri), _stream()))
+        return depth, normal, tri
 
     @staticmethod
     def sample_buffers(cap: int):
