@@ -432,20 +432,35 @@ def other_rows(P, torch, np, peaks, only=None):
     # ---- a8 labelling
     if want("label"):
         out = mesh.label(to, tw)
+        # the sweep over all faces (FP32 issue-bound)
+        mesh.set_accel("none")
         sec = _time(torch, lambda: mesh.label(to, tw, out), 5)
         st = mesh.stats()
         tests = o.shape[0] * F.shape[0]
         alu_peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6      # FP32 lane-instructions / s
+        sweep = {"ms": sec * 1e3, "rays_per_s": o.shape[0] / sec, "tests_per_s": tests / sec,
+                 "fp64_retests_per_ray": st["retests"] / o.shape[0],
+                 "roofline": {"bound": "alu", "achieved": tests / sec * 34 / 1e12,
+                              "peak": alu_peak / 1e12, "unit": "T FP32-instr/s",
+                              "frac": tests / sec * 34 / alu_peak,
+                              "note": "34 FP32 operations per filter test (count of the hot loop; the "
+                                      "thread's two rays run as the lanes of packed FP32 pairs)"}}
+        # the hierarchy (the default): the same labels, a few dozen node visits and face tests per ray
+        mesh.set_accel("bvh")
+        secb = _time(torch, lambda: mesh.label(to, tw, out), 5)
+        bs = mesh.bvh_stats()
+        stb = mesh.stats()
         rows["label"] = {"workload": "2^20 rays (half uniform, half surface-aimed, sigma 0.05 rad) x 8,192-triangle "
                                      "(3,2) knot",
-                         "rays_per_s": o.shape[0] / sec, "tests_per_s": tests / sec, "ms": sec * 1e3,
-                         "fp64_retests_per_ray": st["retests"] / o.shape[0], "fp64_final_evals": st["finals"],
-                         "roofline": {"bound": "alu", "achieved": tests / sec * 34 / 1e12,
-                                      "peak": alu_peak / 1e12, "unit": "T FP32-instr/s",
-                                      "frac": tests / sec * 34 / alu_peak,
-                                      "note": "34 FP32 operations per filter test (count of the hot loop; the "
-                                              "thread's two rays run as the lanes of packed FP32 pairs)"},
-                         "hbm_gbs": (o.shape[0] * 33) / sec / 1e9}
+                         "rays_per_s": o.shape[0] / secb, "ms": secb * 1e3, "accel": "bvh",
+                         "bvh": {"nodes": bs["nodes"], "depth": bs["depth"],
+                                 "node_visits_per_ray": bs["visits"] / o.shape[0],
+                                 "face_tests_per_ray": bs["face_tests"] / o.shape[0],
+                                 "fp64_retests_per_ray": stb["retests"] / o.shape[0],
+                                 "node_bytes_per_s": bs["visits"] * 64 / secb,
+                                 "note": "64-byte two-box nodes and 48-byte faces, all resident in L2: a "
+                                         "latency-bound traversal with no HBM roofline"},
+                         "sweep": sweep, "speedup_vs_sweep": sec / secb}
     # ---- the surface-marching training-set sampler (Sec. 5.2), Table 2's smallest setting
     if want("sampler"):
         s = 10
@@ -453,6 +468,9 @@ def other_rows(P, torch, np, peaks, only=None):
         first = mesh.sample_surface(s, s, s, 1e-4, 21)
         buf = P.DDFMesh.sample_buffers(first["count"])
         sec = _time(torch, lambda: mesh.sample_surface(s, s, s, 1e-4, 21, out=buf), 2)
+        mesh.set_accel("none")
+        sec_sweep = _time(torch, lambda: mesh.sample_surface(s, s, s, 1e-4, 21, out=buf), 1)
+        mesh.set_accel("bvh")
         n = first["count"]
         kinds = np.bincount((first["key"] % 4).cpu().numpy(), minlength=4)
         rays = C + 2 * int(kinds[1])      # candidates + two Eq. 12 rays per march point of a missing one
@@ -460,28 +478,34 @@ def other_rows(P, torch, np, peaks, only=None):
         alu_peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
         rows["sampler"] = {"workload": "s_fc = s_dr = s_p = 10 on the 8,192-triangle (3,2) knot: 819,200 candidate "
                                        "rays, odd-even parity, marching, Eq. 12 rays of the missing candidates",
-                           "samples": n, "samples_per_s": n / sec, "ms": sec * 1e3,
+                           "samples": n, "samples_per_s": n / sec, "ms": sec * 1e3, "accel": "bvh",
                            "kinds": [int(x) for x in kinds], "labelled_rays": rays,
-                           "roofline": {"bound": "alu", "achieved": tests / sec * 34 / 1e12,
-                                        "peak": alu_peak / 1e12, "unit": "T FP32-instr/s",
-                                        "frac": tests / sec * 34 / alu_peak,
-                                        "note": "the labeller's filter tests over the whole call (allocation, "
-                                                "two host scans and the other kernels included)"}}
+                           "sweep": {"ms": sec_sweep * 1e3,
+                                     "roofline": {"bound": "alu", "achieved": tests / sec_sweep * 34 / 1e12,
+                                                  "peak": alu_peak / 1e12, "unit": "T FP32-instr/s",
+                                                  "frac": tests / sec_sweep * 34 / alu_peak,
+                                                  "note": "the labeller's filter tests over the whole call "
+                                                          "(allocation, two host scans and the other kernels "
+                                                          "included)"}}}
         del first, buf
     # ---- the point-of-view sampling of Sec. 6: 10 x 5 cameras, 256 x 256 films
     if want("pov"):
         n = 50 * 256 * 256
         pbuf = mesh.sample_pov(10, 5, 256)
         sec = _time(torch, lambda: mesh.sample_pov(10, 5, 256, out=pbuf), 3)
+        mesh.set_accel("none")
+        sec_sweep = _time(torch, lambda: mesh.sample_pov(10, 5, 256, out=pbuf), 2)
+        mesh.set_accel("bvh")
         tests = n * F.shape[0]
         alu_peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
         rows["pov"] = {"workload": "10 x 5 cameras at distance 2.5, 30 deg field of view, 256 x 256 pixels each "
                                    "(3,276,800 rays) labelled against the 8,192-triangle (3,2) knot",
-                       "rays_per_s": n / sec, "ms": sec * 1e3, "hits": int(pbuf["hit"].sum().item()),
-                       "roofline": {"bound": "alu", "achieved": tests / sec * 34 / 1e12,
-                                    "peak": alu_peak / 1e12, "unit": "T FP32-instr/s",
-                                    "frac": tests / sec * 34 / alu_peak,
-                                    "note": "the labeller's filter tests; ray generation included"}}
+                       "rays_per_s": n / sec, "ms": sec * 1e3, "accel": "bvh", "hits": int(pbuf["hit"].sum().item()),
+                       "sweep": {"ms": sec_sweep * 1e3,
+                                 "roofline": {"bound": "alu", "achieved": tests / sec_sweep * 34 / 1e12,
+                                              "peak": alu_peak / 1e12, "unit": "T FP32-instr/s",
+                                              "frac": tests / sec_sweep * 34 / alu_peak,
+                                              "note": "the labeller's filter tests; ray generation included"}}}
         del pbuf
     # ---- depth + normal images (Fig. 3 / 4) from the field and from the mesh (Fig. 5's comparison)
     if want("aov"):
@@ -495,10 +519,13 @@ def other_rows(P, torch, np, peaks, only=None):
         for label_, (Vm, Fm) in (("8,192-triangle knot", (V, F)),
                                  ("131,072-triangle knot", torus_knot(3, 2, 0.08, 1024, 64))):
             mA = P.DDFMesh(Vm, Fm)
-            mesh_ms[label_] = _time(torch, lambda: mA.render_aov(camA), 2) * 1e3
+            mesh_ms[label_ + ", bvh"] = _time(torch, lambda: mA.render_aov(camA), 3) * 1e3
+            mA.set_accel("none")
+            mesh_ms[label_ + ", all faces"] = _time(torch, lambda: mA.render_aov(camA), 1) * 1e3
             del mA
         rows["aov"] = {"workload": "1920 x 1080 depth + normal images, one ray per pixel: the BF16 field "
-                                   "(78 -> 256 x 8 -> 2) against brute-force casting of the same rays on meshes",
+                                   "(78 -> 256 x 8 -> 2) against casting the same rays on meshes (through the "
+                                   "hierarchy, and against all faces)",
                        "field_ms": secA * 1e3, "field_rays_per_s": npx / secA, "mesh_ms": mesh_ms}
         del netA
     # ---- a9 training step: BF16 tensor-core GEMMs (FP32 accumulate, FP32 masters), and the FP32 path

@@ -64,6 +64,10 @@ extern "C" {
 #define DDF_HEAD_CLAMP 1  /* the paper's single field value y~, clamp loss of Eq. 7                */
 #define DDF_HEAD_SQUISH 2 /* single field value y~, squish loss of Eq. 5 with sigma = tanh         */
 
+/* ---- labelling acceleration (ddf_mesh_set_accel) ---------------------------------------- */
+#define DDF_ACCEL_NONE 0 /* every ray against every face (the linear search of Sec. 1)                */
+#define DDF_ACCEL_BVH 1  /* bounding-volume hierarchy built at mesh creation (the default)           */
+
 typedef struct ddf_net_s* ddf_net;
 typedef struct ddf_mesh_s* ddf_mesh;
 
@@ -309,9 +313,17 @@ DDF_API int ddf_mesh_create(const float* host_verts, int64_t nv, const int32_t* 
                     ddf_mesh* out);
 DDF_API int ddf_mesh_destroy(ddf_mesh mesh);
 
+/* How ddf_label_rays (and every call built on it) searches the faces: DDF_ACCEL_BVH (the
+ * default; a binned-SAH hierarchy built on the host by ddf_mesh_create) or DDF_ACCEL_NONE (every
+ * ray against every face). Both give the same labels bit for bit: the hierarchy only skips boxes
+ * (conservatively padded, conservatively tested) that cannot hold a face the float64 test would
+ * accept at a distance up to the best found so far, and ties go to the lower face index either
+ * way. INVALID_ARG for another value. */
+DDF_API int ddf_mesh_set_accel(ddf_mesh mesh, int accel);
+
 /* Ray labelling for training data (Sec. 5; the nearest-triangle search of Sec. 1): for each
  * ray the nearest Moeller-Trumbore hit over all triangles with t > 0, barycentric bounds
- * inclusive, ties to the lowest triangle index. Outputs (device, n rows): dist = t rounded
+ * inclusive, ties to the lowest triangle index (faces searched as ddf_mesh_set_accel says). Outputs (device, n rows): dist = t rounded
  * to float32 (+inf on a miss), hit (0/1), tri (index or -1; nullable). A float32 pass
  * with rigorous error bounds decides every clear case; every grazing or near-tie
  * (ray, triangle) pair is re-tested in float64 with a fixed, FMA-free order of operations,
@@ -324,6 +336,11 @@ DDF_API int ddf_label_rays(ddf_mesh mesh, const float* d_origins, const float* d
  * host_counts[0] = re-tests of ambiguous pairs, host_counts[1] = final-distance evaluations.
  * Synchronises with the stream of that call. */
 DDF_API int ddf_label_stats(ddf_mesh mesh, int64_t* host_counts);
+
+/* The mesh's hierarchy and the work of its last labelling call through it: host_out[0] = nodes,
+ * [1] = depth, [2] = node visits and [3] = face tests of that call (both 0 after a call that swept
+ * all faces). Synchronises with the stream of that call. */
+DDF_API int ddf_mesh_bvh_stats(ddf_mesh mesh, int64_t* host_out);
 
 /* ---- training-set sampling --------------------------------------------------------------- */
 

@@ -20,6 +20,7 @@ DDF_ERR_NUMERIC = -6
 DDF_ERR_IO = -7
 DDF_FP32, DDF_BF16, DDF_FP8 = 0, 1, 2
 DDF_HEAD_TWO, DDF_HEAD_CLAMP, DDF_HEAD_SQUISH = 0, 1, 2
+DDF_ACCEL_NONE, DDF_ACCEL_BVH = 0, 1
 
 ERR_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "UNSUPPORTED", -5: "TIMEOUT",
              -6: "NUMERIC", -7: "IO"}
@@ -95,6 +96,8 @@ _SIG = {
     "ddf_sample_surface": (C.c_int, [_P, C.POINTER(ddf_sampler), _P, _P, _P, _P, _P, _I64, C.POINTER(_I64), _P]),
     "ddf_sample_pov": (C.c_int, [_P, C.POINTER(ddf_pov), _P, _P, _P, _P, _P]),
     "ddf_set_head": (C.c_int, [_P, C.POINTER(ddf_head), _P]),
+    "ddf_mesh_set_accel": (C.c_int, [_P, C.c_int]),
+    "ddf_mesh_bvh_stats": (C.c_int, [_P, C.POINTER(_I64)]),
     "ddf_render_aov": (C.c_int, [_P, C.POINTER(ddf_camera), _P, _P, _P]),
     "ddf_mesh_render_aov": (C.c_int, [_P, C.POINTER(ddf_camera), _P, _P, _P, _P]),
     "ddf_get_arch": (C.c_int, [_P, C.POINTER(ddf_arch)]),

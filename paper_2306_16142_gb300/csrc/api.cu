@@ -412,6 +412,7 @@ int ddf_mesh_create(const float* host_verts, int64_t nv, const int32_t* host_tri
     int rc = DDF_OK;
     if (e != cudaSuccess) rc = fail(DDF_ERR_CUDA, "mesh upload: %s", cudaGetErrorString(e));
     if (!rc) rc = mesh_prepare(m, host_verts, host_tris);
+    if (!rc) rc = bvh_build(m, host_verts, host_tris);
     if (rc) {
         ddf_mesh_destroy(m);
         return rc;
@@ -428,7 +429,16 @@ int ddf_mesh_destroy(ddf_mesh m) {
     cudaFree(m->tri_hot);
     cudaFree(m->tri_aux);
     cudaFree(m->stats);
+    cudaFree(m->bvh);
+    cudaFree(m->bvh_tri);
     delete m;
+    return DDF_OK;
+}
+
+int ddf_mesh_set_accel(ddf_mesh mesh, int accel) {
+    if (!mesh) return fail(DDF_ERR_INVALID_ARG, "mesh is NULL");
+    if (accel != DDF_ACCEL_NONE && accel != DDF_ACCEL_BVH) return fail(DDF_ERR_INVALID_ARG, "unknown accel %d", accel);
+    mesh->accel = accel;
     return DDF_OK;
 }
 
@@ -481,6 +491,18 @@ int ddf_label_stats(ddf_mesh mesh, int64_t* host_counts) {
     DDF_CUDA_TRY(cudaMemcpy(h, mesh->stats, sizeof(h), cudaMemcpyDeviceToHost));
     host_counts[0] = (int64_t)h[0];
     host_counts[1] = (int64_t)h[1];
+    return DDF_OK;
+}
+
+int ddf_mesh_bvh_stats(ddf_mesh mesh, int64_t* host_out) {
+    if (!mesh || !host_out) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    DDF_CUDA_TRY(cudaStreamSynchronize(mesh->last_stream));
+    unsigned long long h[4];
+    DDF_CUDA_TRY(cudaMemcpy(h, mesh->stats, sizeof(h), cudaMemcpyDeviceToHost));
+    host_out[0] = mesh->bvh_nodes;
+    host_out[1] = mesh->bvh_depth;
+    host_out[2] = (int64_t)h[2];
+    host_out[3] = (int64_t)h[3];
     return DDF_OK;
 }
 

@@ -113,6 +113,12 @@ struct ddf_mesh_s {
     float4* tri_aux = nullptr;   // nt x 2 float4: (centroid, bounding radius), (E, 0, 0, 0)
     unsigned long long* stats = nullptr;   // device [2]
     cudaStream_t last_stream = nullptr;
+    // bounding-volume hierarchy (bvh.cu): 4 float4 per node, faces reordered into bvh_tri
+    int accel = DDF_ACCEL_BVH;
+    float4* bvh = nullptr;
+    int32_t* bvh_tri = nullptr;
+    int64_t bvh_nodes = 0;
+    int bvh_depth = 0;
 };
 
 namespace ddf {
@@ -158,7 +164,9 @@ int render_aov(ddf_net_s* net, const ddf_camera* cam, float* depth, float* norma
 int mesh_render_aov(ddf_mesh_s* m, const ddf_camera* cam, float* depth, float* normal, int32_t* tri,
                     cudaStream_t stream);
 
-// ------------------------------------------------------------------ labelling (label.cu)
+// ------------------------------------------------------------------ labelling (label.cu, bvh.cu)
+constexpr int kBvhMaxDepth = 56;   // the traversal stack holds one entry per level
+int bvh_build(ddf_mesh_s* m, const float* host_verts, const int32_t* host_tris);
 int mesh_prepare(ddf_mesh_s* m, const float* host_verts, const int32_t* host_tris);
 // parity (optional): the parity of the number of faces each ray crosses at t > 0.
 int label_rays(ddf_mesh_s* m, const float* o, const float* w, int64_t n, float* dist,

@@ -85,7 +85,8 @@ __device__ __forceinline__ void exact_best(RayState& st, const float* V, const i
     }
 }
 
-// Offer a float64-confirmed hit (index k > every index seen before, float64 t = t64).
+// Offer a float64-confirmed hit (triangle k, float64 t = t64). Equal t goes to the lower index,
+// so the result does not depend on the order triangles are offered in.
 __device__ __forceinline__ void offer_exact(RayState& st, int k, double t64, const float* V,
                                             const int32_t* F, const float o[3], const float w[3]) {
     if (st.bi < 0) {
@@ -100,7 +101,7 @@ __device__ __forceinline__ void offer_exact(RayState& st, int k, double t64, con
         if (t64 > (double)st.bhi) return;
         exact_best(st, V, F, o, w);
     }
-    if (t64 < st.bt64) set_exact(st, k, t64);   // equal t keeps the lower index
+    if (t64 < st.bt64 || (t64 == st.bt64 && k < st.bi)) set_exact(st, k, t64);
 }
 
 // Rare path: a pair the hot filter could not reject. Returns whether the float64 test hits (a
@@ -314,6 +315,139 @@ __global__ void __launch_bounds__(kThreads) label_kernel(
     if ((threadIdx.x & 31) == 0 && (re | fi)) {
         atomicAdd(stats, re);
         atomicAdd(stats + 1, fi);
+    }
+}
+
+// ------------------------------------------------------------------ BVH traversal
+// The same labels through the hierarchy of bvh.cu: one ray per thread, a stack of (node, entry
+// distance) pairs, every face of every leaf whose box the ray meets classified by candidate()
+// (FP32 filter, FP64 resolution), so the result is the same float64 argmin over all faces (ties
+// to the lower index, whatever the visiting order). The slab test accepts tmin <= tmax (1 + 2^-20),
+// which covers its float32 rounding (each slab distance is within ~2.4e-7 relative of the exact
+// one), and a child is skipped only if tmin (1 - 2^-20) exceeds the upper bound of the best hit so
+// far, so no face that could win or tie is dropped. PARITY prunes nothing and counts every hit.
+constexpr int kBvhThreads = 128;
+constexpr float kSlabSlack = 1.f / 1048576.f;
+
+__device__ __forceinline__ bool slab(float lx, float ly, float lz, float hx, float hy, float hz, const float o[3],
+                                     const float inv[3], float* tnear) {
+    const float ax = (lx - o[0]) * inv[0], bx = (hx - o[0]) * inv[0];
+    const float ay = (ly - o[1]) * inv[1], by = (hy - o[1]) * inv[1];
+    const float az = (lz - o[2]) * inv[2], bz = (hz - o[2]) * inv[2];
+    const float tmin = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), 0.f));
+    const float tmax = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fmaxf(az, bz));
+    *tnear = tmin;
+    return tmin <= tmax * (1.f + kSlabSlack);
+}
+
+template <bool PARITY>
+__global__ void __launch_bounds__(kBvhThreads) bvh_label_kernel(
+    const float4* __restrict__ nodes, const int32_t* __restrict__ btri, const float4* __restrict__ hot,
+    const float4* __restrict__ aux, const float* __restrict__ V, const int32_t* __restrict__ F,
+    const float* __restrict__ O, const float* __restrict__ Wd, int64_t n, float* __restrict__ dist,
+    uint8_t* __restrict__ hit, int32_t* __restrict__ tri, uint8_t* __restrict__ parity,
+    unsigned long long* __restrict__ stats) {
+    const int64_t i = (int64_t)blockIdx.x * kBvhThreads + threadIdx.x;
+    const bool valid = i < n;
+    float o[3], w[3], inv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        o[c] = valid ? O[3 * i + c] : 0.f;
+        w[c] = valid ? Wd[3 * i + c] : 1.f;
+        // a zero component becomes +-1e-30: the slab then spans everything when the origin is
+        // inside it and starts beyond 1e21 when it is not
+        inv[c] = 1.f / (fabsf(w[c]) > 1e-30f ? w[c] : copysignf(1e-30f, w[c]));
+    }
+    RayState st;
+    st.bi = -1; st.blo = INFINITY; st.bhi = INFINITY; st.bexact = false;
+    st.bt64 = 0.0; st.retests = 0; st.finals = 0;
+    unsigned crossings = 0, visits = 0, tests = 0;
+    int stk[kBvhMaxDepth + 2];
+    float stt[kBvhMaxDepth + 2];
+    int sp = 0, node = 0;
+    auto leaf = [&](int ref, int cnt) {
+        const int first = -(ref + 1);
+        tests += (unsigned)cnt;
+        for (int j = 0; j < cnt; ++j) {
+            const int k = btri[first + j];
+            const bool h = candidate(st, k, hot[3 * k], hot[3 * k + 1], hot[3 * k + 2], aux, V, F, o, w);
+            if (PARITY) crossings += h ? 1u : 0u;
+        }
+    };
+    while (valid) {
+        ++visits;
+        const float4 a = nodes[4 * node], b = nodes[4 * node + 1], c = nodes[4 * node + 2];
+        const int4 d = *reinterpret_cast<const int4*>(&nodes[4 * node + 3]);
+        float tl, tr;
+        bool hl = slab(a.x, a.y, a.z, a.w, b.x, b.y, o, inv, &tl);
+        bool hr = slab(b.z, b.w, c.x, c.y, c.z, c.w, o, inv, &tr);
+        if (!PARITY && st.bi >= 0) {
+            hl = hl && !(tl * (1.f - kSlabSlack) > st.bhi);
+            hr = hr && !(tr * (1.f - kSlabSlack) > st.bhi);
+        }
+        if (hl && d.x < 0) {
+            leaf(d.x, d.z);
+            hl = false;
+        }
+        if (hr && d.y < 0) {
+            leaf(d.y, d.w);
+            hr = false;
+        }
+        if (hl && hr) {
+            const bool lfirst = tl <= tr;
+            stk[sp] = lfirst ? d.y : d.x;
+            stt[sp] = lfirst ? tr : tl;
+            ++sp;
+            node = lfirst ? d.x : d.y;
+            continue;
+        }
+        if (hl) {
+            node = d.x;
+            continue;
+        }
+        if (hr) {
+            node = d.y;
+            continue;
+        }
+        // pop the next node still worth visiting
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            if (!PARITY && st.bi >= 0 && stt[sp] * (1.f - kSlabSlack) > st.bhi) continue;
+            node = stk[sp];
+            found = true;
+            break;
+        }
+        if (!found) break;
+    }
+    if (valid) {
+        if (st.bi >= 0) {
+            if (!st.bexact) {
+                double t;
+                mt64(V, F, st.bi, o, w, &t);
+                st.bt64 = t;
+                st.finals++;
+            }
+            dist[i] = __double2float_rn(st.bt64);
+            hit[i] = 1;
+            if (tri) tri[i] = st.bi;
+        } else {
+            dist[i] = INFINITY;
+            hit[i] = 0;
+            if (tri) tri[i] = -1;
+        }
+        if (PARITY) parity[i] = (uint8_t)(crossings & 1u);
+    }
+    // warp-aggregated statistics: re-tests, final evaluations, node visits, face tests
+    unsigned long long cnt[4] = {st.retests, st.finals, visits, tests};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) cnt[k] += __shfl_down_sync(0xffffffffu, cnt[k], off);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (cnt[k]) atomicAdd(stats + k, cnt[k]);
     }
 }
 
@@ -718,19 +852,31 @@ int mesh_prepare(ddf_mesh_s* m, const float* hv, const int32_t* ht) {
     }
     DDF_CUDA_TRY(cudaMalloc(&m->tri_hot, sizeof(float4) * std::max<int64_t>(1, nt * 3)));
     DDF_CUDA_TRY(cudaMalloc(&m->tri_aux, sizeof(float4) * std::max<int64_t>(1, nt * 2)));
-    DDF_CUDA_TRY(cudaMalloc(&m->stats, sizeof(unsigned long long) * 2));
+    DDF_CUDA_TRY(cudaMalloc(&m->stats, sizeof(unsigned long long) * 4));
     if (nt > 0) {
         DDF_CUDA_TRY(cudaMemcpy(m->tri_hot, hot.data(), sizeof(float4) * nt * 3, cudaMemcpyHostToDevice));
         DDF_CUDA_TRY(cudaMemcpy(m->tri_aux, aux.data(), sizeof(float4) * nt * 2, cudaMemcpyHostToDevice));
     }
-    DDF_CUDA_TRY(cudaMemset(m->stats, 0, sizeof(unsigned long long) * 2));
+    DDF_CUDA_TRY(cudaMemset(m->stats, 0, sizeof(unsigned long long) * 4));
     return DDF_OK;
 }
 
 int label_rays(ddf_mesh_s* m, const float* o, const float* w, int64_t n, float* dist,
                uint8_t* hit, int32_t* tri, cudaStream_t stream, uint8_t* parity) {
-    DDF_CUDA_TRY(cudaMemsetAsync(m->stats, 0, sizeof(unsigned long long) * 2, stream));
+    DDF_CUDA_TRY(cudaMemsetAsync(m->stats, 0, sizeof(unsigned long long) * 4, stream));
     m->last_stream = stream;
+    if (m->accel == DDF_ACCEL_BVH && m->bvh) {
+        const int64_t blocks = (n + kBvhThreads - 1) / kBvhThreads;
+        if (blocks > 0x7fffffff) return fail(DDF_ERR_INVALID_ARG, "too many rays");
+        if (parity)
+            bvh_label_kernel<true><<<(unsigned)blocks, kBvhThreads, 0, stream>>>(
+                m->bvh, m->bvh_tri, m->tri_hot, m->tri_aux, m->verts, m->tris, o, w, n, dist, hit, tri, parity, m->stats);
+        else
+            bvh_label_kernel<false><<<(unsigned)blocks, kBvhThreads, 0, stream>>>(
+                m->bvh, m->bvh_tri, m->tri_hot, m->tri_aux, m->verts, m->tris, o, w, n, dist, hit, tri, nullptr, m->stats);
+        DDF_LAUNCH_CHECK();
+        return DDF_OK;
+    }
     const int64_t per_block = (int64_t)kThreads * RPT;
     const int64_t blocks = (n + per_block - 1) / per_block;
     if (blocks > 0x7fffffff) return fail(DDF_ERR_INVALID_ARG, "too many rays");

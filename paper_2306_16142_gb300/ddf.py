@@ -212,7 +212,9 @@ class DDFNet:
 class DDFMesh:
     """A triangle mesh prepared for ray labelling."""
 
-    def __init__(self, verts, tris):
+    ACCEL = {"none": _abi.DDF_ACCEL_NONE, "bvh": _abi.DDF_ACCEL_BVH}
+
+    def __init__(self, verts, tris, accel: str = "bvh"):
         v = np.ascontiguousarray(np.asarray(verts, np.float32))
         t = np.ascontiguousarray(np.asarray(tris, np.int32))
         h = C.c_void_p()
@@ -221,6 +223,13 @@ class DDFMesh:
                                                              C.byref(h)))
         self.h = h
         self.nt = t.shape[0]
+        self.set_accel(accel)
+
+    def set_accel(self, accel: str):
+        """Face search of every labelling call: "bvh" (hierarchy) or "none" (all faces); the labels
+        are the same either way (ddf_mesh_set_accel)."""
+        check("ddf_mesh_set_accel", _abi.load().ddf_mesh_set_accel(self.h, self.ACCEL[accel]))
+        self.accel = accel
 
     def close(self):
         if getattr(self, "h", None):
@@ -246,6 +255,12 @@ class DDFMesh:
         arr = (C.c_int64 * 2)()
         check("ddf_label_stats", _abi.load().ddf_label_stats(self.h, arr))
         return {"retests": arr[0], "finals": arr[1]}
+
+    def bvh_stats(self):
+        """Hierarchy size and depth, and the node visits and face tests of the last labelling call."""
+        arr = (C.c_int64 * 4)()
+        check("ddf_mesh_bvh_stats", _abi.load().ddf_mesh_bvh_stats(self.h, arr))
+        return {"nodes": arr[0], "depth": arr[1], "visits": arr[2], "face_tests": arr[3]}
 
     def render_aov(self, cam):
         """Depth, normal and hit-face maps of the camera's pixel rays cast against the mesh

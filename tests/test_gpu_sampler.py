@@ -36,11 +36,12 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("accel", ["bvh", "none"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_sampler_matches_oracle_bit_for_bit(P, name):
+def test_sampler_matches_oracle_bit_for_bit(P, name, accel):
     make, (s_fc, s_dr, s_p, eps, seed) = CASES[name]
     V, T = make()
-    mesh = P.DDFMesh(V, T)
+    mesh = P.DDFMesh(V, T, accel)
     g = mesh.sample_surface(s_fc, s_dr, s_p, eps, seed)
     torch.cuda.synchronize()
     r = S.sample_surface(V, T, s_fc, s_dr, s_p, eps, seed)
