@@ -365,60 +365,65 @@ __global__ void __launch_bounds__(kBvhThreads) bvh_label_kernel(
     int stk[kBvhMaxDepth + 2];
     float stt[kBvhMaxDepth + 2];
     int sp = 0, node = 0;
-    auto leaf = [&](int ref, int cnt) {
-        const int first = -(ref + 1);
-        tests += (unsigned)cnt;
-        for (int j = 0; j < cnt; ++j) {
-            const int k = btri[first + j];
-            const bool h = candidate(st, k, hot[3 * k], hot[3 * k + 1], hot[3 * k + 2], aux, V, F, o, w);
-            if (PARITY) crossings += h ? 1u : 0u;
+    // Two phases per round so that the warp classifies faces together: each lane walks inner
+    // nodes until it holds a pending leaf (or has nothing left), then every lane with a pending
+    // leaf runs candidate() on its faces at the same point of the program.
+    int pend_ref[2], pend_cnt[2];
+    bool alive = valid;
+    while (__any_sync(0xffffffffu, alive)) {
+        int npend = 0;
+        while (alive && npend == 0) {
+            if (node < 0) {   // pop the next node still worth visiting
+                while (sp > 0) {
+                    --sp;
+                    if (!PARITY && st.bi >= 0 && stt[sp] * (1.f - kSlabSlack) > st.bhi) continue;
+                    node = stk[sp];
+                    break;
+                }
+                if (node < 0) {
+                    alive = false;
+                    break;
+                }
+            }
+            ++visits;
+            const float4 a = nodes[4 * node], b = nodes[4 * node + 1], c = nodes[4 * node + 2];
+            const int4 d = *reinterpret_cast<const int4*>(&nodes[4 * node + 3]);
+            float tl, tr;
+            bool hl = slab(a.x, a.y, a.z, a.w, b.x, b.y, o, inv, &tl);
+            bool hr = slab(b.z, b.w, c.x, c.y, c.z, c.w, o, inv, &tr);
+            if (!PARITY && st.bi >= 0) {
+                hl = hl && !(tl * (1.f - kSlabSlack) > st.bhi);
+                hr = hr && !(tr * (1.f - kSlabSlack) > st.bhi);
+            }
+            if (hl && d.x < 0) {
+                pend_ref[npend] = d.x;
+                pend_cnt[npend++] = d.z;
+                hl = false;
+            }
+            if (hr && d.y < 0) {
+                pend_ref[npend] = d.y;
+                pend_cnt[npend++] = d.w;
+                hr = false;
+            }
+            if (hl && hr) {
+                const bool lfirst = tl <= tr;
+                stk[sp] = lfirst ? d.y : d.x;
+                stt[sp] = lfirst ? tr : tl;
+                ++sp;
+                node = lfirst ? d.x : d.y;
+            } else {
+                node = hl ? d.x : (hr ? d.y : -1);
+            }
         }
-    };
-    while (valid) {
-        ++visits;
-        const float4 a = nodes[4 * node], b = nodes[4 * node + 1], c = nodes[4 * node + 2];
-        const int4 d = *reinterpret_cast<const int4*>(&nodes[4 * node + 3]);
-        float tl, tr;
-        bool hl = slab(a.x, a.y, a.z, a.w, b.x, b.y, o, inv, &tl);
-        bool hr = slab(b.z, b.w, c.x, c.y, c.z, c.w, o, inv, &tr);
-        if (!PARITY && st.bi >= 0) {
-            hl = hl && !(tl * (1.f - kSlabSlack) > st.bhi);
-            hr = hr && !(tr * (1.f - kSlabSlack) > st.bhi);
+        for (int p = 0; p < npend; ++p) {
+            const int first = -(pend_ref[p] + 1), cnt = pend_cnt[p];
+            tests += (unsigned)cnt;
+            for (int j = 0; j < cnt; ++j) {
+                const int k = btri[first + j];
+                const bool h = candidate(st, k, hot[3 * k], hot[3 * k + 1], hot[3 * k + 2], aux, V, F, o, w);
+                if (PARITY) crossings += h ? 1u : 0u;
+            }
         }
-        if (hl && d.x < 0) {
-            leaf(d.x, d.z);
-            hl = false;
-        }
-        if (hr && d.y < 0) {
-            leaf(d.y, d.w);
-            hr = false;
-        }
-        if (hl && hr) {
-            const bool lfirst = tl <= tr;
-            stk[sp] = lfirst ? d.y : d.x;
-            stt[sp] = lfirst ? tr : tl;
-            ++sp;
-            node = lfirst ? d.x : d.y;
-            continue;
-        }
-        if (hl) {
-            node = d.x;
-            continue;
-        }
-        if (hr) {
-            node = d.y;
-            continue;
-        }
-        // pop the next node still worth visiting
-        bool found = false;
-        while (sp > 0) {
-            --sp;
-            if (!PARITY && st.bi >= 0 && stt[sp] * (1.f - kSlabSlack) > st.bhi) continue;
-            node = stk[sp];
-            found = true;
-            break;
-        }
-        if (!found) break;
     }
     if (valid) {
         if (st.bi >= 0) {
