@@ -16,6 +16,7 @@ from .rays import (
     surface_aimed_rays,
     labelled_ray_set,
     sample_surface_points,
+    fibonacci_directions,
 )
 from .weights import ddf_arch_sizes, init_weights, split_weights
 from .scenes import default_camera, CameraSpec

@@ -98,3 +98,14 @@ def labelled_ray_set(verts, tris, n: int, seed: int, sigma: float = 0.05):
     w = np.concatenate([w1, w2])
     perm = np.random.default_rng(seed + 2).permutation(n)
     return np.ascontiguousarray(o[perm]), np.ascontiguousarray(w[perm])
+
+
+def fibonacci_directions(k: int) -> np.ndarray:
+    """k unit directions spread over the sphere (spherical Fibonacci lattice: z uniform in
+    (-1, 1), azimuth advancing by the golden angle), float32 (k, 3)."""
+    i = np.arange(k, dtype=np.float64)
+    z = 1.0 - (2.0 * i + 1.0) / k
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = i * np.pi * (3.0 - np.sqrt(5.0))
+    d = np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+    return (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
