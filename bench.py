@@ -199,7 +199,7 @@ def main():
     ap.add_argument("--no-rows", action="store_true", help="skip the labelling / training / grouped rows")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: 512 x 512 x 8 spp (2^21 paths) for profiler captures")
-    ap.add_argument("--row", default=None, choices=["label", "sampler", "pov", "aov", "train", "grouped", "w512"],
+    ap.add_argument("--row", default=None, choices=["label", "sampler", "pov", "aov", "udf", "train", "grouped", "w512"],
                     help="run only this row's workload (for profiler captures) and print it")
     args = ap.parse_args()
     if args.size == "small":
@@ -528,6 +528,28 @@ def other_rows(P, torch, np, peaks, only=None):
                                    "hierarchy, and against all faces)",
                        "field_ms": secA * 1e3, "field_rays_per_s": npx / secA, "mesh_ms": mesh_ms}
         del netA
+    # ---- the UDF of Eq. 4: the minimum over 256 directions for 65,536 points
+    if want("udf"):
+        from ddf_synth import fibonacci_directions
+        w_ = WORKLOAD
+        netU = P.DDFNet(w_["in_freqs"], w_["hidden"], w_["layers"],
+                        init_weights(w_["in_freqs"], w_["hidden"], w_["layers"], seed=w_["seed"]), "bf16")
+        gU = torch.Generator(device="cuda").manual_seed(17)
+        pts = torch.randn(65536, 3, device="cuda", generator=gU)
+        pts = pts / pts.norm(dim=1, keepdim=True) * torch.rand(65536, 1, device="cuda", generator=gU)
+        dirsU = torch.from_numpy(fibonacci_directions(256)).cuda()
+        secU = _time(torch, lambda: netU.udf(pts, dirsU), 3)
+        q = 65536 * 256
+        fq = 2.0 * ((6 + 6 * w_["in_freqs"]) * w_["hidden"] + (w_["layers"] - 1) * w_["hidden"] ** 2 + 2 * w_["hidden"])
+        peak = peaks["bf16_tflops_sustained"]
+        rows["udf"] = {"workload": "UDF (Eq. 4) of 65,536 points in the unit ball over 256 Fibonacci directions "
+                                   "(16.8M queries), BF16 78 -> 256 x 8 -> 2",
+                       "points_per_s": 65536 / secU, "queries_per_s": q / secU, "ms": secU * 1e3,
+                       "roofline": {"bound": "tensor", "achieved": fq * q / secU / 1e12, "peak": peak,
+                                    "unit": "TFLOP/s", "frac": fq * q / secU / 1e12 / peak,
+                                    "note": "the forward flops of the queries over the whole call (ray build, "
+                                            "min reduction and allocation included)"}}
+        del netU
     # ---- a9 training step: BF16 tensor-core GEMMs (FP32 accumulate, FP32 masters), and the FP32 path
     if want("train"):
         Fq, Wd, Ld = 12, 256, 8

@@ -262,6 +262,15 @@ DDF_API int ddf_group_autotune(ddf_group group, const int64_t* d_offsets, const 
  * and c = 1 (width 256); zeros mean absent / default. */
 DDF_API int ddf_group_config(ddf_group group, int* host_out6);
 
+/* The unsigned distance field of Eq. 4 over a direction set: for every point x_i (DEVICE n x 3),
+ * d_udf[i] = the minimum of the distance output over the directions theta_k (DEVICE n_dirs x 3,
+ * unit vectors) whose ray (x_i, theta_k) hits (logit > 0), +inf if none does; d_arg (DEVICE n,
+ * nullable) = that k (the lowest on equal distances, -1 if none). The rows are queried in the
+ * handle's precision without normals, in chunks of at most 2^22 point-direction rows.
+ * Synchronous (frees its buffers). Errors: INVALID_ARG (NULL, n < 0, n_dirs < 1), OOM, CUDA. */
+DDF_API int ddf_udf(ddf_net net, const float* d_points, int64_t n, const float* d_dirs, int32_t n_dirs, float* d_udf,
+                    int32_t* d_arg, cudaStream_t stream);
+
 /* ---- renderer --------------------------------------------------------------------------- */
 
 /* The modified uni-directional path tracer (Sec. 1, Fig. 1) as a wavefront loop on the

@@ -352,6 +352,15 @@ int ddf_mesh_render_aov(ddf_mesh mesh, const ddf_camera* cam, float* d_depth, fl
     return mesh_render_aov(mesh, cam, d_depth, d_normal, d_tri, stream);
 }
 
+int ddf_udf(ddf_net net, const float* d_points, int64_t n, const float* d_dirs, int32_t n_dirs, float* d_udf,
+            int32_t* d_arg, cudaStream_t stream) {
+    if (!net) return fail(DDF_ERR_INVALID_ARG, "net is NULL");
+    if (n < 0 || n_dirs < 1) return fail(DDF_ERR_INVALID_ARG, "n must be >= 0 and n_dirs >= 1");
+    if (n == 0) return DDF_OK;
+    if (!d_points || !d_dirs || !d_udf) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    return udf(net, d_points, n, d_dirs, n_dirs, d_udf, d_arg, stream);
+}
+
 int ddf_render_stats(ddf_net net, int64_t* host_counts, int max_bounces) {
     if (!net || !host_counts || max_bounces <= 0) return fail(DDF_ERR_INVALID_ARG, "bad argument");
     for (int b = 0; b < max_bounces; ++b) host_counts[b] = 0;

@@ -179,6 +179,11 @@ int sample_surface(ddf_mesh_s* m, int s_fc, int s_dr, int s_p, float eps, uint64
 int sample_pov(ddf_mesh_s* m, int n_az, int n_pol, int res, float dist, float tan_half_fov, float* d_o, float* d_w,
                float* d_dist, uint8_t* d_hit, cudaStream_t stream);
 
+// ------------------------------------------------------------------ UDF (udf.cu)
+// Eq. 4 over a direction set: out[i] = min over k with a hit of dist(x_i, theta_k), arg[i] = k.
+int udf(ddf_net_s* net, const float* pts, int64_t np, const float* dirs, int nd, float* out, int32_t* arg,
+        cudaStream_t s);
+
 // ------------------------------------------------------------------ heads (head.cu)
 bool head_single(const ddf_net_s* net);
 // Derive output row 1 from row 0 of `blob` (a blob-layout array) for a single-output head.

@@ -156,6 +156,19 @@ class DDFNet:
         check("ddf_render_aov", _abi.load().ddf_render_aov(self.h, C.byref(c), _ptr(depth), _ptr(normal), _stream()))
         return depth, normal
 
+    def udf(self, points: torch.Tensor, dirs: torch.Tensor, with_arg: bool = False):
+        """Eq. 4 over a direction set (ddf_udf): the minimum distance over the directions whose ray
+        hits, per point (inf if none); with_arg also returns the minimising direction index."""
+        if points.dtype != torch.float32 or points.dim() != 2 or points.shape[1] != 3 or dirs.dim() != 2 \
+                or dirs.shape[1] != 3 or dirs.dtype != torch.float32:
+            raise ValueError("points and dirs must be float32 (n, 3) tensors")
+        n = points.shape[0]
+        out = torch.empty(n, device=points.device)
+        arg = torch.empty(n, dtype=torch.int32, device=points.device) if with_arg else None
+        check("ddf_udf", _abi.load().ddf_udf(self.h, _ptr(points), n, _ptr(dirs), dirs.shape[0], _ptr(out), _ptr(arg),
+                                             _stream()))
+        return (out, arg) if with_arg else out
+
     def render_stats(self, bounces: int):
         arr = (C.c_int64 * bounces)()
         check("ddf_render_stats", _abi.load().ddf_render_stats(self.h, arr, bounces))
