@@ -199,7 +199,8 @@ def main():
     ap.add_argument("--no-rows", action="store_true", help="skip the labelling / training / grouped rows")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: 512 x 512 x 8 spp (2^21 paths) for profiler captures")
-    ap.add_argument("--row", default=None, choices=["label", "sampler", "pov", "aov", "udf", "train", "grouped", "w512"],
+    ap.add_argument("--row", default=None, choices=["label", "sampler", "pov", "aov", "udf", "mesh_render", "train",
+                                                   "grouped", "w512"],
                     help="run only this row's workload (for profiler captures) and print it")
     args = ap.parse_args()
     if args.size == "small":
@@ -528,6 +529,18 @@ def other_rows(P, torch, np, peaks, only=None):
                                    "hierarchy, and against all faces)",
                        "field_ms": secA * 1e3, "field_rays_per_s": npx / secA, "mesh_ms": mesh_ms}
         del netA
+    # ---- the path tracer with the mesh in place of the field (Fig. 5's "without DDF"), same render
+    if want("mesh_render"):
+        w_ = WORKLOAD
+        camM = default_camera(w_["width"], w_["height"], seed=1)
+        imgM = torch.empty(w_["height"], w_["width"], device="cuda")
+        secM = _time(torch, lambda: mesh.render(camM, w_["spp"], w_["bounces"], imgM), 3)
+        nS = w_["width"] * w_["height"] * w_["spp"]
+        rows["mesh_render"] = {"workload": f"{w_['width']} x {w_['height']} x {w_['spp']} spp, <= {w_['bounces']} bounces "
+                                           "(the headline render) with the 8,192-triangle knot cast through the BVH "
+                                           "in place of the field",
+                               "samples_per_s": nS / secM, "ms": secM * 1e3,
+                               "note": "allocation of the wavefront buffers included (the call is synchronous)"}
     # ---- the UDF of Eq. 4: the minimum over 256 directions for 65,536 points
     if want("udf"):
         from ddf_synth import fibonacci_directions

@@ -300,6 +300,14 @@ DDF_API int ddf_render_aov(ddf_net net, const ddf_camera* cam, float* d_depth, f
 DDF_API int ddf_mesh_render_aov(ddf_mesh mesh, const ddf_camera* cam, float* d_depth, float* d_normal, int32_t* d_tri,
                                 cudaStream_t stream);
 
+/* The path tracer of ddf_render with the mesh in place of the field (the "without DDF" renderer
+ * of Fig. 5): every bounce casts the live paths through the labeller (ddf_mesh_set_accel) and
+ * shades with the hit face's normal turned against the ray; camera, jitter, Lambertian bounce,
+ * albedo, environment and output are those of ddf_render. Synchronous (allocates and frees its
+ * wavefront buffers). Errors as ddf_render. */
+DDF_API int ddf_mesh_render(ddf_mesh mesh, const ddf_camera* cam, int spp, int bounces, float* d_image,
+                            cudaStream_t stream);
+
 /* Number of field queries issued per bounce by the last ddf_render on this handle
  * (counts[b-1] for b = 1..bounces; HOST array of max_bounces entries). Synchronises with
  * the stream of that render. */

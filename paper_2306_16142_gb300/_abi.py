@@ -101,6 +101,7 @@ _SIG = {
     "ddf_render_aov": (C.c_int, [_P, C.POINTER(ddf_camera), _P, _P, _P]),
     "ddf_udf": (C.c_int, [_P, _P, _I64, _P, C.c_int32, _P, _P, _P]),
     "ddf_mesh_render_aov": (C.c_int, [_P, C.POINTER(ddf_camera), _P, _P, _P, _P]),
+    "ddf_mesh_render": (C.c_int, [_P, C.POINTER(ddf_camera), C.c_int, C.c_int, _P, _P]),
     "ddf_get_arch": (C.c_int, [_P, C.POINTER(ddf_arch)]),
     "ddf_get_weight_norm": (C.c_int, [_P, _P, C.c_size_t, _P, C.c_size_t, _P]),
     "ddf_label_stats": (C.c_int, [_P, C.POINTER(_I64)]),

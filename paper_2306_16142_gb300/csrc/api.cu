@@ -337,6 +337,18 @@ int check_aov_camera(const ddf_camera* cam) {
 }
 }  // namespace
 
+int ddf_mesh_render(ddf_mesh mesh, const ddf_camera* cam, int spp, int bounces, float* d_image,
+                    cudaStream_t stream) {
+    if (!mesh || !cam || !d_image) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    if (cam->width <= 0 || cam->height <= 0 || (int64_t)cam->width * cam->height > (int64_t(1) << 31))
+        return fail(DDF_ERR_INVALID_ARG, "bad image size %d x %d", cam->width, cam->height);
+    if (spp <= 0 || spp > (1 << 20)) return fail(DDF_ERR_INVALID_ARG, "spp must be in [1, 2^20]");
+    if (bounces < 1 || bounces > 63) return fail(DDF_ERR_INVALID_ARG, "bounces must be in [1, 63]");
+    if (!(cam->vfov_deg > 0.f && cam->vfov_deg < 180.f))
+        return fail(DDF_ERR_INVALID_ARG, "vfov must be in (0, 180)");
+    return mesh_render(mesh, cam, spp, bounces, d_image, stream);
+}
+
 int ddf_render_aov(ddf_net net, const ddf_camera* cam, float* d_depth, float* d_normal, cudaStream_t stream) {
     if (!net || !cam || !d_depth || !d_normal) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
     int rc = check_aov_camera(cam);

@@ -163,14 +163,18 @@ int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* i
 int render_aov(ddf_net_s* net, const ddf_camera* cam, float* depth, float* normal, cudaStream_t stream);
 int mesh_render_aov(ddf_mesh_s* m, const ddf_camera* cam, float* depth, float* normal, int32_t* tri,
                     cudaStream_t stream);
+// The same path tracer with the mesh (cast through the labeller) in place of the field.
+int mesh_render(ddf_mesh_s* m, const ddf_camera* cam, int spp, int bounces, float* image, cudaStream_t stream);
 
 // ------------------------------------------------------------------ labelling (label.cu, bvh.cu)
 constexpr int kBvhMaxDepth = 56;   // the traversal stack holds one entry per level
 int bvh_build(ddf_mesh_s* m, const float* host_verts, const int32_t* host_tris);
 int mesh_prepare(ddf_mesh_s* m, const float* host_verts, const int32_t* host_tris);
 // parity (optional): the parity of the number of faces each ray crosses at t > 0.
+// d_count (optional, device): label rows [0, min(n, *d_count)) only.
 int label_rays(ddf_mesh_s* m, const float* o, const float* w, int64_t n, float* dist,
-               uint8_t* hit, int32_t* tri, cudaStream_t stream, uint8_t* parity = nullptr);
+               uint8_t* hit, int32_t* tri, cudaStream_t stream, uint8_t* parity = nullptr,
+               const int* d_count = nullptr);
 // The surface-marching sampler of Sec. 5.2 (ddf_sample_surface).
 int sample_surface(ddf_mesh_s* m, int s_fc, int s_dr, int s_p, float eps, uint64_t seed, float* d_o, float* d_w,
                    float* d_dist, uint8_t* d_hit, int64_t* d_key, int64_t cap, int64_t* host_count,

@@ -201,8 +201,10 @@ __global__ void __launch_bounds__(kThreads) label_kernel(
     const float4* __restrict__ hot, const float4* __restrict__ aux, const float* __restrict__ V,
     const int32_t* __restrict__ F, int64_t nt, const float* __restrict__ O,
     const float* __restrict__ Wd, int64_t n, float* __restrict__ dist, uint8_t* __restrict__ hit,
-    int32_t* __restrict__ tri, uint8_t* __restrict__ parity, unsigned long long* __restrict__ stats) {
+    int32_t* __restrict__ tri, uint8_t* __restrict__ parity, unsigned long long* __restrict__ stats,
+    const int* __restrict__ d_count) {
     __shared__ float4 tile[2][TT * 3];
+    if (d_count) n = min(n, (int64_t)*d_count);   // rows [0, *d_count) only
     float o[RPT][3], w[RPT][3], So[RPT];
     bool valid[RPT];
     unsigned crossings[RPT] = {};
@@ -346,8 +348,9 @@ __global__ void __launch_bounds__(kBvhThreads) bvh_label_kernel(
     const float4* __restrict__ aux, const float* __restrict__ V, const int32_t* __restrict__ F,
     const float* __restrict__ O, const float* __restrict__ Wd, int64_t n, float* __restrict__ dist,
     uint8_t* __restrict__ hit, int32_t* __restrict__ tri, uint8_t* __restrict__ parity,
-    unsigned long long* __restrict__ stats) {
+    unsigned long long* __restrict__ stats, const int* __restrict__ d_count) {
     const int64_t i = (int64_t)blockIdx.x * kBvhThreads + threadIdx.x;
+    if (d_count) n = min(n, (int64_t)*d_count);   // rows [0, *d_count) only
     const bool valid = i < n;
     float o[3], w[3], inv[3];
 #pragma unroll
@@ -867,7 +870,7 @@ int mesh_prepare(ddf_mesh_s* m, const float* hv, const int32_t* ht) {
 }
 
 int label_rays(ddf_mesh_s* m, const float* o, const float* w, int64_t n, float* dist,
-               uint8_t* hit, int32_t* tri, cudaStream_t stream, uint8_t* parity) {
+               uint8_t* hit, int32_t* tri, cudaStream_t stream, uint8_t* parity, const int* d_count) {
     DDF_CUDA_TRY(cudaMemsetAsync(m->stats, 0, sizeof(unsigned long long) * 4, stream));
     m->last_stream = stream;
     if (m->accel == DDF_ACCEL_BVH && m->bvh) {
@@ -875,10 +878,12 @@ int label_rays(ddf_mesh_s* m, const float* o, const float* w, int64_t n, float* 
         if (blocks > 0x7fffffff) return fail(DDF_ERR_INVALID_ARG, "too many rays");
         if (parity)
             bvh_label_kernel<true><<<(unsigned)blocks, kBvhThreads, 0, stream>>>(
-                m->bvh, m->bvh_tri, m->tri_hot, m->tri_aux, m->verts, m->tris, o, w, n, dist, hit, tri, parity, m->stats);
+                m->bvh, m->bvh_tri, m->tri_hot, m->tri_aux, m->verts, m->tris, o, w, n, dist, hit, tri, parity, m->stats,
+                d_count);
         else
             bvh_label_kernel<false><<<(unsigned)blocks, kBvhThreads, 0, stream>>>(
-                m->bvh, m->bvh_tri, m->tri_hot, m->tri_aux, m->verts, m->tris, o, w, n, dist, hit, tri, nullptr, m->stats);
+                m->bvh, m->bvh_tri, m->tri_hot, m->tri_aux, m->verts, m->tris, o, w, n, dist, hit, tri, nullptr, m->stats,
+                d_count);
         DDF_LAUNCH_CHECK();
         return DDF_OK;
     }
@@ -887,10 +892,12 @@ int label_rays(ddf_mesh_s* m, const float* o, const float* w, int64_t n, float* 
     if (blocks > 0x7fffffff) return fail(DDF_ERR_INVALID_ARG, "too many rays");
     if (parity)
         label_kernel<true><<<(unsigned)blocks, kThreads, 0, stream>>>(m->tri_hot, m->tri_aux, m->verts, m->tris,
-                                                                      m->nt, o, w, n, dist, hit, tri, parity, m->stats);
+                                                                      m->nt, o, w, n, dist, hit, tri, parity, m->stats,
+                                                                      d_count);
     else
         label_kernel<false><<<(unsigned)blocks, kThreads, 0, stream>>>(m->tri_hot, m->tri_aux, m->verts, m->tris,
-                                                                       m->nt, o, w, n, dist, hit, tri, nullptr, m->stats);
+                                                                       m->nt, o, w, n, dist, hit, tri, nullptr, m->stats,
+                                                                       d_count);
     DDF_LAUNCH_CHECK();
     return DDF_OK;
 }

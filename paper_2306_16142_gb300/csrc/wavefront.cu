@@ -199,30 +199,45 @@ __global__ void camera_rays_kernel(CamDev cam, int64_t npx, float* __restrict__ 
     }
 }
 
-// Unit normal of the hit face, turned towards the viewer (n . w < 0); 0 on a miss.
+// Unit normal of face k turned against the ray direction w (n . w < 0).
+__device__ __forceinline__ void face_normal(const float* __restrict__ V, const int32_t* __restrict__ F, int k,
+                                            const float* w, float* n) {
+    const int i0 = F[3 * k], i1 = F[3 * k + 1], i2 = F[3 * k + 2];
+    const float ax = V[3 * i1] - V[3 * i0], ay = V[3 * i1 + 1] - V[3 * i0 + 1], az = V[3 * i1 + 2] - V[3 * i0 + 2];
+    const float bx = V[3 * i2] - V[3 * i0], by = V[3 * i2 + 1] - V[3 * i0 + 1], bz = V[3 * i2 + 2] - V[3 * i0 + 2];
+    float nx = ay * bz - az * by, ny = az * bx - ax * bz, nz = ax * by - ay * bx;
+    const float len = sqrtf(nx * nx + ny * ny + nz * nz);
+    const float sgn = (nx * w[0] + ny * w[1] + nz * w[2]) > 0.f ? -1.f : 1.f;
+    const float s = len > 0.f ? sgn / len : 0.f;
+    n[0] = nx * s;
+    n[1] = ny * s;
+    n[2] = nz * s;
+}
+
+// Unit normal of the hit face, turned towards the viewer; 0 on a miss.
 __global__ void face_normal_kernel(const float* __restrict__ V, const int32_t* __restrict__ F,
                                    const float* __restrict__ w, const int32_t* __restrict__ tri, int64_t n,
                                    float* __restrict__ normal) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
         const int k = tri[p];
-        float nx = 0.f, ny = 0.f, nz = 0.f;
-        if (k >= 0) {
-            const int i0 = F[3 * k], i1 = F[3 * k + 1], i2 = F[3 * k + 2];
-            const float ax = V[3 * i1] - V[3 * i0], ay = V[3 * i1 + 1] - V[3 * i0 + 1], az = V[3 * i1 + 2] - V[3 * i0 + 2];
-            const float bx = V[3 * i2] - V[3 * i0], by = V[3 * i2 + 1] - V[3 * i0 + 1], bz = V[3 * i2 + 2] - V[3 * i0 + 2];
-            nx = ay * bz - az * by;
-            ny = az * bx - ax * bz;
-            nz = ax * by - ay * bx;
-            const float len = sqrtf(nx * nx + ny * ny + nz * nz);
-            const float sgn = (nx * w[3 * p] + ny * w[3 * p + 1] + nz * w[3 * p + 2]) > 0.f ? -1.f : 1.f;
-            const float s = len > 0.f ? sgn / len : 0.f;
-            nx *= s;
-            ny *= s;
-            nz *= s;
-        }
-        normal[3 * p] = nx;
-        normal[3 * p + 1] = ny;
-        normal[3 * p + 2] = nz;
+        float nv[3] = {0.f, 0.f, 0.f};
+        if (k >= 0) face_normal(V, F, k, w + 3 * p, nv);
+        normal[3 * p] = nv[0];
+        normal[3 * p + 1] = nv[1];
+        normal[3 * p + 2] = nv[2];
+    }
+}
+
+// The mesh in place of the field for one bounce of the path tracer: logit = +1 on a hit and -1 on
+// a miss (dist is the labelled distance), normal = the hit face's, turned against the ray.
+__global__ void mesh_hit_kernel(const int* __restrict__ count, const float* __restrict__ V,
+                                const int32_t* __restrict__ F, const float* __restrict__ w,
+                                const int32_t* __restrict__ tri, float* __restrict__ logit, float* __restrict__ nrm) {
+    const int n = *count;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int k = tri[i];
+        logit[i] = k >= 0 ? 1.f : -1.f;
+        if (k >= 0) face_normal(V, F, k, w + 3 * i, nrm + 3 * i);
     }
 }
 
@@ -272,19 +287,19 @@ int make_cam(const ddf_camera* cam, CamDev* out) {
     return DDF_OK;
 }
 
-// The handle's grow-only render workspace for waves of wave_paths paths.
-int render_bufs(ddf_net_s* net, int64_t wave_paths, WaveBufs* out) {
+// A grow-only render workspace (*ws, *ws_bytes) for waves of wave_paths paths.
+int render_bufs(void** ws, size_t* ws_bytes, int64_t wave_paths, WaveBufs* out) {
     const size_t fvec = align256(sizeof(float) * 3 * wave_paths);
     const size_t fsc = align256(sizeof(float) * wave_paths);
     const size_t need = 2 * (2 * fvec + 2 * fsc) + fsc * 3 + fvec + align256(sizeof(int) * 64);
-    if (net->render_ws_bytes < need) {
-        if (net->render_ws) cudaFree(net->render_ws);
-        net->render_ws = nullptr;
-        net->render_ws_bytes = 0;
-        DDF_CUDA_TRY(cudaMalloc(&net->render_ws, need));
-        net->render_ws_bytes = need;
+    if (*ws_bytes < need) {
+        if (*ws) cudaFree(*ws);
+        *ws = nullptr;
+        *ws_bytes = 0;
+        DDF_CUDA_TRY(cudaMalloc(ws, need));
+        *ws_bytes = need;
     }
-    char* p = (char*)net->render_ws;
+    char* p = (char*)*ws;
     WaveBufs& B = *out;
     for (int k = 0; k < 2; ++k) {
         B.o[k] = (float*)p; p += fvec;
@@ -308,7 +323,7 @@ int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* i
     const int64_t px_per_wave = std::max<int64_t>(1, std::min<int64_t>(npix, kWaveMax / spp));
     const int64_t wave_paths = px_per_wave * spp;
     WaveBufs B;
-    int rc0 = render_bufs(net, wave_paths, &B);
+    int rc0 = render_bufs(&net->render_ws, &net->render_ws_bytes, wave_paths, &B);
     if (rc0) return rc0;
     if (net->render_counts_len < bounces) {
         if (net->render_counts) cudaFree(net->render_counts);
@@ -364,7 +379,7 @@ int render_aov(ddf_net_s* net, const ddf_camera* cam, float* depth, float* norma
     const int64_t npix = (int64_t)cam->width * cam->height;
     const int64_t px_per_wave = std::min<int64_t>(npix, kWaveMax);
     WaveBufs B;
-    int rc = render_bufs(net, px_per_wave, &B);
+    int rc = render_bufs(&net->render_ws, &net->render_ws_bytes, px_per_wave, &B);
     if (rc) return rc;
     CamDev cd;
     if ((rc = make_cam(cam, &cd))) return rc;
@@ -412,6 +427,57 @@ int mesh_render_aov(ddf_mesh_s* m, const ddf_camera* cam, float* depth, float* n
     cudaFree(ws);
     if (rc) return rc;
     if (e != cudaSuccess) return fail(DDF_ERR_CUDA, "mesh AOV render: %s", cudaGetErrorString(e));
+    return DDF_OK;
+}
+
+int mesh_render(ddf_mesh_s* m, const ddf_camera* cam, int spp, int bounces, float* image, cudaStream_t stream) {
+    const int64_t npix = (int64_t)cam->width * cam->height;
+    const int64_t px_per_wave = std::max<int64_t>(1, std::min<int64_t>(npix, kWaveMax / spp));
+    const int64_t wave_paths = px_per_wave * spp;
+    CamDev cd;
+    int rc = make_cam(cam, &cd);
+    if (rc) return rc;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    WaveBufs B;
+    if ((rc = render_bufs(&ws, &ws_bytes, wave_paths, &B))) return rc;
+    uint8_t* hitb = nullptr;
+    int32_t* trib = nullptr;
+    cudaError_t e = cudaMalloc(&hitb, wave_paths);
+    if (e == cudaSuccess) e = cudaMalloc(&trib, sizeof(int32_t) * wave_paths);
+    const int grid = num_sms() * 4;
+    for (int64_t px0 = 0; px0 < npix && e == cudaSuccess && !rc; px0 += px_per_wave) {
+        const int64_t npx = std::min(px_per_wave, npix - px0);
+        const int64_t npaths = npx * spp;
+        const int64_t pid0 = px0 * spp;
+        e = cudaMemsetAsync(B.counts, 0, sizeof(int) * (bounces + 1), stream);
+        if (e != cudaSuccess) break;
+        const int rg = (int)std::min<int64_t>((npaths + kThreads - 1) / kThreads, grid);
+        raygen_kernel<<<rg, kThreads, 0, stream>>>(cd, spp, pid0, npaths, B.o[0], B.w[0], B.lid[0], B.thr[0],
+                                                   B.radiance, B.counts);
+        for (int b = 1; b <= bounces && !rc; ++b) {
+            const int s = (b - 1) & 1;
+            // the mesh in place of the field query: nearest hit through the labeller, face normal
+            rc = label_rays(m, B.o[s], B.w[s], npaths, B.dist, hitb, trib, stream, nullptr, B.counts + (b - 1));
+            if (rc) break;
+            mesh_hit_kernel<<<grid, kThreads, 0, stream>>>(B.counts + (b - 1), m->verts, m->tris, B.w[s], trib, B.logit,
+                                                           B.nrm);
+            shade_kernel<<<grid, kThreads, 0, stream>>>(cd, pid0, b, bounces, B.counts + (b - 1), B.o[s], B.w[s],
+                                                        B.lid[s], B.thr[s], B.dist, B.logit, B.nrm, B.o[s ^ 1],
+                                                        B.w[s ^ 1], B.lid[s ^ 1], B.thr[s ^ 1], B.radiance,
+                                                        B.counts + b);
+        }
+        accumulate_kernel<<<grid, kThreads, 0, stream>>>(B.radiance, spp, px0, npx, image);
+        e = cudaGetLastError();
+    }
+    // the buffers are freed once the kernels that use them are done
+    cudaError_t e2 = cudaStreamSynchronize(stream);
+    cudaFree(hitb);
+    cudaFree(trib);
+    cudaFree(ws);
+    if (rc) return rc;
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return fail(DDF_ERR_CUDA, "mesh render: %s", cudaGetErrorString(e));
     return DDF_OK;
 }
 

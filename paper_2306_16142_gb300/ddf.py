@@ -275,6 +275,15 @@ class DDFMesh:
         check("ddf_mesh_bvh_stats", _abi.load().ddf_mesh_bvh_stats(self.h, arr))
         return {"nodes": arr[0], "depth": arr[1], "visits": arr[2], "face_tests": arr[3]}
 
+    def render(self, cam, spp: int, bounces: int, image: torch.Tensor | None = None):
+        """The path tracer with the mesh in place of the field (ddf_mesh_render)."""
+        c = camera_struct(cam)
+        if image is None:
+            image = torch.empty(cam.height, cam.width, device="cuda")
+        check("ddf_mesh_render", _abi.load().ddf_mesh_render(self.h, C.byref(c), spp, bounces, _ptr(image),
+                                                             _stream()))
+        return image
+
     def render_aov(self, cam):
         """Depth, normal and hit-face maps of the camera's pixel rays cast against the mesh
         (ddf_mesh_render_aov)."""
