@@ -343,7 +343,7 @@ __device__ __forceinline__ bool slab(float lx, float ly, float lz, float hx, flo
 }
 
 template <bool PARITY>
-__global__ void __launch_bounds__(kBvhThreads) bvh_label_kernel(
+__global__ void __launch_bounds__(kBvhThreads, PARITY ? 6 : 8) bvh_label_kernel(
     const float4* __restrict__ nodes, const int32_t* __restrict__ btri, const float4* __restrict__ hot,
     const float4* __restrict__ aux, const float* __restrict__ V, const int32_t* __restrict__ F,
     const float* __restrict__ O, const float* __restrict__ Wd, int64_t n, float* __restrict__ dist,
