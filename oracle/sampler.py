@@ -284,3 +284,43 @@ def sample_pov(verts, tris, n_az: int = 10, n_pol: int = 5, res: int = 64, dist:
     o, w = pov_rays(n_az, n_pol, res, dist, tan_half_fov)
     d, h, _, _ = label_rays(verts, tris, o, w)
     return {"o": o, "w": w, "dist": d, "hit": h}
+
+
+# --------------------------------------------------------------------------- random sampling
+# The "random" baseline of Sec. 6 (Fig. 7): points and directions picked at random, each ray shot
+# into the mesh and its t stored.
+#
+# Readings: the points are uniform in the bounding box of the field's domain, the cube [-1, 1]^3
+# around the unit ball; the directions are uniform on the sphere. Ray i draws Philox counter
+# (i, 0, 4, 0) for the point (words 0, 1, 2 -> x, y, z = 2u - 1, exact in float32) and counter
+# (i, 0, 5, 0) for the direction (words 0, 1: z = 1 - 2 u0, exact; azimuth 2 pi u1; the planar
+# radius sqrt(1 - z^2) in float64, where 1 - z^2 is exact, sines and cosines from ``sincospi``;
+# each coordinate rounded to float32 once). The label is the nearest hit of ``oracle.label``.
+
+
+def _words(seed: int, idx: np.ndarray, stream: int) -> np.ndarray:
+    """The four Philox words of counter (idx lo, idx hi, stream, 0) as u = (w >> 8) 2^-24, float64."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    ctr = np.stack([idx & MASK, idx >> np.uint64(32), np.full_like(idx, stream), np.zeros_like(idx)], axis=1)
+    key = np.array([seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], dtype=np.uint64)
+    return (philox4x32_10(ctr, key) >> np.uint32(8)).astype(np.float64) * 2.0 ** -24
+
+
+def random_rays(n: int, seed: int):
+    """n float32 rays: origins uniform in [-1, 1]^3, unit directions uniform on the sphere."""
+    idx = np.arange(n, dtype=np.uint64)
+    up = _words(seed, idx, 4)
+    o = (2.0 * up[:, :3] - 1.0).astype(np.float32)
+    ud = _words(seed, idx, 5)
+    z = 1.0 - 2.0 * ud[:, 0]
+    r = np.sqrt(1.0 - z * z)
+    s, c = sincospi(2.0 * ud[:, 1])
+    w = np.stack([(r * c).astype(np.float32), (r * s).astype(np.float32), z.astype(np.float32)], axis=1)
+    return o, w
+
+
+def sample_random(verts, tris, n: int, seed: int):
+    """Random samples: dict o, w (n, 3) float32, dist (n,) float32 (inf on a miss), hit (n,) uint8."""
+    o, w = random_rays(n, seed)
+    d, h, _, _ = label_rays(verts, tris, o, w)
+    return {"o": o, "w": w, "dist": d, "hit": h}

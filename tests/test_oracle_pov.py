@@ -1,8 +1,9 @@
-"""Pins of the POV sampling oracle (Sec. 6, the "pov" baseline of Fig. 7) against facts that hold
-independently of it: the camera placement against numpy's trigonometry, an orthonormal
-right-handed frame, every ray through its pixel centre and starting on the unit sphere, the
-centre pixel aimed at the origin, and the labels of an axis-aligned cube against the slab method
-(a closed form that shares nothing with Moeller-Trumbore)."""
+"""Pins of the POV and random sampling oracles (Sec. 6, the "pov" and "random" baselines of
+Fig. 7) against facts that hold independently of them: the camera placement against numpy's
+trigonometry, an orthonormal right-handed frame, every ray through its pixel centre and starting
+on the unit sphere, the centre pixel aimed at the origin, the random rays' moments and
+uniformity, and the labels of an axis-aligned cube against the slab method (a closed form that
+shares nothing with Moeller-Trumbore)."""
 
 import numpy as np
 
@@ -97,3 +98,47 @@ def test_cube_labels_match_the_slab_method():
     h = keep & hit
     assert np.abs(r["dist"][h] - tn[h]).max() < 1e-6 * (1 + tn[h].max())
     assert np.isinf(r["dist"][keep & ~hit]).all()
+
+
+def test_random_rays_are_uniform_in_the_box_and_on_the_sphere():
+    """The random baseline of Sec. 6: origins fill [-1, 1]^3 uniformly (each coordinate's mean 0,
+    variance 1/3, independent), directions are unit and uniform on the sphere (every coordinate's
+    mean 0 and second moment 1/3; z and the azimuth each uniform)."""
+    n = 200000
+    o, w = S.random_rays(n, seed=3)
+    assert o.dtype == np.float32 and w.dtype == np.float32
+    assert (np.abs(o) <= 1).all()
+    assert np.abs(o.mean(0)).max() < 0.01 and np.abs(o.var(0) - 1 / 3).max() < 0.01
+    assert np.abs(np.corrcoef(o.T.astype(np.float64))[np.triu_indices(3, 1)]).max() < 0.01
+    w64 = w.astype(np.float64)
+    assert np.abs(np.linalg.norm(w64, axis=1) - 1).max() < 1e-6
+    assert np.abs(w64.mean(0)).max() < 0.01 and np.abs((w64 ** 2).mean(0) - 1 / 3).max() < 0.01
+    hz, _ = np.histogram(w64[:, 2], bins=20, range=(-1, 1))
+    ha, _ = np.histogram(np.arctan2(w64[:, 1], w64[:, 0]), bins=20, range=(-np.pi, np.pi))
+    for h in (hz, ha):
+        assert np.abs(h / (n / 20) - 1).max() < 0.05
+    # the same seed gives the same rays, another seed others
+    o2, w2 = S.random_rays(1000, seed=3)
+    assert np.array_equal(o2, o[:1000]) and np.array_equal(w2, w[:1000])
+    assert not np.array_equal(S.random_rays(1000, seed=4)[0], o2)
+
+
+def test_random_samples_on_a_box_match_the_slab_method():
+    V, F = _box(0.5)
+    r = S.sample_random(V, F, 20000, seed=7)
+    o, w = r["o"].astype(np.float64), r["w"].astype(np.float64)
+    A = float(np.float32(0.5))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t1, t2 = (-A - o) / w, (A - o) / w
+    tn = np.max(np.minimum(t1, t2), axis=1)
+    tf = np.min(np.maximum(t1, t2), axis=1)
+    inside = np.all(np.abs(o) < A, axis=1)
+    t = np.where(inside, tf, tn)                     # from inside the box the exit face is hit
+    hit = (tn <= tf) & (tf > 0)
+    p = o + t[:, None] * w
+    edge = np.sum(np.abs(np.abs(p) - A) < 1e-5, axis=1) >= 2
+    keep = ~edge & (np.abs(tn - tf) > 1e-5)
+    assert keep.mean() > 0.97 and 0.2 < hit.mean() < 0.9
+    assert np.array_equal(r["hit"][keep].astype(bool), hit[keep])
+    h = keep & hit
+    assert np.abs(r["dist"][h] - t[h]).max() < 1e-6 * (1 + t[h].max())
