@@ -417,6 +417,17 @@ typedef struct ddf_pov {
 DDF_API int ddf_sample_pov(ddf_mesh mesh, const ddf_pov* params, float* d_origins, float* d_dirs, float* d_dist,
                            uint8_t* d_hit, cudaStream_t stream);
 
+/* The random training set of a mesh (the "random" sampling of Sec. 6): n rays with origins uniform
+ * in [-1, 1]^3 (the bounding box of the unit-ball domain) and directions uniform on the sphere,
+ * labelled as by ddf_label_rays. Ray i draws Philox4x32-10 (key = seed) counter (i, 0, 4, 0) for
+ * its origin (x, y, z = 2u - 1 from words 0-2, u = (word >> 8) 2^-24) and (i, 0, 5, 0) for its
+ * direction (z = 1 - 2 u0, azimuth 2 pi u1, planar radius sqrt(1 - z^2) in float64); coordinates
+ * are rounded to float32 once, so the rays are a deterministic function of (n, seed). Outputs
+ * (DEVICE, caller-owned, n rows): origins n x 3, dirs n x 3, dist n (+inf on a miss), hit n.
+ * Asynchronous on stream; allocates nothing. Errors: INVALID_ARG (NULL, n < 0), CUDA. */
+DDF_API int ddf_sample_random(ddf_mesh mesh, int64_t n, uint64_t seed, float* d_origins, float* d_dirs, float* d_dist,
+                              uint8_t* d_hit, cudaStream_t stream);
+
 /* ---- training ---------------------------------------------------------------------------- */
 
 /* Reverse pass of the network for output cotangents (g_dist, g_logit) (device, n each):

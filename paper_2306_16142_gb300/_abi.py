@@ -95,6 +95,7 @@ _SIG = {
     "ddf_label_rays": (C.c_int, [_P, _P, _P, _I64, _P, _P, _P, _P]),
     "ddf_sample_surface": (C.c_int, [_P, C.POINTER(ddf_sampler), _P, _P, _P, _P, _P, _I64, C.POINTER(_I64), _P]),
     "ddf_sample_pov": (C.c_int, [_P, C.POINTER(ddf_pov), _P, _P, _P, _P, _P]),
+    "ddf_sample_random": (C.c_int, [_P, _I64, C.c_uint64, _P, _P, _P, _P, _P]),
     "ddf_set_head": (C.c_int, [_P, C.POINTER(ddf_head), _P]),
     "ddf_mesh_set_accel": (C.c_int, [_P, C.c_int]),
     "ddf_mesh_bvh_stats": (C.c_int, [_P, C.POINTER(_I64)]),

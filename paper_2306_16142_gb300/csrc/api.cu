@@ -488,6 +488,14 @@ int ddf_sample_surface(ddf_mesh mesh, const ddf_sampler* params, float* d_origin
                           d_dist, d_hit, d_key, cap, host_count, stream);
 }
 
+int ddf_sample_random(ddf_mesh mesh, int64_t n, uint64_t seed, float* d_origins, float* d_dirs, float* d_dist,
+                      uint8_t* d_hit, cudaStream_t stream) {
+    if (!mesh) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    if (n < 0 || n > (int64_t(1) << 31)) return fail(DDF_ERR_INVALID_ARG, "n must be in [0, 2^31]");
+    if (n > 0 && (!d_origins || !d_dirs || !d_dist || !d_hit)) return fail(DDF_ERR_INVALID_ARG, "NULL output");
+    return sample_random(mesh, n, seed, d_origins, d_dirs, d_dist, d_hit, stream);
+}
+
 int ddf_sample_pov(ddf_mesh mesh, const ddf_pov* params, float* d_origins, float* d_dirs, float* d_dist,
                    uint8_t* d_hit, cudaStream_t stream) {
     if (!mesh || !params) return fail(DDF_ERR_INVALID_ARG, "NULL argument");

@@ -179,6 +179,9 @@ int label_rays(ddf_mesh_s* m, const float* o, const float* w, int64_t n, float* 
 int sample_surface(ddf_mesh_s* m, int s_fc, int s_dr, int s_p, float eps, uint64_t seed, float* d_o, float* d_w,
                    float* d_dist, uint8_t* d_hit, int64_t* d_key, int64_t cap, int64_t* host_count,
                    cudaStream_t stream);
+// The random-sampling baseline of Sec. 6 (ddf_sample_random).
+int sample_random(ddf_mesh_s* m, int64_t n, uint64_t seed, float* d_o, float* d_w, float* d_dist, uint8_t* d_hit,
+                  cudaStream_t stream);
 // The point-of-view sampling of Sec. 6 (ddf_sample_pov).
 int sample_pov(ddf_mesh_s* m, int n_az, int n_pol, int res, float dist, float tan_half_fov, float* d_o, float* d_w,
                float* d_dist, uint8_t* d_hit, cudaStream_t stream);

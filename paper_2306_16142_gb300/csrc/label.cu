@@ -801,6 +801,34 @@ __global__ void pov_rays_kernel(PovArgs pa, float* __restrict__ o, float* __rest
     }
 }
 
+// ------------------------------------------------------------------ random sampling
+// The "random" baseline of Sec. 6: ray i's origin uniform in [-1, 1]^3 (Philox counter (i, 0, 4, 0),
+// 2u - 1 exact in float32) and its direction uniform on the sphere (counter (i, 0, 5, 0):
+// z = 1 - 2 u0 exact, radius sqrt(1 - z^2) in float64 with 1 - z^2 exact, azimuth 2 pi u1 through
+// the series; each coordinate rounded to float32 once).
+struct RandArgs {
+    int64_t n;
+    uint2 key;
+    SinCosCoef coef;
+};
+
+__global__ void random_rays_kernel(RandArgs ra, float* __restrict__ o, float* __restrict__ w) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ra.n) return;
+    const uint4 p = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), 4u, 0u), ra.key);
+    o[3 * i] = __double2float_rn(__dsub_rn(__dmul_rn(2.0, (double)u24(p.x)), 1.0));
+    o[3 * i + 1] = __double2float_rn(__dsub_rn(__dmul_rn(2.0, (double)u24(p.y)), 1.0));
+    o[3 * i + 2] = __double2float_rn(__dsub_rn(__dmul_rn(2.0, (double)u24(p.z)), 1.0));
+    const uint4 d = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), 5u, 0u), ra.key);
+    const double z = __dsub_rn(1.0, __dmul_rn(2.0, (double)u24(d.x)));
+    const double r = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(z, z)));
+    double s, c;
+    sincospi_series(__dmul_rn(2.0, (double)u24(d.y)), ra.coef, &s, &c);
+    w[3 * i] = __double2float_rn(__dmul_rn(r, c));
+    w[3 * i + 1] = __double2float_rn(__dmul_rn(r, s));
+    w[3 * i + 2] = __double2float_rn(z);
+}
+
 // Exclusive chunk offsets of the set flags of fl[0 .. n) into dev_offs (nblk entries, through the
 // host); returns the total in *total. Synchronises the stream.
 cudaError_t scan_flags(const uint8_t* fl, int64_t n, int64_t* dev_offs, std::vector<int64_t>& h, int64_t* total,
@@ -1030,6 +1058,18 @@ int sample_pov(ddf_mesh_s* m, int n_az, int n_pol, int res, float dist, float ta
     pov_rays_kernel<<<(unsigned)((pa.n + 255) / 256), 256, 0, stream>>>(pa, d_o, d_w);
     DDF_LAUNCH_CHECK();
     return label_rays(m, d_o, d_w, pa.n, d_dist, d_hit, nullptr, stream);
+}
+
+int sample_random(ddf_mesh_s* m, int64_t n, uint64_t seed, float* d_o, float* d_w, float* d_dist, uint8_t* d_hit,
+                  cudaStream_t stream) {
+    if (n == 0) return DDF_OK;
+    RandArgs ra{};
+    ra.n = n;
+    ra.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    fill_series(ra.coef);
+    random_rays_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(ra, d_o, d_w);
+    DDF_LAUNCH_CHECK();
+    return label_rays(m, d_o, d_w, n, d_dist, d_hit, nullptr, stream);
 }
 
 }  // namespace ddf

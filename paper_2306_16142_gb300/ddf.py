@@ -326,6 +326,16 @@ class DDFMesh:
         res["count"] = n.value
         return res
 
+    def sample_random(self, n: int, seed: int = 0):
+        """The random training set of Sec. 6 (ddf_sample_random): dict of CUDA tensors o, w (n, 3),
+        dist (n,), hit (n,)."""
+        dev = torch.device("cuda")
+        out = {"o": torch.empty(max(n, 1), 3, device=dev), "w": torch.empty(max(n, 1), 3, device=dev),
+               "dist": torch.empty(max(n, 1), device=dev), "hit": torch.empty(max(n, 1), dtype=torch.uint8, device=dev)}
+        check("ddf_sample_random", _abi.load().ddf_sample_random(
+            self.h, n, seed, _ptr(out["o"]), _ptr(out["w"]), _ptr(out["dist"]), _ptr(out["hit"]), _stream()))
+        return {k: t[:n] for k, t in out.items()}
+
     def sample_pov(self, n_az: int = 10, n_pol: int = 5, res: int = 64, dist: float = 2.5,
                    tan_half_fov: float = 0.2679491924311227, out: dict | None = None):
         """The point-of-view training set of Sec. 6 (ddf_sample_pov): dict of CUDA tensors o

@@ -121,3 +121,15 @@ def test_pov_rejects_bad_arguments(P):
         with pytest.raises(P.DDFError):
             mesh.sample_pov(**kw)
     assert mesh.sample_pov(n_az=0)["o"].shape[0] == 0
+
+
+@pytest.mark.parametrize("name,n,seed", [("icosphere", 20000, 3), ("knot", 5000, 8), ("box", 7777, 1)])
+def test_random_matches_oracle_bit_for_bit(P, name, n, seed):
+    V, T = {"icosphere": lambda: icosphere(2, 0.5), "knot": lambda: torus_knot(3, 2, 0.08, 64, 8),
+            "box": lambda: _box(0.4)}[name]()
+    g = P.DDFMesh(V, T).sample_random(n, seed)
+    torch.cuda.synchronize()
+    r = S.sample_random(V, T, n, seed)
+    for k in ("o", "w", "dist", "hit"):
+        assert np.array_equal(g[k].cpu().numpy(), r[k]), k
+    assert 0.05 < r["hit"].mean() < 0.95
