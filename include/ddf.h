@@ -181,7 +181,9 @@ typedef struct ddf_head {
  * weight_norm = 1 (Sec. 5.1) trains v and g per output row of every hidden layer. Switching it
  * on sets v = W and g = the row norms; the FP32 masters (ddf_get_weights) then hold the folded
  * g v / |v|, recomputed after every update. ddf_set_weights sets v and g again from the new
- * weights (clearing g's Adam moments). Changing weight_norm resets the Adam state.
+ * weights (clearing g's Adam moments). Changing weight_norm resets the Adam state. A hidden row
+ * with |v| = 0 has no direction: its fold is 0/0 (NaN), as with torch's weight_norm, so switch
+ * weight normalisation on only for weights without all-zero rows.
  * Ordered on stream. Errors: INVALID_ARG (unknown kind, bad delta, the analytic sphere), OOM,
  * CUDA. */
 DDF_API int ddf_set_head(ddf_net net, const ddf_head* head, cudaStream_t stream);
