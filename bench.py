@@ -115,6 +115,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(torch, ms, world, device="cuda"):
+    """The slowest rank's time: every rank's timed region is bracketed by barriers, so the job takes
+    as long as its slowest rank (an all-reduce MAX over the process group when world > 1)."""
+    if world > 1:
+        t = torch.tensor([float(ms)], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = t.item()
+    return ms
+
+
+def whole_job_rate(units_per_rank_step, world, steps, ms):
+    """Units per second of the whole job: every rank processes units_per_rank_step units per step
+    (weak scaling), in ms milliseconds for `steps` steps (the slowest rank's time)."""
+    return units_per_rank_step * world * steps / (ms / 1e3)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -265,14 +281,11 @@ def main():
     ms = ev0.elapsed_time(ev1)
     prof = net.profile_read()
     net.profile(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(torch, ms, world)
     paths = w["width"] * w["height"] * w["spp"]
-    value = paths * world * args.steps / (ms / 1e3)
+    value = whole_job_rate(paths, world, args.steps, ms)
     queries = sum(stats)
-    queries_per_s = queries * world * args.steps / (ms / 1e3)
+    queries_per_s = whole_job_rate(queries, world, args.steps, ms)
 
     # ---- dominant kernel roofline: the field query
     Wd, Ld = w["hidden"], w["layers"]
