@@ -195,3 +195,26 @@ def mesh_aov(verts, tris, cam):
     fn[facing] = -fn[facing]
     normal[h] = fn
     return d.astype(np.float64), normal, tri, o, w
+
+
+def mesh_query(verts, tris):
+    """The path tracer's query with a mesh in place of the field (the "without DDF" renderer of
+    Fig. 5): the labeller's nearest hit (float32 rays, as the GPU casts them), logit +1 on a hit and
+    -1 on a miss, and the hit face's unit normal turned against the ray."""
+    from .label import label_rays
+    V = np.asarray(verts, np.float32)
+    T = np.asarray(tris, np.int64)
+    Vd = V.astype(np.float64)
+
+    def q(o, w):
+        d, h, tri, _ = label_rays(V, T, np.asarray(o).astype(np.float32), np.asarray(w).astype(np.float32))
+        hit = h == 1
+        n = np.zeros((len(d), 3))
+        k = T[tri[hit]]
+        fn = np.cross(Vd[k[:, 1]] - Vd[k[:, 0]], Vd[k[:, 2]] - Vd[k[:, 0]])
+        fn /= np.linalg.norm(fn, axis=1, keepdims=True)
+        flip = np.sum(fn * np.asarray(w, np.float64)[hit], axis=1) > 0
+        fn[flip] = -fn[flip]
+        n[hit] = fn
+        return {"dist": np.where(hit, d, 0.0).astype(np.float64), "logit": np.where(hit, 1.0, -1.0), "normal": n}
+    return q

@@ -8,7 +8,7 @@ import torch
 
 from ddf_synth import default_camera
 from oracle import mlp as omlp
-from oracle.render import primary_rays, render_pixels
+from oracle.render import mesh_query, primary_rays, render_pixels
 from tests._helpers import LOGIT_MARGIN, NETS, ensure_built, net_weights
 
 pytestmark = pytest.mark.gpu
@@ -78,25 +78,6 @@ def test_render_spp1_per_path_parity(P):
     assert np.allclose(img[ok], ref["image"][ok], rtol=0, atol=1e-6)
 
 
-def _mesh_query(V, T):
-    """The oracle path tracer's query with the mesh in place of the field: the FP64 labeller's
-    nearest hit, logit +-1, the hit face's normal turned against the ray."""
-    from oracle.label import label_rays
-    Vd = V.astype(np.float64)
-
-    def q(o, w):
-        d, h, tri, _ = label_rays(V, T, o.astype(np.float32), w.astype(np.float32))
-        n = np.zeros((o.shape[0], 3))
-        k = tri[h == 1]
-        fn = np.cross(Vd[T[k, 1]] - Vd[T[k, 0]], Vd[T[k, 2]] - Vd[T[k, 0]])
-        fn /= np.linalg.norm(fn, axis=1, keepdims=True)
-        flip = np.sum(fn * w[h == 1], 1) > 0
-        fn[flip] = -fn[flip]
-        n[h == 1] = fn
-        return {"dist": np.where(h == 1, d, 0.0).astype(np.float64), "logit": np.where(h == 1, 1.0, -1.0), "normal": n}
-    return q
-
-
 def test_mesh_render_convex_closed_form(P):
     """A convex mesh: a sample that meets it bounces away for good, so each pixel is
     (0.7 k + (spp - k)) / spp with k its samples that meet the mesh."""
@@ -107,7 +88,7 @@ def test_mesh_render_convex_closed_form(P):
     img = P.DDFMesh(V, T).render(cam, spp, 3).cpu().numpy().ravel()
     kk = np.round((1 - img) / 0.3 * spp)
     assert np.allclose(img, (0.7 * kk + (spp - kk)) / spp, atol=2e-6)
-    ref = render_pixels(_mesh_query(V, T), cam, spp, 3, np.arange(40 * 40))
+    ref = render_pixels(mesh_query(V, T), cam, spp, 3, np.arange(40 * 40))
     same = np.abs(img - ref["image"]) < 1e-6
     print(f"convex mesh: {same.mean():.4f} of pixels equal the oracle")
     assert same.mean() > 0.97 and 0.1 < (kk > 0).mean() < 0.9
@@ -127,7 +108,7 @@ def test_mesh_render_two_spheres_against_the_oracle(P):
     mesh.set_accel("none")
     img2 = mesh.render(cam, spp, bounces).cpu().numpy().ravel()
     assert np.array_equal(img, img2)                      # the same labels either way
-    ref = render_pixels(_mesh_query(V, T), cam, spp, bounces, np.arange(32 * 32))
+    ref = render_pixels(mesh_query(V, T), cam, spp, bounces, np.arange(32 * 32))
     same = np.abs(img - ref["image"]) < 1e-6
     print(f"two spheres: {same.mean():.4f} of pixels equal the oracle, mean |diff| {np.abs(img - ref['image']).mean():.5f}")
     assert same.mean() > 0.9 and np.abs(img - ref["image"]).mean() < 0.02

@@ -132,3 +132,27 @@ def test_bounce_cap_gives_black():
     first_hit = res["logit"] > 0
     assert first_hit.any()
     assert (res["radiance"][first_hit] == 0).all() and (res["radiance"][~first_hit] == 1).all()
+
+
+def test_mesh_tracer_convex_closed_form():
+    """The path tracer with a convex mesh in place of the field (oracle.render.mesh_query): a
+    sample that meets the mesh bounces away for good, so each pixel is (0.7 k + (spp - k)) / spp
+    with k its primary rays that meet the mesh, counted here by an independent ray-sphere
+    bracket: rays missing the circumscribed sphere miss, rays meeting the inscribed one hit."""
+    from ddf_synth import icosphere
+    from oracle.render import mesh_query
+    V, T = icosphere(2, 0.5)
+    cam = default_camera(24, 24, seed=2)
+    spp = 4
+    res = render_pixels(mesh_query(V, T), cam, spp, 3, np.arange(24 * 24))
+    kk = np.round((1 - res["image"]) / 0.3 * spp)
+    assert np.allclose(res["image"], (0.7 * kk + (spp - kk)) / spp, atol=1e-12)
+    o, w, alive = primary_rays(cam, res["pids"], spp)
+    b = np.sum(o * w, 1)
+    r_in = 0.5 * np.cos(np.arctan(1 / 2) / 2) ** 2 * 0.95       # well inside every face
+    def meets(r):
+        disc = b * b - (np.sum(o * o, 1) - r * r)
+        return alive & (disc > 0) & (-b - np.sqrt(np.maximum(disc, 0)) > 0)
+    lo = meets(r_in).reshape(-1, spp).sum(1)
+    hi = meets(0.5 * 1.0001).reshape(-1, spp).sum(1)
+    assert (kk >= lo).all() and (kk <= hi).all() and (kk > 0).mean() > 0.2
