@@ -18,9 +18,12 @@ Modules and the passages they follow:
   Sec. 6 "shot rays and calculated t"): brute-force Moeller-Trumbore over all faces.
 * ``sphere``  - the analytic DDF of a sphere (closed form for the definitions of Sec. 3.1).
 * ``render``  - the modified uni-directional path tracer (Sec. 1, Fig. 1): camera rays,
-  one DDF query per bounce, Lambertian shading with cosine-hemisphere sampling.
+  one DDF query per bounce, Lambertian shading with cosine-hemisphere sampling; the same
+  tracer's query with a mesh in place of the field (Fig. 5's comparison), and the depth and
+  normal images of Fig. 3 / Fig. 4.
+* ``udf``     - the unsigned distance field of Eq. 4 as a minimum over a direction set.
 * ``sampler`` - the surface-marching training-set sampler of Sec. 5.2 (Eqs. 8-12) with the
-  odd-even inside test, and the point-of-view sampling of Sec. 6, built on ``label``.
+  odd-even inside test, and the point-of-view and random sampling of Sec. 6, built on ``label``.
 * ``head``    - the paper's single-output head with the clamp loss of Eq. 7 or the squish
   loss of Eq. 5, and the weight-normalised hidden layers of Sec. 5.1.
 
