@@ -340,6 +340,15 @@ DDF_API int ddf_mesh_destroy(ddf_mesh mesh);
  * way. INVALID_ARG for another value. */
 DDF_API int ddf_mesh_set_accel(ddf_mesh mesh, int accel);
 
+/* Self-check of the hierarchy ddf_mesh_create builds, on the host only (no device call): builds it
+ * for the HOST mesh given and verifies that every face lies in exactly one leaf, every leaf's
+ * padded box holds its faces' vertices, every child box lies inside its parent's, every node is
+ * reached once and the depth is within the traversal stack. host_out[0..3] = nodes, depth,
+ * non-empty leaves, largest leaf. DDF_ERR_NUMERIC names the first violated invariant;
+ * INVALID_ARG for bad arguments or a face index out of range. */
+DDF_API int ddf_bvh_selfcheck(const float* host_verts, int64_t nv, const int32_t* host_tris, int64_t nt,
+                              int64_t* host_out);
+
 /* Ray labelling for training data (Sec. 5; the nearest-triangle search of Sec. 1): for each
  * ray the nearest Moeller-Trumbore hit over all triangles with t > 0, barycentric bounds
  * inclusive, ties to the lowest triangle index (faces searched as ddf_mesh_set_accel says). Outputs (device, n rows): dist = t rounded

@@ -98,6 +98,7 @@ _SIG = {
     "ddf_sample_random": (C.c_int, [_P, _I64, C.c_uint64, _P, _P, _P, _P, _P]),
     "ddf_set_head": (C.c_int, [_P, C.POINTER(ddf_head), _P]),
     "ddf_mesh_set_accel": (C.c_int, [_P, C.c_int]),
+    "ddf_bvh_selfcheck": (C.c_int, [_P, _I64, _P, _I64, C.POINTER(_I64)]),
     "ddf_mesh_bvh_stats": (C.c_int, [_P, C.POINTER(_I64)]),
     "ddf_render_aov": (C.c_int, [_P, C.POINTER(ddf_camera), _P, _P, _P]),
     "ddf_udf": (C.c_int, [_P, _P, _I64, _P, C.c_int32, _P, _P, _P]),

@@ -456,6 +456,15 @@ int ddf_mesh_destroy(ddf_mesh m) {
     return DDF_OK;
 }
 
+int ddf_bvh_selfcheck(const float* host_verts, int64_t nv, const int32_t* host_tris, int64_t nt, int64_t* host_out) {
+    if (!host_verts || !host_tris || !host_out || nv <= 0 || nt <= 0 || nt > 0x7fffffff || nv > 0x7fffffff)
+        return fail(DDF_ERR_INVALID_ARG, "bad mesh arguments");
+    for (int64_t i = 0; i < 3 * nt; ++i)
+        if (host_tris[i] < 0 || host_tris[i] >= nv)
+            return fail(DDF_ERR_INVALID_ARG, "face %lld references vertex %d", (long long)(i / 3), host_tris[i]);
+    return bvh_check_host(host_verts, nv, host_tris, nt, host_out);
+}
+
 int ddf_mesh_set_accel(ddf_mesh mesh, int accel) {
     if (!mesh) return fail(DDF_ERR_INVALID_ARG, "mesh is NULL");
     if (accel != DDF_ACCEL_NONE && accel != DDF_ACCEL_BVH) return fail(DDF_ERR_INVALID_ARG, "unknown accel %d", accel);

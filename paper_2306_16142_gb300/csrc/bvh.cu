@@ -169,8 +169,10 @@ void pad_box(const Box& b, float lo[3], float hi[3]) {
 
 }  // namespace
 
-int bvh_build(ddf_mesh_s* m, const float* hv, const int32_t* ht) {
-    const int64_t nt = m->nt;
+// The device image of the hierarchy of a mesh given on the host: 4 float4 per node (see the top of
+// this file), the face order, and the depth. No device call.
+void bvh_build_host(const float* hv, const int32_t* ht, int64_t nt, std::vector<float4>& dev,
+                    std::vector<int32_t>& order, int* depth) {
     Builder B;
     B.tbox.resize(nt);
     B.cen.resize(3 * nt);
@@ -200,7 +202,7 @@ int bvh_build(ddf_mesh_s* m, const float* hv, const int32_t* ht) {
         B.nodes[0].c[1].count = 0;
     }
     const int64_t nn = (int64_t)B.nodes.size();
-    std::vector<float4> dev(4 * nn);
+    dev.assign(4 * nn, make_float4(0.f, 0.f, 0.f, 0.f));
     for (int64_t i = 0; i < nn; ++i) {
         float lo[2][3], hi[2][3];
         int ref[2], cnt[2];
@@ -216,12 +218,92 @@ int bvh_build(ddf_mesh_s* m, const float* hv, const int32_t* ht) {
         int4 d = make_int4(ref[0], ref[1], cnt[0], cnt[1]);
         memcpy(&dev[4 * i + 3], &d, sizeof d);
     }
+    order = std::move(B.idx);
+    *depth = B.max_depth_seen;
+}
+
+int bvh_build(ddf_mesh_s* m, const float* hv, const int32_t* ht) {
+    const int64_t nt = m->nt;
+    std::vector<float4> dev;
+    std::vector<int32_t> order;
+    int depth = 0;
+    bvh_build_host(hv, ht, nt, dev, order, &depth);
+    const int64_t nn = (int64_t)dev.size() / 4;
     DDF_CUDA_TRY(cudaMalloc(&m->bvh, sizeof(float4) * 4 * nn));
     DDF_CUDA_TRY(cudaMalloc(&m->bvh_tri, sizeof(int32_t) * std::max<int64_t>(1, nt)));
     DDF_CUDA_TRY(cudaMemcpy(m->bvh, dev.data(), sizeof(float4) * 4 * nn, cudaMemcpyHostToDevice));
-    DDF_CUDA_TRY(cudaMemcpy(m->bvh_tri, B.idx.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice));
+    DDF_CUDA_TRY(cudaMemcpy(m->bvh_tri, order.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice));
     m->bvh_nodes = nn;
-    m->bvh_depth = B.max_depth_seen;
+    m->bvh_depth = depth;
+    return DDF_OK;
+}
+
+// Host self-check of the hierarchy (no device call): every face in exactly one leaf, every padded
+// leaf box holding its faces' vertices, every child box inside its parent's, every inner node
+// reached once, depth within kBvhMaxDepth. out: nodes, depth, leaves, largest leaf.
+int bvh_check_host(const float* hv, int64_t nv, const int32_t* ht, int64_t nt, int64_t out[4]) {
+    std::vector<float4> dev;
+    std::vector<int32_t> order;
+    int depth = 0;
+    bvh_build_host(hv, ht, nt, dev, order, &depth);
+    const int64_t nn = (int64_t)dev.size() / 4;
+    if ((int64_t)order.size() != nt || depth > kBvhMaxDepth) return fail(DDF_ERR_NUMERIC, "hierarchy shape");
+    std::vector<int> seen_face(nt, 0), seen_node(nn, 0);
+    int64_t leaves = 0, largest = 0;
+    // (node, parent box) pairs; the root's box is unbounded
+    struct Item { int node; float lo[3], hi[3]; };
+    std::vector<Item> stack;
+    Item root{0, {-INFINITY, -INFINITY, -INFINITY}, {INFINITY, INFINITY, INFINITY}};
+    stack.push_back(root);
+    while (!stack.empty()) {
+        const Item it = stack.back();
+        stack.pop_back();
+        if (it.node < 0 || it.node >= nn || seen_node[it.node]++) return fail(DDF_ERR_NUMERIC, "node %d", it.node);
+        const float4 a = dev[4 * it.node], b = dev[4 * it.node + 1], c = dev[4 * it.node + 2];
+        int4 d;
+        memcpy(&d, &dev[4 * it.node + 3], sizeof d);
+        const float lo[2][3] = {{a.x, a.y, a.z}, {b.z, b.w, c.x}};
+        const float hi[2][3] = {{a.w, b.x, b.y}, {c.y, c.z, c.w}};
+        const int ref[2] = {d.x, d.y}, cnt[2] = {d.z, d.w};
+        for (int s = 0; s < 2; ++s) {
+            const bool empty = ref[s] < 0 && cnt[s] == 0;
+            if (!empty)
+                for (int k = 0; k < 3; ++k)
+                    if (!(lo[s][k] >= it.lo[k] && hi[s][k] <= it.hi[k] && lo[s][k] <= hi[s][k]))
+                        return fail(DDF_ERR_NUMERIC, "child box of node %d outside its parent", it.node);
+            if (ref[s] >= 0) {
+                Item ch{ref[s], {lo[s][0], lo[s][1], lo[s][2]}, {hi[s][0], hi[s][1], hi[s][2]}};
+                stack.push_back(ch);
+                continue;
+            }
+            const int64_t first = -(int64_t)(ref[s] + 1);
+            if (cnt[s] < 0 || first + cnt[s] > nt) return fail(DDF_ERR_NUMERIC, "leaf range");
+            if (cnt[s] > 0) {
+                ++leaves;
+                largest = std::max<int64_t>(largest, cnt[s]);
+            }
+            for (int j = 0; j < cnt[s]; ++j) {
+                const int f = order[first + j];
+                if (f < 0 || f >= nt || seen_face[f]++) return fail(DDF_ERR_NUMERIC, "face %d placed twice", f);
+                for (int v = 0; v < 3; ++v) {
+                    const int32_t vi = ht[3 * (int64_t)f + v];
+                    if (vi < 0 || vi >= nv) return fail(DDF_ERR_INVALID_ARG, "face %d references vertex %d", f, vi);
+                    for (int k = 0; k < 3; ++k) {
+                        const float x = hv[3 * (int64_t)vi + k];
+                        if (!(x >= lo[s][k] && x <= hi[s][k])) return fail(DDF_ERR_NUMERIC, "face %d outside its leaf", f);
+                    }
+                }
+            }
+        }
+    }
+    for (int64_t f = 0; f < nt; ++f)
+        if (seen_face[f] != 1) return fail(DDF_ERR_NUMERIC, "face %lld in no leaf", (long long)f);
+    for (int64_t i = 0; i < nn; ++i)
+        if (seen_node[i] != 1) return fail(DDF_ERR_NUMERIC, "node %lld unreachable", (long long)i);
+    out[0] = nn;
+    out[1] = depth;
+    out[2] = leaves;
+    out[3] = largest;
     return DDF_OK;
 }
 

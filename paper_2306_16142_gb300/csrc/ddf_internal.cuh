@@ -169,6 +169,8 @@ int mesh_render(ddf_mesh_s* m, const ddf_camera* cam, int spp, int bounces, floa
 // ------------------------------------------------------------------ labelling (label.cu, bvh.cu)
 constexpr int kBvhMaxDepth = 56;   // the traversal stack holds one entry per level
 int bvh_build(ddf_mesh_s* m, const float* host_verts, const int32_t* host_tris);
+// Host-only build and invariant check (ddf_bvh_selfcheck).
+int bvh_check_host(const float* hv, int64_t nv, const int32_t* ht, int64_t nt, int64_t out[4]);
 int mesh_prepare(ddf_mesh_s* m, const float* host_verts, const int32_t* host_tris);
 // parity (optional): the parity of the number of faces each ray crosses at t > 0.
 // d_count (optional, device): label rows [0, min(n, *d_count)) only.
