@@ -25,7 +25,7 @@ pytestmark = pytest.mark.gpu
 
 EXACT_REL = 1e-5
 # Statistical bound against the BF16 model on random weights: both round every activation and
-# delta to BF16 (reading R13 of Sec. 5.1's training), but they sum the bias and the products in
+# delta to BF16 (the tensor-core reading of Sec. 5.1's training), but they sum the bias and the products in
 # different orders, so a pre-activation within rounding of zero may take either ReLU branch and
 # the gradients differ by such mask flips (a few percent in relative L2 at these sizes). The
 # arithmetic itself is pinned by the exact tests above (dyadic values, EXACT_REL).
