@@ -207,7 +207,7 @@ def sample_surface(verts, tris, s_fc: int, s_dr: int, s_p: int, eps: float, seed
 
 
 # --------------------------------------------------------------------------- POV sampling
-# The point-of-view baseline of Sec. 6 (Fig. 7's "pov" curve): cameras spaced uniformly in
+# The point-of-view baseline of Sec. 6 (Fig. 6's "pov" curve): cameras spaced uniformly in
 # azimuth and polar angle around the mesh centre, aimed at it; every pixel's ray is labelled.
 #
 # Readings (the paper gives only the camera counts, 10 x 5):
@@ -287,7 +287,7 @@ def sample_pov(verts, tris, n_az: int = 10, n_pol: int = 5, res: int = 64, dist:
 
 
 # --------------------------------------------------------------------------- random sampling
-# The "random" baseline of Sec. 6 (Fig. 7): points and directions picked at random, each ray shot
+# The "random" baseline of Sec. 6 (Fig. 6): points and directions picked at random, each ray shot
 # into the mesh and its t stored.
 #
 # Readings: the points are uniform in the bounding box of the field's domain, the cube [-1, 1]^3

@@ -1,5 +1,5 @@
 """Pins of the POV and random sampling oracles (Sec. 6, the "pov" and "random" baselines of
-Fig. 7) against facts that hold independently of them: the camera placement against numpy's
+Fig. 6) against facts that hold independently of them: the camera placement against numpy's
 trigonometry, an orthonormal right-handed frame, every ray through its pixel centre and starting
 on the unit sphere, the centre pixel aimed at the origin, the random rays' moments and
 uniformity, and the labels of an axis-aligned cube against the slab method (a closed form that
