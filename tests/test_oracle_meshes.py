@@ -41,3 +41,21 @@ def test_torus_knot(ns, nr, nt):
     assert np.linalg.norm(V.astype(np.float64), axis=1).max() <= 0.95 + 1e-6
     vol = _signed_volume(V, F)
     assert vol > 0
+
+
+def test_fibonacci_directions_cover_the_sphere_evenly():
+    """The UDF's default direction set: unit float32 vectors whose every spherical cap of a given
+    area holds about its share (the lattice's discrepancy is small), and whose largest angular gap
+    shrinks like 1 / sqrt(k)."""
+    from ddf_synth import fibonacci_directions
+    for k in (64, 256, 1024):
+        d = fibonacci_directions(k).astype(np.float64)
+        assert d.shape == (k, 3) and np.abs(np.linalg.norm(d, axis=1) - 1).max() < 1e-6
+        assert np.abs(d.mean(0)).max() < 2.0 / k + 1e-3
+        probe = np.random.default_rng(k).normal(size=(4000, 3))
+        probe /= np.linalg.norm(probe, axis=1, keepdims=True)
+        gap = np.arccos(np.clip((probe @ d.T).max(1), -1, 1)).max()
+        assert gap < 3.0 / np.sqrt(k)
+        # caps of half-angle 60 degrees hold a quarter of the sphere
+        frac = ((probe[:50] @ d.T) > 0.5).mean(1)
+        assert np.abs(frac - 0.25).max() < 0.05 + 4.0 / np.sqrt(k)
