@@ -8,6 +8,15 @@
  * gradient of the field with respect to the query point (Eq. 3, Sec. 4.2), it is rendered by a
  * path tracer that replaces the nearest-triangle search with one field query per bounce
  * (Sec. 1, Fig. 1) and it is trained on rays labelled against a triangle mesh (Sec. 5).
+ * Around that path the library also provides:
+ *  - the paper's training-set samplers (surface marching with the odd-even test, Sec. 5.2;
+ *    point-of-view and random sampling, Sec. 6);
+ *  - its single-output head with the clamp / squish losses and weight normalisation (Sec. 4.1,
+ *    Sec. 5.1);
+ *  - depth and normal images (Fig. 3, Fig. 4) and the unsigned distance field (Eq. 4);
+ *  - a mesh path tracer for the DDF-vs-mesh comparison (Fig. 5).
+ * Labelling searches faces through a bounding-volume hierarchy or a sweep over all faces, with
+ * identical results.
  *
  * Conventions shared by every entry point:
  *  - Every function returns an int status: DDF_OK (0) or a negative DDF_ERR_* code. The text of
@@ -17,8 +26,9 @@
  *  - Rays are two row-major (n, 3) float32 arrays: origins o and unit directions w
  *    (normalisation is the caller's job). n is int64_t; n == 0 is a no-op returning DDF_OK.
  *  - Calls are asynchronous and ordered on the given cudaStream_t (0 = legacy default
- *    stream) unless documented as synchronous. All device memory the library allocates
- *    belongs to a handle and is released by the handle's destroy function.
+ *    stream) unless documented as synchronous. Device memory the library keeps belongs to a
+ *    handle and is released by the handle's destroy function. The calls documented as
+ *    synchronous that need scratch space allocate it and free it before they return.
  *  - Handles are not thread-safe: one handle must not be used by two calls at once.
  *
  * Network weights are exchanged as one flat float32 blob
