@@ -158,6 +158,16 @@ DDF_API int ddf_device_status(ddf_net net);
  * Synchronous; allocates one int. */
 DDF_API int ddf_selftest_wait(int limit_ms, int arrive);
 
+/* Measured throughput of the arithmetic units on the current device, at the clocks it runs (no
+ * setting is changed), for the rooflines of kernels that no library routine measures:
+ * host_out[0] FP32 FMA (fma.rn.f32) TFLOP/s, [1] packed FP32x2 FMA (fma.rn.f32x2) TFLOP/s,
+ * [2] FP64 FMA TFLOP/s, [3] BF16 tcgen05.mma (kind::f16, M 128 N 256 K 16, FP32 accumulate)
+ * TFLOP/s, [4] FP8 E4M3 tcgen05.mma (kind::f8f6f4, K 32) TFLOP/s, [5] the SM count, [6] 0 (1 if a
+ * bounded wait gave up). Each figure is one timed launch of register- or shared-memory-resident
+ * loops (one CTA per SM for the tensor cores), after one warm-up launch; about a second in all.
+ * Synchronous; allocates 20 bytes. INVALID_ARG if n_out < 7. */
+DDF_API int ddf_measure_peaks(double* host_out, int n_out);
+
 /* Number of float32 values in the weight blob of this network. */
 DDF_API int ddf_num_params(ddf_net net, int64_t* out);
 
@@ -222,13 +232,16 @@ DDF_API int ddf_query(ddf_net net, const float* d_origins, const float* d_dirs, 
  * while they run (for example an engine whose every allocation goes through its own pool, or
  * a render loop that forbids allocation once started). The paper has no counterpart: it is an
  * interface variant, not a step of the method. Same arguments, outputs and results as
- * ddf_query; it calls no cudaMalloc / cudaFree. The BF16 path's hit-row list, the only scratch
- * a query needs, lives in a fixed static device array of the library (4 MiB + 256 B per GPU
- * that loads the library, held until exit), so n is limited to 2^20 rows; larger n returns
- * DDF_ERR_INVALID_ARG. The first call on each device looks the array's address up once
- * (cudaGetSymbolAddress), so make that first call before any stream capture. Every call on a
- * device shares the array: calls whose work overlaps on the GPU (different streams without
- * ordering between them) race on it and must be serialised by the caller. */
+ * ddf_query, for every precision and width; it calls no cudaMalloc / cudaFree. A tensor-core
+ * (BF16 / FP8) query with normals hands its hit rows from the forward launch to the normal
+ * launch in a list; here that list lives in a fixed static device array of the library
+ * (4 MiB + 256 B per GPU that loads the library, held until exit), so such a query is limited
+ * to n <= 2^20 rows and larger n returns DDF_ERR_INVALID_ARG. Queries without normals, FP32
+ * queries and the analytic sphere use no scratch and take any n. The first call on each device
+ * looks the array's address up once (cudaGetSymbolAddress), so make that first call before any
+ * stream capture. Every call on a device shares the array: calls whose work overlaps on the GPU
+ * (different streams without ordering between them) race on it and must be serialised by the
+ * caller. */
 DDF_API int ddf_query_noalloc(ddf_net net, const float* d_origins, const float* d_dirs, int64_t n,
                               float* d_dist, uint8_t* d_hit, float* d_logit, float* d_normals,
                               cudaStream_t stream);
@@ -296,6 +309,28 @@ DDF_API int ddf_udf(ddf_net net, const float* d_points, int64_t n, const float* 
  * buffers between calls. */
 DDF_API int ddf_render(ddf_net net, const ddf_camera* cam, int spp, int bounces, float* d_image,
                cudaStream_t stream);
+
+/* ddf_render with a record of every bounce of chosen paths, for checking the path tracer step by
+ * step (the renderer of Sec. 1 / Fig. 1 exposes nothing between the camera and the image). The
+ * render itself, d_image included, is exactly that of ddf_render with the same arguments.
+ * d_pids (DEVICE, n_trace distinct path ids pid = (y W + x) spp + s) selects the paths. For
+ * traced path i and bounce b = 1 .. bounces, d_trace (DEVICE, n_trace x bounces x 12 floats) gets
+ * the query of that bounce: [o (3), w (3), dist, logit, normal (3), throughput], where o, w are the
+ * ray the field was queried with, dist and logit its outputs, normal the Eq. 3 normal (NaN on a miss
+ * and at the last bounce, where none is computed) and throughput the path's before the bounce. Bounces the
+ * path did not reach (and ids outside the image) stay NaN. d_radiance (DEVICE, n_trace) gets
+ * each path's radiance, of which the pixel is the mean. Synchronous: allocates a slot map of one
+ * int32 per path of a wave and frees it before returning. Errors as ddf_render, and INVALID_ARG
+ * for NULL buffers with n_trace > 0. */
+DDF_API int ddf_render_trace(ddf_net net, const ddf_camera* cam, int spp, int bounces, float* d_image,
+                             const int64_t* d_pids, int64_t n_trace, float* d_trace, float* d_radiance,
+                             cudaStream_t stream);
+
+/* Paths per wave of ddf_render / ddf_render_trace (1 .. 2^24; default 2^24, at least one pixel's
+ * spp paths per wave). The wavefront buffers hold one wave (about 90 bytes per path), so a smaller
+ * wave caps the handle's render memory; the image does not depend on it, bit for bit (every draw
+ * is keyed by the path id). INVALID_ARG outside the range. */
+DDF_API int ddf_render_set_wave(ddf_net net, int64_t max_paths);
 
 /* Depth and normal maps (the t-value and normal images of Fig. 3 and Fig. 4): one primary ray
  * per pixel (the renderer's camera, its bounce-0 jitter with spp = 1), advanced to the unit ball

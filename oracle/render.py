@@ -88,6 +88,15 @@ def cosine_direction(n, u0, u1):
     return lx[:, None] * b1 + ly[:, None] * b2 + lz[:, None] * n
 
 
+def shade_step(o, w, d, nm, seed, pids, bounce: int, eps: float = 1e-4):
+    """The move of a path that hit at this bounce (Sec. 3.1 and the Lambertian bounce of Fig. 1):
+    hit point q = o + max(d, 0) w, new origin q + eps n, new direction cosine-distributed about n
+    from the path's Philox draws of this bounce. Returns (origin, direction)."""
+    q = o + np.maximum(d, 0.0)[:, None] * w
+    uni = path_uniforms(seed, np.asarray(pids, np.int64).astype(np.uint64), bounce)
+    return q + eps * nm, cosine_direction(nm, uni[:, 0], uni[:, 1])
+
+
 def trace_paths(query_fn, cam, spp: int, bounces: int, pids, eps: float = 1e-4):
     """Trace the given paths. query_fn(o, w) -> dict(dist, logit, normal) in float64.
 
@@ -122,10 +131,7 @@ def trace_paths(query_fn, cam, spp: int, bounces: int, pids, eps: float = 1e-4):
             break
         keep = np.nonzero(hit)[0]
         idx, o, w, d, nm, thr = idx[keep], o[keep], w[keep], d[keep], nm[keep], thr[keep]
-        q = o + np.maximum(d, 0.0)[:, None] * w
-        o = q + eps * nm
-        uni = path_uniforms(cam.seed, pids[idx].astype(np.uint64), b)
-        w = cosine_direction(nm, uni[:, 0], uni[:, 1])
+        o, w = shade_step(o, w, d, nm, cam.seed, pids[idx], b, eps)
         thr = thr * cam.albedo
     return {"radiance": rad, "min_abs_logit": min_logit, "dist": aov_d, "logit": aov_l,
             "normal": aov_n}

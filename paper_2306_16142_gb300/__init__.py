@@ -5,5 +5,5 @@ Import is cheap; the library is loaded on first use and a missing build raises I
 (there is no CPU fallback)."""
 
 from ._abi import DDFError, load, LIB_PATH  # noqa: F401
-from .ddf import DDFGroup, DDFNet, DDFMesh, camera_struct  # noqa: F401
+from .ddf import DDFGroup, DDFNet, DDFMesh, camera_struct, measure_peaks  # noqa: F401
 from .autograd import DDFFunction, ddf_apply  # noqa: F401

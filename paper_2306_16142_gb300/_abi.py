@@ -73,6 +73,7 @@ _SIG = {
     "ddf_device_status": (C.c_int, [_P]),
     "ddf_fp8_scales": (C.c_int, [_P, _P, C.c_size_t]),
     "ddf_selftest_wait": (C.c_int, [C.c_int, C.c_int]),
+    "ddf_measure_peaks": (C.c_int, [C.POINTER(C.c_double), C.c_int]),
     "ddf_num_params": (C.c_int, [_P, C.POINTER(_I64)]),
     "ddf_set_weights": (C.c_int, [_P, _P, C.c_size_t, _P]),
     "ddf_get_weights": (C.c_int, [_P, _P, C.c_size_t, _P]),
@@ -87,6 +88,8 @@ _SIG = {
     "ddf_group_autotune": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int, C.c_char_p, _P]),
     "ddf_group_config": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "ddf_render": (C.c_int, [_P, C.POINTER(ddf_camera), C.c_int, C.c_int, _P, _P]),
+    "ddf_render_trace": (C.c_int, [_P, C.POINTER(ddf_camera), C.c_int, C.c_int, _P, _P, _I64, _P, _P, _P]),
+    "ddf_render_set_wave": (C.c_int, [_P, _I64]),
     "ddf_render_stats": (C.c_int, [_P, C.POINTER(_I64), C.c_int]),
     "ddf_profile_enable": (C.c_int, [_P, C.c_int]),
     "ddf_profile_read": (C.c_int, [_P, C.POINTER(C.c_double)]),

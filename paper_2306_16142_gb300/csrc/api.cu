@@ -314,8 +314,8 @@ int ddf_query(ddf_net net, const float* d_origins, const float* d_dirs, int64_t 
     return field_query(net, d_origins, d_dirs, n, nullptr, d_dist, d_logit, d_hit, d_normals, stream);
 }
 
-int ddf_render(ddf_net net, const ddf_camera* cam, int spp, int bounces, float* d_image,
-               cudaStream_t stream) {
+namespace {
+int check_render_args(ddf_net net, const ddf_camera* cam, int spp, int bounces, float* d_image) {
     if (!net || !cam || !d_image) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
     if (cam->width <= 0 || cam->height <= 0 || (int64_t)cam->width * cam->height > (int64_t(1) << 31))
         return fail(DDF_ERR_INVALID_ARG, "bad image size %d x %d", cam->width, cam->height);
@@ -325,7 +325,54 @@ int ddf_render(ddf_net net, const ddf_camera* cam, int spp, int bounces, float* 
         return fail(DDF_ERR_INVALID_ARG, "too many paths");
     if (!(cam->vfov_deg > 0.f && cam->vfov_deg < 180.f))
         return fail(DDF_ERR_INVALID_ARG, "vfov must be in (0, 180)");
+    return DDF_OK;
+}
+}  // namespace
+
+int ddf_render(ddf_net net, const ddf_camera* cam, int spp, int bounces, float* d_image,
+               cudaStream_t stream) {
+    int rc = check_render_args(net, cam, spp, bounces, d_image);
+    if (rc) return rc;
     return render(net, cam, spp, bounces, d_image, stream);
+}
+
+int ddf_render_trace(ddf_net net, const ddf_camera* cam, int spp, int bounces, float* d_image,
+                     const int64_t* d_pids, int64_t n_trace, float* d_trace, float* d_radiance,
+                     cudaStream_t stream) {
+    int rc = check_render_args(net, cam, spp, bounces, d_image);
+    if (rc) return rc;
+    if (n_trace < 0) return fail(DDF_ERR_INVALID_ARG, "n_trace < 0");
+    if (n_trace > 0 && (!d_pids || !d_trace || !d_radiance))
+        return fail(DDF_ERR_INVALID_ARG, "pids, trace and radiance must be non-NULL");
+    if (n_trace >= (int64_t(1) << 31)) return fail(DDF_ERR_INVALID_ARG, "at most 2^31 - 1 traced paths");
+    const int64_t npix = (int64_t)cam->width * cam->height;
+    const int64_t wave = std::max<int64_t>(1, std::min<int64_t>(npix, net->wave_max / spp)) * spp;
+    RenderTrace tr;
+    tr.pids = d_pids;
+    tr.n = n_trace;
+    tr.rec = d_trace;
+    tr.rad = d_radiance;
+    if (n_trace > 0) {
+        DDF_CUDA_TRY(cudaMemsetAsync(d_trace, 0xFF, sizeof(float) * (size_t)n_trace * bounces * kTraceFloats,
+                                     stream));   // 0xFFFFFFFF: a NaN
+        DDF_CUDA_TRY(cudaMemsetAsync(d_radiance, 0xFF, sizeof(float) * (size_t)n_trace, stream));
+        DDF_CUDA_TRY(cudaMalloc(&tr.map, sizeof(int32_t) * (size_t)wave));
+    }
+    rc = render(net, cam, spp, bounces, d_image, stream, n_trace > 0 ? &tr : nullptr);
+    // the slot map is freed once the kernels that read it are done
+    cudaError_t e = cudaStreamSynchronize(stream);
+    cudaFree(tr.map);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(DDF_ERR_CUDA, "render trace: %s", cudaGetErrorString(e));
+    return DDF_OK;
+}
+
+int ddf_render_set_wave(ddf_net net, int64_t max_paths) {
+    if (!net) return fail(DDF_ERR_INVALID_ARG, "net is NULL");
+    if (max_paths < 1 || max_paths > kWaveMax)
+        return fail(DDF_ERR_INVALID_ARG, "paths per wave must be in [1, 2^24], got %lld", (long long)max_paths);
+    net->wave_max = max_paths;
+    return DDF_OK;
 }
 
 namespace {

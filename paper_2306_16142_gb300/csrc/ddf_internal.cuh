@@ -102,6 +102,7 @@ struct ddf_net_s {
     int render_counts_len = 0;
     int last_bounces = 0;
     cudaStream_t last_stream = nullptr;
+    int64_t wave_max = ddf::kWaveMax;   // paths per render wave (ddf_render_set_wave)
     ddf::Profiler prof;
 };
 
@@ -156,8 +157,18 @@ int field_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
                 cudaStream_t stream);
 
 // ------------------------------------------------------------------ renderer (wavefront.cu)
+// Paths whose every bounce a render records (ddf_render_trace): rec gets kTraceFloats floats per
+// (path, bounce), rad the path's radiance.
+constexpr int kTraceFloats = 12;
+struct RenderTrace {
+    const int64_t* pids = nullptr;   // device, n path ids
+    int64_t n = 0;
+    float* rec = nullptr;            // device, n x bounces x kTraceFloats
+    float* rad = nullptr;            // device, n
+    int32_t* map = nullptr;          // device scratch, one slot per path of a wave
+};
 int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* image,
-           cudaStream_t stream);
+           cudaStream_t stream, const RenderTrace* trace = nullptr);
 // Depth (t from the eye) and normal maps of the field (ddf_render_aov) and of a mesh
 // (ddf_mesh_render_aov) from the same pixel rays.
 int render_aov(ddf_net_s* net, const ddf_camera* cam, float* depth, float* normal, cudaStream_t stream);

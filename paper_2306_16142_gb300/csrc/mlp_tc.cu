@@ -1521,6 +1521,298 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// FP8 query at width 512: one 128-row tile per CTA. The E4M3 activation tile (4 K-blocks of 128
+// features, 64 KB) stays in shared memory; the weights stream through a ring of 32 KB stages, each
+// one N-half (256 output units) of one 128-feature K-block. The 512-column accumulator fills
+// TMEM, so every layer runs as two N = 256 halves with a commit per half, each started by a bias
+// MMA (ones column x the half's b / s_w tile). The epilogue turns half 0 into E4M3 codes in
+// registers while half 1 is multiplied, writes them once the layer's last MMA has read the
+// previous activations, and the next layer's MMAs start on K-blocks 0-1 while half 1 is being
+// converted. Scales as in mlp_f8_kernel: code = E4M3(ReLU(acc mu_l)); the last layer's s_w is
+// folded into the FP32 output head.
+__global__ void __launch_bounds__(kThreads, 1)
+    mlp_f8w512_kernel(const __grid_constant__ CUtensorMap map8, const TcArgs a) {
+    constexpr int W = 512;
+    constexpr uint32_t kStage = 32768u;        // 256 rows x 128 bytes
+    constexpr uint32_t kBias = (uint32_t)W * 32u;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int L = a.L;
+    const int NST = a.nst;
+    uint8_t* act = smem;                                          // 4 x 16 KB
+    uint8_t* wst = smem + a.off_wst;                              // NST x 32 KB
+    uint8_t* ones = smem + a.off_mask;                            // 4 KB
+    uint8_t* bslot = smem + a.off_bias;                           // the layer's bias tiles (both halves)
+    float* emul_s = reinterpret_cast<float*>(smem + a.off_grp);   // mu_l
+    float* head_s = reinterpret_cast<float*>(smem + a.off_head);
+    float* part = reinterpret_cast<float*>(smem + a.off_part);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + NST;
+    uint64_t* actr = bars + 2 * NST;   // [4]: K-block written
+    uint64_t* accf = actr + 4;         // [2]: N-half accumulated
+    uint64_t* accfree = accf + 2;      // [2]: N-half read by the epilogue
+    uint64_t* bfull = accfree + 2;     // bias slot loaded / consumed
+    uint64_t* bempty = bfull + 1;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bempty + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int64_t n = a.n;
+    if (a.d_count) n = min(n, (int64_t)*a.d_count);
+    const int64_t ntiles = (n + kTileM - 1) / kTileM;
+
+    if (tid == 0) {
+        for (int i = 0; i < NST; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 4; ++i) mbar_init(&actr[i], kEpiWarps);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accf[i], 1);
+            mbar_init(&accfree[i], kEpiWarps);
+        }
+        mbar_init(bfull, 1);
+        mbar_init(bempty, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // the ones tile: K rows 0 and 1 of both 64-row MN atoms are 1.0 (BF16 0x3F80), the rest 0
+    for (int i = tid; i < 1024; i += kThreads)
+        reinterpret_cast<uint32_t*>(ones)[i] = ((i >> 5) & 15) < 2 ? 0x3F803F80u : 0u;
+    fence_proxy_async();
+    for (int i = tid; i < L; i += kThreads) emul_s[i] = a.f8_emul[i];
+    for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+
+    if (warp == kEpiWarps) {
+        // ---------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            uint32_t cnt = 0, nb = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
+                for (int s = 0; s < L && ok; ++s, ++nb) {
+                    if (!mbar_wait(bempty, (nb & 1u) ^ 1u, a.err)) { ok = false; break; }
+                    mbar_expect_tx(bfull, kBias);
+                    bulk_load(bslot, a.bias_mn + (size_t)s * kBias, kBias, bfull);
+                    const int nk = s == 0 ? 1 : W / 128;
+                    for (int h = 0; h < 2 && ok; ++h)
+                        for (int kb = 0; kb < nk; ++kb, ++cnt) {
+                            const int stg = (int)(cnt % (uint32_t)NST);
+                            if (!mbar_wait(&empty[stg], ((cnt / (uint32_t)NST) & 1u) ^ 1u, a.err)) { ok = false; break; }
+                            mbar_expect_tx(&full[stg], kStage);
+                            tma_load_3d(wst + (size_t)stg * kStage, &map8, &full[stg], kb * 128, h * 256, s);
+                        }
+                }
+        }
+    } else if (warp == kEpiWarps + 1) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t cnt = 0, actph = 0, freeph = 0, nb = 0;
+            bool ok = true;
+            const uint32_t act_s = su32(act), wst_s = su32(wst);
+            const uint32_t idesc = idesc_f8(128, 256);
+            const uint32_t idesc_b = idesc_bf16(128, 256) | (3u << 15);   // bias MMA: both operands MN-major
+            const uint64_t ones_d = sdesc_mn16(su32(ones));
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
+                for (int s = 0; s < L && ok; ++s, ++nb) {
+                    const int nk = s == 0 ? 1 : W / 128;
+                    for (int h = 0; h < 2 && ok; ++h) {
+                        const uint32_t d = tbase + (uint32_t)h * 256u;
+                        if (!mbar_wait(&accfree[h], ((freeph >> h) & 1u) ^ 1u, a.err)) { ok = false; break; }
+                        freeph ^= 1u << h;
+                        for (int kb = 0; kb < nk; ++kb, ++cnt) {
+                            const int stg = (int)(cnt % (uint32_t)NST);
+                            if (!mbar_wait(&full[stg], (cnt / (uint32_t)NST) & 1u, a.err)) { ok = false; break; }
+                            if (h == 0) {
+                                if (!mbar_wait(&actr[kb], (actph >> kb) & 1u, a.err)) { ok = false; break; }
+                                actph ^= 1u << kb;
+                            }
+                            if (kb == 0 && h == 0 && !mbar_wait(bfull, nb & 1u, a.err)) { ok = false; break; }
+                            tc_fence_after();
+                            if (kb == 0) {   // D = b / s_w of this half (BF16 MMA into the FP32 accumulator)
+                                mma_bf16(d, ones_d, sdesc_mn16(su32(bslot) + (uint32_t)h * (kBias / 2)), idesc_b, 0u);
+                                if (h == 1) mma_commit(bempty);
+                            }
+                            const uint64_t ad = sdesc(act_s + (uint32_t)kb * 16384u);
+                            const uint64_t bd = sdesc(wst_s + (uint32_t)stg * kStage);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) mma_f8(d, ad + 2 * k, bd + 2 * k, idesc, 1u);
+                            mma_commit(&empty[stg]);
+                        }
+                        if (ok) mma_commit(&accf[h]);
+                    }
+                }
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        // warp w serves rows 32 (w % 4) .. +31; group w / 4 owns the 64 columns
+        // [128 kb + 64 group, +64) of every 128-column K-block
+        const int grp = warp >> 2;
+        const int r = (warp & 3) * 32 + lane;
+        const uint32_t act_s = su32(act);
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        uint32_t accph = 0;
+        bool ok = true;
+        auto store64 = [&](int kb, const uint32_t* q) {
+            const uint32_t base = act_s + (uint32_t)kb * 16384u;
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                st_shared_v4(base + swz(r, grp * 4 + m), q[4 * m], q[4 * m + 1], q[4 * m + 2], q[4 * m + 3]);
+        };
+        auto load_row = [&](int64_t t, float* vv) {
+            const int64_t i = t * kTileM + r;
+            const bool valid = t < ntiles && i < n;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                vv[c] = valid ? a.o[i * 3 + c] : 0.f;
+                vv[c + 3] = valid ? a.w[i * 3 + c] : 0.f;
+            }
+        };
+        // layer 0: features in [-1, 1], fixed input scale 1 / 448; group g writes [64 g, 64 g + 64)
+        auto encode = [&](const float* vv) {
+            float fe[64];
+            if (grp == 0) encode_feats64<0>(vv, a.F, fe);
+            else encode_feats64<1>(vv, a.F, fe);
+            uint32_t q[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                q[i] = pack_e4m3x4(fe[4 * i] * 448.f, fe[4 * i + 1] * 448.f, fe[4 * i + 2] * 448.f, fe[4 * i + 3] * 448.f);
+            store64(0, q);
+            release_kb_warp(actr, 0);
+        };
+        // this thread's 64 columns of K-block kb of the accumulator -> 16 words of E4M3 codes
+        auto convert = [&](uint32_t col, float mu, uint32_t* q) {
+            uint32_t raw[2][32];
+            TC_LD32(tbase + lane_off + col, raw[0]);
+            TC_LD32(tbase + lane_off + col + 32u, raw[1]);
+            tc_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const uint32_t* x = &raw[i >> 3][(4 * i) & 31];
+                float u0, u1, u2, u3;
+                mul2p(__uint_as_float(x[0]), __uint_as_float(x[1]), mu, u0, u1);
+                mul2p(__uint_as_float(x[2]), __uint_as_float(x[3]), mu, u2, u3);
+                q[i] = pack_relu_e4m3x4(u0, u1, u2, u3);
+            }
+        };
+        auto head_cols = [&](uint32_t col, int c0, float& y0, float& y1) {
+            uint32_t raw[2][32];
+            TC_LD32(tbase + lane_off + col, raw[0]);
+            TC_LD32(tbase + lane_off + col + 32u, raw[1]);
+            tc_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 64; ++c) {
+                const float z = fmaxf(__uint_as_float(raw[c >> 5][c & 31]), 0.f);
+                y0 = fmaf(z, head_s[c0 + c], y0);
+                y1 = fmaf(z, head_s[W + c0 + c], y1);
+            }
+        };
+        auto arrive_free = [&](int h) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accfree[h]);
+        };
+        float vnext[6];
+        if ((int64_t)blockIdx.x < ntiles) {
+            load_row(blockIdx.x, vnext);
+            encode(vnext);
+        }
+        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int64_t tn = t + gridDim.x;
+            for (int s = 0; s < L && ok; ++s) {
+                const bool last = s == L - 1;
+                if (last) load_row(tn, vnext);
+                const float mu = emul_s[s];
+                float y0 = 0.f, y1 = 0.f;
+                // ---- half 0
+                ok = mbar_wait(&accf[0], accph & 1u, a.err);
+                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                tc_fence_after();
+                uint32_t stash[2][16];
+#pragma unroll
+                for (int kl = 0; kl < 2; ++kl) {
+                    const uint32_t col = (uint32_t)(kl * 128 + grp * 64);
+                    if (last) head_cols(col, (int)col, y0, y1);
+                    else convert(col, mu, stash[kl]);
+                }
+                arrive_free(0);
+                // ---- the layer's last MMA is done: the previous activations are free
+                ok = mbar_wait(&accf[1], (accph >> 1) & 1u, a.err);
+                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                accph ^= 3u;
+                tc_fence_after();
+                if (!last) {
+#pragma unroll
+                    for (int kl = 0; kl < 2; ++kl) {
+                        store64(kl, stash[kl]);
+                        release_kb_warp(actr, kl);
+                    }
+                }
+                // ---- half 1
+#pragma unroll
+                for (int kl = 0; kl < 2; ++kl) {
+                    const uint32_t col = (uint32_t)(256 + kl * 128 + grp * 64);
+                    if (last) {
+                        head_cols(col, (int)col, y0, y1);
+                    } else {
+                        uint32_t q[16];
+                        convert(col, mu, q);
+                        if (kl == 1) arrive_free(1);
+                        store64(2 + kl, q);
+                        release_kb_warp(actr, 2 + kl);
+                    }
+                }
+                if (last) {
+                    arrive_free(1);
+                    if (grp == 1) {
+                        part[2 * r] = y0;
+                        part[2 * r + 1] = y1;
+                    }
+                    epi_bar();
+                    if (grp == 0) {
+                        const int64_t i = t * kTileM + r;
+                        const bool valid = i < n;
+                        y0 += part[2 * r] + head_s[2 * W];
+                        y1 += part[2 * r + 1] + head_s[2 * W + 1];
+                        const bool hh = y1 > 0.f;
+                        if (valid) {
+                            a.dist[i] = y0;
+                            if (a.logit) a.logit[i] = y1;
+                            if (a.hit) a.hit[i] = (uint8_t)hh;
+                        }
+                        if (a.hit_list) {
+                            const bool take = valid && hh;
+                            const unsigned m = __ballot_sync(0xffffffffu, take);
+                            int base = 0;
+                            if (lane == 0 && m) base = atomicAdd(a.hit_count, __popc(m));
+                            base = __shfl_sync(0xffffffffu, base, 0);
+                            if (take) a.hit_list[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
+                        }
+                    }
+                    epi_bar();
+                    if (tn < ntiles) encode(vnext);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (*(volatile int*)a.err) {
+        const uint64_t t0 = gtimer();
+        while (gtimer() - t0 < 200000ull) {
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));
+    }
+}
+
 // ------------------------------------------------------------------ packing
 
 __global__ void pack_kernel(const float* __restrict__ master, NetLayout lay, int kmax,
@@ -1711,7 +2003,7 @@ int make_map_u8(CUtensorMap* m, void* base, int inner, int rows, int L) {
     if (!enc) return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
     cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)L};
     cuuint64_t strides[2] = {(cuuint64_t)inner, (cuuint64_t)inner * rows};
-    cuuint32_t box[3] = {128, (cuuint32_t)rows, 1};
+    cuuint32_t box[3] = {128, (cuuint32_t)(rows < 256 ? rows : 256), 1};   // width 512: N-halves
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1903,6 +2195,61 @@ int launch_f8(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_coun
     return DDF_OK;
 }
 
+// Shared memory of the width-512 FP8 kernel: the E4M3 A tile (64 KB), the ring of 32 KB N-half
+// stages, the ones tile and the layer's two bias tiles (both 1 KB aligned), mu_l, the head and the
+// head partial sums.
+Layout smem_layout_f8w512(int L) {
+    Layout s{};
+    const uint32_t act = 4u * 16384u;
+    const uint32_t stage = 32768u;
+    const uint32_t ones = 4096u;
+    const uint32_t bias = 512u * 32u;
+    const uint32_t emul = ((uint32_t)L * 4u + 15u) & ~15u;
+    const uint32_t head = ((uint32_t)(2 * 512 + 2) * 4u + 15u) & ~15u;
+    const uint32_t partb = 128u * 2u * 4u;
+    const uint32_t fixed = act + ones + bias + emul + head + partb + 512u;
+    const uint32_t budget = 227u * 1024u - 1024u;
+    s.nst = std::max(0, std::min(8, (int)((budget - fixed) / stage)));
+    s.off_wst = act;
+    s.off_mask = act + (uint32_t)s.nst * stage;
+    s.off_bias = s.off_mask + ones;
+    s.off_grp = s.off_bias + bias;
+    s.off_head = s.off_grp + emul;
+    s.off_part = s.off_head + head;
+    s.off_bar = s.off_part + partb;
+    s.total = s.off_bar + 512u + 1024u;
+    return s;
+}
+
+int launch_f8w512(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_count, cudaStream_t stream) {
+    const TcPack* P = net->tc;
+    TcArgs a = base;
+    const Layout s = smem_layout_f8w512(a.L);
+    if (s.nst < 2) return fail(DDF_ERR_UNSUPPORTED, "FP8 width-512 MLP: shared memory too small");
+    a.nst = s.nst;
+    a.off_wst = s.off_wst;
+    a.off_mask = s.off_mask;
+    a.off_bias = s.off_bias;
+    a.off_grp = s.off_grp;
+    a.off_head = s.off_head;
+    a.off_part = s.off_part;
+    a.off_bar = s.off_bar;
+    a.f8_emul = P->emul8;
+    a.bias_mn = P->bias8_mn;
+    a.head = P->head8;
+    // one CTA per SM, each walking 128-row tiles
+    int grid = use_count ? num_sms() : (int)std::min<int64_t>((n + kTileM - 1) / kTileM, num_sms());
+    if (grid <= 0) return DDF_OK;
+    static bool attr = false;
+    if (!attr) {
+        DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_f8w512_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr = true;
+    }
+    mlp_f8w512_kernel<<<grid, kThreads, s.total, stream>>>(P->map_f8, a);
+    DDF_LAUNCH_CHECK();
+    return DDF_OK;
+}
+
 uint32_t smem512(int nst) { return 8u * 16384u + (uint32_t)nst * 32768u + 512u + 1024u; }
 
 int launch512(const ddf_net_s* net, int mode, const TcArgs& base, int64_t n, bool use_count, cudaStream_t stream) {
@@ -1952,9 +2299,10 @@ __global__ void grouped_prep(const int64_t* __restrict__ offsets, const GNet* __
 
 bool tc_supported(const NetLayout& lay, int precision) {
     if (precision == DDF_FP8) {
-        if (lay.width != 128 && lay.width != 256) return false;
+        if (lay.width != 128 && lay.width != 256 && lay.width != 512) return false;
         if (lay.E + 2 > 128 || lay.L < 1 || lay.L > kMaxLayers) return false;
-        return smem_layout_f8(lay.width, lay.L).nst >= 2 && tc_supported(lay, DDF_BF16);
+        const int nst = lay.width == 512 ? smem_layout_f8w512(lay.L).nst : smem_layout_f8(lay.width, lay.L).nst;
+        return nst >= 2 && tc_supported(lay, DDF_BF16);
     }
     if (precision != DDF_BF16) return false;
     if (lay.width != 128 && lay.width != 256 && lay.width != 512) return false;
@@ -2050,6 +2398,26 @@ int tc_pack(ddf_net_s* net, int precision, cudaStream_t stream) {
     return DDF_OK;
 }
 
+// The forward query launch of the handle's width and precision (hit rows appended to a.hit_list
+// when it is set), and the normal launch over the rows of b.rows (count *b.d_count).
+int tc_forward_launch(const ddf_net_s* net, const TcArgs& a, int64_t n, bool use_count, cudaStream_t stream) {
+    const int W = net->lay.width;
+    if (net->precision == DDF_FP8)
+        return W == 128   ? launch_f8<128>(net, a, n, use_count, stream)
+               : W == 256 ? launch_f8<256>(net, a, n, use_count, stream)
+                          : launch_f8w512(net, a, n, use_count, stream);
+    return W == 128   ? launch_pair<128, false>(net, a, n, use_count, stream)
+           : W == 256 ? launch_pair<256, false>(net, a, n, use_count, stream)
+                      : launch512(net, 0, a, n, use_count, stream);
+}
+
+int tc_normals_launch(const ddf_net_s* net, const TcArgs& b, int64_t n, cudaStream_t stream) {
+    const int W = net->lay.width;
+    return W == 128   ? launch_mode<128>(net, 1, b, n, true, stream)
+           : W == 256 ? launch_mode<256>(net, 1, b, n, true, stream)
+                      : launch512(net, 1, b, n, true, stream);
+}
+
 int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n, const int* d_count,
                  float* dist, float* logit, uint8_t* hit, float* normals, cudaStream_t stream) {
     TcPack* P = net->tc;
@@ -2082,14 +2450,7 @@ int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n
         a.hit_list = P->hit_list;
         a.hit_count = P->hit_count;
     }
-    int rc;
-    if (net->precision == DDF_FP8)
-        rc = lay.width == 128 ? launch_f8<128>(net, a, n, d_count != nullptr, stream)
-                              : launch_f8<256>(net, a, n, d_count != nullptr, stream);
-    else
-        rc = lay.width == 128   ? launch_pair<128, false>(net, a, n, d_count != nullptr, stream)
-             : lay.width == 256 ? launch_pair<256, false>(net, a, n, d_count != nullptr, stream)
-                                : launch512(net, 0, a, n, d_count != nullptr, stream);
+    int rc = tc_forward_launch(net, a, n, d_count != nullptr, stream);
     if (rc || !normals) return rc;
     TcArgs b = a;
     b.rows = P->hit_list;
@@ -2100,9 +2461,7 @@ int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n
     b.logit = nullptr;
     b.hit = nullptr;
     b.normals = normals;
-    return lay.width == 128   ? launch_mode<128>(net, 1, b, n, true, stream)
-           : lay.width == 256 ? launch_mode<256>(net, 1, b, n, true, stream)
-                              : launch512(net, 1, b, n, true, stream);
+    return tc_normals_launch(net, b, n, stream);
 }
 
 int tc_train_forward(const ddf_net_s* net, const float* o, const float* w, int64_t m, const CUtensorMap* map_a0,
@@ -2192,20 +2551,19 @@ extern "C" DDF_API int ddf_query_noalloc(ddf_net net, const float* d_origins, co
     using namespace ddf;
     if (!net) return fail(DDF_ERR_INVALID_ARG, "net is NULL");
     if (n < 0) return fail(DDF_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return DDF_OK;
+    if (!d_origins || !d_dirs || !d_dist || !d_hit)
+        return fail(DDF_ERR_INVALID_ARG, "origins, dirs, dist and hit must be non-NULL");
+    // The sphere field, the FP32 path and a tensor-core query without normals use no scratch.
+    if (net->is_sphere || net->precision == DDF_FP32 || !d_normals)
+        return field_query(net, d_origins, d_dirs, n, nullptr, d_dist, d_logit, d_hit, d_normals, stream);
+    // Only the hit-row list of a tensor-core query with normals lives in the static array.
     if (n > kNoAllocMaxRows)
         return fail(DDF_ERR_INVALID_ARG,
                     "ddf_query_noalloc: n = %lld rows exceeds the static scratch limit of %lld rows",
                     (long long)n, (long long)kNoAllocMaxRows);
-    if (n == 0) return DDF_OK;
-    if (!d_origins || !d_dirs || !d_dist || !d_hit)
-        return fail(DDF_ERR_INVALID_ARG, "origins, dirs, dist and hit must be non-NULL");
-    // The sphere field, the FP32 path and a BF16 query without normals use no scratch.
-    if (net->is_sphere || net->precision == DDF_FP32 || !d_normals)
-        return field_query(net, d_origins, d_dirs, n, nullptr, d_dist, d_logit, d_hit, d_normals, stream);
     TcPack* P = net->tc;
     if (!P) return fail(DDF_ERR_UNSUPPORTED, "tensor-core weights not packed");
-    if (net->lay.width == 512)
-        return fail(DDF_ERR_UNSUPPORTED, "ddf_query_noalloc: width-512 normals need the handle's mask scratch");
     int* scratch = nullptr;
     int rc = noalloc_scratch(&scratch);
     if (rc) return rc;
@@ -2230,11 +2588,9 @@ extern "C" DDF_API int ddf_query_noalloc(ddf_net net, const float* d_origins, co
     a.err = P->err;
     a.hit_list = hit_list;
     a.hit_count = hit_count;
-    if (net->precision == DDF_FP8)
-        rc = lay.width == 128 ? launch_f8<128>(net, a, n, false, stream) : launch_f8<256>(net, a, n, false, stream);
-    else
-        rc = lay.width == 128 ? launch_pair<128, false>(net, a, n, false, stream)
-                              : launch_pair<256, false>(net, a, n, false, stream);
+    // the same two launches as ddf_query (the width-512 reverse pass keeps its ReLU masks in the
+    // handle's per-SM buffer, allocated once when the weights are packed)
+    rc = tc_forward_launch(net, a, n, false, stream);
     if (rc) return rc;
     TcArgs b = a;
     b.rows = hit_list;
@@ -2245,8 +2601,7 @@ extern "C" DDF_API int ddf_query_noalloc(ddf_net net, const float* d_origins, co
     b.logit = nullptr;
     b.hit = nullptr;
     b.normals = d_normals;
-    return lay.width == 128 ? launch_mode<128>(net, 1, b, n, true, stream)
-                            : launch_mode<256>(net, 1, b, n, true, stream);
+    return tc_normals_launch(net, b, n, stream);
 }
 
 // ------------------------------------------------------------------ grouped multi-object query

@@ -700,16 +700,19 @@ struct TLayout {
 };
 
 // Shared memory: [resident B][stage ring][epilogue blocks][bias][barriers].
-TLayout tlayout(int BN, uint32_t bres_bytes) {
+// Shared memory of the GEMM kernel: resident B (optional), the stages, the epilogue's staging
+// blocks, the forward's bias of all N columns (at least 1 KB) and the barriers.
+TLayout tlayout(int BN, int N, uint32_t bres_bytes) {
     TLayout s;
     const uint32_t stage = 16384u + (bres_bytes ? 0u : (uint32_t)BN * 128u);
-    const uint32_t fixed = kTEpi * 2048 + 1024 + 256;
+    const uint32_t bias = std::max(1024u, (uint32_t)N * 4u);
+    const uint32_t fixed = kTEpi * 2048 + bias + 256;
     const uint32_t avail = kSmemMax - 1024u - fixed - bres_bytes;
     s.nst = (int)std::min<uint32_t>(8u, avail / stage);
     uint32_t off = bres_bytes;
     s.off_stage = off; off += (uint32_t)s.nst * stage;
     s.off_blk = off;  off += kTEpi * 2048;
-    s.off_bias = off; off += 1024;
+    s.off_bias = off; off += bias;
     s.off_bar = off;  off += 256;
     s.total = off + 1024;
     return s;
@@ -741,8 +744,8 @@ int launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, TArgs a, cudaStrea
     if (a.BN % 64 || a.BN > 256 || a.N % a.BN) return fail(DDF_ERR_UNSUPPORTED, "training GEMM tile N=%d", a.BN);
     // weights as B (a single N tile): keep all of B in shared memory when it fits beside 2 A stages
     const uint32_t bres_bytes = (uint32_t)a.nkb * (uint32_t)a.BN * 128u;
-    a.bres = (!a.mn_major && a.N == a.BN && a.ksplit == 1 && tlayout(a.BN, bres_bytes).nst >= 2) ? 1 : 0;
-    const TLayout L = tlayout(a.BN, a.bres ? bres_bytes : 0u);
+    a.bres = (!a.mn_major && a.N == a.BN && a.ksplit == 1 && tlayout(a.BN, a.N, bres_bytes).nst >= 2) ? 1 : 0;
+    const TLayout L = tlayout(a.BN, a.N, a.bres ? bres_bytes : 0u);
     if (L.nst < 2 || L.total > kSmemMax) return fail(DDF_ERR_UNSUPPORTED, "training GEMM shared memory");
     a.nst = L.nst;
     a.off_stage = L.off_stage;
@@ -872,7 +875,7 @@ int tc_forward(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t
     auto act = [&](int l) { return ws.act + (l == 0 ? 0 : ((int64_t)K0 + (int64_t)(l - 1) * W) * ld); };
     auto masks = [&](int l) { return ws.masks + (int64_t)(l - 1) * ld * (W / 32); };
     int rc;
-    if (K0 <= 128) {
+    if (K0 <= 128 && W <= 256) {
         // one persistent launch (the query's pair kernel in its training form): a_0 .. a_{L-1}
         // leave the chip by TMA stores of the A tiles, a_L and the masks from the epilogue
         CUtensorMap m0, ma;
@@ -892,7 +895,7 @@ int tc_forward(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t
         a.mode = T_FWD;
         a.M = (int)m;
         a.N = W;
-        a.BN = W;
+        a.BN = std::min(W, 256);   // width 512: two N tiles
         a.nkb = K / 64;
         a.kb_per = a.nkb;
         a.ksplit = 1;

@@ -155,6 +155,47 @@ __global__ void accumulate_kernel(const float* __restrict__ radiance, int spp, i
     }
 }
 
+// ---- traced paths (ddf_render_trace): slot map of one wave, per-bounce records, radiance
+__global__ void trace_map_kernel(const int64_t* __restrict__ pids, int64_t n, int64_t pid0, int64_t npaths,
+                                 int32_t* __restrict__ map) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = pids[s] - pid0;
+        if (p >= 0 && p < npaths) map[p] = (int32_t)s;
+    }
+}
+
+// The query inputs and outputs of bounce b of every traced path still alive: o, w, dist, logit,
+// normal (NaN where the query computed none: a miss, or the last bounce), throughput.
+__global__ void trace_record_kernel(const int* __restrict__ count, const uint32_t* __restrict__ lid,
+                                    const int32_t* __restrict__ map, const float* __restrict__ o,
+                                    const float* __restrict__ w, const float* __restrict__ dist,
+                                    const float* __restrict__ logit, const float* __restrict__ nrm,
+                                    const float* __restrict__ thr, int bounce, int bounces, float* __restrict__ rec) {
+    const int n = *count;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t s = map[lid[i]];
+        if (s < 0) continue;
+        float* r = rec + ((int64_t)s * bounces + (bounce - 1)) * kTraceFloats;
+        const bool has_n = nrm && logit[i] > 0.f;   // the query writes normals of hit rows only
+        for (int c = 0; c < 3; ++c) {
+            r[c] = o[3 * i + c];
+            r[3 + c] = w[3 * i + c];
+            r[8 + c] = has_n ? nrm[3 * i + c] : __int_as_float(0x7fc00000);
+        }
+        r[6] = dist[i];
+        r[7] = logit[i];
+        r[11] = thr[i];
+    }
+}
+
+__global__ void trace_radiance_kernel(const int64_t* __restrict__ pids, int64_t n, int64_t pid0, int64_t npaths,
+                                      const float* __restrict__ radiance, float* __restrict__ out) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = pids[s] - pid0;
+        if (p >= 0 && p < npaths) out[s] = radiance[p];
+    }
+}
+
 __global__ void add_counts(const int* __restrict__ counts, int bounces, int64_t* __restrict__ totals) {
     const int b = threadIdx.x;
     if (b < bounces) totals[b] += counts[b];
@@ -318,9 +359,9 @@ int render_bufs(void** ws, size_t* ws_bytes, int64_t wave_paths, WaveBufs* out) 
 }  // namespace
 
 int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* image,
-           cudaStream_t stream) {
+           cudaStream_t stream, const RenderTrace* trace) {
     const int64_t npix = (int64_t)cam->width * cam->height;
-    const int64_t px_per_wave = std::max<int64_t>(1, std::min<int64_t>(npix, kWaveMax / spp));
+    const int64_t px_per_wave = std::max<int64_t>(1, std::min<int64_t>(npix, net->wave_max / spp));
     const int64_t wave_paths = px_per_wave * spp;
     WaveBufs B;
     int rc0 = render_bufs(&net->render_ws, &net->render_ws_bytes, wave_paths, &B);
@@ -349,6 +390,11 @@ int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* i
                                                    B.thr[0], B.radiance, B.counts);
         DDF_LAUNCH_CHECK();
         net->prof.end(pe, stream);
+        if (trace) {
+            DDF_CUDA_TRY(cudaMemsetAsync(trace->map, 0xFF, sizeof(int32_t) * npaths, stream));
+            trace_map_kernel<<<grid, kThreads, 0, stream>>>(trace->pids, trace->n, pid0, npaths, trace->map);
+            DDF_LAUNCH_CHECK();
+        }
         for (int b = 1; b <= bounces; ++b) {
             const int s = (b - 1) & 1;
             pe = net->prof.begin(PROF_QUERY, stream);
@@ -356,6 +402,13 @@ int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* i
                                  nullptr, b < bounces ? B.nrm : nullptr, stream);
             if (rc) return rc;
             net->prof.end(pe, stream);
+            if (trace) {
+                trace_record_kernel<<<grid, kThreads, 0, stream>>>(B.counts + (b - 1), B.lid[s], trace->map, B.o[s],
+                                                                   B.w[s], B.dist, B.logit,
+                                                                   b < bounces ? B.nrm : nullptr, B.thr[s], b,
+                                                                   bounces, trace->rec);
+                DDF_LAUNCH_CHECK();
+            }
             pe = net->prof.begin(PROF_SHADE, stream);
             shade_kernel<<<grid, kThreads, 0, stream>>>(cd, pid0, b, bounces, B.counts + (b - 1),
                                                         B.o[s], B.w[s], B.lid[s], B.thr[s], B.dist,
@@ -369,6 +422,11 @@ int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* i
         accumulate_kernel<<<grid, kThreads, 0, stream>>>(B.radiance, spp, px0, npx, image);
         DDF_LAUNCH_CHECK();
         net->prof.end(pe, stream);
+        if (trace) {
+            trace_radiance_kernel<<<grid, kThreads, 0, stream>>>(trace->pids, trace->n, pid0, npaths, B.radiance,
+                                                                 trace->rad);
+            DDF_LAUNCH_CHECK();
+        }
         add_counts<<<1, 64, 0, stream>>>(B.counts, bounces, net->render_counts);
         DDF_LAUNCH_CHECK();
     }
@@ -377,7 +435,7 @@ int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* i
 
 int render_aov(ddf_net_s* net, const ddf_camera* cam, float* depth, float* normal, cudaStream_t stream) {
     const int64_t npix = (int64_t)cam->width * cam->height;
-    const int64_t px_per_wave = std::min<int64_t>(npix, kWaveMax);
+    const int64_t px_per_wave = std::min<int64_t>(npix, net->wave_max);
     WaveBufs B;
     int rc = render_bufs(&net->render_ws, &net->render_ws_bytes, px_per_wave, &B);
     if (rc) return rc;

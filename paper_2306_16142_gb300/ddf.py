@@ -147,6 +147,26 @@ class DDFNet:
                                                    _stream()))
         return image
 
+    def render_trace(self, cam, spp: int, bounces: int, pids: torch.Tensor, image: torch.Tensor | None = None):
+        """ddf_render plus a record of every bounce of the paths in pids (CUDA int64): returns
+        (image, trace, radiance), trace (len(pids), bounces, 12) = o, w, dist, logit, normal,
+        throughput of each bounce's query (NaN where the path did not get that far)."""
+        c = camera_struct(cam)
+        if image is None:
+            image = torch.empty(cam.height, cam.width, device="cuda")
+        if pids.dtype != torch.int64:
+            raise ValueError("pids must be an int64 tensor")
+        n = pids.numel()
+        trace = torch.empty(max(n, 1), bounces, 12, device="cuda")
+        rad = torch.empty(max(n, 1), device="cuda")
+        check("ddf_render_trace", _abi.load().ddf_render_trace(self.h, C.byref(c), spp, bounces, _ptr(image),
+                                                               _ptr(pids), n, _ptr(trace), _ptr(rad), _stream()))
+        return image, trace[:n], rad[:n]
+
+    def set_wave(self, max_paths: int):
+        """Paths per render wave (ddf_render_set_wave; default 2^24)."""
+        check("ddf_render_set_wave", _abi.load().ddf_render_set_wave(self.h, max_paths))
+
     def render_aov(self, cam):
         """Depth (H, W; distance from the eye, inf on a miss) and normal (H, W, 3) maps of one
         primary ray per pixel (ddf_render_aov)."""
@@ -353,6 +373,15 @@ class DDFMesh:
         check("ddf_sample_pov", _abi.load().ddf_sample_pov(
             self.h, C.byref(prm), _ptr(out["o"]), _ptr(out["w"]), _ptr(out["dist"]), _ptr(out["hit"]), _stream()))
         return {name: t[:n] for name, t in out.items()}
+
+
+def measure_peaks():
+    """Measured FP32 / FP32x2 / FP64 FMA and BF16 / FP8 tensor-core throughput of the current
+    device in TFLOP/s, and its SM count (ddf_measure_peaks)."""
+    arr = (C.c_double * 7)()
+    check("ddf_measure_peaks", _abi.load().ddf_measure_peaks(arr, 7))
+    return {"fp32_fma_tflops": arr[0], "fp32x2_fma_tflops": arr[1], "fp64_fma_tflops": arr[2],
+            "bf16_mma_tflops": arr[3], "fp8_mma_tflops": arr[4], "sms": int(arr[5])}
 
 
 def camera_struct(cam) -> ddf_camera:

@@ -22,7 +22,8 @@ def P():
     return P
 
 
-@pytest.mark.parametrize("F,W,L,seed", [(12, 256, 8, 2), (12, 128, 4, 7), (16, 256, 5, 4), (0, 128, 6, 9)])
+@pytest.mark.parametrize("F,W,L,seed", [(12, 256, 8, 2), (12, 128, 4, 7), (16, 256, 5, 4), (0, 128, 6, 9),
+                                        (16, 512, 8, 5), (16, 512, 3, 6)])
 @pytest.mark.parametrize("n", [1, 129, 4000])
 def test_fp8_query_against_model_and_oracle(P, F, W, L, seed, n):
     blob = init_weights(F, W, L, seed=seed)
@@ -77,7 +78,7 @@ def _calibration_rays(n=8192, seed=0x43414C4942):
     return o.astype(np.float32), w.astype(np.float32)
 
 
-@pytest.mark.parametrize("F,W,L,seed", [(12, 256, 8, 2), (0, 128, 6, 9)])
+@pytest.mark.parametrize("F,W,L,seed", [(12, 256, 8, 2), (0, 128, 6, 9), (16, 512, 8, 5)])
 def test_fp8_static_scales_cover_the_activations(P, F, W, L, seed):
     """Layer 0's scale is 1/448; a hidden layer's is twice the channel's calibration maximum
     (floored at 1e-3 of the layer's maximum) / 448: compared with the FP64 column maxima on the
@@ -112,3 +113,42 @@ def test_fp8_scales_follow_set_weights(P):
     assert (s2[0] == s1[0]).all()
     r = s2[1] / s1[1]
     assert np.allclose(r, 2.0, rtol=2e-2), (r.min(), r.max())
+
+
+def test_fp8_width512_full_size_sampled(P):
+    """2^22 queries of the 102 -> 512 x 8 -> 2 network in one FP8 launch (the large-render shape):
+    2,000 sampled rows against the quantisation model and, with the error stated, the FP64 oracle;
+    normals (from the BF16 reverse pass) are unit vectors on the hit rows."""
+    F, W, L, seed = 16, 512, 8, 5
+    blob = init_weights(F, W, L, seed=seed)
+    net = P.DDFNet(F, W, L, blob, "fp8")
+    n = 1 << 22
+    g = torch.Generator(device="cuda").manual_seed(8)
+    o = torch.randn(n, 3, device="cuda", generator=g)
+    o = o / o.norm(dim=1, keepdim=True) * torch.rand(n, 1, device="cuda", generator=g)
+    w = torch.randn(n, 3, device="cuda", generator=g)
+    w = w / w.norm(dim=1, keepdim=True)
+    out = net.query(o, w, normals=True)
+    net.device_status()
+    idx = np.random.default_rng(1).choice(n, 2000, replace=False)
+    idx[:2] = [0, n - 1]
+    on, wn = o[idx].cpu().numpy(), w[idx].cpu().numpy()
+    gs = {k: v[idx].cpu().numpy() for k, v in out.items()}
+    Pm = omlp.unpack(blob, F, W, L)
+    m = query_fp8(Pm, on, wn, F, net.fp8_scales())
+    d = np.abs(gs["dist"] - m["dist"])
+    assert np.quantile(d, 0.99) <= 5e-3 and d.max() <= 3e-2, (np.quantile(d, 0.99), d.max())
+    clear = np.abs(m["logit"]) >= 0.05
+    assert (gs["hit"][clear] == m["hit"][clear]).all()
+    r = omlp.query(Pm, on, wn, F, with_normal=False)
+    err = np.abs(gs["dist"] - r["dist"])
+    print(f"FP8 102 -> 512 x 8 at 2^22 rows: |d dist| vs FP64 max {err.max():.4f} p99 {np.quantile(err, 0.99):.4f}")
+    assert err.max() <= 0.2
+    hit = gs["hit"] == 1
+    if hit.any():
+        assert np.allclose(np.linalg.norm(gs["normal"][hit], axis=1), 1.0, atol=1e-5)
+    # the same rows through the BF16 handle: both tensor-core paths agree with each other loosely
+    net.set_precision("bf16")
+    b = net.query(o, w)
+    diff = (b["dist"][torch.from_numpy(idx).cuda()].cpu().numpy() - gs["dist"])
+    assert np.abs(diff).max() <= 0.2
