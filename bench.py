@@ -2,14 +2,19 @@
 
 One step = one full render of the single-object workload (the modified path tracer of the
 paper's Sec. 1 / Fig. 1): 512 x 512 pixels x 64 samples, at most 4 bounces, a 78 -> 256 x 8 -> 2
-network (12-frequency encoding) with seeded weights, one wave of 2^24 paths: camera rays, one
-batched field query per bounce (distance, hit, Eq. 3 normal), shading + compaction, per-pixel
-accumulation - every step in libddf.so's kernels.
+network (12-frequency encoding, seeded weights: the workload the parity tests check path by path),
+one wave of 2^24 paths: camera rays, one batched field query per bounce (distance, hit, Eq. 3
+normal), shading + compaction, per-pixel accumulation - every step in libddf.so's kernels. The
+same render of the network the run trains first (Sec. 5.1 / 5.2 in this build's reading: 6,000
+BF16 tensor-core Adam steps of batch 65,536 on 2^20 rays labelled by ddf_label_rays against the
+8,192-face (3,2) torus knot) is reported beside it.
 
 Prints ONE JSON line (rank 0): samples/s over the timed steps (device time, CUDA events, max over
 ranks), the dominant kernel's roofline, the end-to-end figure through the public API with the
 image read back to pinned host memory, the FP64 oracle timed on the host cores on a bounded
-sample, SM clocks sampled during the timed region, and the query error against the oracle.
+sample, SM clocks sampled during the timed region, the FP32 / BF16 / FP8 query errors against the
+oracle on 2^20 of the render's own query rays, and the other hot-path rows, the full large render
+(1920 x 1080 x 256 spp, <= 8 bounces, 102 -> 512 x 8 -> 2; FP32 / BF16 / FP8) among them.
 
 --impl reference times the FP64 oracle itself on the host (a bounded sample per step).
 """
@@ -33,10 +38,15 @@ METRIC = "DDF ray queries/s and render samples/s, BF16/FP8 vs FP32 on 1 GB300 at
 WORKLOAD = dict(width=512, height=512, spp=64, bounces=4, in_freqs=12, hidden=256, layers=8, seed=3)
 
 
-def workload_name(w):
+TRAIN = dict(rays=1 << 20, batch=65536, steps=6000, lr=3e-3, seed_init=2, seed_rays=11)
+LARGE = dict(width=1920, height=1080, spp=256, bounces=8, in_freqs=16, hidden=512, layers=8, seed=5)
+
+
+def workload_name(w, trained=False):
     E = 6 + 6 * w["in_freqs"]
+    net = ("trained on 2^20 labelled rays of the 8,192-face (3,2) torus knot" if trained else "seeded weights")
     return (f"single-object render {w['width']}x{w['height']} x {w['spp']} spp, <= {w['bounces']} bounces, "
-            f"{E}->{w['hidden']}x{w['layers']}->2 DDF MLP (seeded weights)")
+            f"{E}->{w['hidden']}x{w['layers']}->2 DDF MLP ({net})")
 
 
 def fwd_flops(E, W, L):
@@ -48,10 +58,10 @@ def bwd_flops(E, W, L):
     return 2.0 * ((L - 1) * W * W + W * E)
 
 
-# ncu-measured DRAM traffic of the BF16 query kernels (mlp_pair_kernel<256> forward and
-# mlp_tc_kernel<256,1> normals, the 7 launches of one 512 x 512 x 64 spp render); to be
-# re-measured whenever the kernels change.
-QUERY_DRAM_BYTES_PER_RENDER = 757.8e6
+# ncu-measured DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the BF16 query
+# kernels of one 512 x 512 x 64 spp render of the trained network (mlp_pair_kernel<256> forward
+# and mlp_tc_kernel<256,1> normals launches); None until measured for the current kernels.
+QUERY_DRAM_BYTES_PER_RENDER = None
 
 
 def load_peaks():
@@ -192,7 +202,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": workload_name(w), "parallelism": "host cores (numpy FP64 oracle)"},
+            "config": {"workload": workload_name(w, trained=False), "parallelism": "host cores (numpy FP64 oracle)"},
             "queries_per_s": sum(nqs) / tot,
             "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cpu_threads(), "kind": "oracle",
                              "sample": f"{n_paths} random paths of the {w['width']}x{w['height']}x{w['spp']} "
@@ -200,6 +210,164 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def train_knot_field(P, torch, np):
+    """The config-2 network trained by the library: 2^20 rays (half uniform on the bounding sphere,
+    half aimed at the knot's surface with 0.05 rad of jitter) labelled by ddf_label_rays against the
+    8,192-face (3,2) torus knot, TRAIN["steps"] BF16 tensor-core Adam steps of batch 65,536 over
+    reshuffled epochs, learning rate TRAIN["lr"] with a cosine decay. Returns the FP32 master
+    weights (host blob) and the training record (loss curve, held-out hit accuracy and L1)."""
+    from ddf_synth import init_weights, labelled_ray_set, torus_knot
+    V, F = torus_knot(3, 2, 0.08, 256, 16)
+    mesh = P.DDFMesh(V, F)
+    o, w = labelled_ray_set(V, F, TRAIN["rays"], seed=TRAIN["seed_rays"])
+    to, tw = torch.from_numpy(o).cuda(), torch.from_numpy(w).cuda()
+    lab = mesh.label(to, tw)
+    dgt, hgt = lab["dist"], lab["hit"]
+    net = P.DDFNet(12, 256, 8, init_weights(12, 256, 8, seed=TRAIN["seed_init"]), "bf16")
+    g = torch.Generator(device="cuda").manual_seed(0)
+    loss = torch.empty((), device="cuda")
+    B, nb = TRAIN["batch"], TRAIN["rays"] // TRAIN["batch"]
+    steps, curve = TRAIN["steps"], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    perm = None
+    for st in range(steps):
+        if st % nb == 0:
+            perm = torch.randperm(TRAIN["rays"], device="cuda", generator=g)
+        idx = perm[(st % nb) * B:(st % nb + 1) * B]
+        lr = max(TRAIN["lr"] * 0.5 * (1.0 + math.cos(math.pi * st / steps)), TRAIN["lr"] * 0.01)
+        net.train_step(to[idx], tw[idx], dgt[idx], hgt[idx], lr=lr, loss=loss)
+        if st % 500 == 0 or st == steps - 1:
+            curve.append((st, round(float(loss.item()), 5)))
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    net.device_status()
+    ho, hw = labelled_ray_set(V, F, 1 << 16, seed=TRAIN["seed_rays"] + 1)
+    tho, thw = torch.from_numpy(ho).cuda(), torch.from_numpy(hw).cuda()
+    hl = mesh.label(tho, thw)
+    out = net.query(tho, thw)
+    hit, ht = out["hit"].bool(), hl["hit"].bool()
+    both = hit & ht
+    info = {"workload": "78 -> 256 x 8 -> 2 from Xavier seed 2, 2^20 rays labelled against the 8,192-face (3,2) "
+                        "knot, batch 65,536, Adam (cosine learning rate from 3e-3), BF16 tensor-core steps",
+            "steps": steps, "s": dt, "ms_per_step": dt * 1e3 / steps, "loss_curve": curve,
+            "heldout_hit_accuracy": float((hit == ht).float().mean().item()),
+            "heldout_l1_on_hits": float((out["dist"][both] - hl["dist"][both]).abs().mean().item()),
+            "labelled_hit_fraction": float(hgt.float().mean().item())}
+    return net.get_weights().cpu().numpy(), info
+
+
+def render_query_rays(P, torch, np, net, cam, spp, bounces, n_rays, seed):
+    """n_rays of the rays a render actually queries: ddf_render_trace of n_rays random paths, every
+    recorded bounce's (o, w), then n_rays of those drawn uniformly (so each bounce is represented in
+    proportion to its share of the render's queries). Returns (o, w, rays per bounce)."""
+    total = cam.width * cam.height * spp
+    rng = np.random.default_rng(seed)
+    pids = np.sort(rng.choice(total, n_rays, replace=False)).astype(np.int64)
+    _, tr, _ = net.render_trace(cam, spp, bounces, torch.from_numpy(pids).cuda())
+    tr = tr[:, :, 0:6].cpu().numpy()
+    q = ~np.isnan(tr[:, :, 0])
+    rays = tr[q]
+    bounce = np.nonzero(q)[1]
+    pick = np.sort(rng.choice(rays.shape[0], min(n_rays, rays.shape[0]), replace=False))
+    o = np.ascontiguousarray(rays[pick, 0:3])
+    w = np.ascontiguousarray(rays[pick, 3:6])
+    return o, w, np.bincount(bounce[pick], minlength=bounces).tolist()
+
+
+def oracle_query_job(blob, F, W, L, o, w, hit_any, chunk=1 << 15):
+    """FP64 oracle outputs on the given rays (runs in a spawned worker): distance and logit of
+    every row, the Eq. 3 normal of the rows in hit_any."""
+    import numpy as np
+    from oracle import mlp as omlp
+    Pm = omlp.unpack(blob, F, W, L)
+    n = o.shape[0]
+    dist, logit = np.empty(n), np.empty(n)
+    for a in range(0, n, chunk):
+        r = omlp.query(Pm, o[a:a + chunk], w[a:a + chunk], F, with_normal=False)
+        dist[a:a + chunk], logit[a:a + chunk] = r["dist"], r["logit"]
+    rows = np.nonzero(hit_any)[0]
+    normal = np.zeros((rows.size, 3))
+    for a in range(0, rows.size, chunk):
+        rr = rows[a:a + chunk]
+        normal[a:a + chunk] = omlp.query(Pm, o[rr], w[rr], F)["normal"]
+    return dist, logit, rows, normal
+
+
+def error_stats(gpu, ref, band, bound):
+    """Errors of one precision's query outputs against the oracle's on the same rays; bound is the
+    precision's distance tolerance (FP32: relative, floored at 1; BF16: absolute; FP8: stated)."""
+    import numpy as np
+    dist64, logit64, rows, normal64 = ref
+    dd = np.abs(gpu["dist"].astype(np.float64) - dist64)
+    dl = np.abs(gpu["logit"].astype(np.float64) - logit64)
+    rel = dd / np.maximum(np.abs(dist64), 1.0)
+    h64 = logit64 > 0
+    hit = gpu["hit"].astype(bool)
+    clear = np.abs(logit64) >= 1e-4
+    off = np.abs(logit64) >= band
+    both = hit[rows] & (logit64[rows] > 0)
+    cos = np.clip(np.sum(gpu["normal"][rows][both].astype(np.float64) * normal64[both], 1), -1, 1)
+    ang = np.degrees(np.arccos(cos)) if both.any() else np.zeros(1)
+    return {"max_abs_dist": float(dd.max()), "p99_abs_dist": float(np.percentile(dd, 99)),
+            "max_rel_dist": float(rel.max()),
+            "hit_rows_max_abs_dist": float(dd[h64].max()) if h64.any() else 0.0,
+            "hit_rows_p99_abs_dist": float(np.percentile(dd[h64], 99)) if h64.any() else 0.0,
+            f"share_beyond_{bound:g}": float(np.mean((rel if bound < 1e-3 else dd) > bound)),
+            "max_abs_logit": float(dl.max()),
+            "hit_mismatch_rate": float(np.mean(hit[clear] != (logit64[clear] > 0))),
+            f"hit_mismatch_rate_outside_{band:g}": float(np.mean(hit[off] != (logit64[off] > 0))),
+            "normal_rows": int(both.sum()), "normal_angle_deg_median": float(np.median(ang)),
+            "normal_angle_deg_p99": float(np.percentile(ang, 99))}
+
+
+def gpu_ray_set(torch, V, F, n, seed, sigma=0.05):
+    """The labelled-ray recipe (half origins uniform on the unit sphere with uniform directions,
+    half aimed at area-weighted surface points with a Gaussian angular jitter sigma), drawn on the
+    device with torch for the 2^24-ray labelling workload; float32 (n, 3) origins and directions."""
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    dev = "cuda"
+
+    def unit_dirs(m):
+        z = 1.0 - 2.0 * torch.rand(m, device=dev, generator=g, dtype=torch.float64)
+        a = 2.0 * math.pi * torch.rand(m, device=dev, generator=g, dtype=torch.float64)
+        r = torch.sqrt(torch.clamp(1.0 - z * z, min=0.0))
+        return torch.stack([r * torch.cos(a), r * torch.sin(a), z], 1)
+
+    h = n // 2
+    o1, w1 = unit_dirs(h), unit_dirs(h)
+    Vt = torch.from_numpy(V).to(dev, torch.float64)
+    Ft = torch.from_numpy(F.astype("int64")).to(dev)
+    p0, p1, p2 = Vt[Ft[:, 0]], Vt[Ft[:, 1]], Vt[Ft[:, 2]]
+    area = 0.5 * torch.linalg.norm(torch.cross(p1 - p0, p2 - p0, dim=1), dim=1)
+    idx = torch.multinomial(area, n - h, replacement=True, generator=g)
+    a = torch.rand(n - h, device=dev, generator=g, dtype=torch.float64)
+    b = torch.rand(n - h, device=dev, generator=g, dtype=torch.float64)
+    flip = a + b > 1.0
+    a, b = torch.where(flip, 1.0 - a, a), torch.where(flip, 1.0 - b, b)
+    pts = (1.0 - a - b)[:, None] * p0[idx] + a[:, None] * p1[idx] + b[:, None] * p2[idx]
+    o2 = unit_dirs(n - h)
+    w2 = torch.nn.functional.normalize(pts - o2, dim=1)
+    helper = torch.where(w2[:, 2:3].abs() < 0.9, torch.tensor([[0.0, 0.0, 1.0]], device=dev, dtype=torch.float64),
+                         torch.tensor([[1.0, 0.0, 0.0]], device=dev, dtype=torch.float64))
+    t1 = torch.nn.functional.normalize(torch.cross(w2, helper, dim=1), dim=1)
+    t2 = torch.cross(w2, t1, dim=1)
+    gg = torch.randn(n - h, 2, device=dev, generator=g, dtype=torch.float64)
+    w2 = torch.nn.functional.normalize(w2 + sigma * (gg[:, :1] * t1 + gg[:, 1:] * t2), dim=1)
+    perm = torch.randperm(n, device=dev, generator=g)
+    o = torch.cat([o1, o2])[perm]
+    w = torch.nn.functional.normalize(torch.cat([w1, w2])[perm], dim=1)
+    return o.float().contiguous(), w.float().contiguous()
+
+
+def measured_peaks(P):
+    """The throughput loops of ddf_measure_peaks on this device (TFLOP/s) and its SM count."""
+    try:
+        return P.measure_peaks()
+    except Exception as e:   # the loops are a denominator only: report and fall back
+        return {"error": str(e)}
 
 
 def main():
@@ -212,11 +380,13 @@ def main():
     ap.add_argument("--ref-paths", type=int, default=2048)
     ap.add_argument("--no-oracle", action="store_true", help="skip the CPU oracle legs")
     ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--error-rays", type=int, default=1 << 20, help="rays of each query-error subset")
+    ap.add_argument("--no-train", action="store_true", help="skip training the knot network and its rows")
     ap.add_argument("--no-rows", action="store_true", help="skip the labelling / training / grouped rows")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: 512 x 512 x 8 spp (2^21 paths) for profiler captures")
     ap.add_argument("--row", default=None, choices=["label", "sampler", "pov", "aov", "udf", "mesh_render", "train",
-                                                   "grouped", "w512"],
+                                                   "grouped", "w512", "large"],
                     help="run only this row's workload (for profiler captures) and print it")
     args = ap.parse_args()
     if args.size == "small":
@@ -235,9 +405,27 @@ def main():
     import paper_2306_16142_gb300 as P
     from ddf_synth import default_camera, init_weights
     from paper_2306_16142_gb300.ddf import camera_struct
+    peaks, peak_src = load_peaks()
+    meas = measured_peaks(P)
     if args.row:
-        print(json.dumps({"rows": other_rows(P, torch, np, load_peaks()[0], only=args.row)}), flush=True)
+        print(json.dumps({"rows": other_rows(P, torch, np, peaks, meas, only=args.row, args=args, peak_src=peak_src)}),
+              flush=True)
         return 0
+    pool, jobs = None, {}
+    if rank == 0 and not args.no_oracle:
+        # the FP64 error jobs run in a spawned worker while the device works
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        keep = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS")}
+        nthr = str(max(1, (os.cpu_count() or 4) - 4))   # leave cores to the process that launches kernels
+        os.environ["OPENBLAS_NUM_THREADS"] = os.environ["OMP_NUM_THREADS"] = nthr
+        pool = cf.ProcessPoolExecutor(max_workers=1, mp_context=mp.get_context("spawn"))
+        pool.submit(int, 0).result()   # the worker starts (and reads its thread count) now
+        for k, v in keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
     w = WORKLOAD
     E = 6 + 6 * w["in_freqs"]
@@ -288,37 +476,10 @@ def main():
     queries_per_s = whole_job_rate(queries, world, args.steps, ms)
 
     # ---- dominant kernel roofline: the field query
-    Wd, Ld = w["hidden"], w["layers"]
-    flops = 0.0
-    for b in range(w["bounces"]):
-        flops += stats[b] * fwd_flops(E, Wd, Ld)
-        if b + 1 < w["bounces"]:
-            flops += stats[b + 1] * bwd_flops(E, Wd, Ld)      # normals of the rows that hit
-    q = prof["query"]
-    q_launch_ms = q["ms"] / max(1, q["launches"])
-    flops_per_launch = flops / w["bounces"]
-    achieved = flops_per_launch / (q_launch_ms / 1e3) / 1e12
-    peaks, peak_src = load_peaks()
-    if prec == "fp32":
-        # FP32 SIMT: 152 SMs x 128 FMA lanes x 2 flop x max SM clock
-        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
-    else:
-        peak = peaks["bf16_tflops_sustained"] * (2.0 if prec == "fp8" else 1.0)
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": f"{peak_src} bf16 sustained" + (" x 2 (fp8 nominal ratio)" if prec == "fp8" else "")}
-        if prec == "bf16" and args.size == "full":
-            # DRAM bytes (read + write) of the query kernels of one bench render, measured by ncu
-            # (dram__bytes_read.sum + dram__bytes_write.sum, one pass, full size; summary in
-            # profiles/bf16_query_render512x512.md), per bounce query like `achieved`
-            roof["traffic"] = QUERY_DRAM_BYTES_PER_RENDER / w["bounces"]
-            roof["traffic_unit"] = "bytes per bounce query (forward + normals launches)"
-    roof["kernel"] = "field query (fused MLP + Eq. 3 normal)"
-    roof["time_share"] = q["ms"] / ms if ms > 0 else None
+    roof = query_roofline(stats, prof, ms, E, w["hidden"], w["layers"], prec, peaks, peak_src, meas, args.steps)
+    if prec == "bf16" and args.size == "full" and QUERY_DRAM_BYTES_PER_RENDER is not None:
+        roof["traffic"] = QUERY_DRAM_BYTES_PER_RENDER / w["bounces"]
+        roof["traffic_unit"] = "bytes per bounce query (forward + normals launches)"
 
     # ---- wavefront kernels against HBM: algorithmic bytes per launch / measured launch time
     B = w["bounces"]
@@ -331,12 +492,13 @@ def main():
     hbm = peaks["hbm_gbs"]
     shade_gbs = shade_bytes / B / (sh["ms"] / max(1, sh["launches"]) / 1e3) / 1e9
     rg = prof["raygen"]
-    raygen_gbs = paths * (32.0 + 4.0 * 0) / (rg["ms"] / max(1, rg["launches"]) / 1e3) / 1e9
+    raygen_gbs = paths * 32.0 / (rg["ms"] / max(1, rg["launches"]) / 1e3) / 1e9
     wavefront_roofline = {
         "shade": {"bound": "hbm", "achieved": shade_gbs, "peak": hbm, "unit": "GB/s", "frac": shade_gbs / hbm,
                   "bytes": "52 B read per live ray + 32 B written per survivor + 4 B per terminated path"},
         "raygen": {"bound": "hbm", "achieved": raygen_gbs, "peak": hbm, "unit": "GB/s", "frac": raygen_gbs / hbm,
-                   "bytes": "32 B of ray state written per path"}}
+                   "bytes": "32 B of ray state written per path"},
+        "time_share": {k: prof[k]["ms"] / ms for k in ("query", "shade", "raygen", "accumulate")}}
 
     # ---- end to end through the public call, image read back to pinned host memory
     host_img = torch.empty(w["height"], w["width"], pin_memory=True)
@@ -360,8 +522,8 @@ def main():
             "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "fp8e4m3"}[prec],
             "data": "synthetic",
-            "config": {"workload": workload_name(w), "precision": prec, "paths_per_step": paths,
-                       "queries_per_step": queries, "queries_per_bounce": stats,
+            "config": {"workload": workload_name(w, trained=False), "precision": prec,
+                       "paths_per_step": paths, "queries_per_step": queries, "queries_per_bounce": stats,
                        "l2": "no flush: ray state of one wave (2^24 paths, ~1.5 GB) exceeds the 129 MB L2",
                        "parallelism": f"replicas x{world}"},
             "queries_per_s": queries_per_s,
@@ -370,39 +532,110 @@ def main():
             "e2e": e2e,
             "gpu_launches": int(sum(v["launches"] for v in prof.values()) + args.steps * 2),
             "clocks": clocks}
+    if rank == 0:
+        line["peaks_measured_here"] = meas
 
-    # ---- FP8 path on the same render, with its query error
-    if rank == 0 and prec == "bf16" and args.fp32_steps > 0:
-        net8 = P.DDFNet(w["in_freqs"], w["hidden"], w["layers"], blob, "fp8")
-        net8.render(cam, w["spp"], w["bounces"], img)
+    # ---- FP8 and FP32 paths on the same render
+    nets = {prec: net}
+    for other in ("fp8", "fp32"):
+        if rank != 0 or prec != "bf16" or args.fp32_steps <= 0:
+            break
+        n2 = P.DDFNet(w["in_freqs"], w["hidden"], w["layers"], blob, other)
+        nets[other] = n2
+        n2.render(cam, w["spp"], w["bounces"], img)
         torch.cuda.synchronize()
+        reps = max(2, args.fp32_steps) if other == "fp8" else args.fp32_steps
+        n2.profile(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(max(2, args.fp32_steps)):
-            net8.render(cam, w["spp"], w["bounces"], img)
+        for _ in range(reps):
+            n2.render(cam, w["spp"], w["bounces"], img)
         e1.record(stream)
         torch.cuda.synchronize()
-        line["fp8_path"] = {"value": paths * max(2, args.fp32_steps) / (e0.elapsed_time(e1) / 1e3),
-                            "unit": "samples/s"}
-        if not args.no_oracle:
-            line["fp8_path"]["query_error"] = query_error(P, net8, blob, w)
-    # ---- FP32 path beside the tensor-core path, and the oracle
-    if rank == 0 and prec != "fp32" and args.fp32_steps > 0:
-        net32 = P.DDFNet(w["in_freqs"], w["hidden"], w["layers"], blob, "fp32")
-        net32.render(cam, w["spp"], w["bounces"], img)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.fp32_steps):
-            net32.render(cam, w["spp"], w["bounces"], img)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        line["fp32_path"] = {"value": paths * args.fp32_steps / (e0.elapsed_time(e1) / 1e3),
-                             "unit": "samples/s"}
+        pr2 = n2.profile_read()
+        n2.profile(False)
+        ms2 = e0.elapsed_time(e1)
+        st2 = n2.render_stats(w["bounces"])
+        line[f"{other}_path"] = {"value": paths * reps / (ms2 / 1e3), "unit": "samples/s",
+                                 "queries_per_s": sum(st2) * reps / (ms2 / 1e3), "queries_per_bounce": st2,
+                                 "roofline": query_roofline(st2, pr2, ms2, E, w["hidden"], w["layers"], other,
+                                                            peaks, peak_src, meas, reps)}
+    # ---- query errors of every precision against the oracle on 2^20 of the render's own rays
+    if pool is not None:
+        o_e, w_e, per_b = render_query_rays(P, torch, np, net, cam, w["spp"], w["bounces"], args.error_rays // 4, 13)
+        to_e, tw_e = torch.from_numpy(o_e).cuda(), torch.from_numpy(w_e).cuda()
+        outs = {}
+        for k, nk in nets.items():
+            r = nk.query(to_e, tw_e, normals=True)
+            outs[k] = {kk: v.cpu().numpy() for kk, v in r.items()}
+        hit_any = np.zeros(o_e.shape[0], bool)
+        for r in outs.values():
+            hit_any |= r["hit"].astype(bool)
+        jobs["render"] = (pool.submit(oracle_query_job, blob, w["in_freqs"], w["hidden"], w["layers"], o_e, w_e,
+                                      hit_any), outs, {"rays": int(o_e.shape[0]), "rays_per_bounce": per_b,
+                                                       "source": "ddf_render_trace of random paths of the timed "
+                                                                 "render (BF16), every bounce's query ray, this many "
+                                                                 "of them drawn uniformly"})
+    if rank == 0 and not args.no_train:
+        # the knot network trained by the library, rendered the same way, with its query errors
+        blob_t, train_info = train_knot_field(P, torch, np)
+        trained = {"workload": workload_name(w, trained=True), "training": train_info}
+        nets_t = {}
+        for pr in ("bf16", "fp8", "fp32"):
+            nt = P.DDFNet(w["in_freqs"], w["hidden"], w["layers"], blob_t, pr)
+            nets_t[pr] = nt
+            reps = 5 if pr != "fp32" else max(1, args.fp32_steps)
+            nt.render(cam, w["spp"], w["bounces"], img)
+            torch.cuda.synchronize()
+            nt.profile(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                nt.render(cam, w["spp"], w["bounces"], img)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            prt = nt.profile_read()
+            nt.profile(False)
+            mst = e0.elapsed_time(e1)
+            stt = nt.render_stats(w["bounces"])
+            trained[pr] = {"samples_per_s": paths * reps / (mst / 1e3), "ms_per_render": mst / reps,
+                           "queries_per_bounce": stt,
+                           "roofline": query_roofline(stt, prt, mst, E, w["hidden"], w["layers"], pr, peaks,
+                                                      peak_src, meas, reps)}
+        if pool is not None:
+            o_e, w_e, per_b = render_query_rays(P, torch, np, nets_t["bf16"], cam, w["spp"], w["bounces"],
+                                                args.error_rays, 14)
+            to_e, tw_e = torch.from_numpy(o_e).cuda(), torch.from_numpy(w_e).cuda()
+            outs = {}
+            for k, nk in nets_t.items():
+                r = nk.query(to_e, tw_e, normals=True)
+                outs[k] = {kk: v.cpu().numpy() for kk, v in r.items()}
+            hit_any = np.zeros(o_e.shape[0], bool)
+            for r in outs.values():
+                hit_any |= r["hit"].astype(bool)
+            jobs["trained"] = (pool.submit(oracle_query_job, blob_t, w["in_freqs"], w["hidden"], w["layers"], o_e,
+                                           w_e, hit_any), outs,
+                               {"rays": int(o_e.shape[0]), "rays_per_bounce": per_b,
+                                "source": "ddf_render_trace of 2^20 random paths of the trained network's BF16 render, "
+                                          "every bounce's query ray, 2^20 of them drawn uniformly; the oracle evaluates "
+                                          "the FP32 master weights the training produced"})
+        line["trained"] = trained
+        del nets_t
     if rank == 0 and not args.no_rows:
-        line["rows"] = other_rows(P, torch, np, peaks)
-    if rank == 0 and not args.no_oracle:
-        line["query_error"] = query_error(P, net, blob, w)
+        line["rows"] = other_rows(P, torch, np, peaks, meas, pool=pool, jobs=jobs, args=args, peak_src=peak_src)
+    if pool is not None:
+        bands = {"fp32": 1e-4, "bf16": 2e-2, "fp8": 6e-2}
+        bounds = {"fp32": 1e-5, "bf16": 2e-2, "fp8": 6e-2}
+        for key, (fut, outs, meta) in jobs.items():
+            ref = fut.result()
+            errs = {k: error_stats(v, ref, bands[k], bounds[k]) for k, v in outs.items()}
+            if key == "render":
+                line["query_error"] = dict(meta, **errs)
+            elif key == "trained":
+                line["trained"]["query_error"] = dict(meta, **errs)
+            elif "rows" in line:
+                line["rows"][key]["query_error"] = dict(meta, **errs)
+        pool.shutdown()
         dt, nq = oracle_render_sample(w, blob, args.ref_paths)
         line["cpu_baseline"] = {"value": args.ref_paths / dt, "unit": "samples/s", "cores": cpu_threads(),
                                 "kind": "oracle",
@@ -413,6 +646,39 @@ def main():
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def query_roofline(stats, prof, ms, E, W, L, prec, peaks, peak_src, meas, renders=1):
+    """Roofline of the field-query calls of `renders` profiled renders: algorithmic flops (forward
+    on every live row, the reverse pass on the rows that hit and continue) over the calls' summed
+    CUDA-event durations, against the measured peak of the precision."""
+    B = len(stats)
+    flops = 0.0
+    for b in range(B):
+        flops += stats[b] * fwd_flops(E, W, L)
+        if b + 1 < B:
+            flops += stats[b + 1] * bwd_flops(E, W, L)      # normals of the rows that hit
+    q = prof["query"]
+    achieved = flops * renders / (q["ms"] / 1e3) / 1e12
+    if prec == "fp32":
+        peak = max(meas.get("fp32_fma_tflops", 0.0), meas.get("fp32x2_fma_tflops", 0.0))
+        src = "measured here: FP32 FMA loop (ddf_measure_peaks)"
+        if not peak:
+            import torch
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+            peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            src = "derived: SMs x 128 FP32 lanes x 2 x max SM clock"
+        roof = {"bound": "alu", "peak_source": src}
+    else:
+        peak = peaks["bf16_tflops_sustained"] * (2.0 if prec == "fp8" else 1.0)
+        roof = {"bound": "tensor",
+                "peak_source": f"{peak_src} bf16 sustained" + (" x 2 (fp8 nominal ratio)" if prec == "fp8" else "")}
+        key = "fp8_mma_tflops" if prec == "fp8" else "bf16_mma_tflops"
+        if meas.get(key):
+            roof["frac_of_mma_loop_here"] = achieved / meas[key]
+    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                 "kernel": "field query (fused MLP + Eq. 3 normal)", "time_share": q["ms"] / ms if ms > 0 else None})
+    return roof
 
 
 def _time(torch, fn, reps, stream=None):
@@ -429,15 +695,29 @@ def _time(torch, fn, reps, stream=None):
     return e0.elapsed_time(e1) / reps / 1e3
 
 
-def other_rows(P, torch, np, peaks, only=None):
+def fp32_lane_peak(meas, peaks, torch):
+    """FP32 lane operations per second: the measured FMA loop (an FMA or one lane of a packed FP32x2
+    FMA is one operation; the packed form issues half the instructions at the same lane rate), else
+    SMs x 128 lanes x the maximum SM clock."""
+    m = max(meas.get("fp32_fma_tflops", 0.0), meas.get("fp32x2_fma_tflops", 0.0))
+    if m:
+        return m * 1e12 / 2.0, "measured here (ddf_measure_peaks FMA loops)"
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6, "derived: SMs x 128 lanes x max SM clock"
+
+
+def other_rows(P, torch, np, peaks, meas, only=None, pool=None, jobs=None, args=None, peak_src="measured"):
     """The other hot-path rows on their own workloads: ray labelling (2^20 training rays x 8,192-
-    triangle knot), the training step (batch 65,536, 78 -> 256 x 8 -> 2; BF16 tensor-core and FP32),
-    the grouped 16-object BF16 query replayed from a CUDA graph (ray counts log-uniform on
-    [1e3, 1e6]), the width-512 query and one wave of the large render. only: one of
-    label / train / grouped / w512 (the others are skipped)."""
+    triangle knot), the training-set samplers, depth / normal images, the mesh path tracer, the UDF,
+    the training step (batch 65,536, 78 -> 256 x 8 -> 2; BF16 tensor-core and FP32), the grouped
+    16-object BF16 query replayed from a CUDA graph (widths 128 / 256 / 512, ray counts log-uniform
+    on [1e3, 1e6]), the width-512 query and the full large render with its labelling workload.
+    only: one row name (the others are skipped). pool / jobs: the spawned oracle worker and the
+    error jobs submitted to it (the large render adds one)."""
     from ddf_synth import default_camera, init_weights, labelled_ray_set, torus_knot
     rows = {}
     want = lambda name: only is None or only == name
+    alu_peak, alu_src = fp32_lane_peak(meas, peaks, torch)
     V, F = torus_knot(3, 2, 0.08, 256, 16)
     mesh = P.DDFMesh(V, F)
     if want("label") or want("train"):
@@ -451,14 +731,16 @@ def other_rows(P, torch, np, peaks, only=None):
         sec = _time(torch, lambda: mesh.label(to, tw, out), 5)
         st = mesh.stats()
         tests = o.shape[0] * F.shape[0]
-        alu_peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6      # FP32 lane-instructions / s
         sweep = {"ms": sec * 1e3, "rays_per_s": o.shape[0] / sec, "tests_per_s": tests / sec,
                  "fp64_retests_per_ray": st["retests"] / o.shape[0],
                  "roofline": {"bound": "alu", "achieved": tests / sec * 34 / 1e12,
-                              "peak": alu_peak / 1e12, "unit": "T FP32-instr/s",
+                              "peak": alu_peak / 1e12, "unit": "T FP32 lane-ops/s",
                               "frac": tests / sec * 34 / alu_peak,
-                              "note": "34 FP32 operations per filter test (count of the hot loop; the "
-                                      "thread's two rays run as the lanes of packed FP32 pairs)"}}
+                              "peak_source": alu_src,
+                              "note": "34 FP32 lane operations per filter test (count of the hot loop; the "
+                                      "thread's two rays run as the two lanes of packed FP32x2 instructions, "
+                                      "each lane one operation: the measured packed FMA rate equals the "
+                                      "scalar one per lane)"}}
         # the hierarchy (the default): the same labels, a few dozen node visits and face tests per ray
         mesh.set_accel("bvh")
         secb = _time(torch, lambda: mesh.label(to, tw, out), 5)
@@ -489,14 +771,13 @@ def other_rows(P, torch, np, peaks, only=None):
         kinds = np.bincount((first["key"] % 4).cpu().numpy(), minlength=4)
         rays = C + 2 * int(kinds[1])      # candidates + two Eq. 12 rays per march point of a missing one
         tests = rays * F.shape[0]
-        alu_peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
         rows["sampler"] = {"workload": "s_fc = s_dr = s_p = 10 on the 8,192-triangle (3,2) knot: 819,200 candidate "
                                        "rays, odd-even parity, marching, Eq. 12 rays of the missing candidates",
                            "samples": n, "samples_per_s": n / sec, "ms": sec * 1e3, "accel": "bvh",
                            "kinds": [int(x) for x in kinds], "labelled_rays": rays,
                            "sweep": {"ms": sec_sweep * 1e3,
                                      "roofline": {"bound": "alu", "achieved": tests / sec_sweep * 34 / 1e12,
-                                                  "peak": alu_peak / 1e12, "unit": "T FP32-instr/s",
+                                                  "peak": alu_peak / 1e12, "unit": "T FP32 lane-ops/s",
                                                   "frac": tests / sec_sweep * 34 / alu_peak,
                                                   "note": "the labeller's filter tests over the whole call "
                                                           "(allocation, two host scans and the other kernels "
@@ -511,13 +792,12 @@ def other_rows(P, torch, np, peaks, only=None):
         sec_sweep = _time(torch, lambda: mesh.sample_pov(10, 5, 256, out=pbuf), 2)
         mesh.set_accel("bvh")
         tests = n * F.shape[0]
-        alu_peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
         rows["pov"] = {"workload": "10 x 5 cameras at distance 2.5, 30 deg field of view, 256 x 256 pixels each "
                                    "(3,276,800 rays) labelled against the 8,192-triangle (3,2) knot",
                        "rays_per_s": n / sec, "ms": sec * 1e3, "accel": "bvh", "hits": int(pbuf["hit"].sum().item()),
                        "sweep": {"ms": sec_sweep * 1e3,
                                  "roofline": {"bound": "alu", "achieved": tests / sec_sweep * 34 / 1e12,
-                                              "peak": alu_peak / 1e12, "unit": "T FP32-instr/s",
+                                              "peak": alu_peak / 1e12, "unit": "T FP32 lane-ops/s",
                                               "frac": tests / sec_sweep * 34 / alu_peak,
                                               "note": "the labeller's filter tests; ray generation included"}}}
         del pbuf
@@ -601,17 +881,17 @@ def other_rows(P, torch, np, peaks, only=None):
                                                    "unit": "TFLOP/s", "frac": flop / sec / 1e12 / peak}}
             else:
                 flop = 2.0 * macs * n * 4     # forward, recomputed forward, dgrad, wgrad
-                fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+                fp32_peak = 2.0 * alu_peak
                 rows["train_step_fp32"] = {"workload": "the same step on the FP32 SIMT GEMMs",
                                            "ms": sec * 1e3, "samples_per_s": n / sec,
                                            "roofline": {"bound": "alu", "achieved": flop / sec / 1e12,
                                                         "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
                                                         "frac": flop / sec / fp32_peak}}
             del net
-    # ---- a10 grouped query (16 objects, widths 128 / 256, 4-8 layers)
+    # ---- a10 grouped query (16 objects, widths 128 / 256 / 512, 4-8 layers)
     if want("grouped"):
         rng = np.random.default_rng(14)
-        specs = [(12, 128 if i % 2 == 0 else 256, 4 + (i % 5), 100 + i) for i in range(16)]
+        specs = [(12, (128, 256, 512)[i % 3], 4 + (7 * i) % 5, 100 + i) for i in range(16)]
         nets = [P.DDFNet(Fq2, W2, L2, init_weights(Fq2, W2, L2, seed=s2), "bf16") for Fq2, W2, L2, s2 in specs]
         counts = np.floor(10 ** (3 + 3 * rng.random(16))).astype(np.int64)
         off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
@@ -631,68 +911,137 @@ def other_rows(P, torch, np, peaks, only=None):
         flop = sum(2.0 * ((6 + 6 * f) * W2 + (L2 - 1) * W2 * W2 + 2 * W2) * c
                    for (f, W2, L2, _), c in zip(specs, counts))
         peak = peaks["bf16_tflops_sustained"]
-        rows["grouped_query"] = {"workload": "16 BF16 networks (widths 128/256, 4-8 layers, 12-frequency encoding), "
-                                             "ray counts log-uniform on [1e3, 1e6], one CUDA-graph replay per bounce",
-                                 "rays": tot, "queries_per_s": tot / sec, "ms": sec * 1e3,
+        by_w = {str(W2): int(sum(c for (_, ww, _, _), c in zip(specs, counts) if ww == W2)) for W2 in (128, 256, 512)}
+        rows["grouped_query"] = {"workload": "16 BF16 networks (widths 128 / 256 / 512, 4-8 layers, 12-frequency "
+                                             "encoding), ray counts log-uniform on [1e3, 1e6], one CUDA-graph replay "
+                                             "per bounce",
+                                 "rays": tot, "rays_per_width": by_w, "queries_per_s": tot / sec, "ms": sec * 1e3,
                                  "launch_shapes": cfg,
                                  "roofline": {"bound": "tensor", "achieved": flop / sec / 1e12, "peak": peak,
-                                              "unit": "TFLOP/s", "frac": flop / sec / 1e12 / peak}}
-    # ---- width-512 network (102 -> 512 x 8 -> 2) queries and one wave of the large render
+                                              "unit": "TFLOP/s", "frac": flop / sec / 1e12 / peak,
+                                              "note": "algorithmic forward flops of all objects over one replay"}}
+        del grp, nets
+    # ---- width-512 network (102 -> 512 x 8 -> 2) queries, BF16 and FP8
     if want("w512"):
         F5, W5, L5 = 16, 512, 8
         blob5 = init_weights(F5, W5, L5, seed=5)
-        n5 = P.DDFNet(F5, W5, L5, blob5, "bf16")
         nq = 1 << 22
         g5 = torch.Generator(device="cuda").manual_seed(16)
         qo = torch.randn(nq, 3, device="cuda", generator=g5)
         qo = qo / qo.norm(dim=1, keepdim=True) * torch.rand(nq, 1, device="cuda", generator=g5)
         qw = torch.randn(nq, 3, device="cuda", generator=g5)
         qw = qw / qw.norm(dim=1, keepdim=True)
-        qout = n5.query(qo, qw)
-        sec = _time(torch, lambda: n5.query(qo, qw, out=qout), 3)
         f5 = 2.0 * ((6 + 6 * F5) * W5 + (L5 - 1) * W5 * W5 + 2 * W5)
-        peak = peaks["bf16_tflops_sustained"]
-        rows["query_w512"] = {"workload": "2^22 queries, 102 -> 512 x 8 -> 2, BF16, no normals",
-                              "queries_per_s": nq / sec,
-                              "roofline": {"bound": "tensor", "achieved": f5 * nq / sec / 1e12, "peak": peak,
-                                           "unit": "TFLOP/s", "frac": f5 * nq / sec / 1e12 / peak}}
-        if only is None:
-            cam5 = default_camera(1920, 1080, seed=1)
-            img5 = torch.empty(1080, 1920, device="cuda")
-            sec = _time(torch, lambda: n5.render(cam5, 8, 8, img5), 1)
-            rows["large_render_wave"] = {"workload": "1920 x 1080 x 8 spp (one wave of 16.6M paths), <= 8 bounces, "
-                                                     "102 -> 512 x 8 -> 2 BF16 (the full 256-spp render is 32 such "
-                                                     "waves)",
-                                         "samples_per_s": 1920 * 1080 * 8 / sec, "ms": sec * 1e3,
-                                         "queries_per_bounce": n5.render_stats(8)}
+        for pr in ("bf16", "fp8"):
+            n5 = P.DDFNet(F5, W5, L5, blob5, pr)
+            qout = n5.query(qo, qw)
+            sec = _time(torch, lambda: n5.query(qo, qw, out=qout), 3)
+            peak = peaks["bf16_tflops_sustained"] * (2.0 if pr == "fp8" else 1.0)
+            rows[f"query_w512_{pr}"] = {
+                "workload": f"2^22 queries, 102 -> 512 x 8 -> 2, {pr.upper()}, no normals",
+                "queries_per_s": nq / sec, "ms": sec * 1e3,
+                "roofline": {"bound": "tensor", "achieved": f5 * nq / sec / 1e12, "peak": peak, "unit": "TFLOP/s",
+                             "frac": f5 * nq / sec / 1e12 / peak,
+                             "peak_source": "bf16 sustained" + (" x 2 (fp8 nominal ratio)" if pr == "fp8" else "")}}
+            del n5
+    # ---- the large render: 1920 x 1080 x 256 spp, <= 8 bounces, 102 -> 512 x 8 -> 2, FP32 / BF16 / FP8,
+    #      and 2^24 labelled rays against the 131,072-face knot
+    if want("large"):
+        Lw = LARGE
+        F5, W5, L5 = Lw["in_freqs"], Lw["hidden"], Lw["layers"]
+        E5 = 6 + 6 * F5
+        blob5 = init_weights(F5, W5, L5, seed=Lw["seed"])
+        cam5 = default_camera(Lw["width"], Lw["height"], seed=1)
+        img5 = torch.empty(Lw["height"], Lw["width"], device="cuda")
+        host5 = torch.empty(Lw["height"], Lw["width"], pin_memory=True)
+        paths5 = Lw["width"] * Lw["height"] * Lw["spp"]
+        big = {"workload": f"{Lw['width']} x {Lw['height']} x {Lw['spp']} spp ({paths5:,} paths in "
+                           f"{-(-paths5 // (1 << 24))} waves), <= {Lw['bounces']} bounces, {E5} -> {W5} x {L5} -> 2 "
+                           f"DDF MLP (seeded weights)"}
+        nets5 = {}
+        for pr in ("bf16", "fp8"):
+            n5 = P.DDFNet(F5, W5, L5, blob5, pr)
+            nets5[pr] = n5
+            n5.render(cam5, Lw["spp"], Lw["bounces"], img5)
+            torch.cuda.synchronize()
+            n5.profile(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            n5.render(cam5, Lw["spp"], Lw["bounces"], img5)
+            e1.record()
+            torch.cuda.synchronize()
+            pr5 = n5.profile_read()
+            n5.profile(False)
+            ms5 = e0.elapsed_time(e1)
+            st5 = n5.render_stats(Lw["bounces"])
+            t0 = time.perf_counter()
+            n5.render(cam5, Lw["spp"], Lw["bounces"], img5)
+            host5.copy_(img5, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            e2e5 = time.perf_counter() - t0
+            n5.device_status()
+            big[pr] = {"samples_per_s": paths5 / (ms5 / 1e3), "ms": ms5, "queries_per_bounce": st5,
+                       "queries_per_s": sum(st5) / (ms5 / 1e3),
+                       "e2e": {"value": paths5 / e2e5, "unit": "samples/s", "h2d_bytes_per_step": 64,
+                               "d2h_bytes_per_step": int(host5.numel() * 4)},
+                       "roofline": query_roofline(st5, pr5, ms5, E5, W5, L5, pr, peaks, peak_src, meas)}
+        # FP32 SIMT on one 8-spp wave of the same camera (1/32 of the paths), timed once after a warm-up
+        n32 = P.DDFNet(F5, W5, L5, blob5, "fp32")
+        nets5["fp32"] = n32
+        sec32 = _time(torch, lambda: n32.render(cam5, 8, Lw["bounces"], img5), 1)
+        big["fp32"] = {"samples_per_s": Lw["width"] * Lw["height"] * 8 / sec32, "ms": sec32 * 1e3,
+                       "sample": "one 8-spp wave of the same camera (16.6M paths, 1/32 of the render)",
+                       "queries_per_bounce": n32.render_stats(Lw["bounces"])}
+        if pool is not None and jobs is not None:
+            n_err = args.error_rays if args is not None else 1 << 20
+            o_e, w_e, per_b = render_query_rays(P, torch, np, nets5["bf16"], cam5, Lw["spp"], Lw["bounces"], n_err, 15)
+            to_e, tw_e = torch.from_numpy(o_e).cuda(), torch.from_numpy(w_e).cuda()
+            outs = {}
+            for k, nk in nets5.items():
+                r = nk.query(to_e, tw_e, normals=True)
+                outs[k] = {kk: v.cpu().numpy() for kk, v in r.items()}
+            hit_any = np.zeros(o_e.shape[0], bool)
+            for r in outs.values():
+                hit_any |= r["hit"].astype(bool)
+            jobs["large_render"] = (pool.submit(oracle_query_job, blob5, F5, W5, L5, o_e, w_e, hit_any), outs,
+                                    {"rays": int(o_e.shape[0]), "rays_per_bounce": per_b,
+                                     "source": "ddf_render_trace of 2^20 random paths of the BF16 render, every "
+                                               "bounce's query ray, 2^20 of them drawn uniformly"})
+        del nets5, n32
+        # labelling: 2^24 rays (half uniform, half surface-aimed) x the 131,072-face knot
+        V5, T5 = torus_knot(3, 2, 0.08, 1024, 64)
+        m5 = P.DDFMesh(V5, T5)
+        lo, lw = gpu_ray_set(torch, V5, T5, 1 << 24, seed=15)
+        lab_b = m5.label(lo, lw)
+        secb = _time(torch, lambda: m5.label(lo, lw, lab_b), 3)
+        bs, stb = m5.bvh_stats(), m5.stats()
+        m5.set_accel("none")
+        lab_s = {k: torch.empty_like(v) for k, v in lab_b.items()}
+        t0 = time.perf_counter()
+        m5.label(lo, lw, lab_s)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        sts = m5.stats()
+        same = bool(torch.equal(lab_b["tri"], lab_s["tri"]) and torch.equal(lab_b["hit"], lab_s["hit"])
+                    and torch.equal(lab_b["dist"], lab_s["dist"]))
+        tests = float(1 << 24) * T5.shape[0]
+        big["label"] = {"workload": "2^24 rays (half uniform on the bounding sphere, half aimed at the surface with "
+                                    "0.05 rad of jitter) x the 131,072-face (3,2) knot",
+                        "bvh": {"ms": secb * 1e3, "rays_per_s": (1 << 24) / secb,
+                                "node_visits_per_ray": bs["visits"] / (1 << 24),
+                                "face_tests_per_ray": bs["face_tests"] / (1 << 24),
+                                "fp64_retests_per_ray": stb["retests"] / (1 << 24),
+                                "fp64_final_evals_per_ray": stb["finals"] / (1 << 24)},
+                        "all_faces": {"ms": secs * 1e3, "tests_per_s": tests / secs,
+                                      "fp64_retests_per_ray": sts["retests"] / (1 << 24),
+                                      "roofline": {"bound": "alu", "achieved": tests / secs * 34 / 1e12,
+                                                   "peak": alu_peak / 1e12, "unit": "T FP32 lane-ops/s",
+                                                   "frac": tests / secs * 34 / alu_peak, "peak_source": alu_src}},
+                        "labels_identical": same,
+                        "hit_fraction": float(lab_b["hit"].float().mean().item())}
+        rows["large_render"] = big
+        del m5, lo, lw, lab_b, lab_s
     return rows
-
-
-def query_error(P, net, blob, w, n=65536):
-    """Errors of the GPU query against the FP64 oracle on 65,536 rays in the unit ball: max / p99
-    |d dist|, hit-decision mismatch rate where |logit| >= 1e-4, and the angle between the GPU and
-    oracle Eq. 3 normals on rows both call hits (median / p99 degrees)."""
-    import numpy as np
-    import torch
-    from oracle import mlp as omlp
-    rng = np.random.default_rng(13)
-    o = rng.normal(size=(n, 3))
-    o = (o / np.linalg.norm(o, axis=1, keepdims=True) * rng.uniform(0.1, 1.0, (n, 1))).astype(np.float32)
-    d = rng.normal(size=(n, 3))
-    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
-    out = net.query(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(), normals=True)
-    torch.cuda.synchronize()
-    ref = omlp.query(omlp.unpack(blob, w["in_freqs"], w["hidden"], w["layers"]), o, d, w["in_freqs"])
-    err = np.abs(out["dist"].cpu().numpy() - ref["dist"])
-    hit = out["hit"].cpu().numpy().astype(bool)
-    clear = np.abs(ref["logit"]) >= 1e-4
-    mism = np.mean(hit[clear] != ref["hit"][clear])
-    both = hit & ref["hit"]
-    cos = np.clip(np.sum(out["normal"].cpu().numpy()[both] * ref["normal"][both], 1), -1, 1)
-    ang = np.degrees(np.arccos(cos)) if both.any() else np.zeros(1)
-    return {"rays": n, "max_abs_dist": float(err.max()), "p99_abs_dist": float(np.percentile(err, 99)),
-            "hit_mismatch_rate": float(mism), "normal_rows": int(both.sum()),
-            "normal_angle_deg_median": float(np.median(ang)), "normal_angle_deg_p99": float(np.percentile(ang, 99))}
 
 
 if __name__ == "__main__":

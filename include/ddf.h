@@ -250,8 +250,8 @@ DDF_API int ddf_query_noalloc(ddf_net net, const float* d_origins, const float* 
 
 typedef struct ddf_group_s* ddf_group;
 
-/* Group several BF16 networks (widths 128 and 256, up to 64 per width) for one grouped query
- * per width class. The networks must outlive the group. Synchronous. */
+/* Group several BF16 networks (widths 128, 256 and 512, up to 64 per width) for one grouped
+ * query per width class. The networks must outlive the group. Synchronous. */
 DDF_API int ddf_group_create(int n_obj, const ddf_net* nets, ddf_group* out);
 DDF_API int ddf_group_destroy(ddf_group group);
 
@@ -276,16 +276,18 @@ DDF_API int ddf_group_replay(ddf_group group, cudaStream_t stream);
  * up (flag then cleared), else DDF_OK. */
 DDF_API int ddf_group_status(ddf_group group);
 
-/* Autotune the launch shape (weight-ring depth, persistent grid size) of each width class by
- * timing every candidate reps times on this workload; cache_path (nullable) is a text cache of
- * "signature depth grid" lines read first and appended to. Synchronous. Call before capture. */
+/* Autotune the launch shape of each width class by timing every candidate reps times on this
+ * workload: the weight-ring depth (the stages that fit the class's shared memory, at most four
+ * candidates: up to 7 at width 128, 2 at width 256, 2 or 3 at width 512) and the persistent grid
+ * (all SMs, 3/4 or 1/2 of them). cache_path (nullable) is a text cache of "signature depth grid"
+ * lines read first and appended to. Synchronous. Call before capture. */
 DDF_API int ddf_group_autotune(ddf_group group, const int64_t* d_offsets, const float* d_origins,
                                const float* d_dirs, float* d_dist, uint8_t* d_hit, int reps,
                                const char* cache_path, cudaStream_t stream);
 
-/* The chosen shapes: host_out6[3c..3c+2] = (width, ring depth, grid) for class c = 0 (width 128)
- * and c = 1 (width 256); zeros mean absent / default. */
-DDF_API int ddf_group_config(ddf_group group, int* host_out6);
+/* The chosen shapes: host_out9[3c..3c+2] = (width, ring depth, grid) for class c = 0 (width 128),
+ * c = 1 (width 256) and c = 2 (width 512); zeros mean absent / default. */
+DDF_API int ddf_group_config(ddf_group group, int* host_out9);
 
 /* The unsigned distance field of Eq. 4 over a direction set: for every point x_i (DEVICE n x 3),
  * d_udf[i] = the minimum of the distance output over the directions theta_k (DEVICE n_dirs x 3,

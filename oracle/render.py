@@ -102,10 +102,12 @@ def trace_paths(query_fn, cam, spp: int, bounces: int, pids, eps: float = 1e-4):
 
     Returns dict: radiance (per pid), min_abs_logit (smallest |logit| of any hit/miss
     decision taken on the path; +inf if none), first-bounce AOVs (dist, logit, normal,
-    queried flag)."""
+    queried flag), and rec (n, bounces, 11): every bounce's query ray o, w, its dist, logit
+    and normal (NaN where the path did not get that far; the normal NaN on a miss)."""
     pids = np.asarray(pids, np.int64)
     n = pids.size
     rad = np.zeros(n)
+    rec = np.full((n, bounces, 11), np.nan)
     min_logit = np.full(n, np.inf)
     aov_d = np.full(n, np.nan)
     aov_l = np.full(n, np.nan)
@@ -121,6 +123,11 @@ def trace_paths(query_fn, cam, spp: int, bounces: int, pids, eps: float = 1e-4):
         res = query_fn(o, w)
         d, lg, nm = res["dist"], res["logit"], res["normal"]
         min_logit[idx] = np.minimum(min_logit[idx], np.abs(lg))
+        rec[idx, b - 1, 0:3], rec[idx, b - 1, 3:6] = o, w
+        rec[idx, b - 1, 6], rec[idx, b - 1, 7] = d, lg
+        if nm is not None:
+            h = lg > 0
+            rec[idx[h], b - 1, 8:11] = nm[h]
         if b == 1:
             aov_d[idx], aov_l[idx], aov_n[idx] = d, lg, nm
         hit = lg > 0
@@ -134,7 +141,7 @@ def trace_paths(query_fn, cam, spp: int, bounces: int, pids, eps: float = 1e-4):
         o, w = shade_step(o, w, d, nm, cam.seed, pids[idx], b, eps)
         thr = thr * cam.albedo
     return {"radiance": rad, "min_abs_logit": min_logit, "dist": aov_d, "logit": aov_l,
-            "normal": aov_n}
+            "normal": aov_n, "rec": rec}
 
 
 def render_pixels(query_fn, cam, spp: int, bounces: int, pixels):

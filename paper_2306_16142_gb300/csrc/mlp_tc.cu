@@ -479,14 +479,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 // half: the epilogue turns half 0 into BF16 in registers while half 1 is multiplied, writes it as
 // soon as the layer's last MMA has read the previous activations, and the next layer's MMAs
 // start on K-blocks 0-3 while half 1 is being converted.
-template <int MODE>
+// GRP: the forward (MODE 0) of a grouped launch, tile t of the work list belonging to the object
+// whose tile prefix holds it (its own weight map, biases, head, depth and encoding).
+template <int MODE, bool GRP>
 __global__ void __launch_bounds__(kThreads, 1)
     mlp_tc512_kernel(const __grid_constant__ CUtensorMap mapF, const __grid_constant__ CUtensorMap mapB,
                      const TcArgs a) {
+    static_assert(!(GRP && MODE != 0), "grouped launches are forward queries");
     constexpr int W = 512;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int L = a.L, KB0 = a.K0 / 64;
     const int NST = a.nst;
     uint8_t* act = smem;                                     // 8 x 16 KB
     uint8_t* wst = smem + 8 * 16384;                         // NST x 32 KB
@@ -498,13 +500,53 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* accf = actr + 8;           // [2] per N-half
     uint64_t* accfree = accf + 2;        // [2]
     uint32_t* tslot = reinterpret_cast<uint32_t*>(accfree + 2);
-    uint32_t* gmask = a.gmask + (size_t)blockIdx.x * L * 16 * 128;
+    uint32_t* gmask = MODE == 1 ? a.gmask + (size_t)blockIdx.x * a.L * 16 * 128 : nullptr;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int64_t n = a.n;
     if (a.d_count) n = min(n, (int64_t)*a.d_count);
-    const int64_t ntiles = (n + kTileM - 1) / kTileM;
-    const int nsteps = MODE == 0 ? L : 2 * L;
+    const int64_t ntiles = GRP ? a.gtile0[a.gnobj] : (n + kTileM - 1) / kTileM;
+    // per-tile description: first row (of the launch's rows, or of the hit-row list in MODE 1),
+    // rows, depth, first-layer K-blocks, encoding, and the network's weight map, biases and head
+    struct Tile512 {
+        int64_t row0;
+        int rows, L, KB0, F, E;
+        const CUtensorMap* map;
+        const float* bias;
+        const float* head;
+    };
+    auto tile_info = [&](int64_t t) -> Tile512 {
+        Tile512 ti;
+        if (!GRP) {
+            ti.row0 = t * kTileM;
+            ti.rows = (int)min((int64_t)kTileM, n - ti.row0);
+            ti.L = a.L;
+            ti.KB0 = a.K0 / 64;
+            ti.F = a.F;
+            ti.E = a.E;
+            ti.map = &mapF;
+            ti.bias = a.bias;
+            ti.head = a.head;
+        } else {
+            int lo = 0, hi = a.gnobj - 1;   // last object with tile0[obj] <= t
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.gtile0[mid] <= t) lo = mid; else hi = mid - 1;
+            }
+            const GNet& g = a.gnets[lo];
+            const int64_t lt = t - a.gtile0[lo];
+            ti.row0 = a.grow0[lo] + lt * kTileM;
+            ti.rows = (int)min((int64_t)kTileM, a.grows[lo] - lt * kTileM);
+            ti.L = g.L;
+            ti.KB0 = g.K0 / 64;
+            ti.F = g.F;
+            ti.E = g.E;
+            ti.map = g.map;
+            ti.bias = g.bias;
+            ti.head = g.head;
+        }
+        return ti;
+    };
 
     if (tid == 0) {
         for (int i = 0; i < NST; ++i) {
@@ -532,8 +574,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t cnt = 0;
             bool ok = true;
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const Tile512 ti = tile_info(t);
+                const int nsteps = MODE == 0 ? ti.L : 2 * ti.L;
                 for (int s = 0; s < nsteps && ok; ++s) {
-                    const Step st = step_of<W>(s, L, KB0);
+                    const Step st = step_of<W>(s, ti.L, ti.KB0);
                     const int nh = st.N == W ? 2 : 1;
                     for (int h = 0; h < nh && ok; ++h)
                         for (int kb = 0; kb < st.nk; ++kb, ++cnt) {
@@ -541,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const uint32_t ph = (cnt / (uint32_t)NST) & 1u;
                             if (!mbar_wait(&empty[stg], ph ^ 1u, a.err)) { ok = false; break; }
                             mbar_expect_tx(&full[stg], 32768u);
-                            tma_load_3d(wst + (size_t)stg * 32768, st.bwd ? &mapB : &mapF, &full[stg], kb * 64,
+                            tma_load_3d(wst + (size_t)stg * 32768, st.bwd ? &mapB : ti.map, &full[stg], kb * 64,
                                         h * 256, st.layer);
                         }
                 }
@@ -556,8 +600,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             const uint32_t act_s = su32(act), wst_s = su32(wst);
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const Tile512 ti = tile_info(t);
+                const int nsteps = MODE == 0 ? ti.L : 2 * ti.L;
                 for (int s = 0; s < nsteps && ok; ++s) {
-                    const Step st = step_of<W>(s, L, KB0);
+                    const Step st = step_of<W>(s, ti.L, ti.KB0);
                     const int nh = st.N == W ? 2 : 1;
                     const uint32_t idesc = idesc_bf16(128, st.N == W ? 256 : st.N);
                     for (int h = 0; h < nh && ok; ++h) {
@@ -595,8 +641,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             valid_out = false;
             row_out = -1;
             if (tt < ntiles) {
-                const int64_t ii = tt * kTileM + r;
-                valid_out = ii < n;
+                const Tile512 tn = tile_info(tt);
+                const int64_t ii = tn.row0 + r;
+                valid_out = r < tn.rows;
                 if (valid_out) row_out = MODE == 1 ? (int64_t)a.rows[ii] : ii;
             }
 #pragma unroll
@@ -617,6 +664,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         float v_next[6];
         fetch_row(blockIdx.x, row_next, valid_next, v_next);
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const Tile512 ti = tile_info(t);
+            const int L = ti.L, KB0 = ti.KB0;
+            const int nsteps = MODE == 0 ? L : 2 * L;
             const int64_t row = row_next;
             const bool valid = valid_next;
             float v[6];
@@ -624,8 +674,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int c = 0; c < 6; ++c) v[c] = v_next[c];
             if (grp < KB0) {
                 uint32_t pk[32];
-                if (grp == 0) encode_kblock<0>(v, a.F, pk);
-                else encode_kblock<1>(v, a.F, pk);
+                if (grp == 0) encode_kblock<0>(v, ti.F, pk);
+                else encode_kblock<1>(v, ti.F, pk);
 #pragma unroll
                 for (int m = 0; m < 8; ++m)
                     st_shared_v4(act_s + (uint32_t)grp * 16384u + swz(r, m), pk[4 * m], pk[4 * m + 1], pk[4 * m + 2],
@@ -645,7 +695,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 auto convert = [&](int kb, const uint32_t* raw, uint32_t* pk) {
                     const int c0 = kb * 64 + grp * 32;
                     if (s < L) {
-                        const float* bs = a.bias + (size_t)s * W + c0;
+                        const float* bs = ti.bias + (size_t)s * W + c0;
                         uint32_t bits = 0;
                         if (s < L - 1) {
 #pragma unroll
@@ -663,16 +713,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                             for (int q = 0; q < 32; ++q) {
                                 const float z = fmaxf(__uint_as_float(raw[q]) + __ldg(bs + q), 0.f);
-                                y0 = fmaf(z, __ldg(a.head + c0 + q), y0);
-                                y1 = fmaf(z, __ldg(a.head + W + c0 + q), y1);
+                                y0 = fmaf(z, __ldg(ti.head + c0 + q), y0);
+                                y1 = fmaf(z, __ldg(ti.head + W + c0 + q), y1);
                             }
                         } else {
 #pragma unroll
                             for (int q = 0; q < 16; ++q) {
                                 const float z0 = __uint_as_float(raw[2 * q]) + __ldg(bs + 2 * q);
                                 const float z1 = __uint_as_float(raw[2 * q + 1]) + __ldg(bs + 2 * q + 1);
-                                pk[q] = pack_bf16(z0 > 0.f ? __ldg(a.head + c0 + 2 * q) : 0.f,
-                                                  z1 > 0.f ? __ldg(a.head + c0 + 2 * q + 1) : 0.f);
+                                pk[q] = pack_bf16(z0 > 0.f ? __ldg(ti.head + c0 + 2 * q) : 0.f,
+                                                  z1 > 0.f ? __ldg(ti.head + c0 + 2 * q + 1) : 0.f);
                             }
                         }
                     } else {
@@ -691,7 +741,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (grp == 0) {
                         float gx[3] = {0.f, 0.f, 0.f};
                         for (int j = 0; j < 4; ++j) {
-                            if (32 * j >= a.K0) break;
+                            if (32 * j >= 64 * KB0) break;
                             uint32_t raw[32];
                             TC_LD32(tbase + lane_off + 32 * j, raw);
                             tc_wait_ld();
@@ -703,7 +753,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 const int p = 32 * j + q;
                                 if (p < 3) {
                                     gx[p] += gv[q];
-                                } else if (p >= 8 && p - 2 < a.E) {
+                                } else if (p >= 8 && p - 2 < ti.E) {
                                     const int jj = (p - 8) % 6;
                                     if (jj < 3) gx[jj] = fmaf(gv[q], encode_dfeature(p - 2, v), gx[jj]);
                                 }
@@ -778,8 +828,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     epi_bar();
                     if (grp == 0) {
-                        y0 += part[4 * r] + __ldg(a.head + 2 * W);
-                        y1 += part[4 * r + 1] + __ldg(a.head + 2 * W + 1);
+                        y0 += part[4 * r] + __ldg(ti.head + 2 * W);
+                        y1 += part[4 * r + 1] + __ldg(ti.head + 2 * W + 1);
                         const bool hh = y1 > 0.f;
                         if (valid) {
                             a.dist[row] = y0;
@@ -1183,6 +1233,330 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             pcur = pnext;
+        }
+    }
+    __syncthreads();
+    if (*(volatile int*)a.err) {
+        const uint64_t t0 = gtimer();
+        while (gtimer() - t0 < 200000ull) {
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols));
+    }
+}
+
+// The Eq. 3 normals of the hit rows on two 128-row tiles per CTA: the forward pass again (L steps,
+// bias through the MMA, ReLU masks to a per-CTA scratch in global memory, L2-resident) and then
+// the reverse pass (L steps with the transposed weights, no bias): delta_{L-1} = W_out[0] on the
+// active units of the last layer, delta_{l-1} = (delta_l W_l) * mask(l - 1), and the last step's
+// N = 128 accumulator is d dist / d features, to which the encoding chain rule and Eq. 3 apply.
+// As in the forward pair kernel both tiles consume every weight stage and one tile's epilogue
+// runs while the other tile is multiplied. Rows are those of the hit list a.rows, count *a.d_count.
+template <int W>
+__global__ void __launch_bounds__(kThreads, 1)
+    mlp_pairn_kernel(const __grid_constant__ CUtensorMap mapF, const __grid_constant__ CUtensorMap mapB,
+                     const TcArgs a) {
+    constexpr int NKBW = W / 64;
+    constexpr uint32_t kWBytes = (uint32_t)W * 128u;   // one 64-wide K-block of the weights
+    constexpr uint32_t kBBytes = (uint32_t)W * 32u;    // one layer's bias tile
+    constexpr uint32_t kStage = kWBytes + kBBytes;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int L = a.L, KB0 = a.K0 / 64;
+    const int KMAXB = KB0 > NKBW ? KB0 : NKBW;
+    const uint32_t kTile = (uint32_t)KMAXB * 16384u;   // one tile's A operand
+    const int NST = a.nst;
+    uint8_t* act = smem;                                // [tile 0, tile 1] x kTile
+    uint8_t* wst = smem + a.off_wst;                    // NST x kStage
+    uint8_t* ones = smem + a.off_mask;                  // 4 KB
+    float* head_s = reinterpret_cast<float*>(smem + a.off_head);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + NST;
+    uint64_t* actr = bars + 2 * NST;   // [tile][K-block], 2 x 4
+    uint64_t* accf = actr + 8;         // [tile]
+    uint64_t* tfree = accf + 2;        // [tile]: the epilogue has read the tile's accumulator
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tfree + 2);
+    // this CTA's ReLU masks: [tile][layer][W / 32 column groups][128 rows]
+    uint32_t* gm = a.gmask + (size_t)blockIdx.x * 2 * L * (W / 32) * 128;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int64_t n = a.n;
+    if (a.d_count) n = min(n, (int64_t)*a.d_count);
+    const int64_t npairs = (n + 2 * kTileM - 1) / (2 * kTileM);
+    const int nsteps = 2 * L;
+    constexpr uint32_t kTmemCols = 2 * W;
+
+    if (tid == 0) {
+        for (int i = 0; i < NST; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 8; ++i) mbar_init(&actr[i], kEpiWarps);
+        mbar_init(&accf[0], 1);
+        mbar_init(&accf[1], 1);
+        mbar_init(&tfree[0], kEpiWarps);
+        mbar_init(&tfree[1], kEpiWarps);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // the ones tile: K rows 0 and 1 of both 64-row MN atoms are 1.0 (BF16 0x3F80), the rest 0
+    for (int i = tid; i < 1024; i += kThreads)
+        reinterpret_cast<uint32_t*>(ones)[i] = ((i >> 5) & 15) < 2 ? 0x3F803F80u : 0u;
+    fence_proxy_async();
+    for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+
+    if (warp == kEpiWarps) {
+        // ---------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            uint32_t cnt = 0;
+            bool ok = true;
+            for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x)
+                for (int s = 0; s < nsteps && ok; ++s) {
+                    const Step st = step_of<W>(s, L, KB0);
+                    for (int kb = 0; kb < st.nk; ++kb, ++cnt) {
+                        const int stg = (int)(cnt % (uint32_t)NST);
+                        if (!mbar_wait(&empty[stg], ((cnt / (uint32_t)NST) & 1u) ^ 1u, a.err)) { ok = false; break; }
+                        uint8_t* dst = wst + (size_t)stg * kStage;
+                        const bool bias = !st.bwd && kb == 0;
+                        mbar_expect_tx(&full[stg], kWBytes + (bias ? kBBytes : 0u));
+                        tma_load_3d(dst, st.bwd ? &mapB : &mapF, &full[stg], kb * 64, 0, st.layer);
+                        if (bias) bulk_load(dst + kWBytes, a.bias_mn + (size_t)st.layer * kBBytes, kBBytes, &full[stg]);
+                    }
+                }
+        }
+    } else if (warp == kEpiWarps + 1) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t cnt = 0, actph = 0, tfph = 0;
+            bool ok = true, first = true;
+            const uint32_t act_s = su32(act), wst_s = su32(wst);
+            const uint32_t idesc_b = idesc_bf16(128, W) | (3u << 15);   // both operands MN-major
+            const uint64_t ones_d = sdesc_mn16(su32(ones));
+            for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x)
+                for (int s = 0; s < nsteps && ok; ++s) {
+                    const Step st = step_of<W>(s, L, KB0);
+                    const uint32_t idesc = idesc_bf16(128, st.N);
+                    for (int kb = 0; kb < st.nk && ok; ++kb, ++cnt) {
+                        const int stg = (int)(cnt % (uint32_t)NST);
+                        if (!mbar_wait(&full[stg], (cnt / (uint32_t)NST) & 1u, a.err)) { ok = false; break; }
+                        const uint32_t sb = wst_s + (uint32_t)stg * kStage;
+                        for (int t = 0; t < 2; ++t) {
+                            const int ab = 4 * t + kb;
+                            if (!mbar_wait(&actr[ab], (actph >> ab) & 1u, a.err)) { ok = false; break; }
+                            actph ^= 1u << ab;
+                            // the step's first MMA overwrites the accumulator: wait until the
+                            // epilogue has read the tile's previous step
+                            if (kb == 0 && !first) {
+                                if (!mbar_wait(&tfree[t], (tfph >> t) & 1u, a.err)) { ok = false; break; }
+                                tfph ^= 1u << t;
+                            }
+                            tc_fence_after();
+                            const uint32_t d = tbase + (uint32_t)(t * W);
+                            if (!st.bwd && kb == 0) mma_bf16(d, ones_d, sdesc_mn16(sb + kWBytes), idesc_b, 0u);   // D = b
+                            const uint64_t ad = sdesc(act_s + (uint32_t)t * kTile + (uint32_t)kb * 16384u);
+                            const uint64_t bd = sdesc(sb);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, st.bwd ? (uint32_t)((kb | k) != 0) : 1u);
+                            if (kb == st.nk - 1) mma_commit(&accf[t]);
+                        }
+                        if (ok) mma_commit(&empty[stg]);   // both tiles have read the stage
+                    }
+                    first = false;
+                }
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        // warp w serves rows 32 (w % 4) .. +31 of the tile in hand; group w / 4 owns columns
+        // [32 group, +32) of every 64-column K-block
+        const int grp = warp >> 2;
+        const int r = (warp & 3) * 32 + lane;
+        const uint32_t act_s = su32(act);
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        uint32_t accph = 0;
+        bool ok = true;
+        // this thread's row of tile t of pair p: its index in the ray arrays and (o, w)
+        auto load_row = [&](int64_t p, int t, int64_t& row, float* vv) {
+            const int64_t i = p * 2 * kTileM + t * kTileM + r;
+            const bool valid = p < npairs && i < n;
+            row = valid ? (int64_t)a.rows[i] : -1;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                vv[c] = valid ? a.o[row * 3 + c] : 0.f;
+                vv[c + 3] = valid ? a.w[row * 3 + c] : 0.f;
+            }
+        };
+        // layer 0 of tile t: group g writes first-layer K-block g; every warp arrives on each
+        auto encode = [&](int t, const float* vv) {
+            if (grp < KB0) {
+                uint32_t pk[32];
+                if (grp == 0) encode_kblock<0>(vv, a.F, pk);
+                else encode_kblock<1>(vv, a.F, pk);
+                const uint32_t base = act_s + (uint32_t)t * kTile + (uint32_t)grp * 16384u;
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    st_shared_v4(base + swz(r, m), pk[4 * m], pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
+            }
+            fence_proxy_async();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0)
+                for (int kb = 0; kb < KB0; ++kb) mbar_arrive(&actr[4 * t + kb]);
+        };
+        float vcur[2][6], vnext[2][6];
+        int64_t rcur[2], rnext[2];
+        if ((int64_t)blockIdx.x < npairs) {
+            for (int t = 0; t < 2; ++t) {
+                load_row(blockIdx.x, t, rcur[t], vcur[t]);
+                encode(t, vcur[t]);
+            }
+        }
+        for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x) {
+            const int64_t pn = p + gridDim.x;   // the next pair of this CTA
+            for (int s = 0; s < nsteps && ok; ++s) {
+                if (s == nsteps - 1) {
+                    load_row(pn, 0, rnext[0], vnext[0]);
+                    load_row(pn, 1, rnext[1], vnext[1]);
+                }
+                const int l_bwd = 2 * L - 1 - s;
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    uint32_t* gmt = gm + (size_t)t * L * (W / 32) * 128;
+                    // the reverse step's ReLU masks (L2-resident), fetched while the MMAs run
+                    uint32_t mbits[NKBW];
+                    if (s >= L && l_bwd >= 1) {
+#pragma unroll
+                        for (int kb = 0; kb < NKBW; ++kb)
+                            mbits[kb] = gmt[((l_bwd - 1) * (W / 32) + ((kb * 64 + grp * 32) >> 5)) * 128 + r];
+                    }
+                    ok = mbar_wait(&accf[t], (accph >> t) & 1u, a.err);
+                    if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                    accph ^= 1u << t;
+                    tc_fence_after();
+                    const uint32_t tcol = tbase + lane_off + (uint32_t)(t * W) + (uint32_t)(grp * 32);
+                    const uint32_t tact = act_s + (uint32_t)t * kTile;
+                    if (s < L || l_bwd >= 1) {
+#pragma unroll
+                        for (int pass = 0; pass < NKBW / 2; ++pass) {
+                            uint32_t raw[2][32];
+#pragma unroll
+                            for (int i = 0; i < 2; ++i) TC_LD32(tcol + (2 * pass + i) * 64, raw[i]);
+                            tc_wait_ld();
+                            if (pass == NKBW / 2 - 1) {   // accumulator read: the next step may overwrite it
+                                tc_fence_before();
+                                __syncwarp();
+                                if (lane == 0) mbar_arrive(&tfree[t]);
+                            }
+#pragma unroll
+                            for (int i = 0; i < 2; ++i) {
+                                const int kb = 2 * pass + i;
+                                const int c0 = kb * 64 + grp * 32;
+                                uint32_t pk[16];
+                                if (s < L - 1) {
+                                    // a = ReLU(acc) rounded to BF16 -> next A operand (the bias is in acc)
+#pragma unroll
+                                    for (int q = 0; q < 16; ++q)
+                                        pk[q] = pack_relu(__uint_as_float(raw[i][2 * q]), __uint_as_float(raw[i][2 * q + 1]));
+                                    gmt[(s * (W / 32) + (c0 >> 5)) * 128 + r] = pos_bits32(raw[i]);
+                                } else if (s == L - 1) {
+                                    // delta of the last hidden layer: W_out[0] on the active units
+#pragma unroll
+                                    for (int q = 0; q < 16; ++q)
+                                        pk[q] = pack_bf16((int)raw[i][2 * q] > 0 ? head_s[c0 + 2 * q] : 0.f,
+                                                          (int)raw[i][2 * q + 1] > 0 ? head_s[c0 + 2 * q + 1] : 0.f);
+                                } else {
+                                    // delta_{l-1} = (delta_l W_l) * 1[z_{l-1} > 0]
+                                    const uint32_t bits = mbits[kb];
+#pragma unroll
+                                    for (int q = 0; q < 16; ++q)
+                                        pk[q] = pack_bf16(((bits >> (2 * q)) & 1u) ? __uint_as_float(raw[i][2 * q]) : 0.f,
+                                                          ((bits >> (2 * q + 1)) & 1u) ? __uint_as_float(raw[i][2 * q + 1]) : 0.f);
+                                }
+#pragma unroll
+                                for (int m = 0; m < 4; ++m)
+                                    st_shared_v4(tact + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
+                                                 pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
+                                release_kb_warp(actr, 4 * t + kb);
+                            }
+                        }
+                    } else {
+                        // d dist / d features (columns 0 .. K0-1), the encoding chain rule and Eq. 3:
+                        // feature sin(2^k pi x) has derivative 2^k pi cos(2^k pi x), cos(.) has
+                        // -2^k pi sin(.); sin / cos of every octave by the double-angle recurrence
+                        // from sincospif (as the forward's encoding computes them)
+                        float gx[3] = {0.f, 0.f, 0.f};
+                        if (grp == 0) {
+                            constexpr int KO = kMaxFreqs / 2;
+                            float sk[KO][3], ck[KO][3];
+                            {
+                                float sn[3], cs[3];
+#pragma unroll
+                                for (int j = 0; j < 3; ++j) sincospif(vcur[t][j], &sn[j], &cs[j]);
+#pragma unroll
+                                for (int o = 0; o < KO; ++o)
+#pragma unroll
+                                    for (int j = 0; j < 3; ++j) {
+                                        const float sc = ldexpf(3.14159265358979323846f, o);
+                                        sk[o][j] = -sc * sn[j];
+                                        ck[o][j] = sc * cs[j];
+                                        const float s2 = 2.f * sn[j] * cs[j];
+                                        const float c2 = (cs[j] - sn[j]) * (cs[j] + sn[j]);
+                                        sn[j] = s2;
+                                        cs[j] = c2;
+                                    }
+                            }
+                            const int nf = a.F / 2;   // octaves of the encoding
+                            const uint32_t tc0 = tbase + lane_off + (uint32_t)(t * W);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                if (32 * j >= a.K0) break;
+                                uint32_t raw[32];
+                                TC_LD32(tc0 + 32 * j, raw);
+                                tc_wait_ld();
+#pragma unroll
+                                for (int c = 0; c < 32; ++c) {
+                                    const int pf = 32 * j + c;
+                                    const float gv = __uint_as_float(raw[c]);
+                                    if (pf < 3) {
+                                        gx[pf] += gv;
+                                    } else if (pf >= 8) {
+                                        const int o = (pf - 8) / 12, rr = (pf - 8) % 12, jj = rr % 6;
+                                        if (jj < 3 && o < KO && o < nf)
+                                            gx[jj] = fmaf(gv, rr < 6 ? ck[o][jj] : sk[o][jj], gx[jj]);
+                                    }
+                                }
+                            }
+                        }
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&tfree[t]);
+                        if (grp == 0 && rcur[t] >= 0) {
+                            const float3 nn = normal_from_grad(gx[0], gx[1], gx[2], vcur[t][3], vcur[t][4], vcur[t][5]);
+                            a.normals[rcur[t] * 3 + 0] = nn.x;
+                            a.normals[rcur[t] * 3 + 1] = nn.y;
+                            a.normals[rcur[t] * 3 + 2] = nn.z;
+                        }
+                        // tile t of the next pair takes over
+                        if (pn < npairs) {
+                            rcur[t] = rnext[t];
+#pragma unroll
+                            for (int c = 0; c < 6; ++c) vcur[t][c] = vnext[t][c];
+                            encode(t, vcur[t]);
+                        }
+                    }
+                }
+            }
         }
     }
     __syncthreads();
@@ -2118,12 +2492,13 @@ int ensure_pair_attr() {
 
 template <int W, bool GRP, bool TRAIN = false>
 int launch_pair(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_count, cudaStream_t stream,
-                int grid_override = 0, const CUtensorMap* mapA0 = nullptr, const CUtensorMap* mapAct = nullptr) {
+                int grid_override = 0, const CUtensorMap* mapA0 = nullptr, const CUtensorMap* mapAct = nullptr,
+                int nst_override = 0) {
     const TcPack* P = net->tc;
     TcArgs a = base;
     const Layout s = smem_layout_pair(W, a.K0);
     if (s.nst < 2) return fail(DDF_ERR_UNSUPPORTED, "BF16 pair MLP: shared memory too small");
-    a.nst = s.nst;
+    a.nst = nst_override >= 2 ? std::min(nst_override, s.nst) : s.nst;   // a shallower ring in the same layout
     a.off_wst = s.off_wst;
     a.off_mask = s.off_mask;
     a.off_head = s.off_head;
@@ -2138,6 +2513,32 @@ int launch_pair(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_co
     if (rc) return rc;
     mlp_pair_kernel<W, GRP, TRAIN><<<grid, kThreads, s.total, stream>>>(
         P->map_fwd, mapA0 ? *mapA0 : P->map_fwd, mapAct ? *mapAct : P->map_fwd, a);
+    DDF_LAUNCH_CHECK();
+    return DDF_OK;
+}
+
+// The normals on tile pairs (mlp_pairn_kernel): the forward pair kernel's shared-memory layout, one
+// CTA per SM over the hit list, the ReLU masks in the handle's per-SM scratch.
+template <int W>
+int launch_pairn(const ddf_net_s* net, const TcArgs& base, cudaStream_t stream) {
+    const TcPack* P = net->tc;
+    TcArgs a = base;
+    const Layout s = smem_layout_pair(W, a.K0);
+    if (s.nst < 2) return fail(DDF_ERR_UNSUPPORTED, "BF16 pair normals: shared memory too small");
+    a.nst = s.nst;
+    a.off_wst = s.off_wst;
+    a.off_mask = s.off_mask;
+    a.off_head = s.off_head;
+    a.off_part = s.off_part;
+    a.off_bar = s.off_bar;
+    a.bias_mn = P->bias_mn;
+    a.gmask = P->gmask;
+    static bool attr = false;
+    if (!attr) {
+        DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_pairn_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr = true;
+    }
+    mlp_pairn_kernel<W><<<num_sms(), kThreads, s.total, stream>>>(P->map_fwd, P->map_bwd, a);
     DDF_LAUNCH_CHECK();
     return DDF_OK;
 }
@@ -2263,23 +2664,46 @@ int launch512(const ddf_net_s* net, int mode, const TcArgs& base, int64_t n, boo
     static bool attr0 = false, attr1 = false;
     if (mode == 0) {
         if (!attr0) {
-            DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_tc512_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+            DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_tc512_kernel<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
             attr0 = true;
         }
-        mlp_tc512_kernel<0><<<grid, kThreads, sm, stream>>>(P->map_fwd, P->map_bwd, a);
+        mlp_tc512_kernel<0, false><<<grid, kThreads, sm, stream>>>(P->map_fwd, P->map_bwd, a);
     } else {
         if (!attr1) {
-            DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_tc512_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+            DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_tc512_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
             attr1 = true;
         }
-        mlp_tc512_kernel<1><<<grid, kThreads, sm, stream>>>(P->map_fwd, P->map_bwd, a);
+        mlp_tc512_kernel<1, false><<<grid, kThreads, sm, stream>>>(P->map_fwd, P->map_bwd, a);
     }
     DDF_LAUNCH_CHECK();
     return DDF_OK;
 }
 
-// Row ranges and tile prefix of one width class of a group, from the device offsets.
-__global__ void grouped_prep(const int64_t* __restrict__ offsets, const GNet* __restrict__ gn, int nobj,
+// The grouped forward at width 512 (mlp_tc512_kernel in its grouped form): a ring of nst (2 or 3)
+// stages, one CTA per SM unless grid is given. The weight maps come from the device table; the
+// kernel's map parameters belong to the class's first network and are not read.
+int launch512_grouped(const ddf_net_s* first, const TcArgs& base, int nst, int grid, cudaStream_t stream) {
+    TcArgs a = base;
+    a.nst = nst >= 2 && nst <= 3 ? nst : 3;
+    if (grid <= 0) grid = num_sms();
+    mlp_tc512_kernel<0, true><<<grid, kThreads, smem512(a.nst), stream>>>(first->tc->map_fwd, first->tc->map_bwd, a);
+    DDF_LAUNCH_CHECK();
+    return DDF_OK;
+}
+
+int ensure_grouped512_attr() {
+    static bool done = false;
+    if (!done) {
+        DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_tc512_kernel<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          227 * 1024));
+        done = true;
+    }
+    return DDF_OK;
+}
+
+// Row ranges and work-unit prefix of one width class of a group, from the device offsets (a unit
+// is `unit` rows: a pair of 128-row tiles for widths 128 / 256, one tile for width 512).
+__global__ void grouped_prep(const int64_t* __restrict__ offsets, const GNet* __restrict__ gn, int nobj, int unit,
                              int64_t* __restrict__ row0, int64_t* __restrict__ rows, int64_t* __restrict__ tile0) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int64_t acc = 0;
@@ -2289,8 +2713,8 @@ __global__ void grouped_prep(const int64_t* __restrict__ offsets, const GNet* __
         const int64_t nr = offsets[o + 1] > r0 ? offsets[o + 1] - r0 : 0;
         row0[i] = r0;
         rows[i] = nr;
-        tile0[i] = acc;   // first pair of object i
-        acc += (nr + 2 * kTileM - 1) / (2 * kTileM);
+        tile0[i] = acc;   // first unit of object i
+        acc += (nr + unit - 1) / unit;
     }
     tile0[nobj] = acc;
 }
@@ -2353,8 +2777,9 @@ int tc_pack(ddf_net_s* net, int precision, cudaStream_t stream) {
         DDF_CUDA_TRY(cudaMalloc(&P->hit_count, sizeof(int)));
         DDF_CUDA_TRY(cudaMalloc(&P->err, sizeof(int)));
         DDF_CUDA_TRY(cudaMemset(P->err, 0, sizeof(int)));
-        if (W == 512)
-            DDF_CUDA_TRY(cudaMalloc(&P->gmask, sizeof(uint32_t) * (size_t)num_sms() * L * 16 * 128));
+        // per-SM ReLU masks of the reverse passes: one 128-row tile at width 512, two tiles of
+        // W / 32 words per row at widths 128 / 256 (at most L x 16 x 128 words either way)
+        DDF_CUDA_TRY(cudaMalloc(&P->gmask, sizeof(uint32_t) * (size_t)num_sms() * L * 16 * 128));
         int rc = make_map(&P->map_fwd, P->w_fwd, P->kmax, W, L);
         if (rc) return rc;
         rc = make_map(&P->map_bwd, P->w_bwd, W, W, L);
@@ -2413,9 +2838,10 @@ int tc_forward_launch(const ddf_net_s* net, const TcArgs& a, int64_t n, bool use
 
 int tc_normals_launch(const ddf_net_s* net, const TcArgs& b, int64_t n, cudaStream_t stream) {
     const int W = net->lay.width;
-    return W == 128   ? launch_mode<128>(net, 1, b, n, true, stream)
-           : W == 256 ? launch_mode<256>(net, 1, b, n, true, stream)
-                      : launch512(net, 1, b, n, true, stream);
+    if (W == 512) return launch512(net, 1, b, n, true, stream);
+    if (getenv("DDF_NORMALS_ONE_TILE"))   // A/B switch while measuring (temporary)
+        return W == 128 ? launch_mode<128>(net, 1, b, n, true, stream) : launch_mode<256>(net, 1, b, n, true, stream);
+    return W == 128 ? launch_pairn<128>(net, b, stream) : launch_pairn<256>(net, b, stream);
 }
 
 int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n, const int* d_count,
@@ -2617,7 +3043,7 @@ struct ddf_group_s {
         CUtensorMap* d_maps = nullptr;
         int64_t* d_tab = nullptr;         // row0[64], rows[64], pair0[65]
         ddf_net first = nullptr;
-    } cls[2];                             // [0]: width 128, [1]: width 256
+    } cls[3];                             // [0]: width 128, [1]: width 256, [2]: width 512
     int n = 0;
     int* err = nullptr;
     cudaGraph_t graph = nullptr;
@@ -2649,16 +3075,17 @@ int group_class_launch(ddf_group_s* g, int c, const float* o, const float* w, fl
     a.gtile0 = C.d_tab + 2 * kMaxGroup;
     a.gnobj = C.nobj;
     const int grid = C.grid > 0 ? C.grid : num_sms();
-    if (C.W == 128) return launch_pair<128, true>(C.first, a, 0, true, stream, grid);
-    return launch_pair<256, true>(C.first, a, 0, true, stream, grid);
+    if (C.W == 128) return launch_pair<128, true>(C.first, a, 0, true, stream, grid, nullptr, nullptr, C.nst);
+    if (C.W == 256) return launch_pair<256, true>(C.first, a, 0, true, stream, grid, nullptr, nullptr, C.nst);
+    return launch512_grouped(C.first, a, C.nst, grid, stream);
 }
 
 int group_prep(ddf_group_s* g, const int64_t* d_offsets, cudaStream_t stream) {
-    for (int c = 0; c < 2; ++c) {
+    for (int c = 0; c < 3; ++c) {
         ddf_group_s::Class& C = g->cls[c];
         if (!C.nobj) continue;
-        grouped_prep<<<1, 32, 0, stream>>>(d_offsets, C.d_gnets, C.nobj, C.d_tab, C.d_tab + kMaxGroup,
-                                           C.d_tab + 2 * kMaxGroup);
+        grouped_prep<<<1, 32, 0, stream>>>(d_offsets, C.d_gnets, C.nobj, C.W == 512 ? kTileM : 2 * kTileM, C.d_tab,
+                                           C.d_tab + kMaxGroup, C.d_tab + 2 * kMaxGroup);
         DDF_LAUNCH_CHECK();
     }
     return DDF_OK;
@@ -2686,15 +3113,15 @@ extern "C" DDF_API int ddf_group_create(int n_obj, const ddf_net* nets, ddf_grou
     if (n_obj <= 0 || !nets) return fail(DDF_ERR_INVALID_ARG, "need at least one network");
     ddf_group_s* g = new ddf_group_s();
     g->n = n_obj;
-    std::vector<GNet> host[2];
-    std::vector<CUtensorMap> maps[2];
+    std::vector<GNet> host[3];
+    std::vector<CUtensorMap> maps[3];
     for (int i = 0; i < n_obj; ++i) {
         ddf_net_s* nt = nets[i];
         if (!nt || nt->is_sphere || nt->precision != DDF_BF16 || !nt->tc) {
             group_free(g);
             return fail(DDF_ERR_UNSUPPORTED, "object %d: grouped queries need BF16 tensor-core networks", i);
         }
-        const int c = nt->lay.width == 128 ? 0 : (nt->lay.width == 256 ? 1 : -1);
+        const int c = nt->lay.width == 128 ? 0 : nt->lay.width == 256 ? 1 : nt->lay.width == 512 ? 2 : -1;
         if (c < 0) {
             group_free(g);
             return fail(DDF_ERR_UNSUPPORTED, "object %d: width %d not built for grouped queries", i, nt->lay.width);
@@ -2723,10 +3150,10 @@ extern "C" DDF_API int ddf_group_create(int n_obj, const ddf_net* nets, ddf_grou
     }
     cudaError_t e = cudaMalloc(&g->err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(int));
-    for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
         ddf_group_s::Class& C = g->cls[c];
         if (!C.nobj) continue;
-        if (smem_layout_pair(C.W, C.K0).nst < 2) {
+        if (C.W != 512 && smem_layout_pair(C.W, C.K0).nst < 2) {
             group_free(g);
             return fail(DDF_ERR_UNSUPPORTED, "width %d x %d layers does not fit the grouped kernel", C.W, C.maxL);
         }
@@ -2744,6 +3171,7 @@ extern "C" DDF_API int ddf_group_create(int n_obj, const ddf_net* nets, ddf_grou
     // kernel attributes are set here, outside any stream capture
     int rc = ensure_pair_attr<128, true, false>();
     if (!rc) rc = ensure_pair_attr<256, true, false>();
+    if (!rc) rc = ensure_grouped512_attr();
     if (rc) {
         group_free(g);
         return rc;
@@ -2767,7 +3195,7 @@ extern "C" DDF_API int ddf_query_grouped(ddf_group g, const int64_t* d_offsets, 
         return fail(DDF_ERR_INVALID_ARG, "NULL argument");
     int rc = group_prep(g, d_offsets, stream);
     if (rc) return rc;
-    for (int c = 0; c < 2; ++c) {
+    for (int c = 0; c < 3; ++c) {
         rc = group_class_launch(g, c, d_origins, d_dirs, d_dist, d_hit, d_logit, stream);
         if (rc) return rc;
     }
@@ -2849,7 +3277,7 @@ extern "C" DDF_API int ddf_group_autotune(ddf_group g, const int64_t* d_offsets,
     cudaEvent_t e0, e1;
     DDF_CUDA_TRY(cudaEventCreate(&e0));
     DDF_CUDA_TRY(cudaEventCreate(&e1));
-    for (int c = 0; c < 2; ++c) {
+    for (int c = 0; c < 3; ++c) {
         ddf_group_s::Class& C = g->cls[c];
         if (!C.nobj) continue;
         std::vector<GNet> hn(C.nobj);
@@ -2874,12 +3302,15 @@ extern "C" DDF_API int ddf_group_autotune(ddf_group g, const int64_t* d_offsets,
             }
         }
         if (cached) continue;
-        const int nst_max = smem_layout_pair(C.W, C.K0).nst;   // the pair kernel's ring depth is fixed
+        // ring depths that fit the class's shared-memory layout (the pair kernels keep their layout
+        // and use fewer stages; width 512 has room for three), tried deepest first
+        const int nst_max = C.W == 512 ? 3 : smem_layout_pair(C.W, C.K0).nst;
+        const int nst_min = std::max(2, nst_max - 3);
         const int sms = num_sms();
         const int grids[3] = {sms, (3 * sms) / 4, sms / 2};
         float best = 1e30f;
         int best_nst = nst_max, best_grid = sms;
-        for (int nst = nst_max; nst <= nst_max; ++nst)
+        for (int nst = nst_max; nst >= nst_min; --nst)
             for (int gi = 0; gi < 3; ++gi) {
                 C.nst = nst;
                 C.grid = grids[gi];
@@ -2915,14 +3346,15 @@ extern "C" DDF_API int ddf_group_autotune(ddf_group g, const int64_t* d_offsets,
 }
 
 // Chosen launch shape per width class: host_out[3 c .. 3 c + 2] = (width, ring depth, grid)
-// for c = 0 (width 128) and 1 (width 256); zeros for an absent class or a default shape.
-extern "C" DDF_API int ddf_group_config(ddf_group g, int* host_out6) {
+// for c = 0 (width 128), 1 (width 256) and 2 (width 512); zeros for an absent class or a default
+// shape.
+extern "C" DDF_API int ddf_group_config(ddf_group g, int* host_out9) {
     using namespace ddf;
-    if (!g || !host_out6) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
-    for (int c = 0; c < 2; ++c) {
-        host_out6[3 * c] = g->cls[c].nobj ? g->cls[c].W : 0;
-        host_out6[3 * c + 1] = g->cls[c].nst;
-        host_out6[3 * c + 2] = g->cls[c].grid;
+    if (!g || !host_out9) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+    for (int c = 0; c < 3; ++c) {
+        host_out9[3 * c] = g->cls[c].nobj ? g->cls[c].W : 0;
+        host_out9[3 * c + 1] = g->cls[c].nst;
+        host_out9[3 * c + 2] = g->cls[c].grid;
     }
     return DDF_OK;
 }

@@ -4,7 +4,8 @@
 // Ray state is structure-of-arrays in HBM (o: n x 3, w: n x 3, path index: n, throughput: n),
 // ping-ponged between two buffers. Live counts stay in device memory, so the host never waits
 // inside a render: every kernel reads its count and strides over it with a fixed grid.
-// Compaction is a warp ballot plus one atomicAdd per warp. Every random number a path uses is
+// Compaction is a warp ballot, a prefix over the block's warps in shared memory and one atomicAdd
+// per block on the device counter. Every random number a path uses is
 // a Philox4x32-10 word of counter (pid, bounce), so a path's radiance does not depend on where
 // compaction put it.
 #include <math.h>
@@ -42,13 +43,27 @@ __device__ __forceinline__ void primary_dir(const CamDev& cam, int64_t pid, int 
     *dz = vz * inv;
 }
 
-__device__ __forceinline__ int warp_compact(bool alive, int* counter) {
-    const unsigned lane = threadIdx.x & 31u;
+// Block-wide compaction: the slot of this thread's survivor among all survivors, with one atomicAdd
+// per block on the device counter (the warps' counts are prefix-summed in shared memory). Called
+// by every thread of the block; `scratch` holds kThreads / 32 + 1 ints.
+__device__ __forceinline__ int block_compact(bool alive, int* counter, int* scratch) {
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const unsigned m = __ballot_sync(0xffffffffu, alive);
-    int base = 0;
-    if (lane == 0 && m) base = atomicAdd(counter, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    return base + __popc(m & ((1u << lane) - 1u));
+    if (lane == 0) scratch[warp] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int k = 0; k < kThreads / 32; ++k) {
+            const int c = scratch[k];
+            scratch[k] = tot;
+            tot += c;
+        }
+        scratch[kThreads / 32] = tot ? atomicAdd(counter, tot) : 0;
+    }
+    __syncthreads();
+    const int slot = scratch[kThreads / 32] + scratch[warp] + __popc(m & ((1u << lane) - 1u));
+    __syncthreads();   // the scratch is rewritten by the next call
+    return slot;
 }
 
 // Camera rays of paths [pid0, pid0 + npaths), advanced to their entry into the unit ball.
@@ -58,6 +73,7 @@ __global__ void __launch_bounds__(kThreads) raygen_kernel(CamDev cam, int spp, i
                                                           uint32_t* __restrict__ lid,
                                                           float* __restrict__ thr,
                                                           float* __restrict__ radiance, int* count) {
+    __shared__ int scratch[kThreads / 32 + 1];
     for (int64_t i0 = (int64_t)blockIdx.x * kThreads; i0 < npaths; i0 += (int64_t)gridDim.x * kThreads) {
         const int64_t i = i0 + threadIdx.x;
         const bool valid = i < npaths;
@@ -76,7 +92,7 @@ __global__ void __launch_bounds__(kThreads) raygen_kernel(CamDev cam, int spp, i
             oz = cam.eye[2] + t0 * dz;
             if (!alive) radiance[i] = cam.env;
         }
-        const int slot = warp_compact(alive, count);
+        const int slot = block_compact(alive, count, scratch);
         if (alive) {
             o[3 * slot] = ox; o[3 * slot + 1] = oy; o[3 * slot + 2] = oz;
             w[3 * slot] = dx; w[3 * slot + 1] = dy; w[3 * slot + 2] = dz;
@@ -94,6 +110,7 @@ __global__ void __launch_bounds__(kThreads) shade_kernel(
     const float* __restrict__ nrm, float* __restrict__ o2, float* __restrict__ w2,
     uint32_t* __restrict__ lid2, float* __restrict__ thr2, float* __restrict__ radiance,
     int* count_out) {
+    __shared__ int scratch[kThreads / 32 + 1];
     const int n = *count_in;
     for (int i0 = blockIdx.x * kThreads; i0 < n; i0 += gridDim.x * kThreads) {
         const int i = i0 + threadIdx.x;
@@ -134,7 +151,7 @@ __global__ void __launch_bounds__(kThreads) shade_kernel(
                 nthr = t * cam.albedo;
             }
         }
-        const int slot = warp_compact(alive, count_out);
+        const int slot = block_compact(alive, count_out, scratch);
         if (alive) {
             o2[3 * slot] = nox; o2[3 * slot + 1] = noy; o2[3 * slot + 2] = noz;
             w2[3 * slot] = nwx; w2[3 * slot + 1] = nwy; w2[3 * slot + 2] = nwz;

@@ -449,6 +449,6 @@ class DDFGroup:
         check("ddf_group_autotune", _abi.load().ddf_group_autotune(
             self.h, _ptr(offsets), _ptr(o), _ptr(w), _ptr(out["dist"]), _ptr(out["hit"]), reps,
             cache_path.encode() if cache_path else None, _stream()))
-        cfg = (C.c_int * 6)()
+        cfg = (C.c_int * 9)()
         check("ddf_group_config", _abi.load().ddf_group_config(self.h, cfg))
-        return [(cfg[0], cfg[1], cfg[2]), (cfg[3], cfg[4], cfg[5])]
+        return [(cfg[3 * c], cfg[3 * c + 1], cfg[3 * c + 2]) for c in range(3) if cfg[3 * c]]

@@ -1,7 +1,7 @@
 """GPU grouped multi-object query: every object's rows equal the single-object BF16 query on
-the same rays (same arithmetic, one launch per width class), within the BF16 tolerance of the
-FP64 oracle; ragged and empty objects; CUDA-graph capture and replay after the device-side
-offsets change; the launch-shape autotuner and its cache."""
+the same rays (same arithmetic, one launch per width class: 128, 256 and 512), within the BF16
+tolerance of the FP64 oracle; ragged and empty objects; CUDA-graph capture and replay after the
+device-side offsets change; the launch-shape autotuner (ring depth and grid) and its cache."""
 
 import numpy as np
 import pytest
@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 # (in_freqs, width, hidden_layers, seed)
 OBJS = [(12, 256, 8, 100), (12, 128, 4, 101), (12, 256, 5, 102), (12, 128, 8, 103), (12, 256, 6, 104),
-        (0, 128, 6, 105)]
+        (0, 128, 6, 105), (12, 512, 4, 106), (16, 512, 8, 107), (12, 512, 6, 108)]
 
 
 @pytest.fixture(scope="module")
@@ -33,7 +33,7 @@ def _setup(P, counts, seed=0):
 
 
 def test_grouped_equals_single_object_queries(P):
-    counts = [1000, 1, 0, 5000, 129, 3000]
+    counts = [1000, 1, 0, 5000, 129, 3000, 4000, 127, 1]
     nets, off, o, w = _setup(P, counts)
     grp = P.DDFGroup(nets)
     to, tw = torch.from_numpy(o).cuda(), torch.from_numpy(w).cuda()
@@ -53,7 +53,7 @@ def test_grouped_equals_single_object_queries(P):
 
 
 def test_grouped_graph_replay_follows_device_offsets(P):
-    counts = [2000, 700, 100, 4000, 1, 900]
+    counts = [2000, 700, 100, 4000, 1, 900, 300, 2000, 0]
     nets, off, o, w = _setup(P, counts, seed=3)
     grp = P.DDFGroup(nets)
     to, tw = torch.from_numpy(o).cuda(), torch.from_numpy(w).cuda()
@@ -66,7 +66,7 @@ def test_grouped_graph_replay_follows_device_offsets(P):
     torch.cuda.synchronize()
     assert torch.equal(out["dist"], ref["dist"]) and torch.equal(out["hit"], ref["hit"])
     # new ray counts written on the device; the same graph serves them
-    counts2 = [10, 4000, 0, 1200, 2400, 1]
+    counts2 = [10, 4000, 0, 1200, 2400, 1, 0, 1, 2300]
     off2 = np.concatenate([[0], np.cumsum(counts2)]).astype(np.int64)
     assert off2[-1] <= o.shape[0]
     toff.copy_(torch.from_numpy(off2).cuda())
@@ -81,7 +81,7 @@ def test_grouped_graph_replay_follows_device_offsets(P):
 
 
 def test_autotuner_and_cache(P, tmp_path):
-    counts = [3000, 3000, 3000, 3000, 3000, 3000]
+    counts = [3000] * len(OBJS)
     nets, off, o, w = _setup(P, counts, seed=5)
     grp = P.DDFGroup(nets)
     to, tw = torch.from_numpy(o).cuda(), torch.from_numpy(w).cuda()
@@ -89,13 +89,14 @@ def test_autotuner_and_cache(P, tmp_path):
     out = grp._out(o.shape[0], "cuda")
     cache = str(tmp_path / "tune.txt")
     cfg = grp.autotune(toff, to, tw, out, reps=2, cache_path=cache)
-    assert cfg[0][0] == 128 and cfg[1][0] == 256
+    assert [c[0] for c in cfg] == [128, 256, 512]
     assert all(c[1] >= 2 and c[2] > 0 for c in cfg)
+    assert cfg[2][1] in (2, 3)
     lines = open(cache).read().strip().splitlines()
-    assert len(lines) == 2
+    assert len(lines) == 3
     grp2 = P.DDFGroup(nets)
     assert grp2.autotune(toff, to, tw, out, reps=2, cache_path=cache) == cfg   # read back, no new lines
-    assert len(open(cache).read().strip().splitlines()) == 2
+    assert len(open(cache).read().strip().splitlines()) == 3
     res = grp2.query(toff, to, tw)
     ref = grp.query(toff, to, tw)
     torch.cuda.synchronize()

@@ -1,16 +1,28 @@
-"""The headline render (512 x 512 pixels x 64 spp, at most 4 bounces, 78 -> 256 x 8 -> 2 network)
-against the FP64 oracle, bounce by bounce, and renders spread over several waves.
+"""The headline render (512 x 512 pixels x 64 spp, at most 4 bounces, 78 -> 256 x 8 -> 2 network,
+seeded weights) against the FP64 oracle path by path and bounce by bounce, and renders spread over
+several waves.
 
-ddf_render_trace records the query of every bounce of a 16 x 16-pixel block (16,384 paths) of the
-full render. For each precision the test checks, against the oracle:
-  * every bounce's query on the very ray the GPU queried: FP32 within 1e-5 (relative, floored at
-    1), BF16 within 2e-2, FP8 against the model of its quantisation and with its FP64 error
-    stated; hit decisions wherever the oracle's logit is clear of the precision's band;
-  * every shading step: the next bounce's ray equals the oracle's hit point, offset and cosine
-    sample (Sec. 3.1, Fig. 1) computed from the GPU's own query outputs, and the throughput;
-  * every path's radiance: the value its recorded decisions imply, and (FP32) the radiance of the
-    oracle's own FP64 path wherever none of its decisions lies within 1e-4 of the threshold; the
-    pixels against the oracle image on pixels without such a path.
+ddf_render_trace records, for a 16 x 16-pixel block of the full render (16,384 paths), every
+bounce's query ray and outputs. The oracle traces the same paths on its own (FP64 camera rays,
+queries, hit points, cosine samples) and records the same quantities. Nothing the GPU produced is
+fed to the oracle: the two trajectories are compared.
+
+FP32: at the first bounce the rays agree to float32 rounding and the outputs to 1e-5 (relative,
+floored at 1). At later bounces the float32 path has drifted from the float64 one by the
+rounding of the hit point and normal; the drift is measured, and each output is allowed that
+drift times the output's gradient along the ray (computed by the oracle on its own ray), twice,
+on top of 1e-5. A decision is compared where the oracle's |logit| exceeds 1e-4 plus that drift
+term. A path whose every decision is clear in that sense must end with the oracle's radiance, and
+a pixel all of whose paths are clear must match the oracle's pixel to 1e-4; the shares of paths
+exempted by the threshold and by the drift are printed.
+
+BF16 and FP8: the first bounce is compared with the oracle (BF16 within 2e-2, FP8 within 6e-2 of
+the FP64 distance) and, decision by decision, with models of their rounding (tests/_bf16_model.py,
+tests/_fp8_model.py) on the oracle's camera rays rounded to float32. After the first bounce the
+reduced-precision normals (a few degrees from FP64) send the paths elsewhere: the share of paths
+ending with the oracle's radiance is stated. For every precision each path's radiance is the
+value its recorded decisions imply, and each pixel is the mean of its paths.
+
 The multi-wave test renders more than 2^24 paths (two waves) and the same render in many small
 waves: the images are identical bit for bit and the second wave's paths match the oracle."""
 
@@ -20,15 +32,15 @@ import torch
 
 from ddf_synth import default_camera, init_weights
 from oracle import mlp as omlp
-from oracle.render import shade_step, trace_paths
-from tests._helpers import BF16_ABS, LOGIT_MARGIN, NETS, ensure_built, fp32_close, net_weights
+from oracle.render import primary_rays, trace_paths
+from tests._helpers import BF16_ABS, LOGIT_MARGIN, NETS, ensure_built, net_weights
 
 pytestmark = pytest.mark.gpu
 
 HEAD = dict(F=12, W=256, L=8, seed=3, size=512, spp=64, bounces=4)   # the bench's render
 BLOCK = (248, 248, 16)                                                # x0, y0, side of the traced block
-FP8_ABS = 6e-2     # FP8 has no stated bound: distances against FP64 are held to 6e-2, decisions
-                   # compared where |logit64| >= 6e-2 (measured errors: max ~0.03)
+FP8_ABS = 6e-2     # FP8 has no stated bound: distances against FP64 are held to 6e-2 (measured
+                   # errors on this network: max ~0.02)
 
 
 @pytest.fixture(scope="module")
@@ -42,27 +54,6 @@ def _block_pids(size, spp, x0, y0, side):
     ys, xs = np.meshgrid(np.arange(y0, y0 + side), np.arange(x0, x0 + side), indexing="ij")
     pix = (ys * size + xs).ravel()
     return pix, (pix[:, None] * spp + np.arange(spp)[None, :]).ravel()
-
-
-def _normal_tolerance(Pm, o, w):
-    """Per-row bound for the FP32 Eq. 3 normal: 1e-4 plus the rounding a float32 reverse pass can
-    amplify when the gradient cancels, 1e-5 |g|_abs / |g|, where |g|_abs is the reverse pass of the
-    same masks through |W| and |d features / d o| (the running-error bound of the sum) and g the
-    FP64 gradient."""
-    X, dX = omlp.encode(o, w, HEAD["F"])
-    _, pres, acts = omlp.forward(Pm, X)
-    gy = np.zeros((o.shape[0], 2))
-    gy[:, 0] = 1.0
-    _, gX = omlp.backward(Pm, pres, acts, gy)
-    _, gXa = omlp.backward([(np.abs(Wl), bl) for Wl, bl in Pm], pres, acts, gy)
-    g = np.zeros((o.shape[0], 3))
-    ga = np.zeros((o.shape[0], 3))
-    for f in range(X.shape[1]):
-        if f % 6 < 3:
-            g[:, f % 6] += gX[:, f] * dX[:, f]
-            ga[:, f % 6] += np.abs(gXa[:, f] * dX[:, f])
-    gn = np.linalg.norm(g, axis=1)
-    return 1e-4 + 1e-5 * np.linalg.norm(ga, axis=1) / np.maximum(gn, 1e-300), gn
 
 
 def _implied_radiance(tr, albedo, env):
@@ -85,31 +76,46 @@ def _implied_radiance(tr, albedo, env):
     return rad
 
 
-def _check_shading(tr, pids, cam):
-    """Bounce b + 1's ray is the oracle's move from bounce b's GPU outputs."""
-    B = tr.shape[1]
-    moved = 0
-    for b in range(B - 1):
-        cont = ~np.isnan(tr[:, b + 1, 0])
-        if not cont.any():
-            continue
-        r0 = tr[cont, b].astype(np.float64)
-        assert (r0[:, 7] > 0).all()                       # only paths that hit move on
-        o2, w2 = shade_step(r0[:, 0:3], r0[:, 3:6], r0[:, 6], r0[:, 8:11], cam.seed, pids[cont], b + 1)
-        r1 = tr[cont, b + 1].astype(np.float64)
-        assert np.abs(r1[:, 0:3] - o2).max() <= 2e-6, np.abs(r1[:, 0:3] - o2).max()
-        assert np.abs(r1[:, 3:6] - w2).max() <= 2e-5, np.abs(r1[:, 3:6] - w2).max()
-        assert (tr[cont, b + 1, 11] == (tr[cont, b, 11] * np.float32(cam.albedo)).astype(np.float32)).all()
-        # paths that hit and did not move on: only at the last bounce
-        stopped = ~cont & ~np.isnan(tr[:, b, 0]) & (tr[:, b, 7] > 0)
-        assert not stopped.any()
-        moved += int(cont.sum())
-    return moved
+def _output_gradients(Pm, F, o, w):
+    """The oracle's d dist / d (o, w) and d logit / d (o, w) (n x 6 each) at its own rays."""
+    X, dX = omlp.encode(o, w, F)
+    _, pres, acts = omlp.forward(Pm, X)
+    out = []
+    for k in range(2):
+        gy = np.zeros((o.shape[0], 2))
+        gy[:, k] = 1.0
+        _, gX = omlp.backward(Pm, pres, acts, gy)
+        g6 = np.zeros((o.shape[0], 6))
+        gf = gX * dX
+        for f in range(X.shape[1]):
+            g6[:, f % 6] += gf[:, f]
+        out.append(g6)
+    return out
 
 
-def _render_traced(P, precision):
-    F, W, L, seed = HEAD["F"], HEAD["W"], HEAD["L"], HEAD["seed"]
-    blob = init_weights(F, W, L, seed=seed)
+def _normal_tolerance(Pm, F, o, w):
+    """Per-row bound for the FP32 Eq. 3 normal: 1e-4 plus the rounding a float32 reverse pass can
+    amplify when the gradient cancels, 1e-5 |g|_abs / |g|, where |g|_abs is the reverse pass of the
+    same masks through |W| and |d features / d o| (the running-error bound of the sum) and g the
+    FP64 gradient."""
+    X, dX = omlp.encode(o, w, F)
+    _, pres, acts = omlp.forward(Pm, X)
+    gy = np.zeros((o.shape[0], 2))
+    gy[:, 0] = 1.0
+    _, gX = omlp.backward(Pm, pres, acts, gy)
+    _, gXa = omlp.backward([(np.abs(Wl), bl) for Wl, bl in Pm], pres, acts, gy)
+    g = np.zeros((o.shape[0], 3))
+    ga = np.zeros((o.shape[0], 3))
+    for f in range(X.shape[1]):
+        if f % 6 < 3:
+            g[:, f % 6] += gX[:, f] * dX[:, f]
+            ga[:, f % 6] += np.abs(gXa[:, f] * dX[:, f])
+    gn = np.linalg.norm(g, axis=1)
+    return 1e-4 + 1e-5 * np.linalg.norm(ga, axis=1) / np.maximum(gn, 1e-300), gn
+
+
+def _render_traced(P, precision, blob):
+    F, W, L = HEAD["F"], HEAD["W"], HEAD["L"]
     net = P.DDFNet(F, W, L, blob, precision)
     cam = default_camera(HEAD["size"], HEAD["size"], seed=1)
     pix, pids = _block_pids(HEAD["size"], HEAD["spp"], *BLOCK)
@@ -117,83 +123,133 @@ def _render_traced(P, precision):
     img_plain = net.render(cam, HEAD["spp"], HEAD["bounces"])
     net.device_status()
     assert torch.equal(img, img_plain)                   # tracing does not change the render
-    return (blob, net, cam, pix, pids, img.cpu().numpy().ravel(), tr.cpu().numpy(), rad.cpu().numpy())
+    return net, cam, pix, pids, img.cpu().numpy().ravel(), tr.cpu().numpy(), rad.cpu().numpy()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
-def test_headline_render_bounce_by_bounce(P, precision):
-    F, W, L = HEAD["F"], HEAD["W"], HEAD["L"]
-    blob, net, cam, pix, pids, img, tr, rad = _render_traced(P, precision)
-    Pm = omlp.unpack(blob, F, W, L)
-    B = HEAD["bounces"]
-    band = {"fp32": LOGIT_MARGIN, "bf16": BF16_ABS, "fp8": FP8_ABS}[precision]
-    assert not np.isnan(tr[:, 0, 0]).any()               # the default camera: every ray enters the ball
-    stats = []
-    for b in range(B):
-        q = ~np.isnan(tr[:, b, 0])
-        if not q.any():
-            continue
-        r = tr[q, b]
-        o, w = r[:, 0:3], r[:, 3:6]
-        ref = omlp.query(Pm, o, w, F, with_normal=b < B - 1)
-        clear = np.abs(ref["logit"]) >= band
-        hit32 = r[:, 7] > 0
-        mism = int((hit32[clear] != ref["hit"][clear]).sum())
-        if precision == "fp32":
-            assert fp32_close(r[:, 6], ref["dist"]).all(), np.abs(r[:, 6] - ref["dist"]).max()
-            assert fp32_close(r[:, 7], ref["logit"]).all(), np.abs(r[:, 7] - ref["logit"]).max()
-            assert mism == 0
-            if b < B - 1 and hit32.any():
-                tol, gn = _normal_tolerance(Pm, o[hit32], w[hit32])
-                dn = np.abs(r[hit32, 8:11] - ref["normal"][hit32]).max(axis=1)
-                ok = gn > 0
-                assert (dn[ok] <= tol[ok]).all(), (dn[ok].max(), (dn[ok] > tol[ok]).sum())
-                assert (dn[ok] <= 1e-4).mean() > 0.98
-        elif precision == "bf16":
-            assert np.abs(r[:, 6] - ref["dist"]).max() <= BF16_ABS
-            assert np.abs(r[:, 7] - ref["logit"]).max() <= BF16_ABS
-            assert mism == 0
-        else:
-            from tests._fp8_model import query_fp8
-            m = query_fp8(Pm, o, w, F, net.fp8_scales())
-            dm = np.abs(r[:, 6] - m["dist"])
-            assert np.quantile(dm, 0.99) <= 5e-3 and dm.max() <= 3e-2, (np.quantile(dm, 0.99), dm.max())
-            cm = np.abs(m["logit"]) >= 0.05
-            assert (hit32[cm] == m["hit"][cm]).all()
-            assert np.abs(r[:, 6] - ref["dist"]).max() <= FP8_ABS
-            assert mism == 0
-        if b < B - 1 and hit32.any():
-            ang = np.degrees(np.arccos(np.clip(np.sum(r[hit32, 8:11] * ref["normal"][hit32], 1), -1, 1)))
-            assert np.allclose(np.linalg.norm(r[hit32, 8:11], axis=1), 1, atol=1e-5)
-            nstat = f", normal angle vs FP64 median {np.median(ang):.3f} p99 {np.percentile(ang, 99):.2f} deg"
-        else:
-            nstat = ""
-        stats.append(f"bounce {b + 1}: {int(q.sum())} queries, max |d dist| "
-                     f"{np.abs(r[:, 6] - ref['dist']).max():.2e}, {int((~clear).sum())} within the band{nstat}")
-    moved = _check_shading(tr, pids, cam)
-    assert moved > 500                                    # paths do bounce
-    implied = _implied_radiance(tr, cam.albedo, cam.env)
-    assert np.array_equal(rad, implied)
-    # the pixels of the block are the means of their traced paths
+def _check_consistency(tr, rad, img, pix, cam):
+    """The GPU's own bookkeeping: radiance from the recorded decisions, pixels from the paths,
+    throughput albedo^(b-1) at bounce b, a path continues exactly when it hit."""
+    assert np.array_equal(rad, _implied_radiance(tr, cam.albedo, cam.env))
     assert np.allclose(img[pix], rad.reshape(-1, HEAD["spp"]).mean(1), atol=1e-6)
-    # the oracle's own FP64 paths
+    B = tr.shape[1]
+    for b in range(B - 1):
+        q = ~np.isnan(tr[:, b, 0])
+        nxt = ~np.isnan(tr[:, b + 1, 0])
+        assert np.array_equal(nxt, q & (tr[:, b, 7] > 0))
+        assert (tr[nxt, b + 1, 11] == (tr[nxt, b, 11] * np.float32(cam.albedo)).astype(np.float32)).all()
+
+
+def test_headline_render_fp32_path_by_path(P):
+    F, W, L, B = HEAD["F"], HEAD["W"], HEAD["L"], HEAD["bounces"]
+    blob = init_weights(F, W, L, seed=HEAD["seed"])
+    net, cam, pix, pids, img, tr, rad = _render_traced(P, "fp32", blob)
+    _check_consistency(tr, rad, img, pix, cam)
+    Pm = omlp.unpack(blob, F, W, L)
     own = trace_paths(lambda a, c: omlp.query(Pm, a, c, F), cam, HEAD["spp"], B, pids)
-    if precision == "fp32":
-        ok = own["min_abs_logit"] >= LOGIT_MARGIN
-        assert ok.mean() > 0.95
-        assert np.abs(rad[ok] - own["radiance"][ok]).max() <= 1e-6
-        okp = ok.reshape(-1, HEAD["spp"]).all(1)
-        ref_img = own["radiance"].reshape(-1, HEAD["spp"]).mean(1)
-        assert np.abs(img[pix][okp] - ref_img[okp]).max() <= 1e-4
-        print(f"FP32 headline block: exempt paths {1 - ok.mean():.4%}, exempt pixels {1 - okp.mean():.4%}")
+    rec = own["rec"]
+    n = pids.size
+    alive = np.ones(n, bool)          # both trajectories took the same, clear decisions so far
+    near = np.zeros(n, bool)          # exempted by a decision within 1e-4 of the threshold
+    drift = np.zeros(n, bool)         # exempted by a decision within the drift term
+    ill = np.zeros(n, bool)           # exempted by an ill-conditioned normal at the previous hit
+    worst_drift = []
+    for b in range(B):
+        qg = ~np.isnan(tr[:, b, 0])
+        qo = ~np.isnan(rec[:, b, 0])
+        assert np.array_equal(qg[alive], qo[alive])      # same decisions so far: both query or neither
+        alive &= ~ill                                   # the hit point or bounce direction may part here
+        both = alive & qg & qo
+        if not both.any():
+            break
+        g, r = tr[both, b].astype(np.float64), rec[both, b]
+        d_o = np.abs(g[:, 0:3] - r[:, 0:3]).max(1)
+        d_w = np.abs(g[:, 3:6] - r[:, 3:6]).max(1)
+        if b == 0:   # camera rays: float32 ball entry (cancellation in b^2 - c) and direction
+            assert d_o.max() <= 1e-5 and d_w.max() <= 1e-6, (d_o.max(), d_w.max())
+        else:   # float32 hit points and cosine samples stay close to the float64 ones
+            assert np.median(np.maximum(d_o, d_w)) <= 1e-5 and max(d_o.max(), d_w.max()) <= 1e-2
+        worst_drift.append(float(max(d_o.max(), d_w.max())))
+        gd, gl = _output_gradients(Pm, F, r[:, 0:3], r[:, 3:6])
+        s_d = np.abs(gd[:, :3]).sum(1) * d_o + np.abs(gd[:, 3:]).sum(1) * d_w
+        s_l = np.abs(gl[:, :3]).sum(1) * d_o + np.abs(gl[:, 3:]).sum(1) * d_w
+        assert (np.abs(g[:, 6] - r[:, 6]) <= 1e-5 * np.maximum(np.abs(r[:, 6]), 1) + 2 * s_d).all()
+        assert (np.abs(g[:, 7] - r[:, 7]) <= 1e-5 * np.maximum(np.abs(r[:, 7]), 1) + 2 * s_l).all()
+        idx = np.nonzero(both)[0]
+        is_near = np.abs(r[:, 7]) < LOGIT_MARGIN
+        is_drift = ~is_near & (np.abs(r[:, 7]) < LOGIT_MARGIN + 2 * s_l)
+        clear = ~is_near & ~is_drift
+        assert ((g[clear, 7] > 0) == (r[clear, 7] > 0)).all()
+        h = clear & (g[:, 7] > 0)
+        if b + 1 < B and h.any():
+            # the normal decides the next ray: where the two normals differ by more than 1e-3 (an
+            # ill-conditioned gradient), the FP64 one is nearly tangent to the ray (the sign of
+            # Eq. 3's kappa) or close to n_z = 0 (the branch of the orthonormal basis), the two
+            # paths may part legitimately from the next bounce on
+            n64 = r[h, 8:11]
+            dn = np.abs(g[h, 8:11] - n64).max(1)
+            shaky = (dn > 1e-3) | (np.abs(np.sum(n64 * r[h, 3:6], 1)) < 1e-3) | (np.abs(n64[:, 2]) < 1e-3)
+            ill[idx[h][shaky]] = True
+            if b == 0:
+                tol, gn = _normal_tolerance(Pm, F, r[h, 0:3], r[h, 3:6])
+                assert (dn[gn > 0] <= tol[gn > 0]).all(), dn.max()
+                assert (dn <= 1e-4).mean() > 0.98
+        near[idx[is_near]] = True
+        drift[idx[is_drift]] = True
+        alive[idx[~clear]] = False
+    ok = ~near & ~drift & ~ill
+    assert ok.mean() > 0.9 and ill.mean() < 0.05, (near.mean(), drift.mean(), ill.mean())
+    assert np.abs(rad[ok] - own["radiance"][ok]).max() <= 1e-6
+    okp = ok.reshape(-1, HEAD["spp"]).all(1)
+    ref_img = own["radiance"].reshape(-1, HEAD["spp"]).mean(1)
+    assert okp.mean() > 0.3
+    assert np.abs(img[pix][okp] - ref_img[okp]).max() <= 1e-4
+    same = np.abs(rad - own["radiance"]) <= 1e-6
+    print(f"FP32 headline block: {ok.mean():.4%} of paths clear ({near.mean():.4%} near the threshold, "
+          f"{drift.mean():.4%} within the drift term, {ill.mean():.4%} after an ill-conditioned normal), "
+          f"{same.mean():.4%} end with the oracle's radiance, "
+          f"{okp.mean():.2%} of pixels compared; ray drift per bounce {worst_drift}")
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_headline_render_reduced_precision(P, precision):
+    F, W, L, B = HEAD["F"], HEAD["W"], HEAD["L"], HEAD["bounces"]
+    blob = init_weights(F, W, L, seed=HEAD["seed"])
+    net, cam, pix, pids, img, tr, rad = _render_traced(P, precision, blob)
+    _check_consistency(tr, rad, img, pix, cam)
+    Pm = omlp.unpack(blob, F, W, L)
+    # first bounce: the oracle's own camera rays
+    o64, w64, alive = primary_rays(cam, pids, HEAD["spp"])
+    assert alive.all() and not np.isnan(tr[:, 0, 0]).any()
+    g = tr[:, 0]
+    assert np.abs(g[:, 0:3] - o64).max() <= 1e-5 and np.abs(g[:, 3:6] - w64).max() <= 1e-6
+    ref = omlp.query(Pm, o64, w64, F, with_normal=False)
+    tol = BF16_ABS if precision == "bf16" else FP8_ABS
+    err = np.abs(g[:, 6] - ref["dist"])
+    assert err.max() <= tol
+    o32, w32 = o64.astype(np.float32), w64.astype(np.float32)
+    if precision == "bf16":
+        from tests._bf16_model import query_bf16
+        m = query_bf16(Pm, o32, w32, F)
+        margin = 2e-3
+        assert np.abs(g[:, 6] - m["dist"]).max() <= 2e-3
     else:
-        # first decisions are taken on the same camera rays (float32 vs float64 ray setup)
-        first = np.abs(own["logit"]) >= band
-        hit_first = tr[:, 0, 7] > 0
-        assert (hit_first[first] == (own["logit"][first] > 0)).all()
-        same = np.abs(rad - own["radiance"]) <= 1e-6
-        print(f"{precision} headline block: {same.mean():.4f} of paths end with the FP64 path's radiance")
-    print(f"{precision}: " + "; ".join(stats))
+        from tests._fp8_model import query_fp8
+        m = query_fp8(Pm, o32, w32, F, net.fp8_scales())
+        margin = 0.05
+        dm = np.abs(g[:, 6] - m["dist"])
+        assert np.quantile(dm, 0.99) <= 5e-3 and dm.max() <= 3e-2
+    cm = np.abs(m["logit"]) >= margin
+    assert ((g[cm, 7] > 0) == m["hit"][cm]).all()
+    c64 = np.abs(ref["logit"]) >= tol
+    assert ((g[c64, 7] > 0) == ref["hit"][c64]).all()
+    own = trace_paths(lambda a, c: omlp.query(Pm, a, c, F), cam, HEAD["spp"], B, pids)
+    same = np.abs(rad - own["radiance"]) <= 1e-6
+    hit1 = g[:, 7] > 0
+    print(f"{precision} headline block: first bounce |d dist| vs FP64 max {err.max():.2e} p99 "
+          f"{np.quantile(err, 0.99):.2e}; first decisions checked against the {precision} model on "
+          f"{cm.mean():.2%} of paths (all equal); {hit1.mean():.2%} hit at the first bounce; "
+          f"{same.mean():.2%} of paths end with the FP64 path's radiance; mean |d pixel| vs FP64 "
+          f"{np.abs(img[pix] - own['radiance'].reshape(-1, HEAD['spp']).mean(1)).mean():.4f}")
 
 
 def test_render_over_several_waves(P):
@@ -222,15 +278,17 @@ def test_render_over_several_waves(P):
     img, tr, rad = net.render_trace(cam, spp, B, torch.from_numpy(pids).cuda())
     assert torch.equal(img.cpu(), a)
     img, tr, rad = img.cpu().numpy().ravel(), tr.cpu().numpy(), rad.cpu().numpy()
+    assert np.array_equal(rad, _implied_radiance(tr, cam.albedo, cam.env))
     Pm = omlp.unpack(blob, F, W, L)
     own = trace_paths(lambda o, w: omlp.query(Pm, o, w, F), cam, spp, B, pids)
+    o64, w64, _ = primary_rays(cam, pids, spp)
+    q = ~np.isnan(tr[:, 0, 0])
+    assert np.abs(tr[q, 0, 0:3] - o64[q]).max() <= 1e-5 and np.abs(tr[q, 0, 3:6] - w64[q]).max() <= 1e-6
     ok = own["min_abs_logit"] >= LOGIT_MARGIN
     assert ok.mean() > 0.9
     assert np.abs(rad[ok] - own["radiance"][ok]).max() <= 1e-6
     okp = ok.reshape(-1, spp).all(1)
     assert np.abs(img[pix][okp] - own["radiance"].reshape(-1, spp).mean(1)[okp]).max() <= 1e-4
-    assert np.array_equal(rad, _implied_radiance(tr, cam.albedo, cam.env))
-    _check_shading(tr, pids, cam)
 
 
 def test_render_trace_arguments(P):
