@@ -59,9 +59,10 @@ def bwd_flops(E, W, L):
 
 
 # ncu-measured DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the BF16 query
-# kernels of one 512 x 512 x 64 spp render of the trained network (mlp_pair_kernel<256> forward
-# and mlp_tc_kernel<256,1> normals launches); None until measured for the current kernels.
-QUERY_DRAM_BYTES_PER_RENDER = None
+# kernels of one 512 x 512 x 64 spp render of the seeded network (the 4 mlp_pair_kernel<256>
+# forward and 3 mlp_pairn_kernel<256> normals launches; profiles/bf16_query_render512x512.md); to
+# be measured again whenever those kernels change.
+QUERY_DRAM_BYTES_PER_RENDER = 760.6e6
 
 
 def load_peaks():

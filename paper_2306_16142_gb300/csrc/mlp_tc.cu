@@ -12,12 +12,13 @@
 //   mlp_pair_kernel<W, GRP>   the forward query (W = 128, 256): two 128-row tiles per CTA share
 //                             every weight stage, each layer's bias enters through one MMA;
 //                             GRP = true serves grouped launches of many networks;
-//   mlp_tc_kernel<W, 1>       the normals of the hit rows: one tile per CTA, the forward pass
-//                             again (ReLU masks kept as bits in shared memory) and then the
-//                             reverse pass with the transposed weights through the same ring,
-//                             the encoding chain rule and Eq. 3;
+//   mlp_pairn_kernel<W>       the normals of the hit rows (W = 128, 256) on tile pairs: the
+//                             forward pass again (ReLU masks to a per-SM scratch in L2), then the
+//                             reverse pass with the transposed weights through the same ring, the
+//                             encoding chain rule and Eq. 3;
 //   mlp_tc512_kernel<MODE>    both launches at width 512 (N-half schedule);
-//   mlp_f8_kernel<W>          the forward query with E4M3 weights and activations.
+//   mlp_f8_kernel<W>          the forward query with E4M3 weights and activations (W = 128, 256);
+//   mlp_f8w512_kernel         the same at width 512 (N-half schedule).
 //
 // Every mbarrier wait is bounded (about 2 s of %globaltimer); on expiry the kernel raises a
 // device error flag, every role leaves its loop, TMEM is released and the host reports
@@ -158,319 +159,6 @@ __device__ __forceinline__ void release_kb_warp(uint64_t* actr, int kb) {
 }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
-
-template <int W, int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
-    mlp_tc_kernel(const __grid_constant__ CUtensorMap mapF, const __grid_constant__ CUtensorMap mapB,
-                  const TcArgs a) {
-    static_assert(MODE == 1, "the forward and grouped queries run on mlp_pair_kernel");
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int NKBW = W / 64;
-    const int L = a.L, KB0 = a.K0 / 64;
-    const int KMAXB = KB0 > NKBW ? KB0 : NKBW;
-    const int NST = a.nst;
-    uint8_t* act = smem;
-    uint8_t* wst = smem + a.off_wst;
-    uint32_t* masks = reinterpret_cast<uint32_t*>(smem + a.off_mask);
-    uint8_t* ones = smem + a.off_grp;       // 4 KB: the A operand of the bias MMA
-    uint8_t* bslot = smem + a.off_bias;     // the current forward layer's bias tile
-    float* head_s = reinterpret_cast<float*>(smem + a.off_head);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
-    uint64_t* full = bars;
-    uint64_t* empty = bars + NST;
-    uint64_t* actr = bars + 2 * NST;
-    uint64_t* accf = actr + KMAXB;
-    uint64_t* bfull = accf + 2;             // bias slot loaded / consumed
-    uint64_t* bempty = bfull + 1;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bempty + 1);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    int64_t n = a.n;
-    if (a.d_count) n = min(n, (int64_t)*a.d_count);
-    const int64_t ntiles = (n + kTileM - 1) / kTileM;
-    constexpr uint32_t kTmemCols = W <= 128 ? 256 : 512;
-    // Per-tile description: rows of the hit list, network depth, first-layer K-blocks, weight map.
-    struct TileInfo {
-        int64_t row0;
-        int rows, L, KB0, F, E;
-        const CUtensorMap* map;
-    };
-    auto tile_info = [&](int64_t t) -> TileInfo {
-        TileInfo ti;
-        ti.row0 = t * kTileM;
-        ti.rows = (int)min((int64_t)kTileM, n - ti.row0);
-        ti.L = L;
-        ti.KB0 = KB0;
-        ti.F = a.F;
-        ti.E = a.E;
-        ti.map = &mapF;
-        return ti;
-    };
-
-    if (tid == 0) {
-        for (int i = 0; i < NST; ++i) {
-            mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
-        }
-        for (int i = 0; i < KMAXB; ++i) mbar_init(&actr[i], 256);
-        mbar_init(&accf[0], 1);
-        mbar_init(&accf[1], 1);
-        mbar_init(bfull, 1);
-        mbar_init(bempty, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
-                     "r"(kTmemCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    // the ones tile: K rows 0 and 1 of both 64-row MN atoms are 1.0 (BF16 0x3F80), the rest 0
-    for (int i = tid; i < 1024; i += kThreads)
-        reinterpret_cast<uint32_t*>(ones)[i] = ((i >> 5) & 15) < 2 ? 0x3F803F80u : 0u;
-    fence_proxy_async();
-    for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tbase = *tslot;
-
-    if (warp == kEpiWarps) {
-        // ---------------------------------------------------------------- TMA producer
-        if (lane == 0) {
-            uint32_t cnt = 0, nb = 0;
-            bool ok = true;
-            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const TileInfo ti = tile_info(t);
-                const int nsteps = MODE == 1 ? 2 * ti.L : ti.L;
-                for (int s = 0; s < nsteps && ok; ++s) {
-                    const Step st = step_of<W>(s, ti.L, ti.KB0);
-                    if (!st.bwd) {   // the forward layer's bias tile into its slot
-                        if (!mbar_wait(bempty, (nb & 1u) ^ 1u, a.err)) { ok = false; break; }
-                        mbar_expect_tx(bfull, (uint32_t)W * 32u);
-                        bulk_load(bslot, a.bias_mn + (size_t)st.layer * W * 32, (uint32_t)W * 32u, bfull);
-                        ++nb;
-                    }
-                    for (int kb = 0; kb < st.nk; ++kb, ++cnt) {
-                        const int stg = (int)(cnt % (uint32_t)NST);
-                        const uint32_t ph = (cnt / (uint32_t)NST) & 1u;
-                        if (!mbar_wait(&empty[stg], ph ^ 1u, a.err)) { ok = false; break; }
-                        mbar_expect_tx(&full[stg], (uint32_t)W * 128u);
-                        tma_load_3d(wst + (size_t)stg * W * 128, st.bwd ? &mapB : ti.map, &full[stg], kb * 64, 0,
-                                    st.layer);
-                    }
-                }
-            }
-        }
-    } else if (warp == kEpiWarps + 1) {
-        // ---------------------------------------------------------------- MMA issuer
-        if (lane == 0) {
-            uint32_t cnt = 0, g = 0, actph = 0, nb = 0;
-            bool ok = true;
-            const uint32_t act_s = su32(act), wst_s = su32(wst);
-            const uint32_t idesc_b = idesc_bf16(128, W) | (3u << 15);   // bias MMA: both operands MN-major
-            const uint64_t ones_d = sdesc_mn16(su32(ones)), bias_d = sdesc_mn16(su32(bslot));
-            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const TileInfo ti = tile_info(t);
-                const int nsteps = MODE == 1 ? 2 * ti.L : ti.L;
-                for (int s = 0; s < nsteps && ok; ++s, ++g) {
-                    const Step st = step_of<W>(s, ti.L, ti.KB0);
-                    const uint32_t d = tbase + (g & 1u) * (uint32_t)W;
-                    const uint32_t idesc = idesc_bf16(128, st.N);
-                    for (int kb = 0; kb < st.nk; ++kb, ++cnt) {
-                        const int stg = (int)(cnt % (uint32_t)NST);
-                        const uint32_t ph = (cnt / (uint32_t)NST) & 1u;
-                        if (!mbar_wait(&full[stg], ph, a.err)) { ok = false; break; }
-                        if (!mbar_wait(&actr[kb], (actph >> kb) & 1u, a.err)) { ok = false; break; }
-                        actph ^= 1u << kb;
-                        if (!st.bwd && kb == 0) {   // forward: the accumulator starts as the bias
-                            if (!mbar_wait(bfull, nb & 1u, a.err)) { ok = false; break; }
-                            ++nb;
-                            tc_fence_after();
-                            mma_bf16(d, ones_d, bias_d, idesc_b, 0u);
-                            mma_commit(bempty);
-                        }
-                        tc_fence_after();
-                        const uint64_t ad = sdesc(act_s + (uint32_t)kb * 16384u);
-                        const uint64_t bd = sdesc(wst_s + (uint32_t)stg * (uint32_t)W * 128u);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, st.bwd ? (uint32_t)((kb | k) != 0) : 1u);
-                        mma_commit(&empty[stg]);
-                    }
-                    if (ok) mma_commit(&accf[g & 1u]);
-                }
-            }
-        }
-    } else {
-        // ---------------------------------------------------------------- epilogue
-        // Two groups of four warps; warp w serves TMEM lanes 32 (w % 4) .. +31 (its rows) and
-        // group w / 4 owns columns [32 group, 32 group + 32) of every 64-column K-block, so each
-        // K-block of the next layer's A operand is written by both groups at once (256 arrivals)
-        // and K-block 0 is released after 32 columns of work per thread.
-        const int grp = warp >> 2;
-        const int r = (warp & 3) * 32 + lane;
-        const uint32_t act_s = su32(act);
-        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
-        uint32_t g = 0, accph = 0;
-        bool ok = true;
-        // this thread's row of a tile: index, validity and (o, w); the next tile's row is
-        // fetched during the current tile's last step so its latency hides behind the MMAs
-        auto fetch_row = [&](int64_t tt, int64_t& row_out, bool& valid_out, float* vv) {
-            valid_out = false;
-            row_out = -1;
-            if (tt < ntiles) {
-                const TileInfo tn = tile_info(tt);
-                valid_out = r < tn.rows;
-                if (valid_out) row_out = (int64_t)a.rows[tn.row0 + r];
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                vv[c] = valid_out ? a.o[row_out * 3 + c] : 0.f;
-                vv[c + 3] = valid_out ? a.w[row_out * 3 + c] : 0.f;
-            }
-        };
-        int64_t row_next = -1;
-        bool valid_next = false;
-        float v_next[6];
-        fetch_row(blockIdx.x, row_next, valid_next, v_next);
-        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const TileInfo ti = tile_info(t);
-            const int Lt = ti.L, KB0t = ti.KB0;
-            const int nsteps = MODE == 1 ? 2 * Lt : Lt;
-            const int64_t row = row_next;
-            const bool valid = valid_next;
-            float v[6];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) v[c] = v_next[c];
-            // input encoding: group g writes first-layer K-block g (K0 <= 128)
-            if (grp < KB0t) {
-                uint32_t pk[32];
-                if (grp == 0) encode_kblock<0>(v, ti.F, pk);
-                else encode_kblock<1>(v, ti.F, pk);
-#pragma unroll
-                for (int m = 0; m < 8; ++m)
-                    st_shared_v4(act_s + (uint32_t)grp * 16384u + swz(r, m), pk[4 * m], pk[4 * m + 1], pk[4 * m + 2],
-                                 pk[4 * m + 3]);
-                release_kb(actr, grp);
-            }
-            // K-blocks are released by 256 arrivals: each group also arrives on the other's block
-            for (int kb = 0; kb < KB0t; ++kb)
-                if (kb != grp) mbar_arrive(&actr[kb]);
-            for (int s = 0; s < nsteps && ok; ++s, ++g) {
-                const int b = (int)(g & 1u);
-                if (s == nsteps - 1) fetch_row(t + gridDim.x, row_next, valid_next, v_next);
-                ok = mbar_wait(&accf[b], (accph >> b) & 1u, a.err);
-                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }   // warp-uniform exit
-                accph ^= 1u << b;
-                tc_fence_after();
-                const uint32_t tcol = tbase + lane_off + (uint32_t)(b * W) + (uint32_t)(grp * 32);
-                const int l_bwd = 2 * Lt - 1 - s;
-                if (s < Lt || l_bwd >= 1) {
-                    // this thread's accumulator columns in two passes of two K-blocks: K-block 0
-                    // is released after two TMEM loads, and half the registers stay live
-#pragma unroll
-                    for (int pass = 0; pass < (NKBW + 1) / 2; ++pass) {
-                    constexpr int PB = NKBW < 2 ? NKBW : 2;
-                    uint32_t raw[PB][32];
-#pragma unroll
-                    for (int i = 0; i < PB; ++i) TC_LD32(tcol + (2 * pass + i) * 64, raw[i]);
-                    tc_wait_ld();
-                    if (s < Lt) {
-#pragma unroll
-                        for (int i = 0; i < PB; ++i) {
-                            const int kb = 2 * pass + i;
-                            const int c0 = kb * 64 + grp * 32;
-                            if (s < Lt - 1) {
-                                // a = ReLU(acc) rounded to BF16 -> next A operand (the bias is in acc)
-                                uint32_t pk[16];
-#pragma unroll
-                                for (int q = 0; q < 16; ++q)
-                                    pk[q] = pack_relu(__uint_as_float(raw[i][2 * q]), __uint_as_float(raw[i][2 * q + 1]));
-                                masks[(s * (W / 32) + (c0 >> 5)) * 128 + r] = pos_bits32(raw[i]);
-#pragma unroll
-                                for (int m = 0; m < 4; ++m)
-                                    st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
-                                                 pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
-                                release_kb(actr, kb);
-                            } else {
-                                // delta of the last hidden layer: W_out[0] on active units
-                                uint32_t pk[16];
-#pragma unroll
-                                for (int q = 0; q < 16; ++q)
-                                    pk[q] = pack_bf16((int)raw[i][2 * q] > 0 ? head_s[c0 + 2 * q] : 0.f,
-                                                      (int)raw[i][2 * q + 1] > 0 ? head_s[c0 + 2 * q + 1] : 0.f);
-#pragma unroll
-                                for (int m = 0; m < 4; ++m)
-                                    st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
-                                                 pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
-                                release_kb(actr, kb);
-                            }
-                        }
-                    } else {
-                        // delta_{l-1} = (delta_l W_l) * 1[z_{l-1} > 0]
-#pragma unroll
-                        for (int i = 0; i < PB; ++i) {
-                            const int kb = 2 * pass + i;
-                            const int c0 = kb * 64 + grp * 32;
-                            const uint32_t bits = masks[((l_bwd - 1) * (W / 32) + (c0 >> 5)) * 128 + r];
-                            uint32_t pk[16];
-#pragma unroll
-                            for (int q = 0; q < 16; ++q)
-                                pk[q] = pack_bf16(((bits >> (2 * q)) & 1u) ? __uint_as_float(raw[i][2 * q]) : 0.f,
-                                                  ((bits >> (2 * q + 1)) & 1u) ? __uint_as_float(raw[i][2 * q + 1]) : 0.f);
-#pragma unroll
-                            for (int m = 0; m < 4; ++m)
-                                st_shared_v4(act_s + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
-                                             pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
-                            release_kb(actr, kb);
-                        }
-                    }
-                    }
-                } else if (grp == 0) {
-                    // d dist / d features (columns 0 .. K0-1), then the encoding chain rule
-                    const uint32_t tc0 = tbase + lane_off + (uint32_t)(b * W);
-                    float gx[3] = {0.f, 0.f, 0.f};
-                    for (int j = 0; j < 4; ++j) {
-                        if (32 * j >= a.K0) break;
-                        uint32_t raw[32];
-                        TC_LD32(tc0 + 32 * j, raw);
-                        tc_wait_ld();
-#pragma unroll
-                        for (int c = 0; c < 32; ++c) {
-                            const int p = 32 * j + c;
-                            const float gv = __uint_as_float(raw[c]);
-                            if (p < 3) {
-                                gx[p] += gv;
-                            } else if (p >= 8 && p - 2 < ti.E) {
-                                const int jj = (p - 8) % 6;
-                                if (jj < 3) gx[jj] = fmaf(gv, encode_dfeature(p - 2, v), gx[jj]);
-                            }
-                        }
-                    }
-                    tc_fence_before();
-                    if (valid) {
-                        const float3 nn = normal_from_grad(gx[0], gx[1], gx[2], v[3], v[4], v[5]);
-                        a.normals[row * 3 + 0] = nn.x;
-                        a.normals[row * 3 + 1] = nn.y;
-                        a.normals[row * 3 + 2] = nn.z;
-                    }
-                }
-            }
-        }
-    }
-    __syncthreads();
-    if (*(volatile int*)a.err) {
-        // error path: let MMAs and TMA copies already issued drain (they wait on nothing)
-        const uint64_t t0 = gtimer();
-        while (gtimer() - t0 < 200000ull) {
-        }
-        __syncthreads();
-    }
-    if (warp == 0) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols));
-    }
-}
 
 // Width 512. Shared memory holds the 128 x 512 BF16 activation tile (8 K-blocks, 128 KB) and a
 // ring of three 32 KB weight stages (one N-half of one K-block: 256 rows x 64 K); biases, the
@@ -2390,73 +2078,6 @@ struct Layout {
     int nst;
 };
 
-// Shared memory of the normals kernel: the A tile, the weight ring, the ReLU masks of every
-// hidden layer (a bit per row and unit), the ones tile and the bias slot of the bias MMA (both
-// 1 KB aligned) and the output head.
-Layout smem_layout(int W, int L, int K0) {
-    Layout s{};
-    const int kmaxb = std::max(K0 / 64, W / 64);
-    const uint32_t act = (uint32_t)kmaxb * 16384u;
-    const uint32_t stage = (uint32_t)W * 128u;
-    const uint32_t mask = ((uint32_t)L * 128u * (W / 32) * 4u + 1023u) & ~1023u;
-    const uint32_t ones = 4096u;
-    const uint32_t bias = (uint32_t)W * 32u;
-    const uint32_t head = ((uint32_t)(2 * W + 2) * 4u + 15u) & ~15u;
-    const uint32_t fixed = act + mask + ones + bias + head + 512u;
-    const uint32_t budget = 227u * 1024u - 1024u;   // minus alignment slack
-    int nst = (int)((budget - fixed) / stage);
-    s.nst = std::max(0, std::min(8, nst));
-    s.off_wst = act;
-    s.off_mask = act + (uint32_t)s.nst * stage;
-    s.off_grp = s.off_mask + mask;   // ones tile
-    s.off_bias = s.off_grp + ones;   // bias slot
-    s.off_head = s.off_bias + bias;
-    s.off_bar = s.off_head + head;
-    s.total = s.off_bar + 512u + 1024u;
-    return s;
-}
-
-template <int W, int MODE>
-int ensure_attr() {
-    static bool done = false;
-    if (!done) {
-        DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_tc_kernel<W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          227 * 1024));
-        done = true;
-    }
-    return DDF_OK;
-}
-
-template <int W>
-int launch_mode(const ddf_net_s* net, int mode, const TcArgs& base, int64_t n, bool use_count,
-                cudaStream_t stream, int nst_override = 0, int grid_override = 0,
-                const CUtensorMap* mapF = nullptr, const CUtensorMap* mapB = nullptr) {
-    const TcPack* P = net ? net->tc : nullptr;
-    TcArgs a = base;
-    const Layout s = smem_layout(W, a.L, a.K0);
-    if (s.nst < 2) return fail(DDF_ERR_UNSUPPORTED, "tensor-core MLP: shared memory too small");
-    a.nst = nst_override > 0 ? std::min(nst_override, s.nst) : s.nst;
-    a.off_wst = s.off_wst;
-    a.off_mask = s.off_mask;
-    a.off_grp = s.off_grp;
-    a.off_bias = s.off_bias;
-    a.off_head = s.off_head;
-    a.off_bar = s.off_bar;
-    a.bias_mn = P->bias_mn;
-    int grid = use_count ? num_sms() : (int)std::min<int64_t>((n + kTileM - 1) / kTileM, num_sms());
-    if (grid_override > 0) grid = grid_override;
-    if (grid <= 0) return DDF_OK;
-    const CUtensorMap& mf = mapF ? *mapF : P->map_fwd;
-    const CUtensorMap& mb = mapB ? *mapB : P->map_bwd;
-    // the forward (mode 0) and grouped (mode 2) queries run on mlp_pair_kernel
-    if (mode != 1) return fail(DDF_ERR_UNSUPPORTED, "one-tile MLP kernel: mode %d", mode);
-    int rc;
-    if ((rc = ensure_attr<W, 1>())) return rc;
-    mlp_tc_kernel<W, 1><<<grid, kThreads, s.total, stream>>>(mf, mb, a);
-    DDF_LAUNCH_CHECK();
-    return DDF_OK;
-}
-
 Layout smem_layout_pair(int W, int K0) {
     Layout s{};
     const int kmaxb = std::max(K0 / 64, W / 64);
@@ -2732,7 +2353,7 @@ bool tc_supported(const NetLayout& lay, int precision) {
     if (lay.width != 128 && lay.width != 256 && lay.width != 512) return false;
     if (lay.E + 2 > 128) return false;
     if (lay.width == 512) return lay.L >= 1 && lay.L <= kMaxLayers && smem512(3) <= 227u * 1024u;
-    return lay.L >= 1 && lay.L <= kMaxLayers && smem_layout(lay.width, lay.L, 64 * ((lay.E + 2 + 63) / 64)).nst >= 2;
+    return lay.L >= 1 && lay.L <= kMaxLayers && smem_layout_pair(lay.width, 64 * ((lay.E + 2 + 63) / 64)).nst >= 2;
 }
 
 void tc_free(ddf_net_s* net) {
@@ -2839,8 +2460,6 @@ int tc_forward_launch(const ddf_net_s* net, const TcArgs& a, int64_t n, bool use
 int tc_normals_launch(const ddf_net_s* net, const TcArgs& b, int64_t n, cudaStream_t stream) {
     const int W = net->lay.width;
     if (W == 512) return launch512(net, 1, b, n, true, stream);
-    if (getenv("DDF_NORMALS_ONE_TILE"))   // A/B switch while measuring (temporary)
-        return W == 128 ? launch_mode<128>(net, 1, b, n, true, stream) : launch_mode<256>(net, 1, b, n, true, stream);
     return W == 128 ? launch_pairn<128>(net, b, stream) : launch_pairn<256>(net, b, stream);
 }
 
