@@ -531,7 +531,9 @@ def main():
             "roofline": roof,
             "wavefront_roofline": wavefront_roofline,
             "e2e": e2e,
-            "gpu_launches": int(sum(v["launches"] for v in prof.values()) + args.steps * 2),
+            # per wave: raygen, a forward launch per bounce, a normals launch per bounce but the
+            # last, a shade launch per bounce, accumulate and the per-bounce count update
+            "gpu_launches": int(args.steps * -(-paths // (1 << 24)) * (3 * w["bounces"] + 2)),
             "clocks": clocks}
     if rank == 0:
         line["peaks_measured_here"] = meas

@@ -28,6 +28,7 @@
 
 #include <mutex>
 #include <string.h>
+#include <type_traits>
 #include <vector>
 
 #include "ddf_internal.cuh"
@@ -961,6 +962,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* wst = smem + a.off_wst;                    // NST x kStage
     uint8_t* ones = smem + a.off_mask;                  // 4 KB
     float* head_s = reinterpret_cast<float*>(smem + a.off_head);
+    float* part = reinterpret_cast<float*>(smem + a.off_part);   // [128][4]: group 1's gradient sums
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
     uint64_t* full = bars;
     uint64_t* empty = bars + NST;
@@ -1183,8 +1185,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         // feature sin(2^k pi x) has derivative 2^k pi cos(2^k pi x), cos(.) has
                         // -2^k pi sin(.); sin / cos of every octave by the double-angle recurrence
                         // from sincospif (as the forward's encoding computes them)
+                        // group g takes feature columns [64 g, 64 g + 64); group 1 hands its sums over
                         float gx[3] = {0.f, 0.f, 0.f};
-                        if (grp == 0) {
+                        {
                             constexpr int KO = kMaxFreqs / 2;
                             float sk[KO][3], ck[KO][3];
                             {
@@ -1205,36 +1208,52 @@ __global__ void __launch_bounds__(kThreads, 1)
                                     }
                             }
                             const int nf = a.F / 2;   // octaves of the encoding
-                            const uint32_t tc0 = tbase + lane_off + (uint32_t)(t * W);
+                            // the group's columns as compile-time indices (no local-memory arrays)
+                            auto chain = [&](auto gc) {
+                                constexpr int g = decltype(gc)::value;
+                                const uint32_t tc0 = tbase + lane_off + (uint32_t)(t * W + g * 64);
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                if (32 * j >= a.K0) break;
-                                uint32_t raw[32];
-                                TC_LD32(tc0 + 32 * j, raw);
-                                tc_wait_ld();
+                                for (int j = 0; j < 2; ++j) {
+                                    if (64 * g + 32 * j >= a.K0) break;
+                                    uint32_t raw[32];
+                                    TC_LD32(tc0 + 32 * j, raw);
+                                    tc_wait_ld();
 #pragma unroll
-                                for (int c = 0; c < 32; ++c) {
-                                    const int pf = 32 * j + c;
-                                    const float gv = __uint_as_float(raw[c]);
-                                    if (pf < 3) {
-                                        gx[pf] += gv;
-                                    } else if (pf >= 8) {
-                                        const int o = (pf - 8) / 12, rr = (pf - 8) % 12, jj = rr % 6;
-                                        if (jj < 3 && o < KO && o < nf)
-                                            gx[jj] = fmaf(gv, rr < 6 ? ck[o][jj] : sk[o][jj], gx[jj]);
+                                    for (int c = 0; c < 32; ++c) {
+                                        const int pf = 64 * g + 32 * j + c;
+                                        const float gv = __uint_as_float(raw[c]);
+                                        if (pf < 3) {
+                                            gx[pf] += gv;
+                                        } else if (pf >= 8) {
+                                            const int o = (pf - 8) / 12, rr = (pf - 8) % 12, jj = rr % 6;
+                                            if (jj < 3 && o < KO && o < nf)
+                                                gx[jj] = fmaf(gv, rr < 6 ? ck[o][jj] : sk[o][jj], gx[jj]);
+                                        }
                                     }
                                 }
-                            }
+                            };
+                            if (grp == 0) chain(std::integral_constant<int, 0>{});
+                            else chain(std::integral_constant<int, 1>{});
                         }
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&tfree[t]);
+                        if (grp == 1) {
+                            part[4 * r] = gx[0];
+                            part[4 * r + 1] = gx[1];
+                            part[4 * r + 2] = gx[2];
+                        }
+                        epi_bar();
                         if (grp == 0 && rcur[t] >= 0) {
+                            gx[0] += part[4 * r];
+                            gx[1] += part[4 * r + 1];
+                            gx[2] += part[4 * r + 2];
                             const float3 nn = normal_from_grad(gx[0], gx[1], gx[2], vcur[t][3], vcur[t][4], vcur[t][5]);
                             a.normals[rcur[t] * 3 + 0] = nn.x;
                             a.normals[rcur[t] * 3 + 1] = nn.y;
                             a.normals[rcur[t] * 3 + 2] = nn.z;
                         }
+                        epi_bar();   // part is rewritten by the other tile
                         // tile t of the next pair takes over
                         if (pn < npairs) {
                             rcur[t] = rnext[t];
@@ -2085,7 +2104,7 @@ Layout smem_layout_pair(int W, int K0) {
     const uint32_t stage = (uint32_t)W * 160u;            // weights K-block + bias tile
     const uint32_t ones = 4096u;
     const uint32_t head = ((uint32_t)(2 * W + 2) * 4u + 15u) & ~15u;
-    const uint32_t partb = 128u * 2u * 4u;
+    const uint32_t partb = 128u * 4u * 4u;   // head partial sums (forward) / gradient sums (normals)
     const uint32_t fixed = act + ones + head + partb + 512u;
     const uint32_t budget = 227u * 1024u - 1024u;
     s.nst = std::max(0, std::min(8, (int)((budget - fixed) / stage)));

@@ -29,8 +29,18 @@ struct CamDev {
 // Unit direction of path pid's primary ray: pixel pid / spp, jitter from the bounce-0 draw.
 __device__ __forceinline__ void primary_dir(const CamDev& cam, int64_t pid, int spp, float* dx, float* dy,
                                             float* dz) {
-    const int64_t pix = pid / spp;
-    const float x = (float)(pix % cam.W), y = (float)(pix / cam.W);
+    // pixel (x, y) of the path; 32-bit divisions whenever the id fits (every render below 2^32 paths)
+    int64_t xi, yi;
+    if (pid >= 0 && pid <= 0xFFFFFFFFll) {
+        const uint32_t pix = (uint32_t)pid / (uint32_t)spp;
+        yi = pix / (uint32_t)cam.W;
+        xi = pix - (uint32_t)yi * (uint32_t)cam.W;
+    } else {
+        const int64_t pix = pid / spp;
+        yi = pix / cam.W;
+        xi = pix - yi * cam.W;
+    }
+    const float x = (float)xi, y = (float)yi;
     const uint4 rnd = path_draw(cam.seed, (uint64_t)pid, 0u);
     const float px = (2.f * (x + u24(rnd.x)) / cam.W - 1.f) * cam.th * cam.aspect;
     const float py = (1.f - 2.f * (y + u24(rnd.y)) / cam.H) * cam.th;
@@ -66,39 +76,76 @@ __device__ __forceinline__ int block_compact(bool alive, int* counter, int* scra
     return slot;
 }
 
-// Camera rays of paths [pid0, pid0 + npaths), advanced to their entry into the unit ball.
+constexpr int kRaysPerThread = 4;   // camera rays generated per thread and block iteration
+
+// Camera rays of paths [pid0, pid0 + npaths), advanced to their entry into the unit ball. A block
+// iteration covers 4 x 256 paths in four rounds (round k: path c0 + 256 k + thread), so each
+// thread has four independent Philox draws in flight while every round's stores stay coalesced:
+// the survivors of round k of warp v go to slots base + prefix(k, v) + (rank in the warp's ballot),
+// one atomicAdd per 1,024 paths.
 __global__ void __launch_bounds__(kThreads) raygen_kernel(CamDev cam, int spp, int64_t pid0,
                                                           int64_t npaths, float* __restrict__ o,
                                                           float* __restrict__ w,
                                                           uint32_t* __restrict__ lid,
                                                           float* __restrict__ thr,
                                                           float* __restrict__ radiance, int* count) {
-    __shared__ int scratch[kThreads / 32 + 1];
-    for (int64_t i0 = (int64_t)blockIdx.x * kThreads; i0 < npaths; i0 += (int64_t)gridDim.x * kThreads) {
-        const int64_t i = i0 + threadIdx.x;
-        const bool valid = i < npaths;
-        bool alive = false;
-        float ox = 0, oy = 0, oz = 0, dx = 0, dy = 0, dz = 0;
-        if (valid) {
-            primary_dir(cam, pid0 + i, spp, &dx, &dy, &dz);
-            const float b = cam.eye[0] * dx + cam.eye[1] * dy + cam.eye[2] * dz;
-            const float c = cam.eye[0] * cam.eye[0] + cam.eye[1] * cam.eye[1] + cam.eye[2] * cam.eye[2] - 1.f;
-            const float disc = b * b - c;
-            const float sq = sqrtf(fmaxf(disc, 0.f));
-            alive = disc > 0.f && (-b + sq) > 0.f;
-            const float t0 = fmaxf(0.f, -b - sq);
-            ox = cam.eye[0] + t0 * dx;
-            oy = cam.eye[1] + t0 * dy;
-            oz = cam.eye[2] + t0 * dz;
-            if (!alive) radiance[i] = cam.env;
+    constexpr int kWarps = kThreads / 32;
+    __shared__ int scratch[kRaysPerThread * kWarps + 1];
+    constexpr int64_t kChunk = (int64_t)kThreads * kRaysPerThread;
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const float c = cam.eye[0] * cam.eye[0] + cam.eye[1] * cam.eye[1] + cam.eye[2] * cam.eye[2] - 1.f;
+    for (int64_t c0 = (int64_t)blockIdx.x * kChunk; c0 < npaths; c0 += (int64_t)gridDim.x * kChunk) {
+        float ov[kRaysPerThread][3], dv[kRaysPerThread][3];
+        unsigned ballot[kRaysPerThread];
+#pragma unroll
+        for (int k = 0; k < kRaysPerThread; ++k) {
+            const int64_t i = c0 + (int64_t)k * kThreads + threadIdx.x;
+            bool alive = false;
+            if (i < npaths) {
+                float dx, dy, dz;
+                primary_dir(cam, pid0 + i, spp, &dx, &dy, &dz);
+                const float b = cam.eye[0] * dx + cam.eye[1] * dy + cam.eye[2] * dz;
+                const float disc = b * b - c;
+                const float sq = sqrtf(fmaxf(disc, 0.f));
+                const float t0 = fmaxf(0.f, -b - sq);
+                ov[k][0] = cam.eye[0] + t0 * dx;
+                ov[k][1] = cam.eye[1] + t0 * dy;
+                ov[k][2] = cam.eye[2] + t0 * dz;
+                dv[k][0] = dx;
+                dv[k][1] = dy;
+                dv[k][2] = dz;
+                alive = disc > 0.f && (-b + sq) > 0.f;
+                if (!alive) radiance[i] = cam.env;
+            }
+            ballot[k] = __ballot_sync(0xffffffffu, alive);
         }
-        const int slot = block_compact(alive, count, scratch);
-        if (alive) {
-            o[3 * slot] = ox; o[3 * slot + 1] = oy; o[3 * slot + 2] = oz;
-            w[3 * slot] = dx; w[3 * slot + 1] = dy; w[3 * slot + 2] = dz;
-            lid[slot] = (uint32_t)i;
-            thr[slot] = 1.f;
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < kRaysPerThread; ++k) scratch[k * kWarps + warp] = __popc(ballot[k]);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int q = 0; q < kRaysPerThread * kWarps; ++q) {
+                const int cq = scratch[q];
+                scratch[q] = tot;
+                tot += cq;
+            }
+            scratch[kRaysPerThread * kWarps] = tot ? atomicAdd(count, tot) : 0;
         }
+        __syncthreads();
+        const int base = scratch[kRaysPerThread * kWarps];
+        const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+        for (int k = 0; k < kRaysPerThread; ++k) {
+            if ((ballot[k] >> lane) & 1u) {
+                const int slot = base + scratch[k * kWarps + warp] + __popc(ballot[k] & below);
+                o[3 * slot] = ov[k][0]; o[3 * slot + 1] = ov[k][1]; o[3 * slot + 2] = ov[k][2];
+                w[3 * slot] = dv[k][0]; w[3 * slot + 1] = dv[k][1]; w[3 * slot + 2] = dv[k][2];
+                lid[slot] = (uint32_t)(c0 + (int64_t)k * kThreads + threadIdx.x);
+                thr[slot] = 1.f;
+            }
+        }
+        __syncthreads();   // the scratch is rewritten by the next iteration
     }
 }
 
@@ -401,7 +448,7 @@ int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* i
         const int64_t npaths = npx * spp;
         DDF_CUDA_TRY(cudaMemsetAsync(B.counts, 0, sizeof(int) * (bounces + 1), stream));
         const int64_t pid0 = px0 * spp;
-        const int rg = (int)std::min<int64_t>((npaths + kThreads - 1) / kThreads, grid);
+        const int rg = (int)std::min<int64_t>((npaths + kThreads * kRaysPerThread - 1) / (kThreads * kRaysPerThread), grid);
         int pe = net->prof.begin(PROF_RAYGEN, stream);
         raygen_kernel<<<rg, kThreads, 0, stream>>>(cd, spp, pid0, npaths, B.o[0], B.w[0], B.lid[0],
                                                    B.thr[0], B.radiance, B.counts);
@@ -463,7 +510,7 @@ int render_aov(ddf_net_s* net, const ddf_camera* cam, float* depth, float* norma
         const int64_t npx = std::min(px_per_wave, npix - px0);
         DDF_CUDA_TRY(cudaMemsetAsync(B.counts, 0, sizeof(int), stream));
         aov_fill_kernel<<<grid, kThreads, 0, stream>>>(px0, npx, depth, normal);
-        const int rg = (int)std::min<int64_t>((npx + kThreads - 1) / kThreads, grid);
+        const int rg = (int)std::min<int64_t>((npx + kThreads * kRaysPerThread - 1) / (kThreads * kRaysPerThread), grid);
         raygen_kernel<<<rg, kThreads, 0, stream>>>(cd, 1, px0, npx, B.o[0], B.w[0], B.lid[0], B.thr[0], B.radiance,
                                                    B.counts);
         DDF_LAUNCH_CHECK();
@@ -527,7 +574,7 @@ int mesh_render(ddf_mesh_s* m, const ddf_camera* cam, int spp, int bounces, floa
         const int64_t pid0 = px0 * spp;
         e = cudaMemsetAsync(B.counts, 0, sizeof(int) * (bounces + 1), stream);
         if (e != cudaSuccess) break;
-        const int rg = (int)std::min<int64_t>((npaths + kThreads - 1) / kThreads, grid);
+        const int rg = (int)std::min<int64_t>((npaths + kThreads * kRaysPerThread - 1) / (kThreads * kRaysPerThread), grid);
         raygen_kernel<<<rg, kThreads, 0, stream>>>(cd, spp, pid0, npaths, B.o[0], B.w[0], B.lid[0], B.thr[0],
                                                    B.radiance, B.counts);
         for (int b = 1; b <= bounces && !rc; ++b) {
