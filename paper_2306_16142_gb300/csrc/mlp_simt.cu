@@ -2,10 +2,11 @@
 //
 // One persistent CTA per SM walks 64-row (or 32-row for width 512) tiles. A tile's inputs
 // are encoded in shared memory and every layer is evaluated on chip: activations live in two
-// shared buffers laid out [unit][row], weights stream from L2 in 32 x 128 chunks, each
-// thread keeps a TR x 8 register tile. ReLU masks are kept as bits so that, for hit rows,
-// the reverse pass d dist / d (o, w) (Sec. 4.2: the normal is the gradient of the field with
-// respect to the query point) runs through the same masks without re-reading activations.
+// shared buffers laid out [unit][row], weights stream from L2 in 32 x NC chunks (NC = 256 at
+// width 256, 128 otherwise), each thread keeps a TR x 8 register tile (8 x 8 at width 256).
+// ReLU masks are kept as bits so that, for hit rows, the reverse pass d dist / d (o, w)
+// (Sec. 4.2: the normal is the gradient of the field with respect to the query point) runs
+// through the same masks without re-reading activations.
 #include "ddf_internal.cuh"
 #include "device_common.cuh"
 
@@ -13,7 +14,6 @@ namespace ddf {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int NC = 128;   // output columns per chunk
 constexpr int KC = 32;    // reduction rows per staged weight chunk
 constexpr int TC = 8;     // columns per thread
 
@@ -35,14 +35,18 @@ struct MlpArgs {
 };
 
 // out[N][MT] = epi(sum_k in[k][MT] * B[k][n]) with B row-major K x N at Bg (row stride ldb).
-template <int MT, int EPI>
+// NC output columns per chunk; thread (tx, ty) owns rows ty TR .. +TR-1 and columns tx 8 .. +7.
+template <int MT, int EPI, int NC>
 __device__ void gemm_layer(const float* __restrict__ Bg, int ldb, int K, int N,
                            const float* __restrict__ in, float* __restrict__ out,
                            float* __restrict__ Ws, const float* __restrict__ bias,
                            uint32_t* __restrict__ mask) {
-    constexpr int TR = MT / 16;
+    constexpr int NTX = NC / TC;             // threads across a chunk's columns
+    constexpr int TR = MT * NTX / kThreads;  // rows per thread
+    static_assert(TR == 2 || TR == 4 || TR == 8, "register tile");
     constexpr int MW = MT / 32;   // mask words per unit
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    constexpr int NQ = KC * NC / 4 / kThreads;   // float4 staging loads per thread and chunk
+    const int tid = threadIdx.x, tx = tid % NTX, ty = tid / NTX;
     const bool vec = (ldb % 4) == 0;
     for (int n0 = 0; n0 < N; n0 += NC) {
         float acc[TR][TC];
@@ -50,12 +54,12 @@ __device__ void gemm_layer(const float* __restrict__ Bg, int ldb, int K, int N,
         for (int i = 0; i < TR; ++i)
 #pragma unroll
             for (int j = 0; j < TC; ++j) acc[i][j] = 0.f;
-        float pre[16];
+        float pre[4 * NQ];
         auto load_chunk = [&](int k0) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < NQ; ++q) {
                 const int idx4 = tid + kThreads * q;
-                const int kk = idx4 >> 5, c = n0 + (idx4 & 31) * 4;
+                const int kk = idx4 / (NC / 4), c = n0 + (idx4 % (NC / 4)) * 4;
                 const int k = k0 + kk;
                 if (k < K && vec && c + 3 < N) {
                     const float4 v = *reinterpret_cast<const float4*>(Bg + (int64_t)k * ldb + c);
@@ -74,9 +78,9 @@ __device__ void gemm_layer(const float* __restrict__ Bg, int ldb, int K, int N,
         for (int k0 = 0; k0 < K; k0 += KC) {
             __syncthreads();
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < NQ; ++q) {
                 const int idx4 = tid + kThreads * q;
-                *reinterpret_cast<float4*>(Ws + (idx4 >> 5) * NC + (idx4 & 31) * 4) =
+                *reinterpret_cast<float4*>(Ws + (idx4 / (NC / 4)) * NC + (idx4 % (NC / 4)) * 4) =
                     make_float4(pre[4 * q], pre[4 * q + 1], pre[4 * q + 2], pre[4 * q + 3]);
             }
             __syncthreads();
@@ -85,7 +89,12 @@ __device__ void gemm_layer(const float* __restrict__ Bg, int ldb, int K, int N,
             for (int kk = 0; kk < kn; ++kk) {
                 float a[TR], b[TC];
                 const float* ap = in + (k0 + kk) * MT + ty * TR;
-                if constexpr (TR == 4) {
+                if constexpr (TR == 8) {
+                    const float4 v0 = *reinterpret_cast<const float4*>(ap);
+                    const float4 v1 = *reinterpret_cast<const float4*>(ap + 4);
+                    a[0] = v0.x; a[1] = v0.y; a[2] = v0.z; a[3] = v0.w;
+                    a[4] = v1.x; a[5] = v1.y; a[6] = v1.z; a[7] = v1.w;
+                } else if constexpr (TR == 4) {
                     const float4 v = *reinterpret_cast<const float4*>(ap);
                     a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
                 } else {
@@ -127,16 +136,20 @@ __device__ void gemm_layer(const float* __restrict__ Bg, int ldb, int K, int N,
 #pragma unroll
                 for (int i = 0; i < TR; ++i) v[i] = acc[i][j];
             }
-            if constexpr (TR == 4)
+            if constexpr (TR == 8) {
                 *reinterpret_cast<float4*>(out + nn * MT + r0) = make_float4(v[0], v[1], v[2], v[3]);
-            else
+                *reinterpret_cast<float4*>(out + nn * MT + r0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+            } else if constexpr (TR == 4) {
+                *reinterpret_cast<float4*>(out + nn * MT + r0) = make_float4(v[0], v[1], v[2], v[3]);
+            } else {
                 *reinterpret_cast<float2*>(out + nn * MT + r0) = make_float2(v[0], v[1]);
+            }
         }
     }
     __syncthreads();
 }
 
-template <int MT>
+template <int MT, int NC>
 __global__ void __launch_bounds__(kThreads, 1) mlp_fp32_kernel(const MlpArgs a) {
     extern __shared__ __align__(16) float smem[];
     constexpr int MW = MT / 32;
@@ -176,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fp32_kernel(const MlpArgs a) 
         float* nxt = bufB;
         int K = E;
         for (int l = 0; l < L; ++l) {
-            gemm_layer<MT, EPI_FWD>(a.Wt + lay.w_off[l], W, K, W, cur, nxt, Ws, a.W + lay.b_off[l],
+            gemm_layer<MT, EPI_FWD, NC>(a.Wt + lay.w_off[l], W, K, W, cur, nxt, Ws, a.W + lay.b_off[l],
                                     masks + l * W * MW);
             float* t = cur; cur = nxt; nxt = t;
             K = W;
@@ -231,11 +244,11 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fp32_kernel(const MlpArgs a) 
         }
         __syncthreads();
         for (int l = L - 1; l >= 1; --l) {
-            gemm_layer<MT, EPI_BWD>(a.W + lay.w_off[l], W, W, W, cur, nxt, Ws, nullptr,
+            gemm_layer<MT, EPI_BWD, NC>(a.W + lay.w_off[l], W, W, W, cur, nxt, Ws, nullptr,
                                     masks + (l - 1) * W * MW);
             float* t = cur; cur = nxt; nxt = t;
         }
-        gemm_layer<MT, EPI_PLAIN>(a.W + lay.w_off[0], E, W, E, cur, nxt, Ws, nullptr, nullptr);
+        gemm_layer<MT, EPI_PLAIN, NC>(a.W + lay.w_off[0], E, W, E, cur, nxt, Ws, nullptr, nullptr);
         if (tid < rows && flag[tid]) {
             float v[6];
 #pragma unroll
@@ -255,19 +268,19 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fp32_kernel(const MlpArgs a) 
     }
 }
 
-template <int MT>
+template <int MT, int NC>
 size_t smem_bytes(const NetLayout& lay, int kmax) {
     return sizeof(float) * (2 * (size_t)kmax * MT + KC * NC) +
            sizeof(uint32_t) * (size_t)lay.L * lay.width * (MT / 32) + sizeof(float) * 6 * MT +
            sizeof(float) * 2 * kThreads + sizeof(int) * kThreads;
 }
 
-template <int MT>
+template <int MT, int NC>
 int launch(const MlpArgs& a, int64_t n, cudaStream_t stream) {
-    const size_t sm = smem_bytes<MT>(a.lay, a.kmax);
+    const size_t sm = smem_bytes<MT, NC>(a.lay, a.kmax);
     static bool attr_done = false;
     if (!attr_done) {
-        DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_fp32_kernel<MT>,
+        DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_fp32_kernel<MT, NC>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         attr_done = true;
     }
@@ -276,7 +289,7 @@ int launch(const MlpArgs& a, int64_t n, cudaStream_t stream) {
     int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms());
     if (a.d_count) grid = num_sms();
     if (grid <= 0) return DDF_OK;
-    mlp_fp32_kernel<MT><<<grid, kThreads, sm, stream>>>(a);
+    mlp_fp32_kernel<MT, NC><<<grid, kThreads, sm, stream>>>(a);
     DDF_LAUNCH_CHECK();
     return DDF_OK;
 }
@@ -350,8 +363,9 @@ int mlp_fp32_query(const ddf_net_s* net, const float* o, const float* w, int64_t
     a.hit = hit;
     a.normals = normals;
     a.kmax = std::max(net->lay.width, net->lay.E);
-    if (net->lay.width <= 256) return launch<64>(a, n, stream);
-    return launch<32>(a, n, stream);
+    if (net->lay.width == 256) return launch<64, 256>(a, n, stream);
+    if (net->lay.width < 256) return launch<64, 128>(a, n, stream);
+    return launch<32, 128>(a, n, stream);
 }
 
 int sphere_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
