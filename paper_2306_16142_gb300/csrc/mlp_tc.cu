@@ -53,6 +53,8 @@ namespace {
 constexpr int kEpiWarps = 8;
 constexpr int kMaxGroup = 64;
 constexpr int kThreads = (kEpiWarps + 2) * 32;
+// The pair kernels: one more warp, so that each tile of the pair has its own MMA-issuing thread.
+constexpr int kThreadsP = (kEpiWarps + 3) * 32;
 constexpr int kTileM = 128;
 
 struct TcArgs {
@@ -587,7 +589,7 @@ struct PairInfo {
 // tiles (issued by the MMA thread once every epilogue warp has released the K-block), a_L and the
 // ReLU masks of a_1 .. a_{L-1} by the epilogue.
 template <int W, bool GRP, bool TRAIN>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreadsP, 1)
     mlp_pair_kernel(const __grid_constant__ CUtensorMap mapF, const __grid_constant__ CUtensorMap mapA0,
                     const __grid_constant__ CUtensorMap mapAct, const TcArgs a) {
     static_assert(!(GRP && TRAIN), "grouped launches are queries");
@@ -655,7 +657,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         for (int i = 0; i < NST; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
+            mbar_init(&empty[i], 2);   // both tiles' MMA threads release a stage
         }
         for (int i = 0; i < 8; ++i) mbar_init(&actr[i], kEpiWarps);
         mbar_init(&accf[0], 1);
@@ -670,13 +672,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     // the ones tile: K rows 0 and 1 of both 64-row MN atoms are 1.0 (BF16 0x3F80), the rest 0
-    for (int i = tid; i < 1024; i += kThreads) {
+    for (int i = tid; i < 1024; i += kThreadsP) {
         const int line = (i >> 5) & 15;   // K row within the atom (32 words of 4 bytes per line)
         reinterpret_cast<uint32_t*>(ones)[i] = line < 2 ? 0x3F803F80u : 0u;
     }
     fence_proxy_async();
     if (!GRP)
-        for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
+        for (int i = tid; i < 2 * W + 2; i += kThreadsP) head_s[i] = a.head[i];
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
@@ -701,56 +703,57 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
-    } else if (warp == kEpiWarps + 1) {
-        // ---------------------------------------------------------------- MMA issuer
+    } else if (warp == kEpiWarps + 1 || warp == kEpiWarps + 2) {
+        // ---------------------------------------------------------------- MMA issuers
+        // one thread per tile of the pair: both read every weight stage (the stage is released
+        // by two commits), each waits only on its own tile's A K-blocks and accumulator
         if (lane == 0) {
-            uint32_t cnt = 0, actph = 0, tfph = 0;
+            const int t = warp - (kEpiWarps + 1);
+            uint32_t stg = 0, ring_ph = 0, actph = 0, tfph = 0;
             bool ok = true, first = true;
-            const uint32_t act_s = su32(act), wst_s = su32(wst);
+            const uint32_t act_t = su32(act) + (uint32_t)t * kTile, wst_s = su32(wst);
             const uint32_t idesc = idesc_bf16(128, W);
             const uint32_t idesc_b = idesc_bf16(128, W) | (3u << 15);   // both operands MN-major
             const uint64_t ones_d = sdesc_mn16(su32(ones));
+            const uint32_t d = tbase + (uint32_t)(t * W);
             for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x) {
                 const PairInfo pi = pair_info(p);
                 for (int s = 0; s < pi.L && ok; ++s) {
-                    // K-block by K-block, tile 0 then tile 1 on each weight stage; a tile's
-                    // accumulator is committed right after its last K-block
+                    // K-block by K-block; the tile's accumulator is committed after its last one
                     const int nk = s == 0 ? pi.KB0 : NKBW;
-                    for (int kb = 0; kb < nk && ok; ++kb, ++cnt) {
-                        const int stg = (int)(cnt % (uint32_t)NST);
-                        if (!mbar_wait(&full[stg], (cnt / (uint32_t)NST) & 1u, a.err)) { ok = false; break; }
-                        const uint32_t sb = wst_s + (uint32_t)stg * kStage;
-                        for (int t = 0; t < 2; ++t) {
-                            const int ab = 4 * t + kb;
-                            if (!mbar_wait(&actr[ab], (actph >> ab) & 1u, a.err)) { ok = false; break; }
-                            actph ^= 1u << ab;
-                            if (TRAIN && t * kTileM < pi.rows) {   // a_s of this tile to the workspace
-                                tma_store_3d(s == 0 ? &mapA0 : &mapAct,
-                                             act_s + (uint32_t)t * kTile + (uint32_t)kb * 16384u, kb * 64,
-                                             (int)(pi.row0 + t * kTileM), s == 0 ? 0 : s - 1);
-                                bulk_commit();
-                            }
-                            // the bias MMA overwrites the whole accumulator: wait until the
-                            // epilogue has read the tile's previous layer
-                            if (kb == 0 && !first) {
-                                if (!mbar_wait(&tfree[t], (tfph >> t) & 1u, a.err)) { ok = false; break; }
-                                tfph ^= 1u << t;
-                            }
-                            tc_fence_after();
-                            const uint32_t d = tbase + (uint32_t)(t * W);
-                            if (kb == 0) mma_bf16(d, ones_d, sdesc_mn16(sb + kWBytes), idesc_b, 0u);   // D = b
-                            const uint64_t ad = sdesc(act_s + (uint32_t)t * kTile + (uint32_t)kb * 16384u);
-                            const uint64_t bd = sdesc(sb);
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, 1u);
-                            if (kb == nk - 1) {
-                                // the epilogue overwrites the A tile after this commit: the stores
-                                // must have read it
-                                if (TRAIN) bulk_wait_read();
-                                mma_commit(&accf[t]);
-                            }
+                    for (int kb = 0; kb < nk; ++kb) {
+                        if (!mbar_wait(&full[stg], ring_ph, a.err)) { ok = false; break; }
+                        if (!mbar_wait(&actr[4 * t + kb], (actph >> kb) & 1u, a.err)) { ok = false; break; }
+                        actph ^= 1u << kb;
+                        if (TRAIN && t * kTileM < pi.rows) {   // a_s of this tile to the workspace
+                            tma_store_3d(s == 0 ? &mapA0 : &mapAct, act_t + (uint32_t)kb * 16384u, kb * 64,
+                                         (int)(pi.row0 + t * kTileM), s == 0 ? 0 : s - 1);
+                            bulk_commit();
                         }
-                        if (ok) mma_commit(&empty[stg]);   // both tiles have read the stage
+                        // the bias MMA overwrites the whole accumulator: wait until the
+                        // epilogue has read the tile's previous layer
+                        if (kb == 0 && !first) {
+                            if (!mbar_wait(&tfree[t], tfph, a.err)) { ok = false; break; }
+                            tfph ^= 1u;
+                        }
+                        tc_fence_after();
+                        const uint32_t sb = wst_s + stg * kStage;
+                        if (kb == 0) mma_bf16(d, ones_d, sdesc_mn16(sb + kWBytes), idesc_b, 0u);   // D = b
+                        const uint64_t ad = sdesc(act_t + (uint32_t)kb * 16384u);
+                        const uint64_t bd = sdesc(sb);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, 1u);
+                        if (kb == nk - 1) {
+                            // the epilogue overwrites the A tile after this commit: the stores
+                            // must have read it
+                            if (TRAIN) bulk_wait_read();
+                            mma_commit(&accf[t]);
+                        }
+                        mma_commit(&empty[stg]);   // this tile has read the stage
+                        if (++stg == (uint32_t)NST) {
+                            stg = 0;
+                            ring_ph ^= 1u;
+                        }
                     }
                     first = false;
                 }
@@ -945,7 +948,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // As in the forward pair kernel both tiles consume every weight stage and one tile's epilogue
 // runs while the other tile is multiplied. Rows are those of the hit list a.rows, count *a.d_count.
 template <int W>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreadsP, 1)
     mlp_pairn_kernel(const __grid_constant__ CUtensorMap mapF, const __grid_constant__ CUtensorMap mapB,
                      const TcArgs a) {
     constexpr int NKBW = W / 64;
@@ -983,7 +986,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         for (int i = 0; i < NST; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
+            mbar_init(&empty[i], 2);   // both tiles' MMA threads release a stage
         }
         for (int i = 0; i < 8; ++i) mbar_init(&actr[i], kEpiWarps);
         mbar_init(&accf[0], 1);
@@ -998,10 +1001,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     // the ones tile: K rows 0 and 1 of both 64-row MN atoms are 1.0 (BF16 0x3F80), the rest 0
-    for (int i = tid; i < 1024; i += kThreads)
+    for (int i = tid; i < 1024; i += kThreadsP)
         reinterpret_cast<uint32_t*>(ones)[i] = ((i >> 5) & 15) < 2 ? 0x3F803F80u : 0u;
     fence_proxy_async();
-    for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
+    for (int i = tid; i < 2 * W + 2; i += kThreadsP) head_s[i] = a.head[i];
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
@@ -1025,43 +1028,45 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
         }
-    } else if (warp == kEpiWarps + 1) {
-        // ---------------------------------------------------------------- MMA issuer
+    } else if (warp == kEpiWarps + 1 || warp == kEpiWarps + 2) {
+        // ---------------------------------------------------------------- MMA issuers
+        // one thread per tile of the pair, as in the forward pair kernel
         if (lane == 0) {
-            uint32_t cnt = 0, actph = 0, tfph = 0;
+            const int t = warp - (kEpiWarps + 1);
+            uint32_t stg = 0, ring_ph = 0, actph = 0, tfph = 0;
             bool ok = true, first = true;
-            const uint32_t act_s = su32(act), wst_s = su32(wst);
+            const uint32_t act_t = su32(act) + (uint32_t)t * kTile, wst_s = su32(wst);
             const uint32_t idesc_b = idesc_bf16(128, W) | (3u << 15);   // both operands MN-major
             const uint64_t ones_d = sdesc_mn16(su32(ones));
+            const uint32_t d = tbase + (uint32_t)(t * W);
             for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x)
                 for (int s = 0; s < nsteps && ok; ++s) {
                     const Step st = step_of<W>(s, L, KB0);
                     const uint32_t idesc = idesc_bf16(128, st.N);
-                    for (int kb = 0; kb < st.nk && ok; ++kb, ++cnt) {
-                        const int stg = (int)(cnt % (uint32_t)NST);
-                        if (!mbar_wait(&full[stg], (cnt / (uint32_t)NST) & 1u, a.err)) { ok = false; break; }
-                        const uint32_t sb = wst_s + (uint32_t)stg * kStage;
-                        for (int t = 0; t < 2; ++t) {
-                            const int ab = 4 * t + kb;
-                            if (!mbar_wait(&actr[ab], (actph >> ab) & 1u, a.err)) { ok = false; break; }
-                            actph ^= 1u << ab;
-                            // the step's first MMA overwrites the accumulator: wait until the
-                            // epilogue has read the tile's previous step
-                            if (kb == 0 && !first) {
-                                if (!mbar_wait(&tfree[t], (tfph >> t) & 1u, a.err)) { ok = false; break; }
-                                tfph ^= 1u << t;
-                            }
-                            tc_fence_after();
-                            const uint32_t d = tbase + (uint32_t)(t * W);
-                            if (!st.bwd && kb == 0) mma_bf16(d, ones_d, sdesc_mn16(sb + kWBytes), idesc_b, 0u);   // D = b
-                            const uint64_t ad = sdesc(act_s + (uint32_t)t * kTile + (uint32_t)kb * 16384u);
-                            const uint64_t bd = sdesc(sb);
-#pragma unroll
-                            for (int k = 0; k < 4; ++k)
-                                mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, st.bwd ? (uint32_t)((kb | k) != 0) : 1u);
-                            if (kb == st.nk - 1) mma_commit(&accf[t]);
+                    for (int kb = 0; kb < st.nk; ++kb) {
+                        if (!mbar_wait(&full[stg], ring_ph, a.err)) { ok = false; break; }
+                        if (!mbar_wait(&actr[4 * t + kb], (actph >> kb) & 1u, a.err)) { ok = false; break; }
+                        actph ^= 1u << kb;
+                        // the step's first MMA overwrites the accumulator: wait until the
+                        // epilogue has read the tile's previous step
+                        if (kb == 0 && !first) {
+                            if (!mbar_wait(&tfree[t], tfph, a.err)) { ok = false; break; }
+                            tfph ^= 1u;
                         }
-                        if (ok) mma_commit(&empty[stg]);   // both tiles have read the stage
+                        tc_fence_after();
+                        const uint32_t sb = wst_s + stg * kStage;
+                        if (!st.bwd && kb == 0) mma_bf16(d, ones_d, sdesc_mn16(sb + kWBytes), idesc_b, 0u);   // D = b
+                        const uint64_t ad = sdesc(act_t + (uint32_t)kb * 16384u);
+                        const uint64_t bd = sdesc(sb);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            mma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, st.bwd ? (uint32_t)((kb | k) != 0) : 1u);
+                        if (kb == st.nk - 1) mma_commit(&accf[t]);
+                        mma_commit(&empty[stg]);   // this tile has read the stage
+                        if (++stg == (uint32_t)NST) {
+                            stg = 0;
+                            ring_ph ^= 1u;
+                        }
                     }
                     first = false;
                 }
@@ -2151,7 +2156,7 @@ int launch_pair(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_co
     if (grid <= 0) return DDF_OK;
     int rc = ensure_pair_attr<W, GRP, TRAIN>();
     if (rc) return rc;
-    mlp_pair_kernel<W, GRP, TRAIN><<<grid, kThreads, s.total, stream>>>(
+    mlp_pair_kernel<W, GRP, TRAIN><<<grid, kThreadsP, s.total, stream>>>(
         P->map_fwd, mapA0 ? *mapA0 : P->map_fwd, mapAct ? *mapAct : P->map_fwd, a);
     DDF_LAUNCH_CHECK();
     return DDF_OK;
@@ -2178,7 +2183,7 @@ int launch_pairn(const ddf_net_s* net, const TcArgs& base, cudaStream_t stream) 
         DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_pairn_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         attr = true;
     }
-    mlp_pairn_kernel<W><<<num_sms(), kThreads, s.total, stream>>>(P->map_fwd, P->map_bwd, a);
+    mlp_pairn_kernel<W><<<num_sms(), kThreadsP, s.total, stream>>>(P->map_fwd, P->map_bwd, a);
     DDF_LAUNCH_CHECK();
     return DDF_OK;
 }
