@@ -607,7 +607,6 @@ __global__ void __launch_bounds__(kThreadsP, 1)
     uint8_t* wst = smem + a.off_wst;                    // NST x kStage
     uint8_t* ones = smem + a.off_mask;                  // 4 KB
     float* head_s = reinterpret_cast<float*>(smem + a.off_head);
-    float* part = reinterpret_cast<float*>(smem + a.off_part);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
     uint64_t* full = bars;
     uint64_t* empty = bars + NST;
@@ -677,8 +676,10 @@ __global__ void __launch_bounds__(kThreadsP, 1)
         reinterpret_cast<uint32_t*>(ones)[i] = line < 2 ? 0x3F803F80u : 0u;
     }
     fence_proxy_async();
+    // the output head interleaved, (W_out[0][c], W_out[1][c]) for c < W, then b_out
     if (!GRP)
-        for (int i = tid; i < 2 * W + 2; i += kThreadsP) head_s[i] = a.head[i];
+        for (int i = tid; i < 2 * W + 2; i += kThreadsP)
+            head_s[i] = i < 2 * W ? a.head[(i & 1) * W + (i >> 1)] : a.head[i];
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
@@ -801,10 +802,102 @@ __global__ void __launch_bounds__(kThreadsP, 1)
         auto load_head = [&](const PairInfo& pi) {
             if (GRP && pi.obj != cur_obj) {
                 epi_bar();
-                for (int i2 = tid; i2 < 2 * W + 2; i2 += 256) head_s[i2] = pi.head[i2];
+                for (int i2 = tid; i2 < 2 * W + 2; i2 += 256)
+                    head_s[i2] = i2 < 2 * W ? pi.head[(i2 & 1) * W + (i2 >> 1)] : pi.head[i2];
                 epi_bar();
                 cur_obj = pi.obj;
             }
+        };
+        // the last layer (queries): group g serves tile g alone, every column of row r: the output
+        // head, the outputs, then the next pair's encoding of the tile, so that the tile's next
+        // layer 0 does not wait for the other tile's epilogue
+        auto last_layer = [&](const PairInfo& pi, const PairInfo& pnext, bool has_next) -> bool {
+            const int t = grp;
+            float vn[6];
+            load_row(pnext, has_next, t, vn);
+            // this group reads none of the other tile's accumulator
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tfree[1 - t]);
+            const bool okw = mbar_wait(&accf[t], (accph >> t) & 1u, a.err);
+            if (!__all_sync(0xffffffffu, okw)) return false;
+            accph ^= 3u;   // both tiles' accumulators have moved on a phase
+            tc_fence_after();
+            const uint32_t tcol = tbase + lane_off + (uint32_t)(t * W);
+            const float2* h2 = reinterpret_cast<const float2*>(head_s);
+            float y0 = 0.f, y1 = 0.f;
+#pragma unroll 1
+            for (int kb = 0; kb < NKBW; ++kb) {
+                uint32_t raw[2][32];
+                TC_LD32(tcol + kb * 64, raw[0]);
+                TC_LD32(tcol + kb * 64 + 32, raw[1]);
+                tc_wait_ld();
+                if (kb == NKBW - 1) {   // accumulator read: the next pair's layer 0 may overwrite it
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tfree[t]);
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int c = 0; c < 32; c += 2) {
+                        const float4 hh = *reinterpret_cast<const float4*>(&h2[kb * 64 + i * 32 + c]);
+                        const float z0 = fmaxf(__uint_as_float(raw[i][c]), 0.f);
+                        const float z1 = fmaxf(__uint_as_float(raw[i][c + 1]), 0.f);
+                        fma2p(z0, z0, hh.x, hh.y, y0, y1, y0, y1);
+                        fma2p(z1, z1, hh.z, hh.w, y0, y1, y0, y1);
+                    }
+            }
+            // outputs of the row, and the hit list (one atomic per warp)
+            {
+                const int64_t i = pi.row0 + t * kTileM + r;
+                const bool valid = t * kTileM + r < pi.rows;
+                y0 += head_s[2 * W];
+                y1 += head_s[2 * W + 1];
+                const bool hh = y1 > 0.f;
+                if (valid) {
+                    a.dist[i] = y0;
+                    if (a.logit) a.logit[i] = y1;
+                    if (a.hit) a.hit[i] = (uint8_t)hh;
+                }
+                if (a.hit_list) {
+                    const bool take = valid && hh;
+                    const unsigned m = __ballot_sync(0xffffffffu, take);
+                    int base = 0;
+                    if (lane == 0 && m) base = atomicAdd(a.hit_count, __popc(m));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (take) a.hit_list[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
+                }
+            }
+            if (has_next) {
+                // the next pair's layer 0 of tile t: every K-block of row r by this thread; the
+                // other tile's K-blocks are written by the other group (this warp's arrival for them
+                // carries no write)
+                const uint32_t base = act_s + (uint32_t)t * kTile;
+                {
+                    uint32_t pk[32];
+                    encode_kblock<0>(vn, pnext.F, pk);
+#pragma unroll
+                    for (int m = 0; m < 8; ++m)
+                        st_shared_v4(base + swz(r, m), pk[4 * m], pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
+                }
+                if (pnext.KB0 > 1) {
+                    uint32_t pk[32];
+                    encode_kblock<1>(vn, pnext.F, pk);
+#pragma unroll
+                    for (int m = 0; m < 8; ++m)
+                        st_shared_v4(base + 16384u + swz(r, m), pk[4 * m], pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
+                }
+                fence_proxy_async();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    for (int kb = 0; kb < pnext.KB0; ++kb) {
+                        mbar_arrive(&actr[4 * t + kb]);
+                        mbar_arrive(&actr[4 * (1 - t) + kb]);
+                    }
+            }
+            return true;
         };
         float vnext[2][6];
         PairInfo pcur{};
@@ -823,7 +916,11 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             load_head(pi);
             const int L = pi.L;
             for (int s = 0; s < L && ok; ++s) {
-                if (s == L - 1) {
+                if (!TRAIN && s == L - 1) {
+                    ok = last_layer(pi, pnext, has_next);
+                    break;
+                }
+                if (TRAIN && s == L - 1) {
                     load_row(pnext, has_next, 0, vnext[0]);
                     load_row(pnext, has_next, 1, vnext[1]);
                 }
@@ -834,7 +931,6 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     tc_fence_after();
                     const uint32_t tcol = tbase + lane_off + (uint32_t)(t * W) + (uint32_t)(grp * 32);
                     const uint32_t tact = act_s + (uint32_t)t * kTile;
-                    float y0 = 0.f, y1 = 0.f;
                     // pairs of K-blocks per TMEM wait
 #pragma unroll
                     for (int pass = 0; pass < NKBW / 2; ++pass) {
@@ -878,50 +974,10 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                                     for (int m = 0; m < 4; ++m)
                                         dst[m] = make_uint4(pk[4 * m], pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
                                 }
-                            } else {
-                                // output head on this thread's columns (FP32)
-#pragma unroll
-                                for (int c = 0; c < 32; ++c) {
-                                    const float z = fmaxf(__uint_as_float(raw[i][c]), 0.f);
-                                    y0 = fmaf(z, head_s[c0 + c], y0);
-                                    y1 = fmaf(z, head_s[W + c0 + c], y1);
-                                }
                             }
                         }
                     }
-                    if (TRAIN && s == L - 1) {
-                        if (has_next) encode(t, vnext[t], pnext);
-                    } else if (s == L - 1) {
-                        // outputs, then tile t of the next pair takes over the accumulator
-                        tc_fence_before();
-                        if (grp == 1) {
-                            part[2 * r] = y0;
-                            part[2 * r + 1] = y1;
-                        }
-                        epi_bar();
-                        if (grp == 0) {
-                            const int64_t i = pi.row0 + t * kTileM + r;
-                            const bool valid = t * kTileM + r < pi.rows;
-                            y0 += part[2 * r] + head_s[2 * W];
-                            y1 += part[2 * r + 1] + head_s[2 * W + 1];
-                            const bool hh = y1 > 0.f;
-                            if (valid) {
-                                a.dist[i] = y0;
-                                if (a.logit) a.logit[i] = y1;
-                                if (a.hit) a.hit[i] = (uint8_t)hh;
-                            }
-                            if (a.hit_list) {
-                                const bool take = valid && hh;
-                                const unsigned m = __ballot_sync(0xffffffffu, take);
-                                int base = 0;
-                                if (lane == 0 && m) base = atomicAdd(a.hit_count, __popc(m));
-                                base = __shfl_sync(0xffffffffu, base, 0);
-                                if (take) a.hit_list[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
-                            }
-                        }
-                        epi_bar();
-                        if (has_next) encode(t, vnext[t], pnext);
-                    }
+                    if (TRAIN && s == L - 1 && has_next) encode(t, vnext[t], pnext);
                 }
             }
             pcur = pnext;
