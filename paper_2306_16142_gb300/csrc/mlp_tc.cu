@@ -815,6 +815,9 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             const int t = grp;
             float vn[6];
             load_row(pnext, has_next, t, vn);
+            // both groups are done with layer L - 2 (every arrival of its phases is in), so this
+            // group's arrivals for the other tile below belong to the phases that follow
+            epi_bar();
             // this group reads none of the other tile's accumulator
             tc_fence_before();
             __syncwarp();
@@ -1021,7 +1024,6 @@ __global__ void __launch_bounds__(kThreadsP, 1)
     uint8_t* wst = smem + a.off_wst;                    // NST x kStage
     uint8_t* ones = smem + a.off_mask;                  // 4 KB
     float* head_s = reinterpret_cast<float*>(smem + a.off_head);
-    float* part = reinterpret_cast<float*>(smem + a.off_part);   // [128][4]: group 1's gradient sums
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
     uint64_t* full = bars;
     uint64_t* empty = bars + NST;
@@ -1148,37 +1150,128 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                 vv[c + 3] = valid ? a.w[row * 3 + c] : 0.f;
             }
         };
-        // layer 0 of tile t: group g writes first-layer K-block g; every warp arrives on each
-        auto encode = [&](int t, const float* vv) {
-            if (grp < KB0) {
+        // Group g owns tile g's rows at both ends of a pair: it encodes the row's layer-0 input
+        // (every K-block of row r of tile g) and turns the row's feature gradient into its normal.
+        // Its warps' arrivals on the other tile's K-block barriers carry no write.
+        auto encode_tile = [&](const float* vv) {
+            const uint32_t base = act_s + (uint32_t)grp * kTile;
+            {
                 uint32_t pk[32];
-                if (grp == 0) encode_kblock<0>(vv, a.F, pk);
-                else encode_kblock<1>(vv, a.F, pk);
-                const uint32_t base = act_s + (uint32_t)t * kTile + (uint32_t)grp * 16384u;
+                encode_kblock<0>(vv, a.F, pk);
 #pragma unroll
                 for (int m = 0; m < 8; ++m)
                     st_shared_v4(base + swz(r, m), pk[4 * m], pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
+            }
+            if (KB0 > 1) {
+                uint32_t pk[32];
+                encode_kblock<1>(vv, a.F, pk);
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    st_shared_v4(base + 16384u + swz(r, m), pk[4 * m], pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
             }
             fence_proxy_async();
             tc_fence_before();
             __syncwarp();
             if (lane == 0)
-                for (int kb = 0; kb < KB0; ++kb) mbar_arrive(&actr[4 * t + kb]);
+                for (int kb = 0; kb < KB0; ++kb) {
+                    mbar_arrive(&actr[4 * grp + kb]);
+                    mbar_arrive(&actr[4 * (1 - grp) + kb]);
+                }
         };
-        float vcur[2][6], vnext[2][6];
-        int64_t rcur[2], rnext[2];
+        float vme[6];     // (o, w) of row r of tile grp of the pair in hand
+        int64_t rme = -1;
         if ((int64_t)blockIdx.x < npairs) {
-            for (int t = 0; t < 2; ++t) {
-                load_row(blockIdx.x, t, rcur[t], vcur[t]);
-                encode(t, vcur[t]);
-            }
+            load_row(blockIdx.x, grp, rme, vme);
+            encode_tile(vme);
         }
         for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x) {
             const int64_t pn = p + gridDim.x;   // the next pair of this CTA
             for (int s = 0; s < nsteps && ok; ++s) {
                 if (s == nsteps - 1) {
-                    load_row(pn, 0, rnext[0], vnext[0]);
-                    load_row(pn, 1, rnext[1], vnext[1]);
+                    // d dist / d features (columns 0 .. K0-1) of tile grp, the encoding chain rule
+                    // and Eq. 3: feature sin(2^k pi x) has derivative 2^k pi cos(2^k pi x), cos(.)
+                    // has -2^k pi sin(.); sin / cos of every octave by the double-angle recurrence
+                    // from sincospif (as the forward's encoding computes them)
+                    const int t = grp;
+                    float vn[6];
+                    int64_t rn;
+                    load_row(pn, t, rn, vn);
+                    // both groups are done with the previous step (every arrival of its phases is
+                    // in), so this group's arrivals for the other tile belong to the phases that follow
+                    epi_bar();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tfree[1 - t]);   // this group reads none of it
+                    ok = mbar_wait(&accf[t], (accph >> t) & 1u, a.err);
+                    if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                    accph ^= 3u;   // both tiles' accumulators have moved on a phase
+                    tc_fence_after();
+                    float gx[3] = {0.f, 0.f, 0.f};
+                    {
+                        constexpr int KO = kMaxFreqs / 2;
+                        float sk[KO][3], ck[KO][3];
+                        {
+                            float sn[3], cs[3];
+#pragma unroll
+                            for (int j = 0; j < 3; ++j) sincospif(vme[j], &sn[j], &cs[j]);
+#pragma unroll
+                            for (int o = 0; o < KO; ++o)
+#pragma unroll
+                                for (int j = 0; j < 3; ++j) {
+                                    const float sc = ldexpf(3.14159265358979323846f, o);
+                                    sk[o][j] = -sc * sn[j];
+                                    ck[o][j] = sc * cs[j];
+                                    const float s2 = 2.f * sn[j] * cs[j];
+                                    const float c2 = (cs[j] - sn[j]) * (cs[j] + sn[j]);
+                                    sn[j] = s2;
+                                    cs[j] = c2;
+                                }
+                        }
+                        const int nf = a.F / 2;   // octaves of the encoding
+                        // 64 feature columns at a time, as compile-time indices (no local-memory arrays)
+                        auto chain = [&](auto gc) {
+                            constexpr int g = decltype(gc)::value;
+                            const uint32_t tc0 = tbase + lane_off + (uint32_t)(t * W + g * 64);
+#pragma unroll
+                            for (int j = 0; j < 2; ++j) {
+                                if (64 * g + 32 * j >= a.K0) break;
+                                uint32_t raw[32];
+                                TC_LD32(tc0 + 32 * j, raw);
+                                tc_wait_ld();
+#pragma unroll
+                                for (int c = 0; c < 32; ++c) {
+                                    const int pf = 64 * g + 32 * j + c;
+                                    const float gv = __uint_as_float(raw[c]);
+                                    if (pf < 3) {
+                                        gx[pf] += gv;
+                                    } else if (pf >= 8) {
+                                        const int o = (pf - 8) / 12, rr = (pf - 8) % 12, jj = rr % 6;
+                                        if (jj < 3 && o < KO && o < nf)
+                                            gx[jj] = fmaf(gv, rr < 6 ? ck[o][jj] : sk[o][jj], gx[jj]);
+                                    }
+                                }
+                            }
+                        };
+                        chain(std::integral_constant<int, 0>{});
+                        chain(std::integral_constant<int, 1>{});
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tfree[t]);
+                    if (rme >= 0) {
+                        const float3 nn = normal_from_grad(gx[0], gx[1], gx[2], vme[3], vme[4], vme[5]);
+                        a.normals[rme * 3 + 0] = nn.x;
+                        a.normals[rme * 3 + 1] = nn.y;
+                        a.normals[rme * 3 + 2] = nn.z;
+                    }
+                    // row r of tile t of the next pair takes over
+                    if (pn < npairs) {
+                        rme = rn;
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) vme[c] = vn[c];
+                        encode_tile(vme);
+                    }
+                    break;
                 }
                 const int l_bwd = 2 * L - 1 - s;
 #pragma unroll
@@ -1197,130 +1290,47 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     tc_fence_after();
                     const uint32_t tcol = tbase + lane_off + (uint32_t)(t * W) + (uint32_t)(grp * 32);
                     const uint32_t tact = act_s + (uint32_t)t * kTile;
-                    if (s < L || l_bwd >= 1) {
 #pragma unroll
-                        for (int pass = 0; pass < NKBW / 2; ++pass) {
-                            uint32_t raw[2][32];
+                    for (int pass = 0; pass < NKBW / 2; ++pass) {
+                        uint32_t raw[2][32];
 #pragma unroll
-                            for (int i = 0; i < 2; ++i) TC_LD32(tcol + (2 * pass + i) * 64, raw[i]);
-                            tc_wait_ld();
-                            if (pass == NKBW / 2 - 1) {   // accumulator read: the next step may overwrite it
-                                tc_fence_before();
-                                __syncwarp();
-                                if (lane == 0) mbar_arrive(&tfree[t]);
+                        for (int i = 0; i < 2; ++i) TC_LD32(tcol + (2 * pass + i) * 64, raw[i]);
+                        tc_wait_ld();
+                        if (pass == NKBW / 2 - 1) {   // accumulator read: the next step may overwrite it
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&tfree[t]);
+                        }
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            const int kb = 2 * pass + i;
+                            const int c0 = kb * 64 + grp * 32;
+                            uint32_t pk[16];
+                            if (s < L - 1) {
+                                // a = ReLU(acc) rounded to BF16 -> next A operand (the bias is in acc)
+#pragma unroll
+                                for (int q = 0; q < 16; ++q)
+                                    pk[q] = pack_relu(__uint_as_float(raw[i][2 * q]), __uint_as_float(raw[i][2 * q + 1]));
+                                gmt[(s * (W / 32) + (c0 >> 5)) * 128 + r] = pos_bits32(raw[i]);
+                            } else if (s == L - 1) {
+                                // delta of the last hidden layer: W_out[0] on the active units
+#pragma unroll
+                                for (int q = 0; q < 16; ++q)
+                                    pk[q] = pack_bf16((int)raw[i][2 * q] > 0 ? head_s[c0 + 2 * q] : 0.f,
+                                                      (int)raw[i][2 * q + 1] > 0 ? head_s[c0 + 2 * q + 1] : 0.f);
+                            } else {
+                                // delta_{l-1} = (delta_l W_l) * 1[z_{l-1} > 0]
+                                const uint32_t bits = mbits[kb];
+#pragma unroll
+                                for (int q = 0; q < 16; ++q)
+                                    pk[q] = pack_bf16(((bits >> (2 * q)) & 1u) ? __uint_as_float(raw[i][2 * q]) : 0.f,
+                                                      ((bits >> (2 * q + 1)) & 1u) ? __uint_as_float(raw[i][2 * q + 1]) : 0.f);
                             }
 #pragma unroll
-                            for (int i = 0; i < 2; ++i) {
-                                const int kb = 2 * pass + i;
-                                const int c0 = kb * 64 + grp * 32;
-                                uint32_t pk[16];
-                                if (s < L - 1) {
-                                    // a = ReLU(acc) rounded to BF16 -> next A operand (the bias is in acc)
-#pragma unroll
-                                    for (int q = 0; q < 16; ++q)
-                                        pk[q] = pack_relu(__uint_as_float(raw[i][2 * q]), __uint_as_float(raw[i][2 * q + 1]));
-                                    gmt[(s * (W / 32) + (c0 >> 5)) * 128 + r] = pos_bits32(raw[i]);
-                                } else if (s == L - 1) {
-                                    // delta of the last hidden layer: W_out[0] on the active units
-#pragma unroll
-                                    for (int q = 0; q < 16; ++q)
-                                        pk[q] = pack_bf16((int)raw[i][2 * q] > 0 ? head_s[c0 + 2 * q] : 0.f,
-                                                          (int)raw[i][2 * q + 1] > 0 ? head_s[c0 + 2 * q + 1] : 0.f);
-                                } else {
-                                    // delta_{l-1} = (delta_l W_l) * 1[z_{l-1} > 0]
-                                    const uint32_t bits = mbits[kb];
-#pragma unroll
-                                    for (int q = 0; q < 16; ++q)
-                                        pk[q] = pack_bf16(((bits >> (2 * q)) & 1u) ? __uint_as_float(raw[i][2 * q]) : 0.f,
-                                                          ((bits >> (2 * q + 1)) & 1u) ? __uint_as_float(raw[i][2 * q + 1]) : 0.f);
-                                }
-#pragma unroll
-                                for (int m = 0; m < 4; ++m)
-                                    st_shared_v4(tact + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
-                                                 pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
-                                release_kb_warp(actr, 4 * t + kb);
-                            }
-                        }
-                    } else {
-                        // d dist / d features (columns 0 .. K0-1), the encoding chain rule and Eq. 3:
-                        // feature sin(2^k pi x) has derivative 2^k pi cos(2^k pi x), cos(.) has
-                        // -2^k pi sin(.); sin / cos of every octave by the double-angle recurrence
-                        // from sincospif (as the forward's encoding computes them)
-                        // group g takes feature columns [64 g, 64 g + 64); group 1 hands its sums over
-                        float gx[3] = {0.f, 0.f, 0.f};
-                        {
-                            constexpr int KO = kMaxFreqs / 2;
-                            float sk[KO][3], ck[KO][3];
-                            {
-                                float sn[3], cs[3];
-#pragma unroll
-                                for (int j = 0; j < 3; ++j) sincospif(vcur[t][j], &sn[j], &cs[j]);
-#pragma unroll
-                                for (int o = 0; o < KO; ++o)
-#pragma unroll
-                                    for (int j = 0; j < 3; ++j) {
-                                        const float sc = ldexpf(3.14159265358979323846f, o);
-                                        sk[o][j] = -sc * sn[j];
-                                        ck[o][j] = sc * cs[j];
-                                        const float s2 = 2.f * sn[j] * cs[j];
-                                        const float c2 = (cs[j] - sn[j]) * (cs[j] + sn[j]);
-                                        sn[j] = s2;
-                                        cs[j] = c2;
-                                    }
-                            }
-                            const int nf = a.F / 2;   // octaves of the encoding
-                            // the group's columns as compile-time indices (no local-memory arrays)
-                            auto chain = [&](auto gc) {
-                                constexpr int g = decltype(gc)::value;
-                                const uint32_t tc0 = tbase + lane_off + (uint32_t)(t * W + g * 64);
-#pragma unroll
-                                for (int j = 0; j < 2; ++j) {
-                                    if (64 * g + 32 * j >= a.K0) break;
-                                    uint32_t raw[32];
-                                    TC_LD32(tc0 + 32 * j, raw);
-                                    tc_wait_ld();
-#pragma unroll
-                                    for (int c = 0; c < 32; ++c) {
-                                        const int pf = 64 * g + 32 * j + c;
-                                        const float gv = __uint_as_float(raw[c]);
-                                        if (pf < 3) {
-                                            gx[pf] += gv;
-                                        } else if (pf >= 8) {
-                                            const int o = (pf - 8) / 12, rr = (pf - 8) % 12, jj = rr % 6;
-                                            if (jj < 3 && o < KO && o < nf)
-                                                gx[jj] = fmaf(gv, rr < 6 ? ck[o][jj] : sk[o][jj], gx[jj]);
-                                        }
-                                    }
-                                }
-                            };
-                            if (grp == 0) chain(std::integral_constant<int, 0>{});
-                            else chain(std::integral_constant<int, 1>{});
-                        }
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&tfree[t]);
-                        if (grp == 1) {
-                            part[4 * r] = gx[0];
-                            part[4 * r + 1] = gx[1];
-                            part[4 * r + 2] = gx[2];
-                        }
-                        epi_bar();
-                        if (grp == 0 && rcur[t] >= 0) {
-                            gx[0] += part[4 * r];
-                            gx[1] += part[4 * r + 1];
-                            gx[2] += part[4 * r + 2];
-                            const float3 nn = normal_from_grad(gx[0], gx[1], gx[2], vcur[t][3], vcur[t][4], vcur[t][5]);
-                            a.normals[rcur[t] * 3 + 0] = nn.x;
-                            a.normals[rcur[t] * 3 + 1] = nn.y;
-                            a.normals[rcur[t] * 3 + 2] = nn.z;
-                        }
-                        epi_bar();   // part is rewritten by the other tile
-                        // tile t of the next pair takes over
-                        if (pn < npairs) {
-                            rcur[t] = rnext[t];
-#pragma unroll
-                            for (int c = 0; c < 6; ++c) vcur[t][c] = vnext[t][c];
-                            encode(t, vcur[t]);
+                            for (int m = 0; m < 4; ++m)
+                                st_shared_v4(tact + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
+                                             pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
+                            release_kb_warp(actr, 4 * t + kb);
                         }
                     }
                 }
