@@ -1404,7 +1404,7 @@ __device__ __forceinline__ void encode_feats64(const float v[6], int F, float fe
 // tile is multiplied. TMEM holds one W-column accumulator per tile; a tile's next-layer MMA
 // starts only after its epilogue has read the whole accumulator and written the first K-block.
 template <int W>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreadsP, 1)
     mlp_f8_kernel(const __grid_constant__ CUtensorMap map8, const TcArgs a) {
     constexpr int NKB = W / 128;                     // hidden-layer K-blocks of 128 features
     constexpr uint32_t kTileAct = (uint32_t)(NKB > 1 ? NKB : 1) * 16384u;   // one tile's A operand
@@ -1415,19 +1415,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* act = smem;                             // [tile 0, tile 1] x kTileAct
     uint8_t* wst = smem + a.off_wst;
     uint8_t* ones = smem + a.off_mask;                            // 4 KB
-    uint8_t* bslot = smem + a.off_bias;                           // the current layer's bias tile
+    constexpr uint32_t kBias = (uint32_t)W * 32u;
+    uint8_t* bslot = smem + a.off_bias;                           // two bias tiles, layer parity
     float* emul_s = reinterpret_cast<float*>(smem + a.off_grp);   // mu_l
     float* head_s = reinterpret_cast<float*>(smem + a.off_head);
-    float* part = reinterpret_cast<float*>(smem + a.off_part);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
     uint64_t* full = bars;
     uint64_t* empty = bars + NST;
     uint64_t* actr = bars + 2 * NST;   // [tile][K-block], 2 x 2
     uint64_t* accf = actr + 4;         // [tile]
     uint64_t* tfree = accf + 2;        // [tile]: the epilogue has read the tile's accumulator
-    uint64_t* bfull = tfree + 2;       // bias slot loaded / consumed
-    uint64_t* bempty = bfull + 1;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bempty + 1);
+    uint64_t* bfull = tfree + 2;       // [slot]: bias tile loaded
+    uint64_t* bempty = bfull + 2;      // [slot]: read by both tiles' bias MMAs
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bempty + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int64_t n = a.n;
@@ -1438,15 +1438,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         for (int i = 0; i < NST; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
+            mbar_init(&empty[i], 2);   // both tiles' MMA threads release a stage
         }
         for (int i = 0; i < 4; ++i) mbar_init(&actr[i], kEpiWarps);
         mbar_init(&accf[0], 1);
         mbar_init(&accf[1], 1);
         mbar_init(&tfree[0], kEpiWarps);
         mbar_init(&tfree[1], kEpiWarps);
-        mbar_init(bfull, 1);
-        mbar_init(bempty, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bfull[i], 1);
+            mbar_init(&bempty[i], 2);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -1455,11 +1457,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     // the ones tile: K rows 0 and 1 of both 64-row MN atoms are 1.0 (BF16 0x3F80), the rest 0
-    for (int i = tid; i < 1024; i += kThreads)
+    for (int i = tid; i < 1024; i += kThreadsP)
         reinterpret_cast<uint32_t*>(ones)[i] = ((i >> 5) & 15) < 2 ? 0x3F803F80u : 0u;
     fence_proxy_async();
-    for (int i = tid; i < L; i += kThreads) emul_s[i] = a.f8_emul[i];
-    for (int i = tid; i < 2 * W + 2; i += kThreads) head_s[i] = a.head[i];
+    for (int i = tid; i < L; i += kThreadsP) emul_s[i] = a.f8_emul[i];
+    // the output head interleaved, (W_out[0][c], W_out[1][c]) for c < W, then b_out
+    for (int i = tid; i < 2 * W + 2; i += kThreadsP)
+        head_s[i] = i < 2 * W ? a.head[(i & 1) * W + (i >> 1)] : a.head[i];
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
@@ -1467,64 +1471,73 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == kEpiWarps) {
         // ---------------------------------------------------------------- TMA producer
         if (lane == 0) {
-            uint32_t cnt = 0, nb = 0;
+            uint32_t stg = 0, ring_ph = 0, lcnt = 0;
             bool ok = true;
             for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x)
-                for (int s = 0; s < L && ok; ++s, ++nb) {
-                    if (!mbar_wait(bempty, (nb & 1u) ^ 1u, a.err)) { ok = false; break; }
-                    mbar_expect_tx(bfull, (uint32_t)W * 32u);
-                    bulk_load(bslot, a.bias_mn + (size_t)s * W * 32, (uint32_t)W * 32u, bfull);
+                for (int s = 0; s < L && ok; ++s, ++lcnt) {
+                    // the layer's bias tile into slot lcnt & 1, once both tiles' bias MMAs of two
+                    // layers back have read it
+                    const uint32_t b = lcnt & 1u;
+                    if (!mbar_wait(&bempty[b], ((lcnt >> 1) & 1u) ^ 1u, a.err)) { ok = false; break; }
+                    mbar_expect_tx(&bfull[b], kBias);
+                    bulk_load(bslot + b * kBias, a.bias_mn + (size_t)s * kBias, kBias, &bfull[b]);
                     const int nk = s == 0 ? 1 : NKB;
-                    for (int kb = 0; kb < nk; ++kb, ++cnt) {
-                        const int stg = (int)(cnt % (uint32_t)NST);
-                        if (!mbar_wait(&empty[stg], ((cnt / (uint32_t)NST) & 1u) ^ 1u, a.err)) { ok = false; break; }
+                    for (int kb = 0; kb < nk; ++kb) {
+                        if (!mbar_wait(&empty[stg], ring_ph ^ 1u, a.err)) { ok = false; break; }
                         mbar_expect_tx(&full[stg], (uint32_t)W * 128u);
                         tma_load_3d(wst + (size_t)stg * W * 128, &map8, &full[stg], kb * 128, 0, s);
+                        if (++stg == (uint32_t)NST) {
+                            stg = 0;
+                            ring_ph ^= 1u;
+                        }
                     }
                 }
         }
-    } else if (warp == kEpiWarps + 1) {
-        // ---------------------------------------------------------------- MMA issuer
+    } else if (warp == kEpiWarps + 1 || warp == kEpiWarps + 2) {
+        // ---------------------------------------------------------------- MMA issuers
+        // one thread per tile of the pair: both read every weight stage and bias tile (each is
+        // released by two commits), each waits only on its own tile's A K-blocks and accumulator,
+        // so tile 0 may start a layer while tile 1 is still on the previous one
         if (lane == 0) {
-            uint32_t cnt = 0, actph = 0, tfph = 0, nb = 0;
+            const int t = warp - (kEpiWarps + 1);
+            uint32_t stg = 0, ring_ph = 0, lcnt = 0, actph = 0, tfph = 0;
             bool ok = true, first = true;
-            const uint32_t act_s = su32(act), wst_s = su32(wst);
+            const uint32_t act_t = su32(act) + (uint32_t)t * kTileAct, wst_s = su32(wst);
             const uint32_t idesc = idesc_f8(128, W);
             const uint32_t idesc_b = idesc_bf16(128, W) | (3u << 15);   // bias MMA: both operands MN-major
-            const uint64_t ones_d = sdesc_mn16(su32(ones)), bias_d = sdesc_mn16(su32(bslot));
+            const uint64_t ones_d = sdesc_mn16(su32(ones));
+            const uint32_t d = tbase + (uint32_t)(t * W);
             for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x)
-                for (int s = 0; s < L && ok; ++s, ++nb) {
+                for (int s = 0; s < L && ok; ++s, ++lcnt) {
                     const int nk = s == 0 ? 1 : NKB;
-                    if (!mbar_wait(bfull, nb & 1u, a.err)) { ok = false; break; }
-                    for (int t = 0; t < 2 && ok; ++t) {
-                        const uint32_t d = tbase + (uint32_t)(t * W);
-                        for (int kb = 0; kb < nk; ++kb) {
-                            const uint32_t c = cnt + (uint32_t)kb;
-                            const int stg = (int)(c % (uint32_t)NST);
-                            if (t == 0 && !mbar_wait(&full[stg], (c / (uint32_t)NST) & 1u, a.err)) { ok = false; break; }
-                            const int ab = 2 * t + kb;
-                            if (!mbar_wait(&actr[ab], (actph >> ab) & 1u, a.err)) { ok = false; break; }
-                            actph ^= 1u << ab;
-                            // the first MMA overwrites the whole accumulator: wait until the
-                            // epilogue has read the tile's previous layer
-                            if (kb == 0 && !first) {
-                                if (!mbar_wait(&tfree[t], (tfph >> t) & 1u, a.err)) { ok = false; break; }
-                                tfph ^= 1u << t;
-                            }
-                            tc_fence_after();
-                            if (kb == 0) {   // D = b / s_w (BF16 MMA into the same FP32 accumulator)
-                                mma_bf16(d, ones_d, bias_d, idesc_b, 0u);
-                                if (t == 1) mma_commit(bempty);
-                            }
-                            const uint64_t ad = sdesc(act_s + (uint32_t)t * kTileAct + (uint32_t)kb * 16384u);
-                            const uint64_t bd = sdesc(wst_s + (uint32_t)stg * (uint32_t)W * 128u);
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) mma_f8(d, ad + 2 * k, bd + 2 * k, idesc, 1u);
-                            if (t == 1) mma_commit(&empty[stg]);   // both tiles have read the stage
+                    const uint32_t b = lcnt & 1u;
+                    if (!mbar_wait(&bfull[b], (lcnt >> 1) & 1u, a.err)) { ok = false; break; }
+                    for (int kb = 0; kb < nk; ++kb) {
+                        if (!mbar_wait(&full[stg], ring_ph, a.err)) { ok = false; break; }
+                        if (!mbar_wait(&actr[2 * t + kb], (actph >> kb) & 1u, a.err)) { ok = false; break; }
+                        actph ^= 1u << kb;
+                        // the first MMA overwrites the whole accumulator: wait until the
+                        // epilogue has read the tile's previous layer
+                        if (kb == 0 && !first) {
+                            if (!mbar_wait(&tfree[t], tfph, a.err)) { ok = false; break; }
+                            tfph ^= 1u;
                         }
-                        if (ok) mma_commit(&accf[t]);
+                        tc_fence_after();
+                        if (kb == 0) {   // D = b / s_w (BF16 MMA into the same FP32 accumulator)
+                            mma_bf16(d, ones_d, sdesc_mn16(su32(bslot) + b * kBias), idesc_b, 0u);
+                            mma_commit(&bempty[b]);
+                        }
+                        const uint64_t ad = sdesc(act_t + (uint32_t)kb * 16384u);
+                        const uint64_t bd = sdesc(wst_s + stg * (uint32_t)W * 128u);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) mma_f8(d, ad + 2 * k, bd + 2 * k, idesc, 1u);
+                        if (kb == nk - 1) mma_commit(&accf[t]);
+                        mma_commit(&empty[stg]);   // this tile has read the stage
+                        if (++stg == (uint32_t)NST) {
+                            stg = 0;
+                            ring_ph ^= 1u;
+                        }
                     }
-                    cnt += (uint32_t)nk;
                     first = false;
                 }
         }
@@ -1567,6 +1580,95 @@ __global__ void __launch_bounds__(kThreads, 1)
             store64(t, 0, q);
             release_kb_warp(actr, 2 * t);
         };
+        // the last layer: group g serves tile g alone, all W columns of row r: the output head,
+        // the outputs, then the next pair's layer-0 input of the tile (both halves of its one
+        // K-block), so that the tile's next layer 0 does not wait for the other tile's epilogue
+        auto last_layer = [&](int64_t p, int64_t pn) -> bool {
+            const int t = grp;
+            float vn[6];
+            load_row(pn, t, vn);
+            // both groups are done with layer L - 2 (every arrival of its phases is in), so this
+            // group's arrivals for the other tile below belong to the phases that follow
+            epi_bar();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tfree[1 - t]);   // this group reads none of it
+            const bool okw = mbar_wait(&accf[t], (accph >> t) & 1u, a.err);
+            if (!__all_sync(0xffffffffu, okw)) return false;
+            accph ^= 3u;   // both tiles' accumulators have moved on a phase
+            tc_fence_after();
+            const uint32_t tcol = tbase + lane_off + (uint32_t)(t * W);
+            const float2* h2 = reinterpret_cast<const float2*>(head_s);
+            float y0 = 0.f, y1 = 0.f;
+#pragma unroll 1
+            for (int pass = 0; pass < W / 64; ++pass) {
+                uint32_t raw[2][32];
+                TC_LD32(tcol + pass * 64, raw[0]);
+                TC_LD32(tcol + pass * 64 + 32, raw[1]);
+                tc_wait_ld();
+                if (pass == W / 64 - 1) {   // accumulator read: the next pair's layer 0 may overwrite it
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tfree[t]);
+                }
+                // output head (s_w folded into its weights), FP32
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int c = 0; c < 32; c += 2) {
+                        const float4 hh = *reinterpret_cast<const float4*>(&h2[pass * 64 + i * 32 + c]);
+                        const float z0 = fmaxf(__uint_as_float(raw[i][c]), 0.f);
+                        const float z1 = fmaxf(__uint_as_float(raw[i][c + 1]), 0.f);
+                        fma2p(z0, z0, hh.x, hh.y, y0, y1, y0, y1);
+                        fma2p(z1, z1, hh.z, hh.w, y0, y1, y0, y1);
+                    }
+            }
+            {
+                const int64_t i = (2 * p + t) * kTileM + r;
+                const bool valid = i < n;
+                y0 += head_s[2 * W];
+                y1 += head_s[2 * W + 1];
+                const bool hh = y1 > 0.f;
+                if (valid) {
+                    a.dist[i] = y0;
+                    if (a.logit) a.logit[i] = y1;
+                    if (a.hit) a.hit[i] = (uint8_t)hh;
+                }
+                if (a.hit_list) {
+                    const bool take = valid && hh;
+                    const unsigned m = __ballot_sync(0xffffffffu, take);
+                    int base = 0;
+                    if (lane == 0 && m) base = atomicAdd(a.hit_count, __popc(m));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (take) a.hit_list[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
+                }
+            }
+            if (pn < npairs) {
+                const uint32_t base = act_s + (uint32_t)t * kTileAct;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float fe[64];
+                    if (h == 0) encode_feats64<0>(vn, a.F, fe);
+                    else encode_feats64<1>(vn, a.F, fe);
+                    uint32_t q[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        q[i] = pack_e4m3x4(fe[4 * i] * 448.f, fe[4 * i + 1] * 448.f, fe[4 * i + 2] * 448.f,
+                                           fe[4 * i + 3] * 448.f);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        st_shared_v4(base + swz(r, h * 4 + m), q[4 * m], q[4 * m + 1], q[4 * m + 2], q[4 * m + 3]);
+                }
+                fence_proxy_async();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&actr[2 * t]);
+                    mbar_arrive(&actr[2 * (1 - t)]);   // carries no write: the other group writes it
+                }
+            }
+            return true;
+        };
         float vnext[2][6];
         if ((int64_t)blockIdx.x < npairs) {
             load_row(blockIdx.x, 0, vnext[0]);
@@ -1578,8 +1680,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t pn = p + gridDim.x;   // the next pair of this CTA
             for (int s = 0; s < L && ok; ++s) {
                 if (s == L - 1) {
-                    load_row(pn, 0, vnext[0]);
-                    load_row(pn, 1, vnext[1]);
+                    ok = last_layer(p, pn);
+                    break;
                 }
                 for (int t = 0; t < 2; ++t) {
                     ok = mbar_wait(&accf[t], (accph >> t) & 1u, a.err);
@@ -1587,7 +1689,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                     accph ^= 1u << t;
                     tc_fence_after();
                     const uint32_t tcol = tbase + lane_off + (uint32_t)(t * W);
-                    float y0 = 0.f, y1 = 0.f;
                     const float mu = emul_s[s];
 #pragma unroll
                     for (int kb = 0; kb < NKB; ++kb) {
@@ -1602,8 +1703,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             __syncwarp();
                             if (lane == 0) mbar_arrive(&tfree[t]);
                         }
-                        const int c0 = kb * 128 + grp * 64;
-                        if (s < L - 1) {
+                        {
                             uint32_t q[16];
 #pragma unroll
                             for (int i = 0; i < 16; ++i) {
@@ -1615,46 +1715,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                             store64(t, kb, q);
                             release_kb_warp(actr, 2 * t + kb);
-                        } else {
-                            // output head (s_w folded into its weights), FP32
-#pragma unroll
-                            for (int c = 0; c < 64; ++c) {
-                                const float z = fmaxf(__uint_as_float(raw[c >> 5][c & 31]), 0.f);
-                                y0 = fmaf(z, head_s[c0 + c], y0);
-                                y1 = fmaf(z, head_s[W + c0 + c], y1);
-                            }
                         }
-                    }
-                    if (s == L - 1) {
-                        // output head, then tile t of the next pair takes over the accumulator
-                        tc_fence_before();
-                        if (grp == 1) {
-                            part[2 * r] = y0;
-                            part[2 * r + 1] = y1;
-                        }
-                        epi_bar();
-                        if (grp == 0) {
-                            const int64_t i = (2 * p + t) * kTileM + r;
-                            const bool valid = i < n;
-                            y0 += part[2 * r] + head_s[2 * W];
-                            y1 += part[2 * r + 1] + head_s[2 * W + 1];
-                            const bool hh = y1 > 0.f;
-                            if (valid) {
-                                a.dist[i] = y0;
-                                if (a.logit) a.logit[i] = y1;
-                                if (a.hit) a.hit[i] = (uint8_t)hh;
-                            }
-                            if (a.hit_list) {
-                                const bool take = valid && hh;
-                                const unsigned m = __ballot_sync(0xffffffffu, take);
-                                int base = 0;
-                                if (lane == 0 && m) base = atomicAdd(a.hit_count, __popc(m));
-                                base = __shfl_sync(0xffffffffu, base, 0);
-                                if (take) a.hit_list[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
-                            }
-                        }
-                        epi_bar();
-                        if (pn < npairs) encode(t, vnext[t]);
                     }
                 }
             }
@@ -2263,13 +2324,13 @@ Layout smem_layout_f8(int W, int L) {
     const uint32_t emul = ((uint32_t)L * 4u + 15u) & ~15u;
     const uint32_t head = ((uint32_t)(2 * W + 2) * 4u + 15u) & ~15u;
     const uint32_t partb = 128u * 2u * 4u;
-    const uint32_t fixed = act + ones + bias + emul + head + partb + 512u;
+    const uint32_t fixed = act + ones + 2u * bias + emul + head + partb + 512u;
     const uint32_t budget = 227u * 1024u - 1024u;
     s.nst = std::max(0, std::min(8, (int)((budget - fixed) / stage)));
     s.off_wst = act;
     s.off_mask = act + (uint32_t)s.nst * stage;   // ones tile (1 KB aligned: stages are multiples of 1 KB)
-    s.off_bias = s.off_mask + ones;               // bias slot (1 KB aligned)
-    s.off_grp = s.off_bias + bias;                // mu_l
+    s.off_bias = s.off_mask + ones;               // two bias slots (1 KB aligned)
+    s.off_grp = s.off_bias + 2u * bias;           // mu_l
     s.off_head = s.off_grp + emul;
     s.off_part = s.off_head + head;
     s.off_bar = s.off_part + partb;
@@ -2302,7 +2363,7 @@ int launch_f8(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_coun
         DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_f8_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         attr = true;
     }
-    mlp_f8_kernel<W><<<grid, kThreads, s.total, stream>>>(P->map_f8, a);
+    mlp_f8_kernel<W><<<grid, kThreadsP, s.total, stream>>>(P->map_f8, a);
     DDF_LAUNCH_CHECK();
     return DDF_OK;
 }
