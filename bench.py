@@ -62,7 +62,7 @@ def bwd_flops(E, W, L):
 # kernels of one 512 x 512 x 64 spp render of the seeded network (the 4 mlp_pair_kernel<256>
 # forward and 3 mlp_pairn_kernel<256> normals launches; profiles/bf16_query_render512x512.md); to
 # be measured again whenever those kernels change.
-QUERY_DRAM_BYTES_PER_RENDER = 759.8e6
+QUERY_DRAM_BYTES_PER_RENDER = 759.5e6
 
 
 def load_peaks():
