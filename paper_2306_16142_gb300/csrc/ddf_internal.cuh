@@ -140,13 +140,16 @@ bool tc_supported(const NetLayout& lay, int precision);
 int tc_pack(ddf_net_s* net, int precision, cudaStream_t stream);
 void tc_free(ddf_net_s* net);
 int tc_device_status(ddf_net_s* net);
-int tc_fp8_scales(ddf_net_s* net, float* host_out);
+int tc_fp8_scales(ddf_net_s* net, float* host_out);   // [L][W] static activation scales
 // The forward pass of a training chunk of m rows in one persistent launch: a_0 and a_1 .. a_{L-1}
 // through the tensor maps (3-D, BF16, 64 x 128 boxes, 128-byte swizzle: [ld][K0] and L - 1
 // consecutive [ld][W] arrays), the ReLU masks of a_1 .. a_{L-1} ([ld][W / 32] each) and a_L
 // ([ld][W]) from the epilogue. Width <= 256, K0 <= 128.
 int tc_train_forward(const ddf_net_s* net, const float* o, const float* w, int64_t m, const CUtensorMap* map_a0,
-                     const CUtensorMap* map_act, uint32_t* masks, __nv_bfloat16* aL, int64_t ld, cudaStream_t stream);   // [L][W] static activation scales
+                     const CUtensorMap* map_act, uint32_t* masks, __nv_bfloat16* aL, int64_t ld, cudaStream_t stream);
+// The data-gradient chain of a training step, one persistent launch (widths 128, 256).
+int tc_train_dgrad(const ddf_net_s* net, __nv_bfloat16* deltas, int64_t m, int64_t ld, const uint32_t* masks,
+                   float* colpart, cudaStream_t stream);
 int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
                  const int* d_count, float* dist, float* logit, uint8_t* hit, float* normals,
                  cudaStream_t stream);

@@ -87,6 +87,7 @@ struct TcArgs {
     uint32_t* train_masks;    // training forward: ReLU masks of a_1 .. a_{L-1}, [ld][W / 32] each
     __nv_bfloat16* train_aL;  // training forward: a_L, row-major [ld][W]
     int64_t train_ld;         // training forward: rows of one workspace array
+    float* train_colpart;     // training reverse: per-32-row column sums of delta_l, [L][ld / 32][W]
     const float* f8_emul;   // FP8 epilogue [L]: accumulator multiplier mu_l
 };
 
@@ -1331,6 +1332,253 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                                 st_shared_v4(tact + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
                                              pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
                             release_kb_warp(actr, 4 * t + kb);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (*(volatile int*)a.err) {
+        const uint64_t t0 = gtimer();
+        while (gtimer() - t0 < 200000ull) {
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols));
+    }
+}
+
+// The data-gradient chain of a training step on two 128-row tiles per CTA (Sec. 5.1: the
+// network is trained by backpropagation): delta_{L-1} (from the output layer) comes in by TMA,
+// then for l = L-1 .. 1, delta_{l-1} = (delta_l W_l) * 1[a_l > 0] with W_l^T streamed through the
+// weight ring, each delta kept on chip as the next step's A operand. Every delta leaves by TMA
+// stores of its A tile (for the weight gradients), and the epilogue takes its per-32-row column
+// sums (the bias gradients) from the A tile in the same order as the training GEMM's epilogue.
+// The pair structure is that of mlp_pairn_kernel's reverse steps: one MMA-issuing thread per
+// tile, eight epilogue warps in two column groups serving tile 0 and then tile 1.
+template <int W>
+__global__ void __launch_bounds__(kThreadsP, 1)
+    mlp_pairb_kernel(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapD,
+                     const TcArgs a) {
+    constexpr int NKBW = W / 64;
+    constexpr uint32_t kStage = (uint32_t)W * 128u;   // one 64-wide K-block of W_l^T
+    constexpr uint32_t kTile = (uint32_t)NKBW * 16384u;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int L = a.L, NST = a.nst;
+    const int64_t n = a.n, ld = a.train_ld;
+    uint8_t* act = smem;                 // [tile 0, tile 1] x kTile
+    uint8_t* wst = smem + a.off_wst;     // NST x kStage
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + NST;
+    uint64_t* actr = bars + 2 * NST;   // [tile][K-block], 2 x 4
+    uint64_t* accf = actr + 8;         // [tile]
+    uint64_t* tfree = accf + 2;        // [tile]: the epilogue has read the tile's accumulator
+    uint64_t* ain = tfree + 2;         // [tile]: the pair's delta_{L-1} loaded
+    uint64_t* afree = ain + 2;         // [tile]: the last delta stored, the A tile may be refilled
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(afree + 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t npairs = (n + 2 * kTileM - 1) / (2 * kTileM);
+    const int nsteps = L - 1;
+    constexpr uint32_t kTmemCols = 2 * W;
+
+    if (tid == 0) {
+        for (int i = 0; i < NST; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 2);   // both tiles' MMA threads release a stage
+        }
+        for (int i = 0; i < 8; ++i) mbar_init(&actr[i], kEpiWarps);
+        for (int t = 0; t < 2; ++t) {
+            mbar_init(&accf[t], 1);
+            mbar_init(&tfree[t], kEpiWarps);
+            mbar_init(&ain[t], 1);
+            mbar_init(&afree[t], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+
+    if (warp == kEpiWarps) {
+        // ---------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            uint32_t stg = 0, ring_ph = 0, k = 0;
+            bool ok = true;
+            for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x, ++k) {
+                // the pair's delta_{L-1} into each tile, once the tile's previous deltas are stored
+                for (int t = 0; t < 2 && ok; ++t) {
+                    if (!mbar_wait(&afree[t], (k & 1u) ^ 1u, a.err)) { ok = false; break; }
+                    mbar_expect_tx(&ain[t], kTile);
+                    for (int kb = 0; kb < NKBW; ++kb)
+                        tma_load_3d(act + (size_t)t * kTile + (size_t)kb * 16384u, &mapD, &ain[t], kb * 64,
+                                    (int)(p * 2 * kTileM + t * kTileM), L - 1);
+                }
+                for (int j = 0; j < nsteps && ok; ++j)
+                    for (int kb = 0; kb < NKBW; ++kb) {
+                        if (!mbar_wait(&empty[stg], ring_ph ^ 1u, a.err)) { ok = false; break; }
+                        mbar_expect_tx(&full[stg], kStage);
+                        tma_load_3d(wst + (size_t)stg * kStage, &mapB, &full[stg], kb * 64, 0, L - 1 - j);
+                        if (++stg == (uint32_t)NST) {
+                            stg = 0;
+                            ring_ph ^= 1u;
+                        }
+                    }
+            }
+        }
+    } else if (warp == kEpiWarps + 1 || warp == kEpiWarps + 2) {
+        // ---------------------------------------------------------------- MMA issuers
+        if (lane == 0) {
+            const int t = warp - (kEpiWarps + 1);
+            uint32_t stg = 0, ring_ph = 0, actph = 0, tfph = 0, k = 0;
+            bool ok = true, first = true;
+            const uint32_t act_t = su32(act) + (uint32_t)t * kTile, wst_s = su32(wst);
+            const uint32_t idesc = idesc_bf16(128, W);
+            const uint32_t d = tbase + (uint32_t)(t * W);
+            // the epilogue's delta in the A tile (K-block kb) to the deltas of layer l
+            auto take = [&](int kb, int64_t row0, int l) -> bool {
+                if (!mbar_wait(&actr[4 * t + kb], (actph >> kb) & 1u, a.err)) return false;
+                actph ^= 1u << kb;
+                if (row0 < n) {
+                    tma_store_3d(&mapD, act_t + (uint32_t)kb * 16384u, kb * 64, (int)row0, l);
+                    bulk_commit();
+                }
+                return true;
+            };
+            for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x, ++k) {
+                const int64_t row0 = p * 2 * kTileM + t * kTileM;
+                if (!mbar_wait(&ain[t], k & 1u, a.err)) { ok = false; break; }
+                for (int j = 0; j < nsteps && ok; ++j) {
+                    const int l = L - 1 - j;   // delta_l x W_l
+                    for (int kb = 0; kb < NKBW; ++kb) {
+                        if (!mbar_wait(&full[stg], ring_ph, a.err)) { ok = false; break; }
+                        if (j > 0 && !take(kb, row0, l)) { ok = false; break; }
+                        // the step's first MMA overwrites the accumulator: wait until the
+                        // epilogue has read the tile's previous step
+                        if (kb == 0 && !first) {
+                            if (!mbar_wait(&tfree[t], tfph, a.err)) { ok = false; break; }
+                            tfph ^= 1u;
+                        }
+                        tc_fence_after();
+                        const uint64_t ad = sdesc(act_t + (uint32_t)kb * 16384u);
+                        const uint64_t bd = sdesc(wst_s + stg * kStage);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) mma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc, (uint32_t)((kb | kk) != 0));
+                        if (kb == NKBW - 1) {
+                            // the epilogue overwrites the A tile after this commit: the stores
+                            // must have read it
+                            bulk_wait_read();
+                            mma_commit(&accf[t]);
+                        }
+                        mma_commit(&empty[stg]);   // this tile has read the stage
+                        if (++stg == (uint32_t)NST) {
+                            stg = 0;
+                            ring_ph ^= 1u;
+                        }
+                    }
+                    first = false;
+                }
+                // delta_0, the last step's output, then the A tile is free for the next pair
+                for (int kb = 0; kb < NKBW && ok; ++kb)
+                    if (!take(kb, row0, 0)) ok = false;
+                bulk_wait_read();
+                if (ok) mbar_arrive(&afree[t]);
+            }
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        // warp w serves rows 32 (w % 4) .. +31 of the tile in hand; group w / 4 owns columns
+        // [32 group, +32) of every 64-column K-block
+        const int grp = warp >> 2, q = warp & 3;
+        const int r = q * 32 + lane;
+        const uint32_t act_s = su32(act);
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        uint32_t accph = 0;
+        bool ok = true;
+        for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x) {
+            for (int j = 0; j < nsteps && ok; ++j) {
+                const int l = L - 1 - j;   // this step's output is delta_{l-1}, masked by a_l
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const int64_t tile0 = p * 2 * kTileM + t * kTileM;
+                    const int64_t row = tile0 + r;
+                    // the step's ReLU mask words of a_l, fetched while the MMAs run
+                    uint32_t mbits[NKBW];
+#pragma unroll
+                    for (int kb = 0; kb < NKBW; ++kb)
+                        mbits[kb] = row < ld ? a.train_masks[((int64_t)(l - 1) * ld + row) * (W / 32) + 2 * kb + grp] : 0u;
+                    ok = mbar_wait(&accf[t], (accph >> t) & 1u, a.err);
+                    if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                    accph ^= 1u << t;
+                    tc_fence_after();
+                    const uint32_t tcol = tbase + lane_off + (uint32_t)(t * W) + (uint32_t)(grp * 32);
+                    const uint32_t tact = act_s + (uint32_t)t * kTile;
+                    const int64_t rblk = tile0 / 32 + q;   // this warp's 32-row block
+#pragma unroll
+                    for (int pass = 0; pass < NKBW / 2; ++pass) {
+                        uint32_t raw[2][32];
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) TC_LD32(tcol + (2 * pass + i) * 64, raw[i]);
+                        tc_wait_ld();
+                        if (pass == NKBW / 2 - 1) {   // accumulator read: the next step may overwrite it
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&tfree[t]);
+                        }
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            const int kb = 2 * pass + i;
+                            const uint32_t bits = mbits[kb];
+                            uint32_t pk[16];
+#pragma unroll
+                            for (int e = 0; e < 16; ++e)
+                                pk[e] = pack_bf16(((bits >> (2 * e)) & 1u) ? __uint_as_float(raw[i][2 * e]) : 0.f,
+                                                  ((bits >> (2 * e + 1)) & 1u) ? __uint_as_float(raw[i][2 * e + 1]) : 0.f);
+                            const uint32_t kbase = tact + (uint32_t)kb * 16384u;
+#pragma unroll
+                            for (int m = 0; m < 4; ++m)
+                                st_shared_v4(kbase + swz(r, grp * 4 + m), pk[4 * m], pk[4 * m + 1], pk[4 * m + 2],
+                                             pk[4 * m + 3]);
+                            release_kb_warp(actr, 4 * t + kb);
+                            // column sums of the warp's 32 rows (BF16 values, as stored): lane
+                            // sums piece lane % 4 of rows 8 i + lane / 4, then a fixed butterfly
+                            float cs[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) cs[e] = 0.f;
+#pragma unroll
+                            for (int i4 = 0; i4 < 4; ++i4) {
+                                uint32_t v[4];
+                                ld_shared_v4(kbase + swz(q * 32 + 8 * i4 + (lane >> 2), grp * 4 + (lane & 3)), v);
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    cs[2 * e] += __uint_as_float(v[e] << 16);
+                                    cs[2 * e + 1] += __uint_as_float(v[e] & 0xffff0000u);
+                                }
+                            }
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                float x = cs[e];
+                                x += __shfl_xor_sync(0xffffffffu, x, 4);
+                                x += __shfl_xor_sync(0xffffffffu, x, 8);
+                                x += __shfl_xor_sync(0xffffffffu, x, 16);
+                                cs[e] = x;
+                            }
+                            if (lane < 4 && rblk < ld / 32) {
+                                float4* dst = reinterpret_cast<float4*>(
+                                    a.train_colpart + ((int64_t)(l - 1) * (ld / 32) + rblk) * W + kb * 64 + grp * 32 + 8 * lane);
+                                dst[0] = make_float4(cs[0], cs[1], cs[2], cs[3]);
+                                dst[1] = make_float4(cs[4], cs[5], cs[6], cs[7]);
+                            }
                         }
                     }
                 }
@@ -2681,6 +2929,60 @@ int tc_train_forward(const ddf_net_s* net, const float* o, const float* w, int64
     a.train_ld = ld;
     return lay.width == 128 ? launch_pair<128, false, true>(net, a, m, false, stream, 0, map_a0, map_act)
                             : launch_pair<256, false, true>(net, a, m, false, stream, 0, map_a0, map_act);
+}
+
+// The data-gradient chain of a training step (mlp_pairb_kernel): deltas [L][ld][W] BF16 row-major
+// (delta_{L-1} from the output layer in, delta_{L-2} .. delta_0 out), the ReLU masks of a_1 ..
+// a_{L-1} ([L - 1][ld][W / 32]) and the per-32-row column sums of delta_0 .. delta_{L-2} into
+// colpart ([L][ld / 32][W]). Rows m .. ld-1 read as zero.
+int tc_train_dgrad(const ddf_net_s* net, __nv_bfloat16* deltas, int64_t m, int64_t ld, const uint32_t* masks,
+                   float* colpart, cudaStream_t stream) {
+    const NetLayout& lay = net->lay;
+    const TcPack* P = net->tc;
+    const int W = lay.width, L = lay.L;
+    if (!P || (W != 128 && W != 256)) return fail(DDF_ERR_UNSUPPORTED, "fused data-gradient chain: width %d", W);
+    if (L < 2 || m <= 0) return DDF_OK;
+    EncodeTiledFn enc = get_encode();
+    if (!enc) return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    CUtensorMap mapD;
+    cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)m, (cuuint64_t)L};
+    cuuint64_t strides[2] = {(cuuint64_t)W * 2, (cuuint64_t)ld * W * 2};
+    cuuint32_t box[3] = {64, 128, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(&mapD, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, deltas, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled (deltas) failed (%d)", (int)r);
+    TcArgs a{};
+    a.L = L;
+    a.n = m;
+    a.err = P->err;
+    a.train_masks = const_cast<uint32_t*>(masks);
+    a.train_colpart = colpart;
+    a.train_ld = ld;
+    const Layout s = smem_layout_pair(W, W);
+    if (s.nst < 2) return fail(DDF_ERR_UNSUPPORTED, "fused data-gradient chain: shared memory too small");
+    a.nst = s.nst;
+    a.off_wst = s.off_wst;
+    a.off_bar = s.off_bar;
+    const int grid = (int)std::min<int64_t>((m + 2 * kTileM - 1) / (2 * kTileM), num_sms());
+    if (W == 128) {
+        static bool attr = false;
+        if (!attr) {
+            DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_pairb_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+            attr = true;
+        }
+        mlp_pairb_kernel<128><<<grid, kThreadsP, s.total, stream>>>(P->map_bwd, mapD, a);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_pairb_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+            attr = true;
+        }
+        mlp_pairb_kernel<256><<<grid, kThreadsP, s.total, stream>>>(P->map_bwd, mapD, a);
+    }
+    DDF_LAUNCH_CHECK();
+    return DDF_OK;
 }
 
 int tc_fp8_scales(ddf_net_s* net, float* host_out) {

@@ -773,7 +773,7 @@ struct TcWs {
     int ksplit_max = 0;
     __nv_bfloat16* act;      // a_l, l = 0..L, row-major: [mp][K0], then [mp][W] each
     uint32_t* masks;         // ReLU masks of a_1..a_{L-1}: [mp][W / 32] each
-    __nv_bfloat16* dl[2];    // deltas, row-major [mp][W]
+    __nv_bfloat16* dl;       // deltas delta_0 .. delta_{L-1}, row-major [mp][W] each
     float* colpart;          // L x [mp / 32][W]
     float* headpart;         // [mp / 32][2W + 2]
     float* wpart;            // [ksplit][W][max(K0, W)]
@@ -796,7 +796,8 @@ int ensure_tc_ws(ddf_net_s* net, int64_t n, TcWs& ws) {
         out[0] = ((size_t)K0 + (size_t)L * W) * mp * 2;                  // act (a_0 .. a_L)
         out[1] = out[2] = 0;
         out[3] = (size_t)(L - 1) * mp * W / 8 + 4;                       // masks
-        out[4] = out[5] = mp * W * 2;                                    // dl[2]
+        out[4] = (size_t)L * mp * W * 2;                                 // dl (L arrays)
+        out[5] = 0;
         out[6] = 0;
         out[7] = (size_t)L * (mp / 32) * W * 4;                          // colpart
         out[8] = (mp / 32) * (2 * W + 2) * 4;                            // headpart
@@ -838,8 +839,7 @@ int ensure_tc_ws(ddf_net_s* net, int64_t n, TcWs& ws) {
     }
     ws.act = (__nv_bfloat16*)q[0];
     ws.masks = (uint32_t*)q[3];
-    ws.dl[0] = (__nv_bfloat16*)q[4];
-    ws.dl[1] = (__nv_bfloat16*)q[5];
+    ws.dl = (__nv_bfloat16*)q[4];
     ws.colpart = (float*)q[7];
     ws.headpart = (float*)q[8];
     ws.wpart = (float*)q[9];
@@ -919,6 +919,7 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
     auto act = [&](int l) { return ws.act + (l == 0 ? 0 : ((int64_t)K0 + (int64_t)(l - 1) * W) * ld); };
     auto masks = [&](int l) { return ws.masks + (int64_t)(l - 1) * ld * (W / 32); };
     auto colpart = [&](int l) { return ws.colpart + (int64_t)l * (ld / 32) * W; };
+    auto dl = [&](int l) { return ws.dl + (int64_t)l * ld * W; };   // delta_l
     int rc;
 
     if ((rc = tc_forward(net, ws, o, w, m, true, s))) return rc;
@@ -927,7 +928,7 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
         HeadArgs h{};
         h.aL = act(L);
         h.head = P->head;
-        h.delta = ws.dl[0];
+        h.delta = dl(L - 1);
         h.colpart = colpart(L - 1);
         h.headpart = ws.headpart;
         h.m = m;
@@ -951,12 +952,15 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
     }
 
     // ---------------------------------------------------------------- reverse
-    int cur = 0;
+    // the data-gradient chain delta_{L-2} .. delta_0 in one persistent launch where the fused
+    // forward runs (and its bias-gradient column sums); otherwise one GEMM per layer below
+    const bool chain = K0 <= 128 && W <= 256;
+    if (chain && (rc = tc_train_dgrad(net, ws.dl, m, ld, ws.masks, ws.colpart, s))) return rc;
     for (int l = L - 1; l >= 0; --l) {
         const int K = l == 0 ? K0 : W;
         {   // dW_l = delta_l^T a_l, split over the rows; both operands MN-major from row-major arrays
             CUtensorMap mA, mB;
-            if ((rc = tmap(&mA, ws.dl[cur], W, W, m, 1, 64))) return rc;
+            if ((rc = tmap(&mA, dl(l), W, W, m, 1, 64))) return rc;
             if ((rc = tmap(&mB, act(l), K, K, m, 1, 64))) return rc;
             const int nkb = (int)((m + 63) / 64);
             const int want = std::max(1, std::min(ws.ksplit_max, nkb));
@@ -980,9 +984,9 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
                                                                             grad + lay.w_off[l]);
             DDF_LAUNCH_CHECK();
         }
-        if (l > 0) {   // delta_{l-1} = (delta_l W_l) * 1[a_l > 0]
+        if (l > 0 && !chain) {   // delta_{l-1} = (delta_l W_l) * 1[a_l > 0]
             CUtensorMap mA;
-            if ((rc = tmap(&mA, ws.dl[cur], W, W, m, 1, 128))) return rc;
+            if ((rc = tmap(&mA, dl(l), W, W, m, 1, 128))) return rc;
             TArgs a{};
             a.mode = T_DGRAD;
             a.M = (int)m;
@@ -993,14 +997,13 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
             a.ksplit = 1;
             a.b_layer = l;
             a.mask_in = masks(l);
-            a.out = ws.dl[cur ^ 1];
+            a.out = dl(l - 1);
             a.colpart = colpart(l - 1);
             a.err = P->err;
             if ((rc = launch_gemm(mA, P->map_bwd, a, s))) return rc;
-            cur ^= 1;
-        } else if (gin) {   // d/d(internal inputs) = delta_0 W_0, then the encoding's Jacobian
+        } else if (l == 0 && gin) {   // d/d(internal inputs) = delta_0 W_0, then the encoding's Jacobian
             CUtensorMap mA, mB;
-            if ((rc = tmap(&mA, ws.dl[cur], W, W, m, 1, 128))) return rc;
+            if ((rc = tmap(&mA, dl(0), W, W, m, 1, 128))) return rc;
             if ((rc = tmap(&mB, P->w_bwd, W, W, W, L, K0))) return rc;
             TArgs a{};
             a.mode = T_STORE;
