@@ -379,6 +379,163 @@ __global__ void __launch_bounds__(kTThreads, 1)
     }
 }
 
+// All layers' weight gradients of a chunk in one launch: work item = (layer l, split s of the
+// batch rows); each CTA accumulates the whole dW_l = delta_l^T a_l (W x N_l, the 128-row halves in
+// two TMEM accumulators) over its split, so every delta and activation K-block is read once, and
+// writes it as one split-K partial slab in wsum_kernel's fragment order. Both operands are read
+// MN-major from the row-major workspace arrays (64 x 64 TMA boxes), as in the per-layer wgrad.
+struct WArgs {
+    int L, W, K0, nst;
+    int ks, kb_per, nkb;   // splits per layer, K-blocks (64 rows) per split, K-blocks in all
+    uint32_t off_bar;
+    float* part;           // layer l: ks slabs of W x N_l floats at part + l * ks * W * max(K0, W)
+    int* err;
+};
+
+__global__ void __launch_bounds__(kTThreads, 1)
+    wgrad_all_kernel(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUtensorMap mapA0,
+                     const __grid_constant__ CUtensorMap mapAct, const WArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int NST = a.nst, W = a.W, KM = a.K0 > a.W ? a.K0 : a.W;
+    const uint32_t a_bytes = (uint32_t)W * 128u;                 // delta K-block: W features x 64 rows
+    const uint32_t stage_bytes = a_bytes + (uint32_t)KM * 128u;   // + activation K-block
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + NST;
+    uint64_t* accf = bars + 2 * NST;
+    uint64_t* acce = accf + 1;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t items = (int64_t)a.L * a.ks;
+    const int nhalf = W / 128;   // M-halves of dW
+    const uint32_t tcols = nhalf == 2 ? 512u : 256u;
+
+    if (tid == 0) {
+        for (int i = 0; i < NST; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(accf, 1);
+        mbar_init(acce, kTEpi * 32);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                     "r"(tcols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    // launched as a programmatic dependent of the data-gradient chain: nothing it wrote is read
+    // before this wait
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
+    auto item_range = [&](int64_t t, int& l, int& s, int& n, int& kb0, int& kb1) {
+        l = (int)(t / a.ks);
+        s = (int)(t % a.ks);
+        n = l == 0 ? a.K0 : W;
+        kb0 = s * a.kb_per;
+        kb1 = min(a.nkb, kb0 + a.kb_per);
+    };
+
+    if (warp == kTEpi) {
+        // ---------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            uint32_t stg = 0, ring_ph = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < items && ok; t += gridDim.x) {
+                int l, s, n, kb0, kb1;
+                item_range(t, l, s, n, kb0, kb1);
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    if (!mbar_wait(&empty[stg], ring_ph ^ 1u, a.err)) { ok = false; break; }
+                    uint8_t* sa = smem + (size_t)stg * stage_bytes;
+                    mbar_expect_tx(&full[stg], a_bytes + (uint32_t)n * 128u);
+                    for (int j = 0; j < W / 64; ++j) tma_load_3d(sa + j * 8192, &mapD, &full[stg], 64 * j, kb * 64, l);
+                    for (int j = 0; j < n / 64; ++j)
+                        tma_load_3d(sa + a_bytes + j * 8192, l == 0 ? &mapA0 : &mapAct, &full[stg], 64 * j, kb * 64,
+                                    l == 0 ? 0 : l - 1);
+                    if (++stg == (uint32_t)NST) {
+                        stg = 0;
+                        ring_ph ^= 1u;
+                    }
+                }
+            }
+        }
+    } else if (warp == kTEpi + 1) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t stg = 0, ring_ph = 0, tl = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < items && ok; t += gridDim.x, ++tl) {
+                int l, s, n, kb0, kb1;
+                item_range(t, l, s, n, kb0, kb1);
+                const uint32_t idesc = idesc_bf16(128, n) | (3u << 15);   // both operands MN-major
+                if (!mbar_wait(acce, (tl & 1u) ^ 1u, a.err)) break;       // the previous item is read
+                tc_fence_after();
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    if (!mbar_wait(&full[stg], ring_ph, a.err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t sa = su32(smem + (size_t)stg * stage_bytes);
+                    for (int h = 0; h < nhalf; ++h)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            mma_bf16(tbase + (uint32_t)h * 256u, sdesc_mn(sa + (uint32_t)h * 16384u + 2048u * k),
+                                     sdesc_mn(sa + a_bytes + 2048u * k), idesc, (kb > kb0 || k > 0));
+                    mma_commit(&empty[stg]);
+                    if (++stg == (uint32_t)NST) {
+                        stg = 0;
+                        ring_ph ^= 1u;
+                    }
+                }
+                if (ok) mma_commit(accf);
+            }
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        // warp w: M-half w / 4 (rows 128 h + 32 (w % 4) + lane of dW_l), every 32-column chunk
+        const int h = warp >> 2, q = warp & 3;
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        uint32_t tl = 0;
+        for (int64_t t = blockIdx.x; t < items; t += gridDim.x, ++tl) {
+            int l, s, n, kb0, kb1;
+            item_range(t, l, s, n, kb0, kb1);
+            if (!mbar_wait(accf, tl & 1u, a.err)) break;
+            tc_fence_after();
+            if (h < nhalf) {
+                float* base = a.part + (int64_t)l * a.ks * W * KM + (int64_t)s * W * n +
+                              ((int64_t)(h * 4 + q) * (n / 32)) * 1024;
+                for (int c = 0; c < n / 32; ++c) {
+                    uint32_t raw[32];
+                    TC_LD32(tbase + lane_off + (uint32_t)h * 256u + (uint32_t)c * 32u, raw);
+                    tc_wait_ld();
+                    float4* dst = reinterpret_cast<float4*>(base + (int64_t)c * 1024) + lane;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        dst[32 * i] = make_float4(__uint_as_float(raw[4 * i]), __uint_as_float(raw[4 * i + 1]),
+                                                  __uint_as_float(raw[4 * i + 2]), __uint_as_float(raw[4 * i + 3]));
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(acce);
+        }
+    }
+    __syncthreads();
+    if (*(volatile int*)a.err) {
+        const uint64_t t0 = gtimer();
+        while (gtimer() - t0 < 200000ull) {
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(tcols));
+    }
+}
+
 // Rows of the batch encoded in the tensor-core feature order (six raw coordinates, two zero
 // columns, then per octave the sines and cosines), BF16, row-major [mp][K0]; rows m..mp-1 are
 // zero.
@@ -768,6 +925,72 @@ int launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, TArgs a, cudaStrea
     return DDF_OK;
 }
 
+// BF16 3-D tensor map of `depth` workspace arrays of `slice_rows` rows (row stride `inner`
+// elements) of which the first `rows` are read (the rest as zero); box 64 x box_rows x 1,
+// 128-byte swizzle.
+int tmap_rows(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, uint64_t slice_rows, uint64_t depth,
+              uint32_t box_rows) {
+    EncodeTiledFn enc = get_encode();
+    if (!enc) return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[3] = {inner, rows, depth};
+    cuuint64_t strides[2] = {inner * 2, inner * slice_rows * 2};
+    cuuint32_t box[3] = {64, box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return DDF_OK;
+}
+
+// wgrad_all_kernel over rows [0, m) of the workspace arrays (row stride ld): deltas [L][ld][W],
+// a_0 [ld][K0], a_1 .. a_{L-1} [L - 1][ld][W]; the partial slabs into part. Returns the splits
+// per layer.
+int launch_wgrad_all(const ddf_net_s* net, const __nv_bfloat16* deltas, const __nv_bfloat16* a0,
+                     const __nv_bfloat16* act1, int64_t m, int64_t ld, float* part, int* ks_out, cudaStream_t s) {
+    const NetLayout& lay = net->lay;
+    const int W = lay.width, L = lay.L, K0 = net->tc->K0, KM = std::max(K0, W);
+    CUtensorMap mD, mA0, mAct;
+    int rc;
+    if ((rc = tmap_rows(&mD, deltas, W, m, ld, L, 64))) return rc;
+    if ((rc = tmap_rows(&mA0, a0, K0, m, ld, 1, 64))) return rc;
+    if ((rc = tmap_rows(&mAct, act1, W, m, ld, std::max(1, L - 1), 64))) return rc;
+    WArgs a{};
+    a.L = L;
+    a.W = W;
+    a.K0 = K0;
+    a.nkb = (int)((m + 63) / 64);
+    const int want = std::max(1, std::min(a.nkb, num_sms() / L));
+    a.kb_per = (a.nkb + want - 1) / want;
+    a.ks = (a.nkb + a.kb_per - 1) / a.kb_per;
+    a.part = part;
+    a.err = net->tc->err;
+    const uint32_t stage = (uint32_t)(W + KM) * 128u;
+    a.nst = (int)std::min<uint32_t>(8u, (kSmemMax - 2048u) / stage);
+    if (a.nst < 2) return fail(DDF_ERR_UNSUPPORTED, "weight-gradient kernel shared memory");
+    a.off_bar = (uint32_t)a.nst * stage;
+    const uint32_t total = a.off_bar + 256u + 1024u;
+    static bool attr = false;
+    if (!attr) {
+        DDF_CUDA_TRY(cudaFuncSetAttribute(wgrad_all_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+        attr = true;
+    }
+    const int64_t items = (int64_t)L * a.ks;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::min<int64_t>(items, num_sms()));
+    cfg.blockDim = dim3(kTThreads);
+    cfg.dynamicSmemBytes = total;
+    cfg.stream = s;
+    cudaLaunchAttribute attrs[1];
+    attrs[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attrs[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attrs;
+    cfg.numAttrs = 1;
+    DDF_CUDA_TRY(cudaLaunchKernelEx(&cfg, wgrad_all_kernel, mD, mA0, mAct, a));
+    *ks_out = a.ks;
+    return DDF_OK;
+}
+
 struct TcWs {
     int64_t m = 0, mp = 0;   // rows per chunk, padded to 128
     int ksplit_max = 0;
@@ -801,7 +1024,7 @@ int ensure_tc_ws(ddf_net_s* net, int64_t n, TcWs& ws) {
         out[6] = 0;
         out[7] = (size_t)L * (mp / 32) * W * 4;                          // colpart
         out[8] = (mp / 32) * (2 * W + 2) * 4;                            // headpart
-        out[9] = (size_t)ws.ksplit_max * W * KM * 4;                     // wpart
+        out[9] = (size_t)std::max(ws.ksplit_max, num_sms()) * W * KM * 4;  // wpart
         out[10] = mp * K0 * 4;                                           // gx
         out[11] = (size_t)lay.n_params * 4;                              // grad
         out[12] = out[13] = (size_t)n * 4;                               // row_l1, row_bce
@@ -955,10 +1178,24 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
     // the data-gradient chain delta_{L-2} .. delta_0 in one persistent launch where the fused
     // forward runs (and its bias-gradient column sums); otherwise one GEMM per layer below
     const bool chain = K0 <= 128 && W <= 256;
-    if (chain && (rc = tc_train_dgrad(net, ws.dl, m, ld, ws.masks, ws.colpart, s))) return rc;
+    if (chain) {
+        // then every layer's weight gradient in one launch and the split sums per layer
+        if ((rc = tc_train_dgrad(net, ws.dl, m, ld, ws.masks, ws.colpart, s))) return rc;
+        int ks = 0;
+        if ((rc = launch_wgrad_all(net, ws.dl, act(0), act(1), m, ld, ws.wpart, &ks, s))) return rc;
+        const int KM = std::max(K0, W);
+        for (int l = 0; l < L; ++l) {
+            const int K = l == 0 ? K0 : W;
+            const int64_t tot4 = (int64_t)W * K / 4;
+            wsum_kernel<<<(unsigned)((tot4 + 31) / 32), dim3(32, 8), 0, s>>>(
+                (const float4*)(ws.wpart + (int64_t)l * ks * W * KM), ks, W, K, l == 0 ? lay.E : W, l == 0,
+                grad + lay.w_off[l]);
+            DDF_LAUNCH_CHECK();
+        }
+    }
     for (int l = L - 1; l >= 0; --l) {
         const int K = l == 0 ? K0 : W;
-        {   // dW_l = delta_l^T a_l, split over the rows; both operands MN-major from row-major arrays
+        if (!chain) {   // dW_l = delta_l^T a_l, split over the rows; both operands MN-major from row-major arrays
             CUtensorMap mA, mB;
             if ((rc = tmap(&mA, dl(l), W, W, m, 1, 64))) return rc;
             if ((rc = tmap(&mB, act(l), K, K, m, 1, 64))) return rc;
