@@ -952,7 +952,8 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                             const int kb = 2 * pass + i;
                             const int c0 = kb * 64 + grp * 32;
                             if (s < L - 1) {
-                                // a = ReLU(acc) rounded to BF16 -> next A operand
+                                // a = ReLU(acc) rounded to BF16 -> next A operand; the pass's two
+                                // K-blocks are released together, behind one proxy fence
                                 uint32_t pk[16];
 #pragma unroll
                                 for (int q = 0; q < 16; ++q)
@@ -961,7 +962,15 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                                 for (int m = 0; m < 4; ++m)
                                     st_shared_v4(tact + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
                                                  pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
-                                release_kb_warp(actr, 4 * t + kb);
+                                if (i == 1) {
+                                    fence_proxy_async();
+                                    tc_fence_before();
+                                    __syncwarp();
+                                    if (lane == 0) {
+                                        mbar_arrive(&actr[4 * t + kb - 1]);
+                                        mbar_arrive(&actr[4 * t + kb]);
+                                    }
+                                }
                                 if (TRAIN && t * kTileM + r < pi.rows)   // ReLU mask of a_{s+1}
                                     a.train_masks[((int64_t)s * a.train_ld + pi.row0 + t * kTileM + r) * (W / 32) +
                                                   2 * kb + grp] = pos_bits32(raw[i]);
