@@ -78,6 +78,7 @@ struct ddf_net_s {
     float sphere_r = 0.f;
     float* master = nullptr;     // FP32 masters, blob layout (device)
     float* master_t = nullptr;   // per-layer transposed FP32 copies W^T [in][out] (device)
+    bool master_t_stale = false;  // master_t predates the last optimiser step (rebuilt on FP32 use)
     ddf::TcPack* tc = nullptr;   // BF16 / FP8 working copy
     // Adam state
     float* adam_m = nullptr;

@@ -344,12 +344,17 @@ int build_transposed(ddf_net_s* net, cudaStream_t stream) {
     dim3 grid(64, net->lay.L + 1);
     transpose_layers<<<grid, 256, 0, stream>>>(net->master, net->master_t, net->lay);
     DDF_LAUNCH_CHECK();
+    net->master_t_stale = false;
     return DDF_OK;
 }
 
 int mlp_fp32_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
                    const int* d_count, float* dist, float* logit, uint8_t* hit, float* normals,
                    cudaStream_t stream) {
+    if (net->master_t_stale) {   // trained since the transposed copy was made (on this stream)
+        const int rc = build_transposed(const_cast<ddf_net_s*>(net), stream);
+        if (rc) return rc;
+    }
     MlpArgs a;
     a.lay = net->lay;
     a.W = net->master;

@@ -1340,7 +1340,15 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                             for (int m = 0; m < 4; ++m)
                                 st_shared_v4(tact + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
                                              pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
-                            release_kb_warp(actr, 4 * t + kb);
+                            if (i == 1) {   // the pass's two K-blocks behind one proxy fence
+                                fence_proxy_async();
+                                tc_fence_before();
+                                __syncwarp();
+                                if (lane == 0) {
+                                    mbar_arrive(&actr[4 * t + kb - 1]);
+                                    mbar_arrive(&actr[4 * t + kb]);
+                                }
+                            }
                         }
                     }
                 }
@@ -1389,7 +1397,8 @@ __global__ void __launch_bounds__(kThreadsP, 1)
     uint64_t* tfree = accf + 2;        // [tile]: the epilogue has read the tile's accumulator
     uint64_t* ain = tfree + 2;         // [tile]: the pair's delta_{L-1} loaded
     uint64_t* afree = ain + 2;         // [tile]: the last delta stored, the A tile may be refilled
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(afree + 2);
+    uint64_t* sdone = afree + 2;       // [tile][K-block]: the step's store of the K-block has read it
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sdone + 8);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t npairs = (n + 2 * kTileM - 1) / (2 * kTileM);
@@ -1401,7 +1410,10 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 2);   // both tiles' MMA threads release a stage
         }
-        for (int i = 0; i < 8; ++i) mbar_init(&actr[i], kEpiWarps);
+        for (int i = 0; i < 8; ++i) {
+            mbar_init(&actr[i], kEpiWarps);
+            mbar_init(&sdone[i], 1);
+        }
         for (int t = 0; t < 2; ++t) {
             mbar_init(&accf[t], 1);
             mbar_init(&tfree[t], kEpiWarps);
@@ -1483,12 +1495,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                         const uint64_t bd = sdesc(wst_s + stg * kStage);
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) mma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc, (uint32_t)((kb | kk) != 0));
-                        if (kb == NKBW - 1) {
-                            // the epilogue overwrites the A tile after this commit: the stores
-                            // must have read it
-                            bulk_wait_read();
-                            mma_commit(&accf[t]);
-                        }
+                        if (kb == NKBW - 1) mma_commit(&accf[t]);
                         mma_commit(&empty[stg]);   // this tile has read the stage
                         if (++stg == (uint32_t)NST) {
                             stg = 0;
@@ -1496,6 +1503,22 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                         }
                     }
                     first = false;
+                    if (!ok) break;
+                    // the epilogue overwrites K-block kb of the A tile once its store has read it
+                    if (j > 0 && row0 < n) {
+                        // the step committed NKBW store groups, K-block order
+#pragma unroll
+                        for (int kb = 0; kb < NKBW; ++kb) {
+                            const int later = NKBW - 1 - kb;   // groups committed after kb's
+                            if (later >= 3) bulk_wait_read_le<3>();
+                            else if (later == 2) bulk_wait_read_le<2>();
+                            else if (later == 1) bulk_wait_read_le<1>();
+                            else bulk_wait_read_le<0>();
+                            mbar_arrive(&sdone[4 * t + kb]);
+                        }
+                    } else {
+                        for (int kb = 0; kb < NKBW; ++kb) mbar_arrive(&sdone[4 * t + kb]);
+                    }
                 }
                 // delta_0, the last step's output, then the A tile is free for the next pair
                 for (int kb = 0; kb < NKBW && ok; ++kb)
@@ -1512,7 +1535,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
         const int r = q * 32 + lane;
         const uint32_t act_s = su32(act);
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-        uint32_t accph = 0;
+        uint32_t accph = 0, sdph = 0;
         bool ok = true;
         for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x) {
             for (int j = 0; j < nsteps && ok; ++j) {
@@ -1548,17 +1571,32 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                         for (int i = 0; i < 2; ++i) {
                             const int kb = 2 * pass + i;
                             const uint32_t bits = mbits[kb];
+                            // the K-block's previous delta has left by TMA
+                            const int sb = 4 * t + kb;
+                            ok = mbar_wait(&sdone[sb], (sdph >> sb) & 1u, a.err);
+                            sdph ^= 1u << sb;
                             uint32_t pk[16];
 #pragma unroll
                             for (int e = 0; e < 16; ++e)
                                 pk[e] = pack_bf16(((bits >> (2 * e)) & 1u) ? __uint_as_float(raw[i][2 * e]) : 0.f,
                                                   ((bits >> (2 * e + 1)) & 1u) ? __uint_as_float(raw[i][2 * e + 1]) : 0.f);
-                            const uint32_t kbase = tact + (uint32_t)kb * 16384u;
 #pragma unroll
                             for (int m = 0; m < 4; ++m)
-                                st_shared_v4(kbase + swz(r, grp * 4 + m), pk[4 * m], pk[4 * m + 1], pk[4 * m + 2],
-                                             pk[4 * m + 3]);
-                            release_kb_warp(actr, 4 * t + kb);
+                                st_shared_v4(tact + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
+                                             pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
+                        }
+                        // the pass's two K-blocks behind one proxy fence
+                        fence_proxy_async();
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) {
+                            mbar_arrive(&actr[4 * t + 2 * pass]);
+                            mbar_arrive(&actr[4 * t + 2 * pass + 1]);
+                        }
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            const int kb = 2 * pass + i;
+                            const uint32_t kbase = tact + (uint32_t)kb * 16384u;
                             // column sums of the warp's 32 rows (BF16 values, as stored): lane
                             // sums piece lane % 4 of rows 8 i + lane / 4, then a fixed butterfly
                             float cs[8];
@@ -1569,19 +1607,16 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                                 uint32_t v[4];
                                 ld_shared_v4(kbase + swz(q * 32 + 8 * i4 + (lane >> 2), grp * 4 + (lane & 3)), v);
 #pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    cs[2 * e] += __uint_as_float(v[e] << 16);
-                                    cs[2 * e + 1] += __uint_as_float(v[e] & 0xffff0000u);
-                                }
+                                for (int e = 0; e < 4; ++e)
+                                    add2(cs[2 * e], cs[2 * e + 1], __uint_as_float(v[e] << 16),
+                                         __uint_as_float(v[e] & 0xffff0000u), cs[2 * e], cs[2 * e + 1]);
                             }
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                float x = cs[e];
-                                x += __shfl_xor_sync(0xffffffffu, x, 4);
-                                x += __shfl_xor_sync(0xffffffffu, x, 8);
-                                x += __shfl_xor_sync(0xffffffffu, x, 16);
-                                cs[e] = x;
-                            }
+                            for (int sh = 4; sh <= 16; sh <<= 1)
+#pragma unroll
+                                for (int e = 0; e < 8; e += 2)
+                                    add2(cs[e], cs[e + 1], __shfl_xor_sync(0xffffffffu, cs[e], sh),
+                                         __shfl_xor_sync(0xffffffffu, cs[e + 1], sh), cs[e], cs[e + 1]);
                             if (lane < 4 && rblk < ld / 32) {
                                 float4* dst = reinterpret_cast<float4*>(
                                     a.train_colpart + ((int64_t)(l - 1) * (ld / 32) + rblk) * W + kb * 64 + grp * 32 + 8 * lane);

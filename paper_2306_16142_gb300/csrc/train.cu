@@ -511,10 +511,13 @@ int adam_and_repack(ddf_net_s* net, float* grad, const ddf_adam* opt, cudaStream
         DDF_LAUNCH_CHECK();
         if ((rc = head_derive(net, net->master, s))) return rc;
     }
-    rc = build_transposed(net, s);
-    if (rc) return rc;
-    if (net->tc) return tc_pack(net, net->precision, s);
-    return DDF_OK;
+    // with a tensor-core working copy the FP32 transposed copy is only read by FP32 queries:
+    // rebuilt by the next one, not after every step
+    if (net->tc) {
+        net->master_t_stale = true;
+        return tc_pack(net, net->precision, s);
+    }
+    return build_transposed(net, s);
 }
 
 int train_step(ddf_net_s* net, const float* o, const float* w, const float* dist_gt,

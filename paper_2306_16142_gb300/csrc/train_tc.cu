@@ -585,8 +585,8 @@ __global__ void tenc_kernel(const float* __restrict__ o, const float* __restrict
 // wgrad epilogue's fragment order (per split: M-tile, lane quadrant, 32-column chunk, float4
 // index, lane); layer 0's internal columns are scattered back to the encoding order and its pad
 // columns dropped.
-__global__ void wsum_kernel(const float4* __restrict__ part, int ksplit, int M, int N, int in_dim, int layer0,
-                            float* __restrict__ gW) {
+__device__ __forceinline__ void wsum_block(const float4* __restrict__ part, int ksplit, int M, int N, int in_dim,
+                                           int layer0, float* __restrict__ gW) {
     // block (32, 8): x = one float4 of the slab, y = a lane over the splits (y, y + 8, ...)
     const int64_t t = blockIdx.x * 32 + threadIdx.x;
     const int64_t slab4 = (int64_t)M * N / 4;
@@ -621,6 +621,52 @@ __global__ void wsum_kernel(const float4* __restrict__ part, int ksplit, int M, 
         const int p = c * 32 + 4 * i + e;
         const int src = layer0 ? in_feature(p) : p;
         if (src >= 0 && src < in_dim) gW[(int64_t)o * in_dim + src] += vals[e];
+    }
+}
+
+__global__ void wsum_kernel(const float4* __restrict__ part, int ksplit, int M, int N, int in_dim, int layer0,
+                            float* __restrict__ gW) {
+    wsum_block(part, ksplit, M, N, in_dim, layer0, gW);
+}
+
+// The split sums of every layer's weight gradient at once (blockIdx.y = layer; layer l's ks slabs
+// of W x N_l floats at part + l * ks * W * KM, in the fragment order of the weight-gradient
+// epilogue). Block (32, 8) takes one 32 x 32 piece of dW_l: thread (x, y) sums fragment float4
+// (lane x, index y) over the splits in split order, the piece is transposed through shared
+// memory, and each warp adds whole 32-column row segments to the gradient.
+__global__ void wsum_all_kernel(const float4* __restrict__ part, int ks, int KM, int K0, NetLayout lay,
+                                float* __restrict__ grad) {
+    const int l = blockIdx.y, W = lay.width;
+    const int N = l == 0 ? K0 : W, nch = N / 32;
+    const int u = blockIdx.x;   // (M-tile, lane quadrant, 32-column chunk) of the fragment order
+    if (u >= (W / 32) * nch) return;
+    const int x = threadIdx.x, y = threadIdx.y;
+    const float4* P = part + (int64_t)l * ks * W * KM / 4;
+    const int64_t slab4 = (int64_t)W * N / 4, t = (int64_t)u * 256 + y * 32 + x;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < ks; ++k) {
+        const float4 v = P[k * slab4 + t];
+        acc.x += v.x;
+        acc.y += v.y;
+        acc.z += v.z;
+        acc.w += v.w;
+    }
+    __shared__ float piece[32][33];   // [row (lane)][column]
+    piece[x][4 * y] = acc.x;
+    piece[x][4 * y + 1] = acc.y;
+    piece[x][4 * y + 2] = acc.z;
+    piece[x][4 * y + 3] = acc.w;
+    __syncthreads();
+    const int c = u % nch, q = (u / nch) & 3, tm = u / (nch * 4);
+    const int in_dim = l == 0 ? lay.E : W;
+    float* gW = grad + lay.w_off[l];
+    const int p = c * 32 + x;
+    const int src = l == 0 ? in_feature(p) : p;
+    if (src < 0 || src >= in_dim) return;
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+        const int row = y + 8 * rr;
+        gW[(int64_t)(tm * 128 + q * 32 + row) * in_dim + src] += piece[row][x];
     }
 }
 
@@ -1184,14 +1230,9 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
         int ks = 0;
         if ((rc = launch_wgrad_all(net, ws.dl, act(0), act(1), m, ld, ws.wpart, &ks, s))) return rc;
         const int KM = std::max(K0, W);
-        for (int l = 0; l < L; ++l) {
-            const int K = l == 0 ? K0 : W;
-            const int64_t tot4 = (int64_t)W * K / 4;
-            wsum_kernel<<<(unsigned)((tot4 + 31) / 32), dim3(32, 8), 0, s>>>(
-                (const float4*)(ws.wpart + (int64_t)l * ks * W * KM), ks, W, K, l == 0 ? lay.E : W, l == 0,
-                grad + lay.w_off[l]);
-            DDF_LAUNCH_CHECK();
-        }
+        wsum_all_kernel<<<dim3((unsigned)((W / 32) * (KM / 32)), (unsigned)L), dim3(32, 8), 0, s>>>(
+            (const float4*)ws.wpart, ks, KM, K0, lay, grad);
+        DDF_LAUNCH_CHECK();
     }
     for (int l = L - 1; l >= 0; --l) {
         const int K = l == 0 ? K0 : W;
