@@ -18,22 +18,47 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Unsigned 32-bit division by a divisor fixed for a launch, as a multiply-high and two shifts
+// (Granlund and Montgomery, "Division by invariant integers using multiplication", PLDI 1994,
+// the round-up method): with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0) for t = (m n) >> 32, every 32-bit n.
+struct DivU32 {
+    uint32_t m;
+    int sh1, sh2;
+};
+DivU32 make_div(uint32_t d) {
+    int l = 0;
+    while (l < 32 && (1ull << l) < d) ++l;
+    DivU32 r;
+    r.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    r.sh1 = l < 1 ? l : 1;
+    r.sh2 = l - 1 > 0 ? l - 1 : 0;
+    return r;
+}
+__device__ __forceinline__ uint32_t udiv(uint32_t n, DivU32 D) {
+    const uint32_t t = __umulhi(n, D.m);
+    return (t + ((n - t) >> D.sh1)) >> D.sh2;
+}
+
 struct CamDev {
     float eye[3], f[3], r[3], u[3];
     float th, aspect;
     int W, H;
+    DivU32 dW;             // division by W
+    float inv2W, inv2H;    // 2 / W, 2 / H
     uint64_t seed;
     float albedo, env;
 };
 
 // Unit direction of path pid's primary ray: pixel pid / spp, jitter from the bounce-0 draw.
-__device__ __forceinline__ void primary_dir(const CamDev& cam, int64_t pid, int spp, float* dx, float* dy,
-                                            float* dz) {
-    // pixel (x, y) of the path; 32-bit divisions whenever the id fits (every render below 2^32 paths)
+__device__ __forceinline__ void primary_dir(const CamDev& cam, int64_t pid, int spp, DivU32 dspp, float* dx,
+                                            float* dy, float* dz) {
+    // pixel (x, y) of the path; 32-bit divisions by the launch's constants whenever the id fits
+    // (every render below 2^32 paths)
     int64_t xi, yi;
     if (pid >= 0 && pid <= 0xFFFFFFFFll) {
-        const uint32_t pix = (uint32_t)pid / (uint32_t)spp;
-        yi = pix / (uint32_t)cam.W;
+        const uint32_t pix = udiv((uint32_t)pid, dspp);
+        yi = udiv(pix, cam.dW);
         xi = pix - (uint32_t)yi * (uint32_t)cam.W;
     } else {
         const int64_t pix = pid / spp;
@@ -42,8 +67,8 @@ __device__ __forceinline__ void primary_dir(const CamDev& cam, int64_t pid, int 
     }
     const float x = (float)xi, y = (float)yi;
     const uint4 rnd = path_draw(cam.seed, (uint64_t)pid, 0u);
-    const float px = (2.f * (x + u24(rnd.x)) / cam.W - 1.f) * cam.th * cam.aspect;
-    const float py = (1.f - 2.f * (y + u24(rnd.y)) / cam.H) * cam.th;
+    const float px = ((x + u24(rnd.x)) * cam.inv2W - 1.f) * cam.th * cam.aspect;
+    const float py = (1.f - (y + u24(rnd.y)) * cam.inv2H) * cam.th;
     float vx = cam.f[0] + px * cam.r[0] + py * cam.u[0];
     float vy = cam.f[1] + px * cam.r[1] + py * cam.u[1];
     float vz = cam.f[2] + px * cam.r[2] + py * cam.u[2];
@@ -83,7 +108,7 @@ constexpr int kRaysPerThread = 4;   // camera rays generated per thread and bloc
 // thread has four independent Philox draws in flight while every round's stores stay coalesced:
 // the survivors of round k of warp v go to slots base + prefix(k, v) + (rank in the warp's ballot),
 // one atomicAdd per 1,024 paths.
-__global__ void __launch_bounds__(kThreads) raygen_kernel(CamDev cam, int spp, int64_t pid0,
+__global__ void __launch_bounds__(kThreads) raygen_kernel(CamDev cam, int spp, DivU32 dspp, int64_t pid0,
                                                           int64_t npaths, float* __restrict__ o,
                                                           float* __restrict__ w,
                                                           uint32_t* __restrict__ lid,
@@ -103,7 +128,7 @@ __global__ void __launch_bounds__(kThreads) raygen_kernel(CamDev cam, int spp, i
             bool alive = false;
             if (i < npaths) {
                 float dx, dy, dz;
-                primary_dir(cam, pid0 + i, spp, &dx, &dy, &dz);
+                primary_dir(cam, pid0 + i, spp, dspp, &dx, &dy, &dz);
                 const float b = cam.eye[0] * dx + cam.eye[1] * dy + cam.eye[2] * dz;
                 const float disc = b * b - c;
                 const float sq = sqrtf(fmaxf(disc, 0.f));
@@ -294,7 +319,7 @@ __global__ void aov_kernel(CamDev cam, int64_t px0, const int* __restrict__ coun
 __global__ void camera_rays_kernel(CamDev cam, int64_t npx, float* __restrict__ o, float* __restrict__ w) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npx; p += (int64_t)gridDim.x * blockDim.x) {
         float dx, dy, dz;
-        primary_dir(cam, p, 1, &dx, &dy, &dz);
+        primary_dir(cam, p, 1, DivU32{1u, 0, 0}, &dx, &dy, &dz);
         o[3 * p] = cam.eye[0];
         o[3 * p + 1] = cam.eye[1];
         o[3 * p + 2] = cam.eye[2];
@@ -385,6 +410,9 @@ int make_cam(const ddf_camera* cam, CamDev* out) {
     cd.aspect = (float)((double)cam->width / cam->height);
     cd.W = cam->width;
     cd.H = cam->height;
+    cd.dW = make_div((uint32_t)cam->width);
+    cd.inv2W = (float)(2.0 / cam->width);
+    cd.inv2H = (float)(2.0 / cam->height);
     cd.seed = cam->seed;
     cd.albedo = cam->albedo;
     cd.env = cam->env;
@@ -450,7 +478,7 @@ int render(ddf_net_s* net, const ddf_camera* cam, int spp, int bounces, float* i
         const int64_t pid0 = px0 * spp;
         const int rg = (int)std::min<int64_t>((npaths + kThreads * kRaysPerThread - 1) / (kThreads * kRaysPerThread), grid);
         int pe = net->prof.begin(PROF_RAYGEN, stream);
-        raygen_kernel<<<rg, kThreads, 0, stream>>>(cd, spp, pid0, npaths, B.o[0], B.w[0], B.lid[0],
+        raygen_kernel<<<rg, kThreads, 0, stream>>>(cd, spp, make_div((uint32_t)spp), pid0, npaths, B.o[0], B.w[0], B.lid[0],
                                                    B.thr[0], B.radiance, B.counts);
         DDF_LAUNCH_CHECK();
         net->prof.end(pe, stream);
@@ -511,7 +539,7 @@ int render_aov(ddf_net_s* net, const ddf_camera* cam, float* depth, float* norma
         DDF_CUDA_TRY(cudaMemsetAsync(B.counts, 0, sizeof(int), stream));
         aov_fill_kernel<<<grid, kThreads, 0, stream>>>(px0, npx, depth, normal);
         const int rg = (int)std::min<int64_t>((npx + kThreads * kRaysPerThread - 1) / (kThreads * kRaysPerThread), grid);
-        raygen_kernel<<<rg, kThreads, 0, stream>>>(cd, 1, px0, npx, B.o[0], B.w[0], B.lid[0], B.thr[0], B.radiance,
+        raygen_kernel<<<rg, kThreads, 0, stream>>>(cd, 1, make_div(1u), px0, npx, B.o[0], B.w[0], B.lid[0], B.thr[0], B.radiance,
                                                    B.counts);
         DDF_LAUNCH_CHECK();
         if ((rc = field_query(net, B.o[0], B.w[0], npx, B.counts, B.dist, B.logit, nullptr, B.nrm, stream))) return rc;
@@ -575,7 +603,7 @@ int mesh_render(ddf_mesh_s* m, const ddf_camera* cam, int spp, int bounces, floa
         e = cudaMemsetAsync(B.counts, 0, sizeof(int) * (bounces + 1), stream);
         if (e != cudaSuccess) break;
         const int rg = (int)std::min<int64_t>((npaths + kThreads * kRaysPerThread - 1) / (kThreads * kRaysPerThread), grid);
-        raygen_kernel<<<rg, kThreads, 0, stream>>>(cd, spp, pid0, npaths, B.o[0], B.w[0], B.lid[0], B.thr[0],
+        raygen_kernel<<<rg, kThreads, 0, stream>>>(cd, spp, make_div((uint32_t)spp), pid0, npaths, B.o[0], B.w[0], B.lid[0], B.thr[0],
                                                    B.radiance, B.counts);
         for (int b = 1; b <= bounces && !rc; ++b) {
             const int s = (b - 1) & 1;
