@@ -84,7 +84,7 @@ struct TcArgs {
     int maxL;
     uint32_t* gmask;   // width 512: per-CTA ReLU masks of the reverse pass
     const uint8_t* bias_mn;   // BF16 pair kernel: [L][32 W bytes] bias operand tiles
-    uint32_t* train_masks;    // training forward: ReLU masks of a_1 .. a_{L-1}, [ld][W / 32] each
+    uint32_t* train_masks;    // training forward: ReLU masks of a_1 .. a_{L-1}, [ld][W / 32] each (nz_bits32 order)
     __nv_bfloat16* train_aL;  // training forward: a_L, row-major [ld][W]
     int64_t train_ld;         // training forward: rows of one workspace array
     float* train_colpart;     // training reverse: per-32-row column sums of delta_l, [L][ld / 32][W]
@@ -146,11 +146,14 @@ __device__ __forceinline__ void release_kb(uint64_t* actr, int kb) {
     tc_fence_before();
     mbar_arrive(&actr[kb]);
 }
-// Bit c = 1 where accumulator value c of 32 is positive (the ReLU mask of 32 columns).
-__device__ __forceinline__ uint32_t pos_bits32(const uint32_t* raw) {
+// The ReLU mask of 32 columns from their packed BF16 activations pk[q] = (ReLU(z_{2q}),
+// ReLU(z_{2q+1})): bit q for column 2q, bit 16 + q for column 2q + 1 (an activation is non-zero
+// exactly when its pre-activation is above 2^-134). Adding 0x7FFF to a non-negative half sets
+// its top bit exactly when the half is non-zero, without a carry into the other half.
+__device__ __forceinline__ uint32_t nz_bits32(const uint32_t* pk) {
     uint32_t b = 0;
 #pragma unroll
-    for (int c = 0; c < 32; ++c) b |= ((int)raw[c] > 0 ? 1u : 0u) << c;
+    for (int q = 0; q < 16; ++q) b |= ((pk[q] + 0x7FFF7FFFu) >> (15 - q)) & ((1u << q) | (1u << (16 + q)));
     return b;
 }
 // The same with one arrival per warp (barrier count = warps): every lane fences its own stores
@@ -973,7 +976,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                                 }
                                 if (TRAIN && t * kTileM + r < pi.rows)   // ReLU mask of a_{s+1}
                                     a.train_masks[((int64_t)s * a.train_ld + pi.row0 + t * kTileM + r) * (W / 32) +
-                                                  2 * kb + grp] = pos_bits32(raw[i]);
+                                                  2 * kb + grp] = nz_bits32(pk);
                             } else if (TRAIN) {
                                 // a_L = ReLU(acc) rounded to BF16, for the output layer's kernel
                                 if (t * kTileM + r < pi.rows) {
@@ -1321,7 +1324,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
 #pragma unroll
                                 for (int q = 0; q < 16; ++q)
                                     pk[q] = pack_relu(__uint_as_float(raw[i][2 * q]), __uint_as_float(raw[i][2 * q + 1]));
-                                gmt[(s * (W / 32) + (c0 >> 5)) * 128 + r] = pos_bits32(raw[i]);
+                                gmt[(s * (W / 32) + (c0 >> 5)) * 128 + r] = nz_bits32(pk);
                             } else if (s == L - 1) {
                                 // delta of the last hidden layer: W_out[0] on the active units
 #pragma unroll
@@ -1333,8 +1336,8 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                                 const uint32_t bits = mbits[kb];
 #pragma unroll
                                 for (int q = 0; q < 16; ++q)
-                                    pk[q] = pack_bf16(((bits >> (2 * q)) & 1u) ? __uint_as_float(raw[i][2 * q]) : 0.f,
-                                                      ((bits >> (2 * q + 1)) & 1u) ? __uint_as_float(raw[i][2 * q + 1]) : 0.f);
+                                    pk[q] = pack_bf16(((bits >> q) & 1u) ? __uint_as_float(raw[i][2 * q]) : 0.f,
+                                                      ((bits >> (16 + q)) & 1u) ? __uint_as_float(raw[i][2 * q + 1]) : 0.f);
                             }
 #pragma unroll
                             for (int m = 0; m < 4; ++m)
@@ -1578,8 +1581,8 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                             uint32_t pk[16];
 #pragma unroll
                             for (int e = 0; e < 16; ++e)
-                                pk[e] = pack_bf16(((bits >> (2 * e)) & 1u) ? __uint_as_float(raw[i][2 * e]) : 0.f,
-                                                  ((bits >> (2 * e + 1)) & 1u) ? __uint_as_float(raw[i][2 * e + 1]) : 0.f);
+                                pk[e] = pack_bf16(((bits >> e) & 1u) ? __uint_as_float(raw[i][2 * e]) : 0.f,
+                                                  ((bits >> (16 + e)) & 1u) ? __uint_as_float(raw[i][2 * e + 1]) : 0.f);
 #pragma unroll
                             for (int m = 0; m < 4; ++m)
                                 st_shared_v4(tact + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],

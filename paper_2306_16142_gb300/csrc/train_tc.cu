@@ -1041,7 +1041,9 @@ struct TcWs {
     int64_t m = 0, mp = 0;   // rows per chunk, padded to 128
     int ksplit_max = 0;
     __nv_bfloat16* act;      // a_l, l = 0..L, row-major: [mp][K0], then [mp][W] each
-    uint32_t* masks;         // ReLU masks of a_1..a_{L-1}: [mp][W / 32] each
+    uint32_t* masks;         // ReLU masks of a_1..a_{L-1}: [mp][W / 32] each; bit order of their
+                             // writer: column c at bit c (GEMM forward, read by its data-gradient
+                             // GEMM), or the fused forward's even / odd halves (read by the chain)
     __nv_bfloat16* dl;       // deltas delta_0 .. delta_{L-1}, row-major [mp][W] each
     float* colpart;          // L x [mp / 32][W]
     float* headpart;         // [mp / 32][2W + 2]
