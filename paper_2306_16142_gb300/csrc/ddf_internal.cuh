@@ -150,7 +150,7 @@ int tc_train_forward(const ddf_net_s* net, const float* o, const float* w, int64
                      const CUtensorMap* map_act, uint32_t* masks, __nv_bfloat16* aL, int64_t ld, cudaStream_t stream);
 // The data-gradient chain of a training step, one persistent launch (widths 128, 256).
 int tc_train_dgrad(const ddf_net_s* net, __nv_bfloat16* deltas, int64_t m, int64_t ld, const uint32_t* masks,
-                   float* colpart, cudaStream_t stream);
+                   cudaStream_t stream);
 int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
                  const int* d_count, float* dist, float* logit, uint8_t* hit, float* normals,
                  cudaStream_t stream);

@@ -84,10 +84,10 @@ struct TcArgs {
     int maxL;
     uint32_t* gmask;   // width 512: per-CTA ReLU masks of the reverse pass
     const uint8_t* bias_mn;   // BF16 pair kernel: [L][32 W bytes] bias operand tiles
-    uint32_t* train_masks;    // training forward: ReLU masks of a_1 .. a_{L-1}, [ld][W / 32] each (nz_bits32 order)
+    uint32_t* train_masks;    // training forward: ReLU masks of a_1 .. a_{L-1}, word (2 kb + group) of row r at
+                              // [layer][2 kb + group][ld] (a warp's 32 rows contiguous; nz_bits32 order)
     __nv_bfloat16* train_aL;  // training forward: a_L, row-major [ld][W]
     int64_t train_ld;         // training forward: rows of one workspace array
-    float* train_colpart;     // training reverse: per-32-row column sums of delta_l, [L][ld / 32][W]
     const float* f8_emul;   // FP8 epilogue [L]: accumulator multiplier mu_l
 };
 
@@ -975,8 +975,8 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                                     }
                                 }
                                 if (TRAIN && t * kTileM + r < pi.rows)   // ReLU mask of a_{s+1}
-                                    a.train_masks[((int64_t)s * a.train_ld + pi.row0 + t * kTileM + r) * (W / 32) +
-                                                  2 * kb + grp] = nz_bits32(pk);
+                                    a.train_masks[((int64_t)s * (W / 32) + 2 * kb + grp) * a.train_ld + pi.row0 +
+                                                  t * kTileM + r] = nz_bits32(pk);
                             } else if (TRAIN) {
                                 // a_L = ReLU(acc) rounded to BF16, for the output layer's kernel
                                 if (t * kTileM + r < pi.rows) {
@@ -1375,8 +1375,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
 // network is trained by backpropagation): delta_{L-1} (from the output layer) comes in by TMA,
 // then for l = L-1 .. 1, delta_{l-1} = (delta_l W_l) * 1[a_l > 0] with W_l^T streamed through the
 // weight ring, each delta kept on chip as the next step's A operand. Every delta leaves by TMA
-// stores of its A tile (for the weight gradients), and the epilogue takes its per-32-row column
-// sums (the bias gradients) from the A tile in the same order as the training GEMM's epilogue.
+// stores of its A tile (for the weight gradients and, in the same kernel, the bias gradients).
 // The pair structure is that of mlp_pairn_kernel's reverse steps: one MMA-issuing thread per
 // tile, eight epilogue warps in two column groups serving tile 0 and then tile 1.
 template <int W>
@@ -1551,14 +1550,13 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     uint32_t mbits[NKBW];
 #pragma unroll
                     for (int kb = 0; kb < NKBW; ++kb)
-                        mbits[kb] = row < ld ? a.train_masks[((int64_t)(l - 1) * ld + row) * (W / 32) + 2 * kb + grp] : 0u;
+                        mbits[kb] = row < ld ? a.train_masks[((int64_t)(l - 1) * (W / 32) + 2 * kb + grp) * ld + row] : 0u;
                     ok = mbar_wait(&accf[t], (accph >> t) & 1u, a.err);
                     if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
                     accph ^= 1u << t;
                     tc_fence_after();
                     const uint32_t tcol = tbase + lane_off + (uint32_t)(t * W) + (uint32_t)(grp * 32);
                     const uint32_t tact = act_s + (uint32_t)t * kTile;
-                    const int64_t rblk = tile0 / 32 + q;   // this warp's 32-row block
 #pragma unroll
                     for (int pass = 0; pass < NKBW / 2; ++pass) {
                         uint32_t raw[2][32];
@@ -1595,37 +1593,6 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                         if (lane == 0) {
                             mbar_arrive(&actr[4 * t + 2 * pass]);
                             mbar_arrive(&actr[4 * t + 2 * pass + 1]);
-                        }
-#pragma unroll
-                        for (int i = 0; i < 2; ++i) {
-                            const int kb = 2 * pass + i;
-                            const uint32_t kbase = tact + (uint32_t)kb * 16384u;
-                            // column sums of the warp's 32 rows (BF16 values, as stored): lane
-                            // sums piece lane % 4 of rows 8 i + lane / 4, then a fixed butterfly
-                            float cs[8];
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) cs[e] = 0.f;
-#pragma unroll
-                            for (int i4 = 0; i4 < 4; ++i4) {
-                                uint32_t v[4];
-                                ld_shared_v4(kbase + swz(q * 32 + 8 * i4 + (lane >> 2), grp * 4 + (lane & 3)), v);
-#pragma unroll
-                                for (int e = 0; e < 4; ++e)
-                                    add2(cs[2 * e], cs[2 * e + 1], __uint_as_float(v[e] << 16),
-                                         __uint_as_float(v[e] & 0xffff0000u), cs[2 * e], cs[2 * e + 1]);
-                            }
-#pragma unroll
-                            for (int sh = 4; sh <= 16; sh <<= 1)
-#pragma unroll
-                                for (int e = 0; e < 8; e += 2)
-                                    add2(cs[e], cs[e + 1], __shfl_xor_sync(0xffffffffu, cs[e], sh),
-                                         __shfl_xor_sync(0xffffffffu, cs[e + 1], sh), cs[e], cs[e + 1]);
-                            if (lane < 4 && rblk < ld / 32) {
-                                float4* dst = reinterpret_cast<float4*>(
-                                    a.train_colpart + ((int64_t)(l - 1) * (ld / 32) + rblk) * W + kb * 64 + grp * 32 + 8 * lane);
-                                dst[0] = make_float4(cs[0], cs[1], cs[2], cs[3]);
-                                dst[1] = make_float4(cs[4], cs[5], cs[6], cs[7]);
-                            }
                         }
                     }
                 }
@@ -2983,7 +2950,7 @@ int tc_train_forward(const ddf_net_s* net, const float* o, const float* w, int64
 // a_{L-1} ([L - 1][ld][W / 32]) and the per-32-row column sums of delta_0 .. delta_{L-2} into
 // colpart ([L][ld / 32][W]). Rows m .. ld-1 read as zero.
 int tc_train_dgrad(const ddf_net_s* net, __nv_bfloat16* deltas, int64_t m, int64_t ld, const uint32_t* masks,
-                   float* colpart, cudaStream_t stream) {
+                   cudaStream_t stream) {
     const NetLayout& lay = net->lay;
     const TcPack* P = net->tc;
     const int W = lay.width, L = lay.L;
@@ -3005,7 +2972,6 @@ int tc_train_dgrad(const ddf_net_s* net, __nv_bfloat16* deltas, int64_t m, int64
     a.n = m;
     a.err = P->err;
     a.train_masks = const_cast<uint32_t*>(masks);
-    a.train_colpart = colpart;
     a.train_ld = ld;
     const Layout s = smem_layout_pair(W, W);
     if (s.nst < 2) return fail(DDF_ERR_UNSUPPORTED, "fused data-gradient chain: shared memory too small");

@@ -384,11 +384,16 @@ __global__ void __launch_bounds__(kTThreads, 1)
 // two TMEM accumulators) over its split, so every delta and activation K-block is read once, and
 // writes it as one split-K partial slab in wsum_kernel's fragment order. Both operands are read
 // MN-major from the row-major workspace arrays (64 x 64 TMA boxes), as in the per-layer wgrad.
+// While the MMAs run, the epilogue warps take the column sums of every delta K-block from the
+// same stages (the bias gradients db_l = sum over rows of delta_l): thread (cc, rg) owns the eight
+// features [8 cc, 8 cc + 8) and the row group rg of each 64-row stage, rows in order, and writes
+// its sums of the split once: bsum[l][s][rg][W] (W / 8 x rg_count threads, rg_count = 2048 / W).
 struct WArgs {
     int L, W, K0, nst;
     int ks, kb_per, nkb;   // splits per layer, K-blocks (64 rows) per split, K-blocks in all
     uint32_t off_bar;
     float* part;           // layer l: ks slabs of W x N_l floats at part + l * ks * W * max(K0, W)
+    float* bsum;           // [L][ks][2048 / W][W] column-sum partials of the deltas
     int* err;
 };
 
@@ -415,7 +420,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
     if (tid == 0) {
         for (int i = 0; i < NST; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
+            mbar_init(&empty[i], 1 + kTEpi);   // the MMA commit and every epilogue warp
         }
         mbar_init(accf, 1);
         mbar_init(acce, kTEpi * 32);
@@ -499,10 +504,45 @@ __global__ void __launch_bounds__(kTThreads, 1)
         // warp w: M-half w / 4 (rows 128 h + 32 (w % 4) + lane of dW_l), every 32-column chunk
         const int h = warp >> 2, q = warp & 3;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-        uint32_t tl = 0;
+        // column sums: thread (cc, rg), features [8 cc, 8 cc + 8) = 16-byte chunk cc % 8 of the
+        // 64-feature box cc / 8, rows [rpg rg, rpg rg + rpg) of every stage
+        const int ncc = W / 8, rgc = kTEpi * 32 / ncc, rpg = 64 / rgc;
+        const int cc = tid % ncc, rg = tid / ncc;
+        const uint32_t cbox = (uint32_t)(cc >> 3) * 8192u, cch = (uint32_t)(cc & 7);
+        uint32_t tl = 0, stg = 0, ring_ph = 0;
         for (int64_t t = blockIdx.x; t < items; t += gridDim.x, ++tl) {
             int l, s, n, kb0, kb1;
             item_range(t, l, s, n, kb0, kb1);
+            float cs[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) cs[e] = 0.f;
+            bool ok = true;
+            for (int kb = kb0; kb < kb1; ++kb) {
+                ok = mbar_wait(&full[stg], ring_ph, a.err);
+                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                const uint32_t sa = su32(smem + (size_t)stg * stage_bytes) + cbox;
+                for (int i = 0; i < rpg; ++i) {
+                    const int r = rg * rpg + i;
+                    uint32_t v[4];
+                    ld_shared_v4(sa + (uint32_t)r * 128u + ((cch ^ (uint32_t)(r & 7)) << 4), v);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        add2(cs[2 * e], cs[2 * e + 1], __uint_as_float(v[e] << 16),
+                             __uint_as_float(v[e] & 0xffff0000u), cs[2 * e], cs[2 * e + 1]);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[stg]);
+                if (++stg == (uint32_t)NST) {
+                    stg = 0;
+                    ring_ph ^= 1u;
+                }
+            }
+            if (!ok) break;
+            {
+                float4* dst = reinterpret_cast<float4*>(a.bsum + (((int64_t)l * a.ks + s) * rgc + rg) * W + 8 * cc);
+                dst[0] = make_float4(cs[0], cs[1], cs[2], cs[3]);
+                dst[1] = make_float4(cs[4], cs[5], cs[6], cs[7]);
+            }
             if (!mbar_wait(accf, tl & 1u, a.err)) break;
             tc_fence_after();
             if (h < nhalf) {
@@ -670,18 +710,20 @@ __global__ void wsum_all_kernel(const float4* __restrict__ part, int ks, int KM,
     }
 }
 
-// Bias gradients db_l (blockIdx.y = l < L, from the per-32-row delta column sums) and the output
-// layer's dW_out / db_out (blockIdx.y = L, from the head partials), in two fixed-order stages:
-// kBGroups row groups of the partials (block (32, 8): 32 consecutive outputs x 8 row lanes), then
-// the groups in order.
+// Bias gradients db_l (blockIdx.y = l < L, from lrows partial column sums of delta_l, layer l's at
+// lpart + l lstride) and the output layer's dW_out / db_out (blockIdx.y = L, from the hrows head
+// partials), in two fixed-order stages: kBGroups groups of the partial rows (block (32, 8): 32
+// consecutive outputs x 8 row lanes), then the groups in order.
 constexpr int kBGroups = 16;
-__global__ void bgrad_partial_kernel(const float* __restrict__ colpart, int64_t nrb, int64_t lstride, NetLayout lay,
-                                     const float* __restrict__ headpart, float* __restrict__ bpart) {
+__global__ void bgrad_partial_kernel(const float* __restrict__ lpart, int64_t lrows, int64_t lstride,
+                                     const float* __restrict__ headpart, int64_t hrows, NetLayout lay,
+                                     float* __restrict__ bpart) {
     const int l = blockIdx.y, g = blockIdx.z, W = lay.width;
     const int c = blockIdx.x * 32 + threadIdx.x;
     const int ncol = l < lay.L ? W : 2 * W + 2;
     const int64_t ld = l < lay.L ? W : 2 * W + 2;
-    const float* P = l < lay.L ? colpart + (int64_t)l * lstride : headpart;
+    const float* P = l < lay.L ? lpart + (int64_t)l * lstride : headpart;
+    const int64_t nrb = l < lay.L ? lrows : hrows;
     const int64_t per = (nrb + kBGroups - 1) / kBGroups;
     const int64_t b0 = g * per, b1 = min(nrb, b0 + per);
     __shared__ float red[8][33];
@@ -733,7 +775,7 @@ __global__ void tenc_backward_kernel(const float* __restrict__ o, const float* _
 // two-output head): y = a_L W_out^T + b_out; the per-row loss terms and G = dLoss/dy (L1 on hit
 // rows + BCE with logits; or the caller's cotangents); delta_{L-1} = (G W_out) * 1[a_L > 0],
 // row-major BF16; and per-32-row partial sums of delta (db_{L-1}), of G a_L (dW_out) and of G
-// (db_out). One warp per 32 rows; lane l owns columns [CPL l, CPL l + CPL).
+// (db_out). One warp per 32 rows; lane l owns columns [CPL l, CPL l + CPL) with CPL = W / 32.
 struct HeadArgs {
     const __nv_bfloat16* aL;
     const float* head;        // W_out [2][W], b_out [2]
@@ -753,146 +795,168 @@ struct HeadArgs {
     float head_delta;
 };
 
+// One lane's chunk of a BF16 row: CPL consecutive columns (CPL = 8: 16 bytes, CPL = 4: 8 bytes).
+template <int CPL>
+struct RowChunk {
+    uint32_t u[CPL / 2];
+    __device__ __forceinline__ void load(const __nv_bfloat16* p) {
+        if constexpr (CPL == 8) {
+            const uint4 v = *reinterpret_cast<const uint4*>(p);
+            u[0] = v.x; u[1] = v.y; u[2] = v.z; u[3] = v.w;
+        } else {
+            const uint2 v = *reinterpret_cast<const uint2*>(p);
+            u[0] = v.x; u[1] = v.y;
+        }
+    }
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int k = 0; k < CPL / 2; ++k) u[k] = 0u;
+    }
+    __device__ __forceinline__ void store(__nv_bfloat16* p) const {
+        if constexpr (CPL == 8) *reinterpret_cast<uint4*>(p) = make_uint4(u[0], u[1], u[2], u[3]);
+        else *reinterpret_cast<uint2*>(p) = make_uint2(u[0], u[1]);
+    }
+    __device__ __forceinline__ float at(int e) const { return (e & 1) ? bf_hi(u[e >> 1]) : bf_lo(u[e >> 1]); }
+};
+
+// v[0..31] of every lane -> v[0] of lane l holds the sum over the 32 lanes of v[l] (recursive
+// halving: each step a lane keeps the half of its values whose index bit matches its lane bit and
+// adds its partner's copy of that half; fixed order).
+__device__ __forceinline__ void transpose_reduce32(float* v, int lane) {
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) {
+        const bool up = (lane & k) != 0;
+#pragma unroll
+        for (int m = 0; m < k; ++m) {
+            const float send = up ? v[m] : v[m + k];
+            const float keep = up ? v[m + k] : v[m];
+            v[m] = keep + __shfl_xor_sync(0xffffffffu, send, k);
+        }
+    }
+}
+
 template <int W>
-__global__ void __launch_bounds__(128) head_kernel(const HeadArgs h) {
-    // half-warp per row, two rows per step: lane (hw = lane / 16, j = lane % 16) owns columns
-    // [CPL j, CPL j + CPL) of the rows 2 i + hw
-    constexpr int CPL = W / 16;
-    const int lane = threadIdx.x & 31, hw = lane >> 4, j = lane & 15;
+__global__ void __launch_bounds__(128, 4) head_kernel(const HeadArgs h) {
+    constexpr int CPL = W / 32;
+    const int lane = threadIdx.x & 31;
     const int64_t rblk = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (rblk * 32 >= h.mp) return;
-    float wo0[CPL], wo1[CPL], cd[CPL], cw0[CPL], cw1[CPL];
+    const int64_t row0 = rblk * 32;
+    const int c0 = CPL * lane;
+    float wo0[CPL], wo1[CPL];
 #pragma unroll
     for (int e = 0; e < CPL; ++e) {
-        wo0[e] = h.head[CPL * j + e];
-        wo1[e] = h.head[W + CPL * j + e];
-        cd[e] = cw0[e] = cw1[e] = 0.f;
+        wo0[e] = h.head[c0 + e];
+        wo1[e] = h.head[W + c0 + e];
     }
-    const float bo0 = h.head[2 * W], bo1 = h.head[2 * W + 1];
-    float sg0 = 0.f, sg1 = 0.f;
-    float inv_h = 0.f, inv_n = 0.f;
-    // this block's 32 labels / cotangents, one per lane, fetched once (no load on the row loop's path)
-    const int64_t rl = rblk * 32 + lane;
-    float lab_a = 0.f, lab_b = 0.f;   // (dist_gt, hit) or (g_dist, g_logit)
-    if (h.hit_gt) {
-        const int nh = *h.n_hit;
-        inv_h = nh > 0 ? 1.f / (float)nh : 0.f;
-        inv_n = 1.f / (float)h.n_total;
-        if (rl < h.m) {
-            lab_b = h.hit_gt[rl] ? 1.f : 0.f;
-            lab_a = lab_b > 0.f ? h.dist_gt[rl] : 0.f;
+    // y of the 32 rows: each lane's CPL-column dot products, then summed across the lanes so that
+    // lane i ends with row row0 + i
+    float p0[32], p1[32];
+#pragma unroll
+    for (int i0 = 0; i0 < 32; i0 += 4) {
+        RowChunk<CPL> ch[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (row0 + i0 + t < h.m) ch[t].load(h.aL + (row0 + i0 + t) * W + c0);
+            else ch[t].zero();
         }
-    } else if (rl < h.m) {
-        lab_a = h.gd_in ? h.gd_in[rl] : 0.f;
-        lab_b = h.gl_in ? h.gl_in[rl] : 0.f;
-    }
-    constexpr int AHEAD = 4;   // rows of this half-warp whose loads are in flight together
-    for (int i0 = 0; i0 < 16; i0 += AHEAD) {
-      uint4 raw[AHEAD][CPL / 8];
 #pragma unroll
-      for (int t = 0; t < AHEAD; ++t) {
-          const uint4* src = reinterpret_cast<const uint4*>(h.aL + (rblk * 32 + 2 * (i0 + t) + hw) * W + CPL * j);
+        for (int t = 0; t < 4; ++t) {
+            float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-          for (int q = 0; q < CPL / 8; ++q) raw[t][q] = src[q];
-      }
-#pragma unroll
-      for (int t = 0; t < AHEAD; ++t) {
-        const int i = i0 + t;
-        const int64_t row = rblk * 32 + 2 * i + hw;
-        float av[CPL];
-#pragma unroll
-        for (int q = 0; q < CPL / 8; ++q) {
-            const uint4 u = raw[t][q];
-            const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                av[8 * q + 2 * k] = bf_lo(uu[k]);
-                av[8 * q + 2 * k + 1] = bf_hi(uu[k]);
+            for (int e = 0; e < CPL; ++e) {
+                s0 = fmaf(ch[t].at(e), wo0[e], s0);
+                s1 = fmaf(ch[t].at(e), wo1[e], s1);
             }
+            p0[i0 + t] = s0;
+            p1[i0 + t] = s1;
         }
-        float p0 = 0.f, p1 = 0.f;
-#pragma unroll
-        for (int e = 0; e < CPL; ++e) {
-            p0 = fmaf(av[e], wo0[e], p0);
-            p1 = fmaf(av[e], wo1[e], p1);
-        }
-#pragma unroll
-        for (int o = 1; o < 16; o <<= 1) {   // fixed butterfly within the half-warp
-            p0 += __shfl_xor_sync(0xffffffffu, p0, o);
-            p1 += __shfl_xor_sync(0xffffffffu, p1, o);
-        }
-        const float d = p0 + bo0, z = p1 + bo1;
-        const float la = __shfl_sync(0xffffffffu, lab_a, 2 * i + hw);
-        const float lb = __shfl_sync(0xffffffffu, lab_b, 2 * i + hw);
-        float gd = 0.f, gl = 0.f;
-        if (row < h.m) {
-            if (h.hit_gt && h.head_kind != DDF_HEAD_TWO) {   // single output: y~ only (Eqs. 5, 7)
+    }
+    transpose_reduce32(p0, lane);
+    transpose_reduce32(p1, lane);
+    // lane i: the loss terms and G = dLoss/dy of row row0 + i
+    const int64_t row = row0 + lane;
+    float gd = 0.f, gl = 0.f;
+    if (row < h.m) {
+        const float d = p0[0] + h.head[2 * W], z = p1[0] + h.head[2 * W + 1];
+        if (h.hit_gt) {
+            const int nh = *h.n_hit;
+            const float inv_h = nh > 0 ? 1.f / (float)nh : 0.f;
+            const float inv_n = 1.f / (float)h.n_total;
+            const bool hit = h.hit_gt[row] != 0;
+            const float dg = hit ? h.dist_gt[row] : 0.f;
+            if (h.head_kind != DDF_HEAD_TWO) {   // single output: y~ only (Eqs. 5, 7)
                 float l;
-                single_head_loss(h.head_kind, h.head_delta, d, lb > 0.f, la, inv_n, &l, &gd);
-                if (j == 0) {
-                    h.row_l1[row] = 0.f;
-                    h.row_bce[row] = l;
-                }
-            } else if (h.hit_gt) {
-                const bool hit = lb > 0.f;
+                single_head_loss(h.head_kind, h.head_delta, d, hit, dg, inv_n, &l, &gd);
+                h.row_l1[row] = 0.f;
+                h.row_bce[row] = l;
+            } else {
+                const float lb = hit ? 1.f : 0.f;
                 float l1 = 0.f;
                 if (hit) {
-                    const float diff = d - la;
+                    const float diff = d - dg;
                     l1 = fabsf(diff);
                     gd = (diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f)) * inv_h;
                 }
                 gl = (1.f / (1.f + expf(-z)) - lb) * inv_n;
-                if (j == 0) {
-                    h.row_l1[row] = l1;
-                    h.row_bce[row] = fmaxf(z, 0.f) - z * lb + log1pf(expf(-fabsf(z)));
-                }
-            } else {
-                gd = la;
-                gl = lb;
+                h.row_l1[row] = l1;
+                h.row_bce[row] = fmaxf(z, 0.f) - z * lb + log1pf(expf(-fabsf(z)));
             }
+        } else {
+            gd = h.gd_in ? h.gd_in[row] : 0.f;
+            gl = h.gl_in ? h.gl_in[row] : 0.f;
         }
-        uint32_t pk[CPL / 2];
-#pragma unroll
-        for (int k = 0; k < CPL / 2; ++k) {
-            const float d0 = av[2 * k] > 0.f ? fmaf(gd, wo0[2 * k], gl * wo1[2 * k]) : 0.f;
-            const float d1 = av[2 * k + 1] > 0.f ? fmaf(gd, wo0[2 * k + 1], gl * wo1[2 * k + 1]) : 0.f;
-            pk[k] = pack_bf16(d0, d1);
-            cd[2 * k] += bf_lo(pk[k]);
-            cd[2 * k + 1] += bf_hi(pk[k]);
-        }
-        uint4* dst = reinterpret_cast<uint4*>(h.delta + row * W + CPL * j);
-#pragma unroll
-        for (int q = 0; q < CPL / 8; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-#pragma unroll
-        for (int e = 0; e < CPL; ++e) {
-            cw0[e] = fmaf(gd, av[e], cw0[e]);
-            cw1[e] = fmaf(gl, av[e], cw1[e]);
-        }
-        sg0 += gd;
-        sg1 += gl;
-      }
     }
-    // the two half-warps' sums (even rows + odd rows), same value in both
+    // db_out partial: the 32 rows' G by a fixed butterfly
+    float sg0 = gd, sg1 = gl;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sg0 += __shfl_xor_sync(0xffffffffu, sg0, o);
+        sg1 += __shfl_xor_sync(0xffffffffu, sg1, o);
+    }
+    // delta_{L-1} = (G W_out) * 1[a_L > 0] row by row (512 contiguous bytes per warp store), its
+    // column sums and the column sums of G a_L, rows in order
+    float cd[CPL], cw0[CPL], cw1[CPL];
+#pragma unroll
+    for (int e = 0; e < CPL; ++e) cd[e] = cw0[e] = cw1[e] = 0.f;
+#pragma unroll
+    for (int i0 = 0; i0 < 32; i0 += 8) {
+        RowChunk<CPL> ch[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            if (row0 + i0 + t < h.m) ch[t].load(h.aL + (row0 + i0 + t) * W + c0);
+            else ch[t].zero();
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const float g0 = __shfl_sync(0xffffffffu, gd, i0 + t);
+            const float g1 = __shfl_sync(0xffffffffu, gl, i0 + t);
+            RowChunk<CPL> dl;
+#pragma unroll
+            for (int k = 0; k < CPL / 2; ++k) {
+                const float a0 = ch[t].at(2 * k), a1 = ch[t].at(2 * k + 1);
+                const float d0 = a0 > 0.f ? fmaf(g0, wo0[2 * k], g1 * wo1[2 * k]) : 0.f;
+                const float d1 = a1 > 0.f ? fmaf(g0, wo0[2 * k + 1], g1 * wo1[2 * k + 1]) : 0.f;
+                dl.u[k] = pack_bf16(d0, d1);
+                cd[2 * k] += bf_lo(dl.u[k]);
+                cd[2 * k + 1] += bf_hi(dl.u[k]);
+                fma2p(g0, g0, a0, a1, cw0[2 * k], cw0[2 * k + 1], cw0[2 * k], cw0[2 * k + 1]);
+                fma2p(g1, g1, a0, a1, cw1[2 * k], cw1[2 * k + 1], cw1[2 * k], cw1[2 * k + 1]);
+            }
+            dl.store(h.delta + (row0 + i0 + t) * W + c0);
+        }
+    }
+    float* cp = h.colpart + rblk * W + c0;
+    float* hp = h.headpart + rblk * (2 * W + 2);
 #pragma unroll
     for (int e = 0; e < CPL; ++e) {
-        cd[e] += __shfl_xor_sync(0xffffffffu, cd[e], 16);
-        cw0[e] += __shfl_xor_sync(0xffffffffu, cw0[e], 16);
-        cw1[e] += __shfl_xor_sync(0xffffffffu, cw1[e], 16);
+        cp[e] = cd[e];
+        hp[c0 + e] = cw0[e];
+        hp[W + c0 + e] = cw1[e];
     }
-    sg0 += __shfl_xor_sync(0xffffffffu, sg0, 16);
-    sg1 += __shfl_xor_sync(0xffffffffu, sg1, 16);
-    if (hw == 0) {
-        float* hp = h.headpart + rblk * (2 * W + 2);
-#pragma unroll
-        for (int e = 0; e < CPL; ++e) {
-            h.colpart[rblk * W + CPL * j + e] = cd[e];
-            hp[CPL * j + e] = cw0[e];
-            hp[W + CPL * j + e] = cw1[e];
-        }
-        if (j == 0) {
-            hp[2 * W] = sg0;
-            hp[2 * W + 1] = sg1;
-        }
+    if (lane == 0) {
+        hp[2 * W] = sg0;
+        hp[2 * W + 1] = sg1;
     }
 }
 
@@ -990,10 +1054,11 @@ int tmap_rows(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows, u
 }
 
 // wgrad_all_kernel over rows [0, m) of the workspace arrays (row stride ld): deltas [L][ld][W],
-// a_0 [ld][K0], a_1 .. a_{L-1} [L - 1][ld][W]; the partial slabs into part. Returns the splits
-// per layer.
+// a_0 [ld][K0], a_1 .. a_{L-1} [L - 1][ld][W]; the partial slabs into part, the deltas' column-sum
+// partials into bsum ([L][ks][2048 / W][W]). Returns the splits per layer.
 int launch_wgrad_all(const ddf_net_s* net, const __nv_bfloat16* deltas, const __nv_bfloat16* a0,
-                     const __nv_bfloat16* act1, int64_t m, int64_t ld, float* part, int* ks_out, cudaStream_t s) {
+                     const __nv_bfloat16* act1, int64_t m, int64_t ld, float* part, float* bsum, int* ks_out,
+                     cudaStream_t s) {
     const NetLayout& lay = net->lay;
     const int W = lay.width, L = lay.L, K0 = net->tc->K0, KM = std::max(K0, W);
     CUtensorMap mD, mA0, mAct;
@@ -1010,6 +1075,7 @@ int launch_wgrad_all(const ddf_net_s* net, const __nv_bfloat16* deltas, const __
     a.kb_per = (a.nkb + want - 1) / want;
     a.ks = (a.nkb + a.kb_per - 1) / a.kb_per;
     a.part = part;
+    a.bsum = bsum;
     a.err = net->tc->err;
     const uint32_t stage = (uint32_t)(W + KM) * 128u;
     a.nst = (int)std::min<uint32_t>(8u, (kSmemMax - 2048u) / stage);
@@ -1041,12 +1107,14 @@ struct TcWs {
     int64_t m = 0, mp = 0;   // rows per chunk, padded to 128
     int ksplit_max = 0;
     __nv_bfloat16* act;      // a_l, l = 0..L, row-major: [mp][K0], then [mp][W] each
-    uint32_t* masks;         // ReLU masks of a_1..a_{L-1}: [mp][W / 32] each; bit order of their
-                             // writer: column c at bit c (GEMM forward, read by its data-gradient
-                             // GEMM), or the fused forward's even / odd halves (read by the chain)
+    uint32_t* masks;         // ReLU masks of a_1..a_{L-1}: mp x W / 32 words each; layout of their
+                             // writer: [mp][W / 32] with column c at bit c (GEMM forward, read by its
+                             // data-gradient GEMM), or [W / 32][mp] with the fused forward's
+                             // even / odd halves (read by the chain)
     __nv_bfloat16* dl;       // deltas delta_0 .. delta_{L-1}, row-major [mp][W] each
     float* colpart;          // L x [mp / 32][W]
     float* headpart;         // [mp / 32][2W + 2]
+    float* bsum;             // [L][ks][2048 / W][W] (the all-layers weight-gradient kernel)
     float* wpart;            // [ksplit][W][max(K0, W)]
     float* gx;               // [mp][K0]
     float* grad;             // [n_params]
@@ -1063,7 +1131,7 @@ int ensure_tc_ws(ddf_net_s* net, int64_t n, TcWs& ws) {
     const int ntm = W / 128;   // wgrad M tiles
     ws.ksplit_max = std::max(1, num_sms() / ntm);
     // buffer sizes in bytes for chunks of mp rows, in carving order
-    auto sizes = [&](size_t mp, size_t out[17]) {
+    auto sizes = [&](size_t mp, size_t out[18]) {
         out[0] = ((size_t)K0 + (size_t)L * W) * mp * 2;                  // act (a_0 .. a_L)
         out[1] = out[2] = 0;
         out[3] = (size_t)(L - 1) * mp * W / 8 + 4;                       // masks
@@ -1079,15 +1147,16 @@ int ensure_tc_ws(ddf_net_s* net, int64_t n, TcWs& ws) {
         out[14] = 4;                                                     // n_hit
         out[15] = 256 * sizeof(double);                                  // loss partials
         out[16] = (size_t)(L + 1) * kBGroups * (2 * W + 2) * 4;          // bias-gradient partials
+        out[17] = (size_t)std::max(num_sms(), L) * (2048 / W) * W * 4;   // delta column-sum partials
     };
     auto total = [&](size_t mp) {
-        size_t b[17], t = 0;
+        size_t b[18], t = 0;
         sizes(mp, b);
         for (size_t x : b) t += (x + 255) / 256 * 256;
         return t;
     };
     const size_t fixed = total(0);
-    const size_t per_128 = total(128) - fixed + 17 * 256;   // bytes per 128 rows (with rounding slack)
+    const size_t per_128 = total(128) - fixed + 18 * 256;   // bytes per 128 rows (with rounding slack)
     int64_t m = net->ws_limit > fixed ? (int64_t)((net->ws_limit - fixed) / per_128) * 128 : 0;
     m = std::max<int64_t>(128, std::min<int64_t>(m, (n + 127) / 128 * 128));
     ws.m = m;
@@ -1100,11 +1169,11 @@ int ensure_tc_ws(ddf_net_s* net, int64_t n, TcWs& ws) {
         DDF_CUDA_TRY(cudaMalloc(&net->train_ws, need));
         net->train_ws_bytes = need;
     }
-    size_t b[17];
+    size_t b[18];
     sizes((size_t)m, b);
     uint8_t* p = (uint8_t*)net->train_ws;
-    void* q[17];
-    for (int i = 0; i < 17; ++i) {
+    void* q[18];
+    for (int i = 0; i < 18; ++i) {
         q[i] = p;
         p += (b[i] + 255) / 256 * 256;
     }
@@ -1121,6 +1190,7 @@ int ensure_tc_ws(ddf_net_s* net, int64_t n, TcWs& ws) {
     ws.n_hit = (int*)q[14];
     ws.loss_part = (double*)q[15];
     ws.bpart = (float*)q[16];
+    ws.bsum = (float*)q[17];
     return DDF_OK;
 }
 
@@ -1226,11 +1296,11 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
     // the data-gradient chain delta_{L-2} .. delta_0 in one persistent launch where the fused
     // forward runs (and its bias-gradient column sums); otherwise one GEMM per layer below
     const bool chain = K0 <= 128 && W <= 256;
+    int ks = 0;
     if (chain) {
         // then every layer's weight gradient in one launch and the split sums per layer
-        if ((rc = tc_train_dgrad(net, ws.dl, m, ld, ws.masks, ws.colpart, s))) return rc;
-        int ks = 0;
-        if ((rc = launch_wgrad_all(net, ws.dl, act(0), act(1), m, ld, ws.wpart, &ks, s))) return rc;
+        if ((rc = tc_train_dgrad(net, ws.dl, m, ld, ws.masks, s))) return rc;
+        if ((rc = launch_wgrad_all(net, ws.dl, act(0), act(1), m, ld, ws.wpart, ws.bsum, &ks, s))) return rc;
         const int KM = std::max(K0, W);
         wsum_all_kernel<<<dim3((unsigned)((W / 32) * (KM / 32)), (unsigned)L), dim3(32, 8), 0, s>>>(
             (const float4*)ws.wpart, ks, KM, K0, lay, grad);
@@ -1301,9 +1371,12 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
             DDF_LAUNCH_CHECK();
         }
     }
+    // bias gradients: from the weight-gradient kernel's column sums on the chain path, from the
+    // per-32-row column sums of the head and the data-gradient GEMMs otherwise
     const unsigned gx = (unsigned)((2 * W + 2 + 31) / 32);
+    const int64_t lrows = chain ? (int64_t)ks * (2048 / W) : mp / 32;
     bgrad_partial_kernel<<<dim3(gx, (unsigned)(L + 1), kBGroups), dim3(32, 8), 0, s>>>(
-        ws.colpart, mp / 32, (ld / 32) * W, lay, ws.headpart, ws.bpart);
+        chain ? ws.bsum : ws.colpart, lrows, chain ? lrows * W : (ld / 32) * W, ws.headpart, mp / 32, lay, ws.bpart);
     bgrad_final_kernel<<<dim3(gx, (unsigned)(L + 1)), 32, 0, s>>>(ws.bpart, lay, grad);
     DDF_LAUNCH_CHECK();
     return DDF_OK;
