@@ -234,6 +234,13 @@ int loss_reduce(const float* row_l1, const float* row_bce, int64_t n, const int*
 // One Adam step on the FP32 masters, then the working copies are rebuilt from them.
 // grad (the batch's weight gradient) is scratch: the weight-normalised path rewrites it in place.
 int adam_and_repack(ddf_net_s* net, float* grad, const ddf_adam* opt, cudaStream_t stream);
+// The Adam moments allocated on first use, the step count advanced, the bias corrections c1, c2.
+int adam_prepare(ddf_net_s* net, const ddf_adam* opt, float* c1, float* c2, cudaStream_t stream);
+// One Adam step on the FP32 masters of a BF16 tensor-core handle (plain two-output head, no weight
+// normalisation) fused with the repacking of its BF16 copy, and the step's loss from the
+// output-layer kernel's per-32-row partials (nlb blocks; loss may be null).
+int tc_adam_pack(ddf_net_s* net, const float* grad, const ddf_adam* opt, float c1, float c2, const double* lossp,
+                 int64_t nlb, const int* n_hit, int64_t n, float* loss, cudaStream_t stream);
 
 // ------------------------------------------------------------------ BF16 tensor-core training (train_tc.cu)
 bool tct_supported(const ddf_net_s* net);

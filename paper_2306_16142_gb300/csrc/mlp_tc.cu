@@ -2459,6 +2459,127 @@ __global__ void pack_bias_mn_kernel(const float* __restrict__ master, NetLayout 
     }
 }
 
+// One Adam step on the FP32 masters of a BF16 handle (the arithmetic of adam_kernel) fused with
+// the repacking of pack_kernel / pack_bias_mn_kernel, and the step's loss. Blocks [0, ntiles):
+// 32 x 32 tiles (32 output units x 32 inputs) of every layer's W_l; each thread updates its
+// elements, writes them to the forward copy [out][packed position] and to a shared-memory tile
+// from which the transposed copy [packed position][out] is written whole 32-unit rows at a time.
+// Blocks [ntiles, ntiles + nbias): the biases (FP32 copy and the two BF16 rows of the MN-major bias
+// operand tile) and the output layer (FP32 head), elementwise. The last block, when loss is set:
+// loss = sum(L1 terms) / n_hit + sum(BCE terms) / n from the per-32-row partials, fixed order.
+// Only parameters are rewritten: the zero padding of the packed copies stays as tc_pack left it.
+struct AdamPack {
+    float* w;
+    const float* g;
+    float* m;
+    float* v;
+    float lr, b1, b2, eps, c1, c2;
+    NetLayout lay;
+    int kmax, ntiles, nbias;
+    __nv_bfloat16* wf;
+    __nv_bfloat16* wb;
+    float* bias;
+    float* head;
+    uint8_t* bias_mn;
+    const double* lossp;
+    int64_t nlb, n;
+    const int* n_hit;
+    float* loss;
+};
+
+__device__ __forceinline__ float adam_one(const AdamPack& a, int64_t i) {
+    const float gi = a.g[i];
+    const float mi = a.b1 * a.m[i] + (1.f - a.b1) * gi;
+    const float vi = a.b2 * a.v[i] + (1.f - a.b2) * gi * gi;
+    a.m[i] = mi;
+    a.v[i] = vi;
+    const float wi = a.w[i] - a.lr * (mi / a.c1) / (sqrtf(vi / a.c2) + a.eps);
+    a.w[i] = wi;
+    return wi;
+}
+
+__global__ void __launch_bounds__(256) adam_pack_kernel(const AdamPack a) {
+    const NetLayout& lay = a.lay;
+    const int W = lay.width, L = lay.L;
+    const int tid = threadIdx.x;
+    if ((int)blockIdx.x < a.ntiles) {
+        int t = blockIdx.x, l = 0, in = 0, nit = 1;
+        for (l = 0; l < L; ++l) {
+            in = l == 0 ? lay.E : W;
+            nit = (in + 31) / 32;
+            if (t < (W / 32) * nit) break;
+            t -= (W / 32) * nit;
+        }
+        const int ot = t / nit, it = t % nit;
+        __shared__ __nv_bfloat16 tile[32][34];
+        const int x = tid & 31, y = tid >> 5;
+        const int i = 32 * it + x;
+        const int pi = l == 0 ? (i < 6 ? i : i + 2) : i;   // packed position of input i (in_feature's inverse)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int rr = y + 8 * k, o = 32 * ot + rr;
+            if (i < in) {
+                const __nv_bfloat16 b = __float2bfloat16_rn(adam_one(a, lay.w_off[l] + (int64_t)o * in + i));
+                a.wf[((int64_t)l * W + o) * a.kmax + pi] = b;
+                tile[rr][x] = b;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int cc = y + 8 * k, i2 = 32 * it + cc;
+            const int p2 = l == 0 ? (i2 < 6 ? i2 : i2 + 2) : i2;
+            if (i2 < in && p2 < W) a.wb[((int64_t)l * W + p2) * W + 32 * ot + x] = tile[x][cc];
+        }
+        return;
+    }
+    if ((int)blockIdx.x < a.ntiles + a.nbias) {
+        const int e = ((int)blockIdx.x - a.ntiles) * 256 + tid;
+        if (e < L * W) {
+            const int l = e / W, nn = e % W;
+            const float b = adam_one(a, lay.b_off[l] + nn);
+            a.bias[e] = b;
+            if (a.bias_mn) {
+                const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+                const __nv_bfloat16 lo = __float2bfloat16_rn(b - __bfloat162float(hi));
+                const int m = nn & 63;
+                uint8_t* dst = a.bias_mn + (size_t)l * W * 32;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const uint32_t off = (uint32_t)(nn >> 6) * 2048u + (uint32_t)k * 128u +
+                                         ((uint32_t)((m >> 3) ^ k) << 4) + (uint32_t)(m & 7) * 2u;
+                    *reinterpret_cast<__nv_bfloat16*>(dst + off) = k == 0 ? hi : lo;
+                }
+            }
+        } else if (e < L * W + 2 * W + 2) {
+            const int hh = e - L * W;
+            a.head[hh] = adam_one(a, hh < 2 * W ? lay.w_off[L] + hh : lay.b_off[L] + (hh - 2 * W));
+        }
+        return;
+    }
+    // the loss
+    __shared__ double r1[256], r2[256];
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t k = tid; k < a.nlb; k += 256) {
+        s1 += a.lossp[2 * k];
+        s2 += a.lossp[2 * k + 1];
+    }
+    r1[tid] = s1;
+    r2[tid] = s2;
+    __syncthreads();
+    for (int hw = 128; hw > 0; hw >>= 1) {
+        if (tid < hw) {
+            r1[tid] += r1[tid + hw];
+            r2[tid] += r2[tid + hw];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const int nh = *a.n_hit;
+        *a.loss = (float)((nh > 0 ? r1[0] / nh : 0.0) + r2[0] / (double)a.n);
+    }
+}
+
 int make_map(CUtensorMap* m, void* base, int inner, int rows, int L) {
     EncodeTiledFn enc = get_encode();
     if (!enc) return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
@@ -2854,6 +2975,43 @@ int tc_pack(ddf_net_s* net, int precision, cudaStream_t stream) {
                                                         P->emul8, P->bias8_mn, P->head8);
         DDF_LAUNCH_CHECK();
     }
+    return DDF_OK;
+}
+
+int tc_adam_pack(ddf_net_s* net, const float* grad, const ddf_adam* opt, float c1, float c2, const double* lossp,
+                 int64_t nlb, const int* n_hit, int64_t n, float* loss, cudaStream_t stream) {
+    const NetLayout& lay = net->lay;
+    TcPack* P = net->tc;
+    if (!P || P->precision != DDF_BF16) return fail(DDF_ERR_UNSUPPORTED, "fused Adam step: BF16 copy required");
+    const int W = lay.width, L = lay.L;
+    AdamPack a{};
+    a.w = net->master;
+    a.g = grad;
+    a.m = net->adam_m;
+    a.v = net->adam_v;
+    a.lr = opt->lr;
+    a.b1 = opt->beta1;
+    a.b2 = opt->beta2;
+    a.eps = opt->eps;
+    a.c1 = c1;
+    a.c2 = c2;
+    a.lay = lay;
+    a.kmax = P->kmax;
+    a.ntiles = 0;
+    for (int l = 0; l < L; ++l) a.ntiles += (W / 32) * (((l == 0 ? lay.E : W) + 31) / 32);
+    a.nbias = (L * W + 2 * W + 2 + 255) / 256;
+    a.wf = P->w_fwd;
+    a.wb = P->w_bwd;
+    a.bias = P->bias;
+    a.head = P->head;
+    a.bias_mn = P->bias_mn;
+    a.lossp = lossp;
+    a.nlb = nlb;
+    a.n = n;
+    a.n_hit = n_hit;
+    a.loss = loss;
+    adam_pack_kernel<<<(unsigned)(a.ntiles + a.nbias + (loss ? 1 : 0)), 256, 0, stream>>>(a);
+    DDF_LAUNCH_CHECK();
     return DDF_OK;
 }
 

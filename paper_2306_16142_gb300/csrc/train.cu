@@ -481,7 +481,7 @@ int loss_reduce(const float* row_l1, const float* row_bce, int64_t n, const int*
     return DDF_OK;
 }
 
-int adam_and_repack(ddf_net_s* net, float* grad, const ddf_adam* opt, cudaStream_t s) {
+int adam_prepare(ddf_net_s* net, const ddf_adam* opt, float* c1, float* c2, cudaStream_t s) {
     const int64_t P = net->lay.n_params;
     if (!net->adam_m) {
         DDF_CUDA_TRY(cudaMalloc(&net->adam_m, sizeof(float) * P));
@@ -491,9 +491,16 @@ int adam_and_repack(ddf_net_s* net, float* grad, const ddf_adam* opt, cudaStream
     }
     net->adam_step += 1;
     const double t = (double)net->adam_step;
-    const float c1 = (float)(1.0 - pow((double)opt->beta1, t));
-    const float c2 = (float)(1.0 - pow((double)opt->beta2, t));
-    int rc;
+    *c1 = (float)(1.0 - pow((double)opt->beta1, t));
+    *c2 = (float)(1.0 - pow((double)opt->beta2, t));
+    return DDF_OK;
+}
+
+int adam_and_repack(ddf_net_s* net, float* grad, const ddf_adam* opt, cudaStream_t s) {
+    const int64_t P = net->lay.n_params;
+    float c1, c2;
+    int rc = adam_prepare(net, opt, &c1, &c2, s);
+    if (rc) return rc;
     if (net->wn_p) {
         // Sec. 5.1's weight-normalised layers: Adam on (v, biases, head) and on g, then fold
         const int64_t G = (int64_t)net->lay.L * net->lay.width;

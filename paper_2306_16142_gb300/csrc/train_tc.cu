@@ -789,6 +789,7 @@ struct HeadArgs {
     int64_t n_total;
     float* row_l1;
     float* row_bce;
+    double* lossp;            // loss form, optional: per 32-row block (sum of L1 terms, sum of BCE terms)
     const float* gd_in;       // cotangent form
     const float* gl_in;
     int head_kind;            // DDF_HEAD_* (loss form)
@@ -876,7 +877,7 @@ __global__ void __launch_bounds__(128, 4) head_kernel(const HeadArgs h) {
     transpose_reduce32(p1, lane);
     // lane i: the loss terms and G = dLoss/dy of row row0 + i
     const int64_t row = row0 + lane;
-    float gd = 0.f, gl = 0.f;
+    float gd = 0.f, gl = 0.f, l1v = 0.f, bcev = 0.f;
     if (row < h.m) {
         const float d = p0[0] + h.head[2 * W], z = p1[0] + h.head[2 * W + 1];
         if (h.hit_gt) {
@@ -886,25 +887,34 @@ __global__ void __launch_bounds__(128, 4) head_kernel(const HeadArgs h) {
             const bool hit = h.hit_gt[row] != 0;
             const float dg = hit ? h.dist_gt[row] : 0.f;
             if (h.head_kind != DDF_HEAD_TWO) {   // single output: y~ only (Eqs. 5, 7)
-                float l;
-                single_head_loss(h.head_kind, h.head_delta, d, hit, dg, inv_n, &l, &gd);
-                h.row_l1[row] = 0.f;
-                h.row_bce[row] = l;
+                single_head_loss(h.head_kind, h.head_delta, d, hit, dg, inv_n, &bcev, &gd);
             } else {
                 const float lb = hit ? 1.f : 0.f;
-                float l1 = 0.f;
                 if (hit) {
                     const float diff = d - dg;
-                    l1 = fabsf(diff);
+                    l1v = fabsf(diff);
                     gd = (diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f)) * inv_h;
                 }
                 gl = (1.f / (1.f + expf(-z)) - lb) * inv_n;
-                h.row_l1[row] = l1;
-                h.row_bce[row] = fmaxf(z, 0.f) - z * lb + log1pf(expf(-fabsf(z)));
+                bcev = fmaxf(z, 0.f) - z * lb + log1pf(expf(-fabsf(z)));
             }
+            h.row_l1[row] = l1v;
+            h.row_bce[row] = bcev;
         } else {
             gd = h.gd_in ? h.gd_in[row] : 0.f;
             gl = h.gl_in ? h.gl_in[row] : 0.f;
+        }
+    }
+    if (h.lossp) {   // the block's loss terms by a fixed butterfly
+        double s1 = l1v, s2 = bcev;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) {
+            h.lossp[2 * rblk] = s1;
+            h.lossp[2 * rblk + 1] = s2;
         }
     }
     // db_out partial: the 32 rows' G by a fixed butterfly
@@ -1121,7 +1131,8 @@ struct TcWs {
     float* row_l1;           // [n]
     float* row_bce;          // [n]
     int* n_hit;
-    double* loss_part;       // [256]
+    double* loss_part;       // the loss reduction's partials: [256], or two per 32-row block of the
+                             // chunks' padded rows (the output-layer kernel's)
     float* bpart;            // (L + 1) x kBGroups x (2W + 2)
 };
 
@@ -1145,7 +1156,7 @@ int ensure_tc_ws(ddf_net_s* net, int64_t n, TcWs& ws) {
         out[11] = (size_t)lay.n_params * 4;                              // grad
         out[12] = out[13] = (size_t)n * 4;                               // row_l1, row_bce
         out[14] = 4;                                                     // n_hit
-        out[15] = 256 * sizeof(double);                                  // loss partials
+        out[15] = (size_t)std::max<int64_t>(256, 8 * ((n + 127) / 128)) * sizeof(double);   // loss partials
         out[16] = (size_t)(L + 1) * kBGroups * (2 * W + 2) * 4;          // bias-gradient partials
         out[17] = (size_t)std::max(num_sms(), L) * (2048 / W) * W * 4;   // delta column-sum partials
     };
@@ -1202,6 +1213,7 @@ struct ChunkTargets {
     int64_t n_total = 0;
     float* row_l1 = nullptr;
     float* row_bce = nullptr;
+    double* lossp = nullptr;   // per-32-row loss partials of the chunk (optional)
     const float* gd = nullptr;
     const float* gl = nullptr;
 };
@@ -1280,6 +1292,7 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
         h.n_total = tg.n_total;
         h.row_l1 = tg.row_l1;
         h.row_bce = tg.row_bce;
+        h.lossp = tg.lossp;
         h.gd_in = tg.gd;
         h.gl_in = tg.gl;
         h.head_kind = net->head_kind;
@@ -1436,6 +1449,9 @@ int tct_train_step(ddf_net_s* net, const float* o, const float* w, const float* 
     if (rc) return rc;
     DDF_CUDA_TRY(cudaMemsetAsync(ws.grad, 0, sizeof(float) * net->lay.n_params, s));
     if ((rc = count_hits(hit_gt, n, ws.n_hit, s))) return rc;
+    // BF16 handles with the plain two-output head: the output-layer kernel leaves per-32-row loss
+    // partials and one launch takes the loss, the Adam step and the repacking
+    const bool fused_tail = net->precision == DDF_BF16 && !net->wn_p && !head_single(net);
     for (int64_t r0 = 0; r0 < n; r0 += ws.m) {
         const int64_t m = std::min(ws.m, n - r0);
         ChunkTargets tg;
@@ -1445,7 +1461,14 @@ int tct_train_step(ddf_net_s* net, const float* o, const float* w, const float* 
         tg.n_total = n;
         tg.row_l1 = ws.row_l1 + r0;
         tg.row_bce = ws.row_bce + r0;
+        tg.lossp = fused_tail ? ws.loss_part + 2 * (r0 / 32) : nullptr;
         if ((rc = tc_chunk(net, ws, o + 3 * r0, w + 3 * r0, m, tg, ws.grad, nullptr, s))) return rc;
+    }
+    if (fused_tail) {
+        float c1, c2;
+        if ((rc = adam_prepare(net, opt, &c1, &c2, s))) return rc;
+        net->master_t_stale = true;   // the FP32 transposed copy is rebuilt by the next FP32 query
+        return tc_adam_pack(net, ws.grad, opt, c1, c2, ws.loss_part, (n + 127) / 128 * 4, ws.n_hit, n, loss, s);
     }
     if (loss && (rc = loss_reduce(ws.row_l1, ws.row_bce, n, ws.n_hit, loss, ws.loss_part, s))) return rc;
     return adam_and_repack(net, ws.grad, opt, s);
