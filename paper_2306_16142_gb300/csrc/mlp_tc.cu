@@ -1197,6 +1197,11 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             load_row(blockIdx.x, grp, rme, vme);
             encode_tile(vme);
         }
+        uint32_t mnext[2][NKBW];   // each tile's masks of its next reverse step
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+            for (int kb = 0; kb < NKBW; ++kb) mnext[t][kb] = 0u;
         for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x) {
             const int64_t pn = p + gridDim.x;   // the next pair of this CTA
             for (int s = 0; s < nsteps && ok; ++s) {
@@ -1286,16 +1291,19 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     }
                     break;
                 }
-                const int l_bwd = 2 * L - 1 - s;
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
                     uint32_t* gmt = gm + (size_t)t * L * (W / 32) * 128;
-                    // the reverse step's ReLU masks (L2-resident), fetched while the MMAs run
+                    // the reverse step's ReLU masks (L2-resident, this thread's own words), fetched
+                    // one step ahead
                     uint32_t mbits[NKBW];
-                    if (s >= L && l_bwd >= 1) {
+#pragma unroll
+                    for (int kb = 0; kb < NKBW; ++kb) mbits[kb] = mnext[t][kb];
+                    if (s + 1 >= L && 2 * L - 2 - s >= 1) {
+                        const int lb = 2 * L - 2 - s;   // the next step's layer
 #pragma unroll
                         for (int kb = 0; kb < NKBW; ++kb)
-                            mbits[kb] = gmt[((l_bwd - 1) * (W / 32) + ((kb * 64 + grp * 32) >> 5)) * 128 + r];
+                            mnext[t][kb] = gmt[((lb - 1) * (W / 32) + ((kb * 64 + grp * 32) >> 5)) * 128 + r];
                     }
                     ok = mbar_wait(&accf[t], (accph >> t) & 1u, a.err);
                     if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
@@ -1398,8 +1406,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
     uint64_t* accf = actr + 8;         // [tile]
     uint64_t* tfree = accf + 2;        // [tile]: the epilogue has read the tile's accumulator
     uint64_t* ain = tfree + 2;         // [tile]: the pair's delta_{L-1} loaded
-    uint64_t* afree = ain + 2;         // [tile]: the last delta stored, the A tile may be refilled
-    uint64_t* sdone = afree + 2;       // [tile][K-block]: the step's store of the K-block has read it
+    uint64_t* sdone = ain + 4;         // [tile][K-block]: the step's store of the K-block has read it
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sdone + 8);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1420,7 +1427,6 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             mbar_init(&accf[t], 1);
             mbar_init(&tfree[t], kEpiWarps);
             mbar_init(&ain[t], 1);
-            mbar_init(&afree[t], 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -1436,17 +1442,9 @@ __global__ void __launch_bounds__(kThreadsP, 1)
     if (warp == kEpiWarps) {
         // ---------------------------------------------------------------- TMA producer
         if (lane == 0) {
-            uint32_t stg = 0, ring_ph = 0, k = 0;
+            uint32_t stg = 0, ring_ph = 0;
             bool ok = true;
-            for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x, ++k) {
-                // the pair's delta_{L-1} into each tile, once the tile's previous deltas are stored
-                for (int t = 0; t < 2 && ok; ++t) {
-                    if (!mbar_wait(&afree[t], (k & 1u) ^ 1u, a.err)) { ok = false; break; }
-                    mbar_expect_tx(&ain[t], kTile);
-                    for (int kb = 0; kb < NKBW; ++kb)
-                        tma_load_3d(act + (size_t)t * kTile + (size_t)kb * 16384u, &mapD, &ain[t], kb * 64,
-                                    (int)(p * 2 * kTileM + t * kTileM), L - 1);
-                }
+            for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x)
                 for (int j = 0; j < nsteps && ok; ++j)
                     for (int kb = 0; kb < NKBW; ++kb) {
                         if (!mbar_wait(&empty[stg], ring_ph ^ 1u, a.err)) { ok = false; break; }
@@ -1457,13 +1455,21 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                             ring_ph ^= 1u;
                         }
                     }
-            }
         }
     } else if (warp == kEpiWarps + 1 || warp == kEpiWarps + 2) {
         // ---------------------------------------------------------------- MMA issuers
         if (lane == 0) {
             const int t = warp - (kEpiWarps + 1);
             uint32_t stg = 0, ring_ph = 0, actph = 0, tfph = 0, k = 0;
+            // delta_{L-1} of pair pp into this tile's A operand (issued by this thread once the
+            // tile's previous deltas have been stored, so the weight ring never waits for it)
+            auto load_in = [&](int64_t pp) {
+                mbar_expect_tx(&ain[t], kTile);
+                for (int kb = 0; kb < NKBW; ++kb)
+                    tma_load_3d(act + (size_t)t * kTile + (size_t)kb * 16384u, &mapD, &ain[t], kb * 64,
+                                (int)(pp * 2 * kTileM + t * kTileM), L - 1);
+            };
+            if ((int64_t)blockIdx.x < npairs) load_in(blockIdx.x);
             bool ok = true, first = true;
             const uint32_t act_t = su32(act) + (uint32_t)t * kTile, wst_s = su32(wst);
             const uint32_t idesc = idesc_bf16(128, W);
@@ -1526,7 +1532,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                 for (int kb = 0; kb < NKBW && ok; ++kb)
                     if (!take(kb, row0, 0)) ok = false;
                 bulk_wait_read();
-                if (ok) mbar_arrive(&afree[t]);
+                if (ok && p + gridDim.x < npairs) load_in(p + gridDim.x);
             }
         }
     } else {
@@ -1539,18 +1545,26 @@ __global__ void __launch_bounds__(kThreadsP, 1)
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         uint32_t accph = 0, sdph = 0;
         bool ok = true;
+        // the ReLU mask words of a_l for step jj (l = L - 1 - jj) of tile t of pair pp
+        auto load_masks = [&](int64_t pp, int jj, int t, uint32_t* mb) {
+            const int64_t row = pp * 2 * kTileM + t * kTileM + r;
+            const bool valid = pp < npairs && row < ld;
+#pragma unroll
+            for (int kb = 0; kb < NKBW; ++kb)
+                mb[kb] = valid ? a.train_masks[((int64_t)(L - 2 - jj) * (W / 32) + 2 * kb + grp) * ld + row] : 0u;
+        };
+        uint32_t mnext[2][NKBW];   // each tile's masks of its next step, fetched one step ahead
+        load_masks(blockIdx.x, 0, 0, mnext[0]);
+        load_masks(blockIdx.x, 0, 1, mnext[1]);
         for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x) {
             for (int j = 0; j < nsteps && ok; ++j) {
-                const int l = L - 1 - j;   // this step's output is delta_{l-1}, masked by a_l
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
-                    const int64_t tile0 = p * 2 * kTileM + t * kTileM;
-                    const int64_t row = tile0 + r;
-                    // the step's ReLU mask words of a_l, fetched while the MMAs run
                     uint32_t mbits[NKBW];
 #pragma unroll
-                    for (int kb = 0; kb < NKBW; ++kb)
-                        mbits[kb] = row < ld ? a.train_masks[((int64_t)(l - 1) * (W / 32) + 2 * kb + grp) * ld + row] : 0u;
+                    for (int kb = 0; kb < NKBW; ++kb) mbits[kb] = mnext[t][kb];
+                    if (j + 1 < nsteps) load_masks(p, j + 1, t, mnext[t]);
+                    else load_masks(p + gridDim.x, 0, t, mnext[t]);
                     ok = mbar_wait(&accf[t], (accph >> t) & 1u, a.err);
                     if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
                     accph ^= 1u << t;
