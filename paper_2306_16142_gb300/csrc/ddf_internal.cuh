@@ -48,6 +48,21 @@ NetLayout make_layout(int in_freqs, int width, int L);
 
 struct TcPack;   // tensor-core packed weights (mlp_tc.cu)
 
+// The output layer folded into the fused training forward (loss form, two-output head): labels,
+// the hit count, per-row loss terms, optional per-32-row loss partials, delta_{L-1} ([ld][W] BF16)
+// and the per-32-row head partials ([ld / 32][2W + 2]: G_0 a_L, G_1 a_L, G). delta = null: not folded.
+struct TrainHeadIO {
+    const float* dist_gt = nullptr;
+    const uint8_t* hit_gt = nullptr;
+    const int* n_hit = nullptr;
+    int64_t n_total = 0;
+    float* row_l1 = nullptr;
+    float* row_bce = nullptr;
+    double* lossp = nullptr;
+    __nv_bfloat16* delta = nullptr;
+    float* headpart = nullptr;
+};
+
 // CUDA-event timing of the renderer's launches, by kind.
 enum ProfKind { PROF_QUERY = 0, PROF_SHADE = 1, PROF_RAYGEN = 2, PROF_ACCUM = 3, PROF_KINDS = 4 };
 struct Profiler {
@@ -147,7 +162,8 @@ int tc_fp8_scales(ddf_net_s* net, float* host_out);   // [L][W] static activatio
 // consecutive [ld][W] arrays), the ReLU masks of a_1 .. a_{L-1} ([ld][W / 32] each) and a_L
 // ([ld][W]) from the epilogue. Width <= 256, K0 <= 128.
 int tc_train_forward(const ddf_net_s* net, const float* o, const float* w, int64_t m, const CUtensorMap* map_a0,
-                     const CUtensorMap* map_act, uint32_t* masks, __nv_bfloat16* aL, int64_t ld, cudaStream_t stream);
+                     const CUtensorMap* map_act, uint32_t* masks, __nv_bfloat16* aL, int64_t ld,
+                     const TrainHeadIO* head, cudaStream_t stream);
 // The data-gradient chain of a training step, one persistent launch (widths 128, 256).
 int tc_train_dgrad(const ddf_net_s* net, __nv_bfloat16* deltas, int64_t m, int64_t ld, const uint32_t* masks,
                    cudaStream_t stream);

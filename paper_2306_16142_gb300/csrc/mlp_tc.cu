@@ -86,8 +86,9 @@ struct TcArgs {
     const uint8_t* bias_mn;   // BF16 pair kernel: [L][32 W bytes] bias operand tiles
     uint32_t* train_masks;    // training forward: ReLU masks of a_1 .. a_{L-1}, word (2 kb + group) of row r at
                               // [layer][2 kb + group][ld] (a warp's 32 rows contiguous; nz_bits32 order)
-    __nv_bfloat16* train_aL;  // training forward: a_L, row-major [ld][W]
+    __nv_bfloat16* train_aL;  // training forward: a_L, row-major [ld][W] (when the output layer is not folded in)
     int64_t train_ld;         // training forward: rows of one workspace array
+    TrainHeadIO th;           // training forward: the folded output layer (th.delta set) or none
     const float* f8_emul;   // FP8 epilogue [L]: accumulator multiplier mu_l
 };
 
@@ -906,6 +907,115 @@ __global__ void __launch_bounds__(kThreadsP, 1)
             }
             return true;
         };
+        // TRAIN with the output layer folded in (loss form, Sec. 4.1's two-output head): a_L of tile t
+        // is in its A tile and each group holds its share of y = a_L W_out^T for row r. The outputs,
+        // the per-row loss terms (L1 on hit rows + BCE with logits) and G = dLoss/dy; then warp w
+        // takes rows 32 (w % 4) .. +31 and columns 128 (w / 4) .. +127 of the tile (lane: 4
+        // columns), rows in order: delta_{L-1} = (G W_out) * 1[a_L > 0] to the deltas (256
+        // contiguous bytes per warp row), and the per-32-row partial sums of G a_L (dW_out) and G
+        // (db_out) to the head partials, as the output-layer kernel writes them.
+        auto train_head = [&](int t, const PairInfo& pi, float ty0, float ty1, bool hit, float dgt, int nh) {
+            if (t * kTileM >= pi.rows) return;   // uniform: no row of this tile exists
+            float* part = reinterpret_cast<float*>(smem + a.off_part);   // [tile][group][row][2]
+            float* gs = part + 2 * 2 * kTileM * 2;                       // [tile][row][2]
+            part[((t * 2 + grp) * kTileM + r) * 2] = ty0;
+            part[((t * 2 + grp) * kTileM + r) * 2 + 1] = ty1;
+            epi_bar();
+            const int64_t i = pi.row0 + t * kTileM + r;
+            const bool valid = t * kTileM + r < pi.rows;
+            float gd = 0.f, gl = 0.f, l1v = 0.f, bcev = 0.f;
+            if (valid) {
+                const float* p0 = part + (t * 2 * kTileM + r) * 2;
+                const float* p1 = part + ((t * 2 + 1) * kTileM + r) * 2;
+                const float d = (p0[0] + p1[0]) + head_s[2 * W], z = (p0[1] + p1[1]) + head_s[2 * W + 1];
+                const float inv_h = nh > 0 ? 1.f / (float)nh : 0.f;
+                const float inv_n = 1.f / (float)a.th.n_total;
+                const float lb = hit ? 1.f : 0.f;
+                if (hit) {
+                    const float diff = d - dgt;
+                    l1v = fabsf(diff);
+                    gd = (diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f)) * inv_h;
+                }
+                gl = (1.f / (1.f + expf(-z)) - lb) * inv_n;
+                bcev = fmaxf(z, 0.f) - z * lb + log1pf(expf(-fabsf(z)));
+            }
+            const int q = warp & 3;
+            const int64_t rblk = (pi.row0 + t * kTileM) / 32 + q;   // this warp's 32-row block
+            if (grp == 0) {
+                if (valid) {
+                    a.th.row_l1[i] = l1v;
+                    a.th.row_bce[i] = bcev;
+                }
+                gs[(t * kTileM + r) * 2] = gd;
+                gs[(t * kTileM + r) * 2 + 1] = gl;
+                if (a.th.lossp) {   // the block's loss terms by a fixed butterfly
+                    double s1 = l1v, s2 = bcev;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                    }
+                    if (lane == 0) {
+                        a.th.lossp[2 * rblk] = s1;
+                        a.th.lossp[2 * rblk + 1] = s2;
+                    }
+                }
+            }
+            epi_bar();
+            {
+                constexpr int CP = W / 64;                             // columns per lane: 4 or 2
+                const int c = (W / 2) * grp + CP * lane;               // this lane's first column
+                const uint32_t kbase = act_s + (uint32_t)t * kTile + (uint32_t)(c >> 6) * 16384u + (uint32_t)(c & 7) * 2u;
+                const int ch = (c & 63) >> 3;
+                float wv0[CP], wv1[CP];
+#pragma unroll
+                for (int e = 0; e < CP; ++e) {
+                    wv0[e] = head_s[2 * (c + e)];       // interleaved (W_out[0][c], W_out[1][c])
+                    wv1[e] = head_s[2 * (c + e) + 1];
+                }
+                float cw0[CP], cw1[CP];
+#pragma unroll
+                for (int e = 0; e < CP; ++e) cw0[e] = cw1[e] = 0.f;
+                float sg0 = 0.f, sg1 = 0.f;
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int row = 32 * q + rr;
+                    uint32_t u[2];
+                    if constexpr (CP == 4)
+                        asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(u[0]), "=r"(u[1]) : "r"(kbase + swz(row, ch)) : "memory");
+                    else
+                        asm volatile("ld.shared.b32 %0, [%1];" : "=r"(u[0]) : "r"(kbase + swz(row, ch)) : "memory");
+                    const float2 g = *reinterpret_cast<const float2*>(&gs[(t * kTileM + row) * 2]);
+                    uint32_t dk[CP / 2];
+#pragma unroll
+                    for (int k = 0; k < CP / 2; ++k) {
+                        const float a0 = bf_lo(u[k]), a1 = bf_hi(u[k]);
+                        const float d0 = a0 > 0.f ? fmaf(g.x, wv0[2 * k], g.y * wv1[2 * k]) : 0.f;
+                        const float d1 = a1 > 0.f ? fmaf(g.x, wv0[2 * k + 1], g.y * wv1[2 * k + 1]) : 0.f;
+                        dk[k] = pack_bf16(d0, d1);
+                        fma2p(g.x, g.x, a0, a1, cw0[2 * k], cw0[2 * k + 1], cw0[2 * k], cw0[2 * k + 1]);
+                        fma2p(g.y, g.y, a0, a1, cw1[2 * k], cw1[2 * k + 1], cw1[2 * k], cw1[2 * k + 1]);
+                    }
+                    if (t * kTileM + row < pi.rows) {
+                        __nv_bfloat16* dst = a.th.delta + (pi.row0 + t * kTileM + row) * W + c;
+                        if constexpr (CP == 4) *reinterpret_cast<uint2*>(dst) = make_uint2(dk[0], dk[1]);
+                        else *reinterpret_cast<uint32_t*>(dst) = dk[0];
+                    }
+                    sg0 += g.x;
+                    sg1 += g.y;
+                }
+                float* hp = a.th.headpart + rblk * (2 * W + 2);
+#pragma unroll
+                for (int e = 0; e < CP; e += 2) {
+                    *reinterpret_cast<float2*>(hp + c + e) = make_float2(cw0[e], cw0[e + 1]);
+                    *reinterpret_cast<float2*>(hp + W + c + e) = make_float2(cw1[e], cw1[e + 1]);
+                }
+                if (grp == 0 && lane == 0) {
+                    hp[2 * W] = sg0;
+                    hp[2 * W + 1] = sg1;
+                }
+            }
+            epi_bar();   // the A tile is read: the next pair's encoding may overwrite it
+        };
         float vnext[2][6];
         PairInfo pcur{};
         if ((int64_t)blockIdx.x < npairs) {
@@ -927,9 +1037,23 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     ok = last_layer(pi, pnext, has_next);
                     break;
                 }
+                // the folded output layer's labels of row r of both tiles and the hit count
+                bool lhit[2] = {false, false};
+                float ldist[2] = {0.f, 0.f};
+                int lnh = 0;
                 if (TRAIN && s == L - 1) {
                     load_row(pnext, has_next, 0, vnext[0]);
                     load_row(pnext, has_next, 1, vnext[1]);
+                    if (a.th.delta) {
+                        lnh = *a.th.n_hit;
+#pragma unroll
+                        for (int t = 0; t < 2; ++t)
+                            if (t * kTileM + r < pi.rows) {
+                                const int64_t i = pi.row0 + t * kTileM + r;
+                                lhit[t] = a.th.hit_gt[i] != 0;
+                                ldist[t] = lhit[t] ? a.th.dist_gt[i] : 0.f;
+                            }
+                    }
                 }
                 for (int t = 0; t < 2; ++t) {
                     ok = mbar_wait(&accf[t], (accph >> t) & 1u, a.err);
@@ -938,6 +1062,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     tc_fence_after();
                     const uint32_t tcol = tbase + lane_off + (uint32_t)(t * W) + (uint32_t)(grp * 32);
                     const uint32_t tact = act_s + (uint32_t)t * kTile;
+                    float ty0 = 0.f, ty1 = 0.f;   // folded output layer: this group's share of row r's y
                     // pairs of K-blocks per TMEM wait
 #pragma unroll
                     for (int pass = 0; pass < NKBW / 2; ++pass) {
@@ -977,6 +1102,24 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                                 if (TRAIN && t * kTileM + r < pi.rows)   // ReLU mask of a_{s+1}
                                     a.train_masks[((int64_t)s * (W / 32) + 2 * kb + grp) * a.train_ld + pi.row0 +
                                                   t * kTileM + r] = nz_bits32(pk);
+                            } else if (TRAIN && a.th.delta) {
+                                // a_L = ReLU(acc) rounded to BF16 into the free A tile, and this
+                                // group's share of y = a_L W_out^T
+                                uint32_t pk[16];
+#pragma unroll
+                                for (int q = 0; q < 16; ++q)
+                                    pk[q] = pack_relu(__uint_as_float(raw[i][2 * q]), __uint_as_float(raw[i][2 * q + 1]));
+#pragma unroll
+                                for (int m = 0; m < 4; ++m)
+                                    st_shared_v4(tact + (uint32_t)kb * 16384u + swz(r, grp * 4 + m), pk[4 * m],
+                                                 pk[4 * m + 1], pk[4 * m + 2], pk[4 * m + 3]);
+                                const float2* h2 = reinterpret_cast<const float2*>(head_s);
+#pragma unroll
+                                for (int q = 0; q < 16; ++q) {
+                                    const float4 hh = *reinterpret_cast<const float4*>(&h2[c0 + 2 * q]);
+                                    fma2p(bf_lo(pk[q]), bf_lo(pk[q]), hh.x, hh.y, ty0, ty1, ty0, ty1);
+                                    fma2p(bf_hi(pk[q]), bf_hi(pk[q]), hh.z, hh.w, ty0, ty1, ty0, ty1);
+                                }
                             } else if (TRAIN) {
                                 // a_L = ReLU(acc) rounded to BF16, for the output layer's kernel
                                 if (t * kTileM + r < pi.rows) {
@@ -993,6 +1136,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                             }
                         }
                     }
+                    if (TRAIN && s == L - 1 && a.th.delta) train_head(t, pi, ty0, ty1, lhit[t], ldist[t], lnh);
                     if (TRAIN && s == L - 1 && has_next) encode(t, vnext[t], pnext);
                 }
             }
@@ -2633,7 +2777,8 @@ Layout smem_layout_pair(int W, int K0) {
     const uint32_t stage = (uint32_t)W * 160u;            // weights K-block + bias tile
     const uint32_t ones = 4096u;
     const uint32_t head = ((uint32_t)(2 * W + 2) * 4u + 15u) & ~15u;
-    const uint32_t partb = 128u * 4u * 4u;   // head partial sums (forward) / gradient sums (normals)
+    // the training forward's folded output layer: both groups' partial outputs and G of two tiles
+    const uint32_t partb = 2u * 2u * 128u * 2u * 4u + 2u * 128u * 2u * 4u;
     const uint32_t fixed = act + ones + head + partb + 512u;
     const uint32_t budget = 227u * 1024u - 1024u;
     s.nst = std::max(0, std::min(8, (int)((budget - fixed) / stage)));
@@ -3095,7 +3240,8 @@ int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n
 }
 
 int tc_train_forward(const ddf_net_s* net, const float* o, const float* w, int64_t m, const CUtensorMap* map_a0,
-                     const CUtensorMap* map_act, uint32_t* masks, __nv_bfloat16* aL, int64_t ld, cudaStream_t stream) {
+                     const CUtensorMap* map_act, uint32_t* masks, __nv_bfloat16* aL, int64_t ld,
+                     const TrainHeadIO* head, cudaStream_t stream) {
     const NetLayout& lay = net->lay;
     const TcPack* P = net->tc;
     if (!P || lay.width > 256 || P->K0 > 128 || !P->bias_mn)
@@ -3113,14 +3259,14 @@ int tc_train_forward(const ddf_net_s* net, const float* o, const float* w, int64
     a.train_masks = masks;
     a.train_aL = aL;
     a.train_ld = ld;
+    if (head) a.th = *head;
     return lay.width == 128 ? launch_pair<128, false, true>(net, a, m, false, stream, 0, map_a0, map_act)
                             : launch_pair<256, false, true>(net, a, m, false, stream, 0, map_a0, map_act);
 }
 
 // The data-gradient chain of a training step (mlp_pairb_kernel): deltas [L][ld][W] BF16 row-major
-// (delta_{L-1} from the output layer in, delta_{L-2} .. delta_0 out), the ReLU masks of a_1 ..
-// a_{L-1} ([L - 1][ld][W / 32]) and the per-32-row column sums of delta_0 .. delta_{L-2} into
-// colpart ([L][ld / 32][W]). Rows m .. ld-1 read as zero.
+// (delta_{L-1} from the output layer in, delta_{L-2} .. delta_0 out) and the ReLU masks of a_1 ..
+// a_{L-1} ([L - 1][W / 32][ld], the fused forward's layout). Rows m .. ld-1 read as zero.
 int tc_train_dgrad(const ddf_net_s* net, __nv_bfloat16* deltas, int64_t m, int64_t ld, const uint32_t* masks,
                    cudaStream_t stream) {
     const NetLayout& lay = net->lay;

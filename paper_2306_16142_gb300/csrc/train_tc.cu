@@ -54,9 +54,6 @@ struct TArgs {
     int* err;
 };
 
-__device__ __forceinline__ float bf_lo(uint32_t p) { return __uint_as_float(p << 16); }
-__device__ __forceinline__ float bf_hi(uint32_t p) { return __uint_as_float(p & 0xffff0000u); }
-
 // A warp's 32 x 32 BF16 block lives in 2 KB of shared memory: 32 lines of 64 B, the four 16-byte
 // pieces of line l stored at piece ^ ((l >> 1) & 3), so that eight consecutive lines written at
 // one logical piece, and two consecutive lines read whole, both touch every bank once. Reads go
@@ -1219,8 +1216,10 @@ struct ChunkTargets {
 };
 
 // Encoding and forward GEMMs of rows [0, m): a_1 .. a_L row-major BF16 in ws.act (and the ReLU
-// masks of a_1 .. a_{L-1} when masks is set).
-int tc_forward(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m, bool with_masks, cudaStream_t s) {
+// masks of a_1 .. a_{L-1} when masks is set). head (fused forward only): the output layer folded
+// into the forward's last layer, a_L not stored.
+int tc_forward(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m, bool with_masks, cudaStream_t s,
+               const TrainHeadIO* head = nullptr) {
     const NetLayout& lay = net->lay;
     TcPack* P = net->tc;
     const int W = lay.width, L = lay.L, K0 = P->K0;
@@ -1234,7 +1233,7 @@ int tc_forward(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t
         CUtensorMap m0, ma;
         if ((rc = tmap(&m0, act(0), K0, K0, ld, 1, 128))) return rc;
         if ((rc = tmap(&ma, act(1), W, W, ld, L, 128))) return rc;   // L consecutive [ld][W] arrays
-        return tc_train_forward(net, o, w, m, &m0, &ma, ws.masks, act(L), ld, s);
+        return tc_train_forward(net, o, w, m, &m0, &ma, ws.masks, act(L), ld, head, s);
     }
     tenc_kernel<<<(unsigned)((mp + 127) / 128), 128, 0, s>>>(o, w, m, mp, lay.E, K0, act(0));
     DDF_LAUNCH_CHECK();
@@ -1275,9 +1274,23 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
     auto dl = [&](int l) { return ws.dl + (int64_t)l * ld * W; };   // delta_l
     int rc;
 
-    if ((rc = tc_forward(net, ws, o, w, m, true, s))) return rc;
+    // the output layer folded into the fused forward (loss form, two-output head), or its own kernel
+    const bool fold = K0 <= 128 && W <= 256 && tg.hit_gt && net->head_kind == DDF_HEAD_TWO;
+    TrainHeadIO th;
+    if (fold) {
+        th.dist_gt = tg.dist_gt;
+        th.hit_gt = tg.hit_gt;
+        th.n_hit = tg.n_hit;
+        th.n_total = tg.n_total;
+        th.row_l1 = tg.row_l1;
+        th.row_bce = tg.row_bce;
+        th.lossp = tg.lossp;
+        th.delta = dl(L - 1);
+        th.headpart = ws.headpart;
+    }
+    if ((rc = tc_forward(net, ws, o, w, m, true, s, fold ? &th : nullptr))) return rc;
 
-    {   // output layer, loss and delta_{L-1}
+    if (!fold) {   // output layer, loss and delta_{L-1}
         HeadArgs h{};
         h.aL = act(L);
         h.head = P->head;
