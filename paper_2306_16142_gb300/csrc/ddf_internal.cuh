@@ -163,7 +163,7 @@ int tc_fp8_scales(ddf_net_s* net, float* host_out);   // [L][W] static activatio
 // ([ld][W]) from the epilogue. Width <= 256, K0 <= 128.
 int tc_train_forward(const ddf_net_s* net, const float* o, const float* w, int64_t m, const CUtensorMap* map_a0,
                      const CUtensorMap* map_act, uint32_t* masks, __nv_bfloat16* aL, int64_t ld,
-                     const TrainHeadIO* head, cudaStream_t stream);
+                     const TrainHeadIO* head, bool pdl, cudaStream_t stream);
 // The data-gradient chain of a training step, one persistent launch (widths 128, 256).
 int tc_train_dgrad(const ddf_net_s* net, __nv_bfloat16* deltas, int64_t m, int64_t ld, const uint32_t* masks,
                    cudaStream_t stream);

@@ -598,6 +598,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
     mlp_pair_kernel(const __grid_constant__ CUtensorMap mapF, const __grid_constant__ CUtensorMap mapA0,
                     const __grid_constant__ CUtensorMap mapAct, const TcArgs a) {
     static_assert(!(GRP && TRAIN), "grouped launches are queries");
+    pdl_trigger();
     constexpr int NKBW = W / 64;
     constexpr uint32_t kWBytes = (uint32_t)W * 128u;   // one 64-wide K-block of the weights
     constexpr uint32_t kBBytes = (uint32_t)W * 32u;    // one layer's bias tile
@@ -1045,6 +1046,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     load_row(pnext, has_next, 0, vnext[0]);
                     load_row(pnext, has_next, 1, vnext[1]);
                     if (a.th.delta) {
+                        pdl_wait();   // a programmatic dependent of the hit count
                         lnh = *a.th.n_hit;
 #pragma unroll
                         for (int t = 0; t < 2; ++t)
@@ -1534,6 +1536,7 @@ template <int W>
 __global__ void __launch_bounds__(kThreadsP, 1)
     mlp_pairb_kernel(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapD,
                      const TcArgs a) {
+    pdl_trigger();
     constexpr int NKBW = W / 64;
     constexpr uint32_t kStage = (uint32_t)W * 128u;   // one 64-wide K-block of W_l^T
     constexpr uint32_t kTile = (uint32_t)NKBW * 16384u;
@@ -1613,6 +1616,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                     tma_load_3d(act + (size_t)t * kTile + (size_t)kb * 16384u, &mapD, &ain[t], kb * 64,
                                 (int)(pp * 2 * kTileM + t * kTileM), L - 1);
             };
+            pdl_wait();   // a programmatic dependent of the forward: the deltas and masks are written
             if ((int64_t)blockIdx.x < npairs) load_in(blockIdx.x);
             bool ok = true, first = true;
             const uint32_t act_t = su32(act) + (uint32_t)t * kTile, wst_s = su32(wst);
@@ -1698,6 +1702,7 @@ __global__ void __launch_bounds__(kThreadsP, 1)
                 mb[kb] = valid ? a.train_masks[((int64_t)(L - 2 - jj) * (W / 32) + 2 * kb + grp) * ld + row] : 0u;
         };
         uint32_t mnext[2][NKBW];   // each tile's masks of its next step, fetched one step ahead
+        pdl_wait();
         load_masks(blockIdx.x, 0, 0, mnext[0]);
         load_masks(blockIdx.x, 0, 1, mnext[1]);
         for (int64_t p = blockIdx.x; p < npairs && ok; p += gridDim.x) {
@@ -2657,6 +2662,7 @@ __device__ __forceinline__ float adam_one(const AdamPack& a, int64_t i) {
 }
 
 __global__ void __launch_bounds__(256) adam_pack_kernel(const AdamPack a) {
+    pdl_wait();   // a programmatic dependent of the last bias-gradient launch
     const NetLayout& lay = a.lay;
     const int W = lay.width, L = lay.L;
     const int tid = threadIdx.x;
@@ -2807,7 +2813,7 @@ int ensure_pair_attr() {
 template <int W, bool GRP, bool TRAIN = false>
 int launch_pair(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_count, cudaStream_t stream,
                 int grid_override = 0, const CUtensorMap* mapA0 = nullptr, const CUtensorMap* mapAct = nullptr,
-                int nst_override = 0) {
+                int nst_override = 0, bool pdl = false) {
     const TcPack* P = net->tc;
     TcArgs a = base;
     const Layout s = smem_layout_pair(W, a.K0);
@@ -2825,9 +2831,8 @@ int launch_pair(const ddf_net_s* net, const TcArgs& base, int64_t n, bool use_co
     if (grid <= 0) return DDF_OK;
     int rc = ensure_pair_attr<W, GRP, TRAIN>();
     if (rc) return rc;
-    mlp_pair_kernel<W, GRP, TRAIN><<<grid, kThreadsP, s.total, stream>>>(
-        P->map_fwd, mapA0 ? *mapA0 : P->map_fwd, mapAct ? *mapAct : P->map_fwd, a);
-    DDF_LAUNCH_CHECK();
+    DDF_CUDA_TRY(launch_k(mlp_pair_kernel<W, GRP, TRAIN>, dim3(grid), dim3(kThreadsP), s.total, stream, pdl,
+                          P->map_fwd, mapA0 ? *mapA0 : P->map_fwd, mapAct ? *mapAct : P->map_fwd, a));
     return DDF_OK;
 }
 
@@ -3169,8 +3174,8 @@ int tc_adam_pack(ddf_net_s* net, const float* grad, const ddf_adam* opt, float c
     a.n = n;
     a.n_hit = n_hit;
     a.loss = loss;
-    adam_pack_kernel<<<(unsigned)(a.ntiles + a.nbias + (loss ? 1 : 0)), 256, 0, stream>>>(a);
-    DDF_LAUNCH_CHECK();
+    DDF_CUDA_TRY(launch_k(adam_pack_kernel, dim3((unsigned)(a.ntiles + a.nbias + (loss ? 1 : 0))), dim3(256), 0, stream,
+                          true, a));
     return DDF_OK;
 }
 
@@ -3241,7 +3246,7 @@ int mlp_tc_query(const ddf_net_s* net, const float* o, const float* w, int64_t n
 
 int tc_train_forward(const ddf_net_s* net, const float* o, const float* w, int64_t m, const CUtensorMap* map_a0,
                      const CUtensorMap* map_act, uint32_t* masks, __nv_bfloat16* aL, int64_t ld,
-                     const TrainHeadIO* head, cudaStream_t stream) {
+                     const TrainHeadIO* head, bool pdl, cudaStream_t stream) {
     const NetLayout& lay = net->lay;
     const TcPack* P = net->tc;
     if (!P || lay.width > 256 || P->K0 > 128 || !P->bias_mn)
@@ -3260,8 +3265,8 @@ int tc_train_forward(const ddf_net_s* net, const float* o, const float* w, int64
     a.train_aL = aL;
     a.train_ld = ld;
     if (head) a.th = *head;
-    return lay.width == 128 ? launch_pair<128, false, true>(net, a, m, false, stream, 0, map_a0, map_act)
-                            : launch_pair<256, false, true>(net, a, m, false, stream, 0, map_a0, map_act);
+    return lay.width == 128 ? launch_pair<128, false, true>(net, a, m, false, stream, 0, map_a0, map_act, 0, pdl)
+                            : launch_pair<256, false, true>(net, a, m, false, stream, 0, map_a0, map_act, 0, pdl);
 }
 
 // The data-gradient chain of a training step (mlp_pairb_kernel): deltas [L][ld][W] BF16 row-major
@@ -3303,14 +3308,16 @@ int tc_train_dgrad(const ddf_net_s* net, __nv_bfloat16* deltas, int64_t m, int64
             DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_pairb_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
             attr = true;
         }
-        mlp_pairb_kernel<128><<<grid, kThreadsP, s.total, stream>>>(P->map_bwd, mapD, a);
+        DDF_CUDA_TRY(launch_k(mlp_pairb_kernel<128>, dim3(grid), dim3(kThreadsP), s.total, stream, true, P->map_bwd,
+                              mapD, a));
     } else {
         static bool attr = false;
         if (!attr) {
             DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_pairb_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
             attr = true;
         }
-        mlp_pairb_kernel<256><<<grid, kThreadsP, s.total, stream>>>(P->map_bwd, mapD, a);
+        DDF_CUDA_TRY(launch_k(mlp_pairb_kernel<256>, dim3(grid), dim3(kThreadsP), s.total, stream, true, P->map_bwd,
+                              mapD, a));
     }
     DDF_LAUNCH_CHECK();
     return DDF_OK;

@@ -175,6 +175,7 @@ __global__ void gather_cot_kernel(const float* __restrict__ gd, const float* __r
 
 // Number of labelled hit rays (single block, fixed order).
 __global__ void count_hits_kernel(const uint8_t* __restrict__ h, int64_t n, int* out) {
+    pdl_trigger();   // the training forward reads the count only in its last layer
     int c = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         c += h[i] ? 1 : 0;

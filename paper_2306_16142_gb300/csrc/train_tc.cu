@@ -673,6 +673,8 @@ __global__ void wsum_kernel(const float4* __restrict__ part, int ksplit, int M, 
 // memory, and each warp adds whole 32-column row segments to the gradient.
 __global__ void wsum_all_kernel(const float4* __restrict__ part, int ks, int KM, int K0, NetLayout lay,
                                 float* __restrict__ grad) {
+    pdl_trigger();
+    pdl_wait();
     const int l = blockIdx.y, W = lay.width;
     const int N = l == 0 ? K0 : W, nch = N / 32;
     const int u = blockIdx.x;   // (M-tile, lane quadrant, 32-column chunk) of the fragment order
@@ -715,6 +717,8 @@ constexpr int kBGroups = 16;
 __global__ void bgrad_partial_kernel(const float* __restrict__ lpart, int64_t lrows, int64_t lstride,
                                      const float* __restrict__ headpart, int64_t hrows, NetLayout lay,
                                      float* __restrict__ bpart) {
+    pdl_trigger();
+    pdl_wait();
     const int l = blockIdx.y, g = blockIdx.z, W = lay.width;
     const int c = blockIdx.x * 32 + threadIdx.x;
     const int ncol = l < lay.L ? W : 2 * W + 2;
@@ -737,6 +741,8 @@ __global__ void bgrad_partial_kernel(const float* __restrict__ lpart, int64_t lr
 }
 
 __global__ void bgrad_final_kernel(const float* __restrict__ bpart, NetLayout lay, float* __restrict__ grad) {
+    pdl_trigger();
+    pdl_wait();
     const int l = blockIdx.y, W = lay.width;
     const int c = blockIdx.x * 32 + threadIdx.x;
     const int ncol = l < lay.L ? W : 2 * W + 2;
@@ -1211,6 +1217,7 @@ struct ChunkTargets {
     float* row_l1 = nullptr;
     float* row_bce = nullptr;
     double* lossp = nullptr;   // per-32-row loss partials of the chunk (optional)
+    bool pdl_forward = false;  // the forward may launch as a programmatic dependent of the hit count
     const float* gd = nullptr;
     const float* gl = nullptr;
 };
@@ -1219,7 +1226,7 @@ struct ChunkTargets {
 // masks of a_1 .. a_{L-1} when masks is set). head (fused forward only): the output layer folded
 // into the forward's last layer, a_L not stored.
 int tc_forward(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m, bool with_masks, cudaStream_t s,
-               const TrainHeadIO* head = nullptr) {
+               const TrainHeadIO* head = nullptr, bool pdl = false) {
     const NetLayout& lay = net->lay;
     TcPack* P = net->tc;
     const int W = lay.width, L = lay.L, K0 = P->K0;
@@ -1233,7 +1240,7 @@ int tc_forward(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t
         CUtensorMap m0, ma;
         if ((rc = tmap(&m0, act(0), K0, K0, ld, 1, 128))) return rc;
         if ((rc = tmap(&ma, act(1), W, W, ld, L, 128))) return rc;   // L consecutive [ld][W] arrays
-        return tc_train_forward(net, o, w, m, &m0, &ma, ws.masks, act(L), ld, head, s);
+        return tc_train_forward(net, o, w, m, &m0, &ma, ws.masks, act(L), ld, head, pdl, s);
     }
     tenc_kernel<<<(unsigned)((mp + 127) / 128), 128, 0, s>>>(o, w, m, mp, lay.E, K0, act(0));
     DDF_LAUNCH_CHECK();
@@ -1288,7 +1295,7 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
         th.delta = dl(L - 1);
         th.headpart = ws.headpart;
     }
-    if ((rc = tc_forward(net, ws, o, w, m, true, s, fold ? &th : nullptr))) return rc;
+    if ((rc = tc_forward(net, ws, o, w, m, true, s, fold ? &th : nullptr, fold && tg.pdl_forward))) return rc;
 
     if (!fold) {   // output layer, loss and delta_{L-1}
         HeadArgs h{};
@@ -1328,9 +1335,8 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
         if ((rc = tc_train_dgrad(net, ws.dl, m, ld, ws.masks, s))) return rc;
         if ((rc = launch_wgrad_all(net, ws.dl, act(0), act(1), m, ld, ws.wpart, ws.bsum, &ks, s))) return rc;
         const int KM = std::max(K0, W);
-        wsum_all_kernel<<<dim3((unsigned)((W / 32) * (KM / 32)), (unsigned)L), dim3(32, 8), 0, s>>>(
-            (const float4*)ws.wpart, ks, KM, K0, lay, grad);
-        DDF_LAUNCH_CHECK();
+        DDF_CUDA_TRY(launch_k(wsum_all_kernel, dim3((unsigned)((W / 32) * (KM / 32)), (unsigned)L), dim3(32, 8), 0, s,
+                              true, (const float4*)ws.wpart, ks, KM, K0, lay, grad));
     }
     for (int l = L - 1; l >= 0; --l) {
         const int K = l == 0 ? K0 : W;
@@ -1401,10 +1407,11 @@ int tc_chunk(ddf_net_s* net, TcWs& ws, const float* o, const float* w, int64_t m
     // per-32-row column sums of the head and the data-gradient GEMMs otherwise
     const unsigned gx = (unsigned)((2 * W + 2 + 31) / 32);
     const int64_t lrows = chain ? (int64_t)ks * (2048 / W) : mp / 32;
-    bgrad_partial_kernel<<<dim3(gx, (unsigned)(L + 1), kBGroups), dim3(32, 8), 0, s>>>(
-        chain ? ws.bsum : ws.colpart, lrows, chain ? lrows * W : (ld / 32) * W, ws.headpart, mp / 32, lay, ws.bpart);
-    bgrad_final_kernel<<<dim3(gx, (unsigned)(L + 1)), 32, 0, s>>>(ws.bpart, lay, grad);
-    DDF_LAUNCH_CHECK();
+    DDF_CUDA_TRY(launch_k(bgrad_partial_kernel, dim3(gx, (unsigned)(L + 1), kBGroups), dim3(32, 8), 0, s, true,
+                          (const float*)(chain ? ws.bsum : ws.colpart), lrows, chain ? lrows * W : (ld / 32) * W,
+                          (const float*)ws.headpart, (int64_t)(mp / 32), lay, ws.bpart));
+    DDF_CUDA_TRY(launch_k(bgrad_final_kernel, dim3(gx, (unsigned)(L + 1)), dim3(32), 0, s, true, (const float*)ws.bpart,
+                          lay, grad));
     return DDF_OK;
 }
 
@@ -1475,6 +1482,7 @@ int tct_train_step(ddf_net_s* net, const float* o, const float* w, const float* 
         tg.row_l1 = ws.row_l1 + r0;
         tg.row_bce = ws.row_bce + r0;
         tg.lossp = fused_tail ? ws.loss_part + 2 * (r0 / 32) : nullptr;
+        tg.pdl_forward = r0 == 0;   // later chunks' forwards overwrite what the previous chunk reads
         if ((rc = tc_chunk(net, ws, o + 3 * r0, w + 3 * r0, m, tg, ws.grad, nullptr, s))) return rc;
     }
     if (fused_tail) {
