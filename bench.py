@@ -58,11 +58,13 @@ def bwd_flops(E, W, L):
     return 2.0 * ((L - 1) * W * W + W * E)
 
 
-# ncu-measured DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the BF16 query
-# kernels of one 512 x 512 x 64 spp render of the seeded network (the 4 mlp_pair_kernel<256>
-# forward and 3 mlp_pairn_kernel<256> normals launches; profiles/bf16_query_render512x512.md); to
-# be measured again whenever those kernels change.
-QUERY_DRAM_BYTES_PER_RENDER = 759.5e6
+# ncu-measured DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per row of the BF16
+# query kernels, captured on one bounce-1 launch each of the 512 x 512 x 32 spp render (whose rays
+# exceed the L2): mlp_pair_kernel<256> forward over 8,388,608 rows, mlp_pairn_kernel<256> normals
+# over 1,265,231 hit rows (profiles/bf16_query_render512x512.md). A render's traffic is these
+# times its rows; to be measured again whenever those kernels change.
+QUERY_DRAM_BYTES_PER_FWD_ROW = (203441920 + 51336960) / 8388608
+QUERY_DRAM_BYTES_PER_NRM_ROW = (40118784 + 855296) / 1265231
 
 
 def load_peaks():
@@ -384,14 +386,17 @@ def main():
     ap.add_argument("--error-rays", type=int, default=1 << 20, help="rays of each query-error subset")
     ap.add_argument("--no-train", action="store_true", help="skip training the knot network and its rows")
     ap.add_argument("--no-rows", action="store_true", help="skip the labelling / training / grouped rows")
-    ap.add_argument("--size", default="full", choices=["full", "small"],
-                    help="small: 512 x 512 x 8 spp (2^21 paths) for profiler captures")
+    ap.add_argument("--size", default="full", choices=["full", "small", "medium"],
+                    help="small: 512 x 512 x 8 spp (2^21 paths) for profiler captures; medium: 512 x 512 x 32 spp "
+                         "(2^23 paths: each bounce-1 launch's rays exceed the L2) for DRAM-traffic captures")
     ap.add_argument("--row", default=None, choices=["label", "sampler", "pov", "aov", "udf", "mesh_render", "train",
                                                    "grouped", "w512", "large"],
                     help="run only this row's workload (for profiler captures) and print it")
     args = ap.parse_args()
     if args.size == "small":
         WORKLOAD["spp"] = 8
+    elif args.size == "medium":
+        WORKLOAD["spp"] = 32
     if args.impl == "reference":
         return run_reference(args)
 
@@ -478,9 +483,12 @@ def main():
 
     # ---- dominant kernel roofline: the field query
     roof = query_roofline(stats, prof, ms, E, w["hidden"], w["layers"], prec, peaks, peak_src, meas, args.steps)
-    if prec == "bf16" and args.size == "full" and QUERY_DRAM_BYTES_PER_RENDER is not None:
-        roof["traffic"] = QUERY_DRAM_BYTES_PER_RENDER / w["bounces"]
-        roof["traffic_unit"] = "bytes per bounce query (forward + normals launches)"
+    if prec == "bf16":
+        # forward rows: every bounce's live rays; normal rows: the hits, i.e. the next bounce's rays
+        render_bytes = QUERY_DRAM_BYTES_PER_FWD_ROW * sum(stats) + QUERY_DRAM_BYTES_PER_NRM_ROW * sum(stats[1:])
+        roof["traffic"] = render_bytes / w["bounces"]
+        roof["traffic_unit"] = ("bytes per bounce query (forward + normals launches), the per-row DRAM bytes of "
+                                "one ncu capture of each kernel times this render's rows")
 
     # ---- wavefront kernels against HBM: algorithmic bytes per launch / measured launch time
     B = w["bounces"]
