@@ -19,6 +19,14 @@ constexpr int TC = 8;     // columns per thread
 
 enum { EPI_FWD = 0, EPI_BWD = 1, EPI_PLAIN = 2 };
 
+// (dx, dy) = (a bx + cx, a by + cy): one packed FP32x2 FMA, each lane rounded as fmaf.
+__device__ __forceinline__ void ffma2(float a, float bx, float by, float& cx, float& cy) {
+    asm("{\n .reg .b64 ra, rb, rc;\n mov.b64 ra, {%2, %2};\n mov.b64 rb, {%3, %4};\n"
+        " mov.b64 rc, {%0, %1};\n fma.rn.f32x2 rc, ra, rb, rc;\n mov.b64 {%0, %1}, rc;\n}\n"
+        : "+f"(cx), "+f"(cy)
+        : "f"(a), "f"(bx), "f"(by));
+}
+
 struct MlpArgs {
     NetLayout lay;
     const float* W;    // masters, blob layout
@@ -35,7 +43,10 @@ struct MlpArgs {
 };
 
 // out[N][MT] = epi(sum_k in[k][MT] * B[k][n]) with B row-major K x N at Bg (row stride ldb).
-// NC output columns per chunk; thread (tx, ty) owns rows ty TR .. +TR-1 and columns tx 8 .. +7.
+// NC output columns per chunk; thread (tx, ty) owns rows ty TR .. +TR-1 and the columns
+// [4 tx, 4 tx + 4) and [NC / 2 + 4 tx, NC / 2 + 4 tx + 4) of the chunk, so that a warp's two
+// 128-bit weight loads per reduction step each read 512 contiguous bytes (no bank conflicts); the
+// products are packed FP32x2 FMAs (each lane an IEEE FMA, as fmaf).
 template <int MT, int EPI, int NC>
 __device__ void gemm_layer(const float* __restrict__ Bg, int ldb, int K, int N,
                            const float* __restrict__ in, float* __restrict__ out,
@@ -86,6 +97,7 @@ __device__ void gemm_layer(const float* __restrict__ Bg, int ldb, int K, int N,
             __syncthreads();
             if (k0 + KC < K) load_chunk(k0 + KC);
             const int kn = min(KC, K - k0);
+#pragma unroll 4
             for (int kk = 0; kk < kn; ++kk) {
                 float a[TR], b[TC];
                 const float* ap = in + (k0 + kk) * MT + ty * TR;
@@ -101,21 +113,22 @@ __device__ void gemm_layer(const float* __restrict__ Bg, int ldb, int K, int N,
                     const float2 v = *reinterpret_cast<const float2*>(ap);
                     a[0] = v.x; a[1] = v.y;
                 }
-                const float4 b0 = *reinterpret_cast<const float4*>(Ws + kk * NC + tx * TC);
-                const float4 b1 = *reinterpret_cast<const float4*>(Ws + kk * NC + tx * TC + 4);
+                const float4 b0 = *reinterpret_cast<const float4*>(Ws + kk * NC + tx * 4);
+                const float4 b1 = *reinterpret_cast<const float4*>(Ws + kk * NC + NC / 2 + tx * 4);
                 b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
                 b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
 #pragma unroll
                 for (int i = 0; i < TR; ++i)
 #pragma unroll
-                    for (int j = 0; j < TC; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                    for (int j = 0; j < TC; j += 2)
+                        ffma2(a[i], b[j], b[j + 1], acc[i][j], acc[i][j + 1]);
             }
         }
         // epilogue
         const int r0 = ty * TR;
 #pragma unroll
         for (int j = 0; j < TC; ++j) {
-            const int nn = n0 + tx * TC + j;
+            const int nn = n0 + (j < 4 ? tx * 4 + j : NC / 2 + tx * 4 + (j - 4));
             if (nn >= N) continue;
             float v[TR];
             if constexpr (EPI == EPI_FWD) {
