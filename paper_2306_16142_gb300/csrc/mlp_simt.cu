@@ -19,6 +19,20 @@ constexpr int TC = 8;     // columns per thread
 
 enum { EPI_FWD = 0, EPI_BWD = 1, EPI_PLAIN = 2 };
 
+// Asynchronous global -> shared copies (16 bytes, or 4 bytes with src_bytes 0 or 4; the bytes
+// beyond src_bytes are zero-filled).
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // (dx, dy) = (a bx + cx, a by + cy): one packed FP32x2 FMA, each lane rounded as fmaf.
 __device__ __forceinline__ void ffma2(float a, float bx, float by, float& cx, float& cy) {
     asm("{\n .reg .b64 ra, rb, rc;\n mov.b64 ra, {%2, %2};\n mov.b64 rb, {%3, %4};\n"
@@ -47,7 +61,8 @@ struct MlpArgs {
 // [4 tx, 4 tx + 4) and [NC / 2 + 4 tx, NC / 2 + 4 tx + 4) of the chunk, so that a warp's two
 // 128-bit weight loads per reduction step each read 512 contiguous bytes (no bank conflicts); the
 // products are packed FP32x2 FMAs (each lane an IEEE FMA, as fmaf).
-template <int MT, int EPI, int NC>
+// NB chunk buffers at Ws: 2 = the next chunk's copies overlap this chunk's products, 1 = in turn.
+template <int MT, int EPI, int NC, int NB>
 __device__ void gemm_layer(const float* __restrict__ Bg, int ldb, int K, int N,
                            const float* __restrict__ in, float* __restrict__ out,
                            float* __restrict__ Ws, const float* __restrict__ bias,
@@ -65,37 +80,39 @@ __device__ void gemm_layer(const float* __restrict__ Bg, int ldb, int K, int N,
         for (int i = 0; i < TR; ++i)
 #pragma unroll
             for (int j = 0; j < TC; ++j) acc[i][j] = 0.f;
-        float pre[4 * NQ];
-        auto load_chunk = [&](int k0) {
+        // the weight chunk of rows [k0, k0 + KC) into dst, by asynchronous copies (zero outside B)
+        auto issue_chunk = [&](int k0, float* dst) {
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 const int idx4 = tid + kThreads * q;
                 const int kk = idx4 / (NC / 4), c = n0 + (idx4 % (NC / 4)) * 4;
                 const int k = k0 + kk;
+                float* d = dst + kk * NC + (idx4 % (NC / 4)) * 4;
                 if (k < K && vec && c + 3 < N) {
-                    const float4 v = *reinterpret_cast<const float4*>(Bg + (int64_t)k * ldb + c);
-                    pre[4 * q + 0] = v.x;
-                    pre[4 * q + 1] = v.y;
-                    pre[4 * q + 2] = v.z;
-                    pre[4 * q + 3] = v.w;
+                    cp_async16(d, Bg + (int64_t)k * ldb + c);
                 } else {
 #pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        pre[4 * q + e] = (k < K && c + e < N) ? Bg[(int64_t)k * ldb + c + e] : 0.f;
+                    for (int e = 0; e < 4; ++e) {
+                        const bool in = k < K && c + e < N;
+                        cp_async4(d + e, in ? Bg + (int64_t)k * ldb + c + e : Bg, in ? 4u : 0u);
+                    }
                 }
             }
+            cp_async_commit();
         };
-        load_chunk(0);
-        for (int k0 = 0; k0 < K; k0 += KC) {
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const int idx4 = tid + kThreads * q;
-                *reinterpret_cast<float4*>(Ws + (idx4 / (NC / 4)) * NC + (idx4 % (NC / 4)) * 4) =
-                    make_float4(pre[4 * q], pre[4 * q + 1], pre[4 * q + 2], pre[4 * q + 3]);
+        __syncthreads();   // every thread is done with the chunk buffers of the previous column block
+        if (NB == 2) issue_chunk(0, Ws);
+        int chunk = 0;
+        for (int k0 = 0; k0 < K; k0 += KC, ++chunk) {
+            if (NB == 1) {   // the previous chunk's products are done: refill the one buffer
+                if (k0 > 0) __syncthreads();
+                issue_chunk(k0, Ws);
             }
+            // chunk `chunk` has landed, and every thread is done with the other buffer
+            cp_async_wait_all();
             __syncthreads();
-            if (k0 + KC < K) load_chunk(k0 + KC);
+            const float* Wc = NB == 2 ? Ws + (chunk & 1) * KC * NC : Ws;
+            if (NB == 2 && k0 + KC < K) issue_chunk(k0 + KC, Ws + ((chunk + 1) & 1) * KC * NC);
             const int kn = min(KC, K - k0);
 #pragma unroll 4
             for (int kk = 0; kk < kn; ++kk) {
@@ -113,8 +130,8 @@ __device__ void gemm_layer(const float* __restrict__ Bg, int ldb, int K, int N,
                     const float2 v = *reinterpret_cast<const float2*>(ap);
                     a[0] = v.x; a[1] = v.y;
                 }
-                const float4 b0 = *reinterpret_cast<const float4*>(Ws + kk * NC + tx * 4);
-                const float4 b1 = *reinterpret_cast<const float4*>(Ws + kk * NC + NC / 2 + tx * 4);
+                const float4 b0 = *reinterpret_cast<const float4*>(Wc + kk * NC + tx * 4);
+                const float4 b1 = *reinterpret_cast<const float4*>(Wc + kk * NC + NC / 2 + tx * 4);
                 b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
                 b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
 #pragma unroll
@@ -162,7 +179,7 @@ __device__ void gemm_layer(const float* __restrict__ Bg, int ldb, int K, int N,
     __syncthreads();
 }
 
-template <int MT, int NC>
+template <int MT, int NC, int NB>
 __global__ void __launch_bounds__(kThreads, 1) mlp_fp32_kernel(const MlpArgs a) {
     extern __shared__ __align__(16) float smem[];
     constexpr int MW = MT / 32;
@@ -171,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fp32_kernel(const MlpArgs a) 
     float* bufA = smem;
     float* bufB = bufA + a.kmax * MT;
     float* Ws = bufB + a.kmax * MT;
-    uint32_t* masks = reinterpret_cast<uint32_t*>(Ws + KC * NC);
+    uint32_t* masks = reinterpret_cast<uint32_t*>(Ws + NB * KC * NC);   // after the chunk buffers
     float* rowv = reinterpret_cast<float*>(masks + L * W * MW);   // [6][MT]
     float* red = rowv + 6 * MT;                                     // [kThreads / MT][2][MT]
     int* flag = reinterpret_cast<int*>(red + 2 * kThreads);
@@ -202,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fp32_kernel(const MlpArgs a) 
         float* nxt = bufB;
         int K = E;
         for (int l = 0; l < L; ++l) {
-            gemm_layer<MT, EPI_FWD, NC>(a.Wt + lay.w_off[l], W, K, W, cur, nxt, Ws, a.W + lay.b_off[l],
+            gemm_layer<MT, EPI_FWD, NC, NB>(a.Wt + lay.w_off[l], W, K, W, cur, nxt, Ws, a.W + lay.b_off[l],
                                     masks + l * W * MW);
             float* t = cur; cur = nxt; nxt = t;
             K = W;
@@ -257,11 +274,11 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fp32_kernel(const MlpArgs a) 
         }
         __syncthreads();
         for (int l = L - 1; l >= 1; --l) {
-            gemm_layer<MT, EPI_BWD, NC>(a.W + lay.w_off[l], W, W, W, cur, nxt, Ws, nullptr,
+            gemm_layer<MT, EPI_BWD, NC, NB>(a.W + lay.w_off[l], W, W, W, cur, nxt, Ws, nullptr,
                                     masks + (l - 1) * W * MW);
             float* t = cur; cur = nxt; nxt = t;
         }
-        gemm_layer<MT, EPI_PLAIN, NC>(a.W + lay.w_off[0], E, W, E, cur, nxt, Ws, nullptr, nullptr);
+        gemm_layer<MT, EPI_PLAIN, NC, NB>(a.W + lay.w_off[0], E, W, E, cur, nxt, Ws, nullptr, nullptr);
         if (tid < rows && flag[tid]) {
             float v[6];
 #pragma unroll
@@ -282,18 +299,22 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fp32_kernel(const MlpArgs a) 
 }
 
 template <int MT, int NC>
-size_t smem_bytes(const NetLayout& lay, int kmax) {
-    return sizeof(float) * (2 * (size_t)kmax * MT + KC * NC) +
+size_t smem_bytes(const NetLayout& lay, int kmax, int nb) {
+    return sizeof(float) * (2 * (size_t)kmax * MT + (size_t)nb * KC * NC) +
            sizeof(uint32_t) * (size_t)lay.L * lay.width * (MT / 32) + sizeof(float) * 6 * MT +
            sizeof(float) * 2 * kThreads + sizeof(int) * kThreads;
 }
 
 template <int MT, int NC>
 int launch(const MlpArgs& a, int64_t n, cudaStream_t stream) {
-    const size_t sm = smem_bytes<MT, NC>(a.lay, a.kmax);
+    // two weight-chunk buffers where they fit (deep networks at width 256 get one)
+    const int nb = smem_bytes<MT, NC>(a.lay, a.kmax, 2) <= 227 * 1024 ? 2 : 1;
+    const size_t sm = smem_bytes<MT, NC>(a.lay, a.kmax, nb);
     static bool attr_done = false;
     if (!attr_done) {
-        DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_fp32_kernel<MT, NC>,
+        DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_fp32_kernel<MT, NC, 1>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        DDF_CUDA_TRY(cudaFuncSetAttribute(mlp_fp32_kernel<MT, NC, 2>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         attr_done = true;
     }
@@ -302,7 +323,10 @@ int launch(const MlpArgs& a, int64_t n, cudaStream_t stream) {
     int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms());
     if (a.d_count) grid = num_sms();
     if (grid <= 0) return DDF_OK;
-    mlp_fp32_kernel<MT, NC><<<grid, kThreads, sm, stream>>>(a);
+    if (nb == 2)
+        mlp_fp32_kernel<MT, NC, 2><<<grid, kThreads, sm, stream>>>(a);
+    else
+        mlp_fp32_kernel<MT, NC, 1><<<grid, kThreads, sm, stream>>>(a);
     DDF_LAUNCH_CHECK();
     return DDF_OK;
 }

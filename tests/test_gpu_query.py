@@ -53,6 +53,20 @@ def test_fp32_query_parity(lib, name, n):
     _check_fp32(_gpu(lib, name, o, w), _oracle(name, o, w))
 
 
+def test_fp32_query_deep_network(lib):
+    """16 hidden layers at width 256: the FP32 kernel's shared memory then holds one weight-chunk
+    buffer instead of two (the chunks are copied and multiplied in turn); same parity."""
+    from ddf_synth import init_weights
+    F, W, L = 12, 256, 16
+    blob = init_weights(F, W, L, seed=6)
+    o, w = rays_in_ball(1000, seed=61)
+    net = lib.DDFNet(F, W, L, blob, "fp32")
+    out = net.query(torch.from_numpy(o).cuda(), torch.from_numpy(w).cuda(), normals=True)
+    torch.cuda.synchronize()
+    g = {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+    _check_fp32(g, omlp.query(omlp.unpack(blob, F, W, L), o, w, F, with_normal=True))
+
+
 def test_fp32_query_empty(lib):
     F, W, L, _, _ = NETS["tiny_6x64x4"]
     net = lib.DDFNet(F, W, L, net_weights("tiny_6x64x4"))
