@@ -14,26 +14,41 @@
 namespace ddf {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, kGemmThreads = 256;
+constexpr int BM = 128, BN = 128, BK = 16, kGemmThreads = 256;
 
 enum { G_STORE = 0, G_BIAS_RELU = 1, G_BIAS = 2, G_MASK = 3, G_ACCUM = 4 };
 
+// (cx, cy) += (a bx, a by): one packed FP32x2 FMA, each lane rounded as fmaf.
+__device__ __forceinline__ void gffma2(float a, float bx, float by, float& cx, float& cy) {
+    asm("{\n .reg .b64 ra, rb, rc;\n mov.b64 ra, {%2, %2};\n mov.b64 rb, {%3, %4};\n"
+        " mov.b64 rc, {%0, %1};\n fma.rn.f32x2 rc, ra, rb, rc;\n mov.b64 {%0, %1}, rc;\n}\n"
+        : "+f"(cx), "+f"(cy)
+        : "f"(a), "f"(bx), "f"(by));
+}
+
 // C[i][j] (ldc) = epi(sum_k A(i,k) B(k,j)), A(i,k) = A[i*sai + k*sak], B(k,j) = B[k*sbk + j*sbj].
-__global__ void __launch_bounds__(kGemmThreads) gemm_kernel(
+// 128 x 128 tiles; thread (tx, ty) holds the 8 x 8 products of rows {4 ty + x, 64 + 4 ty + x} and
+// columns {4 tx + y, 64 + 4 tx + y} (x, y < 4), so that a warp's 128-bit shared loads of a
+// reduction step are broadcasts (A) or 256 contiguous bytes (B); every product is an IEEE FMA in
+// k order, as with scalar fmaf.
+__global__ void __launch_bounds__(kGemmThreads, 2) gemm_kernel(
     int M, int N, int K, const float* __restrict__ A, int64_t sai, int64_t sak,
     const float* __restrict__ Bm, int64_t sbk, int64_t sbj, float* __restrict__ C, int64_t ldc,
     int epi, const float* __restrict__ bias, const float* __restrict__ mask, int64_t ldm, int kslice,
     int64_t zstride) {
-    __shared__ float As[BK][BM + 4];
-    __shared__ float Bs[BK][BN + 4];
+    __shared__ __align__(16) float As[BK][BM + 4];
+    __shared__ __align__(16) float Bs[BK][BN + 4];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
     // split-K: slice z covers k in [z kslice, (z + 1) kslice) and writes its own partial C
     const int k_lo = blockIdx.z * kslice, k_hi = min(K, k_lo + kslice);
     C += blockIdx.z * zstride;
-    float acc[4][4] = {};
+    float acc[8][8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
     for (int k0 = k_lo; k0 < k_hi; k0 += BK) {
-        // A tile: BM x BK
         for (int e = tid; e < BM * BK; e += kGemmThreads) {
             int ii, kk;
             if (sak == 1) { ii = e / BK; kk = e % BK; } else { kk = e / BM; ii = e % BM; }
@@ -47,28 +62,28 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_kernel(
             Bs[kk][jj] = (gk < k_hi && gj < N) ? Bm[gk * sbk + gj * sbj] : 0.f;
         }
         __syncthreads();
-#pragma unroll
+#pragma unroll 4
         for (int kk = 0; kk < BK; ++kk) {
-            float a[4], b[4];
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                a[q] = As[kk][ty * 4 + q];
-                b[q] = Bs[kk][tx * 4 + q];
-            }
+            for (int x = 0; x < 8; ++x)
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
-#pragma unroll
-                for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+                for (int y = 0; y < 8; y += 2) gffma2(a[x], b[y], b[y + 1], acc[x][y], acc[x][y + 1]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int x = 0; x < 4; ++x) {
-        const int gi = i0 + ty * 4 + x;
+    for (int x = 0; x < 8; ++x) {
+        const int gi = i0 + (x < 4 ? ty * 4 + x : 64 + ty * 4 + (x - 4));
         if (gi >= M) continue;
 #pragma unroll
-        for (int y = 0; y < 4; ++y) {
-            const int gj = j0 + tx * 4 + y;
+        for (int y = 0; y < 8; ++y) {
+            const int gj = j0 + (y < 4 ? tx * 4 + y : 64 + tx * 4 + (y - 4));
             if (gj >= N) continue;
             float v = acc[x][y];
             float* cp = C + gi * ldc + gj;
