@@ -237,7 +237,9 @@ DDF_API int ddf_query(ddf_net net, const float* d_origins, const float* d_dirs, 
  * launch in a list; here that list lives in a fixed static device array of the library
  * (4 MiB + 256 B per GPU that loads the library, held until exit), so such a query is limited
  * to n <= 2^20 rows and larger n returns DDF_ERR_INVALID_ARG. Queries without normals, FP32
- * queries and the analytic sphere use no scratch and take any n. The first call on each device
+ * queries (here the reverse pass for the normals runs inside the forward launch, on every tile
+ * of rows that holds a hit, instead of on a list of the hit rows: the same results) and the
+ * analytic sphere use no scratch and take any n. The first call on each device
  * looks the array's address up once (cudaGetSymbolAddress), so make that first call before any
  * stream capture. Every call on a device shares the array: calls whose work overlaps on the GPU
  * (different streams without ordering between them) race on it and must be serialised by the

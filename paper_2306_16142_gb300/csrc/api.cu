@@ -103,6 +103,7 @@ void free_net(ddf_net_s* n) {
     tc_free(n);
     cudaFree(n->master);
     cudaFree(n->master_t);
+    cudaFree(n->f32_hits);
     cudaFree(n->adam_m);
     cudaFree(n->adam_v);
     wn_free(n);

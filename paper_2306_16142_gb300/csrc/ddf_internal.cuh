@@ -93,6 +93,8 @@ struct ddf_net_s {
     float sphere_r = 0.f;
     float* master = nullptr;     // FP32 masters, blob layout (device)
     float* master_t = nullptr;   // per-layer transposed FP32 copies W^T [in][out] (device)
+    int* f32_hits = nullptr;     // FP32 path: hit count, then the hit-row list of a query with normals
+    int64_t f32_hit_cap = 0;
     bool master_t_stale = false;  // master_t predates the last optimiser step (rebuilt on FP32 use)
     ddf::TcPack* tc = nullptr;   // BF16 / FP8 working copy
     // Adam state
@@ -143,9 +145,11 @@ namespace ddf {
 // ------------------------------------------------------------------ FP32 SIMT MLP (mlp_simt.cu)
 // Forward of the whole network for rows [0, n) (n capped by *d_count when d_count != null),
 // writing dist / logit / hit and, for hit rows, the Eq. 3 normal.
+// compact: with normals, a forward launch that lists the hit rows and a normal launch over them
+// (the handle's hit-row buffer grows to n); otherwise one launch (nothing allocated).
 int mlp_fp32_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
                    const int* d_count, float* dist, float* logit, uint8_t* hit, float* normals,
-                   cudaStream_t stream);
+                   cudaStream_t stream, bool compact = true);
 int sphere_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
                  const int* d_count, float* dist, float* logit, uint8_t* hit, float* normals,
                  cudaStream_t stream);

@@ -54,6 +54,9 @@ struct MlpArgs {
     uint8_t* hit;
     float* normals;
     int kmax;          // max(width, E)
+    int* hit_list;     // forward launch feeding a normal launch: hit rows appended here (count at hit_count)
+    int* hit_count;
+    const int* rows;   // normal launch: the tile rows are these rows of o, w (count *d_count), all hits
 };
 
 // out[N][MT] = epi(sum_k in[k][MT] * B[k][n]) with B row-major K x N at Bg (row stride ldb).
@@ -202,7 +205,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fp32_kernel(const MlpArgs a) 
         for (int i = tid; i < 6 * MT; i += kThreads) {
             const int r = i / 6, c = i % 6;
             float v = 0.f;
-            if (r < rows) v = c < 3 ? a.o[(row0 + r) * 3 + c] : a.w[(row0 + r) * 3 + c - 3];
+            if (r < rows) {
+                const int64_t ri = a.rows ? (int64_t)a.rows[row0 + r] : row0 + r;
+                v = c < 3 ? a.o[ri * 3 + c] : a.w[ri * 3 + c - 3];
+            }
             rowv[c * MT + r] = v;
         }
         for (int i = tid; i < L * W * MW; i += kThreads) masks[i] = 0u;
@@ -251,11 +257,19 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fp32_kernel(const MlpArgs a) 
             }
             y0 += bo[0];
             y1 += bo[1];
-            my_hit = (tid < rows) && (y1 > 0.f);
-            if (tid < rows) {
+            // a normal launch's rows are the hits of the forward launch (the same arithmetic)
+            my_hit = (tid < rows) && (a.rows || y1 > 0.f);
+            if (tid < rows && a.dist) {
                 a.dist[row0 + tid] = y0;
                 if (a.logit) a.logit[row0 + tid] = y1;
                 if (a.hit) a.hit[row0 + tid] = (uint8_t)(y1 > 0.f);
+            }
+            if (a.hit_list) {   // one atomic per warp (MT is a multiple of 32)
+                const unsigned m = __ballot_sync(0xffffffffu, my_hit);
+                int base = 0;
+                if ((tid & 31) == 0 && m) base = atomicAdd(a.hit_count, __popc(m));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (my_hit) a.hit_list[base + __popc(m & ((1u << (tid & 31)) - 1u))] = (int)(row0 + tid);
             }
             flag[tid] = my_hit;   // reuse as per-row hit flags (MT <= kThreads)
         }
@@ -289,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fp32_kernel(const MlpArgs a) 
                 if (c < 3) g[c] = fmaf(nxt[f * MT + tid], encode_dfeature(f, v), g[c]);
             }
             const float3 nrm = normal_from_grad(g[0], g[1], g[2], v[3], v[4], v[5]);
-            float* np = a.normals + (row0 + tid) * 3;
+            float* np = a.normals + (a.rows ? (int64_t)a.rows[row0 + tid] : row0 + tid) * 3;
             np[0] = nrm.x;
             np[1] = nrm.y;
             np[2] = nrm.z;
@@ -387,12 +401,12 @@ int build_transposed(ddf_net_s* net, cudaStream_t stream) {
 
 int mlp_fp32_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,
                    const int* d_count, float* dist, float* logit, uint8_t* hit, float* normals,
-                   cudaStream_t stream) {
+                   cudaStream_t stream, bool compact) {
     if (net->master_t_stale) {   // trained since the transposed copy was made (on this stream)
         const int rc = build_transposed(const_cast<ddf_net_s*>(net), stream);
         if (rc) return rc;
     }
-    MlpArgs a;
+    MlpArgs a{};
     a.lay = net->lay;
     a.W = net->master;
     a.Wt = net->master_t;
@@ -405,9 +419,42 @@ int mlp_fp32_query(const ddf_net_s* net, const float* o, const float* w, int64_t
     a.hit = hit;
     a.normals = normals;
     a.kmax = std::max(net->lay.width, net->lay.E);
-    if (net->lay.width == 256) return launch<64, 256>(a, n, stream);
-    if (net->lay.width < 256) return launch<64, 128>(a, n, stream);
-    return launch<32, 128>(a, n, stream);
+    auto run = [&](const MlpArgs& x) {
+        if (net->lay.width == 256) return launch<64, 256>(x, n, stream);
+        if (net->lay.width < 256) return launch<64, 128>(x, n, stream);
+        return launch<32, 128>(x, n, stream);
+    };
+    if (!normals || !compact) return run(a);   // the reverse pass on every tile that holds a hit
+    // the forward appends the hit rows to a list; a second launch recomputes the forward pass and
+    // runs the reverse pass on those rows alone (a tile with any hit would otherwise run it on all
+    // of its rows)
+    ddf_net_s* mnet = const_cast<ddf_net_s*>(net);
+    if (mnet->f32_hit_cap < n) {
+        cudaFree(mnet->f32_hits);
+        mnet->f32_hits = nullptr;
+        mnet->f32_hit_cap = 0;
+        const int64_t cap = std::max<int64_t>(n, 1024);
+        DDF_CUDA_TRY(cudaMalloc(&mnet->f32_hits, sizeof(int) * (size_t)(cap + 64)));
+        mnet->f32_hit_cap = cap;
+    }
+    int* count = mnet->f32_hits;
+    int* list = mnet->f32_hits + 64;
+    DDF_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int), stream));
+    a.normals = nullptr;
+    a.hit_list = list;
+    a.hit_count = count;
+    int rc = run(a);
+    if (rc) return rc;
+    MlpArgs b = a;
+    b.hit_list = nullptr;
+    b.hit_count = nullptr;
+    b.rows = list;
+    b.d_count = count;
+    b.dist = nullptr;
+    b.logit = nullptr;
+    b.hit = nullptr;
+    b.normals = normals;
+    return run(b);
 }
 
 int sphere_query(const ddf_net_s* net, const float* o, const float* w, int64_t n,

@@ -3390,8 +3390,11 @@ extern "C" DDF_API int ddf_query_noalloc(ddf_net net, const float* d_origins, co
     if (n == 0) return DDF_OK;
     if (!d_origins || !d_dirs || !d_dist || !d_hit)
         return fail(DDF_ERR_INVALID_ARG, "origins, dirs, dist and hit must be non-NULL");
-    // The sphere field, the FP32 path and a tensor-core query without normals use no scratch.
-    if (net->is_sphere || net->precision == DDF_FP32 || !d_normals)
+    // The sphere field, the FP32 path (its normals in the forward launch, on every tile that holds a
+    // hit) and a tensor-core query without normals use no scratch.
+    if (!net->is_sphere && net->precision == DDF_FP32)
+        return mlp_fp32_query(net, d_origins, d_dirs, n, nullptr, d_dist, d_logit, d_hit, d_normals, stream, false);
+    if (net->is_sphere || !d_normals)
         return field_query(net, d_origins, d_dirs, n, nullptr, d_dist, d_logit, d_hit, d_normals, stream);
     // Only the hit-row list of a tensor-core query with normals lives in the static array.
     if (n > kNoAllocMaxRows)

@@ -1,7 +1,9 @@
-"""The BF16 query with normals at widths 128 / 256 through ddf_query and through
-ddf_query_noalloc (the same forward and normal launches, the hit-row list in the library's static
-array instead of the handle's): the outputs, normals included, are equal bit for bit, on two calls
-in a row and on ragged tiles of hit rows."""
+"""The query with normals through ddf_query and through ddf_query_noalloc: BF16 at widths 128 / 256
+(the same forward and normal launches, the hit-row list in the library's static array instead of
+the handle's) and FP32 (ddf_query lists the hit rows and runs the reverse pass on them alone, the
+allocation-free form runs it inside the forward launch on every tile that holds a hit). The
+outputs, normals included, are equal bit for bit, on two calls in a row and on ragged tiles of
+hit rows."""
 
 import ctypes as C
 
@@ -30,9 +32,11 @@ def _call(lib, fn, net, o, w):
     return out
 
 
-@pytest.mark.parametrize("shape", [(12, 256, 8, 2), (0, 128, 6, 9), (16, 256, 3, 4)])
+@pytest.mark.parametrize("precision,shape", [("bf16", (12, 256, 8, 2)), ("bf16", (0, 128, 6, 9)),
+                                             ("bf16", (16, 256, 3, 4)), ("fp32", (12, 256, 8, 2)),
+                                             ("fp32", (0, 128, 6, 9))])
 @pytest.mark.parametrize("n", [5000, 70001])
-def test_query_and_noalloc_agree_bit_for_bit(shape, n):
+def test_query_and_noalloc_agree_bit_for_bit(precision, shape, n):
     ensure_built()
     import paper_2306_16142_gb300 as P
     lib = P.load()
@@ -44,7 +48,7 @@ def test_query_and_noalloc_agree_bit_for_bit(shape, n):
     os_, ws_ = rays_in_ball(4096, seed=seed + 100)
     lg = omlp.query(omlp.unpack(blob, F, W, L), os_, ws_, F, with_normal=False)["logit"]
     blob[-1] -= np.float32(np.quantile(lg, 0.6))
-    net = P.DDFNet(F, W, L, blob, "bf16")
+    net = P.DDFNet(F, W, L, blob, precision)
     o, w = [torch.from_numpy(x).cuda() for x in rays_in_ball(n, seed=seed + 100)]
     first = _call(lib, "ddf_query", net, o, w)
     again = _call(lib, "ddf_query", net, o, w)            # the second call reuses the buffers
