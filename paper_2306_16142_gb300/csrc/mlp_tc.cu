@@ -2,16 +2,19 @@
 // FP32 accumulators in tensor memory, fed by TMA. (MLP_w of Sec. 4.1; normals by the gradient of
 // Eq. 3 / Sec. 4.2.)
 //
-// Every kernel here is persistent (one CTA per SM) with 320 threads split by role: one warp
-// streams weight K-blocks into a ring of shared-memory stages with TMA, one thread of another
-// warp issues tcgen05.mma, and eight epilogue warps (thread = row = TMEM lane, two column
-// groups) read the accumulators with tcgen05.ld and write the next layer's A operand straight
-// into the swizzled K-major shared-memory tile, releasing it one K-block at a time so the next
-// layer's MMAs start while the rest is still being written. The 2-unit output head runs on CUDA
-// cores in FP32.
-//   mlp_pair_kernel<W, GRP>   the forward query (W = 128, 256): two 128-row tiles per CTA share
+// Every kernel here is persistent (one CTA per SM) and split by role: one warp streams weight
+// K-blocks into a ring of shared-memory stages with TMA, one thread issues tcgen05.mma (one per
+// tile in the pair kernels, 352 threads; one in all in the width-512 kernels, 320 threads), and
+// eight epilogue warps (thread = row = TMEM lane, two column groups) read the accumulators with
+// tcgen05.ld and write the next layer's A operand straight into the swizzled K-major
+// shared-memory tile, releasing it K-block by K-block so the next layer's MMAs start while the
+// rest is still being written. The 2-unit output head runs on CUDA cores in FP32.
+//   mlp_pair_kernel<W, GRP, TRAIN>
+//                             the forward query (W = 128, 256): two 128-row tiles per CTA share
 //                             every weight stage, each layer's bias enters through one MMA;
-//                             GRP = true serves grouped launches of many networks;
+//                             GRP = true serves grouped launches of many networks, TRAIN = true
+//                             the forward of a training step;
+//   mlp_pairb_kernel<W>       the data-gradient chain of a training step on tile pairs;
 //   mlp_pairn_kernel<W>       the normals of the hit rows (W = 128, 256) on tile pairs: the
 //                             forward pass again (ReLU masks to a per-SM scratch in L2), then the
 //                             reverse pass with the transposed weights through the same ring, the
@@ -589,10 +592,12 @@ struct PairInfo {
     const float* head;
 };
 
-// TRAIN: the forward pass of a training step. The head is skipped; the encoded input a_0 and the
-// hidden activations a_1 .. a_{L-1} are written to the workspace by TMA stores of the on-chip A
-// tiles (issued by the MMA thread once every epilogue warp has released the K-block), a_L and the
-// ReLU masks of a_1 .. a_{L-1} by the epilogue.
+// TRAIN: the forward pass of a training step. The encoded input a_0 and the hidden activations
+// a_1 .. a_{L-1} are written to the workspace by TMA stores of the on-chip A tiles (issued by the
+// MMA thread once every epilogue warp has released the K-block) and the ReLU masks of
+// a_1 .. a_{L-1} by the epilogue. The last layer either runs the output layer itself (a.th.delta:
+// the loss form of the two-output head, see train_head below) or writes a_L for the output-layer
+// kernel.
 template <int W, bool GRP, bool TRAIN>
 __global__ void __launch_bounds__(kThreadsP, 1)
     mlp_pair_kernel(const __grid_constant__ CUtensorMap mapF, const __grid_constant__ CUtensorMap mapA0,
