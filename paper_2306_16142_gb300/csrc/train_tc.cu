@@ -4,21 +4,25 @@
 //
 //   forward  a_{l+1} = ReLU(a_l W_l^T + b_l)          A = a_l      [m][K_l]   B = W_l   [W][K_l]
 //   head     y = a_L W_out^T + b_out, the loss, G = dLoss/dy and
-//            delta_{L-1} = (G W_out) * 1[a_L > 0]      (epilogue of the last forward GEMM)
+//            delta_{L-1} = (G W_out) * 1[a_L > 0]
 //   dgrad    delta_{l-1} = (delta_l W_l) * 1[a_l > 0] A = delta_l  [m][W]     B = W_l^T [K_l][W]
 //   wgrad    dW_l = delta_l^T a_l                     A = delta_l^T [W][m]    B = a_l^T [K_l][m]
 //            (K = the batch: split over CTAs, partials summed in a fixed order)
 //
-// One persistent kernel serves all four: per CTA a TMA producer warp, an MMA warp (one thread
-// issues M = 128, N = BN, K = 16 MMAs into one of two TMEM accumulators, so a tile's epilogue
-// overlaps the next tile's MMAs) and eight epilogue warps (two column halves x four TMEM lane
-// quadrants; thread = row). Activations and deltas are written once, row-major BF16: the next
-// forward / dgrad GEMM reads them K-major, and the wgrad reads the same arrays as MN-major
-// operands (its K is the batch), so no transposed copy is ever made. Epilogue stores go through
-// a swizzled 32 x 32 block per warp in shared memory so that each store instruction writes whole
-// sectors. ReLU masks are kept as bits; bias gradients and the output layer's gradients are
-// per-32-row partial sums taken in the same epilogues and reduced in a fixed order afterwards,
-// so a step is bit-reproducible.
+// For widths 128 / 256 with K0 <= 128 the step runs as fused persistent kernels: the forward on
+// tile pairs (the query's pair kernel in its training form; the loss form of the two-output head
+// folded into its last layer), the data-gradient chain on tile pairs (mlp_pairb_kernel, every
+// delta kept on chip as the next step's A operand), all layers' weight gradients in one launch
+// (wgrad_all_kernel, which also takes the deltas' column sums, the bias gradients, from its
+// operand stages), their split sums (wsum_all_kernel), the fixed-order bias-gradient stages and
+// one launch for the loss, Adam and the repacking (adam_pack_kernel). Other shapes use the one
+// persistent GEMM kernel below for every contraction: per CTA a TMA producer warp, an MMA warp
+// (one thread issues M = 128, N = BN, K = 16 MMAs into one of two TMEM accumulators, so a tile's
+// epilogue overlaps the next tile's MMAs) and eight epilogue warps (two column halves x four TMEM
+// lane quadrants; thread = row). Either way activations and deltas are written once, row-major
+// BF16: the forward / dgrad read them K-major, and the wgrad reads the same arrays as MN-major
+// operands (its K is the batch), so no transposed copy is ever made. ReLU masks are kept as bits;
+// every gradient sum is a fixed-order reduction of partials, so a step is bit-reproducible.
 #include <math.h>
 
 #include <algorithm>
