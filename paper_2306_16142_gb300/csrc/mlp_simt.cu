@@ -117,7 +117,7 @@ __device__ void gemm_layer(const float* __restrict__ Bg, int ldb, int K, int N,
             const float* Wc = NB == 2 ? Ws + (chunk & 1) * KC * NC : Ws;
             if (NB == 2 && k0 + KC < K) issue_chunk(k0 + KC, Ws + ((chunk + 1) & 1) * KC * NC);
             const int kn = min(KC, K - k0);
-#pragma unroll 4
+#pragma unroll 16
             for (int kk = 0; kk < kn; ++kk) {
                 float a[TR], b[TC];
                 const float* ap = in + (k0 + kk) * MT + ty * TR;
