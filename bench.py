@@ -67,6 +67,13 @@ QUERY_DRAM_BYTES_PER_FWD_ROW = (203441920 + 51336960) / 8388608
 QUERY_DRAM_BYTES_PER_NRM_ROW = (40118784 + 855296) / 1265231
 
 
+def query_traffic_per_bounce(stats, bounces):
+    """DRAM bytes of the BF16 query launches per bounce query: forward rows are every bounce's live
+    rays, normal rows the hits, i.e. the next bounce's rays."""
+    render_bytes = QUERY_DRAM_BYTES_PER_FWD_ROW * sum(stats) + QUERY_DRAM_BYTES_PER_NRM_ROW * sum(stats[1:])
+    return render_bytes / bounces
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -484,9 +491,7 @@ def main():
     # ---- dominant kernel roofline: the field query
     roof = query_roofline(stats, prof, ms, E, w["hidden"], w["layers"], prec, peaks, peak_src, meas, args.steps)
     if prec == "bf16":
-        # forward rows: every bounce's live rays; normal rows: the hits, i.e. the next bounce's rays
-        render_bytes = QUERY_DRAM_BYTES_PER_FWD_ROW * sum(stats) + QUERY_DRAM_BYTES_PER_NRM_ROW * sum(stats[1:])
-        roof["traffic"] = render_bytes / w["bounces"]
+        roof["traffic"] = query_traffic_per_bounce(stats, w["bounces"])
         roof["traffic_unit"] = ("bytes per bounce query (forward + normals launches), the per-row DRAM bytes of "
                                 "one ncu capture of each kernel times this render's rows")
 
